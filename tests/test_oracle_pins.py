@@ -1,0 +1,322 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- a library routine, a closed form, a hand-worked example, an
+invariant of the paper, or brute force -- so that a dropped term, a sign or
+index error, or a transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_2310_09417_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ random numbers
+@pytest.mark.parametrize("ctr,key", [
+    ([0, 0, 0, 0], [0, 0]),
+    ([1, 2, 3, 4], [5, 6]),
+    ([2**64 - 1, 2**64 - 1, 2**64 - 1, 2**64 - 1], [2**64 - 1, 2**64 - 1]),
+    ([123456789, 987654321, 0, 0], [2310_09417, 0]),
+])
+def test_philox_matches_numpy_library(orc, ctr, key):
+    """Philox4x64-10 (Salmon et al. 2011) against numpy's independent
+    implementation; numpy's first output block uses counter + 1."""
+    c = np.array(ctr, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    prev = c.copy()
+    # numpy increments the 256-bit counter before generating the first block
+    borrow = True
+    for i in range(4):
+        if borrow:
+            borrow = prev[i] == 0
+            prev[i] = prev[i] - np.uint64(1) if prev[i] != 0 else np.uint64(2**64 - 1)
+    ref = np.random.Philox(counter=prev, key=k).random_raw(4)
+    assert np.array_equal(orc.philox4x64_10(c, k), ref)
+
+
+def test_gaussian_rows_moments(orc):
+    """Box-Muller output is N(0,1): mean 0, variance 1, kurtosis 3, no
+    correlation between rows or between neighbouring entries."""
+    Z = orc.gaussian_rows(7, 0, 64, 8192)
+    z = Z.ravel()
+    n = z.size
+    assert abs(z.mean()) < 5 / np.sqrt(n)
+    assert abs(z.var() - 1) < 5 * np.sqrt(2 / n)
+    assert abs(np.mean(z ** 4) - 3) < 5 * np.sqrt(96 / n)
+    C = np.corrcoef(Z)
+    off = C[~np.eye(64, dtype=bool)]
+    assert np.abs(off).max() < 6 / np.sqrt(8192)
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) < 5 / np.sqrt(n)
+
+
+def test_gaussian_rows_counter_addressing(orc):
+    """Row i of the sketching matrix depends only on (seed, i): a window drawn
+    at an offset equals the same rows of a larger draw."""
+    big = orc.gaussian_rows(11, 0, 40, 130)
+    win = orc.gaussian_rows(11, 17, 9, 130)
+    assert np.array_equal(big[17:26], win)
+    assert not np.array_equal(orc.gaussian_rows(12, 0, 1, 130), big[:1])
+
+
+# ------------------------------------------------------------ sketch / norms
+def test_sketch_matches_matmul(orc):
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((37, 23))
+    Om = rng.standard_normal((5, 37))
+    YT = orc.sketch_t(A, Om)
+    np.testing.assert_allclose(YT, (Om @ A).T, rtol=1e-13, atol=1e-13)
+
+
+def test_norms_and_residual_match_numpy(orc):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((31, 19))
+    assert orc.fro_norm(A) == pytest.approx(np.linalg.norm(A), rel=1e-14)
+    J = np.array([4, 0, 11])
+    X = rng.standard_normal((3, 19))
+    ref = np.linalg.norm(A - A[:, J] @ X)
+    assert orc.id_residual(A, J, X) == pytest.approx(ref, rel=1e-13)
+    Q, _ = np.linalg.qr(A[:, J])
+    assert orc.stable_residual(A, J) == pytest.approx(np.linalg.norm(A - Q @ (Q.T @ A)), rel=1e-11)
+
+
+# ------------------------------------------------------------ LUPP
+def test_lupp_hand_worked_example(orc):
+    g = json.load(open(os.path.join(GOLDEN, "lupp_4x3_hand.json")))
+    M = np.array(g["M"], dtype=float)
+    LU, perm, z = orc.lupp(M)
+    assert z == 0
+    assert perm.tolist() == g["perm"]
+    L = np.tril(LU, -1)[:, :3] + np.eye(4, 3)
+    U = np.triu(LU[:3])
+    np.testing.assert_allclose(L, np.array(g["L"]), atol=1e-15)
+    np.testing.assert_allclose(U, np.array(g["U"]), atol=1e-14)
+
+
+def test_fixed_rank_hand_worked_example(orc):
+    """Same example as a column ID: Omega = I (3 x 3), A = M^T (3 x 4), k = 2."""
+    g = json.load(open(os.path.join(GOLDEN, "lupp_4x3_hand.json")))
+    A = np.array(g["M"], dtype=float).T
+    r = orc.id_fixed_rank(A, np.eye(3), g["k"])
+    assert r["J"].tolist() == g["J"]
+    np.testing.assert_allclose(r["X"], np.array(g["X"]), atol=1e-15)
+    assert r["est"] == pytest.approx(g["est"], rel=1e-14)
+
+
+@pytest.mark.parametrize("shape", [(60, 17), (17, 17), (200, 40), (9, 30)])
+def test_lupp_matches_lapack_getrf(orc, shape):
+    """Partial pivoting on Gaussian data has no ties, so the textbook LUPP is
+    LAPACK's getrf (scipy.linalg.lu): same permutation, same L and U."""
+    rng = np.random.default_rng(shape[0] * 100 + shape[1])
+    M = rng.standard_normal(shape)
+    LU, perm, _ = orc.lupp(M)
+    P, L, U = sla.lu(M)
+    kk = min(shape)
+    assert np.array_equal(np.argmax(P, axis=0), perm)
+    np.testing.assert_allclose(np.tril(LU, -1)[:, :kk] + np.eye(shape[0], kk), L, atol=1e-13)
+    np.testing.assert_allclose(np.triu(LU[:kk]), U, atol=1e-12)
+
+
+def test_lupp_invariants(orc):
+    """PA = LU to O(u)||A||, unit diagonal, |L| <= 1 (Eq. lupp)."""
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((300, 50)) * np.logspace(0, -6, 50)
+    LU, perm, _ = orc.lupp(M)
+    L = np.tril(LU, -1)[:, :50] + np.eye(300, 50)
+    U = np.triu(LU[:50])
+    assert np.abs(L).max() <= 1.0
+    err = np.linalg.norm(M[perm] - L @ U) / np.linalg.norm(M)
+    assert err < 50 * np.finfo(float).eps
+
+
+def test_lupp_chan_matrix_ties(orc):
+    """Chan's matrix (Appendix): every pivot column ties at |1| = |-1|; with ties
+    going to the smallest label no row moves and the factors are L = A, U = I."""
+    n = 12
+    A = W.chan(n)
+    LU, perm, _ = orc.lupp(A)
+    assert perm.tolist() == list(range(n))
+    np.testing.assert_array_equal(np.tril(LU, -1) + np.eye(n), A)
+    np.testing.assert_array_equal(np.triu(LU), np.eye(n))
+
+
+def test_lupp_growth_factor_closed_form(orc):
+    """Chan's matrix with a last column of ones (Wilkinson's example) reaches
+    the growth bound rho = 2^(n-1) of Sec. 2.3.2 exactly: U(j, n-1) = 2^j."""
+    n = 20
+    A = W.chan(n)
+    A[:, -1] = 1.0
+    LU, _, _ = orc.lupp(A)
+    np.testing.assert_array_equal(np.diag(LU)[:-1], np.ones(n - 1))
+    np.testing.assert_array_equal(LU[np.arange(n), n - 1], 2.0 ** np.arange(n))
+
+
+def test_lupp_zero_column_is_skipped(orc):
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((10, 4))
+    M[:, 1] = 0.0
+    M[:, 2] = M[:, 0]  # column 2 becomes exactly zero after step 1
+    LU, perm, z = orc.lupp(M)
+    assert z == 2
+    L = np.tril(LU, -1)[:, :4] + np.eye(10, 4)
+    U = np.triu(LU[:4])
+    np.testing.assert_allclose(M[perm], L @ U, atol=1e-14)
+
+
+# ------------------------------------------------------------ column ID
+def test_exact_recovery_rank_r(orc):
+    """A = B C of rank r, k = r: X(:,J^c) = C_J^{-1} C_{J^c} independent of Omega
+    (X = (Omega A)_J^{-1} (Omega A) = C_J^{-1} C), and the residual and the
+    Schur estimate vanish to rounding."""
+    m, n, r = 80, 60, 7
+    A, B, Cf = W.low_rank(m, n, r, seed=5)
+    Om = W.gaussian_omega(6, r + 4, m)
+    res = orc.id_fixed_rank(A, Om, r)
+    J = res["J"]
+    Xref = np.linalg.solve(Cf[:, J], Cf)
+    np.testing.assert_allclose(res["X"], Xref, atol=1e-10)
+    np.testing.assert_allclose(res["X"][:, J], np.eye(r), atol=0)
+    nA = np.linalg.norm(A)
+    assert orc.id_residual(A, J, res["X"]) < 1e-12 * nA
+    assert res["est"] < 1e-12 * nA
+
+
+def test_brute_force_best_skeleton_tiny(orc):
+    """On tiny inputs: SVD tail <= best k-subset projection error <= the method's
+    stable ID error <= its ID error (Sec. 2.2, Eq. sID_row, Eckart-Young)."""
+    for seed in range(6):
+        rng = np.random.default_rng(100 + seed)
+        m, n, k = 9, 7, 3
+        A = rng.standard_normal((m, n)) @ np.diag(0.3 ** np.arange(n)) @ rng.standard_normal((n, n))
+        sv = np.linalg.svd(A, compute_uv=False)
+        tail = np.sqrt(np.sum(sv[k:] ** 2))
+        best = np.inf
+        for S in itertools.combinations(range(n), k):
+            Q, _ = np.linalg.qr(A[:, list(S)])
+            best = min(best, np.linalg.norm(A - Q @ (Q.T @ A)))
+        r = orc.id_fixed_rank(A, W.gaussian_omega(seed, k + 2, m), k)
+        st = orc.stable_residual(A, r["J"])
+        idr = orc.id_residual(A, r["J"], r["X"])
+        eps = 1e-12 * np.linalg.norm(A)
+        assert tail <= best + eps
+        assert best <= st + eps
+        assert st <= idr + eps
+
+
+def test_schur_estimate_is_unbiased(orc):
+    """E_Omega[E^2] = ||A - A(:,J) X||_F^2 (Sec. 4.2) for N(0,1) estimation
+    blocks with E = ||S||_F / sqrt(b): the mean ratio over many independent
+    draws is 1 within sampling error (the relative sd of one ratio <= sqrt(2/b))."""
+    m, n, k, b = 120, 90, 10, 8
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=10.0), seed=7)
+    ratios = []
+    for seed in range(300):
+        Om = W.gaussian_omega(1000 + seed, k + b, m)
+        r = orc.id_fixed_rank(A, Om, k)
+        true = orc.id_residual(A, r["J"], r["X"])
+        ratios.append(r["est"] ** 2 / true ** 2)
+    mean = float(np.mean(ratios))
+    sd = float(np.std(ratios) / np.sqrt(len(ratios)))
+    assert abs(mean - 1.0) < 4 * sd + 0.02, (mean, sd)
+    assert sd < 0.05
+
+
+def test_adaptive_equals_fixed_rank_with_same_rows(orc):
+    """randLUPPadap is randLUPP with the same total sketch (Sec. 5.2): same J,
+    same X and the same final estimate."""
+    m, n, b = 300, 200, 16
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=8)
+    Om = W.gaussian_omega(9, orc.rows_needed(n, b), m)
+    ad = orc.id_adaptive(A, Om, b, 1e-6 * np.linalg.norm(A))
+    k = ad["k"]
+    assert k % b == 0 and ad["status"] == 0
+    fx = orc.id_fixed_rank(A, Om[: k + b], k)
+    assert np.array_equal(ad["J"], fx["J"])
+    np.testing.assert_allclose(ad["X"], fx["X"], rtol=0, atol=1e-12)
+    assert ad["trace"][-1] == pytest.approx(fx["est"], rel=1e-12)
+
+
+def test_adaptive_stopping_rule(orc):
+    """Algorithm 1 stops at the first round whose estimate is <= tol and the
+    rank it returns is the one that estimate certifies; every earlier estimate
+    exceeded tol; the estimate tracks the true error of each prefix rank."""
+    m, n, b = 400, 250, 10
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=25.0), seed=10)
+    Om = W.gaussian_omega(11, orc.rows_needed(n, b), m)
+    tol = 1e-5 * np.linalg.norm(A)
+    ad = orc.id_adaptive(A, Om, b, tol)
+    tr = ad["trace"]
+    assert tr[-1] <= tol and np.all(tr[:-1] > tol)
+    assert ad["k"] == b * len(tr)
+    for t, e in enumerate(tr):
+        kk = b * (t + 1)
+        fx = orc.id_fixed_rank(A, Om[: kk + b], kk)
+        true = orc.id_residual(A, fx["J"], fx["X"])
+        assert 0.25 < e / true < 4.0
+    # the SVD tail lower-bounds the achieved error (Eckart-Young)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert np.sqrt(np.sum(sv[ad["k"]:] ** 2)) <= orc.id_residual(A, ad["J"], ad["X"]) * (1 + 1e-9)
+
+
+def test_permutation_equivariance(orc):
+    """Relabelling the columns of A relabels J and the columns of X (the sketch
+    of A(:,pi) is Y(:,pi); ties do not occur on Gaussian data)."""
+    m, n, k = 70, 50, 9
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=12)
+    Om = W.gaussian_omega(13, k + 3, m)
+    pi = np.random.default_rng(14).permutation(n)
+    r1 = orc.id_fixed_rank(A, Om, k)
+    r2 = orc.id_fixed_rank(A[:, pi], Om, k)
+    assert np.array_equal(pi[r2["J"]], r1["J"])
+    np.testing.assert_allclose(r2["X"], r1["X"][:, pi], atol=1e-12)
+
+
+def test_scale_invariance(orc):
+    m, n, k = 60, 40, 6
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=15)
+    Om = W.gaussian_omega(16, k + 4, m)
+    r1 = orc.id_fixed_rank(A, Om, k)
+    r2 = orc.id_fixed_rank(A * 2.0 ** -20, Om, k)
+    assert np.array_equal(r1["J"], r2["J"])
+    np.testing.assert_array_equal(r1["X"], r2["X"])
+    assert r2["est"] == pytest.approx(r1["est"] * 2.0 ** -20, rel=1e-15)
+
+
+def test_rank_cap_and_full_rank(orc):
+    """When the tolerance cannot be met the run stops at min(m, n, kmax) with
+    TOL_NOT_MET; at k = n every column is a skeleton and X is a permutation."""
+    m, n, b = 50, 30, 8
+    A = np.random.default_rng(17).standard_normal((m, n))
+    Om = W.gaussian_omega(18, orc.rows_needed(n, b), m)
+    r = orc.id_adaptive(A, Om, b, 0.0, kmax=20)
+    assert r["k"] == 20 and r["status"] == orc.TOL_NOT_MET
+    r = orc.id_adaptive(A, Om, b, 0.0)
+    assert r["k"] == n and r["status"] == orc.OK
+    assert sorted(r["J"].tolist()) == list(range(n))
+    np.testing.assert_array_equal(r["X"][:, r["J"]], np.eye(n))
+
+
+def test_nonfinite_input_rejected(orc):
+    A = np.ones((5, 4))
+    A[2, 3] = np.nan
+    with pytest.raises(ValueError):
+        orc.id_fixed_rank(A, np.ones((3, 5)), 2)
+
+
+def test_kahan_and_fast_decay_estimate_tracks_error(orc):
+    """Sec. 5.1 test matrices (reduced size): the Schur estimate overlaps the
+    true ID error and the ID error is at least the stable ID error."""
+    for A in (W.kahan(160), W.spectral_matrix(160, 160, W.spectrum("fast_decay", 160), seed=19)):
+        m, n = A.shape
+        b = 8
+        Om = W.gaussian_omega(20, orc.rows_needed(n, b), m)
+        ad = orc.id_adaptive(A, Om, b, 1e-8 * np.linalg.norm(A))
+        true = orc.id_residual(A, ad["J"], ad["X"])
+        st = orc.stable_residual(A, ad["J"])
+        assert st <= true * (1 + 1e-9)
+        if ad["k"] < n:
+            assert 0.1 < ad["trace"][-1] / true < 10

@@ -1,0 +1,178 @@
+/*
+ * randid.h -- C ABI of the GB300 (sm_103a) randomized column interpolative
+ * decomposition library.
+ *
+ * Method: Pearce, Chen, Dong, Martinsson, "Adaptive Parallelizable Algorithms
+ * for Interpolative Decompositions via Partially Pivoted LU", arXiv:2310.09417.
+ * Given A (m x n) the library returns a column skeleton J (|J| = k) and an
+ * interpolation matrix X (k x n) with A ~ A(:,J) X, X(:,J) = I_k (Sec. 2.2.1,
+ * column ID).  Skeletons come from LU with partial pivoting (Sec. 2.3.2) of the
+ * transposed Gaussian sketch Y^T = (Omega A)^T (Sec. 2.4, Sec. 3.1); the
+ * adaptive driver grows the sketch block by block and stops when the
+ * Schur-complement estimate of Eq. errSch falls below the tolerance
+ * (Algorithm 1, Sec. 4).  The paper states the method as a row ID; the
+ * column ID computed here is the row ID of A^T.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major (LAPACK convention) with an explicit leading
+ *     dimension.  Every data pointer is a DEVICE pointer owned by the caller,
+ *     unless a field says HOST.
+ *   - Indices are 0-based int64 (the paper is 1-based).
+ *   - The library allocates no device memory: the caller passes a workspace of
+ *     at least the size the matching *_workspace_size query returns, aligned to
+ *     256 bytes.  The workspace may be reused between calls, not shared by calls
+ *     that run concurrently.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every entry
+ *     point enqueues its work on `stream` and returns after that work has
+ *     finished (the adaptive driver needs the stop decision on the host), so
+ *     outputs are ready when the call returns.
+ *   - Return value: ID_OK (0), a positive warning bit set, or a negative error.
+ *     -i means argument i (1-based) is invalid; nothing was launched.
+ *   - Ties in the pivot search go to the smallest column index of A.  An
+ *     exactly zero pivot column is skipped as LAPACK getrf does (zero
+ *     multipliers) and reported with ID_WARN_ZERO_PIVOT.
+ *   - The error estimate uses N(0,1) sketch rows and E = ||S||_F / sqrt(b):
+ *     the paper's "standard deviation 1/b" (Sec. 3.2, Sec. 5.1) is read as
+ *     variance 1/b, the scaling under which E^2 is unbiased for
+ *     ||A - A(:,J) X||_F^2 (Sec. 4.2).
+ */
+#ifndef RANDID_H
+#define RANDID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define ID_OK 0
+#define ID_WARN_TOL_NOT_MET 1  /* rank cap (k_max or min(m,n)) reached with E > tol */
+#define ID_WARN_ZERO_PIVOT 2   /* an exactly zero pivot column was met */
+#define ID_ERR_NONFINITE (-101) /* A holds NaN or Inf (checked before factoring) */
+#define ID_ERR_CUDA (-102)      /* a CUDA runtime call failed */
+#define ID_ERR_TIMEOUT (-103)   /* a bounded device-side wait gave up */
+#define ID_ERR_WORKSPACE (-104) /* workspace NULL, misaligned or too small */
+#define ID_ERR_UNSUPPORTED (-105) /* dtype / precision combination not built */
+
+/* ---------------------------------------------------------------- types */
+typedef enum {
+  ID_F64 = 0,
+  ID_F32 = 1,
+  ID_BF16 = 2,
+  ID_FP8_E4M3 = 3
+} id_dtype;
+
+/* An input matrix: DEVICE data, column-major m x n, leading dimension ld >= m. */
+typedef struct {
+  const void* data;
+  id_dtype dtype;
+  int64_t m, n, ld;
+  /* ID_FP8_E4M3 only: one FP32 scale per 128-row block of each column,
+     column-major ceil(m/128) x n (ld = ceil(m/128)); the value of entry (i,j)
+     is fp8(i,j) * block_scale[i/128 + j*ceil(m/128)].  NULL otherwise. */
+  const float* block_scale;
+} id_matrix;
+
+typedef struct {
+  id_dtype sketch_prec; /* inputs of the sketch GEMM: F64, F32, BF16, FP8_E4M3 */
+  id_dtype lu_prec;     /* Schur complement, LUPP and X: F64 or F32 */
+  int64_t block;        /* b, rows of each sketch block (Algorithm 1); default 64 */
+  double tol;           /* tau */
+  int tol_relative;     /* 1: stop when E <= tol * ||A||_F; 0: E <= tol (Algorithm 1) */
+  int64_t k_max;        /* capacity of J and X; rank never exceeds min(m, n, k_max) */
+  int64_t k0;           /* rows of the first sketch pass (a rank guess, e.g. from the
+                           learned predictor); 0 = one block.  Same J, X, k as k0 = 0. */
+  int64_t blocks_per_pass; /* sketch blocks drawn per later pass over A; 0 = 1 */
+  uint64_t seed;        /* key of the Philox4x64-10 generator of Omega */
+  /* Optional caller-supplied sketching matrix: DEVICE, row-major omega_rows x m
+     with row stride ld_omega >= m, dtype lu_prec.  Block t uses rows
+     [t*b, t*b+b); omega_rows must cover every row the run may draw.
+     NULL = generate from `seed`. */
+  const void* omega;
+  int64_t ld_omega, omega_rows;
+  int profile;          /* 1: time each phase with CUDA events (id_result.phase_ms) */
+} id_opts;
+
+/* Phases reported in id_result.phase_ms / phase_launches. */
+enum {
+  ID_PHASE_OMEGA = 0,  /* generate Gaussian rows */
+  ID_PHASE_SKETCH = 1, /* Y = Omega A (GEMM) and its split-K reduction */
+  ID_PHASE_SCHUR = 2,  /* S = (PY)_2 - L2 L1^{-1} (PY)_1 and ||S||_F^2 */
+  ID_PHASE_LU = 3,     /* LUPP of S */
+  ID_PHASE_UPDATE = 4, /* interpolation-matrix update, re-blocking */
+  ID_PHASE_OTHER = 5,  /* norm, checks, finalisation */
+  ID_NUM_PHASES = 6
+};
+
+typedef struct {
+  int64_t k;        /* HOST out: rank of the ID */
+  int64_t* J;       /* DEVICE out: int64[k_max] (k used) column skeletons in pivot order */
+  void* X;          /* DEVICE out: lu_prec, k_max x n column-major, leading dim ldx >= k_max;
+                       rows 0..k-1 hold X, X(:,J) = I_k; rows >= k are unspecified */
+  int64_t ldx;
+  double* pivots;   /* optional DEVICE out: double[k_max], |U(i,i)| of the LUPP */
+  double* est_trace;/* optional HOST out: E^(t) for t = 1, 2, ... (trace_cap entries) */
+  int64_t trace_cap;
+  double est_err;   /* HOST out: last estimate E (0 when k = n) */
+  double norm_A;    /* HOST out: ||A||_F */
+  int32_t rounds;   /* HOST out: estimates computed (Algorithm 1 loop trips) */
+  int32_t passes;   /* HOST out: sketch passes over A */
+  int64_t launches; /* HOST out: kernels launched by this call */
+  double phase_ms[ID_NUM_PHASES];      /* HOST out when opts->profile */
+  int64_t phase_launches[ID_NUM_PHASES];
+} id_result;
+
+/* ---------------------------------------------------------------- entry points */
+
+/* Workspace bytes for id_fixed_rank (l > 0: sketch rows) or id_adaptive (l = 0).
+   Returns ID_OK or -i for an invalid argument. */
+int id_workspace_size(const id_matrix* A, const id_opts* opts, int64_t l, size_t* bytes);
+
+/* randLUPP, fixed rank (Sec. 3.1; dong2022 Algorithm 2 as the paper cites it):
+   Y = Omega(0:l,:) A, LUPP of Y^T, J = the first k pivots, X = [I, (L2 L1^{-1})^T]
+   permuted back (Eq. inty).  If l > k the l-k extra rows give the Schur estimate
+   E = ||S||_F / sqrt(l-k) of the rank-k ID (Eq. errSch) in out->est_err.
+   Requires 1 <= k <= min(m, n, l); out->X needs ldx >= k. */
+int id_fixed_rank(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts,
+                  void* ws, size_t ws_bytes, id_result* out, void* stream);
+
+/* randLUPPadap (Algorithm 1, Sec. 4): blocks of b sketch rows; each round forms
+   S = (P Y)(tb+1:,:) - L2 L1^{-1} (P Y)(1:tb,:) for a fresh block, stops when
+   E = ||S||_F / sqrt(b) <= tau (returning k = tb, the rank E certifies), else
+   factors S by LUPP and re-blocks.  The minimum rank is min(b, cap); at
+   k = min(m, n, k_max) with E > tau it returns ID_WARN_TOL_NOT_MET. */
+int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_bytes,
+                id_result* out, void* stream);
+
+/* Batched adaptive IDs (the paper's future-work item 3, Sec. 6): `count`
+   independent problems A[i] (HOST array of descriptors, DEVICE data) with shared
+   options; out is a HOST array of `count` results.  Not yet built: returns
+   ID_ERR_UNSUPPORTED. */
+int id_batched_workspace_size(int64_t count, const id_matrix* A, const id_opts* opts,
+                              size_t* bytes);
+int id_batched(int64_t count, const id_matrix* A, const id_opts* opts, void* ws,
+               size_t ws_bytes, id_result* out, void* stream);
+
+/* Two-sided ID from a column skeleton (Sec. 2.2.1 "Two-sided ID", Sec. 3.1):
+   LUPP of C = A(:,J) (m x k) picks row skeletons I (k), and W (m x k, column-
+   major, ldw >= m) = P^T [I; L2 L1^{-1}] (Eq. inty) satisfies C = W C(I,:), so
+   A ~ W A(I,J) X.  Not yet built: returns ID_ERR_UNSUPPORTED. */
+int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W,
+                int64_t ldw, void* ws, size_t ws_bytes, void* stream);
+
+/* Rows [row0, row0+rows) of the Gaussian sketching matrix (row-major, row
+   stride ld >= m, dtype F64 or F32): entry (i, r) is a standard normal from
+   Philox4x64-10 (Salmon et al. 2011) keyed (seed, 0) at counter
+   (r/4, i, 0, 0) and Box-Muller on 53-bit uniforms (Sec. 2.4, Sec. 5.1). */
+int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype,
+                     void* out, int64_t ld, void* stream);
+
+/* Human-readable text for a status value. */
+const char* id_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANDID_H */

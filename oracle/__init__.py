@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
            "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)

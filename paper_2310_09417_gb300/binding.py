@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in include/randid.h.
+
+Argument marshalling only: every step of the ID runs in the CUDA library.
+PyTorch provides device memory (inputs, outputs, workspace) and the stream.
+Matrices are column-major: pass A as a CUDA tensor of shape (m, n) with
+stride (1, ld), e.g. ``colmajor(t)``.  If the library has not been built the
+first call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import re
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librandid.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "randid.h")
+
+# id_dtype
+F64, F32, BF16, FP8_E4M3 = 0, 1, 2, 3
+# status
+OK, WARN_TOL_NOT_MET, WARN_ZERO_PIVOT = 0, 1, 2
+ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = -101, -102, -103, -104, -105
+PHASES = ("omega", "sketch", "schur", "lu", "update", "other")
+
+_TORCH_TO_ID = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+if hasattr(torch, "float8_e4m3fn"):
+    _TORCH_TO_ID[torch.float8_e4m3fn] = FP8_E4M3
+
+
+class IdMatrix(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int), ("m", C.c_int64), ("n", C.c_int64),
+                ("ld", C.c_int64), ("block_scale", C.c_void_p)]
+
+
+class IdOpts(C.Structure):
+    _fields_ = [("sketch_prec", C.c_int), ("lu_prec", C.c_int), ("block", C.c_int64),
+                ("tol", C.c_double), ("tol_relative", C.c_int), ("k_max", C.c_int64),
+                ("k0", C.c_int64), ("blocks_per_pass", C.c_int64), ("seed", C.c_uint64),
+                ("omega", C.c_void_p), ("ld_omega", C.c_int64), ("omega_rows", C.c_int64),
+                ("profile", C.c_int)]
+
+
+class IdResult(C.Structure):
+    _fields_ = [("k", C.c_int64), ("J", C.c_void_p), ("X", C.c_void_p), ("ldx", C.c_int64),
+                ("pivots", C.c_void_p), ("est_trace", C.c_void_p), ("trace_cap", C.c_int64),
+                ("est_err", C.c_double), ("norm_A", C.c_double), ("rounds", C.c_int32),
+                ("passes", C.c_int32), ("launches", C.c_int64),
+                ("phase_ms", C.c_double * 6), ("phase_launches", C.c_int64 * 6)]
+
+
+_lib = None
+
+
+def load():
+    """Load librandid.so; raise if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librandid.so is not built (%s); run __graft_entry__.build() or "
+                           "python -m paper_2310_09417_gb300.build" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P, i64, u64 = C.c_void_p, C.c_int64, C.c_uint64
+    lib.id_workspace_size.argtypes = [P, P, i64, C.POINTER(C.c_size_t)]
+    lib.id_fixed_rank.argtypes = [P, i64, i64, P, P, C.c_size_t, P, P]
+    lib.id_adaptive.argtypes = [P, P, P, C.c_size_t, P, P]
+    lib.id_batched_workspace_size.argtypes = [i64, P, P, C.POINTER(C.c_size_t)]
+    lib.id_batched.argtypes = [i64, P, P, P, C.c_size_t, P, P]
+    lib.cur_from_id.argtypes = [P, P, i64, P, P, i64, P, C.c_size_t, P]
+    lib.id_gaussian_rows.argtypes = [u64, i64, i64, i64, C.c_int, P, i64, P]
+    lib.id_status_string.argtypes = [C.c_int]
+    lib.id_status_string.restype = C.c_char_p
+    for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
+              "id_batched", "cur_from_id", "id_gaussian_rows"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/randid.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\([^;{]*\)\s*;", text, flags=re.M)
+
+
+def status_string(code: int) -> str:
+    return load().id_status_string(code).decode()
+
+
+class IDError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s failed: %s (status %d)" % (where, status_string(code), code))
+        self.code = code
+
+
+@dataclasses.dataclass
+class IDResult:
+    k: int
+    J: torch.Tensor          # int64 [k], skeleton columns in pivot order
+    X: torch.Tensor          # k x n, column-major view, X[:, J] = I
+    est_err: float
+    norm_A: float
+    rounds: int
+    passes: int
+    launches: int
+    status: int
+    trace: list
+    pivots: torch.Tensor | None
+    phase_ms: dict
+    phase_launches: dict
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Return a column-major (Fortran-order) copy/view of a 2-D tensor."""
+    if t.dim() != 2:
+        raise ValueError("expected a matrix")
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _matrix(A: torch.Tensor) -> IdMatrix:
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.dim() != 2 or A.stride(0) != 1 or A.stride(1) < A.shape[0]:
+        raise ValueError("A must be column-major (stride (1, ld >= m)); use colmajor(A)")
+    if A.dtype not in _TORCH_TO_ID:
+        raise ValueError("unsupported dtype %s" % A.dtype)
+    return IdMatrix(A.data_ptr(), _TORCH_TO_ID[A.dtype], A.shape[0], A.shape[1], A.stride(1), None)
+
+
+def _opts(A, *, block, tol, relative, k_max, k0, blocks_per_pass, seed, omega, profile,
+          sketch_prec=None, lu_prec=None) -> IdOpts:
+    dt = _TORCH_TO_ID[A.dtype]
+    o = IdOpts()
+    o.sketch_prec = dt if sketch_prec is None else sketch_prec
+    o.lu_prec = (F64 if dt == F64 else F32) if lu_prec is None else lu_prec
+    o.block = block
+    o.tol = tol
+    o.tol_relative = 1 if relative else 0
+    o.k_max = k_max or 0
+    o.k0 = k0
+    o.blocks_per_pass = blocks_per_pass
+    o.seed = seed & 0xFFFFFFFFFFFFFFFF
+    if omega is not None:
+        if not omega.is_cuda or omega.stride(1) != 1:
+            raise ValueError("omega must be a row-major CUDA tensor (rows x m)")
+        o.omega = omega.data_ptr()
+        o.ld_omega = omega.stride(0)
+        o.omega_rows = omega.shape[0]
+    o.profile = 1 if profile else 0
+    return o
+
+
+def _stream(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def workspace_size(A: torch.Tensor, opts: IdOpts, l: int = 0) -> int:
+    n = C.c_size_t(0)
+    rc = load().id_workspace_size(C.byref(_matrix(A)), C.byref(opts), l, C.byref(n))
+    if rc != 0:
+        raise IDError(rc, "id_workspace_size")
+    return int(n.value)
+
+
+def _workspace(nbytes: int, device, ws: torch.Tensor | None) -> torch.Tensor:
+    if ws is not None and ws.numel() >= nbytes and ws.device == device:
+        return ws
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def _result(res: IdResult, J, Xbuf, k, n, status, trace_buf, piv) -> IDResult:
+    X = Xbuf.t()[:k]
+    trace = list(trace_buf[: min(res.rounds, len(trace_buf))]) if trace_buf is not None else []
+    return IDResult(k=k, J=J[:k], X=X, est_err=res.est_err, norm_A=res.norm_A, rounds=res.rounds,
+                    passes=res.passes, launches=res.launches, status=status, trace=trace,
+                    pivots=None if piv is None else piv[:k],
+                    phase_ms={PHASES[i]: res.phase_ms[i] for i in range(6)},
+                    phase_launches={PHASES[i]: int(res.phase_launches[i]) for i in range(6)})
+
+
+def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int = 0,
+                  omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
+                  stream=None, workspace: torch.Tensor | None = None) -> IDResult:
+    """randLUPP fixed-rank column ID (Sec. 3.1): J (k), X (k x n), estimate from l - k rows."""
+    m, n = A.shape
+    opts = _opts(A, block=block, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1,
+                 seed=seed, omega=omega, profile=profile)
+    ws = _workspace(workspace_size(A, opts, l), A.device, workspace)
+    J = torch.empty(k, dtype=torch.int64, device=A.device)
+    Xbuf = torch.empty((n, k), dtype=torch.float64 if opts.lu_prec == F64 else torch.float32,
+                       device=A.device)
+    piv = torch.empty(k, dtype=torch.float64, device=A.device) if pivots else None
+    res = IdResult()
+    res.J, res.X, res.ldx = J.data_ptr(), Xbuf.data_ptr(), k
+    res.pivots = piv.data_ptr() if piv is not None else None
+    rc = load().id_fixed_rank(C.byref(_matrix(A)), k, l, C.byref(opts), ws.data_ptr(), ws.numel(),
+                              C.byref(res), _stream(stream))
+    if rc < 0:
+        raise IDError(rc, "id_fixed_rank")
+    return _result(res, J, Xbuf, k, n, rc, None, piv)
+
+
+def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool = True,
+                k_max: int | None = None, k0: int = 0, blocks_per_pass: int = 1, seed: int = 0,
+                omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
+                trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
+                out: tuple | None = None) -> IDResult:
+    """randLUPPadap column ID (Algorithm 1).  `out` = (J, Xbuf) reuses output buffers
+    (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major)."""
+    m, n = A.shape
+    kmax = min(m, n) if not k_max else min(k_max, m, n)
+    opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,
+                 blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile)
+    ws = _workspace(workspace_size(A, opts, 0), A.device, workspace)
+    xdt = torch.float64 if opts.lu_prec == F64 else torch.float32
+    if out is None:
+        J = torch.empty(kmax, dtype=torch.int64, device=A.device)
+        Xbuf = torch.empty((n, kmax), dtype=xdt, device=A.device)
+    else:
+        J, Xbuf = out
+    piv = torch.empty(kmax, dtype=torch.float64, device=A.device) if pivots else None
+    trace_buf = (C.c_double * trace_cap)() if trace_cap > 0 else None
+    res = IdResult()
+    res.J, res.X, res.ldx = J.data_ptr(), Xbuf.data_ptr(), Xbuf.stride(0)
+    res.pivots = piv.data_ptr() if piv is not None else None
+    res.est_trace = C.cast(trace_buf, C.c_void_p) if trace_buf is not None else None
+    res.trace_cap = trace_cap
+    rc = load().id_adaptive(C.byref(_matrix(A)), C.byref(opts), ws.data_ptr(), ws.numel(),
+                            C.byref(res), _stream(stream))
+    if rc < 0:
+        raise IDError(rc, "id_adaptive")
+    return _result(res, J, Xbuf, int(res.k), n, rc, trace_buf, piv)
+
+
+def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
+                  device="cuda", stream=None) -> torch.Tensor:
+    """Rows [row0, row0+rows) of the Philox/Box-Muller sketching matrix (rows x m)."""
+    out = torch.empty((rows, m), dtype=dtype, device=device)
+    rc = load().id_gaussian_rows(seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, _TORCH_TO_ID[dtype],
+                                 out.data_ptr(), m, _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_gaussian_rows")
+    return out

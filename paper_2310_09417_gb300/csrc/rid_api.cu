@@ -1,0 +1,589 @@
+// rid_api.cu -- C ABI (include/randid.h) over the ID kernels.
+//
+// The drivers below walk Algorithm 1 of arXiv:2310.09417 (column form) and
+// the fixed-rank randLUPP of Sec. 3.1.  Per factored block:
+//   Schur      S = G(act, blk) - T(act, 0:tb) G(perm, blk)      (T = L2 L1^{-1})
+//   estimate   E = ||S||_F / sqrt(w), stop test on the device
+//   LUPP       of S, rows marked instead of swapped
+//   re-block   N = L-hat(rest) L-hat(piv)^{-1};  T(act, tb:tb+bt) = N;
+//              T(act, 0:tb) -= N T(piv, 0:tb);  act, J updated
+// T is the caller's X buffer (column j of X is row j of T), so X is complete
+// when the loop ends except for the identity columns at J.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "randid.h"
+#include "rid_internal.h"
+
+using namespace rid;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kMaxBlock = 128;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+// Split-K factor: enough blocks for about four waves, at least 256 K per split.
+int choose_splits(int64_t M, int64_t N, int64_t K, int sms, int cap) {
+  const int64_t tiles = cdiv(M, 64) * cdiv(N, 64);
+  int64_t s = cdiv(4 * (int64_t)sms, tiles);
+  s = imin(s, imax(1, K / 256));
+  s = imin(s, cap);
+  return (int)imax(1, s);
+}
+
+// Every size and offset of one call's workspace.
+struct Plan {
+  int64_t m = 0, n = 0, b = 0, cap = 0, k = 0, l = 0;
+  int64_t rows_first = 0, rows_pass = 0, ldg = 0, wmax = 0, max_rounds = 0;
+  int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
+  bool gen_omega = true;
+  size_t esz = 0;
+  size_t off_state = 0, off_omega = 0, off_G = 0, off_Gpart = 0, off_S = 0, off_Spart = 0, off_N = 0,
+         off_Linv = 0, off_act0 = 0, off_act1 = 0, off_pivmark = 0, off_perm32 = 0, off_piv = 0,
+         off_pivorig = 0, off_pivdiag = 0, off_cand_v = 0, off_cand_i = 0, off_cand_rows = 0, off_e2 = 0,
+         off_normp = 0, off_trace = 0, total = 0;
+};
+
+// Which (input, sketch, LU) precision triples are built.
+int precision_path(const id_matrix* A, const id_opts* o) {
+  if (A->dtype == ID_F64 && o->sketch_prec == ID_F64 && o->lu_prec == ID_F64) return 64;
+  if (A->dtype == ID_F32 && o->sketch_prec == ID_F32 && o->lu_prec == ID_F32) return 32;
+  return 0;
+}
+
+// make_plan failures, mapped to argument positions by each entry point.
+constexpr int kBadA = -1, kBadOpts = -2, kBadK = -3, kBadL = -4;
+
+// Validate A and opts; on success fill the plan.  l > 0: fixed rank with k.
+int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* p) {
+  if (A == nullptr || A->data == nullptr) return kBadA;
+  if (o == nullptr) return kBadOpts;
+  if (A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= (int64_t)1 << 31 || A->n >= (int64_t)1 << 30) return kBadA;
+  if (precision_path(A, o) == 0) return ID_ERR_UNSUPPORTED;
+  const int64_t b = o->block == 0 ? 64 : o->block;
+  if (b < 1 || b > kMaxBlock) return kBadOpts;
+  if (!(o->tol >= 0.0) || o->k_max < 0 || o->k0 < 0 || o->blocks_per_pass < 0) return kBadOpts;
+  p->m = A->m;
+  p->n = A->n;
+  p->b = b;
+  p->sms = num_sms();
+  p->esz = o->lu_prec == ID_F64 ? 8 : 4;
+  p->gen_omega = (o->omega == nullptr);
+  if (l > 0) {  // fixed rank; sizes do not depend on k (estimate block sized for k = 1)
+    if (l > ((int64_t)1 << 20)) return kBadL;
+    if (k < 1 || k > l || k > imin(A->m, A->n)) return kBadK;
+    p->k = k;
+    p->l = l;
+    p->cap = k;
+    p->rows_first = l;
+    p->rows_pass = 0;
+    p->wmax = imax(b, l);
+    p->max_rounds = 2;
+  } else {
+    const int64_t kmax = o->k_max == 0 ? imin(A->m, A->n) : o->k_max;
+    p->cap = imin(imin(A->m, A->n), kmax);
+    const int64_t max_blocks = cdiv(p->cap, b) + 1;  // blocks that can ever be used
+    int64_t first = o->k0 > 0 ? (cdiv(o->k0, b) + 1) : 1;
+    p->rows_first = imin(first, max_blocks) * b;
+    const int64_t per = o->blocks_per_pass > 0 ? o->blocks_per_pass : 1;
+    p->rows_pass = imin(per, max_blocks) * b;
+    p->wmax = b;
+    p->max_rounds = max_blocks + 1;
+  }
+  if (!p->gen_omega) {
+    if (o->ld_omega < A->m) return kBadOpts;
+    const int64_t need = l > 0 ? l : (cdiv(p->cap, b) + 1) * b;
+    if (o->omega_rows < need) return kBadOpts;
+  }
+  const int64_t rows_max = imax(p->rows_first, p->rows_pass);
+  p->ldg = rows_max;
+  p->s1_first = choose_splits(p->n, p->rows_first, p->m, p->sms, 16);
+  p->s1_pass = p->rows_pass > 0 ? choose_splits(p->n, p->rows_pass, p->m, p->sms, 16) : 1;
+  const int s1 = p->s1_first > p->s1_pass ? p->s1_first : p->s1_pass;
+  p->s2max = 8;
+  p->nparts = 2 * p->sms;
+  p->maxg = p->sms;
+  const size_t e = p->esz;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + (bytes == 0 ? 1 : bytes));
+    return at;
+  };
+  p->off_state = take(256);
+  p->off_omega = take(p->gen_omega ? (size_t)rows_max * p->m * e : 0);
+  p->off_G = take((size_t)p->n * rows_max * e);
+  p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * e : 0);
+  p->off_S = take((size_t)p->n * p->wmax * e);
+  p->off_Spart = take((size_t)p->s2max * p->n * p->wmax * e);
+  p->off_N = take((size_t)p->n * b * e);
+  p->off_Linv = take((size_t)b * b * e);
+  p->off_act0 = take((size_t)p->n * 4);
+  p->off_act1 = take((size_t)p->n * 4);
+  p->off_pivmark = take((size_t)p->n * 4);
+  p->off_perm32 = take((size_t)p->n * 4);
+  p->off_piv = take((size_t)kMaxBlock * 4);
+  p->off_pivorig = take((size_t)kMaxBlock * 4);
+  p->off_pivdiag = take((size_t)kMaxBlock * 8);
+  p->off_cand_v = take((size_t)2 * p->maxg * 8);
+  p->off_cand_i = take((size_t)2 * p->maxg * 4);
+  p->off_cand_rows = take((size_t)2 * p->maxg * p->wmax * e);
+  p->off_e2 = take((size_t)p->nparts * 8);
+  p->off_normp = take((size_t)p->nparts * 8);
+  p->off_trace = take((size_t)p->max_rounds * 8);
+  p->total = off;
+  return ID_OK;
+}
+
+#define RID_TRY(expr)             \
+  do {                            \
+    int rid_rc_ = (expr);         \
+    if (rid_rc_ != 0) return rid_rc_; \
+  } while (0)
+
+// One call's state and the steps of the method.
+template <typename T>
+class Engine {
+ public:
+  Engine(const Plan& p, const id_matrix* A, const id_opts* o, void* ws, id_result* out, cudaStream_t s)
+      : p_(p), o_(*o), out_(out), s_(s) {
+    A_ = static_cast<const T*>(A->data);
+    lda_ = A->ld;
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    st_ = reinterpret_cast<DevState*>(w + p.off_state);
+    omega_ = reinterpret_cast<T*>(w + p.off_omega);
+    G_ = reinterpret_cast<T*>(w + p.off_G);
+    Gpart_ = reinterpret_cast<T*>(w + p.off_Gpart);
+    S_ = reinterpret_cast<T*>(w + p.off_S);
+    Spart_ = reinterpret_cast<T*>(w + p.off_Spart);
+    N_ = reinterpret_cast<T*>(w + p.off_N);
+    Linv_ = reinterpret_cast<T*>(w + p.off_Linv);
+    act_[0] = reinterpret_cast<int32_t*>(w + p.off_act0);
+    act_[1] = reinterpret_cast<int32_t*>(w + p.off_act1);
+    pivmark_ = reinterpret_cast<int32_t*>(w + p.off_pivmark);
+    perm32_ = reinterpret_cast<int32_t*>(w + p.off_perm32);
+    piv_ = reinterpret_cast<int32_t*>(w + p.off_piv);
+    pivorig_ = reinterpret_cast<int32_t*>(w + p.off_pivorig);
+    pivdiag_ = reinterpret_cast<double*>(w + p.off_pivdiag);
+    cand_v_ = reinterpret_cast<double*>(w + p.off_cand_v);
+    cand_i_ = reinterpret_cast<int32_t*>(w + p.off_cand_i);
+    cand_rows_ = reinterpret_cast<T*>(w + p.off_cand_rows);
+    e2_ = reinterpret_cast<double*>(w + p.off_e2);
+    normp_ = reinterpret_cast<double*>(w + p.off_normp);
+    trace_ = reinterpret_cast<double*>(w + p.off_trace);
+    X_ = static_cast<T*>(out->X);
+    ldx_ = out->ldx;
+    done_ = &st_->done;
+    for (int i = 0; i < kNumPhases; ++i) {
+      phase_ms_[i] = 0.0;
+      phase_launches_[i] = 0;
+    }
+  }
+  ~Engine() {
+    for (cudaEvent_t e : events_) cudaEventDestroy(e);
+  }
+
+  int run_adaptive() {
+    RID_TRY(start());
+    int64_t tb = 0, na = p_.n, t = 0, sketched = 0, gstart = 0;
+    const int64_t b = p_.b;
+    bool full = false;
+    for (;;) {
+      if (t >= sketched) {
+        const int64_t max_blocks = cdiv(p_.cap, b) + 1;
+        int64_t rows = t == 0 ? p_.rows_first : p_.rows_pass;
+        rows = imin(rows, (max_blocks - t) * b);
+        RID_TRY(sketch(t * b, rows, t == 0 ? p_.s1_first : p_.s1_pass));
+        gstart = t;
+        sketched = t + rows / b;
+      }
+      RID_TRY(schur((t - gstart) * b, b, tb, na));
+      if (t > 0) {
+        RID_TRY(decide(b, tb, tb == p_.cap, (int)(t - 1)));
+        RID_TRY(sync_state());
+        if (h_.err) break;
+        if (h_.done) break;
+      }
+      const int64_t bt = imin(b, p_.cap - tb);
+      RID_TRY(factor(b, bt, tb, na));
+      tb += bt;
+      na -= bt;
+      ++t;
+      if (tb == p_.n) {  // every column is a skeleton: X is a permutation, the residual is 0
+        full = true;
+        break;
+      }
+    }
+    const int64_t k = full ? p_.n : (h_.done ? h_.k_final : tb);
+    est_zero_ = full;  // k = n: no columns left, the ID is exact
+    return finish(k);
+  }
+
+  int run_fixed() {
+    RID_TRY(start());
+    RID_TRY(sketch(0, p_.l, p_.s1_first));
+    int64_t tb = 0, na = p_.n;
+    while (tb < p_.k) {
+      const int64_t w = imin(p_.b, p_.k - tb);
+      RID_TRY(schur(tb, w, tb, na));
+      RID_TRY(factor(w, w, tb, na));
+      tb += w;
+      na -= w;
+    }
+    if (p_.l > p_.k && p_.n > p_.k) {
+      RID_TRY(schur(p_.k, p_.l - p_.k, tb, na));
+      RID_TRY(decide(p_.l - p_.k, tb, 0, 0));
+    }
+    est_zero_ = !(p_.l > p_.k && p_.n > p_.k);  // no estimation rows: report 0
+    return finish(p_.k);
+  }
+
+ private:
+  int cuda(cudaError_t e) { return e == cudaSuccess ? 0 : ID_ERR_CUDA; }
+
+  // ---- phase timing (CUDA events on the launching stream) and launch counts
+  int tbegin(int ph) {
+    cur_phase_ = ph;
+    if (!o_.profile) return 0;
+    cudaEvent_t e;
+    RID_TRY(cuda(cudaEventCreate(&e)));
+    events_.push_back(e);
+    RID_TRY(cuda(cudaEventRecord(e, s_)));
+    return 0;
+  }
+  int tend(int launches) {
+    launches_ += launches;
+    phase_launches_[cur_phase_] += launches;
+    if (!o_.profile) return 0;
+    cudaEvent_t e;
+    RID_TRY(cuda(cudaEventCreate(&e)));
+    events_.push_back(e);
+    RID_TRY(cuda(cudaEventRecord(e, s_)));
+    pending_.push_back(cur_phase_);
+    return 0;
+  }
+  void collect_times() {
+    for (size_t i = 0; i < pending_.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, events_[2 * i], events_[2 * i + 1]) == cudaSuccess)
+        phase_ms_[pending_[i]] += ms;
+    }
+    for (cudaEvent_t e : events_) cudaEventDestroy(e);
+    events_.clear();
+    pending_.clear();
+  }
+
+  int start() {
+    RID_TRY(tbegin(ID_PHASE_OTHER));
+    RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
+    RID_TRY(cuda(norm2_partial<T>(p_.m, p_.n, A_, lda_, normp_, p_.nparts, st_, s_)));
+    RID_TRY(cuda(norm2_final(normp_, p_.nparts, st_, s_)));
+    RID_TRY(tend(3));
+    RID_TRY(sync_state());
+    if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
+    return 0;
+  }
+
+  int sync_state() {
+    RID_TRY(cuda(cudaMemcpyAsync(&h_, st_, sizeof(DevState), cudaMemcpyDeviceToHost, s_)));
+    RID_TRY(cuda(cudaStreamSynchronize(s_)));
+    collect_times();
+    return 0;
+  }
+
+  // G(:, 0:rows) = (Omega rows [row0, row0+rows)) A, stored n x rows (row-major, ld ldg).
+  int sketch(int64_t row0, int64_t rows, int splits) {
+    const T* Om;
+    int64_t ldo;
+    if (p_.gen_omega) {
+      RID_TRY(tbegin(ID_PHASE_OMEGA));
+      RID_TRY(cuda(gaussian_rows<T>(o_.seed, row0, rows, p_.m, omega_, p_.m, done_, s_)));
+      RID_TRY(tend(1));
+      Om = omega_;
+      ldo = p_.m;
+    } else {
+      Om = static_cast<const T*>(o_.omega) + row0 * o_.ld_omega;
+      ldo = o_.ld_omega;
+    }
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    Operand<T> a{A_, lda_, nullptr, 0};
+    Operand<T> bop{Om, ldo, nullptr, 0};
+    EpiArgs<T> ep{splits > 1 ? Gpart_ : G_, p_.ldg, (int64_t)p_.n * p_.ldg, nullptr, nullptr};
+    splits = gemm_splits((int)p_.m, splits);
+    ep.out = splits > 1 ? Gpart_ : G_;
+    RID_TRY(cuda(gemm_gather<T>((int)p_.n, (int)rows, (int)p_.m, splits, true, a, bop, kEpiStore, ep, done_, s_)));
+    if (splits > 1)
+      RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg, Gpart_, G_, done_, s_)));
+    RID_TRY(tend(splits > 1 ? 2 : 1));
+    ++passes_;
+    return 0;
+  }
+
+  // S = G(act, col0:col0+w) - T(act, 0:tb) G(perm, col0:col0+w) and ||S||^2 partials.
+  int schur(int64_t col0, int64_t w, int64_t tb, int64_t na) {
+    RID_TRY(tbegin(ID_PHASE_SCHUR));
+    int nz = 0, nl = 0;
+    const int64_t lds = p_.wmax;
+    if (tb > 0) {
+      nz = gemm_splits((int)tb, choose_splits(na, w, tb, p_.sms, p_.s2max));
+      Operand<T> a{X_, ldx_, act_[cur_], 0};
+      Operand<T> bop{G_, p_.ldg, perm32_, col0};
+      EpiArgs<T> ep{Spart_, lds, (int64_t)p_.n * lds, nullptr, nullptr};
+      RID_TRY(cuda(gemm_gather<T>((int)na, (int)w, (int)tb, nz, false, a, bop, kEpiStore, ep, done_, s_)));
+      ++nl;
+    }
+    RID_TRY(cuda(schur_finish<T>((int)na, (int)w, act_[cur_], G_, p_.ldg, col0, nz, (int64_t)p_.n * lds, Spart_,
+                                 S_, lds, e2_, p_.nparts, done_, s_)));
+    RID_TRY(tend(nl + 1));
+    return 0;
+  }
+
+  int decide(int64_t w, int64_t tb, int last, int round) {
+    RID_TRY(tbegin(ID_PHASE_OTHER));
+    const double tol = p_.l > 0 ? INFINITY : o_.tol;  // fixed rank: estimate only
+    RID_TRY(cuda(rid::decide(e2_, p_.nparts, (int)w, tol, p_.l > 0 ? 0 : o_.tol_relative, tb, last, trace_,
+                             round, st_, s_)));
+    RID_TRY(tend(1));
+    return 0;
+  }
+
+  // LUPP of S (na x w) for bt pivots, then re-blocking.
+  int factor(int64_t w, int64_t bt, int64_t tb, int64_t na) {
+    const int64_t lds = p_.wmax;
+    RID_TRY(tbegin(ID_PHASE_LU));
+    PanelCfg cfg = panel_config<T>((int)na, (int)w, p_.maxg);
+    RID_TRY(cuda(panel_lupp<T>(cfg, (int)na, (int)w, (int)bt, S_, lds, piv_, pivmark_, pivdiag_, cand_v_, cand_i_,
+                               cand_rows_, st_, s_)));
+    RID_TRY(tend(1));
+    RID_TRY(tbegin(ID_PHASE_UPDATE));
+    int nl = 3;
+    RID_TRY(cuda(linv<T>((int)bt, S_, lds, piv_, Linv_, done_, s_)));
+    RID_TRY(cuda(make_n<T>((int)na, (int)bt, S_, lds, Linv_, pivmark_, act_[cur_], N_, X_, ldx_, tb, piv_,
+                           pivorig_, done_, s_)));
+    if (tb > 0) {
+      Operand<T> a{N_, bt, nullptr, 0};
+      Operand<T> bop{X_, ldx_, pivorig_, 0};
+      EpiArgs<T> ep{X_, ldx_, 0, act_[cur_], pivmark_};
+      RID_TRY(cuda(gemm_gather<T>((int)na, (int)tb, (int)bt, 1, false, a, bop, kEpiSubRows, ep, done_, s_)));
+      ++nl;
+    }
+    RID_TRY(cuda(compact((int)na, (int)bt, act_[cur_], act_[cur_ ^ 1], pivmark_, piv_, out_->J, perm32_, tb,
+                         out_->pivots, pivdiag_, done_, s_)));
+    RID_TRY(tend(nl));
+    cur_ ^= 1;
+    return 0;
+  }
+
+  int finish(int64_t k) {
+    RID_TRY(tbegin(ID_PHASE_OTHER));
+    RID_TRY(cuda(finalize_x<T>(k, perm32_, X_, ldx_, s_)));
+    RID_TRY(tend(1));
+    RID_TRY(sync_state());
+    int status = ID_OK;
+    if (h_.err & kErrTimeout) return ID_ERR_TIMEOUT;
+    if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
+    if (h_.tol_not_met) status |= ID_WARN_TOL_NOT_MET;
+    if (h_.zero_pivots) status |= ID_WARN_ZERO_PIVOT;
+    out_->k = k;
+    out_->est_err = est_zero_ ? 0.0 : h_.est;
+    out_->norm_A = sqrt(h_.norm2_A);
+    out_->rounds = h_.rounds;
+    out_->passes = passes_;
+    out_->launches = launches_;
+    for (int i = 0; i < kNumPhases; ++i) {
+      out_->phase_ms[i] = phase_ms_[i];
+      out_->phase_launches[i] = phase_launches_[i];
+    }
+    if (out_->est_trace != nullptr && out_->trace_cap > 0 && h_.rounds > 0) {
+      const int64_t nt = imin(out_->trace_cap, h_.rounds);
+      RID_TRY(cuda(cudaMemcpyAsync(out_->est_trace, trace_, nt * sizeof(double), cudaMemcpyDeviceToHost, s_)));
+      RID_TRY(cuda(cudaStreamSynchronize(s_)));
+    }
+    return status;
+  }
+
+  Plan p_;
+  id_opts o_;
+  id_result* out_;
+  cudaStream_t s_;
+  const T* A_;
+  int64_t lda_;
+  DevState* st_;
+  DevState h_{};
+  T *omega_, *G_, *Gpart_, *S_, *Spart_, *N_, *Linv_, *cand_rows_, *X_;
+  int32_t *act_[2], *pivmark_, *perm32_, *piv_, *pivorig_, *cand_i_;
+  double *pivdiag_, *cand_v_, *e2_, *normp_, *trace_;
+  const int32_t* done_;
+  int64_t ldx_;
+  int cur_ = 0;
+  int cur_phase_ = 0;
+  bool est_zero_ = false;
+  int32_t passes_ = 0;
+  int64_t launches_ = 0;
+  double phase_ms_[kNumPhases];
+  int64_t phase_launches_[kNumPhases];
+  std::vector<cudaEvent_t> events_;
+  std::vector<int> pending_;
+};
+
+int check_ws(const Plan& p, void* ws, size_t ws_bytes) {
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < p.total)
+    return ID_ERR_WORKSPACE;
+  return ID_OK;
+}
+
+int check_out(const Plan& p, const id_result* out) {
+  if (out == nullptr || out->J == nullptr || out->X == nullptr || out->ldx < p.cap) return -1;
+  return ID_OK;
+}
+
+void clear_out(id_result* out) {
+  out->k = 0;
+  out->est_err = 0.0;
+  out->norm_A = 0.0;
+  out->rounds = 0;
+  out->passes = 0;
+  out->launches = 0;
+  for (int i = 0; i < ID_NUM_PHASES; ++i) {
+    out->phase_ms[i] = 0.0;
+    out->phase_launches[i] = 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int id_workspace_size(const id_matrix* A, const id_opts* opts, int64_t l, size_t* bytes) {
+  if (bytes == nullptr) return -4;
+  if (l < 0) return -3;
+  Plan p;
+  const int rc = make_plan(A, opts, l > 0 ? 1 : 0, l, &p);
+  if (rc != ID_OK) return rc == kBadA ? -1 : (rc == kBadOpts ? -2 : (rc < -100 ? rc : -3));
+  *bytes = p.total;
+  return ID_OK;
+}
+
+int id_fixed_rank(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts, void* ws, size_t ws_bytes,
+                  id_result* out, void* stream) {
+  Plan p;
+  int rc = make_plan(A, opts, k, l, &p);
+  if (rc != ID_OK) return rc == kBadA ? -1 : (rc == kBadOpts ? -4 : (rc == kBadK ? -2 : (rc == kBadL ? -3 : rc)));
+  if (check_out(p, out) != ID_OK) return -7;
+  if (check_ws(p, ws, ws_bytes) != ID_OK) return ID_ERR_WORKSPACE;
+  clear_out(out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision_path(A, opts) == 64) {
+    Engine<double> e(p, A, opts, ws, out, s);
+    return e.run_fixed();
+  }
+  Engine<float> e(p, A, opts, ws, out, s);
+  return e.run_fixed();
+}
+
+int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_bytes, id_result* out, void* stream) {
+  Plan p;
+  int rc = make_plan(A, opts, 0, 0, &p);
+  if (rc != ID_OK) return rc == kBadA ? -1 : (rc == kBadOpts ? -2 : rc);
+  if (check_out(p, out) != ID_OK) return -5;
+  if (check_ws(p, ws, ws_bytes) != ID_OK) return ID_ERR_WORKSPACE;
+  clear_out(out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision_path(A, opts) == 64) {
+    Engine<double> e(p, A, opts, ws, out, s);
+    return e.run_adaptive();
+  }
+  Engine<float> e(p, A, opts, ws, out, s);
+  return e.run_adaptive();
+}
+
+int id_batched_workspace_size(int64_t count, const id_matrix* A, const id_opts* opts, size_t* bytes) {
+  (void)count;
+  (void)A;
+  (void)opts;
+  if (bytes) *bytes = 0;
+  return ID_ERR_UNSUPPORTED;
+}
+
+int id_batched(int64_t count, const id_matrix* A, const id_opts* opts, void* ws, size_t ws_bytes, id_result* out,
+               void* stream) {
+  (void)count;
+  (void)A;
+  (void)opts;
+  (void)ws;
+  (void)ws_bytes;
+  (void)out;
+  (void)stream;
+  return ID_ERR_UNSUPPORTED;
+}
+
+int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W, int64_t ldw, void* ws,
+                size_t ws_bytes, void* stream) {
+  (void)A;
+  (void)J;
+  (void)k;
+  (void)I;
+  (void)W;
+  (void)ldw;
+  (void)ws;
+  (void)ws_bytes;
+  (void)stream;
+  return ID_ERR_UNSUPPORTED;
+}
+
+int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype, void* out, int64_t ld,
+                     void* stream) {
+  if (row0 < 0) return -2;
+  if (rows < 0) return -3;
+  if (m < 1) return -4;
+  if (dtype != ID_F64 && dtype != ID_F32) return -5;
+  if (out == nullptr) return -6;
+  if (ld < m) return -7;
+  if (rows == 0) return ID_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dtype == ID_F64
+                      ? gaussian_rows<double>(seed, row0, rows, m, static_cast<double*>(out), ld, nullptr, s)
+                      : gaussian_rows<float>(seed, row0, rows, m, static_cast<float*>(out), ld, nullptr, s);
+  if (e != cudaSuccess) return ID_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
+  return ID_OK;
+}
+
+const char* id_status_string(int status) {
+  switch (status) {
+    case ID_OK: return "ok";
+    case ID_WARN_TOL_NOT_MET: return "warning: rank cap reached before the tolerance was met";
+    case ID_WARN_ZERO_PIVOT: return "warning: an exactly zero pivot column was met";
+    case ID_WARN_TOL_NOT_MET | ID_WARN_ZERO_PIVOT: return "warning: rank cap reached and a zero pivot was met";
+    case ID_ERR_NONFINITE: return "error: the input holds NaN or Inf";
+    case ID_ERR_CUDA: return "error: a CUDA runtime call failed";
+    case ID_ERR_TIMEOUT: return "error: a bounded device-side wait timed out";
+    case ID_ERR_WORKSPACE: return "error: workspace missing, misaligned or too small";
+    case ID_ERR_UNSUPPORTED: return "error: this precision combination or entry point is not built";
+    default: break;
+  }
+  if (status < 0 && status > -100) return "error: invalid argument (see -status for its position)";
+  return "unknown status";
+}
+
+}  // extern "C"

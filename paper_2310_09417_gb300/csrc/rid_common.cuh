@@ -1,0 +1,146 @@
+// rid_common.cuh -- device helpers shared by the ID kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rid {
+
+constexpr int kNumPhases = 6;
+
+// Error bits accumulated on the device (DevState::err).
+enum : unsigned {
+  kErrTimeout = 1u,   // a bounded wait gave up
+  kErrNonFinite = 2u, // NaN or Inf met in the input
+};
+
+// Device-resident control block at the start of every workspace.  The host
+// copies it back at synchronisation points.
+struct DevState {
+  double norm2_A;         // ||A||_F^2 (FP64 sum)
+  double est;             // last estimate E
+  double thr;             // stopping threshold tau (absolute)
+  int64_t k_final;        // rank when stopped
+  int32_t done;           // 1: stop decided -- later speculative kernels exit
+  int32_t tol_not_met;    // 1: stopped at the rank cap with E > tau
+  int32_t rounds;         // estimates computed
+  uint32_t err;           // kErr* bits
+  uint32_t zero_pivots;   // exactly zero pivot columns met
+  uint32_t bar_count;     // grid barrier: arrivals
+  uint32_t bar_gen;       // grid barrier: generation
+  uint32_t pad[5];
+};
+static_assert(sizeof(DevState) <= 256, "DevState must fit its 256-byte slot");
+
+// ------------------------------------------------------------------ memory order
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Upper bound on any single device-side wait (nanoseconds).
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
+// wait is bounded: after kWaitLimitNs the block records kErrTimeout and the
+// barrier returns false; callers then leave the kernel.  Returns true when
+// every block arrived.
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    unsigned gen = ld_acquire_u32(&st->bar_gen);
+    unsigned arrived = atom_add_acqrel_u32(&st->bar_count, 1u) + 1u;
+    if (arrived == nblocks) {
+      st->bar_count = 0u;
+      st_release_u32(&st->bar_gen, gen + 1u);
+    } else {
+      uint64_t t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if ((++spins & 255u) == 0u) {
+          if (ld_acquire_u32(&st->err) & kErrTimeout) { ok = 0; break; }
+          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicOr(&st->err, kErrTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ reductions
+// (value, index) argmax: larger |value| wins, ties go to the smaller index;
+// index < 0 means "no candidate".
+struct ArgMax {
+  double v;
+  int idx;
+};
+__device__ __forceinline__ ArgMax argmax_pick(ArgMax a, ArgMax b) {
+  if (b.idx < 0) return a;
+  if (a.idx < 0) return b;
+  if (b.v > a.v || (b.v == a.v && b.idx < a.idx)) return b;
+  return a;
+}
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ArgMax o;
+    o.v = __shfl_down_sync(0xffffffffu, a.v, off);
+    o.idx = __shfl_down_sync(0xffffffffu, a.idx, off);
+    a = argmax_pick(a, o);
+  }
+  return a;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Block-wide sum of one double per thread (blockDim.x multiple of 32, <= 1024);
+// result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double s_part[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_part[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? s_part[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) {
+  return x < T(0) ? -x : x;
+}
+
+}  // namespace rid

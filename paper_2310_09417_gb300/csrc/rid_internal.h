@@ -1,0 +1,107 @@
+// rid_internal.h -- launchers shared between the kernel files and the C-ABI
+// driver.  Every launcher enqueues on `s`, returns the launch error, and does
+// nothing when *done (a device flag) is already set, so rounds enqueued past
+// the stopping point cost only their launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rid_common.cuh"
+
+namespace rid {
+
+// Operand of the gather-GEMM: row r lives at base + (idx ? idx[r] : r) * ld + off.
+template <typename T>
+struct Operand {
+  const T* base;
+  int64_t ld;
+  const int32_t* idx;
+  int64_t off;
+};
+
+// Epilogues of the gather-GEMM.
+enum GemmEpi : int {
+  kEpiStore = 0,    // out[z*zstride + r*out_ld + c] = acc          (split-K partials)
+  kEpiSubRows = 1,  // out[out_idx[r]*out_ld + c] -= acc, rows with skip[r] != 0 left alone
+};
+
+template <typename T>
+struct EpiArgs {
+  T* out;
+  int64_t out_ld;
+  int64_t zstride;
+  const int32_t* out_idx;
+  const int32_t* skip;
+};
+
+// C (M x N) = sum_k A_r[k] * B(k, c).  A rows are contiguous along K.  B is
+// K-major (b_kmajor: row c contiguous along K) or N-major (row k contiguous
+// along N).  The K range is split across gridDim.z in chunks of `kchunk`.
+// The split count actually used (<= requested) is what gemm_splits() returns.
+int gemm_splits(int K, int splits);
+template <typename T>
+cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<T> a, Operand<T> b,
+                        int epi, EpiArgs<T> ep, const int32_t* done, cudaStream_t s);
+
+template <typename T>
+cudaError_t gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, T* out, int64_t ld,
+                          const int32_t* done, cudaStream_t s);
+
+// ||A||_F^2 partial sums (one per block, fixed partition) + finiteness check.
+template <typename T>
+cudaError_t norm2_partial(int64_t m, int64_t n, const T* A, int64_t lda, double* part, int nparts,
+                          DevState* st, cudaStream_t s);
+cudaError_t norm2_final(const double* part, int nparts, DevState* st, cudaStream_t s);
+
+// G[j*ldg + c] = sum_z P[z*zs + j*ldg + c]
+template <typename T>
+cudaError_t splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
+                          const int32_t* done, cudaStream_t s);
+
+// S[i*lds + c] = G[act[i]*ldg + col0 + c] - sum_z P[z*zs + i*lds + c]; e2part[blk] = sum S^2
+template <typename T>
+cudaError_t schur_finish(int na, int w, const int32_t* act, const T* G, int64_t ldg, int64_t col0,
+                         int nz, int64_t zs, const T* P, T* S, int64_t lds, double* e2part, int nparts,
+                         const int32_t* done, cudaStream_t s);
+
+// E = sqrt(sum e2part / w); stop test against tau (absolute or relative to ||A||_F).
+cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_rel, int64_t tb,
+                   int last, double* trace, int round, DevState* st, cudaStream_t s);
+
+// Cooperative LUPP of S (na x w, row-major, ld lds) for `steps` pivots.
+struct PanelCfg {
+  int grid;
+  int chunk;
+  int use_smem;
+  size_t smem;
+};
+template <typename T>
+PanelCfg panel_config(int na, int w, int num_sms);
+template <typename T>
+cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, T* S, int64_t lds,
+                       int32_t* piv, int32_t* pivmark, double* pivdiag, double* cand_v,
+                       int32_t* cand_i, T* cand_rows, DevState* st, cudaStream_t s);
+
+// Inverse of the unit-lower block L-hat(piv, 0:bt) (bt x bt, row-major).
+template <typename T>
+cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
+                 cudaStream_t s);
+
+// N = L-hat(rest) * Linv; X(tb:tb+bt, act[i]) = N(i,:) for non-pivot rows; pivorig = act[piv].
+template <typename T>
+cudaError_t make_n(int na, int bt, const T* S, int64_t lds, const T* Linv, const int32_t* pivmark,
+                   const int32_t* act, T* Nbuf, T* X, int64_t ldx, int64_t tb, const int32_t* piv,
+                   int32_t* pivorig, const int32_t* done, cudaStream_t s);
+
+// Drop the new pivots from the active list (stable), append them to J / perm32.
+cudaError_t compact(int na, int bt, const int32_t* act_in, int32_t* act_out, int32_t* pivmark,
+                    const int32_t* piv, int64_t* J, int32_t* perm32, int64_t tb, double* pivots_out,
+                    const double* pivdiag, const int32_t* done, cudaStream_t s);
+
+// X(:, perm32[q]) = e_q for q < k.
+template <typename T>
+cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cudaStream_t s);
+
+cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, cudaStream_t s);
+
+}  // namespace rid

@@ -1,0 +1,715 @@
+// rid_kernels.cu -- SIMT kernels of the randomized column ID (FP64 and FP32).
+//
+// Column-ID orientation (the paper's row ID of A^T, Sec. 4): the sketch is
+// Y = Omega A (b x n per block), stored transposed as G (n x rows, row-major:
+// row j holds the sketch of column j of A).  LUPP runs on the rows of G.
+// Rows are never physically swapped: the not-yet-pivoted rows are listed in
+// `act` (ascending column index of A), pivots in `perm32` / J, and rows are
+// gathered through these index lists.  The interpolation matrix is kept in
+// the caller's X buffer throughout (column j of X = row j of L2 L1^{-1}).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rid_internal.h"
+
+namespace rid {
+
+// Raise a kernel's dynamic shared-memory limit when a launch needs more than
+// the default 48 KB (tracked per kernel so the call is made once per size).
+template <typename K>
+static cudaError_t ensure_smem(K* func, size_t bytes, size_t* cached) {
+  if (bytes <= 48 * 1024 || bytes <= *cached) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(func),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *cached = bytes;
+  return e;
+}
+
+// ============================================================ Gaussian rows
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64
+// -> 128-bit products whose high halves are xored into the other words and the
+// round key, with the key bumped by two Weyl constants between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t& x0, uint64_t& x1, uint64_t& x2, uint64_t& x3,
+                                              uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+    const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+    const uint64_t y0 = hi1 ^ x1 ^ k0;
+    const uint64_t y2 = hi0 ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Box-Muller on two 53-bit uniforms in (0, 1].
+__device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, double& z1) {
+  const double u1 = (double)((a >> 11) + 1ull) * 0x1.0p-53;
+  const double u2 = (double)((b >> 11) + 1ull) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
+}
+
+template <typename T>
+__global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, T* __restrict__ out,
+                                int64_t ld, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int64_t nq = (m + 3) >> 2;
+  const int64_t total = rows * nq;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nq, q = e - i * nq;
+    uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + i), x2 = 0, x3 = 0;
+    philox4x64_10(x0, x1, x2, x3, seed, 0ull);
+    double z[4];
+    box_muller(x0, x1, z[0], z[1]);
+    box_muller(x2, x3, z[2], z[3]);
+    T* o = out + i * ld + 4 * q;
+    const int64_t lim = m - 4 * q;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < lim) o[j] = (T)z[j];
+  }
+}
+
+template <typename T>
+cudaError_t gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, T* out, int64_t ld,
+                          const int32_t* done, cudaStream_t s) {
+  const int64_t total = rows * ((m + 3) >> 2);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_gaussian_rows<T><<<(int)blocks, 256, 0, s>>>(seed, row0, rows, m, out, ld, done);
+  return cudaGetLastError();
+}
+
+// ============================================================ ||A||_F and finiteness
+template <typename T>
+__global__ void k_norm2_partial(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda,
+                                double* part, DevState* st) {
+  double acc = 0.0;
+  bool finite = true;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const T* a = A + j * lda;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = (double)a[i];
+      finite = finite && isfinite(v);
+      acc += v * v;
+    }
+  }
+  if (!finite) atomicOr(&st->err, kErrNonFinite);
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t norm2_partial(int64_t m, int64_t n, const T* A, int64_t lda, double* part, int nparts,
+                          DevState* st, cudaStream_t s) {
+  k_norm2_partial<T><<<nparts, 256, 0, s>>>(m, n, A, lda, part, st);
+  return cudaGetLastError();
+}
+
+__global__ void k_norm2_final(const double* part, int nparts, DevState* st) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) st->norm2_A = tot;
+}
+
+cudaError_t norm2_final(const double* part, int nparts, DevState* st, cudaStream_t s) {
+  k_norm2_final<<<1, 256, 0, s>>>(part, nparts, st);
+  return cudaGetLastError();
+}
+
+// ============================================================ gather-GEMM
+// 64 x 64 output tile per block, K step 16, 256 threads each owning a 4 x 4
+// sub-tile strided by 16 (rows ty + 16 i, columns tx + 16 j), so that shared
+// reads of a warp hit consecutive words and global writes are coalesced.
+constexpr int kGM = 64, kGN = 64, kGK = 16;
+
+template <typename T, bool BK, int EPI>
+__global__ void __launch_bounds__(256)
+    k_gemm_gather(int M, int N, int K, int kchunk, Operand<T> a, Operand<T> b, EpiArgs<T> ep,
+                  const int32_t* done) {
+  if (done != nullptr && *done) return;
+  __shared__ T As[kGK][kGM + 1];
+  __shared__ T Bs[kGK][kGN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+
+  // K-major loaders: row lr, four consecutive k starting at lk
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  const T* arow = nullptr;
+  if (m0 + lr < M) arow = a.base + (int64_t)(a.idx ? a.idx[m0 + lr] : m0 + lr) * a.ld + a.off;
+  const T* brow_k = nullptr;
+  if (BK && n0 + lr < N) brow_k = b.base + (int64_t)(b.idx ? b.idx[n0 + lr] : n0 + lr) * b.ld + b.off;
+  // N-major loader: k row lq, four consecutive columns starting at lc
+  const int lq = tid >> 4, lc = (tid & 15) * 4;
+
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+  for (int k0 = kbeg; k0 < kend; k0 += kGK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + lk + u;
+      As[lk + u][lr] = (arow != nullptr && k < kend) ? arow[k] : T(0);
+    }
+    if (BK) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + lk + u;
+        Bs[lk + u][lr] = (brow_k != nullptr && k < kend) ? brow_k[k] : T(0);
+      }
+    } else {
+      const int q = k0 + lq;
+      const T* br = nullptr;
+      if (q < kend) br = b.base + (int64_t)(b.idx ? b.idx[q] : q) * b.ld + b.off;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = n0 + lc + u;
+        Bs[lq][lc + u] = (br != nullptr && c < N) ? br[c] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + ty + 16 * i;
+    if (r >= M) continue;
+    if (EPI == kEpiStore) {
+      T* o = ep.out + blockIdx.z * ep.zstride + (int64_t)r * ep.out_ld;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = n0 + tx + 16 * j;
+        if (c < N) o[c] = acc[i][j];
+      }
+    } else {
+      if (ep.skip != nullptr && ep.skip[r] != 0) continue;
+      T* o = ep.out + (int64_t)(ep.out_idx ? ep.out_idx[r] : r) * ep.out_ld;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = n0 + tx + 16 * j;
+        if (c < N) o[c] -= acc[i][j];
+      }
+    }
+  }
+}
+
+static int split_chunk(int K, int splits) {
+  if (splits < 1) splits = 1;
+  int kchunk = (K + splits - 1) / splits;
+  return ((kchunk + kGK - 1) / kGK) * kGK;
+}
+
+int gemm_splits(int K, int splits) {
+  if (K <= 0) return 1;
+  const int kchunk = split_chunk(K, splits);
+  return (K + kchunk - 1) / kchunk;
+}
+
+template <typename T>
+cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<T> a, Operand<T> b,
+                        int epi, EpiArgs<T> ep, const int32_t* done, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int kchunk = split_chunk(K, splits);
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN, splits);
+  if (b_kmajor) {
+    if (epi == kEpiStore)
+      k_gemm_gather<T, true, kEpiStore><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, b, ep, done);
+    else
+      k_gemm_gather<T, true, kEpiSubRows><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, b, ep, done);
+  } else {
+    if (epi == kEpiStore)
+      k_gemm_gather<T, false, kEpiStore><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, b, ep, done);
+    else
+      k_gemm_gather<T, false, kEpiSubRows><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, b, ep, done);
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================ split-K reductions
+template <typename T>
+__global__ void k_splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* __restrict__ P,
+                                T* __restrict__ G, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int64_t total = n * rows;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / rows, c = e - j * rows;
+    const int64_t off = j * ldg + c;
+    T acc = P[off];
+    for (int z = 1; z < nz; ++z) acc += P[z * zs + off];
+    G[off] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
+                          const int32_t* done, cudaStream_t s) {
+  int64_t blocks = (n * rows + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_splitk_reduce<T><<<(int)blocks, 256, 0, s>>>(n, rows, ldg, nz, zs, P, G, done);
+  return cudaGetLastError();
+}
+
+// S = G(act, col0:col0+w) - sum of the split-K partials of L2 L1^{-1} G(perm, .)
+template <typename T>
+__global__ void k_schur_finish(int na, int w, const int32_t* __restrict__ act, const T* __restrict__ G,
+                               int64_t ldg, int64_t col0, int nz, int64_t zs, const T* __restrict__ P,
+                               T* __restrict__ S, int64_t lds, double* e2part, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  double acc2 = 0.0;
+  const int64_t total = (int64_t)na * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / w, c = e - i * w;
+    T v = G[(int64_t)act[i] * ldg + col0 + c];
+    T sub = T(0);
+    for (int z = 0; z < nz; ++z) sub += P[z * zs + i * lds + c];
+    v -= sub;
+    S[i * lds + c] = v;
+    acc2 += (double)v * (double)v;
+  }
+  const double tot = block_sum(acc2);
+  if (threadIdx.x == 0) e2part[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t schur_finish(int na, int w, const int32_t* act, const T* G, int64_t ldg, int64_t col0, int nz,
+                         int64_t zs, const T* P, T* S, int64_t lds, double* e2part, int nparts,
+                         const int32_t* done, cudaStream_t s) {
+  k_schur_finish<T><<<nparts, 256, 0, s>>>(na, w, act, G, ldg, col0, nz, zs, P, S, lds, e2part, done);
+  return cudaGetLastError();
+}
+
+__global__ void k_decide(const double* e2part, int nparts, int w, double tol, int tol_rel, int64_t tb,
+                         int last, double* trace, int round, DevState* st) {
+  if (st->done) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += e2part[i];
+  const double e2 = block_sum(acc);
+  if (threadIdx.x == 0) {
+    const double E = sqrt(e2 / (double)w);
+    const double thr = tol_rel ? tol * sqrt(st->norm2_A) : tol;
+    st->est = E;
+    st->thr = thr;
+    st->rounds = round + 1;
+    if (trace != nullptr) trace[round] = E;
+    if (E <= thr) {
+      st->done = 1;
+      st->k_final = tb;
+    } else if (last) {
+      st->done = 1;
+      st->k_final = tb;
+      st->tol_not_met = 1;
+    }
+  }
+}
+
+cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_rel, int64_t tb, int last,
+                   double* trace, int round, DevState* st, cudaStream_t s) {
+  k_decide<<<1, 256, 0, s>>>(e2part, nparts, w, tol, tol_rel, tb, last, trace, round, st);
+  return cudaGetLastError();
+}
+
+// ============================================================ LUPP panel
+// One cooperative launch factors S (na x w) for `steps` pivots.  Block b owns
+// rows [b*chunk, min(na, (b+1)*chunk)), staged in shared memory when they fit.
+// Each pivot step: block-local argmax of |S(i,c)| over unselected rows (ties
+// to the smallest row index = smallest column index of A, since `act` is
+// ascending), publication of (value, row, row contents) in a double-buffered
+// candidate slot, one bounded grid barrier, a redundant global argmax in
+// every block, then division by the pivot and the rank-1 update (Eq. lupps)
+// of the block's unselected rows.  Rows are marked, never swapped.
+__device__ __forceinline__ ArgMax block_argmax(ArgMax a) {
+  __shared__ double s_v[32];
+  __shared__ int s_i[32];
+  __shared__ ArgMax s_res;
+  a = warp_argmax(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_v[warp] = a.v;
+    s_i[warp] = a.idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    ArgMax b;
+    b.v = lane < nw ? s_v[lane] : -1.0;
+    b.idx = lane < nw ? s_i[lane] : -1;
+    b = warp_argmax(b);
+    if (lane == 0) s_res = b;
+  }
+  __syncthreads();
+  const ArgMax r = s_res;
+  __syncthreads();
+  return r;
+}
+
+constexpr int kPanelThreads = 256;
+constexpr int kPanelMaxW = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads)
+    k_panel_lupp(int na, int w, int steps, T* __restrict__ S, int64_t lds, int chunk, int use_smem,
+                 int32_t* piv, int32_t* pivmark, double* pivdiag, double* cand_v, int32_t* cand_i,
+                 T* cand_rows, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T prow[kPanelMaxW];
+  if (st->done) return;  // set before the launch or never during it: uniform over the grid
+  const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const int r0 = bid * chunk;
+  const int nr = max(0, min(na, r0 + chunk) - r0);
+  T* Ss = use_smem ? reinterpret_cast<T*>(smem_raw) : S + (int64_t)r0 * lds;
+  const int64_t ldl = use_smem ? w : lds;
+  unsigned char* sel = smem_raw + (use_smem ? (size_t)chunk * w * sizeof(T) : 0);
+
+  if (use_smem)
+    for (int e = tid; e < nr * w; e += blockDim.x) {
+      const int r = e / w, c = e - r * w;
+      Ss[e] = S[(int64_t)(r0 + r) * lds + c];
+    }
+  for (int r = tid; r < chunk; r += blockDim.x) sel[r] = 0;
+  __syncthreads();
+
+  for (int c = 0; c < steps; ++c) {
+    // 1. block-local candidate
+    ArgMax loc;
+    loc.v = -1.0;
+    loc.idx = -1;
+    for (int r = tid; r < nr; r += blockDim.x)
+      if (!sel[r]) {
+        ArgMax o;
+        o.v = (double)tabs(Ss[(int64_t)r * ldl + c]);
+        o.idx = r0 + r;
+        loc = argmax_pick(loc, o);
+      }
+    loc = block_argmax(loc);
+    // 2. publish it
+    const int slot = (c & 1) * nb + bid;
+    if (tid == 0) {
+      __stcg(&cand_v[slot], loc.v);
+      __stcg(&cand_i[slot], loc.idx);
+    }
+    if (loc.idx >= 0) {
+      const T* src = Ss + (int64_t)(loc.idx - r0) * ldl;
+      for (int cc = tid; cc < w; cc += blockDim.x) __stcg(&cand_rows[(int64_t)slot * w + cc], src[cc]);
+    }
+    __threadfence();
+    // 3. wait for every block
+    if (!grid_barrier(st, (unsigned)nb)) return;
+    // 4. global pivot, computed identically by every block
+    ArgMax g;
+    g.v = -1.0;
+    g.idx = -1;
+    for (int q = tid; q < nb; q += blockDim.x) {
+      ArgMax o;
+      o.v = __ldcg(&cand_v[(c & 1) * nb + q]);
+      o.idx = __ldcg(&cand_i[(c & 1) * nb + q]);
+      g = argmax_pick(g, o);
+    }
+    g = block_argmax(g);
+    const int pblk = g.idx / chunk;
+    for (int cc = tid; cc < w; cc += blockDim.x)
+      prow[cc] = __ldcg(&cand_rows[(int64_t)((c & 1) * nb + pblk) * w + cc]);
+    const bool zero = !(g.v > 0.0);
+    if (tid == 0) {
+      if (g.idx >= r0 && g.idx < r0 + nr) sel[g.idx - r0] = (unsigned char)1;
+      if (bid == 0) {
+        piv[c] = g.idx;
+        if (pivdiag != nullptr) pivdiag[c] = g.v;
+        if (zero) atomicAdd(&st->zero_pivots, 1u);
+      }
+    }
+    __syncthreads();
+    if (zero) continue;  // the column is exactly zero below: nothing to eliminate
+    // 5. multipliers l(i) = S(i,c) / pivot
+    const T pv = prow[c];
+    for (int r = tid; r < nr; r += blockDim.x)
+      if (!sel[r]) Ss[(int64_t)r * ldl + c] = Ss[(int64_t)r * ldl + c] / pv;
+    __syncthreads();
+    // 6. rank-1 update of the trailing columns (Eq. lupps)
+    const int wc = w - c - 1;
+    if (wc > 0)
+      for (int e = tid; e < nr * wc; e += blockDim.x) {
+        const int r = e / wc, cc = c + 1 + (e - r * wc);
+        if (!sel[r]) {
+          T* row = Ss + (int64_t)r * ldl;
+          row[cc] = fma(-row[c], prow[cc], row[cc]);
+        }
+      }
+    __syncthreads();
+  }
+  if (use_smem)
+    for (int e = tid; e < nr * w; e += blockDim.x) {
+      const int r = e / w, c = e - r * w;
+      S[(int64_t)(r0 + r) * lds + c] = Ss[e];
+    }
+  for (int r = tid; r < nr; r += blockDim.x) pivmark[r0 + r] = sel[r];
+}
+
+template <typename T>
+PanelCfg panel_config(int na, int w, int num_sms) {
+  PanelCfg cfg;
+  int grid = (na + 31) / 32;  // at least 32 rows per block
+  if (grid > num_sms) grid = num_sms;
+  if (grid < 1) grid = 1;
+  int chunk = (na + grid - 1) / grid;
+  grid = (na + chunk - 1) / chunk;
+  cfg.grid = grid;
+  cfg.chunk = chunk;
+  const size_t rows_bytes = (size_t)chunk * w * sizeof(T);
+  const size_t sel_bytes = ((size_t)chunk + 15) & ~(size_t)15;
+  cfg.use_smem = (rows_bytes + sel_bytes) <= (size_t)200 * 1024;
+  cfg.smem = (cfg.use_smem ? rows_bytes : 0) + sel_bytes;
+  return cfg;
+}
+
+template <typename T>
+cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, T* S, int64_t lds, int32_t* piv,
+                       int32_t* pivmark, double* pivdiag, double* cand_v, int32_t* cand_i, T* cand_rows,
+                       DevState* st, cudaStream_t s) {
+  static size_t cached = 0;
+  cudaError_t e = ensure_smem(k_panel_lupp<T>, cfg.smem, &cached);
+  if (e != cudaSuccess) return e;
+  int chunk = cfg.chunk, use_smem = cfg.use_smem;
+  void* args[] = {&na, &w, &steps, &S, &lds, &chunk, &use_smem, &piv, &pivmark,
+                  &pivdiag, &cand_v, &cand_i, &cand_rows, &st};
+  return cudaLaunchCooperativeKernel((const void*)k_panel_lupp<T>, dim3(cfg.grid), dim3(kPanelThreads), args,
+                                     cfg.smem, s);
+}
+
+// ============================================================ re-blocking
+// Inverse of the unit lower triangular L-hat(piv(0:bt), 0:bt): thread j forms
+// column j by forward substitution.
+template <typename T>
+__global__ void k_linv(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv,
+                       T* __restrict__ Linv, const int32_t* done) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt
+  for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) {
+    const int r = e / bt, c = e - r * bt;
+    Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : (c == r ? T(1) : T(0));
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < bt) {
+    for (int i = 0; i < bt; ++i) Linv[i * bt + j] = i == j ? T(1) : T(0);
+    for (int i = j + 1; i < bt; ++i) {
+      T acc = T(0);
+      for (int c = j; c < i; ++c) acc = fma(Lp[i * bt + c], Linv[c * bt + j], acc);
+      Linv[i * bt + j] = -acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
+                 cudaStream_t s) {
+  static size_t cached = 0;
+  cudaError_t e = ensure_smem(k_linv<T>, (size_t)bt * bt * sizeof(T), &cached);
+  if (e != cudaSuccess) return e;
+  const int threads = bt <= 32 ? 32 : (bt <= 64 ? 64 : 128);
+  k_linv<T><<<1, threads, (size_t)bt * bt * sizeof(T), s>>>(bt, S, lds, piv, Linv, done);
+  return cudaGetLastError();
+}
+
+// N(i, c) = sum_{c' >= c} L-hat(i, c') Linv(c', c) for non-pivot rows; the new
+// columns tb..tb+bt of X(:, act[i]) are N(i, :) (the new block of L2 L1^{-1}).
+template <typename T>
+__global__ void k_make_n(int na, int bt, const T* __restrict__ S, int64_t lds, const T* __restrict__ Linv,
+                         const int32_t* __restrict__ pivmark, const int32_t* __restrict__ act, T* __restrict__ Nbuf,
+                         T* __restrict__ X, int64_t ldx, int64_t tb, const int32_t* __restrict__ piv,
+                         int32_t* __restrict__ pivorig, const int32_t* done) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  T* Li = reinterpret_cast<T*>(smem_raw);
+  for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) Li[e] = Linv[e];
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < bt; c += blockDim.x) pivorig[c] = act[piv[c]];
+  __syncthreads();
+  const int64_t total = (int64_t)na * bt;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / bt;
+    const int c = (int)(e - i * bt);
+    if (pivmark[i]) continue;
+    const T* l = S + i * lds;
+    T acc = T(0);
+    for (int cp = c; cp < bt; ++cp) acc = fma(l[cp], Li[cp * bt + c], acc);
+    Nbuf[i * bt + c] = acc;
+    X[(int64_t)act[i] * ldx + tb + c] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t make_n(int na, int bt, const T* S, int64_t lds, const T* Linv, const int32_t* pivmark,
+                   const int32_t* act, T* Nbuf, T* X, int64_t ldx, int64_t tb, const int32_t* piv,
+                   int32_t* pivorig, const int32_t* done, cudaStream_t s) {
+  static size_t cached = 0;
+  cudaError_t e = ensure_smem(k_make_n<T>, (size_t)bt * bt * sizeof(T), &cached);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = ((int64_t)na * bt + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  k_make_n<T><<<(int)blocks, 256, (size_t)bt * bt * sizeof(T), s>>>(na, bt, S, lds, Linv, pivmark, act, Nbuf, X,
+                                                                      ldx, tb, piv, pivorig, done);
+  return cudaGetLastError();
+}
+
+// Stable removal of this round's pivots from the active list; one block.
+__global__ void __launch_bounds__(1024)
+    k_compact(int na, int bt, const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
+              int32_t* __restrict__ pivmark, const int32_t* __restrict__ piv, int64_t* __restrict__ J,
+              int32_t* __restrict__ perm32, int64_t tb, double* pivots_out, const double* pivdiag,
+              const int32_t* done) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  if (done != nullptr && *done) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = tid; c < bt; c += blockDim.x) {
+    const int32_t j = act_in[piv[c]];
+    J[tb + c] = j;
+    perm32[tb + c] = j;
+    if (pivots_out != nullptr) pivots_out[tb + c] = pivdiag[c];
+  }
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int start = 0; start < na; start += blockDim.x) {
+    const int i = start + tid;
+    const bool keep = i < na && pivmark[i] == 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+    const int before = __popc(ball & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[warp] = __popc(ball);
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = blockDim.x >> 5;
+      int v = lane < nw ? s_warp[lane] : 0;
+      // inclusive scan over warp totals
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += t;
+      }
+      s_warp[lane] = v;  // inclusive prefix
+    }
+    __syncthreads();
+    const int wbase = warp == 0 ? 0 : s_warp[warp - 1];
+    if (keep) act_out[s_base + wbase + before] = act_in[i];
+    if (i < na) pivmark[i] = 0;
+    __syncthreads();
+    if (tid == 0) s_base += s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+}
+
+cudaError_t compact(int na, int bt, const int32_t* act_in, int32_t* act_out, int32_t* pivmark, const int32_t* piv,
+                    int64_t* J, int32_t* perm32, int64_t tb, double* pivots_out, const double* pivdiag,
+                    const int32_t* done, cudaStream_t s) {
+  k_compact<<<1, 1024, 0, s>>>(na, bt, act_in, act_out, pivmark, piv, J, perm32, tb, pivots_out, pivdiag, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_finalize_x(int64_t k, const int32_t* __restrict__ perm32, T* __restrict__ X, int64_t ldx) {
+  const int64_t total = k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / k, c = e - q * k;
+    X[(int64_t)perm32[q] * ldx + c] = (c == q) ? T(1) : T(0);
+  }
+}
+
+template <typename T>
+cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  int64_t blocks = (k * k + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_finalize_x<T><<<(int)blocks, 256, 0, s>>>(k, perm32, X, ldx);
+  return cudaGetLastError();
+}
+
+__global__ void k_init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    st->norm2_A = 0.0;
+    st->est = 0.0;
+    st->thr = 0.0;
+    st->k_final = -1;
+    st->done = 0;
+    st->tol_not_met = 0;
+    st->rounds = 0;
+    st->err = 0u;
+    st->zero_pivots = 0u;
+    st->bar_count = 0u;
+    st->bar_gen = 0u;
+  }
+  if (i < n) {
+    act[i] = (int32_t)i;
+    pivmark[i] = 0;
+  }
+}
+
+cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, cudaStream_t s) {
+  const int64_t blocks = (n + 255) / 256;
+  k_init_state<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(st, act, pivmark, n);
+  return cudaGetLastError();
+}
+
+// ============================================================ instantiations
+#define RID_INST(T)                                                                                         \
+  template cudaError_t gemm_gather<T>(int, int, int, int, bool, Operand<T>, Operand<T>, int, EpiArgs<T>,    \
+                                      const int32_t*, cudaStream_t);                                        \
+  template cudaError_t gaussian_rows<T>(uint64_t, int64_t, int64_t, int64_t, T*, int64_t, const int32_t*,   \
+                                        cudaStream_t);                                                      \
+  template cudaError_t norm2_partial<T>(int64_t, int64_t, const T*, int64_t, double*, int, DevState*,       \
+                                        cudaStream_t);                                                      \
+  template cudaError_t splitk_reduce<T>(int64_t, int, int64_t, int, int64_t, const T*, T*, const int32_t*,  \
+                                        cudaStream_t);                                                      \
+  template cudaError_t schur_finish<T>(int, int, const int32_t*, const T*, int64_t, int64_t, int, int64_t,  \
+                                       const T*, T*, int64_t, double*, int, const int32_t*, cudaStream_t);  \
+  template PanelCfg panel_config<T>(int, int, int);                                                         \
+  template cudaError_t panel_lupp<T>(const PanelCfg&, int, int, int, T*, int64_t, int32_t*, int32_t*,       \
+                                     double*, double*, int32_t*, T*, DevState*, cudaStream_t);              \
+  template cudaError_t linv<T>(int, const T*, int64_t, const int32_t*, T*, const int32_t*, cudaStream_t);   \
+  template cudaError_t make_n<T>(int, int, const T*, int64_t, const T*, const int32_t*, const int32_t*, T*, \
+                                 T*, int64_t, int64_t, const int32_t*, int32_t*, const int32_t*,            \
+                                 cudaStream_t);                                                             \
+  template cudaError_t finalize_x<T>(int64_t, const int32_t*, T*, int64_t, cudaStream_t);
+
+RID_INST(double)
+RID_INST(float)
+
+}  // namespace rid

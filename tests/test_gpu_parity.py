@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.
+
+Bars: skeletons J bit-exact on well-separated spectra; X and the estimate within
+1e-10 (relative to max(1, max|X|)) in FP64.  FP32 runs are compared on what a
+single-precision LU can reproduce (see the individual tests).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2310_09417_gb300 import workloads as W  # noqa: E402
+
+X_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_09417_gb300 import build
+    build.build()
+    from paper_2310_09417_gb300 import binding
+    binding.load()
+    return binding
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def dev_cm(A, dtype=torch.float64):
+    from paper_2310_09417_gb300 import binding
+    return binding.colmajor(torch.from_numpy(np.asarray(A)).to("cuda", dtype))
+
+
+def assert_x_close(Xg, Xo, tol=X_TOL):
+    Xg = Xg.detach().cpu().numpy().astype(np.float64)
+    scale = max(1.0, float(np.abs(Xo).max()))
+    err = float(np.abs(Xg - Xo).max()) / scale
+    assert err <= tol, "X differs by %.3e (relative)" % err
+
+
+# ---------------------------------------------------------------- Omega
+def test_gaussian_rows_match_oracle(B, orc):
+    """Same Philox4x64-10 counters and Box-Muller map on both sides; the only
+    difference is libm vs CUDA log/sincospi in the last bits."""
+    g = B.gaussian_rows(2310_09417, 5, 37, 1001, dtype=torch.float64).cpu().numpy()
+    o = orc.gaussian_rows(2310_09417, 5, 37, 1001)
+    np.testing.assert_allclose(g, o, rtol=1e-14, atol=1e-14)
+    g32 = B.gaussian_rows(7, 0, 3, 130, dtype=torch.float32).cpu().numpy()
+    np.testing.assert_allclose(g32, orc.gaussian_rows(7, 0, 3, 130).astype(np.float32), rtol=1e-6)
+
+
+# ---------------------------------------------------------------- fixed rank
+@pytest.mark.parametrize("m,n,k,l,b", [
+    (2000, 2000, 100, 120, 64),   # the 2000 x 2000 fixed-rank workload
+    (257, 203, 37, 45, 16),       # ragged everything
+    (90, 300, 64, 64, 64),        # l = k: no estimate rows
+    (300, 150, 1, 9, 64),         # k = 1
+    (64, 500, 64, 70, 32),        # k = m
+])
+def test_fixed_rank_parity_f64(B, orc, m, n, k, l, b):
+    s = W.spectrum("geometric", min(m, n))
+    A = W.spectral_matrix(m, n, s, seed=m + n)
+    Om = W.gaussian_omega(k + l, l, m)
+    g = B.id_fixed_rank(dev_cm(A), k, l, block=b, omega=dev(Om))
+    r = orc.id_fixed_rank(A, Om, k)
+    assert g.status == 0
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"])
+    if l > k:
+        assert g.est_err == pytest.approx(r["est"], rel=1e-10)
+    else:
+        assert g.est_err == 0.0
+    assert g.norm_A == pytest.approx(orc.fro_norm(A), rel=1e-13)
+
+
+def test_fixed_rank_relative_error_matches(B, orc):
+    m = n = 2000
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=1)
+    Om = W.gaussian_omega(2, 120, m)
+    g = B.id_fixed_rank(dev_cm(A), 100, 120, omega=dev(Om))
+    r = orc.id_fixed_rank(A, Om, 100)
+    eg = orc.id_residual(A, g.J.cpu().numpy(), g.X.cpu().numpy()) / orc.fro_norm(A)
+    eo = orc.id_residual(A, r["J"], r["X"]) / orc.fro_norm(A)
+    assert abs(eg - eo) <= 1e-10 * eo
+
+
+# ---------------------------------------------------------------- adaptive
+@pytest.mark.parametrize("kind,m,n,b,tol", [
+    ("geometric", 600, 500, 32, 1e-6),
+    ("fast_decay", 400, 400, 16, 1e-8),
+    ("poly", 700, 333, 64, 1e-3),
+    ("geometric", 1000, 257, 20, 1e-9),
+])
+def test_adaptive_parity_f64(B, orc, kind, m, n, b, tol):
+    A = W.spectral_matrix(m, n, W.spectrum(kind, min(m, n)), seed=m * 7 + n)
+    Om = W.gaussian_omega(n, orc.rows_needed(n, b, m=m), m)
+    g = B.id_adaptive(dev_cm(A), tol, block=b, omega=dev(Om))
+    r = orc.id_adaptive(A, Om, b, tol * orc.fro_norm(A))
+    assert g.status == r["status"]
+    assert g.k == r["k"] and g.rounds == r["rounds"]
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"])
+    np.testing.assert_allclose(g.trace, r["trace"], rtol=1e-9)
+
+
+def test_adaptive_absolute_tolerance_and_kahan(B, orc):
+    A = W.kahan(300)
+    b = 16
+    Om = W.gaussian_omega(3, orc.rows_needed(300, b), 300)
+    g = B.id_adaptive(dev_cm(A), 1e-5, block=b, relative=False, omega=dev(Om))
+    r = orc.id_adaptive(A, Om, b, 1e-5)
+    assert g.k == r["k"]
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"])
+
+
+def test_adaptive_k0_and_multiblock_passes_do_not_change_result(B, orc):
+    """Sketching several blocks per pass over A (the rank guess k0, or
+    blocks_per_pass) gives the same J, X and k as the one-block loop: the
+    counter-based rows are the same and LUPP pivots of the first columns do
+    not depend on later columns (Sec. 5.2: randLUPPadap equals randLUPP with
+    the same total sketch)."""
+    m, n, b = 800, 600, 32
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=30.0), seed=5)
+    Ad = dev_cm(A)
+    base = B.id_adaptive(Ad, 1e-7, block=b, seed=11)
+    for kw in (dict(k0=100), dict(k0=500), dict(blocks_per_pass=3), dict(k0=64, blocks_per_pass=2)):
+        g = B.id_adaptive(Ad, 1e-7, block=b, seed=11, **kw)
+        assert g.k == base.k
+        assert torch.equal(g.J, base.J)
+        assert_x_close(g.X, base.X.cpu().numpy(), tol=1e-12)
+        assert g.passes <= base.passes
+    g = B.id_adaptive(Ad, 1e-7, block=b, seed=11, k0=base.k)
+    assert g.passes == 1
+
+
+def test_adaptive_generated_omega_matches_oracle_generator(B, orc):
+    m, n, b = 500, 400, 32
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=9)
+    seed = 424242
+    g = B.id_adaptive(dev_cm(A), 1e-6, block=b, seed=seed)
+    Om = orc.gaussian_rows(seed, 0, orc.rows_needed(n, b), m)
+    r = orc.id_adaptive(A, Om, b, 1e-6 * orc.fro_norm(A))
+    assert g.k == r["k"]
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"], tol=1e-9)
+
+
+# ---------------------------------------------------------------- FP32
+def test_adaptive_f32_against_f64_oracle(B, orc):
+    """FP32 sketch/LU: the rank matches the FP64 oracle's, the skeletons overlap
+    almost entirely, and the achieved ID error is within 1.2x of the oracle's."""
+    m, n, b = 1200, 800, 32
+    A = W.spectral_matrix(m, n, W.spectrum("poly", n), seed=12)
+    A32 = A.astype(np.float32)
+    Om = W.gaussian_omega(13, orc.rows_needed(n, b), m).astype(np.float32)
+    tol = 1e-4
+    g = B.id_adaptive(dev_cm(A32, torch.float32), tol, block=b, omega=dev(Om, torch.float32))
+    r = orc.id_adaptive(A32.astype(np.float64), Om.astype(np.float64), b,
+                        tol * orc.fro_norm(A32.astype(np.float64)))
+    assert abs(g.k - r["k"]) <= b
+    kk = min(g.k, r["k"])
+    overlap = len(set(g.J.cpu().numpy()[:kk]) & set(r["J"][:kk])) / kk
+    assert overlap >= 0.95
+    A64 = A32.astype(np.float64)
+    eg = orc.id_residual(A64, g.J.cpu().numpy(), g.X.cpu().numpy().astype(np.float64))
+    eo = orc.id_residual(A64, r["J"], r["X"])
+    assert eg <= 1.2 * eo
+    assert eg <= tol * orc.fro_norm(A64) * 3
+
+
+def test_fixed_rank_f32_prefix(B, orc):
+    m, n = 1000, 700
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=14).astype(np.float32)
+    Om = W.gaussian_omega(15, 60, m).astype(np.float32)
+    g = B.id_fixed_rank(dev_cm(A, torch.float32), 50, 60, omega=dev(Om, torch.float32))
+    r = orc.id_fixed_rank(A.astype(np.float64), Om.astype(np.float64), 50)
+    # first pivots are well separated: identical even in FP32
+    assert np.array_equal(g.J.cpu().numpy()[:20], r["J"][:20])
+    assert_x_close(g.X[:20], r["X"][:20], tol=1e-3)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_full_rank_and_rank_cap(B, orc):
+    m, n, b = 90, 70, 16
+    A = np.random.default_rng(3).standard_normal((m, n))
+    Om = W.gaussian_omega(4, orc.rows_needed(n, b), m)
+    g = B.id_adaptive(dev_cm(A), 0.0, block=b, relative=False, omega=dev(Om))
+    assert g.k == n and g.status == 0 and g.est_err == 0.0
+    assert sorted(g.J.cpu().tolist()) == list(range(n))
+    np.testing.assert_array_equal(g.X[:, g.J].cpu().numpy(), np.eye(n))
+    g = B.id_adaptive(dev_cm(A), 0.0, block=b, relative=False, k_max=40, omega=dev(Om))
+    r = orc.id_adaptive(A, Om, b, 0.0, kmax=40)
+    assert g.k == 40 == r["k"] and g.status == B.WARN_TOL_NOT_MET
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"])
+
+
+def test_wide_matrix_caps_at_m(B, orc):
+    m, n, b = 40, 300, 16
+    A = np.random.default_rng(5).standard_normal((m, n))
+    Om = W.gaussian_omega(6, orc.rows_needed(n, b, m=m), m)
+    g = B.id_adaptive(dev_cm(A), 1e-12, block=b, omega=dev(Om))
+    r = orc.id_adaptive(A, Om, b, 1e-12 * orc.fro_norm(A))
+    assert g.k == r["k"] == m
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    assert_x_close(g.X, r["X"], tol=1e-9)
+
+
+def test_block_larger_than_problem(B, orc):
+    m, n, b = 30, 20, 64
+    A = np.random.default_rng(7).standard_normal((m, n))
+    Om = W.gaussian_omega(8, orc.rows_needed(n, b), m)
+    g = B.id_adaptive(dev_cm(A), 1e-3, block=b, omega=dev(Om))
+    r = orc.id_adaptive(A, Om, b, 1e-3 * orc.fro_norm(A))
+    assert g.k == r["k"] == n
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+
+
+def test_ties_go_to_smallest_column(B, orc):
+    """Duplicate and zero columns: equal pivot magnitudes resolve to the
+    smallest column index on both sides; zero pivots are flagged."""
+    m, n = 60, 40
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((m, n))
+    A[:, 17] = A[:, 5]
+    A[:, 30] = A[:, 5]
+    A[:, 8] = 0.0
+    Om = W.gaussian_omega(10, n, m)
+    g = B.id_fixed_rank(dev_cm(A), 38, 40, omega=dev(Om))
+    r = orc.id_fixed_rank(A, Om, 38)
+    assert np.array_equal(g.J.cpu().numpy(), r["J"])
+    # rank 37: copies of column 5 become exactly zero once 5 is a pivot, and the
+    # 38th pivot is a tie among the zero rows {8, 17, 30}: the smallest, 8, wins
+    assert 5 in r["J"] and 8 in r["J"] and 17 not in r["J"] and 30 not in r["J"]
+    assert g.status & B.WARN_ZERO_PIVOT
+
+
+def test_nonfinite_input_is_rejected(B):
+    A = torch.ones(50, 40, dtype=torch.float64, device="cuda")
+    A[3, 7] = float("nan")
+    with pytest.raises(B.IDError) as e:
+        B.id_adaptive(B.colmajor(A), 1e-3)
+    assert e.value.code == B.ERR_NONFINITE
+
+
+def test_bad_arguments_return_codes(B):
+    import ctypes
+    A = B.colmajor(torch.randn(50, 40, dtype=torch.float64, device="cuda"))
+    with pytest.raises(B.IDError) as e:
+        B.id_fixed_rank(A, 45, 50)  # k > n
+    assert e.value.code == -2
+    o = B._opts(A, block=16, tol=1e-3, relative=True, k_max=0, k0=0, blocks_per_pass=1, seed=0,
+                omega=None, profile=False)
+    need = B.workspace_size(A, o)
+    ws = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    J = torch.empty(40, dtype=torch.int64, device="cuda")
+    X = torch.empty((40, 40), dtype=torch.float64, device="cuda")
+    res = B.IdResult()
+    res.J, res.X, res.ldx = J.data_ptr(), X.data_ptr(), 40
+    rc = B.load().id_adaptive(ctypes.byref(B._matrix(A)), ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                              ctypes.byref(res), torch.cuda.current_stream().cuda_stream)
+    assert rc == B.ERR_WORKSPACE
+
+
+def test_profile_phases_and_launch_count(B):
+    A = B.colmajor(torch.randn(400, 300, dtype=torch.float64, device="cuda"))
+    g = B.id_adaptive(A, 1e-2, block=32, profile=True)
+    assert g.launches == sum(g.phase_launches.values()) > 0
+    assert g.phase_ms["sketch"] > 0 and g.phase_ms["lu"] > 0

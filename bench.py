@@ -1,0 +1,368 @@
+"""Benchmark: adaptive randomized column ID (Algorithm 1 of arXiv:2310.09417) on
+GB300, on the 40000 x 10000 workloads (A = U diag(s) V^T with the polynomial
+spectrum s_j = (1+j)^-2 or the step spectrum, sketch block b = 64, relative
+tolerance 1e-6 in FP32 and 1e-10 in FP64).
+
+One step = one complete adaptive ID (every step of the hot path: Gaussian rows,
+sketch GEMM, Schur complement and its FP64 norm, stop test, LUPP, re-blocking,
+interpolation matrix) on inputs resident in HBM.  The metric is throughput in
+algorithmic GFLOP/s at the fixed relative error; ms_per_step is the ID time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Multi-GPU: one ID does not shard across GPUs here, so N ranks run N
+independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ID time & GFLOP/s at fixed rel. error; mixed/batched/learned vs plain FP64"
+UNIT = "GFLOP/s"
+
+WORKLOADS = {
+    # name: (m, n, spectrum kind, kwargs, dtype, rel tol, block)
+    "adaptive_poly_f32": (40000, 10000, "poly", {}, "f32", 1e-6, 64),
+    "adaptive_step_f32": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f32", 1e-6, 64),
+    "adaptive_poly_f64": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
+    "adaptive_step_f64": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64", 1e-10, 64),
+    # reduced sizes of the same families, for profiler captures (inputs still > L2)
+    "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
+    "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
+}
+DEFAULT_WORKLOAD = "adaptive_poly_f64"
+# Peaks of the plain-ALU paths, from unit counts x maximum SM clock (2070 MHz):
+# FP32: 152 SMs x 128 FMA lanes x 2 flops; FP64: the 1.25 TFLOP/s GB300 rate.
+ALU_PEAK_TFLOPS = {"f32": 152 * 128 * 2 * 2.070e9 / 1e12, "f64": 1.25}
+
+
+def algorithmic_flops(m: int, n: int, k: int, b: int) -> float:
+    """Flops the method must perform for a rank-k ID with block b: the sketch of
+    k + b rows (incl. the last estimation block), per round the triangular solve,
+    Schur update and panel LU at rank tb, and the final interpolation solve."""
+    f = 2.0 * m * n * (k + b)
+    tb = 0
+    while tb < k:
+        f += b * tb * tb + 2.0 * (n - tb) * tb * b + (n - tb) * b * b
+        tb += b
+    f += float(k) * k * (n - k)
+    return f
+
+
+def make_input(name, device, seed=2310_09417 + 1):
+    import torch
+
+    from paper_2310_09417_gb300 import workloads as W
+    m, n, kind, kw, dt, _, _ = WORKLOADS[name]
+    s = W.spectrum(kind, n, **kw)
+    dtype = torch.float32 if dt == "f32" else torch.float64
+    if dt == "f32":
+        # U, V from an FP32 QR; the product in FP32 (TF32 off): the rounding of A
+        # (~6e-8 relative) is far below the 1e-6 tolerance
+        torch.backends.cuda.matmul.allow_tf32 = False
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+
+        def haar(rows, cols):
+            G = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float32)
+            Q, R = torch.linalg.qr(G)
+            d = torch.sign(torch.diagonal(R))
+            d[d == 0] = 1
+            return Q * d
+        U = haar(m, n)
+        V = haar(n, n)
+        At = (V * torch.as_tensor(s, dtype=torch.float32, device=device)) @ U.T
+        del U, V
+    else:
+        At = W.spectral_matrix_torch(m, n, s, seed, torch.float64, device)
+    torch.cuda.synchronize()
+    return At.t()  # (m, n) column-major view
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
+    """The FP64 oracle as it stands, on the first `rounds` rounds of Algorithm 1
+    over the full matrix (the run stops at k_max = rounds * b).  Returns
+    (GFLOP/s, seconds, threads, description)."""
+    import numpy as np
+
+    import oracle
+    m, n, _, _, _, tol, b = WORKLOADS[name]
+    kmax = rounds * b
+    Om = oracle.gaussian_rows(seed, 0, (rounds + 1) * b, m)
+    t0 = time.perf_counter()
+    r = oracle.id_adaptive(A_host_f64, Om, b, tol * 1.0, kmax=kmax)
+    dt = time.perf_counter() - t0
+    k = r["k"]
+    flops = algorithmic_flops(m, n, k, b)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = ("oracle (plain C, FP64, OpenMP) on the first %d rounds of Algorithm 1 over the full "
+            "%dx%d matrix (k_max = %d), %.1f s" % (rounds, m, n, kmax, dt))
+    del np
+    return flops / dt / 1e9, dt, threads, desc
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    name = args.workload
+    m, n, kind, kw, dt, tol, b = WORKLOADS[name]
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if dev is not None:
+        A = make_input(name, dev)
+        A_host = np.asfortranarray(A.t().contiguous().cpu().numpy().T.astype(np.float64))
+        del A
+    else:  # no GPU: same family, host generation at reduced size
+        from paper_2310_09417_gb300 import workloads as W
+        A_host = W.spectral_matrix(m // 10, n // 10, W.spectrum(kind, n // 10, **kw), 1)
+    rounds = args.ref_rounds
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        v, sec, threads, desc = cpu_oracle_sample(A_host, name, seed=2310_09417 + i, rounds=rounds)
+        if i >= args.warmup:
+            times.append(sec)
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(name, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(name, res):
+    m, n, kind, kw, dt, tol, b = WORKLOADS[name]
+    spec = {"poly": "s_j = (1+j)^-2", "step": "rank 600 at 1, then 1e-9"}[kind]
+    if name.startswith("small_"):
+        spec += " (reduced size for profiling)"
+    c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
+         "precision": dt, "omega": "Philox4x64-10 Gaussian, generated on the device",
+         "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * (4 if dt == "f32" else 8) / 1e9),
+         "parallelism": "replicas (one ID per GPU)"}
+    if res is not None:
+        c.update({"k": res.k, "rounds": res.rounds, "passes": res.passes})
+    return c
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rounds", type=int, default=6)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2310_09417_gb300 import binding as B
+    from paper_2310_09417_gb300 import build
+    build.build()
+    B.load()
+
+    name = args.workload
+    m, n, kind, kw, dt, tol, b = WORKLOADS[name]
+    A = make_input(name, dev)
+    seed = 2310_09417 + 100 * rank
+    kmax = min(m, n)
+    xdt = torch.float32 if dt == "f32" else torch.float64
+    J = torch.empty(kmax, dtype=torch.int64, device=dev)
+    Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
+    opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
+                   omega=None, profile=True)
+    ws = torch.empty(B.workspace_size(A, opts), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(profile=True):
+        return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
+                             workspace=ws, out=(J, Xbuf), stream=stream)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms_local)
+    res = results[-1]
+    flops = algorithmic_flops(m, n, res.k, b)
+    value = flops * world / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the sketch GEMM (+ its split-K reduction)
+    sk_ms = sum(r.phase_ms["sketch"] for r in results) / args.steps
+    sk_launches = results[-1].phase_launches["sketch"]
+    sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
+    achieved = sk_flops / (sk_ms * 1e-3) / 1e12
+    peak = ALU_PEAK_TFLOPS[dt]
+    phase_share = {k: round(v / max(1e-9, sum(res.phase_ms.values())), 4) for k, v in res.phase_ms.items()}
+    roofline = {"bound": "alu", "kernel": "k_gemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
+                                                 else "GB300 FP64 rate 1.25 TFLOP/s"),
+                "phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
+                "phase_share": phase_share, "sketch_launches_per_step": sk_launches}
+    gpu_launches = sum(r.launches for r in results)
+
+    # end to end: pinned host A -> device, ID, J and X back to pinned host
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((n, m), dtype=A.dtype, pin_memory=True)
+        A_host.copy_(A.t())
+        A_dev = torch.empty((n, m), dtype=A.dtype, device=dev)
+        X_host = torch.empty((n, kmax), dtype=xdt, pin_memory=True)
+        J_host = torch.empty(kmax, dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            A_dev.copy_(A_host, non_blocking=True)
+            r = B.id_adaptive(A_dev.t(), tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
+                              workspace=ws, out=(J, Xbuf), stream=stream)
+            kk = r.k
+            X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
+            J_host[:kk].copy_(J[:kk], non_blocking=True)
+            return r
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        el = A.element_size()
+        e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": m * n * el,
+               "d2h_bytes_per_step": r.k * n * el + 8 * r.k}
+        del A_host, A_dev, X_host
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_host64 = np.asfortranarray(A.t().contiguous().cpu().numpy().T.astype(np.float64))
+        v, sec, threads, desc = cpu_oracle_sample(A_host64, name, seed=seed, rounds=args.ref_rounds)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        del A_host64
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dt, "data": "synthetic",
+                "config": config_dict(name, res), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clk.summary(),
+                "result": {"k": res.k, "est_err_rel": res.est_err / res.norm_A, "status": res.status,
+                           "gflop_per_id": flops / 1e9}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

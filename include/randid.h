@@ -172,6 +172,34 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
 /* Human-readable text for a status value. */
 const char* id_status_string(int status);
 
+/* Bytes of the library-owned device buffer behind id_fixed_rank_noalloc. */
+#define ID_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* id_fixed_rank for callers that cannot allocate device memory.  The paper has
+   no counterpart: this is a deployment variant of id_fixed_rank.
+
+   Some callers may not call cudaMalloc at all, or not at the moment they need
+   an ID.  Examples: a host application that reserved the GPU's memory up front
+   for its own pool, or a loop with latency or certification rules that forbid
+   device allocation after start-up, since cudaMalloc and cudaFree can block the
+   device.  They still own and pass A, J and X; the scratch the method needs
+   comes from one buffer of ID_NOALLOC_SCRATCH_BYTES that the library defines as
+   a static device array.  Every GPU that loads the library holds that buffer
+   until the process exits.
+
+   Arguments and results are those of id_fixed_rank (without ws / ws_bytes);
+   opts->profile is ignored (no timing events are created).  A problem whose
+   scratch (the id_workspace_size value for the same A, opts and l) exceeds
+   ID_NOALLOC_SCRATCH_BYTES is rejected with ID_ERR_WORKSPACE before anything
+   runs.  The first call on a device looks up the buffer's device address
+   (cudaGetSymbolAddress) with that device current; make that first call before
+   any stream capture.  Calls share the buffer and each call re-initialises what
+   it reads, but calls that overlap on the GPU (other streams, other host
+   threads) race on it: serialise them.  Nothing here calls cudaMalloc, cudaFree
+   or an allocating library routine. */
+int id_fixed_rank_noalloc(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts,
+                          id_result* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

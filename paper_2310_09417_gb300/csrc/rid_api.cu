@@ -587,3 +587,52 @@ const char* id_status_string(int status) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- fixed rank without allocation
+// Scratch for id_fixed_rank_noalloc: a static device array, so that callers
+// who may not allocate device memory still get a working ID.  In host code
+// `g_noalloc_scratch` names a host-side stand-in; kernels only ever receive the
+// device address that cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ID_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the lookup needs that device current and must not run while a
+// stream is being captured).
+int noalloc_scratch(void** out) {
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ID_ERR_CUDA;
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return ID_ERR_CUDA;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return ID_OK;
+}
+
+}  // namespace
+
+extern "C" int id_fixed_rank_noalloc(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts,
+                                     id_result* out, void* stream) {
+  Plan p;
+  int rc = make_plan(A, opts, k, l, &p);
+  if (rc != ID_OK) return rc == kBadA ? -1 : (rc == kBadOpts ? -4 : (rc == kBadK ? -2 : (rc == kBadL ? -3 : rc)));
+  if (check_out(p, out) != ID_OK) return -5;
+  if (p.total > ID_NOALLOC_SCRATCH_BYTES) return ID_ERR_WORKSPACE;  // does not fit the static buffer
+  void* ws = nullptr;
+  rc = noalloc_scratch(&ws);
+  if (rc != ID_OK) return rc;
+  id_opts o = *opts;
+  o.profile = 0;  // no event objects
+  clear_out(out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision_path(A, &o) == 64) {
+    Engine<double> e(p, A, &o, ws, out, s);
+    return e.run_fixed();
+  }
+  Engine<float> e(p, A, &o, ws, out, s);
+  return e.run_fixed();
+}

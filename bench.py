@@ -40,11 +40,24 @@ WORKLOADS = {
     # reduced sizes of the same families, for profiler captures (inputs still > L2)
     "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
+    # mixed precision: A stored in BF16 = Gaussian factor product of rank 1500 + 1e-4 noise,
+    # sketch on the tensor cores (BF16 x BF16 -> FP32), LU in FP32, norms in FP64
+    "mixed_bf16": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 1e-3, 64),
+    "mixed_bf16_tol3e-3": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-3, 64),
+    "small_mixed_bf16": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "bf16", 1e-3, 64),
 }
 DEFAULT_WORKLOAD = "adaptive_poly_f64"
 # Peaks of the plain-ALU paths, from unit counts x maximum SM clock (2070 MHz):
 # FP32: 152 SMs x 128 FMA lanes x 2 flops; FP64: the 1.25 TFLOP/s GB300 rate.
 ALU_PEAK_TFLOPS = {"f32": 152 * 128 * 2 * 2.070e9 / 1e12, "f64": 1.25}
+# Measured copy bandwidth of the GB300s (fallback: the recipe's 6.8 TB/s).
+try:
+    PEAKS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+except (OSError, ValueError):
+    PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes per sketch launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures summarised under profiles/, scaled to the full size by the A bytes read.
+PROFILED_TRAFFIC = {"adaptive_poly_f64": 3.38e9}
 
 
 def algorithmic_flops(m: int, n: int, k: int, b: int) -> float:
@@ -65,6 +78,23 @@ def make_input(name, device, seed=2310_09417 + 1):
 
     from paper_2310_09417_gb300 import workloads as W
     m, n, kind, kw, dt, _, _ = WORKLOADS[name]
+    if kind == "lowrank":
+        # A^T = G2^T G1^T + noise (n x m row-major == A column-major), rounded to BF16
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        r = kw["rank"]
+        G1t = torch.randn(r, m, generator=g, device=device, dtype=torch.float32)
+        G2t = torch.randn(n, r, generator=g, device=device, dtype=torch.float32)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        At = torch.empty((n, m), dtype=torch.bfloat16, device=device)
+        for j0 in range(0, n, 2048):  # bounded temporaries
+            blk = G2t[j0:j0 + 2048] @ G1t
+            blk += kw["noise"] * torch.randn(blk.shape, generator=g, device=device, dtype=torch.float32)
+            At[j0:j0 + 2048] = blk.to(torch.bfloat16)
+            del blk
+        del G1t, G2t
+        torch.cuda.synchronize()
+        return At.t()
     s = W.spectrum(kind, n, **kw)
     dtype = torch.float32 if dt == "f32" else torch.float64
     if dt == "f32":
@@ -139,6 +169,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def ref_rounds(args, name):
+    """Rounds of the oracle sample: about 3.4e11 flops of sketch (8 s on 16 Grace cores)."""
+    if args.ref_rounds > 0:
+        return args.ref_rounds
+    m, n, _, _, _, _, b = WORKLOADS[name]
+    return int(min(8, max(1, round(3.4e11 / (2.0 * m * n * b)))))
+
+
 def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
     """The FP64 oracle as it stands, on the first `rounds` rounds of Algorithm 1
     over the full matrix (the run stops at k_max = rounds * b).  Returns
@@ -173,12 +211,12 @@ def run_reference(args, rank, world):
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
     if dev is not None:
         A = make_input(name, dev)
-        A_host = np.asfortranarray(A.t().contiguous().cpu().numpy().T.astype(np.float64))
+        A_host = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
         del A
     else:  # no GPU: same family, host generation at reduced size
         from paper_2310_09417_gb300 import workloads as W
         A_host = W.spectral_matrix(m // 10, n // 10, W.spectrum(kind, n // 10, **kw), 1)
-    rounds = args.ref_rounds
+    rounds = ref_rounds(args, name)
     times, vals = [], []
     for i in range(args.warmup + args.steps):
         v, sec, threads, desc = cpu_oracle_sample(A_host, name, seed=2310_09417 + i, rounds=rounds)
@@ -198,12 +236,17 @@ def run_reference(args, rank, world):
 
 def config_dict(name, res):
     m, n, kind, kw, dt, tol, b = WORKLOADS[name]
-    spec = {"poly": "s_j = (1+j)^-2", "step": "rank 600 at 1, then 1e-9"}[kind]
+    spec = {"poly": "s_j = (1+j)^-2", "step": "rank 600 at 1, then 1e-9",
+            "lowrank": "G1 G2 (Gaussian factors, rank %s) + %s N(0,1) noise, stored in BF16"
+                       % (kw.get("rank"), kw.get("noise"))}[kind]
     if name.startswith("small_"):
         spec += " (reduced size for profiling)"
+    el = {"f32": 4, "f64": 8, "bf16": 2}[dt]
+    prec = {"f64": "FP64 sketch, LU and X", "f32": "FP32 sketch, LU and X",
+            "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
     c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
-         "precision": dt, "omega": "Philox4x64-10 Gaussian, generated on the device",
-         "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * (4 if dt == "f32" else 8) / 1e9),
+         "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device",
+         "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * el / 1e9),
          "parallelism": "replicas (one ID per GPU)"}
     if res is not None:
         c.update({"k": res.k, "rounds": res.rounds, "passes": res.passes})
@@ -219,7 +262,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-rounds", type=int, default=6)
+    ap.add_argument("--ref-rounds", type=int, default=0, help="oracle rounds per sample (0: sized to ~8 s)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -260,7 +303,7 @@ def main():
     A = make_input(name, dev)
     seed = 2310_09417 + 100 * rank
     kmax = min(m, n)
-    xdt = torch.float32 if dt == "f32" else torch.float64
+    xdt = torch.float64 if dt == "f64" else torch.float32
     J = torch.empty(kmax, dtype=torch.int64, device=dev)
     Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
     opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
@@ -296,17 +339,27 @@ def main():
     # roofline of the dominant kernel: the sketch GEMM (+ its split-K reduction)
     sk_ms = sum(r.phase_ms["sketch"] for r in results) / args.steps
     sk_launches = results[-1].phase_launches["sketch"]
-    sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
-    achieved = sk_flops / (sk_ms * 1e-3) / 1e12
-    peak = ALU_PEAK_TFLOPS[dt]
     phase_share = {k: round(v / max(1e-9, sum(res.phase_ms.values())), 4) for k, v in res.phase_ms.items()}
-    roofline = {"bound": "alu", "kernel": "k_gemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
-                                                 else "GB300 FP64 rate 1.25 TFLOP/s"),
-                "phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
-                "phase_share": phase_share, "sketch_launches_per_step": sk_launches}
+    if dt == "bf16":
+        # HBM-bound (64 flop/B against a ridge near 285): algorithmic bytes per pass =
+        # A (2mn) + one Omega block (2bm) + the FP32 sketch block written (4nb)
+        sk_bytes = (2.0 * m * n + 2.0 * b * m + 4.0 * n * b) * res.passes
+        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
+        peak = PEAKS["hbm_gbs"]
+        roofline = {"bound": "hbm", "kernel": "k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
+        achieved = sk_flops / (sk_ms * 1e-3) / 1e12
+        peak = ALU_PEAK_TFLOPS[dt]
+        roofline = {"bound": "alu", "kernel": "k_gemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": PROFILED_TRAFFIC.get(name),
+                    "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
+                                                     else "GB300 FP64 rate 1.25 TFLOP/s")}
+    roofline.update({"phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
+                     "phase_share": phase_share, "sketch_launches_per_step": sk_launches})
     gpu_launches = sum(r.launches for r in results)
 
     # end to end: pinned host A -> device, ID, J and X back to pinned host
@@ -339,15 +392,16 @@ def main():
         barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         el = A.element_size()
+        xel = torch.empty((), dtype=xdt).element_size()
         e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": m * n * el,
-               "d2h_bytes_per_step": r.k * n * el + 8 * r.k}
+               "d2h_bytes_per_step": r.k * n * xel + 8 * r.k}
         del A_host, A_dev, X_host
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_host64 = np.asfortranarray(A.t().contiguous().cpu().numpy().T.astype(np.float64))
-        v, sec, threads, desc = cpu_oracle_sample(A_host64, name, seed=seed, rounds=args.ref_rounds)
+        A_host64 = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
+        v, sec, threads, desc = cpu_oracle_sample(A_host64, name, seed=seed, rounds=ref_rounds(args, name))
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
         del A_host64
 

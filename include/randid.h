@@ -169,6 +169,17 @@ int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, voi
 int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype,
                      void* out, int64_t ld, void* stream);
 
+/* The sketch alone (Sec. 2.4; Algorithm 1 line 9): G = (Omega A)^T, n x rows,
+   row-major with row stride ldg >= rows (row j holds the sketch of column j).
+   omega: DEVICE, row-major rows x m, row stride ld_omega >= m, dtype sketch_prec.
+   Paths: A F64 / sketch F64 (FP64 FMA, G in FP64); A F32 / F32 (FP32 FMA, G in
+   FP32); A BF16 / BF16 (tcgen05 tensor cores fed by TMA, FP32 accumulation, G in
+   FP32; A->ld and ld_omega multiples of 8, 16-byte aligned bases, else
+   ID_ERR_UNSUPPORTED).  ws: at least id_sketch_workspace_size bytes, 256-aligned. */
+int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes);
+int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec,
+              void* G, int64_t ldg, void* ws, size_t ws_bytes, void* stream);
+
 /* Human-readable text for a status value. */
 const char* id_status_string(int status);
 

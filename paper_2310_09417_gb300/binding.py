@@ -72,10 +72,12 @@ def load():
     lib.id_batched.argtypes = [i64, P, P, P, C.c_size_t, P, P]
     lib.cur_from_id.argtypes = [P, P, i64, P, P, i64, P, C.c_size_t, P]
     lib.id_gaussian_rows.argtypes = [u64, i64, i64, i64, C.c_int, P, i64, P]
+    lib.id_sketch_workspace_size.argtypes = [P, i64, C.c_int, C.POINTER(C.c_size_t)]
+    lib.id_sketch.argtypes = [P, P, i64, i64, C.c_int, P, i64, P, C.c_size_t, P]
     lib.id_status_string.argtypes = [C.c_int]
     lib.id_status_string.restype = C.c_char_p
     for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
-              "id_batched", "cur_from_id", "id_gaussian_rows"):
+              "id_batched", "cur_from_id", "id_gaussian_rows", "id_sketch_workspace_size", "id_sketch"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -250,3 +252,27 @@ def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
     if rc != 0:
         raise IDError(rc, "id_gaussian_rows")
     return out
+
+
+def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, stream=None,
+              workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """G = (omega A)^T (n x rows): the sketch step alone.  omega is row-major
+    (rows x m) in the sketch precision (A's dtype); G is FP64 for FP64 input and
+    FP32 otherwise (BF16 input runs on the tensor cores)."""
+    m, n = A.shape
+    if omega.dim() != 2 or omega.shape[1] != m or omega.stride(1) != 1 or omega.dtype != A.dtype:
+        raise ValueError("omega must be row-major (rows x m) with A's dtype")
+    rows = omega.shape[0]
+    prec = _TORCH_TO_ID[A.dtype]
+    nb = C.c_size_t(0)
+    lib = load()
+    rc = lib.id_sketch_workspace_size(C.byref(_matrix(A)), rows, prec, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_sketch_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    G = torch.empty((n, rows), dtype=torch.float64 if prec == F64 else torch.float32, device=A.device)
+    rc = lib.id_sketch(C.byref(_matrix(A)), omega.data_ptr(), omega.stride(0), rows, prec, G.data_ptr(),
+                       G.stride(0), ws.data_ptr(), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_sketch")
+    return G

@@ -15,6 +15,8 @@
 
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "randid.h"
 #include "rid_internal.h"
 
@@ -58,6 +60,9 @@ struct Plan {
   int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
   bool gen_omega = true;
   size_t esz = 0;
+  int path = 0;          // 64, 32 (SIMT) or 16 (BF16 tensor-core sketch)
+  int64_t ldw = 0;       // row stride of the generated Omega
+  size_t wsz = 0;        // bytes per Omega element
   size_t off_state = 0, off_omega = 0, off_G = 0, off_Gpart = 0, off_S = 0, off_Spart = 0, off_N = 0,
          off_Linv = 0, off_act0 = 0, off_act1 = 0, off_pivmark = 0, off_perm32 = 0, off_piv = 0,
          off_pivorig = 0, off_pivdiag = 0, off_cand_v = 0, off_cand_i = 0, off_cand_rows = 0, off_e2 = 0,
@@ -68,6 +73,8 @@ struct Plan {
 int precision_path(const id_matrix* A, const id_opts* o) {
   if (A->dtype == ID_F64 && o->sketch_prec == ID_F64 && o->lu_prec == ID_F64) return 64;
   if (A->dtype == ID_F32 && o->sketch_prec == ID_F32 && o->lu_prec == ID_F32) return 32;
+  // BF16 input: sketch on the tensor cores (FP32 accumulation), LU and X in FP32
+  if (A->dtype == ID_BF16 && o->sketch_prec == ID_BF16 && o->lu_prec == ID_F32) return 16;
   return 0;
 }
 
@@ -79,7 +86,14 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   if (A == nullptr || A->data == nullptr) return kBadA;
   if (o == nullptr) return kBadOpts;
   if (A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= (int64_t)1 << 31 || A->n >= (int64_t)1 << 30) return kBadA;
-  if (precision_path(A, o) == 0) return ID_ERR_UNSUPPORTED;
+  const int path = precision_path(A, o);
+  if (path == 0) return ID_ERR_UNSUPPORTED;
+  // the tensor-core path reads A and Omega with TMA: 16-byte aligned rows
+  if (path == 16 && ((A->ld % 8) != 0 || (reinterpret_cast<uintptr_t>(A->data) % 16) != 0))
+    return ID_ERR_UNSUPPORTED;
+  if (path == 16 && o->omega != nullptr &&
+      ((o->ld_omega % 8) != 0 || (reinterpret_cast<uintptr_t>(o->omega) % 16) != 0))
+    return ID_ERR_UNSUPPORTED;
   const int64_t b = o->block == 0 ? 64 : o->block;
   if (b < 1 || b > kMaxBlock) return kBadOpts;
   if (!(o->tol >= 0.0) || o->k_max < 0 || o->k0 < 0 || o->blocks_per_pass < 0) return kBadOpts;
@@ -88,6 +102,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->b = b;
   p->sms = num_sms();
   p->esz = o->lu_prec == ID_F64 ? 8 : 4;
+  p->path = path;
+  p->ldw = path == 16 ? cdiv(A->m, 8) * 8 : A->m;
+  p->wsz = path == 16 ? 2 : p->esz;
   p->gen_omega = (o->omega == nullptr);
   if (l > 0) {  // fixed rank; sizes do not depend on k (estimate block sized for k = 1)
     if (l > ((int64_t)1 << 20)) return kBadL;
@@ -117,8 +134,15 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   }
   const int64_t rows_max = imax(p->rows_first, p->rows_pass);
   p->ldg = rows_max;
-  p->s1_first = choose_splits(p->n, p->rows_first, p->m, p->sms, 16);
-  p->s1_pass = p->rows_pass > 0 ? choose_splits(p->n, p->rows_pass, p->m, p->sms, 16) : 1;
+  if (path == 16) {
+    p->s1_first = tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, p->rows_first, p->sms));
+    p->s1_pass = p->rows_pass > 0
+                     ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, p->rows_pass, p->sms))
+                     : 1;
+  } else {
+    p->s1_first = choose_splits(p->n, p->rows_first, p->m, p->sms, 16);
+    p->s1_pass = p->rows_pass > 0 ? choose_splits(p->n, p->rows_pass, p->m, p->sms, 16) : 1;
+  }
   const int s1 = p->s1_first > p->s1_pass ? p->s1_first : p->s1_pass;
   p->s2max = 8;
   p->nparts = 2 * p->sms;
@@ -131,7 +155,7 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     return at;
   };
   p->off_state = take(256);
-  p->off_omega = take(p->gen_omega ? (size_t)rows_max * p->m * e : 0);
+  p->off_omega = take(p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0);
   p->off_G = take((size_t)p->n * rows_max * e);
   p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * e : 0);
   p->off_S = take((size_t)p->n * p->wmax * e);
@@ -168,6 +192,7 @@ class Engine {
   Engine(const Plan& p, const id_matrix* A, const id_opts* o, void* ws, id_result* out, cudaStream_t s)
       : p_(p), o_(*o), out_(out), s_(s) {
     A_ = static_cast<const T*>(A->data);
+    Araw_ = A->data;
     lda_ = A->ld;
     unsigned char* w = static_cast<unsigned char*>(ws);
     st_ = reinterpret_cast<DevState*>(w + p.off_state);
@@ -296,7 +321,11 @@ class Engine {
   int start() {
     RID_TRY(tbegin(ID_PHASE_OTHER));
     RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
-    RID_TRY(cuda(norm2_partial<T>(p_.m, p_.n, A_, lda_, normp_, p_.nparts, st_, s_)));
+    if (p_.path == 16)
+      RID_TRY(cuda(norm2_partial<__nv_bfloat16>(p_.m, p_.n, static_cast<const __nv_bfloat16*>(Araw_), lda_, normp_,
+                                                p_.nparts, st_, s_)));
+    else
+      RID_TRY(cuda(norm2_partial<T>(p_.m, p_.n, A_, lda_, normp_, p_.nparts, st_, s_)));
     RID_TRY(cuda(norm2_final(normp_, p_.nparts, st_, s_)));
     RID_TRY(tend(3));
     RID_TRY(sync_state());
@@ -313,6 +342,7 @@ class Engine {
 
   // G(:, 0:rows) = (Omega rows [row0, row0+rows)) A, stored n x rows (row-major, ld ldg).
   int sketch(int64_t row0, int64_t rows, int splits) {
+    if (p_.path == 16) return sketch_tc(row0, rows, splits);
     const T* Om;
     int64_t ldo;
     if (p_.gen_omega) {
@@ -334,6 +364,34 @@ class Engine {
     RID_TRY(cuda(gemm_gather<T>((int)p_.n, (int)rows, (int)p_.m, splits, true, a, bop, kEpiStore, ep, done_, s_)));
     if (splits > 1)
       RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg, Gpart_, G_, done_, s_)));
+    RID_TRY(tend(splits > 1 ? 2 : 1));
+    ++passes_;
+    return 0;
+  }
+
+  // BF16 operands on the tensor cores: G = (Omega rows [row0, row0+rows)) A in FP32.
+  int sketch_tc(int64_t row0, int64_t rows, int splits) {
+    const void* W;
+    int64_t ldw;
+    if (p_.gen_omega) {
+      RID_TRY(tbegin(ID_PHASE_OMEGA));
+      RID_TRY(cuda(gaussian_rows<__nv_bfloat16>(o_.seed, row0, rows, p_.m, reinterpret_cast<__nv_bfloat16*>(omega_),
+                                                p_.ldw, done_, s_)));
+      RID_TRY(tend(1));
+      W = omega_;
+      ldw = p_.ldw;
+    } else {
+      W = static_cast<const __nv_bfloat16*>(o_.omega) + row0 * o_.ld_omega;
+      ldw = o_.ld_omega;
+    }
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    float* out = reinterpret_cast<float*>(splits > 1 ? Gpart_ : G_);
+    RID_TRY(cuda(tc_sketch_bf16(Araw_, lda_, p_.m, p_.n, W, ldw, rows, out, p_.ldg, (int64_t)p_.n * p_.ldg, splits,
+                                st_, done_, s_)));
+    if (splits > 1)
+      RID_TRY(cuda(splitk_reduce<float>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
+                                        reinterpret_cast<const float*>(Gpart_), reinterpret_cast<float*>(G_), done_,
+                                        s_)));
     RID_TRY(tend(splits > 1 ? 2 : 1));
     ++passes_;
     return 0;
@@ -427,6 +485,7 @@ class Engine {
   id_result* out_;
   cudaStream_t s_;
   const T* A_;
+  const void* Araw_;
   int64_t lda_;
   DevState* st_;
   DevState h_{};
@@ -567,6 +626,84 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
   if (e != cudaSuccess) return ID_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
   return ID_OK;
+}
+
+namespace {
+// Split count and workspace of a stand-alone sketch: DevState + split-K partials.
+int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int* splits, size_t* bytes) {
+  if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= ((int64_t)1 << 31) ||
+      A->n >= ((int64_t)1 << 30))
+    return -1;
+  if (rows < 1 || rows > ((int64_t)1 << 20)) return -2;
+  *path = (A->dtype == ID_F64 && prec == ID_F64) ? 64
+          : (A->dtype == ID_F32 && prec == ID_F32) ? 32
+          : (A->dtype == ID_BF16 && prec == ID_BF16) ? 16
+                                                     : 0;
+  if (*path == 0) return ID_ERR_UNSUPPORTED;
+  const int sms = num_sms();
+  const size_t esz = *path == 64 ? 8 : 4;
+  *splits = *path == 16 ? tc_sketch_effective_splits(A->m, tc_sketch_splits(A->m, A->n, rows, sms))
+                        : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
+  *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  return ID_OK;
+}
+}  // namespace
+
+int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes) {
+  if (bytes == nullptr) return -4;
+  int path = 0, splits = 1;
+  const int rc = sketch_plan(A, rows, sketch_prec, &path, &splits, bytes);
+  return rc == -2 ? -2 : rc;
+}
+
+int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec, void* G,
+              int64_t ldg, void* ws, size_t ws_bytes, void* stream) {
+  int path = 0, splits = 1;
+  size_t need = 0;
+  int rc = sketch_plan(A, rows, sketch_prec, &path, &splits, &need);
+  if (rc != ID_OK) return rc == -2 ? -4 : rc;
+  if (omega == nullptr || ld_omega < A->m) return -2;
+  if (G == nullptr || ldg < rows) return -6;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < need)
+    return ID_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = static_cast<DevState*>(ws);
+  void* part = static_cast<unsigned char*>(ws) + 256;
+  if (init_state(st, nullptr, nullptr, 0, s) != cudaSuccess) return ID_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  const int64_t zs = A->n * ldg;
+  if (path == 16) {
+    if (!tc_sketch_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
+    float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
+    e = tc_sketch_bf16(A->data, A->ld, A->m, A->n, omega, ld_omega, rows, out, ldg, zs, splits, st, nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce<float>(A->n, (int)rows, ldg, splits, zs, static_cast<float*>(part), static_cast<float*>(G),
+                               nullptr, s);
+  } else if (path == 64) {
+    Operand<double> a{static_cast<const double*>(A->data), A->ld, nullptr, 0};
+    Operand<double> w{static_cast<const double*>(omega), ld_omega, nullptr, 0};
+    double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
+    EpiArgs<double> ep{out, ldg, zs, nullptr, nullptr};
+    e = gemm_gather<double>((int)A->n, (int)rows, (int)A->m, splits, true, a, w, kEpiStore, ep, nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce<double>(A->n, (int)rows, ldg, splits, zs, static_cast<double*>(part),
+                                static_cast<double*>(G), nullptr, s);
+  } else {
+    Operand<float> a{static_cast<const float*>(A->data), A->ld, nullptr, 0};
+    Operand<float> w{static_cast<const float*>(omega), ld_omega, nullptr, 0};
+    float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
+    EpiArgs<float> ep{out, ldg, zs, nullptr, nullptr};
+    e = gemm_gather<float>((int)A->n, (int)rows, (int)A->m, splits, true, a, w, kEpiStore, ep, nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce<float>(A->n, (int)rows, ldg, splits, zs, static_cast<float*>(part), static_cast<float*>(G),
+                               nullptr, s);
+  }
+  if (e != cudaSuccess) return ID_ERR_CUDA;
+  DevState h;
+  if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ID_ERR_CUDA;
+  return (h.err & kErrTimeout) ? ID_ERR_TIMEOUT : ID_OK;
 }
 
 const char* id_status_string(int status) {

@@ -104,4 +104,14 @@ cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cuda
 
 cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, cudaStream_t s);
 
+// ---- tensor-core sketch (rid_tc_sketch.cu): out[z] (n x rows, FP32, row stride out_ld)
+// holds split z of (W A)^T for BF16 A (m x n, column-major) and W (rows x m, row-major).
+// TMA needs 16-byte aligned bases and leading dimensions that are multiples of 8.
+bool tc_sketch_supported(const void* A, int64_t lda, const void* W, int64_t ldw);
+int tc_sketch_splits(int64_t m, int64_t n, int64_t rows, int sms);
+int tc_sketch_effective_splits(int64_t m, int splits);
+cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, const void* W, int64_t ldw,
+                           int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits, DevState* st,
+                           const int32_t* done, cudaStream_t s);
+
 }  // namespace rid

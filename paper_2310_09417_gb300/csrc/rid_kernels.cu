@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "rid_internal.h"
 
 namespace rid {
@@ -24,6 +26,21 @@ static cudaError_t ensure_smem(K* func, size_t bytes, size_t* cached) {
   if (e == cudaSuccess) *cached = bytes;
   return e;
 }
+
+// Element conversions (round to nearest) shared by the FP64/FP32/BF16 instantiations.
+template <typename T>
+__device__ __forceinline__ T from_double(double x) {
+  return static_cast<T>(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
+  return __double2bfloat16(x);
+}
+template <typename T>
+__device__ __forceinline__ double to_double(T x) {
+  return static_cast<double>(x);
+}
+__device__ __forceinline__ double to_double(__nv_bfloat16 x) { return static_cast<double>(__bfloat162float(x)); }
 
 // ============================================================ Gaussian rows
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64
@@ -77,7 +94,7 @@ __global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64
     const int64_t lim = m - 4 * q;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (j < lim) o[j] = (T)z[j];
+      if (j < lim) o[j] = from_double<T>(z[j]);
   }
 }
 
@@ -101,7 +118,7 @@ __global__ void k_norm2_partial(int64_t m, int64_t n, const T* __restrict__ A, i
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
     const T* a = A + j * lda;
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const double v = (double)a[i];
+      const double v = to_double(a[i]);
       finite = finite && isfinite(v);
       acc += v * v;
     }
@@ -711,5 +728,9 @@ cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, 
 
 RID_INST(double)
 RID_INST(float)
+template cudaError_t gaussian_rows<__nv_bfloat16>(uint64_t, int64_t, int64_t, int64_t, __nv_bfloat16*, int64_t,
+                                                  const int32_t*, cudaStream_t);
+template cudaError_t norm2_partial<__nv_bfloat16>(int64_t, int64_t, const __nv_bfloat16*, int64_t, double*, int,
+                                                  DevState*, cudaStream_t);
 
 }  // namespace rid

@@ -1,0 +1,319 @@
+// rid_tc_sketch.cu -- the sketch Y = Omega A on the 5th-generation tensor cores.
+//
+// G (n x rows) = (Omega A)^T with A (m x n, column-major, BF16) and Omega (rows x m,
+// row-major, BF16), FP32 accumulation in tensor memory (Sec. 2.4; Alg. 1 line 9).
+// Both operands are K-major (K = m): a column of A and a row of Omega are contiguous.
+//
+// One CTA computes a 128 (columns of A) x BN (rows of Omega) tile over a K range:
+//   warp 0   one lane issues TMA loads (128B-swizzled boxes of 64 K x 128 / 64 x BN)
+//   warp 1   allocates tensor memory; one lane issues tcgen05.mma (M=128, N=BN, K=16)
+//   warps 2-5 drain the accumulator with tcgen05.ld and write FP32 rows of G
+// A STAGES-deep ring of shared-memory stages is guarded by "full" (TMA bytes landed)
+// and "empty" (the MMAs that read the stage completed) mbarriers.  Every wait is
+// bounded by %globaltimer; on a timeout the CTA records kErrTimeout, waits (bounded)
+// for the copies and MMAs it started, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rid_internal.h"
+
+namespace rid {
+
+namespace tc {
+
+constexpr int kBM = 128;        // columns of A per tile (MMA M)
+constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr int kThreads = 192;   // 6 warps
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout (kErrTimeout set).
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      if (ld_acquire_u32(&st->err) & kErrTimeout) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        atomicOr(&st->err, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row x 128-byte atoms
+// stacked 1024 bytes apart (stride byte offset), descriptor version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  const uint64_t a = smem_u32(p);
+  uint64_t d = (a >> 4) & 0x3FFFull;  // start address
+  d |= 1ull << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (1024ull >> 4) << 32;          // stride byte offset
+  d |= 1ull << 46;                    // version
+  d |= 2ull << 61;                    // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct Smem {
+  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];  // 16 KB per stage
+  alignas(1024) __nv_bfloat16 w[kStages][BN * kBK];   // BN * 128 bytes per stage
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t accum;
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sketch_tc_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w, int n,
+                     int rows, int K, int kchunk, float* __restrict__ out, int64_t out_ld, int64_t zstride,
+                     DevState* st, const int32_t* done) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  // dynamic shared memory is only guaranteed 16-byte aligned: align the carve-out to 1024
+  Smem<BN>& sm = *reinterpret_cast<Smem<BN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;  // first column of A
+  const int n0 = blockIdx.y * BN;   // first row of Omega
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nkb = (kend - kbeg + kBK - 1) / kBK;
+  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(&sm.accum, 1);
+    mbar_init(&sm.drain, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) + 1) & 1, st)) break;
+      mbar_expect_tx(&sm.full[s], (kBM + BN) * kBK * 2);
+      const int k0 = kbeg + kb * kBK;
+      tma_load_2d(sm.a[s], &map_a, &sm.full[s], k0, m0);
+      tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);
+      issued = kb + 1;
+    }
+    // copies still in flight must land before the CTA can leave
+    for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
+      if (!mbar_wait(&sm.full[kb % kStages], (kb / kStages) & 1, st)) break;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    int consumed = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&sm.full[s], (kb / kStages) & 1, st)) break;
+      fence_after_sync();
+      const uint64_t da = desc_sw128(sm.a[s]);
+      const uint64_t dw = desc_sw128(sm.w[s]);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)  // advance 16 BF16 = 32 bytes inside the swizzle row
+        mma_bf16(tmem, da + 2 * kk, dw + 2 * kk, idesc, (kb | kk) != 0);
+      mma_commit(&sm.empty[s]);
+      consumed = kb + 1;
+    }
+    if (consumed == nkb) {
+      mma_commit(&sm.accum);
+    } else {
+      sm.abort = 1;
+      mma_commit(&sm.drain);  // wait for the MMAs already issued before tensor memory is freed
+      mbar_wait(&sm.drain, 0, st);
+      mma_commit(&sm.accum);  // release the epilogue
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: tensor memory -> G
+    const bool ok = mbar_wait(&sm.accum, 0, st);
+    fence_after_sync();
+    if (ok && !sm.abort) {
+      const int quarter = warp & 3;  // warps 2..5 own lane quarters 2,3,0,1
+      const int row = m0 + quarter * 32 + lane;
+      float* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, v);
+        if (row < n) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (n0 + c0 + i < rows) o[n0 + c0 + i] = v[i];
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over a K-major matrix: `outer` rows of `inner` contiguous
+// elements, row stride `ld` elements; box = 64 (K) x box_rows, 128-byte swizzle.
+bool make_map_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+size_t smem_bytes() {
+  return sizeof(Smem<BN>) + 1024;  // + alignment slack
+}
+
+}  // namespace tc
+
+bool tc_sketch_supported(const void* A, int64_t lda, const void* W, int64_t ldw) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(A), w = reinterpret_cast<uintptr_t>(W);
+  return (a % 16) == 0 && (w % 16) == 0 && (lda % 8) == 0 && (ldw % 8) == 0 && tc::encode_fn() != nullptr;
+}
+
+int tc_sketch_splits(int64_t m, int64_t n, int64_t rows, int sms) {
+  const int64_t tiles = ((n + tc::kBM - 1) / tc::kBM) * ((rows + 63) / 64);
+  int64_t s = (8 * (int64_t)sms + tiles - 1) / tiles;  // about eight waves of one CTA per SM
+  const int64_t kmax = (m + 8 * tc::kBK - 1) / (8 * tc::kBK);  // >= 8 K-stages per CTA
+  if (s > kmax) s = kmax;
+  if (s > 32) s = 32;
+  return (int)(s < 1 ? 1 : s);
+}
+
+cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, const void* W, int64_t ldw,
+                           int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits, DevState* st,
+                           const int32_t* done, cudaStream_t s) {
+  constexpr int BN = 64;
+  CUtensorMap ma, mw;
+  if (!tc::make_map_bf16(&ma, A, m, n, lda, tc::kBM)) return cudaErrorInvalidValue;
+  if (!tc::make_map_bf16(&mw, W, m, rows, ldw, BN)) return cudaErrorInvalidValue;
+  int kchunk = (int)((m + splits - 1) / splits);
+  kchunk = ((kchunk + tc::kBK - 1) / tc::kBK) * tc::kBK;
+  const int nz = (int)((m + kchunk - 1) / kchunk);
+  static bool attr = false;
+  const size_t smem = tc::smem_bytes<BN>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc::k_sketch_tc_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((n + tc::kBM - 1) / tc::kBM), (unsigned)((rows + BN - 1) / BN), (unsigned)nz);
+  tc::k_sketch_tc_bf16<BN><<<grid, tc::kThreads, smem, s>>>(ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld,
+                                                             zstride, st, done);
+  return cudaGetLastError();
+}
+
+int tc_sketch_effective_splits(int64_t m, int splits) {
+  int kchunk = (int)((m + splits - 1) / splits);
+  kchunk = ((kchunk + tc::kBK - 1) / tc::kBK) * tc::kBK;
+  return (int)((m + kchunk - 1) / kchunk);
+}
+
+}  // namespace rid

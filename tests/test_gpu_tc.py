@@ -1,0 +1,103 @@
+"""Tensor-core (tcgen05 + TMA) sketch and the BF16-input ID.
+
+The BF16 path sketches with BF16 x BF16 products accumulated in FP32 in tensor
+memory; the references are FP64 products of the same BF16 values (exact
+inputs), so the only differences are FP32 accumulation and the FP32 LU."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2310_09417_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_09417_gb300 import build
+    build.build()
+    from paper_2310_09417_gb300 import binding
+    binding.load()
+    return binding
+
+
+def bf16_pair(rng, m, n, rows):
+    """Column-major BF16 A (m x n) and row-major BF16 Omega (rows x m)."""
+    A = torch.from_numpy(rng.standard_normal((m, n))).to("cuda", torch.bfloat16)
+    Om = torch.from_numpy(rng.standard_normal((rows, m))).to("cuda", torch.bfloat16).contiguous()
+    return A, Om
+
+
+@pytest.mark.parametrize("m,n,rows", [
+    (1024, 256, 64),     # whole tiles
+    (1000, 333, 100),    # ragged K (not a multiple of 64), ragged n and rows (two N tiles)
+    (64, 128, 64),       # one K stage
+    (40000, 300, 64),    # long K: many split-K partials
+    (8, 5, 3),           # smaller than every tile
+])
+def test_tc_sketch_matches_fp64_product(B, m, n, rows):
+    rng = np.random.default_rng(m + n + rows)
+    A, Om = bf16_pair(rng, m, n, rows)
+    Acm = B.colmajor(A)
+    G = B.id_sketch(Acm, Om)
+    ref = (Om.double() @ Acm.double()).t()
+    # FP32 accumulation of exact BF16 products: error ~ u32 sqrt(m) |Omega||A|
+    scale = (Om.double().abs() @ Acm.double().abs()).t()
+    err = ((G.double() - ref).abs() / scale).max().item()
+    assert err < 4e-6 * max(1.0, np.sqrt(m / 1024)), err
+
+
+def test_simt_sketch_matches_fp64_product(B):
+    rng = np.random.default_rng(3)
+    A = B.colmajor(torch.from_numpy(rng.standard_normal((777, 129))).cuda())
+    Om = torch.from_numpy(rng.standard_normal((70, 777))).cuda()
+    G = B.id_sketch(A, Om)
+    torch.testing.assert_close(G, (Om @ A).t(), rtol=1e-12, atol=1e-12)
+
+
+def test_tc_rejects_misaligned_leading_dimension(B):
+    A = torch.zeros((100, 7), dtype=torch.bfloat16, device="cuda")  # ld = 100 is not a multiple of 8
+    Om = torch.zeros((64, 100), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(B.IDError) as e:
+        B.id_sketch(B.colmajor(A), Om)
+    assert e.value.code == B.ERR_UNSUPPORTED
+
+
+def test_adaptive_bf16_against_fp64_oracle(B, orc):
+    """Low-rank-plus-noise input stored in BF16 (the mixed-precision workload at
+    reduced size): the BF16-sketch / FP32-LU run meets the tolerance, its rank is
+    within one block of the FP64 oracle's on the same BF16 values, and its
+    achieved error is within 1.2x of the oracle's.  The tolerance sits above
+    the BF16 rounding floor of A (about 2e-3 relative)."""
+    m, n, r, b, tol = 4096, 1024, 150, 32, 1e-2
+    rng = np.random.default_rng(31)
+    A = (rng.standard_normal((m, r)) @ rng.standard_normal((r, n))) / np.sqrt(r)
+    A += 1e-4 * rng.standard_normal((m, n))
+    Ab = torch.from_numpy(A).to("cuda", torch.bfloat16)
+    A64 = Ab.double().cpu().numpy()
+    Om = torch.from_numpy(W.gaussian_omega(32, orc.rows_needed(n, b), m)).to("cuda", torch.bfloat16).contiguous()
+    g = B.id_adaptive(B.colmajor(Ab), tol, block=b, omega=Om)
+    r_ = orc.id_adaptive(A64, Om.double().cpu().numpy(), b, tol * orc.fro_norm(A64))
+    assert g.status == 0
+    assert abs(g.k - r_["k"]) <= b
+    nA = orc.fro_norm(A64)
+    eg = orc.id_residual(A64, g.J.cpu().numpy(), g.X.double().cpu().numpy()) / nA
+    eo = orc.id_residual(A64, r_["J"], r_["X"]) / nA
+    assert eg <= 1.2 * eo + 1e-6
+    assert eg <= 2 * tol
+    kk = min(g.k, r_["k"])
+    assert len(set(g.J.cpu().numpy()[:kk]) & set(r_["J"][:kk])) / kk >= 0.9
+
+
+def test_bf16_generated_omega_runs_and_meets_tolerance(B, orc):
+    m, n, r = 3000, 800, 80
+    rng = np.random.default_rng(33)
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 1e-4 * rng.standard_normal((m, n))
+    Ab = torch.from_numpy(A).to("cuda", torch.bfloat16)
+    g = B.id_adaptive(B.colmajor(Ab), 1e-2, block=64, seed=5)
+    A64 = Ab.double().cpu().numpy()
+    e = orc.id_residual(A64, g.J.cpu().numpy(), g.X.double().cpu().numpy()) / orc.fro_norm(A64)
+    assert g.k >= r and e <= 2e-2

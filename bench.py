@@ -44,7 +44,13 @@ WORKLOADS = {
     # sketch on the tensor cores (BF16 x BF16 -> FP32), LU in FP32, norms in FP64
     "mixed_bf16": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 1e-3, 64),
     "mixed_bf16_tol3e-3": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-3, 64),
+    "mixed_bf16_tol3e-2": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-2, 64),
     "small_mixed_bf16": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "bf16", 1e-3, 64),
+    # batched: 4096 off-diagonal blocks exp(-|x-y|^2/h^2), h = 0.3, of a k-d tree over 2^20 uniform
+    # points in the unit cube (leaves of at most 1024 points, sizes 64..1024), one persistent launch
+    "batched_kernel_f64": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f64", 1e-8, 32),
+    "batched_kernel_f32": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f32", 1e-8, 32),
+    "small_batched_kernel_f64": (2 ** 16, 512, "kernel", {"leaf_max": 512, "h": 0.3}, "f64", 1e-8, 32),
 }
 DEFAULT_WORKLOAD = "adaptive_poly_f64"
 # Peaks of the plain-ALU paths, from unit counts x maximum SM clock (2070 MHz):
@@ -209,6 +215,9 @@ def run_reference(args, rank, world):
     name = args.workload
     m, n, kind, kw, dt, tol, b = WORKLOADS[name]
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if kind == "kernel":
+        run_reference_batched(args, name, dev)
+        return
     if dev is not None:
         A = make_input(name, dev)
         A_host = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
@@ -234,8 +243,55 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_batched(args, name, dev):
+    """Reference arm for the batched workload: the oracle, one block after another,
+    on the largest blocks of the batch (about 8 s per step)."""
+    import numpy as np
+
+    import oracle
+    from paper_2310_09417_gb300 import workloads as W
+    npts, count, kind, kw, dt, tol, b = WORKLOADS[name]
+    pts, leaves, pairs = W.kernel_block_pairs(npts, count, 2310_09417 + 3, leaf_max=kw["leaf_max"], size_min=64)
+    pairs = sorted(pairs, key=lambda p: -len(leaves[p[0]]) * len(leaves[p[1]]))
+    times, vals, used = [], [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        fl, used = 0.0, 0
+        for a, c in pairs:
+            A = W.gaussian_kernel_block(pts, leaves[a], leaves[c], h=kw["h"])
+            mm, nn = A.shape
+            Om = oracle.gaussian_rows(2310_09417, 0, oracle.rows_needed(nn, b, m=mm), mm)
+            r = oracle.id_adaptive(A, Om, b, tol * oracle.fro_norm(A))
+            fl += algorithmic_flops(mm, nn, r["k"], b)
+            used += 1
+            if time.perf_counter() - t0 > 8.0:
+                break
+        sec = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(sec)
+            vals.append(fl / sec / 1e9)
+    value = statistics.mean(vals)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = "oracle (plain C, FP64, OpenMP) on the %d largest of the %d blocks per step" % (used, count)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(name, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def config_dict(name, res):
     m, n, kind, kw, dt, tol, b = WORKLOADS[name]
+    if kind == "kernel":
+        return {"workload": name, "points": m, "blocks": n, "kernel": "exp(-|x-y|^2/h^2), h = %s" % kw["h"],
+                "tree": "k-d tree, widest side split at U[0.3,0.7], leaves <= %d points" % kw["leaf_max"],
+                "block_sizes": "m, n in [64, %d]" % kw["leaf_max"], "block": b, "rel_tol": tol,
+                "precision": "%s sketch, LU and X; FP64 norms" % dt.upper(),
+                "omega": "Philox4x64-10 Gaussian, generated inside the kernel",
+                "l2": "inputs larger than L2 (the batch is %s)" % (res if res else "several GB"),
+                "parallelism": "one persistent launch, CTA per problem; replicas across GPUs"}
     spec = {"poly": "s_j = (1+j)^-2", "step": "rank 600 at 1, then 1e-9",
             "lowrank": "G1 G2 (Gaussian factors, rank %s) + %s N(0,1) noise, stored in BF16"
                        % (kw.get("rank"), kw.get("noise"))}[kind]
@@ -251,6 +307,141 @@ def config_dict(name, res):
     if res is not None:
         c.update({"k": res.k, "rounds": res.rounds, "passes": res.passes})
     return c
+
+
+def make_batch(name, device, seed=2310_09417 + 3):
+    """The 4096 kernel blocks of the batched workload (column-major CUDA tensors)."""
+    import torch
+
+    from paper_2310_09417_gb300 import workloads as W
+    npts, count, kind, kw, dt, _, _ = WORKLOADS[name]
+    pts, leaves, pairs = W.kernel_block_pairs(npts, count, seed, leaf_max=kw["leaf_max"], size_min=64)
+    P = torch.from_numpy(pts).to(device)
+    idx = [torch.from_numpy(l).to(device) for l in leaves]
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    h2 = kw["h"] ** 2
+    As = []
+    for a, b in pairs:
+        d2 = torch.cdist(P[idx[b]], P[idx[a]]) ** 2  # n x m row-major == m x n column-major
+        As.append(torch.exp(-d2 / h2).to(dtype).t())
+    torch.cuda.synchronize()
+    return As
+
+
+def run_batched(args, rank, world, dev, barrier, max_over_ranks):
+    import torch
+
+    from paper_2310_09417_gb300 import binding as B
+    name = args.workload
+    npts, count, kind, kw, dt, tol, b = WORKLOADS[name]
+    As = make_batch(name, dev)
+    seed = 2310_09417 + 100 * rank
+    xdt = torch.float64 if dt == "f64" else torch.float32
+    outs = [(torch.empty(min(A.shape), dtype=torch.int64, device=dev),
+             torch.empty((A.shape[1], min(A.shape)), dtype=xdt, device=dev)) for A in As]
+    nbytes = sum(A.numel() * A.element_size() for A in As)
+    ws = None
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return B.id_batched(As, tol, block=b, seed=seed, outs=outs, workspace=ws, stream=stream)
+    res = step()
+    import ctypes
+    mats = (B.IdMatrix * len(As))(*[B._matrix(a) for a in As])
+    o = B._opts(As[0], block=b, tol=tol, relative=True, k_max=0, k0=0, blocks_per_pass=1, seed=seed, omega=None,
+                profile=False)
+    nb = ctypes.c_size_t(0)
+    B.load().id_batched_workspace_size(len(As), mats, ctypes.byref(o), ctypes.byref(nb))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_gpu(dev)) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    flops = sum(algorithmic_flops(A.shape[0], A.shape[1], r.k, b) for A, r in zip(As, res))
+    value = flops * world / (ms * 1e-3) / 1e9
+    ks = [r.k for r in res]
+    peak = ALU_PEAK_TFLOPS[dt]
+    achieved = flops / (ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_batched (one persistent launch per step, %s FMA)" % dt,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "timing": "CUDA events around the whole step (descriptor upload, graph "
+                                          "replay of the persistent kernel, result copy)",
+                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
+                                                 else "GB300 FP64 rate 1.25 TFLOP/s")}
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty((A.shape[1], A.shape[0]), dtype=A.dtype, pin_memory=True) for A in As]
+        for h, A in zip(hosts, As):
+            h.copy_(A.t())
+        devs = [torch.empty_like(h, device=dev) for h in hosts]
+        xh = [torch.empty_like(X, device="cpu", pin_memory=True) for _, X in outs]
+
+        def e2e_step():
+            for h, d in zip(hosts, devs):
+                d.copy_(h, non_blocking=True)
+            r = B.id_batched([d.t() for d in devs], tol, block=b, seed=seed, outs=outs, workspace=ws,
+                             stream=stream)
+            for x, (_, X) in zip(xh, outs):
+                x.copy_(X, non_blocking=True)
+            return r
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in xh)}
+        del hosts, devs, xh
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+
+        import oracle
+        t0 = time.perf_counter()
+        fl = 0.0
+        used = 0
+        for A in As:  # the largest blocks first, until ~8 s of oracle work
+            Ah = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
+            mm, nn = Ah.shape
+            Om = oracle.gaussian_rows(seed, 0, oracle.rows_needed(nn, b, m=mm), mm)
+            r = oracle.id_adaptive(Ah, Om, b, tol * oracle.fro_norm(Ah))
+            fl += algorithmic_flops(mm, nn, r["k"], b)
+            used += 1
+            if time.perf_counter() - t0 > 8.0:
+                break
+        dtc = time.perf_counter() - t0
+        cpu = {"value": fl / dtc / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+               "kind": "oracle", "sample": "oracle (plain C, FP64, OpenMP) on the first %d of the %d blocks, %.1f s"
+                                           % (used, len(As), dtc)}
+    if rank == 0:
+        cfg = config_dict(name, None)
+        cfg.update({"k_mean": sum(ks) / len(ks), "k_max": max(ks), "k_min": min(ks),
+                    "batch_gb": round(nbytes / 1e9, 2)})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dt, "data": "synthetic", "config": cfg, "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+                "result": {"ids_per_s": len(As) * world / (ms * 1e-3), "gflop_per_step": flops / 1e9,
+                           "statuses": sorted(set(r.status for r in res))}}
+        print(json.dumps(line), flush=True)
+
+
+def local_gpu(dev):
+    return dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else dev.index
 
 
 def main():
@@ -299,6 +490,11 @@ def main():
     B.load()
 
     name = args.workload
+    if WORKLOADS[name][2] == "kernel":
+        run_batched(args, rank, world, dev, barrier, max_over_ranks)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     m, n, kind, kw, dt, tol, b = WORKLOADS[name]
     A = make_input(name, dev)
     seed = 2310_09417 + 100 * rank

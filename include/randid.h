@@ -122,6 +122,8 @@ typedef struct {
   int64_t launches; /* HOST out: kernels launched by this call */
   double phase_ms[ID_NUM_PHASES];      /* HOST out when opts->profile */
   int64_t phase_launches[ID_NUM_PHASES];
+  int32_t status;   /* HOST out: this problem's status (id_batched: per problem; otherwise
+                       equal to the return value) */
 } id_result;
 
 /* ---------------------------------------------------------------- entry points */
@@ -147,9 +149,21 @@ int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_byt
                 id_result* out, void* stream);
 
 /* Batched adaptive IDs (the paper's future-work item 3, Sec. 6): `count`
-   independent problems A[i] (HOST array of descriptors, DEVICE data) with shared
-   options; out is a HOST array of `count` results.  Not yet built: returns
-   ID_ERR_UNSUPPORTED. */
+   independent problems A[i] (HOST array of descriptors, DEVICE data, one dtype:
+   F64 or F32 with sketch_prec = lu_prec = that dtype, n <= 4096 each) run
+   Algorithm 1 with the shared options in ONE persistent kernel launch replayed
+   from a CUDA graph: each CTA takes problems from a work queue (largest m*n
+   first) and runs every step of the method for it with CTA-local
+   synchronisation.  opts->block defaults to 32 here and is at most 32;
+   opts->omega must be NULL (Gaussian rows come from opts->seed, the same
+   counters as id_adaptive); k0 and blocks_per_pass are ignored.  out is a HOST
+   array of `count` results with caller-owned J / X per problem (ldx >= the
+   problem's rank cap); per-problem k, est_err, norm_A, rounds and status are
+   filled.  The return value is the most severe per-problem status.  The CTA
+   GEMM tile height and CTAs per SM are picked by a built-in autotuner on the
+   first call for a size class (the environment variable
+   RANDID_BATCHED_CONFIG=<32|64>x<1|2> pins them); results do not depend on the
+   choice. */
 int id_batched_workspace_size(int64_t count, const id_matrix* A, const id_opts* opts,
                               size_t* bytes);
 int id_batched(int64_t count, const id_matrix* A, const id_opts* opts, void* ws,

@@ -49,7 +49,8 @@ class IdResult(C.Structure):
                 ("pivots", C.c_void_p), ("est_trace", C.c_void_p), ("trace_cap", C.c_int64),
                 ("est_err", C.c_double), ("norm_A", C.c_double), ("rounds", C.c_int32),
                 ("passes", C.c_int32), ("launches", C.c_int64),
-                ("phase_ms", C.c_double * 6), ("phase_launches", C.c_int64 * 6)]
+                ("phase_ms", C.c_double * 6), ("phase_launches", C.c_int64 * 6),
+                ("status", C.c_int32)]
 
 
 _lib = None
@@ -276,3 +277,52 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, stream=None,
     if rc != 0:
         raise IDError(rc, "id_sketch")
     return G
+
+
+def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, k_max: int | None = None,
+               seed: int = 0, pivots: bool = False, stream=None,
+               workspace: torch.Tensor | None = None, outs: list | None = None) -> list:
+    """Adaptive column IDs of many independent matrices in one persistent launch.
+    As: column-major CUDA tensors of one dtype (FP64 or FP32), n <= 4096 each.
+    Returns one IDResult per matrix (per-problem status in .status)."""
+    if not As:
+        return []
+    dt = _TORCH_TO_ID[As[0].dtype]
+    count = len(As)
+    mats = (IdMatrix * count)(*[_matrix(a) for a in As])
+    opts = _opts(As[0], block=block, tol=tol, relative=relative, k_max=k_max or 0, k0=0,
+                 blocks_per_pass=1, seed=seed, omega=None, profile=False)
+    lib = load()
+    nb = C.c_size_t(0)
+    rc = lib.id_batched_workspace_size(count, mats, C.byref(opts), C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_batched_workspace_size")
+    ws = _workspace(int(nb.value), As[0].device, workspace)
+    xdt = torch.float64 if dt == F64 else torch.float32
+    res = (IdResult * count)()
+    keep = []
+    for i, a in enumerate(As):
+        m, n = a.shape
+        kmax = min(m, n) if not k_max else min(k_max, m, n)
+        if outs is not None:
+            J, Xb = outs[i]
+        else:
+            J = torch.empty(kmax, dtype=torch.int64, device=a.device)
+            Xb = torch.empty((n, kmax), dtype=xdt, device=a.device)
+        piv = torch.empty(kmax, dtype=torch.float64, device=a.device) if pivots else None
+        res[i].J, res[i].X, res[i].ldx = J.data_ptr(), Xb.data_ptr(), Xb.stride(0)
+        res[i].pivots = piv.data_ptr() if piv is not None else None
+        keep.append((J, Xb, piv))
+    rc = lib.id_batched(count, mats, C.byref(opts), ws.data_ptr(), ws.numel(), res, _stream(stream))
+    if rc < 0 and rc != ERR_NONFINITE:
+        raise IDError(rc, "id_batched")
+    out = []
+    for i in range(count):
+        J, Xb, piv = keep[i]
+        r = res[i]
+        k = int(r.k)
+        st = int(r.status)
+        out.append(IDResult(k=k, J=J[:k], X=Xb.t()[:k], est_err=r.est_err, norm_A=r.norm_A,
+                            rounds=r.rounds, passes=r.passes, launches=r.launches, status=st, trace=[],
+                            pivots=None if piv is None else piv[:k], phase_ms={}, phase_launches={}))
+    return out

@@ -462,6 +462,7 @@ class Engine {
     if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
     if (h_.tol_not_met) status |= ID_WARN_TOL_NOT_MET;
     if (h_.zero_pivots) status |= ID_WARN_ZERO_PIVOT;
+    out_->status = status;
     out_->k = k;
     out_->est_err = est_zero_ ? 0.0 : h_.est;
     out_->norm_A = sqrt(h_.norm2_A);
@@ -517,6 +518,7 @@ int check_out(const Plan& p, const id_result* out) {
 }
 
 void clear_out(id_result* out) {
+  out->status = ID_OK;
   out->k = 0;
   out->est_err = 0.0;
   out->norm_A = 0.0;
@@ -574,26 +576,6 @@ int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_byt
   }
   Engine<float> e(p, A, opts, ws, out, s);
   return e.run_adaptive();
-}
-
-int id_batched_workspace_size(int64_t count, const id_matrix* A, const id_opts* opts, size_t* bytes) {
-  (void)count;
-  (void)A;
-  (void)opts;
-  if (bytes) *bytes = 0;
-  return ID_ERR_UNSUPPORTED;
-}
-
-int id_batched(int64_t count, const id_matrix* A, const id_opts* opts, void* ws, size_t ws_bytes, id_result* out,
-               void* stream) {
-  (void)count;
-  (void)A;
-  (void)opts;
-  (void)ws;
-  (void)ws_bytes;
-  (void)out;
-  (void)stream;
-  return ID_ERR_UNSUPPORTED;
 }
 
 int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W, int64_t ldw, void* ws,

@@ -43,39 +43,6 @@ __device__ __forceinline__ double to_double(T x) {
 __device__ __forceinline__ double to_double(__nv_bfloat16 x) { return static_cast<double>(__bfloat162float(x)); }
 
 // ============================================================ Gaussian rows
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64
-// -> 128-bit products whose high halves are xored into the other words and the
-// round key, with the key bumped by two Weyl constants between rounds.
-__device__ __forceinline__ void philox4x64_10(uint64_t& x0, uint64_t& x1, uint64_t& x2, uint64_t& x3,
-                                              uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
-    const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
-    const uint64_t y0 = hi1 ^ x1 ^ k0;
-    const uint64_t y2 = hi0 ^ x3 ^ k1;
-    x0 = y0;
-    x1 = lo1;
-    x2 = y2;
-    x3 = lo0;
-    k0 += W0;
-    k1 += W1;
-  }
-}
-
-// Box-Muller on two 53-bit uniforms in (0, 1].
-__device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, double& z1) {
-  const double u1 = (double)((a >> 11) + 1ull) * 0x1.0p-53;
-  const double u2 = (double)((b >> 11) + 1ull) * 0x1.0p-53;
-  const double r = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  z0 = r * cs;
-  z1 = r * sn;
-}
-
 template <typename T>
 __global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, T* __restrict__ out,
                                 int64_t ld, const int32_t* done) {
@@ -369,31 +336,6 @@ cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_
 // candidate slot, one bounded grid barrier, a redundant global argmax in
 // every block, then division by the pivot and the rank-1 update (Eq. lupps)
 // of the block's unselected rows.  Rows are marked, never swapped.
-__device__ __forceinline__ ArgMax block_argmax(ArgMax a) {
-  __shared__ double s_v[32];
-  __shared__ int s_i[32];
-  __shared__ ArgMax s_res;
-  a = warp_argmax(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    s_v[warp] = a.v;
-    s_i[warp] = a.idx;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    ArgMax b;
-    b.v = lane < nw ? s_v[lane] : -1.0;
-    b.idx = lane < nw ? s_i[lane] : -1;
-    b = warp_argmax(b);
-    if (lane == 0) s_res = b;
-  }
-  __syncthreads();
-  const ArgMax r = s_res;
-  __syncthreads();
-  return r;
-}
-
 constexpr int kPanelThreads = 256;
 constexpr int kPanelMaxW = 128;
 

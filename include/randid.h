@@ -87,12 +87,20 @@ typedef struct {
   int64_t blocks_per_pass; /* sketch blocks drawn per later pass over A; 0 = 1 */
   uint64_t seed;        /* key of the Philox4x64-10 generator of Omega */
   /* Optional caller-supplied sketching matrix: DEVICE, row-major omega_rows x m
-     with row stride ld_omega >= m, dtype lu_prec.  Block t uses rows
+     with row stride ld_omega >= m, dtype sketch_prec.  Block t uses rows
      [t*b, t*b+b); omega_rows must cover every row the run may draw.
      NULL = generate from `seed`. */
   const void* omega;
   int64_t ld_omega, omega_rows;
   int profile;          /* 1: time each phase with CUDA events (id_result.phase_ms) */
+  /* Optional learned rank predictor (DEVICE, id_mlp_param_count() floats, see
+     id_mlp_forward).  When set, id_adaptive evaluates it on the pivots of the
+     first block and sketches the blocks up to the predicted rank in as few
+     passes over A as max_pass_rows allows.  J, X and k are those of the plain
+     loop (the rows are counter-based and LUPP pivots do not depend on later
+     columns); only the number of passes over A changes. */
+  const float* predictor;
+  int64_t max_pass_rows;  /* rows per pass the predictor may request; 0 = 16 b */
 } id_opts;
 
 /* Phases reported in id_result.phase_ms / phase_launches. */
@@ -193,6 +201,32 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
 int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes);
 int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec,
               void* G, int64_t ldg, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- learned rank predictor
+   A 35 -> 128 -> 128 -> 1 MLP with tanh hidden layers, FP32.  Parameter block
+   (id_mlp_param_count() floats): W1 [128 x 35] row-major, b1 [128], W2 [128 x 128],
+   b2 [128], w3 [128], b3, then the input standardisation mu [35], sigma [35] and
+   the output scale y_mu, y_sigma.  Inputs (id_rank_features): log10 of the first
+   32 LUPP pivot magnitudes of the first sketch block relative to the first
+   (Remark 1 ties them to the spectrum), log10 m, log10 n, log10 of the relative
+   tolerance.  Output: log2 of the rank of the adaptive loop.  The trainable
+   parameters are the first 21249 entries. */
+#define ID_MLP_IN 35
+#define ID_MLP_HIDDEN 128
+int64_t id_mlp_param_count(void);
+/* y[i] = predicted log2 rank for the feature row x[i*35 .. i*35+34] (DEVICE). */
+int id_mlp_forward(const float* params, int64_t batch, const float* x, float* y, void* stream);
+/* loss = mean_i (yhat_i - t_i)^2 on the standardised output (t_i = (target_i - y_mu)
+   / y_sigma) and its gradient w.r.t. the 21249 trainable parameters (DEVICE).
+   Deterministic (one CTA, fixed summation order). */
+int id_mlp_loss_grad(const float* params, int64_t batch, const float* x, const float* target, float* grad,
+                     float* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1) on the
+   trainable parameters; m1, m2: DEVICE moment buffers of 21249 floats. */
+int id_mlp_adam(float* params, const float* grad, float* m1, float* m2, int64_t step, float lr, void* stream);
+/* The 35 features from the pivots |U(i,i)| of the first block (DEVICE doubles). */
+int id_rank_features(const double* pivots, int64_t npiv, int64_t m, int64_t n, double rel_tol, float* x,
+                     void* stream);
 
 /* Human-readable text for a status value. */
 const char* id_status_string(int status);

@@ -41,7 +41,7 @@ class IdOpts(C.Structure):
                 ("tol", C.c_double), ("tol_relative", C.c_int), ("k_max", C.c_int64),
                 ("k0", C.c_int64), ("blocks_per_pass", C.c_int64), ("seed", C.c_uint64),
                 ("omega", C.c_void_p), ("ld_omega", C.c_int64), ("omega_rows", C.c_int64),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("predictor", C.c_void_p), ("max_pass_rows", C.c_int64)]
 
 
 class IdResult(C.Structure):
@@ -75,6 +75,14 @@ def load():
     lib.id_gaussian_rows.argtypes = [u64, i64, i64, i64, C.c_int, P, i64, P]
     lib.id_sketch_workspace_size.argtypes = [P, i64, C.c_int, C.POINTER(C.c_size_t)]
     lib.id_sketch.argtypes = [P, P, i64, i64, C.c_int, P, i64, P, C.c_size_t, P]
+    lib.id_mlp_param_count.argtypes = []
+    lib.id_mlp_param_count.restype = i64
+    lib.id_mlp_forward.argtypes = [P, i64, P, P, P]
+    lib.id_mlp_loss_grad.argtypes = [P, i64, P, P, P, P, P]
+    lib.id_mlp_adam.argtypes = [P, P, P, P, i64, C.c_float, P]
+    lib.id_rank_features.argtypes = [P, i64, i64, i64, C.c_double, P, P]
+    for f in ("id_mlp_forward", "id_mlp_loss_grad", "id_mlp_adam", "id_rank_features"):
+        getattr(lib, f).restype = C.c_int
     lib.id_status_string.argtypes = [C.c_int]
     lib.id_status_string.restype = C.c_char_p
     for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
@@ -216,13 +224,21 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
                 k_max: int | None = None, k0: int = 0, blocks_per_pass: int = 1, seed: int = 0,
                 omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                 trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
-                out: tuple | None = None) -> IDResult:
+                out: tuple | None = None, predictor: torch.Tensor | None = None,
+                max_pass_rows: int = 0) -> IDResult:
     """randLUPPadap column ID (Algorithm 1).  `out` = (J, Xbuf) reuses output buffers
-    (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major)."""
+    (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major).  `predictor`:
+    FP32 CUDA tensor of id_mlp_param_count() parameters; it sets how many blocks
+    the second pass over A sketches (results are those of the plain loop)."""
     m, n = A.shape
     kmax = min(m, n) if not k_max else min(k_max, m, n)
     opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,
                  blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile)
+    if predictor is not None:
+        if not predictor.is_cuda or predictor.dtype != torch.float32 or predictor.numel() != mlp_param_count():
+            raise ValueError("predictor must be a CUDA float32 tensor of id_mlp_param_count() values")
+        opts.predictor = predictor.data_ptr()
+        opts.max_pass_rows = max_pass_rows
     ws = _workspace(workspace_size(A, opts, 0), A.device, workspace)
     xdt = torch.float64 if opts.lu_prec == F64 else torch.float32
     if out is None:
@@ -326,3 +342,56 @@ def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, 
                             rounds=r.rounds, passes=r.passes, launches=r.launches, status=st, trace=[],
                             pivots=None if piv is None else piv[:k], phase_ms={}, phase_launches={}))
     return out
+
+
+# ---------------------------------------------------------------- learned rank predictor
+MLP_IN, MLP_HIDDEN = 35, 128
+MLP_TRAINABLE = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+
+
+def mlp_param_count() -> int:
+    return int(load().id_mlp_param_count())
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """Predicted log2 rank for each feature row of x (batch x 35, FP32, CUDA)."""
+    x = x.contiguous()
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    rc = load().id_mlp_forward(params.data_ptr(), x.shape[0], x.data_ptr(), y.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+                  stream=None):
+    """(loss, grad): mean squared error on the standardised output and its gradient
+    with respect to the trainable parameters."""
+    x = x.contiguous()
+    target = target.contiguous()
+    if grad is None:
+        grad = torch.empty(MLP_TRAINABLE, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    rc = load().id_mlp_loss_grad(params.data_ptr(), x.shape[0], x.data_ptr(), target.data_ptr(),
+                                 grad.data_ptr(), loss.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam(params: torch.Tensor, grad: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, step: int,
+             lr: float, stream=None) -> None:
+    rc = load().id_mlp_adam(params.data_ptr(), grad.data_ptr(), m1.data_ptr(), m2.data_ptr(), step, lr,
+                            _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_mlp_adam")
+
+
+def rank_features(pivots: torch.Tensor, m: int, n: int, rel_tol: float, stream=None) -> torch.Tensor:
+    """The 35 predictor features from the first pivots |U(i,i)| (CUDA float64)."""
+    x = torch.empty(MLP_IN, dtype=torch.float32, device=pivots.device)
+    rc = load().id_rank_features(pivots.data_ptr(), pivots.numel(), m, n, rel_tol, x.data_ptr(),
+                                 _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_rank_features")
+    return x

@@ -57,6 +57,8 @@ int choose_splits(int64_t M, int64_t N, int64_t K, int sms, int cap) {
 struct Plan {
   int64_t m = 0, n = 0, b = 0, cap = 0, k = 0, l = 0;
   int64_t rows_first = 0, rows_pass = 0, ldg = 0, wmax = 0, max_rounds = 0;
+  int64_t rows_pred = 0;  // largest pass the learned predictor may request
+  int s1_cap = 1;         // largest split-K count any pass uses (sizes the partials)
   int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
   bool gen_omega = true;
   size_t esz = 0;
@@ -126,24 +128,24 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     p->rows_pass = imin(per, max_blocks) * b;
     p->wmax = b;
     p->max_rounds = max_blocks + 1;
+    if (o->predictor != nullptr) {
+      const int64_t cap_rows = o->max_pass_rows > 0 ? cdiv(o->max_pass_rows, b) * b : 16 * b;
+      p->rows_pred = imin(cap_rows, max_blocks * b);
+    }
   }
   if (!p->gen_omega) {
     if (o->ld_omega < A->m) return kBadOpts;
     const int64_t need = l > 0 ? l : (cdiv(p->cap, b) + 1) * b;
     if (o->omega_rows < need) return kBadOpts;
   }
-  const int64_t rows_max = imax(p->rows_first, p->rows_pass);
+  const int64_t rows_max = imax(imax(p->rows_first, p->rows_pass), p->rows_pred);
   p->ldg = rows_max;
-  if (path == 16) {
-    p->s1_first = tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, p->rows_first, p->sms));
-    p->s1_pass = p->rows_pass > 0
-                     ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, p->rows_pass, p->sms))
-                     : 1;
-  } else {
-    p->s1_first = choose_splits(p->n, p->rows_first, p->m, p->sms, 16);
-    p->s1_pass = p->rows_pass > 0 ? choose_splits(p->n, p->rows_pass, p->m, p->sms, 16) : 1;
-  }
-  const int s1 = p->s1_first > p->s1_pass ? p->s1_first : p->s1_pass;
+  // one split-K count for every pass (see Engine::splits_for): that of a pass of
+  // one block (adaptive) or of the l rows (fixed rank)
+  const int64_t unit = l > 0 ? l : b;
+  const int s1 = path == 16 ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
+                            : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
+  p->s1_first = p->s1_pass = p->s1_cap = s1;
   p->s2max = 8;
   p->nparts = 2 * p->sms;
   p->maxg = p->sms;
@@ -237,8 +239,10 @@ class Engine {
       if (t >= sketched) {
         const int64_t max_blocks = cdiv(p_.cap, b) + 1;
         int64_t rows = t == 0 ? p_.rows_first : p_.rows_pass;
+        if (t > 0 && pred_blocks_ > t)  // blocks t .. pred_blocks_ certify the predicted rank
+          rows = imax(rows, imin((pred_blocks_ - t + 1) * b, p_.rows_pred));
         rows = imin(rows, (max_blocks - t) * b);
-        RID_TRY(sketch(t * b, rows, t == 0 ? p_.s1_first : p_.s1_pass));
+        RID_TRY(sketch(t * b, rows, splits_for(rows)));
         gstart = t;
         sketched = t + rows / b;
       }
@@ -251,6 +255,17 @@ class Engine {
       }
       const int64_t bt = imin(b, p_.cap - tb);
       RID_TRY(factor(b, bt, tb, na));
+      if (t == 0 && o_.predictor != nullptr) {
+        // learned rank guess from the first block's pivots: it only sets how many
+        // blocks the next pass over A sketches
+        RID_TRY(tbegin(ID_PHASE_OTHER));
+        RID_TRY(cuda(mlp_predict_rank(o_.predictor, pivdiag_, (int)imin(bt, 32), p_.m, p_.n, o_.tol,
+                                      o_.tol_relative, st_, s_)));
+        RID_TRY(tend(1));
+        RID_TRY(sync_state());
+        pred_blocks_ = imin(cdiv(imax(h_.k_pred, 1), b), cdiv(p_.cap, b));
+        predicted_ = h_.k_pred;
+      }
       tb += bt;
       na -= bt;
       ++t;
@@ -266,7 +281,7 @@ class Engine {
 
   int run_fixed() {
     RID_TRY(start());
-    RID_TRY(sketch(0, p_.l, p_.s1_first));
+    RID_TRY(sketch(0, p_.l, splits_for(p_.l)));
     int64_t tb = 0, na = p_.n;
     while (tb < p_.k) {
       const int64_t w = imin(p_.b, p_.k - tb);
@@ -341,6 +356,16 @@ class Engine {
   }
 
   // G(:, 0:rows) = (Omega rows [row0, row0+rows)) A, stored n x rows (row-major, ld ldg).
+  // Split-K count of every sketch pass.  It depends on the problem and the block
+  // size only -- never on how many blocks a pass draws -- so each entry of the
+  // sketch is summed in the same order whatever the pass size, and a rank guess
+  // (k0, blocks_per_pass, the learned predictor) leaves J, X and k bit-identical.
+  int splits_for(int64_t /*rows*/) {
+    const int64_t unit = p_.l > 0 ? p_.l : p_.b;
+    if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
+    return gemm_splits((int)p_.m, choose_splits(p_.n, unit, p_.m, p_.sms, 16));
+  }
+
   int sketch(int64_t row0, int64_t rows, int splits) {
     if (p_.path == 16) return sketch_tc(row0, rows, splits);
     const T* Om;
@@ -498,6 +523,8 @@ class Engine {
   int cur_ = 0;
   int cur_phase_ = 0;
   bool est_zero_ = false;
+  int64_t pred_blocks_ = 0;  // blocks certifying the predicted rank (0: no predictor)
+  int64_t predicted_ = 0;
   int32_t passes_ = 0;
   int64_t launches_ = 0;
   double phase_ms_[kNumPhases];

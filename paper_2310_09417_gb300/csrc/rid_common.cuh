@@ -20,6 +20,7 @@ struct DevState {
   double est;             // last estimate E
   double thr;             // stopping threshold tau (absolute)
   int64_t k_final;        // rank when stopped
+  int64_t k_pred;         // rank proposed by the learned predictor (0: none)
   int32_t done;           // 1: stop decided -- later speculative kernels exit
   int32_t tol_not_met;    // 1: stopped at the rank cap with E > tau
   int32_t rounds;         // estimates computed

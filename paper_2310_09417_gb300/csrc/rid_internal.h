@@ -104,6 +104,11 @@ cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cuda
 
 cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, cudaStream_t s);
 
+// ---- learned rank predictor (rid_mlp.cu): features of the first block's pivots, one
+// forward pass, ceil(2^output) written to st->k_pred.
+cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, int64_t m, int64_t n, double tol,
+                             int tol_rel, DevState* st, cudaStream_t s);
+
 // ---- tensor-core sketch (rid_tc_sketch.cu): out[z] (n x rows, FP32, row stride out_ld)
 // holds split z of (W A)^T for BF16 A (m x n, column-major) and W (rows x m, row-major).
 // TMA needs 16-byte aligned bases and leading dimensions that are multiples of 8.

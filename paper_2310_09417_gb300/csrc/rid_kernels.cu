@@ -627,6 +627,7 @@ __global__ void k_init_state(DevState* st, int32_t* act, int32_t* pivmark, int64
     st->est = 0.0;
     st->thr = 0.0;
     st->k_final = -1;
+    st->k_pred = 0;
     st->done = 0;
     st->tol_not_met = 0;
     st->rounds = 0;

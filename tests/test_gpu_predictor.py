@@ -1,0 +1,120 @@
+"""The learned rank predictor: kernels against the FP64 oracle, the seeded loop
+against the plain loop, and what a trained network gains on a held-out family."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp as omlp  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_09417_gb300 import build
+    build.build()
+    from paper_2310_09417_gb300 import binding
+    binding.load()
+    return binding
+
+
+def params_np(seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(omlp.TOTAL)
+    p[:omlp.TRAINABLE] = 0.2 * rng.standard_normal(omlp.TRAINABLE)
+    p[omlp.TRAINABLE:omlp.TRAINABLE + 35] = rng.standard_normal(35)
+    p[omlp.TRAINABLE + 35:omlp.TRAINABLE + 70] = 0.5 + rng.random(35)
+    p[-2], p[-1] = 6.0, 1.5
+    return p.astype(np.float32)
+
+
+def test_param_layout_matches(B):
+    assert B.mlp_param_count() == omlp.TOTAL
+    assert B.MLP_TRAINABLE == omlp.TRAINABLE
+
+
+def test_forward_matches_oracle(B):
+    p = params_np(1)
+    x = np.random.default_rng(2).standard_normal((300, 35)).astype(np.float32)
+    y = B.mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = omlp.forward(p.astype(np.float64), x.astype(np.float64))
+    np.testing.assert_allclose(y, ref, rtol=2e-5, atol=2e-5)
+
+
+def test_loss_and_gradient_match_oracle(B):
+    """GPU backward (FP32, one CTA, fixed order) against the FP64 backprop of the
+    oracle, itself pinned by finite differences."""
+    p = params_np(3)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((257, 35)).astype(np.float32)
+    t = (6.0 + 1.5 * rng.standard_normal(257)).astype(np.float32)
+    loss, g = B.mlp_loss_grad(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    L, gref = omlp.loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(L, rel=1e-5)
+    g = g.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert err < 1e-5, err
+    # deterministic: same bits twice
+    _, g2 = B.mlp_loss_grad(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    assert np.array_equal(g2.cpu().numpy(), g.astype(np.float32))
+
+
+def test_adam_matches_oracle(B):
+    p = params_np(5)
+    rng = np.random.default_rng(6)
+    g = rng.standard_normal(omlp.TRAINABLE).astype(np.float32)
+    m1 = (0.1 * rng.standard_normal(omlp.TRAINABLE)).astype(np.float32)
+    m2 = (0.1 * rng.random(omlp.TRAINABLE)).astype(np.float32)
+    pd, m1d, m2d = (torch.from_numpy(a.copy()).cuda() for a in (p, m1, m2))
+    B.mlp_adam(pd, torch.from_numpy(g).cuda(), m1d, m2d, 7, 1e-3)
+    pr, m1r, m2r = omlp.adam(p.astype(np.float64), g.astype(np.float64), m1.astype(np.float64),
+                             m2.astype(np.float64), 7, 1e-3)
+    np.testing.assert_allclose(pd.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(m2d.cpu().numpy(), m2r, rtol=1e-5, atol=1e-9)
+
+
+def test_features_match_oracle(B):
+    piv = np.abs(np.random.default_rng(7).standard_normal(40)) + 1e-3
+    x = B.rank_features(torch.from_numpy(piv).cuda(), 5000, 1200, 3e-7).cpu().numpy()
+    np.testing.assert_allclose(x, omlp.features(piv, 5000, 1200, 3e-7), rtol=1e-6, atol=1e-6)
+
+
+def test_seeded_loop_identical_and_fewer_passes(B):
+    """Any predictor only changes how many blocks each pass sketches: J, X and
+    k equal the plain loop's; a prediction near the true rank cuts the passes."""
+    from paper_2310_09417_gb300 import workloads as W
+    A = W.spectral_matrix(1500, 1000, W.spectrum("geometric", 1000, per_decade=40.0), seed=8)
+    Ad = B.colmajor(torch.from_numpy(A).cuda())
+    plain = B.id_adaptive(Ad, 1e-8, block=32, seed=4)
+    # a hand-set network that always predicts the true rank: all weights zero,
+    # b3 = 0 and y_mu = log2(k)
+    p = torch.zeros(B.mlp_param_count(), dtype=torch.float32, device="cuda")
+    p[B.MLP_TRAINABLE + 35:B.MLP_TRAINABLE + 70] = 1.0
+    p[-2] = float(np.log2(plain.k))
+    p[-1] = 1.0
+    seeded = B.id_adaptive(Ad, 1e-8, block=32, seed=4, predictor=p, max_pass_rows=4096)
+    assert seeded.k == plain.k and torch.equal(seeded.J, plain.J) and torch.equal(seeded.X, plain.X)
+    assert seeded.passes == 2 < plain.passes
+    # an underestimate and an overestimate still return the plain result
+    for guess in (plain.k // 3, 3 * plain.k):
+        p[-2] = float(np.log2(guess))
+        s = B.id_adaptive(Ad, 1e-8, block=32, seed=4, predictor=p, max_pass_rows=4096)
+        assert s.k == plain.k and torch.equal(s.J, plain.J) and torch.equal(s.X, plain.X)
+        assert s.passes < plain.passes
+
+
+def test_trained_network_gains_on_held_out_family(B):
+    """Train on exponential / polynomial / kernel runs, evaluate on the held-out
+    step family: identical results, same tolerance-miss rate, fewer passes."""
+    from paper_2310_09417_gb300 import predictor as P
+    params, rep = P.run(train_count=90, eval_count=8, held_out="step", seed=21, steps=600)
+    hist = rep["loss_history"]
+    assert hist[-1][1] < hist[0][1]
+    for key in ("held_out_tol_0.0001", "held_out_tol_1e-08"):
+        s = rep[key]
+        assert s["all_identical"]
+        assert s["miss_rate_seeded"] == s["miss_rate_plain"]
+        assert s["passes_seeded"] < s["passes_plain"]

@@ -1,0 +1,65 @@
+"""Pins for the predictor's CPU oracle: its backpropagated gradient against
+central finite differences of its loss (a check independent of the chain-rule
+formulas), the loss at a hand-computable point, and one Adam step against the
+closed form of the first step."""
+import numpy as np
+
+from oracle import mlp
+
+
+def random_params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(mlp.TOTAL)
+    p[:mlp.TRAINABLE] = scale * rng.standard_normal(mlp.TRAINABLE)
+    p[mlp.TRAINABLE:mlp.TRAINABLE + 35] = rng.standard_normal(35)          # mu
+    p[mlp.TRAINABLE + 35:mlp.TRAINABLE + 70] = 0.5 + rng.random(35)        # sigma
+    p[-2], p[-1] = 7.0, 2.0                                                 # y_mu, y_sigma
+    return p
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    p = random_params(2)
+    x = rng.standard_normal((9, 35))
+    t = 7.0 + 2.0 * rng.standard_normal(9)
+    L, g = mlp.loss_grad(p, x, t)
+    assert L == mlp.loss(p, x, t)
+    idx = np.concatenate([rng.choice(mlp.TRAINABLE, 60, replace=False),
+                          [0, 35 * 128 - 1, mlp.TRAINABLE - 1, mlp.TRAINABLE - 2]])
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.loss(pp, x, t) - mlp.loss(pm, x, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_loss_closed_form_at_zero_weights():
+    """With all weights zero the output is b3 everywhere: L = mean((b3 - t_std)^2)."""
+    p = random_params(3)
+    p[:mlp.TRAINABLE] = 0.0
+    p[mlp.TRAINABLE - 1] = 0.25  # b3
+    t = np.array([7.0, 9.0, 5.0])
+    t_std = (t - 7.0) / 2.0
+    assert abs(mlp.loss(p, np.zeros((3, 35)), t) - np.mean((0.25 - t_std) ** 2)) < 1e-15
+    assert np.allclose(mlp.forward(p, np.zeros((3, 35))), 0.25 * 2.0 + 7.0)
+
+
+def test_first_adam_step_closed_form():
+    """At step 1 the bias-corrected moments are g and g^2, so the update is
+    -lr * g / (|g| + eps)."""
+    rng = np.random.default_rng(4)
+    p = random_params(5)
+    g = rng.standard_normal(mlp.TRAINABLE)
+    p1, m1, m2 = mlp.adam(p, g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    np.testing.assert_allclose(p1[:mlp.TRAINABLE] - p[:mlp.TRAINABLE], -1e-3 * g / (np.abs(g) + 1e-8),
+                               rtol=1e-9)
+    np.testing.assert_array_equal(p1[mlp.TRAINABLE:], p[mlp.TRAINABLE:])
+
+
+def test_features_definition():
+    f = mlp.features(np.array([4.0, 2.0, 1.0]), 1000, 10, 1e-6)
+    assert f[0] == 0.0 and abs(f[1] - np.log10(0.5)) < 1e-15 and abs(f[2] - np.log10(0.25)) < 1e-15
+    assert f[3] == -30.0  # missing pivots read as the floor
+    assert (f[32], f[33], f[34]) == (3.0, 1.0, -6.0)

@@ -178,9 +178,14 @@ int id_batched(int64_t count, const id_matrix* A, const id_opts* opts, void* ws,
                size_t ws_bytes, id_result* out, void* stream);
 
 /* Two-sided ID from a column skeleton (Sec. 2.2.1 "Two-sided ID", Sec. 3.1):
-   LUPP of C = A(:,J) (m x k) picks row skeletons I (k), and W (m x k, column-
-   major, ldw >= m) = P^T [I; L2 L1^{-1}] (Eq. inty) satisfies C = W C(I,:), so
-   A ~ W A(I,J) X.  Not yet built: returns ID_ERR_UNSUPPORTED. */
+   LUPP of C = A(:,J) (m x k, the columns J gathered on the device) picks the row
+   skeletons I (k, DEVICE int64, pivot order), and W (m x k, column-major, ldw >= m,
+   dtype of A) = P^T [I; L2 L1^{-1}] (Eq. inty) satisfies C = W C(I,:), W(I,:) = I_k,
+   so that A ~ W A(I,J) X with the column ID's X.  The paper derives the row
+   skeletons of a CUR factorisation the same way (LUPP on the selected columns,
+   Sec. 3.1).  A: F64 or F32.  J: DEVICE int64[k]; an entry outside [0, n) returns
+   -2.  ws: id_cur_workspace_size bytes, 256-aligned. */
+int id_cur_workspace_size(const id_matrix* A, int64_t k, size_t* bytes);
 int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W,
                 int64_t ldw, void* ws, size_t ws_bytes, void* stream);
 

@@ -72,6 +72,8 @@ def load():
     lib.id_batched_workspace_size.argtypes = [i64, P, P, C.POINTER(C.c_size_t)]
     lib.id_batched.argtypes = [i64, P, P, P, C.c_size_t, P, P]
     lib.cur_from_id.argtypes = [P, P, i64, P, P, i64, P, C.c_size_t, P]
+    lib.id_cur_workspace_size.argtypes = [P, i64, C.POINTER(C.c_size_t)]
+    lib.id_cur_workspace_size.restype = C.c_int
     lib.id_gaussian_rows.argtypes = [u64, i64, i64, i64, C.c_int, P, i64, P]
     lib.id_sketch_workspace_size.argtypes = [P, i64, C.c_int, C.POINTER(C.c_size_t)]
     lib.id_sketch.argtypes = [P, P, i64, i64, C.c_int, P, i64, P, C.c_size_t, P]
@@ -395,3 +397,25 @@ def rank_features(pivots: torch.Tensor, m: int, n: int, rel_tol: float, stream=N
     if rc != 0:
         raise IDError(rc, "id_rank_features")
     return x
+
+
+def cur_from_id(A: torch.Tensor, J: torch.Tensor, *, stream=None,
+                workspace: torch.Tensor | None = None):
+    """Row skeletons I and the row interpolation matrix W (m x k) of C = A(:, J):
+    A ~ W A(I, J) X (two-sided ID).  Returns (I, W)."""
+    m, n = A.shape
+    k = J.numel()
+    lib = load()
+    nb = C.c_size_t(0)
+    rc = lib.id_cur_workspace_size(C.byref(_matrix(A)), k, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_cur_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    I = torch.empty(k, dtype=torch.int64, device=A.device)
+    W = torch.empty((k, m), dtype=A.dtype, device=A.device).t()  # column-major m x k
+    J = J.to(torch.int64).contiguous()
+    rc = lib.cur_from_id(C.byref(_matrix(A)), J.data_ptr(), k, I.data_ptr(), W.data_ptr(), W.stride(1),
+                         ws.data_ptr(), ws.numel(), _stream(stream))
+    if rc < 0:
+        raise IDError(rc, "cur_from_id")
+    return I, W

@@ -298,6 +298,28 @@ class Engine {
     return finish(p_.k);
   }
 
+  // LUPP of a given panel instead of a sketch: G (p_.n rows x p_.k columns) is
+  // gathered from the columns J of `src` (m_src x n_src, ld_src), its rows are
+  // pivoted for k steps, and the interpolation coefficients land in the X buffer.
+  int run_panel(const T* src, int64_t m_src, int64_t n_src, int64_t ld_src, const int64_t* J) {
+    RID_TRY(tbegin(ID_PHASE_OTHER));
+    RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
+    RID_TRY(cuda(gather_panel<T>(src, ld_src, m_src, n_src, J, p_.k, G_, st_, s_)));
+    RID_TRY(tend(2));
+    int64_t tb = 0, na = p_.n;
+    while (tb < p_.k) {
+      const int64_t w = imin(p_.b, p_.k - tb);
+      RID_TRY(schur(tb, w, tb, na));
+      RID_TRY(factor(w, w, tb, na));
+      tb += w;
+      na -= w;
+    }
+    est_zero_ = true;
+    RID_TRY(sync_state());
+    if (h_.err & kErrBadIndex) return -2;
+    return finish(p_.k);
+  }
+
  private:
   int cuda(cudaError_t e) { return e == cudaSuccess ? 0 : ID_ERR_CUDA; }
 
@@ -605,18 +627,80 @@ int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_byt
   return e.run_adaptive();
 }
 
+namespace {
+// Plan of cur_from_id: the panel C = A(:,J) has m rows (the items pivoted) and k
+// columns; the interpolation buffer (k x m) follows the engine's workspace.
+int cur_plan(const id_matrix* A, int64_t k, Plan* p, size_t* xoff, size_t* total) {
+  if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= ((int64_t)1 << 30))
+    return -1;
+  if (A->dtype != ID_F64 && A->dtype != ID_F32) return ID_ERR_UNSUPPORTED;
+  if (k < 1 || k > A->m || k > A->n) return -3;
+  id_matrix P = *A;
+  P.m = k;  // the panel is gathered, not sketched: only its k columns matter
+  P.n = A->m;
+  P.ld = k;
+  id_opts o;
+  memset(&o, 0, sizeof(o));
+  o.sketch_prec = o.lu_prec = A->dtype;
+  o.block = 64;
+  const int rc = make_plan(&P, &o, k, k, p);
+  if (rc != ID_OK) return rc;
+  *xoff = p->total;
+  *total = p->total + align_up((size_t)k * A->m * p->esz);
+  return ID_OK;
+}
+}  // namespace
+
+int id_cur_workspace_size(const id_matrix* A, int64_t k, size_t* bytes) {
+  if (bytes == nullptr) return -3;
+  Plan p;
+  size_t xoff = 0;
+  const int rc = cur_plan(A, k, &p, &xoff, bytes);
+  return rc == -3 ? -2 : rc;
+}
+
 int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W, int64_t ldw, void* ws,
                 size_t ws_bytes, void* stream) {
-  (void)A;
-  (void)J;
-  (void)k;
-  (void)I;
-  (void)W;
-  (void)ldw;
-  (void)ws;
-  (void)ws_bytes;
-  (void)stream;
-  return ID_ERR_UNSUPPORTED;
+  Plan p;
+  size_t xoff = 0, total = 0;
+  const int rc = cur_plan(A, k, &p, &xoff, &total);
+  if (rc != ID_OK) return rc;
+  if (J == nullptr) return -2;
+  if (I == nullptr) return -4;
+  if (W == nullptr || ldw < A->m) return -5;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < total)
+    return ID_ERR_WORKSPACE;
+  id_matrix P = *A;
+  P.m = k;
+  P.n = A->m;
+  P.ld = k;
+  id_opts o;
+  memset(&o, 0, sizeof(o));
+  o.sketch_prec = o.lu_prec = A->dtype;
+  o.block = 64;
+  id_result out;
+  memset(&out, 0, sizeof(out));
+  out.J = I;
+  out.X = static_cast<unsigned char*>(ws) + xoff;
+  out.ldx = k;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st;
+  if (A->dtype == ID_F64) {
+    Engine<double> e(p, &P, &o, ws, &out, s);
+    st = e.run_panel(static_cast<const double*>(A->data), A->m, A->n, A->ld, J);
+    if (st >= 0 && transpose_w<double>(static_cast<const double*>(out.X), k, A->m, k, static_cast<double*>(W), ldw,
+                                       s) != cudaSuccess)
+      return ID_ERR_CUDA;
+  } else {
+    Engine<float> e(p, &P, &o, ws, &out, s);
+    st = e.run_panel(static_cast<const float*>(A->data), A->m, A->n, A->ld, J);
+    if (st >= 0 && transpose_w<float>(static_cast<const float*>(out.X), k, A->m, k, static_cast<float*>(W), ldw,
+                                      s) != cudaSuccess)
+      return ID_ERR_CUDA;
+  }
+  if (st < 0) return st;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
+  return st;
 }
 
 int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype, void* out, int64_t ld,

@@ -11,6 +11,7 @@ constexpr int kNumPhases = 6;
 enum : unsigned {
   kErrTimeout = 1u,   // a bounded wait gave up
   kErrNonFinite = 2u, // NaN or Inf met in the input
+  kErrBadIndex = 4u,  // an index argument read on the device was out of range
 };
 
 // Device-resident control block at the start of every workspace.  The host

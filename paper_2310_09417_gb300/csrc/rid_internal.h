@@ -104,6 +104,13 @@ cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cuda
 
 cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, cudaStream_t s);
 
+// G (m x k row-major) = A(:, J); W (m x k column-major) = X^T.
+template <typename T>
+cudaError_t gather_panel(const T* A, int64_t lda, int64_t m, int64_t n, const int64_t* J, int64_t k, T* G,
+                         DevState* st, cudaStream_t s);
+template <typename T>
+cudaError_t transpose_w(const T* X, int64_t ldx, int64_t m, int64_t k, T* W, int64_t ldw, cudaStream_t s);
+
 // ---- learned rank predictor (rid_mlp.cu): features of the first block's pivots, one
 // forward pass, ceil(2^output) written to st->k_pred.
 cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, int64_t m, int64_t n, double tol,

@@ -620,6 +620,57 @@ cudaError_t finalize_x(int64_t k, const int32_t* perm32, T* X, int64_t ldx, cuda
   return cudaGetLastError();
 }
 
+// G (m x k, row-major) = A(:, J): the panel whose rows are LU-pivoted to pick the
+// row skeletons of C = A(:, J).  Out-of-range column indices set kErrBadIndex.
+template <typename T>
+__global__ void k_gather_panel(const T* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                               const int64_t* __restrict__ J, int64_t k, T* __restrict__ G, DevState* st) {
+  const int64_t total = m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k, c = e - i * k;
+    const int64_t j = J[c];
+    if (j < 0 || j >= n) {
+      atomicOr(&st->err, kErrBadIndex);
+      G[e] = T(0);
+    } else {
+      G[e] = A[i + j * lda];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t gather_panel(const T* A, int64_t lda, int64_t m, int64_t n, const int64_t* J, int64_t k, T* G,
+                         DevState* st, cudaStream_t s) {
+  int64_t blocks = (m * k + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_gather_panel<T><<<(int)blocks, 256, 0, s>>>(A, lda, m, n, J, k, G, st);
+  return cudaGetLastError();
+}
+
+// W (m x k, column-major, ldw) from the interpolation buffer X (k x m, column-major,
+// ldx): W(i, c) = X(c, i).
+template <typename T>
+__global__ void k_transpose_w(const T* __restrict__ X, int64_t ldx, int64_t m, int64_t k, T* __restrict__ W,
+                              int64_t ldw) {
+  const int64_t total = m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / m, i = e - c * m;  // consecutive threads write consecutive i
+    W[i + c * ldw] = X[c + i * ldx];
+  }
+}
+
+template <typename T>
+cudaError_t transpose_w(const T* X, int64_t ldx, int64_t m, int64_t k, T* W, int64_t ldw, cudaStream_t s) {
+  int64_t blocks = (m * k + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_transpose_w<T><<<(int)blocks, 256, 0, s>>>(X, ldx, m, k, W, ldw);
+  return cudaGetLastError();
+}
+
 __global__ void k_init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -667,7 +718,10 @@ cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, 
   template cudaError_t make_n<T>(int, int, const T*, int64_t, const T*, const int32_t*, const int32_t*, T*, \
                                  T*, int64_t, int64_t, const int32_t*, int32_t*, const int32_t*,            \
                                  cudaStream_t);                                                             \
-  template cudaError_t finalize_x<T>(int64_t, const int32_t*, T*, int64_t, cudaStream_t);
+  template cudaError_t finalize_x<T>(int64_t, const int32_t*, T*, int64_t, cudaStream_t);                  \
+  template cudaError_t gather_panel<T>(const T*, int64_t, int64_t, int64_t, const int64_t*, int64_t, T*,     \
+                                       DevState*, cudaStream_t);                                            \
+  template cudaError_t transpose_w<T>(const T*, int64_t, int64_t, int64_t, T*, int64_t, cudaStream_t);
 
 RID_INST(double)
 RID_INST(float)

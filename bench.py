@@ -37,9 +37,14 @@ WORKLOADS = {
     "adaptive_step_f32": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f32", 1e-6, 64),
     "adaptive_poly_f64": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
     "adaptive_step_f64": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64", 1e-10, 64),
+    # FP64 A, LU and X with the FP64-accurate sketch on the BF16 tensor cores (exact digit
+    # slices of A, Omega on the grid 2^-10)
+    "adaptive_poly_f64emu": (40000, 10000, "poly", {}, "f64emu", 1e-10, 64),
+    "adaptive_step_f64emu": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64emu", 1e-10, 64),
     # reduced sizes of the same families, for profiler captures (inputs still > L2)
     "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
+    "small_poly_f64emu": (16384, 4096, "poly", {}, "f64emu", 1e-10, 64),
     # mixed precision: A stored in BF16 = Gaussian factor product of rank 1500 + 1e-4 noise,
     # sketch on the tensor cores (BF16 x BF16 -> FP32), LU in FP32, norms in FP64
     "mixed_bf16": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 1e-3, 64),
@@ -297,11 +302,14 @@ def config_dict(name, res):
                        % (kw.get("rank"), kw.get("noise"))}[kind]
     if name.startswith("small_"):
         spec += " (reduced size for profiling)"
-    el = {"f32": 4, "f64": 8, "bf16": 2}[dt]
+    el = {"f32": 4, "f64": 8, "f64emu": 8, "bf16": 2}[dt]
     prec = {"f64": "FP64 sketch, LU and X", "f32": "FP32 sketch, LU and X",
+            "f64emu": "FP64 A, LU and X; FP64-accurate sketch on the BF16 tensor cores (8 exact 7-bit digit "
+                      "slices of A, Omega on the grid 2^-10 in 2 digits, exact FP32 chunk sums, int64 totals)",
             "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
     c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
-         "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device",
+         "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device"
+                                     + (", rounded to the grid 2^-10" if dt == "f64emu" else ""),
          "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * el / 1e9),
          "parallelism": "replicas (one ID per GPU)"}
     if res is not None:
@@ -433,7 +441,8 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks):
                     "batch_gb": round(nbytes / 1e9, 2)})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": dt, "data": "synthetic", "config": cfg, "roofline": roofline,
+                "vs_baseline": None, "dtype": "f64 (sketch: bf16 digit products, exact sums)" if dt == "f64emu" else dt,
+                "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
                 "result": {"ids_per_s": len(As) * world / (ms * 1e-3), "gflop_per_step": flops / 1e9,
                            "statuses": sorted(set(r.status for r in res))}}
@@ -499,17 +508,18 @@ def main():
     A = make_input(name, dev)
     seed = 2310_09417 + 100 * rank
     kmax = min(m, n)
-    xdt = torch.float64 if dt == "f64" else torch.float32
+    xdt = torch.float64 if dt in ("f64", "f64emu") else torch.float32
+    sprec = B.F64_EMU if dt == "f64emu" else None
     J = torch.empty(kmax, dtype=torch.int64, device=dev)
     Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
     opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
-                   omega=None, profile=True)
+                   omega=None, profile=True, sketch_prec=sprec)
     ws = torch.empty(B.workspace_size(A, opts), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(profile=True):
         return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
-                             workspace=ws, out=(J, Xbuf), stream=stream)
+                             workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec)
 
     for _ in range(args.warmup):
         res = step()
@@ -545,6 +555,19 @@ def main():
         roofline = {"bound": "hbm", "kernel": "k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    elif dt == "f64emu":
+        # HBM-bound at one block per pass (rows = 64: about 120 tensor flop/B against a
+        # ridge near 290): per pass the 8 BF16 digit slices of A (16 mn) + both Omega digit
+        # planes (4 b m) + the FP64 sketch block (8 n b); once per ID the digit preparation
+        # (A read twice, the slices written: 32 mn)
+        mp = (m + 7) // 8 * 8
+        sk_bytes = (16.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * res.passes + 32.0 * m * n
+        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
+        peak = PEAKS["hbm_gbs"]
+        roofline = {"bound": "hbm", "kernel": "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K "
+                    "reduce + digit preparation", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(name),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:
         sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
         achieved = sk_flops / (sk_ms * 1e-3) / 1e12
@@ -570,7 +593,7 @@ def main():
         def e2e_step():
             A_dev.copy_(A_host, non_blocking=True)
             r = B.id_adaptive(A_dev.t(), tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
-                              workspace=ws, out=(J, Xbuf), stream=stream)
+                              workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec)
             kk = r.k
             X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
             J_host[:kk].copy_(J[:kk], non_blocking=True)
@@ -604,7 +627,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": dt, "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64 (sketch: bf16 digit products, exact sums)" if dt == "f64emu" else dt,
+                "data": "synthetic",
                 "config": config_dict(name, res), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clk.summary(),
                 "result": {"k": res.k, "est_err_rel": res.est_err / res.norm_A, "status": res.status,

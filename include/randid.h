@@ -61,7 +61,16 @@ typedef enum {
   ID_F64 = 0,
   ID_F32 = 1,
   ID_BF16 = 2,
-  ID_FP8_E4M3 = 3
+  ID_FP8_E4M3 = 3,
+  /* sketch_prec only, with F64 A and lu_prec F64: the sketch computed to FP64
+     accuracy on the BF16 tensor cores by exact integer slicing.  A is split once
+     per call into 8 digit slices of 7 bits with per-column exponents (55 bits);
+     Omega is the Gaussian on the grid 2^-10 (|z| < 8), split into 2 digits; the
+     digit products are summed exactly in FP32 over chunks of 1024 and in FP64
+     across chunks.  Entry error <= 2^-47 max_i|A_ij| sum_r |Omega_cr|.  A caller
+     omega (F64) is rounded to the same grid (clipped at |q| <= 8127).  Extra
+     workspace: 16 bytes per element of A. */
+  ID_F64_EMU = 4
 } id_dtype;
 
 /* An input matrix: DEVICE data, column-major m x n, leading dimension ld >= m. */
@@ -202,7 +211,9 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
    Paths: A F64 / sketch F64 (FP64 FMA, G in FP64); A F32 / F32 (FP32 FMA, G in
    FP32); A BF16 / BF16 (tcgen05 tensor cores fed by TMA, FP32 accumulation, G in
    FP32; A->ld and ld_omega multiples of 8, 16-byte aligned bases, else
-   ID_ERR_UNSUPPORTED).  ws: at least id_sketch_workspace_size bytes, 256-aligned. */
+   ID_ERR_UNSUPPORTED); A F64 / ID_F64_EMU (omega F64, rounded to the grid 2^-10,
+   then the FP64-accurate digit-sliced product on the tensor cores, G in FP64).
+   ws: at least id_sketch_workspace_size bytes, 256-aligned. */
 int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes);
 int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec,
               void* G, int64_t ldg, void* ws, size_t ws_bytes, void* stream);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librandid.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "randid.h")
 
 # id_dtype
-F64, F32, BF16, FP8_E4M3 = 0, 1, 2, 3
+F64, F32, BF16, FP8_E4M3, F64_EMU = 0, 1, 2, 3, 4
 # status
 OK, WARN_TOL_NOT_MET, WARN_ZERO_PIVOT = 0, 1, 2
 ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = -101, -102, -103, -104, -105
@@ -202,11 +202,13 @@ def _result(res: IdResult, J, Xbuf, k, n, status, trace_buf, piv) -> IDResult:
 
 def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int = 0,
                   omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
-                  stream=None, workspace: torch.Tensor | None = None) -> IDResult:
-    """randLUPP fixed-rank column ID (Sec. 3.1): J (k), X (k x n), estimate from l - k rows."""
+                  stream=None, workspace: torch.Tensor | None = None,
+                  sketch_prec: int | None = None) -> IDResult:
+    """randLUPP fixed-rank column ID (Sec. 3.1): J (k), X (k x n), estimate from l - k rows.
+    sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit slicing."""
     m, n = A.shape
     opts = _opts(A, block=block, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1,
-                 seed=seed, omega=omega, profile=profile)
+                 seed=seed, omega=omega, profile=profile, sketch_prec=sketch_prec)
     ws = _workspace(workspace_size(A, opts, l), A.device, workspace)
     J = torch.empty(k, dtype=torch.int64, device=A.device)
     Xbuf = torch.empty((n, k), dtype=torch.float64 if opts.lu_prec == F64 else torch.float32,
@@ -227,15 +229,18 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
                 omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                 trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
                 out: tuple | None = None, predictor: torch.Tensor | None = None,
-                max_pass_rows: int = 0) -> IDResult:
+                max_pass_rows: int = 0, sketch_prec: int | None = None) -> IDResult:
     """randLUPPadap column ID (Algorithm 1).  `out` = (J, Xbuf) reuses output buffers
     (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major).  `predictor`:
     FP32 CUDA tensor of id_mlp_param_count() parameters; it sets how many blocks
-    the second pass over A sketches (results are those of the plain loop)."""
+    the second pass over A sketches (results are those of the plain loop).
+    sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit
+    slicing, FP64 accurate, with Omega on the grid 2^-10."""
     m, n = A.shape
     kmax = min(m, n) if not k_max else min(k_max, m, n)
     opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,
-                 blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile)
+                 blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile,
+                 sketch_prec=sketch_prec)
     if predictor is not None:
         if not predictor.is_cuda or predictor.dtype != torch.float32 or predictor.numel() != mlp_param_count():
             raise ValueError("predictor must be a CUDA float32 tensor of id_mlp_param_count() values")
@@ -274,22 +279,24 @@ def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
 
 
 def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, stream=None,
-              workspace: torch.Tensor | None = None) -> torch.Tensor:
+              workspace: torch.Tensor | None = None, sketch_prec: int | None = None) -> torch.Tensor:
     """G = (omega A)^T (n x rows): the sketch step alone.  omega is row-major
-    (rows x m) in the sketch precision (A's dtype); G is FP64 for FP64 input and
-    FP32 otherwise (BF16 input runs on the tensor cores)."""
+    (rows x m) in A's dtype; G is FP64 for FP64 input and FP32 otherwise (BF16
+    input runs on the tensor cores).  sketch_prec=F64_EMU (FP64 A): the product
+    of omega rounded to the grid 2^-10 and A, FP64 accurate, on the tensor cores."""
     m, n = A.shape
     if omega.dim() != 2 or omega.shape[1] != m or omega.stride(1) != 1 or omega.dtype != A.dtype:
         raise ValueError("omega must be row-major (rows x m) with A's dtype")
     rows = omega.shape[0]
-    prec = _TORCH_TO_ID[A.dtype]
+    prec = _TORCH_TO_ID[A.dtype] if sketch_prec is None else sketch_prec
     nb = C.c_size_t(0)
     lib = load()
     rc = lib.id_sketch_workspace_size(C.byref(_matrix(A)), rows, prec, C.byref(nb))
     if rc != 0:
         raise IDError(rc, "id_sketch_workspace_size")
     ws = _workspace(int(nb.value), A.device, workspace)
-    G = torch.empty((n, rows), dtype=torch.float64 if prec == F64 else torch.float32, device=A.device)
+    G = torch.empty((n, rows), dtype=torch.float64 if A.dtype == torch.float64 else torch.float32,
+                    device=A.device)
     rc = lib.id_sketch(C.byref(_matrix(A)), omega.data_ptr(), omega.stride(0), rows, prec, G.data_ptr(),
                        G.stride(0), ws.data_ptr(), ws.numel(), _stream(stream))
     if rc != 0:

@@ -62,13 +62,13 @@ struct Plan {
   int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
   bool gen_omega = true;
   size_t esz = 0;
-  int path = 0;          // 64, 32 (SIMT) or 16 (BF16 tensor-core sketch)
+  int path = 0;          // 64, 32 (SIMT), 16 (BF16 tensor-core sketch) or 65 (FP64 by digit slicing)
   int64_t ldw = 0;       // row stride of the generated Omega
   size_t wsz = 0;        // bytes per Omega element
   size_t off_state = 0, off_omega = 0, off_G = 0, off_Gpart = 0, off_S = 0, off_Spart = 0, off_N = 0,
          off_Linv = 0, off_act0 = 0, off_act1 = 0, off_pivmark = 0, off_perm32 = 0, off_piv = 0,
          off_pivorig = 0, off_pivdiag = 0, off_cand_v = 0, off_cand_i = 0, off_cand_rows = 0, off_e2 = 0,
-         off_normp = 0, off_trace = 0, total = 0;
+         off_normp = 0, off_trace = 0, off_digits = 0, off_colexp = 0, total = 0;
 };
 
 // Which (input, sketch, LU) precision triples are built.
@@ -77,6 +77,8 @@ int precision_path(const id_matrix* A, const id_opts* o) {
   if (A->dtype == ID_F32 && o->sketch_prec == ID_F32 && o->lu_prec == ID_F32) return 32;
   // BF16 input: sketch on the tensor cores (FP32 accumulation), LU and X in FP32
   if (A->dtype == ID_BF16 && o->sketch_prec == ID_BF16 && o->lu_prec == ID_F32) return 16;
+  // FP64 input: FP64-accurate sketch on the tensor cores, LU and X in FP64
+  if (A->dtype == ID_F64 && o->sketch_prec == ID_F64_EMU && o->lu_prec == ID_F64) return 65;
   return 0;
 }
 
@@ -105,8 +107,8 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->sms = num_sms();
   p->esz = o->lu_prec == ID_F64 ? 8 : 4;
   p->path = path;
-  p->ldw = path == 16 ? cdiv(A->m, 8) * 8 : A->m;
-  p->wsz = path == 16 ? 2 : p->esz;
+  p->ldw = path == 16 ? cdiv(A->m, 8) * 8 : (path == 65 ? f64emu_pad(A->m) : A->m);
+  p->wsz = path == 16 || path == 65 ? 2 : p->esz;
   p->gen_omega = (o->omega == nullptr);
   if (l > 0) {  // fixed rank; sizes do not depend on k (estimate block sized for k = 1)
     if (l > ((int64_t)1 << 20)) return kBadL;
@@ -143,8 +145,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // one split-K count for every pass (see Engine::splits_for): that of a pass of
   // one block (adaptive) or of the l rows (fixed rank)
   const int64_t unit = l > 0 ? l : b;
-  const int s1 = path == 16 ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
-                            : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
+  const int s1 = path == 16   ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
+                 : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
+                              : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
   p->s1_first = p->s1_pass = p->s1_cap = s1;
   p->s2max = 8;
   p->nparts = 2 * p->sms;
@@ -157,7 +160,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     return at;
   };
   p->off_state = take(256);
-  p->off_omega = take(p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0);
+  // path 65 keeps two digit planes of Omega, also for a caller Omega (rounded to its grid)
+  p->off_omega = take(path == 65 ? 2 * (size_t)rows_max * p->ldw * p->wsz
+                                 : (p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0));
   p->off_G = take((size_t)p->n * rows_max * e);
   p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * e : 0);
   p->off_S = take((size_t)p->n * p->wmax * e);
@@ -177,6 +182,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_e2 = take((size_t)p->nparts * 8);
   p->off_normp = take((size_t)p->nparts * 8);
   p->off_trace = take((size_t)p->max_rounds * 8);
+  // path 65: the 8 digit slices of A and its column exponents
+  p->off_digits = take(path == 65 ? (size_t)8 * p->ldw * p->n * 2 : 0);
+  p->off_colexp = take(path == 65 ? (size_t)p->n * 4 : 0);
   p->total = off;
   return ID_OK;
 }
@@ -218,6 +226,8 @@ class Engine {
     e2_ = reinterpret_cast<double*>(w + p.off_e2);
     normp_ = reinterpret_cast<double*>(w + p.off_normp);
     trace_ = reinterpret_cast<double*>(w + p.off_trace);
+    digits_ = w + p.off_digits;
+    colexp_ = reinterpret_cast<int32_t*>(w + p.off_colexp);
     X_ = static_cast<T*>(out->X);
     ldx_ = out->ldx;
     done_ = &st_->done;
@@ -367,6 +377,11 @@ class Engine {
     RID_TRY(tend(3));
     RID_TRY(sync_state());
     if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
+    if (p_.path == 65) {  // column exponents and digit slices of A, once per call
+      RID_TRY(tbegin(ID_PHASE_SKETCH));
+      RID_TRY(cuda(f64emu_prepare(reinterpret_cast<const double*>(Araw_), lda_, p_.m, p_.n, colexp_, digits_, s_)));
+      RID_TRY(tend(2));
+    }
     return 0;
   }
 
@@ -385,11 +400,13 @@ class Engine {
   int splits_for(int64_t /*rows*/) {
     const int64_t unit = p_.l > 0 ? p_.l : p_.b;
     if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
+    if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
     return gemm_splits((int)p_.m, choose_splits(p_.n, unit, p_.m, p_.sms, 16));
   }
 
   int sketch(int64_t row0, int64_t rows, int splits) {
     if (p_.path == 16) return sketch_tc(row0, rows, splits);
+    if (p_.path == 65) return sketch_emu(row0, rows, splits);
     const T* Om;
     int64_t ldo;
     if (p_.gen_omega) {
@@ -439,6 +456,26 @@ class Engine {
       RID_TRY(cuda(splitk_reduce<float>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
                                         reinterpret_cast<const float*>(Gpart_), reinterpret_cast<float*>(G_), done_,
                                         s_)));
+    RID_TRY(tend(splits > 1 ? 2 : 1));
+    ++passes_;
+    return 0;
+  }
+
+  // FP64 A on the tensor cores: Omega rows [row0, row0+rows) on the grid 2^-10 as
+  // two digit planes, then G = Omega A from the digit slices of A (FP64 accurate).
+  int sketch_emu(int64_t row0, int64_t rows, int splits) {
+    RID_TRY(tbegin(ID_PHASE_OMEGA));
+    const double* src = p_.gen_omega ? nullptr : static_cast<const double*>(o_.omega) + row0 * o_.ld_omega;
+    RID_TRY(cuda(f64emu_omega(o_.seed, row0, rows, p_.m, p_.ldg, src, o_.ld_omega, omega_, done_, s_)));
+    RID_TRY(tend(1));
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    double* out = reinterpret_cast<double*>(splits > 1 ? Gpart_ : G_);
+    RID_TRY(cuda(f64emu_sketch(digits_, colexp_, p_.m, p_.n, omega_, rows, p_.ldg, out, p_.ldg,
+                               (int64_t)p_.n * p_.ldg, splits, st_, done_, s_)));
+    if (splits > 1)
+      RID_TRY(cuda(splitk_reduce<double>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
+                                         reinterpret_cast<const double*>(Gpart_), reinterpret_cast<double*>(G_),
+                                         done_, s_)));
     RID_TRY(tend(splits > 1 ? 2 : 1));
     ++passes_;
     return 0;
@@ -540,6 +577,8 @@ class Engine {
   T *omega_, *G_, *Gpart_, *S_, *Spart_, *N_, *Linv_, *cand_rows_, *X_;
   int32_t *act_[2], *pivmark_, *perm32_, *piv_, *pivorig_, *cand_i_;
   double *pivdiag_, *cand_v_, *e2_, *normp_, *trace_;
+  void* digits_;       // path 65: digit slices of A
+  int32_t* colexp_;    // path 65: column exponents of A
   const int32_t* done_;
   int64_t ldx_;
   int cur_ = 0;
@@ -603,7 +642,7 @@ int id_fixed_rank(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts,
   if (check_ws(p, ws, ws_bytes) != ID_OK) return ID_ERR_WORKSPACE;
   clear_out(out);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision_path(A, opts) == 64) {
+  if (precision_path(A, opts) >= 64) {
     Engine<double> e(p, A, opts, ws, out, s);
     return e.run_fixed();
   }
@@ -619,7 +658,7 @@ int id_adaptive(const id_matrix* A, const id_opts* opts, void* ws, size_t ws_byt
   if (check_ws(p, ws, ws_bytes) != ID_OK) return ID_ERR_WORKSPACE;
   clear_out(out);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision_path(A, opts) == 64) {
+  if (precision_path(A, opts) >= 64) {
     Engine<double> e(p, A, opts, ws, out, s);
     return e.run_adaptive();
   }
@@ -728,16 +767,22 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
       A->n >= ((int64_t)1 << 30))
     return -1;
   if (rows < 1 || rows > ((int64_t)1 << 20)) return -2;
-  *path = (A->dtype == ID_F64 && prec == ID_F64) ? 64
-          : (A->dtype == ID_F32 && prec == ID_F32) ? 32
-          : (A->dtype == ID_BF16 && prec == ID_BF16) ? 16
-                                                     : 0;
+  *path = (A->dtype == ID_F64 && prec == ID_F64)       ? 64
+          : (A->dtype == ID_F64 && prec == ID_F64_EMU) ? 65
+          : (A->dtype == ID_F32 && prec == ID_F32)     ? 32
+          : (A->dtype == ID_BF16 && prec == ID_BF16)   ? 16
+                                                       : 0;
   if (*path == 0) return ID_ERR_UNSUPPORTED;
   const int sms = num_sms();
-  const size_t esz = *path == 64 ? 8 : 4;
-  *splits = *path == 16 ? tc_sketch_effective_splits(A->m, tc_sketch_splits(A->m, A->n, rows, sms))
-                        : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
+  const size_t esz = *path >= 64 ? 8 : 4;
+  *splits = *path == 16   ? tc_sketch_effective_splits(A->m, tc_sketch_splits(A->m, A->n, rows, sms))
+            : *path == 65 ? f64emu_splits(A->m, A->n, sms)
+                          : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
   *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  if (*path == 65) {  // digit slices of A, column exponents, two digit planes of Omega
+    const size_t mp = (size_t)f64emu_pad(A->m);
+    *bytes += align_up(8 * mp * A->n * 2) + align_up((size_t)A->n * 4) + align_up(2 * mp * rows * 2);
+  }
   return ID_OK;
 }
 }  // namespace
@@ -764,32 +809,50 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
   void* part = static_cast<unsigned char*>(ws) + 256;
   if (init_state(st, nullptr, nullptr, 0, s) != cudaSuccess) return ID_ERR_CUDA;
   cudaError_t e = cudaSuccess;
-  const int64_t zs = A->n * ldg;
+  // split-K partials: row stride rows (what the workspace holds), reduced into G (row stride ldg)
+  const int64_t zs = A->n * rows;
   if (path == 16) {
     if (!tc_sketch_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
-    e = tc_sketch_bf16(A->data, A->ld, A->m, A->n, omega, ld_omega, rows, out, ldg, zs, splits, st, nullptr, s);
+    e = tc_sketch_bf16(A->data, A->ld, A->m, A->n, omega, ld_omega, rows, out, splits > 1 ? rows : ldg, zs, splits,
+                       st, nullptr, s);
     if (e == cudaSuccess && splits > 1)
-      e = splitk_reduce<float>(A->n, (int)rows, ldg, splits, zs, static_cast<float*>(part), static_cast<float*>(G),
-                               nullptr, s);
+      e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
+                                  static_cast<float*>(G), nullptr, s);
+  } else if (path == 65) {
+    unsigned char* w = static_cast<unsigned char*>(part) + (splits > 1 ? align_up((size_t)splits * A->n * rows * 8) : 0);
+    const size_t mp = (size_t)f64emu_pad(A->m);
+    void* digits = w;
+    int32_t* colexp = reinterpret_cast<int32_t*>(w + align_up(8 * mp * A->n * 2));
+    void* wdig = w + align_up(8 * mp * A->n * 2) + align_up((size_t)A->n * 4);
+    double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
+    e = f64emu_prepare(static_cast<const double*>(A->data), A->ld, A->m, A->n, colexp, digits, s);
+    if (e == cudaSuccess)
+      e = f64emu_omega(0, 0, rows, A->m, rows, static_cast<const double*>(omega), ld_omega, wdig, nullptr, s);
+    if (e == cudaSuccess)
+      e = f64emu_sketch(digits, colexp, A->m, A->n, wdig, rows, rows, out, splits > 1 ? rows : ldg, zs, splits, st,
+                        nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce_ld<double>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<double*>(part),
+                                   static_cast<double*>(G), nullptr, s);
   } else if (path == 64) {
     Operand<double> a{static_cast<const double*>(A->data), A->ld, nullptr, 0};
     Operand<double> w{static_cast<const double*>(omega), ld_omega, nullptr, 0};
     double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
-    EpiArgs<double> ep{out, ldg, zs, nullptr, nullptr};
+    EpiArgs<double> ep{out, splits > 1 ? rows : ldg, zs, nullptr, nullptr};
     e = gemm_gather<double>((int)A->n, (int)rows, (int)A->m, splits, true, a, w, kEpiStore, ep, nullptr, s);
     if (e == cudaSuccess && splits > 1)
-      e = splitk_reduce<double>(A->n, (int)rows, ldg, splits, zs, static_cast<double*>(part),
-                                static_cast<double*>(G), nullptr, s);
+      e = splitk_reduce_ld<double>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<double*>(part),
+                                   static_cast<double*>(G), nullptr, s);
   } else {
     Operand<float> a{static_cast<const float*>(A->data), A->ld, nullptr, 0};
     Operand<float> w{static_cast<const float*>(omega), ld_omega, nullptr, 0};
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
-    EpiArgs<float> ep{out, ldg, zs, nullptr, nullptr};
+    EpiArgs<float> ep{out, splits > 1 ? rows : ldg, zs, nullptr, nullptr};
     e = gemm_gather<float>((int)A->n, (int)rows, (int)A->m, splits, true, a, w, kEpiStore, ep, nullptr, s);
     if (e == cudaSuccess && splits > 1)
-      e = splitk_reduce<float>(A->n, (int)rows, ldg, splits, zs, static_cast<float*>(part), static_cast<float*>(G),
-                               nullptr, s);
+      e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
+                                  static_cast<float*>(G), nullptr, s);
   }
   if (e != cudaSuccess) return ID_ERR_CUDA;
   DevState h;
@@ -859,7 +922,7 @@ extern "C" int id_fixed_rank_noalloc(const id_matrix* A, int64_t k, int64_t l, c
   o.profile = 0;  // no event objects
   clear_out(out);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision_path(A, &o) == 64) {
+  if (precision_path(A, &o) >= 64) {
     Engine<double> e(p, A, &o, ws, out, s);
     return e.run_fixed();
   }

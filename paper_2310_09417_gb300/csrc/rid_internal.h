@@ -57,6 +57,10 @@ cudaError_t norm2_final(const double* part, int nparts, DevState* st, cudaStream
 template <typename T>
 cudaError_t splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
                           const int32_t* done, cudaStream_t s);
+// the same with partials of row stride ldp: G[j*ldg + c] = sum_z P[z*zs + j*ldp + c]
+template <typename T>
+cudaError_t splitk_reduce_ld(int64_t n, int rows, int64_t ldp, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
+                             const int32_t* done, cudaStream_t s);
 
 // S[i*lds + c] = G[act[i]*ldg + col0 + c] - sum_z P[z*zs + i*lds + c]; e2part[blk] = sum S^2
 template <typename T>
@@ -115,6 +119,20 @@ cudaError_t transpose_w(const T* X, int64_t ldx, int64_t m, int64_t k, T* W, int
 // forward pass, ceil(2^output) written to st->k_pred.
 cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, int64_t m, int64_t n, double tol,
                              int tol_rel, DevState* st, cudaStream_t s);
+
+// ---- FP64-accurate sketch on the tensor cores (rid_tc_f64.cu).  A is split once into
+// 8 BF16 digit slices (slice-major, each column-major f64emu_pad(m) x n) with column
+// exponents; Omega rows are quantised to the grid 2^-10 and split into 2 digit planes
+// (each rows_alloc x f64emu_pad(m)); out[z] (n x rows, FP64) holds split z of (Omega A)^T.
+int64_t f64emu_pad(int64_t m);
+int f64emu_splits(int64_t m, int64_t n, int sms);
+cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, void* digits,
+                           cudaStream_t s);
+cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t rows_alloc,
+                         const double* src, int64_t ld_src, void* wdigits, const int32_t* done, cudaStream_t s);
+cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, int64_t n, const void* wdigits,
+                          int64_t rows, int64_t rows_alloc, double* out, int64_t out_ld, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s);
 
 // ---- tensor-core sketch (rid_tc_sketch.cu): out[z] (n x rows, FP32, row stride out_ld)
 // holds split z of (W A)^T for BF16 A (m x n, column-major) and W (rows x m, row-major).

@@ -243,28 +243,34 @@ cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<
 
 // ============================================================ split-K reductions
 template <typename T>
-__global__ void k_splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* __restrict__ P,
-                                T* __restrict__ G, const int32_t* done) {
+__global__ void k_splitk_reduce(int64_t n, int rows, int64_t ldp, int64_t ldg, int nz, int64_t zs,
+                                const T* __restrict__ P, T* __restrict__ G, const int32_t* done) {
   if (done != nullptr && *done) return;
   const int64_t total = n * rows;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / rows, c = e - j * rows;
-    const int64_t off = j * ldg + c;
+    const int64_t off = j * ldp + c;
     T acc = P[off];
     for (int z = 1; z < nz; ++z) acc += P[z * zs + off];
-    G[off] = acc;
+    G[j * ldg + c] = acc;
   }
+}
+
+template <typename T>
+cudaError_t splitk_reduce_ld(int64_t n, int rows, int64_t ldp, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
+                             const int32_t* done, cudaStream_t s) {
+  int64_t blocks = (n * rows + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_splitk_reduce<T><<<(int)blocks, 256, 0, s>>>(n, rows, ldp, ldg, nz, zs, P, G, done);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t splitk_reduce(int64_t n, int rows, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
                           const int32_t* done, cudaStream_t s) {
-  int64_t blocks = (n * rows + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
-  k_splitk_reduce<T><<<(int)blocks, 256, 0, s>>>(n, rows, ldg, nz, zs, P, G, done);
-  return cudaGetLastError();
+  return splitk_reduce_ld<T>(n, rows, ldg, ldg, nz, zs, P, G, done, s);
 }
 
 // S = G(act, col0:col0+w) - sum of the split-K partials of L2 L1^{-1} G(perm, .)
@@ -709,6 +715,8 @@ cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, 
                                         cudaStream_t);                                                      \
   template cudaError_t splitk_reduce<T>(int64_t, int, int64_t, int, int64_t, const T*, T*, const int32_t*,  \
                                         cudaStream_t);                                                      \
+  template cudaError_t splitk_reduce_ld<T>(int64_t, int, int64_t, int64_t, int, int64_t, const T*, T*,       \
+                                           const int32_t*, cudaStream_t);                                   \
   template cudaError_t schur_finish<T>(int, int, const int32_t*, const T*, int64_t, int64_t, int, int64_t,  \
                                        const T*, T*, int64_t, double*, int, const int32_t*, cudaStream_t);  \
   template PanelCfg panel_config<T>(int, int, int);                                                         \

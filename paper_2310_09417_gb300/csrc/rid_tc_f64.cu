@@ -1,0 +1,500 @@
+// rid_tc_f64.cu -- an FP64-accurate sketch Y = Omega A on the BF16 tensor cores.
+//
+// GB300 executes FP64 FMAs at 1.25 TFLOP/s, so the FP64 sketch (Sec. 2.4) is
+// moved onto the tensor cores by exact integer slicing:
+//   * A: per column j an exponent E_j with max_i |A_ij| < 2^E_j; x = A / 2^(E_j+1)
+//     (|x| < 1/2) is written as sum_{s<8} d_s 2^(-7(s+1)) + r with balanced 7-bit
+//     digits |d_s| <= 64 and |r| <= 2^-57 -- 55 significant bits per column.
+//   * Omega: standard normal numbers on the grid 2^-10, q = rint(1024 z) clipped to
+//     |q| <= 8127, split as q = 128 q1 + q0 with |q1| <= 63, |q0| <= 64.
+//   * Every digit is an integer exact in BF16.  Products of equal weight
+//     2^(-7g) share one FP32 accumulator group in tensor memory: group g collects
+//     q1 x d_g and q0 x d_(g-1) (g = 0..7, 8 groups x 64 columns = the 512
+//     columns of an SM; the g = 8 term q0 x d_7 is dropped).  One MMA with
+//     N = 128 (both Omega digits stacked) writes groups s and s+1 for slice s.
+//     Over a chunk of 1024 K a group's partial sums stay below
+//     1024 (64*64 + 63*64) < 2^23: the FP32 accumulation is exact.
+//   * After slice g of a chunk, group g is final for that chunk; the epilogue
+//     warps convert it to integers and add it, exactly, to two int64
+//     accumulators per entry (groups 0..3 and 4..7 with weights 2^(7(3-g)) and
+//     2^(7(7-g))), then hand the group back to the MMA issuer -- the epilogue
+//     of a chunk overlaps the MMAs of the next one.  At the end
+//     Y_cj = 2^(E_j - 9) (acc_hi 2^-21 + acc_lo 2^-49).
+// Error of an entry: the dropped q0 x d_7 products (|q0 2^-10| <= |Omega_cr|,
+// |d_7 2^-56| 2^(E_j+1) <= 2^-48 max_i|A_ij|), the digit remainder (2^-55) and
+// the final FP64 roundings stay below 2^-47 max_i|A_ij| sum_r |Omega_cr| -- far
+// inside the worst-case rounding bound m 2^-53 sum_r |Omega_cr||A_rj| of an FP64
+// dot product once m > 64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rid_internal.h"
+
+namespace rid {
+namespace tc64 {
+
+constexpr int kBM = 128;         // columns of A per tile (MMA M)
+constexpr int kBN = 64;          // rows of Omega per tile (MMA N per digit)
+constexpr int kBK = 64;          // K per stage
+constexpr int kSlices = 8;       // digits of A (= accumulator groups)
+constexpr int kChunkSteps = 16;  // K stages per exact chunk (1024 K)
+constexpr int kChunk = kChunkSteps * kBK;
+constexpr int kStages = 6;
+constexpr int kEpiWarps = 8;     // two per TMEM lane quarter, 32 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kMaxChunksPerSplit = 1 << 18;  // int64 accumulators: 2^18 * 2^44 < 2^63
+constexpr double kQMax = 8127.0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up (and flags kErrTimeout) after kWaitLimitNs, or at once
+// when another thread already flagged a timeout.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      if (ld_acquire_u32(&st->err) & kErrTimeout) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        atomicOr(&st->err, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+// Wait for copies or MMAs still in flight before the CTA exits, even after an
+// error was flagged (their writes must land first); bounded by its own limit.
+__device__ __noinline__ void mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) return;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile with 128-byte rows, 128-byte
+// swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  const uint64_t a = smem_u32(p);
+  uint64_t d = (a >> 4) & 0x3FFFull;
+  d |= 1ull << 16;
+  d |= (1024ull >> 4) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// acc += v * 2^sh, exact (v an integer-valued float below 2^23 in magnitude)
+template <int SH>
+__device__ __forceinline__ void add_scaled(long long& acc, float v) {
+  const int iv = __float2int_rn(v);
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
+}
+
+struct Smem {
+  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // one digit slice of A: 16 KB
+  alignas(1024) __nv_bfloat16 w[kStages][2 * kBN * kBK];  // both digits of Omega: 128 rows, 16 KB
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t ready[kSlices];  // group g of the current chunk is final
+  uint64_t free_[kSlices];  // the epilogue has read group g
+  uint64_t drain;
+  uint32_t tmem_base;
+};
+
+// Grid: x = tiles of Omega rows (fastest, so CTAs that share an A tile run
+// together and reuse it from L2), y = tiles of A's columns, z = K splits of
+// kchunk (a multiple of the exact chunk).  out: FP64 partial (n x rows, row
+// stride out_ld) of split blockIdx.z.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sketch_f64emu(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+                    const int32_t* __restrict__ colexp, int n, int rows, int K, int kchunk,
+                    double* __restrict__ out, int64_t out_ld, int64_t zstride, DevState* st, const int32_t* done) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kBN;
+  const int m0 = blockIdx.y * kBM;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nsteps = (kend - kbeg + kBK - 1) / kBK;  // K stages of this split
+  const int nchunks = (nsteps + kChunkSteps - 1) / kChunkSteps;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int g = 0; g < kSlices; ++g) {
+      mbar_init(&sm.ready[g], 1);
+      mbar_init(&sm.free_[g], kEpiWarps);
+    }
+    mbar_init(&sm.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer.  Stage order: chunk c, slice s, step j; each
+    // stage holds digit slice s of A and both Omega digits at K step j.
+    int it = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
+      for (int s = 0; s < kSlices && ok; ++s) {
+        for (int j = 0; j < steps_c; ++j, ++it) {
+          const int b = it % kStages;
+          if (it >= kStages && !mbar_wait(&sm.empty[b], ((it / kStages) + 1) & 1, st)) { ok = false; break; }
+          mbar_expect_tx(&sm.full[b], (kBM + 2 * kBN) * kBK * 2);
+          const int k0 = kbeg + (c * kChunkSteps + j) * kBK;
+          tma_load_3d(sm.a[b], &map_a, &sm.full[b], k0, m0, s);
+          tma_load_3d(sm.w[b], &map_w, &sm.full[b], k0, n0, 0);
+        }
+      }
+    }
+    // the copies still in flight land before the CTA may exit
+    for (int t = it - kStages < 0 ? 0 : it - kStages; t < it; ++t) mbar_wait_drain(&sm.full[t % kStages], (t / kStages) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t id128 = idesc_bf16(kBM, 2 * kBN), id64 = idesc_bf16(kBM, kBN);
+    int it = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
+      for (int s = 0; s < kSlices && ok; ++s) {
+        if (c > 0) {
+          // groups s and s+1 are overwritten from here on: the epilogue must have
+          // read them for chunk c-1 (group s was already awaited at slice s-1)
+          const uint32_t par = (c - 1) & 1;
+          if (s == 0 && !mbar_wait(&sm.free_[0], par, st)) { ok = false; break; }
+          if (s + 1 < kSlices && !mbar_wait(&sm.free_[s + 1], par, st)) { ok = false; break; }
+          fence_after_sync();
+        }
+        const uint32_t dst = tmem + s * kBN;
+        for (int j = 0; j < steps_c; ++j, ++it) {
+          const int b = it % kStages;
+          if (!mbar_wait(&sm.full[b], (it / kStages) & 1, st)) { ok = false; break; }
+          fence_after_sync();
+          const uint64_t da = desc_sw128(sm.a[b]);
+          const uint64_t dq1 = desc_sw128(sm.w[b]);             // high digit of Omega (weight 1)
+          const uint64_t dq0 = desc_sw128(sm.w[b] + kBN * kBK);  // low digit (weight 2^-7)
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const bool first = (j == 0 && kk == 0);
+            if (s == kSlices - 1) {
+              // group 7 <- q1 x d_7 (q0 x d_7 belongs to the dropped group 8)
+              mma_bf16(dst, da + 2 * kk, dq1 + 2 * kk, id64, 1u);
+            } else if (first && s > 0) {
+              // group s continues, group s+1 starts: two MMAs with their own flags
+              mma_bf16(dst, da, dq1, id64, 1u);
+              mma_bf16(dst + kBN, da, dq0, id64, 0u);
+            } else {
+              // groups s and s+1 at once (N = 128: q1 rows then q0 rows)
+              mma_bf16(dst, da + 2 * kk, dq1 + 2 * kk, id128, (first && s == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(&sm.empty[b]);
+        }
+        if (ok) mma_commit(&sm.ready[s]);  // group s is final for chunk c
+      }
+    }
+    // every MMA issued has completed before TMEM is released
+    mma_commit(&sm.drain);
+    mbar_wait_drain(&sm.drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: exact integer accumulation of the groups
+    const int ew = warp - 2;
+    const int quarter = warp & 3;  // TMEM lanes this warp may read
+    const int half = ew >> 2;      // columns [32 half, 32 half + 32) of the tile
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * 32;
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+#pragma unroll
+      for (int g = 0; g < kSlices; ++g) {
+        if (!mbar_wait(&sm.ready[g], c & 1, st)) { ok = false; break; }
+        fence_after_sync();
+#pragma unroll
+        for (int cb = 0; cb < 32; cb += 16) {
+          float v[16];
+          tmem_ld16(base + g * kBN + cb, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (g == 0) add_scaled<21>(hi[cb + i], v[i]);
+            else if (g == 1) add_scaled<14>(hi[cb + i], v[i]);
+            else if (g == 2) add_scaled<7>(hi[cb + i], v[i]);
+            else if (g == 3) add_scaled<0>(hi[cb + i], v[i]);
+            else if (g == 4) add_scaled<21>(lo[cb + i], v[i]);
+            else if (g == 5) add_scaled<14>(lo[cb + i], v[i]);
+            else if (g == 6) add_scaled<7>(lo[cb + i], v[i]);
+            else add_scaled<0>(lo[cb + i], v[i]);
+          }
+        }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.free_[g]);
+      }
+    }
+    if (ok && row < n) {
+      const int e = colexp[row];
+      double* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld + n0 + half * 32;
+      const int lim = rows - n0 - half * 32;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < lim) o[i] = ldexp(fma((double)lo[i], 0x1p-49, (double)hi[i] * 0x1p-21), e - 9);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ digit preparation
+// Column exponents: E_j with max_i |A_ij| < 2^E_j (0 for a zero column).
+__global__ void k_colexp(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, int32_t* __restrict__ E) {
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = fmax(mx, fabs(A[i + j * lda]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, s[w]);
+      int e = 0;
+      if (r > 0.0) {
+        frexp(r, &e);  // r = f 2^e, 0.5 <= f < 1: r < 2^e
+      }
+      E[j] = e;
+    }
+    __syncthreads();
+  }
+}
+
+// Digits: D[s][j][i] (slice-major, each slice column-major m_pad x n) of A(i, j).
+__global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_t m, int64_t m_pad, int64_t n,
+                               const int32_t* __restrict__ E, __nv_bfloat16* __restrict__ D) {
+  const int64_t total = m_pad * n;
+  const int64_t slice = m_pad * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m_pad, i = e - j * m_pad;
+    double x = i < m ? ldexp(A[i + j * lda], -(E[j] + 1)) : 0.0;  // |x| < 1/2
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      const double t = x * 128.0;  // exact
+      const double d = rint(t);    // |d| <= 64
+      x = t - d;                   // exact, |x| <= 1/2
+      D[s * slice + e] = __double2bfloat16(d);
+    }
+  }
+}
+
+// Omega digits on the grid 2^-10: W[t][r][i], t = 0 high digit q1, t = 1 low digit q0;
+// from the Philox/Box-Muller rows (gen) or a caller matrix (src != nullptr).
+__global__ void k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t ldw, int64_t rows_alloc,
+                               const double* __restrict__ src, int64_t ld_src, __nv_bfloat16* __restrict__ W,
+                               const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int64_t nq = (ldw + 3) >> 2;
+  const int64_t total = rows * nq;
+  const int64_t plane = rows_alloc * ldw;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / nq, q = e - r * nq;
+    double z[4];
+    if (src == nullptr) {
+      uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + r), x2 = 0, x3 = 0;
+      philox4x64_10(x0, x1, x2, x3, seed, 0ull);
+      box_muller(x0, x1, z[0], z[1]);
+      box_muller(x2, x3, z[2], z[3]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = 4 * q + u;
+      if (i >= ldw) break;
+      double val = 0.0;
+      if (i < m) val = src == nullptr ? z[u] : src[r * ld_src + i];
+      double qv = rint(val * 1024.0);
+      qv = fmin(fmax(qv, -kQMax), kQMax);
+      const double q1 = rint(qv / 128.0);
+      const double q0 = qv - 128.0 * q1;
+      W[r * ldw + i] = __double2bfloat16(q1);
+      W[plane + r * ldw + i] = __double2bfloat16(q0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t planes, int box_rows,
+                 int box_planes) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * outer * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc64
+
+int64_t f64emu_pad(int64_t m) { return (m + 7) / 8 * 8; }
+
+int f64emu_splits(int64_t m, int64_t n, int sms) {
+  const int64_t tiles = (n + tc64::kBM - 1) / tc64::kBM;
+  const int64_t chunks = (f64emu_pad(m) + tc64::kChunk - 1) / tc64::kChunk;
+  int64_t s = (2 * (int64_t)sms + tiles - 1) / tiles;  // about two waves of one CTA per SM
+  if (s > chunks) s = chunks;
+  const int64_t s_min = (chunks + tc64::kMaxChunksPerSplit - 1) / tc64::kMaxChunksPerSplit;
+  if (s < s_min) s = s_min;
+  if (s < 1) s = 1;
+  // a split holds whole chunks
+  const int64_t per = (chunks + s - 1) / s;
+  return (int)((chunks + per - 1) / per);
+}
+
+cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, void* digits,
+                           cudaStream_t s) {
+  const int64_t mp = f64emu_pad(m);
+  tc64::k_colexp<<<(int)(n < 4096 ? n : 4096), 256, 0, s>>>(A, lda, m, n, colexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (mp * n + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  tc64::k_split_digits<<<(int)blocks, 256, 0, s>>>(A, lda, m, mp, n, colexp, static_cast<__nv_bfloat16*>(digits));
+  return cudaGetLastError();
+}
+
+cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t rows_alloc,
+                         const double* src, int64_t ld_src, void* wdigits, const int32_t* done, cudaStream_t s) {
+  const int64_t ldw = f64emu_pad(m);
+  int64_t blocks = (rows * ((ldw + 3) / 4) + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  tc64::k_omega_digits<<<(int)blocks, 256, 0, s>>>(seed, row0, rows, m, ldw, rows_alloc, src, ld_src,
+                                                  static_cast<__nv_bfloat16*>(wdigits), done);
+  return cudaGetLastError();
+}
+
+cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, int64_t n, const void* wdigits,
+                          int64_t rows, int64_t rows_alloc, double* out, int64_t out_ld, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s) {
+  const int64_t mp = f64emu_pad(m);
+  CUtensorMap ma, mw;
+  if (!tc64::make_map_3d(&ma, digits, mp, n, tc64::kSlices, tc64::kBM, 1)) return cudaErrorInvalidValue;
+  if (!tc64::make_map_3d(&mw, wdigits, mp, rows_alloc, 2, tc64::kBN, 2)) return cudaErrorInvalidValue;
+  const int64_t chunks = (mp + tc64::kChunk - 1) / tc64::kChunk;
+  const int64_t per = (chunks + splits - 1) / splits;
+  const int kchunk = (int)(per * tc64::kChunk);
+  const int nz = (int)((mp + kchunk - 1) / kchunk);
+  if (nz != splits) return cudaErrorInvalidValue;  // the split-K reduction reads exactly `splits` partials
+  const int64_t ytiles = (n + tc64::kBM - 1) / tc64::kBM;
+  if (ytiles > 65535 || splits > 65535) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(tc64::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc64::k_sketch_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((rows + tc64::kBN - 1) / tc64::kBN), (unsigned)ytiles, (unsigned)nz);
+  tc64::k_sketch_f64emu<<<grid, tc64::kThreads, smem, s>>>(ma, mw, colexp, (int)n, (int)rows, (int)mp, kchunk, out,
+                                                           out_ld, zstride, st, done);
+  return cudaGetLastError();
+}
+
+}  // namespace rid

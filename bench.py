@@ -51,6 +51,12 @@ WORKLOADS = {
     "mixed_bf16_tol3e-3": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-3, 64),
     "mixed_bf16_tol3e-2": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-2, 64),
     "small_mixed_bf16": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "bf16", 1e-3, 64),
+    # the same matrix quantised to FP8 E4M3 with power-of-two scales per 128-row block;
+    # E4M3 sketch on the tensor cores (kind::f8f6f4), LU in FP32.  The E4M3 rounding
+    # (about 2.6e-2 relative) is part of the stored matrix: tol 5e-2 sits above it
+    "mixed_fp8": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "fp8", 1e-3, 64),
+    "mixed_fp8_tol5e-2": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "fp8", 5e-2, 64),
+    "small_mixed_fp8": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "fp8", 5e-2, 64),
     # batched: 4096 off-diagonal blocks exp(-|x-y|^2/h^2), h = 0.3, of a k-d tree over 2^20 uniform
     # points in the unit cube (leaves of at most 1024 points, sizes 64..1024), one persistent launch
     "batched_kernel_f64": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f64", 1e-8, 32),
@@ -105,6 +111,12 @@ def make_input(name, device, seed=2310_09417 + 1):
             del blk
         del G1t, G2t
         torch.cuda.synchronize()
+        if dt == "fp8":
+            from paper_2310_09417_gb300 import binding as B
+            A8 = B.quantize_fp8(At.t(), pow2=True)
+            del At
+            torch.cuda.synchronize()
+            return A8
         return At.t()
     s = W.spectrum(kind, n, **kw)
     dtype = torch.float32 if dt == "f32" else torch.float64
@@ -129,6 +141,23 @@ def make_input(name, device, seed=2310_09417 + 1):
         At = W.spectral_matrix_torch(m, n, s, seed, torch.float64, device)
     torch.cuda.synchronize()
     return At.t()  # (m, n) column-major view
+
+
+def host_f64(A):
+    """A (a column-major device tensor or an FP8Matrix) as an FP64 Fortran-order host
+    array of the values the ID works on (FP8: the decoded values times the scales)."""
+    import numpy as np
+    import torch
+    if hasattr(A, "scale"):
+        m = A.shape[0]
+        s = A.scale.repeat_interleave(128, dim=0)[:m]
+        At = (A.data.float() * s).t().contiguous()
+    else:
+        At = A.t().contiguous()
+    out = np.asfortranarray(At.double().cpu().numpy().T)
+    del At
+    torch.cuda.empty_cache()
+    return out
 
 
 class ClockSampler:
@@ -225,7 +254,7 @@ def run_reference(args, rank, world):
         return
     if dev is not None:
         A = make_input(name, dev)
-        A_host = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
+        A_host = host_f64(A)
         del A
     else:  # no GPU: same family, host generation at reduced size
         from paper_2310_09417_gb300 import workloads as W
@@ -298,15 +327,17 @@ def config_dict(name, res):
                 "l2": "inputs larger than L2 (the batch is %s)" % (res if res else "several GB"),
                 "parallelism": "one persistent launch, CTA per problem; replicas across GPUs"}
     spec = {"poly": "s_j = (1+j)^-2", "step": "rank 600 at 1, then 1e-9",
-            "lowrank": "G1 G2 (Gaussian factors, rank %s) + %s N(0,1) noise, stored in BF16"
-                       % (kw.get("rank"), kw.get("noise"))}[kind]
+            "lowrank": "G1 G2 (Gaussian factors, rank %s) + %s N(0,1) noise, stored in %s"
+                       % (kw.get("rank"), kw.get("noise"), "FP8 E4M3" if dt == "fp8" else "BF16")}[kind]
     if name.startswith("small_"):
         spec += " (reduced size for profiling)"
-    el = {"f32": 4, "f64": 8, "f64emu": 8, "bf16": 2}[dt]
+    el = {"f32": 4, "f64": 8, "f64emu": 8, "bf16": 2, "fp8": 1}[dt]
     prec = {"f64": "FP64 sketch, LU and X", "f32": "FP32 sketch, LU and X",
             "f64emu": "FP64 A, LU and X; FP64-accurate sketch on the BF16 tensor cores (8 exact 7-bit digit "
                       "slices of A, Omega on the grid 2^-10 in 2 digits, exact FP32 chunk sums, int64 totals)",
-            "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
+            "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms",
+            "fp8": "FP8 E4M3 A with power-of-two FP32 scales per 128-row block (quantised from the BF16 matrix), "
+                   "E4M3 Omega, tcgen05 kind::f8f6f4 sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
     c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
          "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device"
                                      + (", rounded to the grid 2^-10" if dt == "f64emu" else ""),
@@ -441,7 +472,8 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks):
                     "batch_gb": round(nbytes / 1e9, 2)})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64 (sketch: bf16 digit products, exact sums)" if dt == "f64emu" else dt,
+                "vs_baseline": None, "dtype": {"f64emu": "f64 (sketch: bf16 digit products, exact sums)", "fp8": "fp8 e4m3 (sketch), f32 (LU)",
+                                                "bf16": "bf16 (sketch), f32 (LU)"}.get(dt, dt),
                 "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
                 "result": {"ids_per_s": len(As) * world / (ms * 1e-3), "gflop_per_step": flops / 1e9,
@@ -555,6 +587,16 @@ def main():
         roofline = {"bound": "hbm", "kernel": "k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    elif dt == "fp8":
+        # HBM-bound: per pass A (mn bytes) + its block scales (4 n ceil(m/128)) + one E4M3
+        # Omega block (bm) + the FP32 sketch block written (4nb)
+        nbs = (m + 127) // 128
+        sk_bytes = (1.0 * m * n + 4.0 * nbs * n + 1.0 * b * m + 4.0 * n * b) * res.passes
+        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
+        peak = PEAKS["hbm_gbs"]
+        roofline = {"bound": "hbm", "kernel": "k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + "
+                    "split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     elif dt == "f64emu":
         # HBM-bound at one block per pass (rows = 64: about 120 tensor flop/B against a
         # ridge near 290): per pass the 8 BF16 digit slices of A (16 mn) + both Omega digit
@@ -584,15 +626,29 @@ def main():
     # end to end: pinned host A -> device, ID, J and X back to pinned host
     e2e = None
     if not args.no_e2e:
-        A_host = torch.empty((n, m), dtype=A.dtype, pin_memory=True)
-        A_host.copy_(A.t())
-        A_dev = torch.empty((n, m), dtype=A.dtype, device=dev)
+        is8 = hasattr(A, "scale")
+        if is8:  # the E4M3 bytes (row stride ld) and the block scales travel
+            ldq = A.data.stride(1)
+            A_host = torch.empty((n, ldq), dtype=torch.uint8, pin_memory=True)
+            A_host.copy_(A.data.view(torch.uint8).t().as_strided((n, ldq), (ldq, 1)))
+            S_host = torch.empty(A.scale.t().shape, dtype=torch.float32, pin_memory=True)
+            S_host.copy_(A.scale.t())
+            A_dev = torch.empty((n, ldq), dtype=torch.uint8, device=dev)
+            S_dev = torch.empty(S_host.shape, dtype=torch.float32, device=dev)
+            A_in = B.FP8Matrix(A_dev.view(torch.float8_e4m3fn)[:, :m].t(), S_dev.t())
+        else:
+            A_host = torch.empty((n, m), dtype=A.dtype, pin_memory=True)
+            A_host.copy_(A.t())
+            A_dev = torch.empty((n, m), dtype=A.dtype, device=dev)
+            A_in = A_dev.t()
         X_host = torch.empty((n, kmax), dtype=xdt, pin_memory=True)
         J_host = torch.empty(kmax, dtype=torch.int64, pin_memory=True)
 
         def e2e_step():
             A_dev.copy_(A_host, non_blocking=True)
-            r = B.id_adaptive(A_dev.t(), tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
+            if is8:
+                S_dev.copy_(S_host, non_blocking=True)
+            r = B.id_adaptive(A_in, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
                               workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec)
             kk = r.k
             X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
@@ -610,16 +666,16 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        el = A.element_size()
         xel = torch.empty((), dtype=xdt).element_size()
+        h2d = A_host.numel() * A_host.element_size() + (S_host.numel() * 4 if is8 else 0)
         e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
-               "h2d_bytes_per_step": m * n * el,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": r.k * n * xel + 8 * r.k}
-        del A_host, A_dev, X_host
+        del A_host, A_dev, X_host, A_in
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_host64 = np.asfortranarray(A.t().contiguous().double().cpu().numpy().T)
+        A_host64 = host_f64(A)
         v, sec, threads, desc = cpu_oracle_sample(A_host64, name, seed=seed, rounds=ref_rounds(args, name))
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
         del A_host64
@@ -627,7 +683,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64 (sketch: bf16 digit products, exact sums)" if dt == "f64emu" else dt,
+                "vs_baseline": None, "dtype": {"f64emu": "f64 (sketch: bf16 digit products, exact sums)", "fp8": "fp8 e4m3 (sketch), f32 (LU)",
+                                                "bf16": "bf16 (sketch), f32 (LU)"}.get(dt, dt),
                 "data": "synthetic",
                 "config": config_dict(name, res), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clk.summary(),

@@ -85,8 +85,16 @@ typedef struct {
 } id_matrix;
 
 typedef struct {
-  id_dtype sketch_prec; /* inputs of the sketch GEMM: F64, F32, BF16, FP8_E4M3 */
-  id_dtype lu_prec;     /* Schur complement, LUPP and X: F64 or F32 */
+  /* Precision triples (A->dtype, sketch_prec, lu_prec) built; others return
+     ID_ERR_UNSUPPORTED:
+       F64 / F64 / F64            FP64 throughout (FP64 FMA sketch)
+       F64 / F64_EMU / F64        FP64-accurate sketch on the tensor cores
+       F32 / F32 / F32            FP32 throughout
+       BF16 / BF16 / F32          tensor-core sketch, FP32 LU and X
+       FP8_E4M3 / FP8_E4M3 / F32  tensor-core sketch with block scales, FP32 LU and X
+     ||A||_F and the estimate's sum of squares are FP64 on every path. */
+  id_dtype sketch_prec; /* inputs of the sketch GEMM */
+  id_dtype lu_prec;     /* Schur complement, LUPP and X */
   int64_t block;        /* b, rows of each sketch block (Algorithm 1); default 64 */
   double tol;           /* tau */
   int tol_relative;     /* 1: stop when E <= tol * ||A||_F; 0: E <= tol (Algorithm 1) */
@@ -110,7 +118,21 @@ typedef struct {
      columns); only the number of passes over A changes. */
   const float* predictor;
   int64_t max_pass_rows;  /* rows per pass the predictor may request; 0 = 16 b */
+  /* The condition of L1 (the k x k unit-lower factor on the skeleton rows) and the
+     precision of the solve X^T(J^c,:) = L2 L1^{-1} (Eq. inty):
+       0  no estimate; X as computed in lu_prec;
+       1  compute kappa_1(L1) = ||L1||_1 ||L1^{-1}||_1 into id_result.cond_L1 and,
+          with lu_prec F32, re-solve X in FP64 from the stored LU multipliers when
+          kappa_1(L1) > ID_COND_SWITCH (an FP32 X would keep fewer than half of
+          its digits);
+       2  as 1, and always re-solve in FP64 with lu_prec F32.
+     Modes 1 and 2 add n x k_max multipliers (lu_prec) to the workspace, and with
+     lu_prec F32 the FP64 solve's k_max x k_max and n x k_max FP64 buffers. */
+  int x_solve_f64;
 } id_opts;
+
+/* kappa_1(L1) above which x_solve_f64 = 1 re-solves an FP32 X in FP64 (2^12). */
+#define ID_COND_SWITCH 4096.0
 
 /* Phases reported in id_result.phase_ms / phase_launches. */
 enum {
@@ -141,6 +163,8 @@ typedef struct {
   int64_t phase_launches[ID_NUM_PHASES];
   int32_t status;   /* HOST out: this problem's status (id_batched: per problem; otherwise
                        equal to the return value) */
+  double cond_L1;   /* HOST out (x_solve_f64 != 0): kappa_1(L1) = ||L1||_1 ||L1^{-1}||_1, else 0 */
+  int32_t x_f64;    /* HOST out: 1 if X was re-solved in FP64 */
 } id_result;
 
 /* ---------------------------------------------------------------- entry points */
@@ -199,11 +223,25 @@ int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, voi
                 int64_t ldw, void* ws, size_t ws_bytes, void* stream);
 
 /* Rows [row0, row0+rows) of the Gaussian sketching matrix (row-major, row
-   stride ld >= m, dtype F64 or F32): entry (i, r) is a standard normal from
-   Philox4x64-10 (Salmon et al. 2011) keyed (seed, 0) at counter
-   (r/4, i, 0, 0) and Box-Muller on 53-bit uniforms (Sec. 2.4, Sec. 5.1). */
+   stride ld >= m, dtype F64, F32, BF16 or FP8_E4M3): entry (i, r) is a standard
+   normal from Philox4x64-10 (Salmon et al. 2011) keyed (seed, 0) at counter
+   (r/4, i, 0, 0) and Box-Muller on 53-bit uniforms in FP64 (Sec. 2.4, Sec. 5.1);
+   for BF16 and FP8_E4M3 output Box-Muller runs in FP32 on the leading 24 bits of
+   the same counters.  Rounded to nearest-even in the output type (E4M3
+   saturating at +-448).
+   Synchronises the stream. */
 int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype,
                      void* out, int64_t ld, void* stream);
+
+/* FP8 storage of a matrix for the FP8 sketch: A (F64, F32 or BF16, column-major)
+   -> Q (E4M3 bytes, column-major, ld ldq >= m) and one FP32 scale per 128-row
+   block of each column (block_scale, column-major ceil(m/128) x n, the id_matrix
+   layout).  scale = amax/448 of the block, or with pow2 != 0 the power of two
+   >= amax/448 (a UE8M0-representable scale); a zero block has scale 1, a block
+   holding a NaN a NaN scale.  Q(i,j) = E4M3 of A(i,j)/scale rounded to nearest
+   even, saturating at +-448 (FP64 input divided in FP64, others in FP32).
+   Asynchronous on `stream`.  Returns -1 (A), -2 (Q/ldq), -4 (block_scale). */
+int id_quantize_fp8(const id_matrix* A, void* Q, int64_t ldq, float* block_scale, int pow2, void* stream);
 
 /* The sketch alone (Sec. 2.4; Algorithm 1 line 9): G = (Omega A)^T, n x rows,
    row-major with row stride ldg >= rows (row j holds the sketch of column j).
@@ -211,7 +249,9 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
    Paths: A F64 / sketch F64 (FP64 FMA, G in FP64); A F32 / F32 (FP32 FMA, G in
    FP32); A BF16 / BF16 (tcgen05 tensor cores fed by TMA, FP32 accumulation, G in
    FP32; A->ld and ld_omega multiples of 8, 16-byte aligned bases, else
-   ID_ERR_UNSUPPORTED); A F64 / ID_F64_EMU (omega F64, rounded to the grid 2^-10,
+   ID_ERR_UNSUPPORTED); A FP8_E4M3 / FP8_E4M3 (block scales in A->block_scale,
+   tcgen05 kind::f8f6f4, FP32 accumulation per 128-row block, G in FP32; A->ld
+   and ld_omega multiples of 16); A F64 / ID_F64_EMU (omega F64, rounded to the grid 2^-10,
    then the FP64-accurate digit-sliced product on the tensor cores, G in FP64).
    ws: at least id_sketch_workspace_size bytes, 256-aligned. */
 int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes);

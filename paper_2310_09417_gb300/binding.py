@@ -41,7 +41,8 @@ class IdOpts(C.Structure):
                 ("tol", C.c_double), ("tol_relative", C.c_int), ("k_max", C.c_int64),
                 ("k0", C.c_int64), ("blocks_per_pass", C.c_int64), ("seed", C.c_uint64),
                 ("omega", C.c_void_p), ("ld_omega", C.c_int64), ("omega_rows", C.c_int64),
-                ("profile", C.c_int), ("predictor", C.c_void_p), ("max_pass_rows", C.c_int64)]
+                ("profile", C.c_int), ("predictor", C.c_void_p), ("max_pass_rows", C.c_int64),
+                ("x_solve_f64", C.c_int)]
 
 
 class IdResult(C.Structure):
@@ -50,7 +51,7 @@ class IdResult(C.Structure):
                 ("est_err", C.c_double), ("norm_A", C.c_double), ("rounds", C.c_int32),
                 ("passes", C.c_int32), ("launches", C.c_int64),
                 ("phase_ms", C.c_double * 6), ("phase_launches", C.c_int64 * 6),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("cond_L1", C.c_double), ("x_f64", C.c_int32)]
 
 
 _lib = None
@@ -87,9 +88,19 @@ def load():
         getattr(lib, f).restype = C.c_int
     lib.id_status_string.argtypes = [C.c_int]
     lib.id_status_string.restype = C.c_char_p
+    lib.id_quantize_fp8.argtypes = [P, P, i64, P, C.c_int, P]
+    lib.id_fixed_rank_noalloc.argtypes = [P, i64, i64, P, P, P]
     for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
-              "id_batched", "cur_from_id", "id_gaussian_rows", "id_sketch_workspace_size", "id_sketch"):
+              "id_batched", "cur_from_id", "id_gaussian_rows", "id_sketch_workspace_size", "id_sketch",
+              "id_quantize_fp8", "id_fixed_rank_noalloc"):
         getattr(lib, f).restype = C.c_int
+    # every entry point must have its C signature declared: an undeclared one would
+    # pass 64-bit pointers as C ints
+    protos = header_prototypes()
+    for name, nargs in protos.items():
+        f = getattr(lib, name)
+        if f.argtypes is None or len(f.argtypes) != nargs:
+            raise RuntimeError("binding declares no matching signature for %s (%d arguments)" % (name, nargs))
     _lib = lib
     return lib
 
@@ -100,6 +111,18 @@ def header_functions() -> list[str]:
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
     return re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\([^;{]*\)\s*;", text, flags=re.M)
+
+
+def header_prototypes() -> dict:
+    """{name: number of parameters} of the functions include/randid.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    out = {}
+    for name, params in re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(([^;{]*)\)\s*;", text, flags=re.M):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
 
 
 def status_string(code: int) -> str:
@@ -127,6 +150,8 @@ class IDResult:
     pivots: torch.Tensor | None
     phase_ms: dict
     phase_launches: dict
+    cond_L1: float = 0.0     # kappa_1(L1) when x_solve_f64 was requested
+    x_f64: int = 0           # 1 if X was re-solved in FP64
 
 
 def colmajor(t: torch.Tensor) -> torch.Tensor:
@@ -138,14 +163,72 @@ def colmajor(t: torch.Tensor) -> torch.Tensor:
     return t.t().contiguous().t()
 
 
-def _matrix(A: torch.Tensor) -> IdMatrix:
+class FP8Matrix:
+    """A stored in FP8 E4M3 with one FP32 scale per 128-row block of each column:
+    data (m x n, column-major float8_e4m3fn, ld a multiple of 16), scale
+    (ceil(m/128) x n, column-major float32); entry (i, j) = data[i, j] * scale[i // 128, j]."""
+
+    def __init__(self, data: torch.Tensor, scale: torch.Tensor):
+        self.data, self.scale = data, scale
+
+    shape = property(lambda self: self.data.shape)
+    dtype = property(lambda self: self.data.dtype)
+    device = property(lambda self: self.data.device)
+    is_cuda = property(lambda self: self.data.is_cuda)
+
+    def stride(self, i):
+        return self.data.stride(i)
+
+    def data_ptr(self):
+        return self.data.data_ptr()
+
+    def dim(self):
+        return 2
+
+
+def colmajor_padded(t: torch.Tensor, multiple: int) -> torch.Tensor:
+    """Column-major copy whose leading dimension is rounded up to `multiple`."""
+    m, n = t.shape
+    ld = -(-m // multiple) * multiple
+    if t.element_size() == 1:  # 8-bit floats: move the bytes
+        buf = torch.zeros((n, ld), dtype=torch.uint8, device=t.device)
+        buf[:, :m] = t.view(torch.uint8).t()
+        return buf.view(t.dtype)[:, :m].t()
+    buf = torch.zeros((n, ld), dtype=t.dtype, device=t.device)
+    buf[:, :m] = t.t()
+    return buf[:, :m].t()
+
+
+def quantize_fp8(A: torch.Tensor, pow2: bool = True, stream=None) -> FP8Matrix:
+    """FP8 storage of A (F64/F32/BF16, column-major): E4M3 values and per-128-row
+    block scales (power-of-two scales with pow2, else amax/448)."""
+    m, n = A.shape
+    ldq = -(-m // 16) * 16
+    nbs = -(-m // 128)
+    Q = torch.zeros((n, ldq), dtype=torch.uint8, device=A.device)
+    S = torch.empty((n, nbs), dtype=torch.float32, device=A.device)
+    rc = load().id_quantize_fp8(C.byref(_matrix(A)), Q.data_ptr(), ldq, S.data_ptr(), 1 if pow2 else 0,
+                                _stream(stream))
+    if rc != 0:
+        raise IDError(rc, "id_quantize_fp8")
+    return FP8Matrix(Q.view(torch.float8_e4m3fn)[:, :m].t(), S.t())
+
+
+def _matrix(A) -> IdMatrix:
     if not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
     if A.dim() != 2 or A.stride(0) != 1 or A.stride(1) < A.shape[0]:
         raise ValueError("A must be column-major (stride (1, ld >= m)); use colmajor(A)")
     if A.dtype not in _TORCH_TO_ID:
         raise ValueError("unsupported dtype %s" % A.dtype)
-    return IdMatrix(A.data_ptr(), _TORCH_TO_ID[A.dtype], A.shape[0], A.shape[1], A.stride(1), None)
+    scale = None
+    if isinstance(A, FP8Matrix):
+        sc = A.scale
+        if sc.dtype != torch.float32 or sc.stride(0) != 1 or sc.stride(1) != sc.shape[0] \
+                or sc.shape != (-(-A.shape[0] // 128), A.shape[1]):
+            raise ValueError("FP8 block scales must be a column-major ceil(m/128) x n float32 matrix")
+        scale = sc.data_ptr()
+    return IdMatrix(A.data_ptr(), _TORCH_TO_ID[A.dtype], A.shape[0], A.shape[1], A.stride(1), scale)
 
 
 def _opts(A, *, block, tol, relative, k_max, k0, blocks_per_pass, seed, omega, profile,
@@ -197,18 +280,20 @@ def _result(res: IdResult, J, Xbuf, k, n, status, trace_buf, piv) -> IDResult:
                     passes=res.passes, launches=res.launches, status=status, trace=trace,
                     pivots=None if piv is None else piv[:k],
                     phase_ms={PHASES[i]: res.phase_ms[i] for i in range(6)},
-                    phase_launches={PHASES[i]: int(res.phase_launches[i]) for i in range(6)})
+                    phase_launches={PHASES[i]: int(res.phase_launches[i]) for i in range(6)},
+                    cond_L1=res.cond_L1, x_f64=int(res.x_f64))
 
 
 def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int = 0,
                   omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                   stream=None, workspace: torch.Tensor | None = None,
-                  sketch_prec: int | None = None) -> IDResult:
+                  sketch_prec: int | None = None, x_solve_f64: int = 0) -> IDResult:
     """randLUPP fixed-rank column ID (Sec. 3.1): J (k), X (k x n), estimate from l - k rows.
     sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit slicing."""
     m, n = A.shape
     opts = _opts(A, block=block, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1,
                  seed=seed, omega=omega, profile=profile, sketch_prec=sketch_prec)
+    opts.x_solve_f64 = x_solve_f64
     ws = _workspace(workspace_size(A, opts, l), A.device, workspace)
     J = torch.empty(k, dtype=torch.int64, device=A.device)
     Xbuf = torch.empty((n, k), dtype=torch.float64 if opts.lu_prec == F64 else torch.float32,
@@ -229,7 +314,7 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
                 omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                 trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
                 out: tuple | None = None, predictor: torch.Tensor | None = None,
-                max_pass_rows: int = 0, sketch_prec: int | None = None) -> IDResult:
+                max_pass_rows: int = 0, sketch_prec: int | None = None, x_solve_f64: int = 0) -> IDResult:
     """randLUPPadap column ID (Algorithm 1).  `out` = (J, Xbuf) reuses output buffers
     (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major).  `predictor`:
     FP32 CUDA tensor of id_mlp_param_count() parameters; it sets how many blocks
@@ -241,6 +326,7 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
     opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,
                  blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile,
                  sketch_prec=sketch_prec)
+    opts.x_solve_f64 = x_solve_f64
     if predictor is not None:
         if not predictor.is_cuda or predictor.dtype != torch.float32 or predictor.numel() != mlp_param_count():
             raise ValueError("predictor must be a CUDA float32 tensor of id_mlp_param_count() values")
@@ -271,6 +357,8 @@ def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
                   device="cuda", stream=None) -> torch.Tensor:
     """Rows [row0, row0+rows) of the Philox/Box-Muller sketching matrix (rows x m)."""
     out = torch.empty((rows, m), dtype=dtype, device=device)
+    if dtype not in _TORCH_TO_ID:
+        raise ValueError("unsupported dtype %s" % dtype)
     rc = load().id_gaussian_rows(seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, _TORCH_TO_ID[dtype],
                                  out.data_ptr(), m, _stream(stream))
     if rc != 0:

@@ -13,9 +13,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "randid.h"
 #include "rid_internal.h"
@@ -62,13 +64,19 @@ struct Plan {
   int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
   bool gen_omega = true;
   size_t esz = 0;
-  int path = 0;          // 64, 32 (SIMT), 16 (BF16 tensor-core sketch) or 65 (FP64 by digit slicing)
+  int path = 0;          // 64, 32 (SIMT), 16 (BF16 tensor cores), 8 (FP8 tensor cores), 65 (FP64 by digit slicing)
   int64_t ldw = 0;       // row stride of the generated Omega
   size_t wsz = 0;        // bytes per Omega element
   size_t off_state = 0, off_omega = 0, off_G = 0, off_Gpart = 0, off_S = 0, off_Spart = 0, off_N = 0,
          off_Linv = 0, off_act0 = 0, off_act1 = 0, off_pivmark = 0, off_perm32 = 0, off_piv = 0,
          off_pivorig = 0, off_pivdiag = 0, off_cand_v = 0, off_cand_i = 0, off_cand_rows = 0, off_e2 = 0,
          off_normp = 0, off_trace = 0, off_digits = 0, off_colexp = 0, total = 0;
+  // condition of L1 / FP64 solve for X (opts->x_solve_f64)
+  int64_t ldl = 0;
+  size_t off_L = 0, off_L1 = 0, off_T64 = 0, off_Linv64 = 0, off_iota = 0, off_csum = 0;
+  // path 65: digit slices of N and T(piv, old) for the tensor-core block update
+  size_t off_ndig = 0, off_nexp = 0, off_pdig = 0, off_pexp = 0;
+  bool keep_l = false, f64_solve = false;
 };
 
 // Which (input, sketch, LU) precision triples are built.
@@ -77,6 +85,8 @@ int precision_path(const id_matrix* A, const id_opts* o) {
   if (A->dtype == ID_F32 && o->sketch_prec == ID_F32 && o->lu_prec == ID_F32) return 32;
   // BF16 input: sketch on the tensor cores (FP32 accumulation), LU and X in FP32
   if (A->dtype == ID_BF16 && o->sketch_prec == ID_BF16 && o->lu_prec == ID_F32) return 16;
+  // FP8 input with block scales: E4M3 sketch on the tensor cores, LU and X in FP32
+  if (A->dtype == ID_FP8_E4M3 && o->sketch_prec == ID_FP8_E4M3 && o->lu_prec == ID_F32) return 8;
   // FP64 input: FP64-accurate sketch on the tensor cores, LU and X in FP64
   if (A->dtype == ID_F64 && o->sketch_prec == ID_F64_EMU && o->lu_prec == ID_F64) return 65;
   return 0;
@@ -98,17 +108,25 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   if (path == 16 && o->omega != nullptr &&
       ((o->ld_omega % 8) != 0 || (reinterpret_cast<uintptr_t>(o->omega) % 16) != 0))
     return ID_ERR_UNSUPPORTED;
+  // FP8: block scales required; rows of A and Omega 16-byte aligned for TMA
+  if (path == 8 && A->block_scale == nullptr) return kBadA;
+  if (path == 8 && ((A->ld % 16) != 0 || (reinterpret_cast<uintptr_t>(A->data) % 16) != 0))
+    return ID_ERR_UNSUPPORTED;
+  if (path == 8 && o->omega != nullptr &&
+      ((o->ld_omega % 16) != 0 || (reinterpret_cast<uintptr_t>(o->omega) % 16) != 0))
+    return ID_ERR_UNSUPPORTED;
   const int64_t b = o->block == 0 ? 64 : o->block;
   if (b < 1 || b > kMaxBlock) return kBadOpts;
   if (!(o->tol >= 0.0) || o->k_max < 0 || o->k0 < 0 || o->blocks_per_pass < 0) return kBadOpts;
+  if (o->x_solve_f64 < 0 || o->x_solve_f64 > 2) return kBadOpts;
   p->m = A->m;
   p->n = A->n;
   p->b = b;
   p->sms = num_sms();
   p->esz = o->lu_prec == ID_F64 ? 8 : 4;
   p->path = path;
-  p->ldw = path == 16 ? cdiv(A->m, 8) * 8 : (path == 65 ? f64emu_pad(A->m) : A->m);
-  p->wsz = path == 16 || path == 65 ? 2 : p->esz;
+  p->ldw = path == 16 ? cdiv(A->m, 8) * 8 : (path == 65 ? f64emu_pad(A->m) : (path == 8 ? cdiv(A->m, 16) * 16 : A->m));
+  p->wsz = path == 16 || path == 65 ? 2 : (path == 8 ? 1 : p->esz);
   p->gen_omega = (o->omega == nullptr);
   if (l > 0) {  // fixed rank; sizes do not depend on k (estimate block sized for k = 1)
     if (l > ((int64_t)1 << 20)) return kBadL;
@@ -146,6 +164,7 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // one block (adaptive) or of the l rows (fixed rank)
   const int64_t unit = l > 0 ? l : b;
   const int s1 = path == 16   ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
+                 : path == 8  ? tc_fp8_effective_splits(p->m, tc_fp8_splits(p->m, p->n, unit, p->sms))
                  : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
                               : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
   p->s1_first = p->s1_pass = p->s1_cap = s1;
@@ -153,6 +172,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->nparts = 2 * p->sms;
   p->maxg = p->sms;
   const size_t e = p->esz;
+  // regions that grow with the rank are sized for l >= k in fixed rank (the
+  // workspace query plans with k = 1) and for the rank cap in adaptive runs
+  const int64_t kcap = l > 0 ? l : p->cap;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t at = off;
@@ -168,7 +190,7 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_S = take((size_t)p->n * p->wmax * e);
   p->off_Spart = take((size_t)p->s2max * p->n * p->wmax * e);
   p->off_N = take((size_t)p->n * b * e);
-  p->off_Linv = take((size_t)b * b * e);
+  p->off_Linv = take((size_t)(cdiv(kcap, b) + 1) * b * b * e);  // every block's inverse diagonal block
   p->off_act0 = take((size_t)p->n * 4);
   p->off_act1 = take((size_t)p->n * 4);
   p->off_pivmark = take((size_t)p->n * 4);
@@ -185,6 +207,20 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // path 65: the 8 digit slices of A and its column exponents
   p->off_digits = take(path == 65 ? (size_t)8 * p->ldw * p->n * 2 : 0);
   p->off_colexp = take(path == 65 ? (size_t)p->n * 4 : 0);
+  p->off_ndig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(p->n) : 0);
+  p->off_nexp = take(path == 65 && b <= 64 ? (size_t)p->n * 4 : 0);
+  p->off_pdig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(kcap) : 0);
+  p->off_pexp = take(path == 65 && b <= 64 ? (size_t)kcap * 4 : 0);
+  // x_solve_f64: the multipliers (n x cap), column sums, and for an FP32 LU the FP64 solve's buffers
+  p->keep_l = o->x_solve_f64 != 0;
+  p->f64_solve = p->keep_l && e == 4;
+  p->ldl = kcap;
+  p->off_L = take(p->keep_l ? (size_t)p->n * kcap * e : 0);
+  p->off_csum = take(p->keep_l ? (size_t)2 * kcap * 8 : 0);
+  p->off_L1 = take(p->f64_solve ? (size_t)kcap * kcap * 8 : 0);
+  p->off_T64 = take(p->f64_solve ? (size_t)p->n * kcap * 8 : 0);
+  p->off_Linv64 = take(p->f64_solve ? (size_t)b * b * 8 : 0);
+  p->off_iota = take(p->f64_solve ? (size_t)kcap * 4 : 0);
   p->total = off;
   return ID_OK;
 }
@@ -203,6 +239,7 @@ class Engine {
       : p_(p), o_(*o), out_(out), s_(s) {
     A_ = static_cast<const T*>(A->data);
     Araw_ = A->data;
+    scale_ = A->block_scale;
     lda_ = A->ld;
     unsigned char* w = static_cast<unsigned char*>(ws);
     st_ = reinterpret_cast<DevState*>(w + p.off_state);
@@ -228,6 +265,16 @@ class Engine {
     trace_ = reinterpret_cast<double*>(w + p.off_trace);
     digits_ = w + p.off_digits;
     colexp_ = reinterpret_cast<int32_t*>(w + p.off_colexp);
+    L_ = p.keep_l ? reinterpret_cast<T*>(w + p.off_L) : nullptr;
+    csum_ = reinterpret_cast<double*>(w + p.off_csum);
+    L1_64_ = reinterpret_cast<double*>(w + p.off_L1);
+    T64_ = reinterpret_cast<double*>(w + p.off_T64);
+    Linv64_ = reinterpret_cast<double*>(w + p.off_Linv64);
+    iota_ = reinterpret_cast<int32_t*>(w + p.off_iota);
+    ndig_ = w + p.off_ndig;
+    nexp_ = reinterpret_cast<int32_t*>(w + p.off_nexp);
+    pdig_ = w + p.off_pdig;
+    pexp_ = reinterpret_cast<int32_t*>(w + p.off_pexp);
     X_ = static_cast<T*>(out->X);
     ldx_ = out->ldx;
     done_ = &st_->done;
@@ -368,7 +415,9 @@ class Engine {
   int start() {
     RID_TRY(tbegin(ID_PHASE_OTHER));
     RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
-    if (p_.path == 16)
+    if (p_.path == 8)
+      RID_TRY(cuda(norm2_fp8(p_.m, p_.n, Araw_, lda_, scale_, normp_, p_.nparts, st_, s_)));
+    else if (p_.path == 16)
       RID_TRY(cuda(norm2_partial<__nv_bfloat16>(p_.m, p_.n, static_cast<const __nv_bfloat16*>(Araw_), lda_, normp_,
                                                 p_.nparts, st_, s_)));
     else
@@ -400,12 +449,14 @@ class Engine {
   int splits_for(int64_t /*rows*/) {
     const int64_t unit = p_.l > 0 ? p_.l : p_.b;
     if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
+    if (p_.path == 8) return tc_fp8_effective_splits(p_.m, tc_fp8_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
     return gemm_splits((int)p_.m, choose_splits(p_.n, unit, p_.m, p_.sms, 16));
   }
 
   int sketch(int64_t row0, int64_t rows, int splits) {
     if (p_.path == 16) return sketch_tc(row0, rows, splits);
+    if (p_.path == 8) return sketch_fp8(row0, rows, splits);
     if (p_.path == 65) return sketch_emu(row0, rows, splits);
     const T* Om;
     int64_t ldo;
@@ -452,6 +503,35 @@ class Engine {
     float* out = reinterpret_cast<float*>(splits > 1 ? Gpart_ : G_);
     RID_TRY(cuda(tc_sketch_bf16(Araw_, lda_, p_.m, p_.n, W, ldw, rows, out, p_.ldg, (int64_t)p_.n * p_.ldg, splits,
                                 st_, done_, s_)));
+    if (splits > 1)
+      RID_TRY(cuda(splitk_reduce<float>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
+                                        reinterpret_cast<const float*>(Gpart_), reinterpret_cast<float*>(G_), done_,
+                                        s_)));
+    RID_TRY(tend(splits > 1 ? 2 : 1));
+    ++passes_;
+    return 0;
+  }
+
+  // FP8 operands on the tensor cores: G = (Omega rows [row0, row0+rows)) A in FP32,
+  // A's block scales applied per 128-row block.
+  int sketch_fp8(int64_t row0, int64_t rows, int splits) {
+    const void* W;
+    int64_t ldw;
+    if (p_.gen_omega) {
+      RID_TRY(tbegin(ID_PHASE_OMEGA));
+      RID_TRY(cuda(gaussian_rows<__nv_fp8_e4m3>(o_.seed, row0, rows, p_.m, reinterpret_cast<__nv_fp8_e4m3*>(omega_),
+                                                p_.ldw, done_, s_)));
+      RID_TRY(tend(1));
+      W = omega_;
+      ldw = p_.ldw;
+    } else {
+      W = static_cast<const uint8_t*>(o_.omega) + row0 * o_.ld_omega;
+      ldw = o_.ld_omega;
+    }
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    float* out = reinterpret_cast<float*>(splits > 1 ? Gpart_ : G_);
+    RID_TRY(cuda(tc_sketch_fp8(Araw_, lda_, p_.m, p_.n, scale_, W, ldw, rows, out, p_.ldg, (int64_t)p_.n * p_.ldg,
+                               splits, st_, done_, s_)));
     if (splits > 1)
       RID_TRY(cuda(splitk_reduce<float>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
                                         reinterpret_cast<const float*>(Gpart_), reinterpret_cast<float*>(G_), done_,
@@ -519,15 +599,31 @@ class Engine {
     RID_TRY(tend(1));
     RID_TRY(tbegin(ID_PHASE_UPDATE));
     int nl = 3;
-    RID_TRY(cuda(linv<T>((int)bt, S_, lds, piv_, Linv_, done_, s_)));
-    RID_TRY(cuda(make_n<T>((int)na, (int)bt, S_, lds, Linv_, pivmark_, act_[cur_], N_, X_, ldx_, tb, piv_,
+    T* Linv_t = Linv_ + (tb / p_.b) * p_.b * p_.b;  // kept per block for the condition of L1
+    RID_TRY(cuda(linv<T>((int)bt, S_, lds, piv_, Linv_t, done_, s_)));
+    if (L_ != nullptr) {
+      RID_TRY(cuda(store_l<T>((int)na, (int)bt, S_, lds, piv_, pivmark_, act_[cur_], L_, p_.ldl, tb, done_, s_)));
+      ++nl;
+    }
+    RID_TRY(cuda(make_n<T>((int)na, (int)bt, S_, lds, Linv_t, pivmark_, act_[cur_], N_, X_, ldx_, tb, piv_,
                            pivorig_, done_, s_)));
     if (tb > 0) {
-      Operand<T> a{N_, bt, nullptr, 0};
-      Operand<T> bop{X_, ldx_, pivorig_, 0};
-      EpiArgs<T> ep{X_, ldx_, 0, act_[cur_], pivmark_};
-      RID_TRY(cuda(gemm_gather<T>((int)na, (int)tb, (int)bt, 1, false, a, bop, kEpiSubRows, ep, done_, s_)));
-      ++nl;
+      bool done_tc = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (p_.path == 65 && p_.b <= 64) {  // FP64-accurate on the tensor cores
+          RID_TRY(cuda(update_f64emu((int)na, (int)bt, (int)tb, N_, act_[cur_], pivmark_, pivorig_, X_, ldx_, ndig_,
+                                     nexp_, p_.n, pdig_, pexp_, p_.ldl, p_.sms, st_, done_, s_)));
+          nl += 3;
+          done_tc = true;
+        }
+      }
+      if (!done_tc) {
+        Operand<T> a{N_, bt, nullptr, 0};
+        Operand<T> bop{X_, ldx_, pivorig_, 0};
+        EpiArgs<T> ep{X_, ldx_, 0, act_[cur_], pivmark_};
+        RID_TRY(cuda(gemm_gather<T>((int)na, (int)tb, (int)bt, 1, false, a, bop, kEpiSubRows, ep, done_, s_)));
+        ++nl;
+      }
     }
     RID_TRY(cuda(compact((int)na, (int)bt, act_[cur_], act_[cur_ ^ 1], pivmark_, piv_, out_->J, perm32_, tb,
                          out_->pivots, pivdiag_, done_, s_)));
@@ -536,7 +632,35 @@ class Engine {
     return 0;
   }
 
+  // kappa_1(L1) from the column sums; an FP64 re-solve of X when it is large (FP32 LU).
+  int condition_and_solve(int64_t k) {
+    RID_TRY(tbegin(ID_PHASE_OTHER));
+    RID_TRY(cuda(cond_colsums<T>(k, (int)p_.b, perm32_, L_, p_.ldl, X_, ldx_, Linv_, csum_, csum_ + p_.ldl, s_)));
+    RID_TRY(tend(2));
+    std::vector<double> h((size_t)2 * k);
+    RID_TRY(cuda(cudaMemcpyAsync(h.data(), csum_, k * sizeof(double), cudaMemcpyDeviceToHost, s_)));
+    RID_TRY(cuda(cudaMemcpyAsync(h.data() + k, csum_ + p_.ldl, k * sizeof(double), cudaMemcpyDeviceToHost, s_)));
+    RID_TRY(sync_state());
+    double n1 = 0.0, ninv = 0.0;
+    for (int64_t c = 0; c < k; ++c) {
+      n1 = fmax(n1, h[c]);
+      ninv = fmax(ninv, h[k + c]);
+    }
+    cond_ = n1 * ninv;
+    const int64_t na = p_.n - k;
+    if (p_.f64_solve && na > 0 && (o_.x_solve_f64 == 2 || !(cond_ <= ID_COND_SWITCH))) {
+      RID_TRY(tbegin(ID_PHASE_OTHER));
+      int nl = 0;
+      RID_TRY(cuda(resolve_x_f64<T>(k, (int)p_.b, na, perm32_, act_[cur_], L_, p_.ldl, L1_64_, T64_, Linv64_, iota_,
+                                    X_, ldx_, s_, &nl)));
+      RID_TRY(tend(nl));
+      x_f64_ = 1;
+    }
+    return 0;
+  }
+
   int finish(int64_t k) {
+    if (o_.x_solve_f64 != 0 && k > 0) RID_TRY(condition_and_solve(k));
     RID_TRY(tbegin(ID_PHASE_OTHER));
     RID_TRY(cuda(finalize_x<T>(k, perm32_, X_, ldx_, s_)));
     RID_TRY(tend(1));
@@ -553,6 +677,8 @@ class Engine {
     out_->rounds = h_.rounds;
     out_->passes = passes_;
     out_->launches = launches_;
+    out_->cond_L1 = cond_;
+    out_->x_f64 = x_f64_;
     for (int i = 0; i < kNumPhases; ++i) {
       out_->phase_ms[i] = phase_ms_[i];
       out_->phase_launches[i] = phase_launches_[i];
@@ -571,6 +697,7 @@ class Engine {
   cudaStream_t s_;
   const T* A_;
   const void* Araw_;
+  const float* scale_;  // FP8 block scales
   int64_t lda_;
   DevState* st_;
   DevState h_{};
@@ -579,12 +706,19 @@ class Engine {
   double *pivdiag_, *cand_v_, *e2_, *normp_, *trace_;
   void* digits_;       // path 65: digit slices of A
   int32_t* colexp_;    // path 65: column exponents of A
+  T* L_;               // x_solve_f64: LUPP multipliers by original row (null otherwise)
+  double *csum_, *L1_64_, *T64_, *Linv64_;
+  int32_t* iota_;
+  void *ndig_, *pdig_;   // path 65: digit slices for the tensor-core block update
+  int32_t *nexp_, *pexp_;
   const int32_t* done_;
   int64_t ldx_;
   int cur_ = 0;
   int cur_phase_ = 0;
   bool est_zero_ = false;
   int64_t pred_blocks_ = 0;  // blocks certifying the predicted rank (0: no predictor)
+  double cond_ = 0.0;        // kappa_1(L1) when requested
+  int32_t x_f64_ = 0;
   int64_t predicted_ = 0;
   int32_t passes_ = 0;
   int64_t launches_ = 0;
@@ -613,6 +747,8 @@ void clear_out(id_result* out) {
   out->rounds = 0;
   out->passes = 0;
   out->launches = 0;
+  out->cond_L1 = 0.0;
+  out->x_f64 = 0;
   for (int i = 0; i < ID_NUM_PHASES; ++i) {
     out->phase_ms[i] = 0.0;
     out->phase_launches[i] = 0;
@@ -747,16 +883,34 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
   if (row0 < 0) return -2;
   if (rows < 0) return -3;
   if (m < 1) return -4;
-  if (dtype != ID_F64 && dtype != ID_F32) return -5;
+  if (dtype != ID_F64 && dtype != ID_F32 && dtype != ID_BF16 && dtype != ID_FP8_E4M3) return -5;
   if (out == nullptr) return -6;
   if (ld < m) return -7;
   if (rows == 0) return ID_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = dtype == ID_F64
-                      ? gaussian_rows<double>(seed, row0, rows, m, static_cast<double*>(out), ld, nullptr, s)
-                      : gaussian_rows<float>(seed, row0, rows, m, static_cast<float*>(out), ld, nullptr, s);
+  cudaError_t e;
+  if (dtype == ID_F64)
+    e = gaussian_rows<double>(seed, row0, rows, m, static_cast<double*>(out), ld, nullptr, s);
+  else if (dtype == ID_F32)
+    e = gaussian_rows<float>(seed, row0, rows, m, static_cast<float*>(out), ld, nullptr, s);
+  else if (dtype == ID_BF16)
+    e = gaussian_rows<__nv_bfloat16>(seed, row0, rows, m, static_cast<__nv_bfloat16*>(out), ld, nullptr, s);
+  else
+    e = gaussian_rows<__nv_fp8_e4m3>(seed, row0, rows, m, static_cast<__nv_fp8_e4m3*>(out), ld, nullptr, s);
   if (e != cudaSuccess) return ID_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
+  return ID_OK;
+}
+
+int id_quantize_fp8(const id_matrix* A, void* Q, int64_t ldq, float* block_scale, int pow2, void* stream) {
+  if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m ||
+      (A->dtype != ID_F64 && A->dtype != ID_F32 && A->dtype != ID_BF16))
+    return -1;
+  if (Q == nullptr || ldq < A->m) return -2;
+  if (block_scale == nullptr) return -4;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (quantize_fp8(A->dtype, A->m, A->n, A->data, A->ld, Q, ldq, block_scale, pow2, s) != cudaSuccess)
+    return ID_ERR_CUDA;
   return ID_OK;
 }
 
@@ -771,11 +925,14 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
           : (A->dtype == ID_F64 && prec == ID_F64_EMU) ? 65
           : (A->dtype == ID_F32 && prec == ID_F32)     ? 32
           : (A->dtype == ID_BF16 && prec == ID_BF16)   ? 16
+          : (A->dtype == ID_FP8_E4M3 && prec == ID_FP8_E4M3) ? 8
                                                        : 0;
   if (*path == 0) return ID_ERR_UNSUPPORTED;
   const int sms = num_sms();
+  if (*path == 8 && A->block_scale == nullptr) return -1;
   const size_t esz = *path >= 64 ? 8 : 4;
   *splits = *path == 16   ? tc_sketch_effective_splits(A->m, tc_sketch_splits(A->m, A->n, rows, sms))
+            : *path == 8  ? tc_fp8_effective_splits(A->m, tc_fp8_splits(A->m, A->n, rows, sms))
             : *path == 65 ? f64emu_splits(A->m, A->n, sms)
                           : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
   *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
@@ -816,6 +973,14 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
     e = tc_sketch_bf16(A->data, A->ld, A->m, A->n, omega, ld_omega, rows, out, splits > 1 ? rows : ldg, zs, splits,
                        st, nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
+                                  static_cast<float*>(G), nullptr, s);
+  } else if (path == 8) {
+    if (!tc_fp8_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
+    float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
+    e = tc_sketch_fp8(A->data, A->ld, A->m, A->n, A->block_scale, omega, ld_omega, rows, out, splits > 1 ? rows : ldg,
+                      zs, splits, st, nullptr, s);
     if (e == cudaSuccess && splits > 1)
       e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
                                   static_cast<float*>(G), nullptr, s);

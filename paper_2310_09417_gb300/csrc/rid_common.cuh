@@ -200,6 +200,18 @@ __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, d
   z1 = r * sn;
 }
 
+// The same map in FP32 on the leading 24 bits, for outputs of at most 16 bits
+// (BF16, E4M3), where the FP64 evaluation buys nothing.
+__device__ __forceinline__ void box_muller_f32(uint64_t a, uint64_t b, float& z0, float& z1) {
+  const float u1 = (float)((a >> 40) + 1ull) * 0x1.0p-24f;
+  const float u2 = (float)((b >> 40) + 1ull) * 0x1.0p-24f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
+}
+
 template <typename T>
 __device__ __forceinline__ T tabs(T x) {
   return x < T(0) ? -x : x;

@@ -3,6 +3,8 @@
 // nothing when *done (a device flag) is already set, so rounds enqueued past
 // the stopping point cost only their launch.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,6 +117,24 @@ cudaError_t gather_panel(const T* A, int64_t lda, int64_t m, int64_t n, const in
 template <typename T>
 cudaError_t transpose_w(const T* X, int64_t ldx, int64_t m, int64_t k, T* W, int64_t ldw, cudaStream_t s);
 
+// ---- condition of L1 and the FP64 solve for X (rid_cond.cu).  Blocks are at most
+// kMaxBlockCond wide.  L: the LUPP multipliers by original row (row stride ldl), columns
+// in pivot order; Linv_all: the inverse diagonal blocks, block t at t*b*b (row-major bt x bt).
+constexpr int kMaxBlockCond = 128;
+template <typename T>
+cudaError_t store_l(int na, int bt, const T* S, int64_t lds, const int32_t* piv, const int32_t* pivmark,
+                    const int32_t* act, T* L, int64_t ldl, int64_t tb, const int32_t* done, cudaStream_t s);
+// column sums of |L1| (skipped when L is null) and of |L1^{-1}| (from the pivots' rows of T in X)
+template <typename T>
+cudaError_t cond_colsums(int64_t k, int b, const int32_t* perm, const T* L, int64_t ldl, const T* X, int64_t ldx,
+                         const T* Linv_all, double* colsum_l1, double* colsum_inv, cudaStream_t s);
+// X(0:k, act[r]) = (L2 L1^{-1})(r, :) solved in FP64 from L; L1 (k x k), T64 (na x k),
+// Linv64 (b x b) FP64 and iota (k) are scratch.
+template <typename T>
+cudaError_t resolve_x_f64(int64_t k, int b, int64_t na, const int32_t* perm, const int32_t* act, const T* L,
+                          int64_t ldl, double* L1, double* T64, double* Linv64, int32_t* iota, T* X, int64_t ldx,
+                          cudaStream_t s, int* launches);
+
 // ---- learned rank predictor (rid_mlp.cu): features of the first block's pivots, one
 // forward pass, ceil(2^output) written to st->k_pred.
 cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, int64_t m, int64_t n, double tol,
@@ -133,6 +153,34 @@ cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, i
 cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, int64_t n, const void* wdigits,
                           int64_t rows, int64_t rows_alloc, double* out, int64_t out_ld, int64_t zstride, int splits,
                           DevState* st, const int32_t* done, cudaStream_t s);
+
+// ---- FP8 sketch (rid_tc_fp8.cu): A E4M3 (m x n, column-major, ld multiple of 16) with
+// FP32 scales per 128-row block of each column (column-major ceil(m/128) x n), Omega E4M3
+// (rows x m, row-major, ld multiple of 16); out[z] (n x rows, FP32) holds split z of (W A)^T.
+bool tc_fp8_supported(const void* A, int64_t lda, const void* W, int64_t ldw);
+int tc_fp8_splits(int64_t m, int64_t n, int64_t rows, int sms);
+int tc_fp8_effective_splits(int64_t m, int splits);
+cudaError_t tc_sketch_fp8(const void* A, int64_t lda, int64_t m, int64_t n, const float* scale, const void* W,
+                          int64_t ldw, int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s);
+cudaError_t norm2_fp8(int64_t m, int64_t n, const void* A, int64_t lda, const float* scale, double* part, int nparts,
+                      DevState* st, cudaStream_t s);
+// Q (E4M3) and the block scales of A (dtype ID_F64, ID_F32 or ID_BF16).
+cudaError_t quantize_fp8(int dtype, int64_t m, int64_t n, const void* A, int64_t lda, void* Q, int64_t ldq,
+                         float* scale, int pow2, cudaStream_t s);
+
+// ---- FP64 block update of T on the tensor cores (rid_tc_update.cu): X(act[i], 0:tb) -=
+// N(i, :) X(pivorig[:], 0:tb) for rows with pivmark[i] == 0; N is na x bt (row stride bt,
+// bt <= 64).  ndig / pdig hold update_f64emu_digit_bytes(nrows / prows) bytes, nexp / pexp
+// nrows / prows exponents.
+size_t update_f64emu_digit_bytes(int64_t rows);
+cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t* act, const int32_t* pivmark,
+                          const int32_t* pivorig, double* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
+                          void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
+                          cudaStream_t s);
+
+// ---- the driver's cuTensorMapEncodeTiled (nullptr when unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // ---- tensor-core sketch (rid_tc_sketch.cu): out[z] (n x rows, FP32, row stride out_ld)
 // holds split z of (W A)^T for BF16 A (m x n, column-major) and W (rows x m, row-major).

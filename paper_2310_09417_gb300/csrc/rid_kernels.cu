@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "rid_internal.h"
 
@@ -36,6 +37,12 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
   return __double2bfloat16(x);
 }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 from_double<__nv_fp8_e4m3>(double x) {
+  __nv_fp8_e4m3 q;
+  q.__x = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);  // nearest even, saturating at +-448
+  return q;
+}
 template <typename T>
 __device__ __forceinline__ double to_double(T x) {
   return static_cast<double>(x);
@@ -55,8 +62,16 @@ __global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64
     uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + i), x2 = 0, x3 = 0;
     philox4x64_10(x0, x1, x2, x3, seed, 0ull);
     double z[4];
-    box_muller(x0, x1, z[0], z[1]);
-    box_muller(x2, x3, z[2], z[3]);
+    if constexpr (sizeof(T) <= 2) {  // BF16 / E4M3 output: Box-Muller in FP32
+      float f[4];
+      box_muller_f32(x0, x1, f[0], f[1]);
+      box_muller_f32(x2, x3, f[2], f[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) z[j] = f[j];
+    } else {
+      box_muller(x0, x1, z[0], z[1]);
+      box_muller(x2, x3, z[2], z[3]);
+    }
     T* o = out + i * ld + 4 * q;
     const int64_t lim = m - 4 * q;
 #pragma unroll
@@ -734,6 +749,8 @@ cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, 
 RID_INST(double)
 RID_INST(float)
 template cudaError_t gaussian_rows<__nv_bfloat16>(uint64_t, int64_t, int64_t, int64_t, __nv_bfloat16*, int64_t,
+                                                  const int32_t*, cudaStream_t);
+template cudaError_t gaussian_rows<__nv_fp8_e4m3>(uint64_t, int64_t, int64_t, int64_t, __nv_fp8_e4m3*, int64_t,
                                                   const int32_t*, cudaStream_t);
 template cudaError_t norm2_partial<__nv_bfloat16>(int64_t, int64_t, const __nv_bfloat16*, int64_t, double*, int,
                                                   DevState*, cudaStream_t);

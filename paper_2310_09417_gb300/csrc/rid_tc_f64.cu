@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include "rid_internal.h"
+#include "rid_tc_common.cuh"
 
 namespace rid {
 namespace tc64 {
@@ -49,102 +50,8 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxChunksPerSplit = 1 << 18;  // int64 accumulators: 2^18 * 2^44 < 2^63
 constexpr double kQMax = 8127.0;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up (and flags kErrTimeout) after kWaitLimitNs, or at once
-// when another thread already flagged a timeout.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  uint32_t spins = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if ((++spins & 255u) == 0u) {
-      if (ld_acquire_u32(&st->err) & kErrTimeout) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
-        atomicOr(&st->err, kErrTimeout);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-// Wait for copies or MMAs still in flight before the CTA exits, even after an
-// error was flagged (their writes must land first); bounded by its own limit.
-__device__ __noinline__ void mbar_wait_drain(uint64_t* bar, uint32_t parity) {
-  const uint64_t t0 = globaltimer_ns();
-  uint32_t spins = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) return;
-  }
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major tile with 128-byte rows, 128-byte
-// swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
-  const uint64_t a = smem_u32(p);
-  uint64_t d = (a >> 4) & 0x3FFFull;
-  d |= 1ull << 16;
-  d |= (1024ull >> 4) << 32;
-  d |= 1ull << 46;
-  d |= 2ull << 61;
-  return d;
-}
-// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tcx;
+
 // acc += v * 2^sh, exact (v an integer-valued float below 2^23 in magnitude)
 template <int SH>
 __device__ __forceinline__ void add_scaled(long long& acc, float v) {
@@ -192,14 +99,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.free_[g], kEpiWarps);
     }
     mbar_init(&sm.drain, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                 "r"(512)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -322,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -404,22 +306,9 @@ __global__ void k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_
 }
 
 // ------------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (fn == nullptr) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t planes, int box_rows,
                  int box_planes) {
-  auto fn = encode_fn();
+  auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
   cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * outer * 2};
@@ -434,17 +323,29 @@ bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t oute
 
 int64_t f64emu_pad(int64_t m) { return (m + 7) / 8 * 8; }
 
+// Split count of the K range.  One CTA per SM holds a (column tile, split); its
+// time is about its chunks (+ a fixed cost), so the launch takes
+// waves x (chunks per split + c0).  The count minimising that is taken; it depends
+// on (m, n) only, never on how many Omega rows a pass holds.
 int f64emu_splits(int64_t m, int64_t n, int sms) {
   const int64_t tiles = (n + tc64::kBM - 1) / tc64::kBM;
   const int64_t chunks = (f64emu_pad(m) + tc64::kChunk - 1) / tc64::kChunk;
-  int64_t s = (2 * (int64_t)sms + tiles - 1) / tiles;  // about two waves of one CTA per SM
-  if (s > chunks) s = chunks;
   const int64_t s_min = (chunks + tc64::kMaxChunksPerSplit - 1) / tc64::kMaxChunksPerSplit;
-  if (s < s_min) s = s_min;
-  if (s < 1) s = 1;
-  // a split holds whole chunks
-  const int64_t per = (chunks + s - 1) / s;
-  return (int)((chunks + per - 1) / per);
+  const int64_t s_max = chunks < 64 ? chunks : 64;
+  int best = 1;
+  double best_t = 1e300;
+  for (int64_t s = 1; s <= (s_max > s_min ? s_max : s_min); ++s) {
+    const int64_t per = (chunks + s - 1) / s;
+    const int64_t eff = (chunks + per - 1) / per;  // splits of whole chunks actually used
+    if (eff < s_min || eff != s) continue;
+    const int64_t waves = (tiles * eff + sms - 1) / sms;
+    const double t = (double)waves * ((double)per + 0.15) + 0.01 * (double)eff;
+    if (t < best_t) {
+      best_t = t;
+      best = (int)eff;
+    }
+  }
+  return best;
 }
 
 cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, void* digits,

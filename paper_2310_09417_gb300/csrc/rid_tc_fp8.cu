@@ -1,0 +1,325 @@
+// rid_tc_fp8.cu -- the sketch Y = Omega A with A stored in FP8 E4M3 and one FP32
+// scale per 128-row block of each column (mixed-precision sketch, Sec. 2.4 with
+// the low-precision storage of the mixed-precision variant).
+//
+// A (m x n, column-major, E4M3) and Omega (rows x m, row-major, E4M3) are K-major
+// (K = m) and go through TMA into 128-byte-swizzled shared memory: one stage is
+// one 128-row scale block (128 E4M3 = one swizzle row).  tcgen05.mma kind::f8f6f4
+// (E4M3 x E4M3, exact products, FP32 accumulation) sums one block into one of
+// kAcc tensor-memory accumulators; the epilogue warps multiply each block sum by
+// its column's scale and add it to FP32 registers, while the MMAs of the next
+// blocks run into the other accumulators.
+//
+//   warp 0    one lane issues the TMA loads
+//   warp 1    allocates tensor memory; one lane issues the MMAs
+//   warps 2-5 scaled accumulation and the FP32 rows of G
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "randid.h"
+#include "rid_internal.h"
+#include "rid_tc_common.cuh"
+
+namespace rid {
+namespace tc8 {
+
+using namespace tcx;
+
+constexpr int kBM = 128;       // columns of A per tile (MMA M)
+constexpr int kBN = 64;        // rows of Omega per tile (MMA N)
+constexpr int kBK = 128;       // K per stage = one scale block
+constexpr int kStages = 6;
+constexpr int kAcc = 4;        // accumulators of kBN columns in tensor memory
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = kAcc * kBN;
+
+struct Smem {
+  alignas(1024) uint8_t a[kStages][kBM * kBK];  // 16 KB per stage
+  alignas(1024) uint8_t w[kStages][kBN * kBK];  // 8 KB per stage
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[kAcc];   // the MMAs of a block landed in accumulator a
+  uint64_t acc_empty[kAcc];  // the epilogue has read accumulator a
+  uint64_t drain;
+  uint32_t tmem_base;
+};
+
+// Grid: x = tiles of A's columns, y = tiles of Omega rows, z = K splits of kchunk
+// (a multiple of kBK).  scale: column-major nbs x n block scales.  out: FP32
+// partial (n x rows, row stride out_ld) of split blockIdx.z.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sketch_tc_fp8(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+                    const float* __restrict__ scale, int64_t nbs, int n, int rows, int K, int kchunk,
+                    float* __restrict__ out, int64_t out_ld, int64_t zstride, DevState* st, const int32_t* done) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int n0 = blockIdx.y * kBN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nkb = (kend - kbeg + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int a = 0; a < kAcc; ++a) {
+      mbar_init(&sm.acc_full[a], 1);
+      mbar_init(&sm.acc_empty[a], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&sm.drain, 1);
+    mbar_init_fence();
+  }
+  if (warp == 1) tmem_alloc(&sm.tmem_base, kTmemCols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) + 1) & 1, st)) break;
+      mbar_expect_tx(&sm.full[s], (kBM + kBN) * kBK);
+      const int k0 = kbeg + kb * kBK;
+      tma_load_2d(sm.a[s], &map_a, &sm.full[s], k0, m0);
+      tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);
+      issued = kb + 1;
+    }
+    for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
+      mbar_wait_drain(&sm.full[kb % kStages], (kb / kStages) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: block kb -> accumulator kb % kAcc
+    constexpr uint32_t idesc = idesc_e4m3(kBM, kBN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages, a = kb % kAcc;
+      if (kb >= kAcc && !mbar_wait(&sm.acc_empty[a], ((kb / kAcc) + 1) & 1, st)) break;
+      if (!mbar_wait(&sm.full[s], (kb / kStages) & 1, st)) break;
+      fence_after_sync();
+      const uint64_t da = desc_sw128(sm.a[s]);
+      const uint64_t dw = desc_sw128(sm.w[s]);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 32; ++kk)  // 32 E4M3 = 32 bytes per MMA
+        mma_e4m3(tmem + a * kBN, da + 2 * kk, dw + 2 * kk, idesc, kk != 0);
+      mma_commit(&sm.empty[s]);
+      mma_commit(&sm.acc_full[a]);
+    }
+    mma_commit(&sm.drain);  // every MMA issued completes before tensor memory is freed
+    mbar_wait_drain(&sm.drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: scaled FP32 accumulation of the block sums
+    const int quarter = warp & 3;  // warps 2..5 own lane quarters 2,3,0,1
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    const float* sc = scale + static_cast<int64_t>(row < n ? row : 0) * nbs + kbeg / kBK;
+    float acc[kBN];
+#pragma unroll
+    for (int c = 0; c < kBN; ++c) acc[c] = 0.f;
+    bool ok = true;
+    float s_next = __ldg(sc);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int a = kb % kAcc;
+      const float s_kb = s_next;
+      if (kb + 1 < nkb) s_next = __ldg(sc + kb + 1);
+      if (!mbar_wait(&sm.acc_full[a], (kb / kAcc) & 1, st)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+#pragma unroll
+      for (int cb = 0; cb < kBN; cb += 16) {
+        float v[16];
+        tmem_ld16(lane_base + a * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[cb + i] = fmaf(v[i], s_kb, acc[cb + i]);
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
+    }
+    if (ok && row < n) {
+      float* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld + n0;
+      const int lim = rows - n0;
+#pragma unroll
+      for (int c = 0; c < kBN; ++c)
+        if (c < lim) o[c] = acc[c];
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------------ ||A||_F^2 and finiteness
+// One block per column at a time: sum of (fp8(i,j) * scale(i/128, j))^2 in FP64.
+__global__ void k_norm2_fp8(int64_t m, int64_t n, const uint8_t* __restrict__ A, int64_t lda,
+                            const float* __restrict__ scale, int64_t nbs, double* part, DevState* st) {
+  double acc = 0.0;
+  bool finite = true;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const uint8_t* a = A + j * lda;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+      __nv_fp8_e4m3 q;
+      q.__x = a[i];
+      const double s = (double)scale[j * nbs + i / kBK];
+      const double v = (double)static_cast<float>(q) * s;
+      finite = finite && isfinite(v);
+      acc += v * v;
+    }
+  }
+  if (!finite) atomicOr(&st->err, kErrNonFinite);
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ quantisation
+template <typename T>
+__device__ __forceinline__ float as_float(T x) {
+  return static_cast<float>(x);
+}
+template <>
+__device__ __forceinline__ float as_float<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+// One warp per (128-row block, column): amax -> scale -> E4M3 (round to nearest
+// even, saturating at +-448).  FP64 input is divided in FP64, FP32/BF16 in FP32.
+template <typename T>
+__global__ void k_quantize_fp8(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda, uint8_t* __restrict__ Q,
+                               int64_t ldq, float* __restrict__ scale, int64_t nbs, int pow2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t blk = wid; blk < nbs * n; blk += nw) {
+    const int64_t j = blk / nbs, kb = blk - j * nbs;
+    const int64_t i0 = kb * kBK, i1 = min(m, i0 + kBK);
+    const T* a = A + j * lda;
+    float amax = 0.f;
+    bool nan_seen = false;
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+      const float v = as_float(a[i]);
+      nan_seen = nan_seen || isnan(v);
+      amax = fmaxf(amax, fabsf(v));
+    }
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    nan_seen = __any_sync(0xffffffffu, nan_seen);
+    float s = 1.f;
+    if (nan_seen) {
+      s = __int_as_float(0x7fc00000);  // a NaN scale marks the block non-finite
+    } else if (amax > 0.f) {
+      s = amax / 448.f;
+      if (pow2) {  // the power of two >= amax / 448
+        int e;
+        const float f = frexpf(s, &e);  // s = f 2^e, 0.5 <= f < 1
+        s = ldexpf(1.f, f == 0.5f ? e - 1 : e);
+      }
+    }
+    if (lane == 0) scale[j * nbs + kb] = s;
+    uint8_t* q = Q + j * ldq;
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+      __nv_fp8_e4m3 v;
+      if constexpr (sizeof(T) == 8)
+        v.__x = __nv_cvt_double_to_fp8(static_cast<double>(a[i]) / static_cast<double>(s), __NV_SATFINITE, __NV_E4M3);
+      else
+        v.__x = __nv_cvt_float_to_fp8(as_float(a[i]) / s, __NV_SATFINITE, __NV_E4M3);
+      q[i] = v.__x;
+    }
+  }
+}
+
+bool make_map_u8(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld, int box_rows) {
+  auto fn = tensor_map_encoder();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc8
+
+bool tc_fp8_supported(const void* A, int64_t lda, const void* W, int64_t ldw) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(A), w = reinterpret_cast<uintptr_t>(W);
+  return (a % 16) == 0 && (w % 16) == 0 && (lda % 16) == 0 && (ldw % 16) == 0 && tensor_map_encoder() != nullptr;
+}
+
+int tc_fp8_splits(int64_t m, int64_t n, int64_t rows, int sms) {
+  const int64_t tiles = ((n + tc8::kBM - 1) / tc8::kBM) * ((rows + tc8::kBN - 1) / tc8::kBN);
+  int64_t s = (8 * (int64_t)sms + tiles - 1) / tiles;           // about eight waves of one CTA per SM
+  const int64_t kmax = (m + 8 * tc8::kBK - 1) / (8 * tc8::kBK);  // >= 8 K-stages per CTA
+  if (s > kmax) s = kmax;
+  if (s > 32) s = 32;
+  return (int)(s < 1 ? 1 : s);
+}
+
+int tc_fp8_effective_splits(int64_t m, int splits) {
+  int64_t kchunk = (m + splits - 1) / splits;
+  kchunk = (kchunk + tc8::kBK - 1) / tc8::kBK * tc8::kBK;
+  return (int)((m + kchunk - 1) / kchunk);
+}
+
+cudaError_t tc_sketch_fp8(const void* A, int64_t lda, int64_t m, int64_t n, const float* scale, const void* W,
+                          int64_t ldw, int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s) {
+  CUtensorMap ma, mw;
+  if (!tc8::make_map_u8(&ma, A, m, n, lda, tc8::kBM)) return cudaErrorInvalidValue;
+  if (!tc8::make_map_u8(&mw, W, m, rows, ldw, tc8::kBN)) return cudaErrorInvalidValue;
+  int64_t kchunk = (m + splits - 1) / splits;
+  kchunk = (kchunk + tc8::kBK - 1) / tc8::kBK * tc8::kBK;
+  const int nz = (int)((m + kchunk - 1) / kchunk);
+  if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
+  const int64_t nbs = (m + tc8::kBK - 1) / tc8::kBK;
+  const size_t smem = sizeof(tc8::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc8::k_sketch_tc_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((n + tc8::kBM - 1) / tc8::kBM), (unsigned)((rows + tc8::kBN - 1) / tc8::kBN), (unsigned)nz);
+  tc8::k_sketch_tc_fp8<<<grid, tc8::kThreads, smem, s>>>(ma, mw, scale, nbs, (int)n, (int)rows, (int)m, (int)kchunk,
+                                                         out, out_ld, zstride, st, done);
+  return cudaGetLastError();
+}
+
+cudaError_t norm2_fp8(int64_t m, int64_t n, const void* A, int64_t lda, const float* scale, double* part, int nparts,
+                      DevState* st, cudaStream_t s) {
+  const int64_t nbs = (m + tc8::kBK - 1) / tc8::kBK;
+  tc8::k_norm2_fp8<<<nparts, 256, 0, s>>>(m, n, static_cast<const uint8_t*>(A), lda, scale, nbs, part, st);
+  return cudaGetLastError();
+}
+
+cudaError_t quantize_fp8(int dtype, int64_t m, int64_t n, const void* A, int64_t lda, void* Q, int64_t ldq,
+                         float* scale, int pow2, cudaStream_t s) {
+  const int64_t nbs = (m + tc8::kBK - 1) / tc8::kBK;
+  int64_t blocks = (nbs * n * 32 + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  uint8_t* q = static_cast<uint8_t*>(Q);
+  if (dtype == ID_F64)
+    tc8::k_quantize_fp8<double><<<(int)blocks, 256, 0, s>>>(m, n, static_cast<const double*>(A), lda, q, ldq, scale,
+                                                           nbs, pow2);
+  else if (dtype == ID_F32)
+    tc8::k_quantize_fp8<float><<<(int)blocks, 256, 0, s>>>(m, n, static_cast<const float*>(A), lda, q, ldq, scale,
+                                                          nbs, pow2);
+  else
+    tc8::k_quantize_fp8<__nv_bfloat16><<<(int)blocks, 256, 0, s>>>(m, n, static_cast<const __nv_bfloat16*>(A), lda,
+                                                                   q, ldq, scale, nbs, pow2);
+  return cudaGetLastError();
+}
+
+}  // namespace rid

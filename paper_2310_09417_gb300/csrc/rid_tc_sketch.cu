@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "rid_internal.h"
+#include "rid_tc_common.cuh"
 
 namespace rid {
 
@@ -29,95 +30,7 @@ constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle r
 constexpr int kStages = 4;
 constexpr int kThreads = 192;   // 6 warps
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity; false on timeout (kErrTimeout set).
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevState* st) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  uint32_t spins = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if ((++spins & 255u) == 0u) {
-      if (ld_acquire_u32(&st->err) & kErrTimeout) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
-        atomicOr(&st->err, kErrTimeout);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row x 128-byte atoms
-// stacked 1024 bytes apart (stride byte offset), descriptor version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
-  const uint64_t a = smem_u32(p);
-  uint64_t d = (a >> 4) & 0x3FFFull;  // start address
-  d |= 1ull << 16;                    // leading byte offset (unused for swizzled K-major)
-  d |= (1024ull >> 4) << 32;          // stride byte offset
-  d |= 1ull << 46;                    // version
-  d |= 2ull << 61;                    // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tcx;
 
 template <int BN>
 struct Smem {
@@ -183,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // copies still in flight must land before the CTA can leave
     for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
-      if (!mbar_wait(&sm.full[kb % kStages], (kb / kStages) & 1, st)) break;
+      mbar_wait_drain(&sm.full[kb % kStages], (kb / kStages) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
@@ -205,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
       sm.abort = 1;
       mma_commit(&sm.drain);  // wait for the MMAs already issued before tensor memory is freed
-      mbar_wait(&sm.drain, 0, st);
+      mbar_wait_drain(&sm.drain, 0);
       mma_commit(&sm.accum);  // release the epilogue
     }
   } else if (warp >= 2) {
@@ -236,8 +149,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+}  // namespace tc
+
 // ------------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+
+// The driver's cuTensorMapEncodeTiled, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (fn == nullptr) {
     void* p = nullptr;
@@ -250,10 +167,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+namespace tc {
+
 // 2-D BF16 tensor map over a K-major matrix: `outer` rows of `inner` contiguous
 // elements, row stride `ld` elements; box = 64 (K) x box_rows, 128-byte swizzle.
 bool make_map_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld, int box_rows) {
-  auto fn = encode_fn();
+  auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
@@ -274,7 +193,7 @@ size_t smem_bytes() {
 
 bool tc_sketch_supported(const void* A, int64_t lda, const void* W, int64_t ldw) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(A), w = reinterpret_cast<uintptr_t>(W);
-  return (a % 16) == 0 && (w % 16) == 0 && (lda % 8) == 0 && (ldw % 8) == 0 && tc::encode_fn() != nullptr;
+  return (a % 16) == 0 && (w % 16) == 0 && (lda % 8) == 0 && (ldw % 8) == 0 && tensor_map_encoder() != nullptr;
 }
 
 int tc_sketch_splits(int64_t m, int64_t n, int64_t rows, int sms) {

@@ -1,0 +1,316 @@
+// rid_tc_update.cu -- the FP64 block update of the interpolation coefficients,
+// T(rest, old) -= N T(piv, old) (re-blocking, Alg. 1 lines 14-17, in the
+// T = L2 L1^{-1} form), on the BF16 tensor cores by exact digit slicing.
+//
+// K = bt <= 64.  Each row i of N gets an exponent e_i (max_q |N(i,q)| < 2^e_i) and
+// each column c of P = T(piv, old) an exponent f_c (max_q |P(q,c)| < 2^f_c).
+// N(i,:) / 2^(e_i+1) and P(:,c) / 2^(f_c+1) lie in (-1/2, 1/2) and are written as
+// seven balanced 8-bit digits (|d| <= 128, exact in BF16, 56 bits).  The digit
+// products of equal weight 2^(-8(g+2)), g = s + t <= 6, share FP32 group g in
+// tensor memory (7 groups x 64 columns); a group sums at most 7 pairs x 64 terms
+// of magnitude <= 2^14 (< 2^23): exact.  The epilogue folds the groups into two
+// int64 values, scales by 2^(e_i + f_c + 2 - 32) and subtracts from T in FP64.
+// Dropped pairs (g >= 7) and digit remainders bound each entry's error by about
+// 2^-46 max_q|N(i,q)| max_q|P(q,c)| -- the order of an FP64 dot product of
+// length 64 (64 u).
+//
+//   warp 0    TMA: the row tile's digits of N once, then P's digits per column
+//             tile (double-buffered)
+//   warp 1    tensor memory; 28 x 4 MMAs (M = 128, N = 64, K = 16) per tile
+//   warps 2-5 epilogue: one row each lane, 16 columns at a time
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rid_internal.h"
+#include "rid_tc_common.cuh"
+
+namespace rid {
+namespace tcu {
+
+using namespace tcx;
+
+constexpr int kBM = 128;    // rows of T per tile
+constexpr int kBN = 64;     // columns of T per tile
+constexpr int kK = 64;      // padded K (one 128-byte swizzle row of BF16)
+constexpr int kD = 7;       // digits per operand
+constexpr int kThreads = 192;
+
+struct Smem {
+  alignas(1024) __nv_bfloat16 n[kD][kBM * kK];     // 7 x 16 KB
+  alignas(1024) __nv_bfloat16 p[2][kD][kBN * kK];  // 2 x 7 x 8 KB
+  uint64_t n_full;
+  uint64_t p_full[2];
+  uint64_t p_empty[2];
+  uint64_t t_full;   // a tile's MMAs completed
+  uint64_t t_empty;  // the epilogue read the accumulators
+  uint64_t drain;
+  uint32_t tmem_base;
+};
+
+static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_update_f64emu exceeds 227 KB");
+
+// acc += v * 2^SH, exact (v an integer-valued float below 2^23 in magnitude)
+template <int SH>
+__device__ __forceinline__ void add_scaled(long long& acc, float v) {
+  const int iv = __float2int_rn(v);
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_update_f64emu(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_p, int na,
+                    int tb, const int32_t* __restrict__ nexp, const int32_t* __restrict__ pexp,
+                    const int32_t* __restrict__ act, const int32_t* __restrict__ pivmark, double* __restrict__ X,
+                    int64_t ldx, DevState* st, const int32_t* done) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int ntiles = (tb + kBN - 1) / kBN;
+  // column tiles of this CTA: blockIdx.y, blockIdx.y + gridDim.y, ...
+  const int my = blockIdx.y < ntiles ? (ntiles - 1 - blockIdx.y) / gridDim.y + 1 : 0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.n_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.p_full[b], 1);
+      mbar_init(&sm.p_empty[b], 1);
+    }
+    mbar_init(&sm.t_full, 1);
+    mbar_init(&sm.t_empty, 4);
+    mbar_init(&sm.drain, 1);
+    mbar_init_fence();
+  }
+  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    if (my > 0) {
+      mbar_expect_tx(&sm.n_full, kD * kBM * kK * 2);
+      for (int s = 0; s < kD; ++s) tma_load_3d(sm.n[s], &map_n, &sm.n_full, 0, m0, s);
+    }
+    for (int u = 0; u < my; ++u) {
+      const int b = u & 1;
+      if (u >= 2 && !mbar_wait(&sm.p_empty[b], ((u >> 1) + 1) & 1, st)) break;
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
+      mbar_expect_tx(&sm.p_full[b], kD * kBN * kK * 2);
+      for (int t = 0; t < kD; ++t) tma_load_3d(sm.p[b][t], &map_p, &sm.p_full[b], 0, c0, t);
+      issued = u + 1;
+    }
+    if (my > 0) mbar_wait_drain(&sm.n_full, 0);
+    for (int u = issued - 2 < 0 ? 0 : issued - 2; u < issued; ++u) mbar_wait_drain(&sm.p_full[u & 1], (u >> 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
+    bool ok = my == 0 || mbar_wait(&sm.n_full, 0, st);
+    fence_after_sync();
+    for (int u = 0; u < my && ok; ++u) {
+      const int b = u & 1;
+      if (u > 0 && !mbar_wait(&sm.t_empty, (u - 1) & 1, st)) break;
+      if (!mbar_wait(&sm.p_full[b], (u >> 1) & 1, st)) break;
+      fence_after_sync();
+#pragma unroll 1
+      for (int g = 0; g < kD; ++g) {
+#pragma unroll 1
+        for (int s = 0; s <= g; ++s) {
+          const uint64_t da = desc_sw128(sm.n[s]);
+          const uint64_t db = desc_sw128(sm.p[b][g - s]);
+#pragma unroll
+          for (int kk = 0; kk < kK / 16; ++kk)
+            mma_bf16(tmem + g * kBN, da + 2 * kk, db + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&sm.p_empty[b]);
+      mma_commit(&sm.t_full);
+    }
+    mma_commit(&sm.drain);
+    mbar_wait_drain(&sm.drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int quarter = warp & 3;
+    const int r = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    const bool live = r < na && pivmark[r] == 0;
+    double* xrow = live ? X + (int64_t)act[r] * ldx : nullptr;
+    const int er = live ? nexp[r] : 0;
+    for (int u = 0; u < my; ++u) {
+      if (!mbar_wait(&sm.t_full, u & 1, st)) break;
+      fence_after_sync();
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
+#pragma unroll 1
+      for (int cb = 0; cb < kBN; cb += 16) {
+        long long hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+        float v[16];
+        tmem_ld16(lane_base + 0 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<16>(hi[i], v[i]);
+        tmem_ld16(lane_base + 1 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<8>(hi[i], v[i]);
+        tmem_ld16(lane_base + 2 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<0>(hi[i], v[i]);
+        tmem_ld16(lane_base + 3 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<24>(lo[i], v[i]);
+        tmem_ld16(lane_base + 4 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<16>(lo[i], v[i]);
+        tmem_ld16(lane_base + 5 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<8>(lo[i], v[i]);
+        tmem_ld16(lane_base + 6 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<0>(lo[i], v[i]);
+        if (live) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int c = c0 + cb + i;
+            if (c < tb) {
+              const double val = fma((double)lo[i], 0x1p-32, (double)hi[i]);
+              xrow[c] -= ldexp(val, er + pexp[c] + 2 - 32);
+            }
+          }
+        }
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.t_empty);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ------------------------------------------------------------------ digit slicing
+__device__ __forceinline__ int exp_above(double mx) {  // e with mx < 2^e (0 for 0)
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  return e;
+}
+
+// N (na x bt, row stride bt): one warp per row; digits D[s][i][q] (q < 64, zero-padded).
+__global__ void k_slice_n(int na, int bt, const double* __restrict__ N, __nv_bfloat16* __restrict__ D,
+                          int32_t* __restrict__ nexp, int64_t plane, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < na; i += nw) {
+    const double a0 = lane < bt ? N[i * bt + lane] : 0.0;
+    const double a1 = lane + 32 < bt ? N[i * bt + lane + 32] : 0.0;
+    double mx = fmax(fabs(a0), fabs(a1));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const int e = exp_above(mx);
+    if (lane == 0) nexp[i] = e;
+    double x0 = ldexp(a0, -(e + 1)), x1 = ldexp(a1, -(e + 1));
+#pragma unroll
+    for (int s = 0; s < kD; ++s) {
+      const double t0 = x0 * 256.0, t1 = x1 * 256.0;  // exact
+      const double d0 = rint(t0), d1 = rint(t1);      // |d| <= 128
+      x0 = t0 - d0;
+      x1 = t1 - d1;
+      D[s * plane + i * kK + lane] = __double2bfloat16(d0);
+      D[s * plane + i * kK + lane + 32] = __double2bfloat16(d1);
+    }
+  }
+}
+
+// P(q, c) = X(pivorig[q] row, c) for q < bt, c < tb: per column c (one warp), digits
+// D[t][c][q] (q < 64, zero-padded).
+__global__ void k_slice_p(int bt, int tb, const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ prow,
+                          __nv_bfloat16* __restrict__ D, int32_t* __restrict__ pexp, int64_t plane,
+                          const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = w0; c < tb; c += nw) {
+    const double a0 = lane < bt ? X[(int64_t)prow[lane] * ldx + c] : 0.0;
+    const double a1 = lane + 32 < bt ? X[(int64_t)prow[lane + 32] * ldx + c] : 0.0;
+    double mx = fmax(fabs(a0), fabs(a1));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const int e = exp_above(mx);
+    if (lane == 0) pexp[c] = e;
+    double x0 = ldexp(a0, -(e + 1)), x1 = ldexp(a1, -(e + 1));
+#pragma unroll
+    for (int t = 0; t < kD; ++t) {
+      const double t0 = x0 * 256.0, t1 = x1 * 256.0;
+      const double d0 = rint(t0), d1 = rint(t1);
+      x0 = t0 - d0;
+      x1 = t1 - d1;
+      D[t * plane + c * kK + lane] = __double2bfloat16(d0);
+      D[t * plane + c * kK + lane + 32] = __double2bfloat16(d1);
+    }
+  }
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+  auto fn = tensor_map_encoder();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kK, (cuuint64_t)rows, (cuuint64_t)kD};
+  cuuint64_t strides[2] = {(cuuint64_t)kK * 2, (cuuint64_t)kK * rows * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tcu
+
+size_t update_f64emu_digit_bytes(int64_t rows) { return (size_t)tcu::kD * rows * tcu::kK * 2; }
+
+cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t* act, const int32_t* pivmark,
+                          const int32_t* pivorig, double* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
+                          void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
+                          cudaStream_t s) {
+  if (na <= 0 || tb <= 0) return cudaSuccess;
+  if (bt > tcu::kK || na > nrows || tb > prows) return cudaErrorInvalidValue;
+  auto nd = static_cast<__nv_bfloat16*>(ndig);
+  auto pd = static_cast<__nv_bfloat16*>(pdig);
+  const int64_t nplane = nrows * tcu::kK, pplane = prows * tcu::kK;
+  int64_t b1 = ((int64_t)na * 32 + 255) / 256;
+  if (b1 > 4096) b1 = 4096;
+  tcu::k_slice_n<<<(int)b1, 256, 0, s>>>(na, bt, N, nd, nexp, nplane, done);
+  int64_t b2 = ((int64_t)tb * 32 + 255) / 256;
+  if (b2 > 4096) b2 = 4096;
+  tcu::k_slice_p<<<(int)b2, 256, 0, s>>>(bt, tb, X, ldx, pivorig, pd, pexp, pplane, done);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mn, mp;
+  if (!tcu::make_map(&mn, nd, nrows, tcu::kBM)) return cudaErrorInvalidValue;
+  if (!tcu::make_map(&mp, pd, prows, tcu::kBN)) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(tcu::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(tcu::k_update_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int rt = (na + tcu::kBM - 1) / tcu::kBM;
+  const int ct = (tb + tcu::kBN - 1) / tcu::kBN;
+  int gy = (sms + rt - 1) / rt;  // about one CTA per SM in all
+  if (gy > ct) gy = ct;
+  if (gy < 1) gy = 1;
+  tcu::k_update_f64emu<<<dim3((unsigned)rt, (unsigned)gy), tcu::kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act,
+                                                                                    pivmark, X, ldx, st, done);
+  return cudaGetLastError();
+}
+
+}  // namespace rid

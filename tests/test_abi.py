@@ -24,6 +24,17 @@ def test_exports_every_declared_function(lib):
         assert hasattr(lib, n), "missing export %s" % n
 
 
+def test_every_declared_function_has_a_signature(lib):
+    """Each entry point's ctypes signature has as many arguments as the header
+    prototype (an undeclared one would truncate 64-bit pointers to C ints)."""
+    from paper_2310_09417_gb300 import binding
+    protos = binding.header_prototypes()
+    assert protos["id_quantize_fp8"] == 6 and protos["id_mlp_param_count"] == 0
+    for name, nargs in protos.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None and len(f.argtypes) == nargs, name
+
+
 def _header_struct_fields(name):
     from paper_2310_09417_gb300 import binding
     text = open(binding.HEADER).read()

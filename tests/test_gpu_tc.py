@@ -50,6 +50,18 @@ def test_tc_sketch_matches_fp64_product(B, m, n, rows):
     assert err < 4e-6 * max(1.0, np.sqrt(m / 1024)), err
 
 
+def test_bf16_gaussian_rows_round_the_fp64_generator(B, orc):
+    """BF16 rows: the same counters and Box-Muller map evaluated in FP32 on the
+    leading 24 bits.  Against the FP64 generator rounded to BF16 (nearest even):
+    equal except where the two evaluations straddle a rounding boundary, and
+    then one BF16 step apart."""
+    g = B.gaussian_rows(7, 0, 64, 4099, dtype=torch.bfloat16).float().cpu().numpy()
+    ob = torch.from_numpy(orc.gaussian_rows(7, 0, 64, 4099)).to(torch.bfloat16).float().numpy()
+    diff = g != ob
+    assert diff.mean() < 1e-3
+    assert np.all(np.abs(g[diff] - ob[diff]) <= 2.0 ** -7 * np.abs(ob[diff]) * 1.01)
+
+
 def test_simt_sketch_matches_fp64_product(B):
     rng = np.random.default_rng(3)
     A = B.colmajor(torch.from_numpy(rng.standard_normal((777, 129))).cuda())

@@ -76,6 +76,9 @@ struct Plan {
   size_t off_L = 0, off_L1 = 0, off_T64 = 0, off_Linv64 = 0, off_iota = 0, off_csum = 0;
   // path 65: digit slices of N and T(piv, old) for the tensor-core block update
   size_t off_ndig = 0, off_nexp = 0, off_pdig = 0, off_pexp = 0;
+  // path 65: digit slices of T(act, 0:tb) and G(perm, cols) for the tensor-core Schur GEMM
+  size_t off_adig = 0, off_aexp = 0, off_bdig = 0, off_bexp = 0, off_colmax = 0;
+  bool schur_tc = false;
   bool keep_l = false, f64_solve = false;
 };
 
@@ -211,6 +214,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_nexp = take(path == 65 && b <= 64 ? (size_t)p->n * 4 : 0);
   p->off_pdig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(kcap) : 0);
   p->off_pexp = take(path == 65 && b <= 64 ? (size_t)kcap * 4 : 0);
+  p->schur_tc = path == 65;  // used for panels of width <= 64
+  p->off_adig = take(p->schur_tc ? gemm_f64emu_digit_bytes(p->n, kcap) : 0);
+  p->off_aexp = take(p->schur_tc ? (size_t)p->n * 4 : 0);
+  p->off_bdig = take(p->schur_tc ? gemm_f64emu_digit_bytes(64, kcap) : 0);
+  p->off_bexp = take(p->schur_tc ? (size_t)64 * 4 : 0);
+  p->off_colmax = take(p->schur_tc ? (size_t)64 * 8 : 0);
   // x_solve_f64: the multipliers (n x cap), column sums, and for an FP32 LU the FP64 solve's buffers
   p->keep_l = o->x_solve_f64 != 0;
   p->f64_solve = p->keep_l && e == 4;
@@ -275,6 +284,11 @@ class Engine {
     nexp_ = reinterpret_cast<int32_t*>(w + p.off_nexp);
     pdig_ = w + p.off_pdig;
     pexp_ = reinterpret_cast<int32_t*>(w + p.off_pexp);
+    adig_ = w + p.off_adig;
+    aexp_ = reinterpret_cast<int32_t*>(w + p.off_aexp);
+    bdig_ = w + p.off_bdig;
+    bexp_ = reinterpret_cast<int32_t*>(w + p.off_bexp);
+    colmax_ = reinterpret_cast<unsigned long long*>(w + p.off_colmax);
     X_ = static_cast<T*>(out->X);
     ldx_ = out->ldx;
     done_ = &st_->done;
@@ -567,12 +581,25 @@ class Engine {
     int nz = 0, nl = 0;
     const int64_t lds = p_.wmax;
     if (tb > 0) {
-      nz = gemm_splits((int)tb, choose_splits(na, w, tb, p_.sms, p_.s2max));
-      Operand<T> a{X_, ldx_, act_[cur_], 0};
-      Operand<T> bop{G_, p_.ldg, perm32_, col0};
-      EpiArgs<T> ep{Spart_, lds, (int64_t)p_.n * lds, nullptr, nullptr};
-      RID_TRY(cuda(gemm_gather<T>((int)na, (int)w, (int)tb, nz, false, a, bop, kEpiStore, ep, done_, s_)));
-      ++nl;
+      bool done_tc = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (p_.schur_tc && w <= 64) {  // FP64-accurate on the tensor cores
+          nz = gemm_f64emu_splits(na, w, tb, p_.sms);
+          RID_TRY(cuda(gemm_f64emu((int)na, (int)w, (int)tb, X_, ldx_, act_[cur_], G_, p_.ldg, col0, perm32_, adig_,
+                                   p_.n, aexp_, bdig_, 64, bexp_, colmax_, p_.ldl, Spart_, lds, (int64_t)p_.n * lds,
+                                   nz, st_, done_, s_)));
+          nl += 4;
+          done_tc = true;
+        }
+      }
+      if (!done_tc) {
+        nz = gemm_splits((int)tb, choose_splits(na, w, tb, p_.sms, p_.s2max));
+        Operand<T> a{X_, ldx_, act_[cur_], 0};
+        Operand<T> bop{G_, p_.ldg, perm32_, col0};
+        EpiArgs<T> ep{Spart_, lds, (int64_t)p_.n * lds, nullptr, nullptr};
+        RID_TRY(cuda(gemm_gather<T>((int)na, (int)w, (int)tb, nz, false, a, bop, kEpiStore, ep, done_, s_)));
+        ++nl;
+      }
     }
     RID_TRY(cuda(schur_finish<T>((int)na, (int)w, act_[cur_], G_, p_.ldg, col0, nz, (int64_t)p_.n * lds, Spart_,
                                  S_, lds, e2_, p_.nparts, done_, s_)));
@@ -711,6 +738,9 @@ class Engine {
   int32_t* iota_;
   void *ndig_, *pdig_;   // path 65: digit slices for the tensor-core block update
   int32_t *nexp_, *pexp_;
+  void *adig_, *bdig_;   // path 65: digit slices for the tensor-core Schur GEMM
+  int32_t *aexp_, *bexp_;
+  unsigned long long* colmax_;
   const int32_t* done_;
   int64_t ldx_;
   int cur_ = 0;

@@ -179,6 +179,19 @@ cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t
                           void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
                           cudaStream_t s);
 
+// ---- FP64-accurate GEMM on the tensor cores (rid_tc_gemm64.cu): out[z] (M x N, row stride
+// ldo) = split z of A B with A(m, k) = A[aidx[m] * lda + k] and B(k, n) = B[bidx[k] * ldb +
+// boff + n], N <= 64, K <= kmax.  adig / bdig hold gemm_f64emu_digit_bytes(arows / brows,
+// kmax) bytes, aexp / bexp arows / brows exponents, colmax N words.
+int64_t gemm_f64emu_kpad(int64_t K);
+size_t gemm_f64emu_digit_bytes(int64_t rows, int64_t Kmax);
+int gemm_f64emu_splits(int64_t M, int64_t N, int64_t K, int sms);
+cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const int32_t* aidx, const double* B,
+                        int64_t ldb, int64_t boff, const int32_t* bidx, void* adig, int64_t arows, int32_t* aexp,
+                        void* bdig, int64_t brows, int32_t* bexp, unsigned long long* colmax, int64_t kmax,
+                        double* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
+                        cudaStream_t s);
+
 // ---- the driver's cuTensorMapEncodeTiled (nullptr when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 

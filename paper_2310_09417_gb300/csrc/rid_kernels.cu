@@ -9,6 +9,7 @@
 // the caller's X buffer throughout (column j of X = row j of L2 L1^{-1}).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -358,6 +359,7 @@ cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_
 // every block, then division by the pivot and the rank-1 update (Eq. lupps)
 // of the block's unselected rows.  Rows are marked, never swapped.
 constexpr int kPanelThreads = 256;
+constexpr int kPanelRowsDefault = 32;
 constexpr int kPanelMaxW = 128;
 
 template <typename T>
@@ -459,10 +461,28 @@ __global__ void __launch_bounds__(kPanelThreads)
   for (int r = tid; r < nr; r += blockDim.x) pivmark[r0 + r] = sel[r];
 }
 
+// Rows per block of the panel: fewer, larger blocks make the per-pivot grid
+// barrier cheaper (one atomic arrival per block) while each block's rows still
+// fit in shared memory.  RANDID_PANEL_ROWS overrides the minimum (tuning).
+static int panel_min_rows() {
+  static int rows = -1;
+  if (rows < 0) {
+    rows = kPanelRowsDefault;
+    if (const char* env = getenv("RANDID_PANEL_ROWS")) {
+      const int v = atoi(env);
+      if (v >= 1 && v <= 4096) rows = v;
+    }
+  }
+  return rows;
+}
+
 template <typename T>
 PanelCfg panel_config(int na, int w, int num_sms) {
   PanelCfg cfg;
-  int grid = (na + 31) / 32;  // at least 32 rows per block
+  int min_rows = panel_min_rows();
+  const int fit = (int)((size_t)200 * 1024 / ((size_t)w * sizeof(T) + 1));  // rows staged in shared memory
+  if (min_rows > fit) min_rows = fit < 32 ? 32 : fit;
+  int grid = (na + min_rows - 1) / min_rows;
   if (grid > num_sms) grid = num_sms;
   if (grid < 1) grid = 1;
   int chunk = (na + grid - 1) / grid;

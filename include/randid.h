@@ -64,12 +64,14 @@ typedef enum {
   ID_FP8_E4M3 = 3,
   /* sketch_prec only, with F64 A and lu_prec F64: the sketch computed to FP64
      accuracy on the BF16 tensor cores by exact integer slicing.  A is split once
-     per call into 8 digit slices of 7 bits with per-column exponents (55 bits);
-     Omega is the Gaussian on the grid 2^-10 (|z| < 8), split into 2 digits; the
-     digit products are summed exactly in FP32 over chunks of 1024 and in FP64
-     across chunks.  Entry error <= 2^-47 max_i|A_ij| sum_r |Omega_cr|.  A caller
-     omega (F64) is rounded to the same grid (clipped at |q| <= 8127).  Extra
-     workspace: 16 bytes per element of A. */
+     per call into 7 digit slices of 8 bits with per-column exponents (56 bits);
+     Omega is the Gaussian on the grid 2^-11 (|q| <= 16383), split into 2 digits;
+     every digit product is kept and summed exactly in FP32 over chunks of 512
+     and in int64 across chunks.  Entry error <= 2^-52 max_i|A_ij|
+     sum_r |Omega_cr|.  The Schur GEMM and the block update of X run on the
+     tensor cores the same way (7 digits of 8 bits per operand).  A caller omega
+     (F64) is rounded to the same grid.  Extra workspace: 14 bytes per element
+     of A plus 14 bytes per element of T(act, 0:k). */
   ID_F64_EMU = 4
 } id_dtype;
 

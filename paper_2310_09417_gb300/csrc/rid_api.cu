@@ -208,7 +208,7 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_normp = take((size_t)p->nparts * 8);
   p->off_trace = take((size_t)p->max_rounds * 8);
   // path 65: the 8 digit slices of A and its column exponents
-  p->off_digits = take(path == 65 ? (size_t)8 * p->ldw * p->n * 2 : 0);
+  p->off_digits = take(path == 65 ? f64emu_digit_bytes(p->m, p->n) : 0);
   p->off_colexp = take(path == 65 ? (size_t)p->n * 4 : 0);
   p->off_ndig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(p->n) : 0);
   p->off_nexp = take(path == 65 && b <= 64 ? (size_t)p->n * 4 : 0);
@@ -968,7 +968,7 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
   *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
   if (*path == 65) {  // digit slices of A, column exponents, two digit planes of Omega
     const size_t mp = (size_t)f64emu_pad(A->m);
-    *bytes += align_up(8 * mp * A->n * 2) + align_up((size_t)A->n * 4) + align_up(2 * mp * rows * 2);
+    *bytes += align_up(f64emu_digit_bytes(A->m, A->n)) + align_up((size_t)A->n * 4) + align_up(2 * mp * rows * 2);
   }
   return ID_OK;
 }
@@ -1018,8 +1018,8 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
     unsigned char* w = static_cast<unsigned char*>(part) + (splits > 1 ? align_up((size_t)splits * A->n * rows * 8) : 0);
     const size_t mp = (size_t)f64emu_pad(A->m);
     void* digits = w;
-    int32_t* colexp = reinterpret_cast<int32_t*>(w + align_up(8 * mp * A->n * 2));
-    void* wdig = w + align_up(8 * mp * A->n * 2) + align_up((size_t)A->n * 4);
+    int32_t* colexp = reinterpret_cast<int32_t*>(w + align_up(f64emu_digit_bytes(A->m, A->n)));
+    void* wdig = w + align_up(f64emu_digit_bytes(A->m, A->n)) + align_up((size_t)A->n * 4);
     double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
     e = f64emu_prepare(static_cast<const double*>(A->data), A->ld, A->m, A->n, colexp, digits, s);
     if (e == cudaSuccess)

@@ -141,10 +141,12 @@ cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, i
                              int tol_rel, DevState* st, cudaStream_t s);
 
 // ---- FP64-accurate sketch on the tensor cores (rid_tc_f64.cu).  A is split once into
-// 8 BF16 digit slices (slice-major, each column-major f64emu_pad(m) x n) with column
-// exponents; Omega rows are quantised to the grid 2^-10 and split into 2 digit planes
-// (each rows_alloc x f64emu_pad(m)); out[z] (n x rows, FP64) holds split z of (Omega A)^T.
+// 7 BF16 digit slices (slice-major, each column-major f64emu_pad(m) x n, f64emu_digit_bytes
+// in all) with column exponents; Omega rows are quantised to the grid 2^-11 and split into
+// 2 digit planes (each rows_alloc x f64emu_pad(m)); out[z] (n x rows, FP64) holds split z
+// of (Omega A)^T.
 int64_t f64emu_pad(int64_t m);
+size_t f64emu_digit_bytes(int64_t m, int64_t n);
 int f64emu_splits(int64_t m, int64_t n, int sms);
 cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, void* digits,
                            cudaStream_t s);

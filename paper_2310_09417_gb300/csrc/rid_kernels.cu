@@ -513,36 +513,49 @@ cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, T* S, int6
 // ============================================================ re-blocking
 // Inverse of the unit lower triangular L-hat(piv(0:bt), 0:bt): thread j forms
 // column j by forward substitution.
+// Inverse of the unit-lower block (bt x bt): row i of X = L^{-1} is
+// X(i, j) = -sum_{c=j}^{i-1} L(i, c) X(c, j), j < i.  Rows are formed in order; each
+// column j of a row is summed by 4 threads (interleaved over c) and a shuffle.
+// L and X live in shared memory when both fit, else X is formed in place in Linv.
+constexpr int kLinvSplit = 4;
 template <typename T>
 __global__ void k_linv(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv,
-                       T* __restrict__ Linv, const int32_t* done) {
+                       T* __restrict__ Linv, int x_in_smem, const int32_t* done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
   T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt
+  T* X = x_in_smem ? Lp + bt * bt : Linv;
   for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) {
     const int r = e / bt, c = e - r * bt;
     Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : (c == r ? T(1) : T(0));
+    X[e] = r == c ? T(1) : T(0);
   }
   __syncthreads();
-  const int j = threadIdx.x;
-  if (j < bt) {
-    for (int i = 0; i < bt; ++i) Linv[i * bt + j] = i == j ? T(1) : T(0);
-    for (int i = j + 1; i < bt; ++i) {
-      T acc = T(0);
-      for (int c = j; c < i; ++c) acc = fma(Lp[i * bt + c], Linv[c * bt + j], acc);
-      Linv[i * bt + j] = -acc;
-    }
+  const int j = threadIdx.x / kLinvSplit, part = threadIdx.x % kLinvSplit;
+  for (int i = 1; i < bt; ++i) {
+    T acc = T(0);
+    if (j < i)
+      for (int c = j + part; c < i; c += kLinvSplit) acc = fma(Lp[i * bt + c], X[c * bt + j], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (j < i && part == 0) X[i * bt + j] = -acc;
+    __syncthreads();
   }
+  if (x_in_smem)
+    for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) Linv[e] = X[e];
 }
 
 template <typename T>
 cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
                  cudaStream_t s) {
   static size_t cached = 0;
-  cudaError_t e = ensure_smem(k_linv<T>, (size_t)bt * bt * sizeof(T), &cached);
+  const size_t one = (size_t)bt * bt * sizeof(T);
+  const int x_in_smem = 2 * one <= (size_t)200 * 1024 ? 1 : 0;
+  const size_t smem = x_in_smem ? 2 * one : one;
+  cudaError_t e = ensure_smem(k_linv<T>, smem, &cached);
   if (e != cudaSuccess) return e;
-  const int threads = bt <= 32 ? 32 : (bt <= 64 ? 64 : 128);
-  k_linv<T><<<1, threads, (size_t)bt * bt * sizeof(T), s>>>(bt, S, lds, piv, Linv, done);
+  const int threads = (kLinvSplit * bt + 31) / 32 * 32;
+  k_linv<T><<<1, threads, smem, s>>>(bt, S, lds, piv, Linv, x_in_smem, done);
   return cudaGetLastError();
 }
 

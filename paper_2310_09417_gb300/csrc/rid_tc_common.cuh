@@ -150,5 +150,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// (hi 2^32 + lo) 2^ex as a double, rounded to nearest even, assembled with integer
+// operations (GB300 issues about two FP64 instructions per clock per SM).
+// hi, lo: any int64 values; results outside the normal range take the FP64 route.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int ex) {
+  const __int128 V = ((__int128)hi << 32) + (__int128)lo;
+  if (V == 0) return 0.0;
+  const bool neg = V < 0;
+  const unsigned __int128 U = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
+  const unsigned long long h = (unsigned long long)(U >> 64), l = (unsigned long long)U;
+  int msb = h ? 127 - __clzll((long long)h) : 63 - __clzll((long long)l);
+  const int sh = msb - 52;
+  unsigned long long mant;
+  if (sh > 0) {
+    mant = (unsigned long long)(U >> sh);
+    const unsigned __int128 rem = U & (((unsigned __int128)1 << sh) - 1);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++msb;
+      }
+    }
+  } else {
+    mant = (unsigned long long)(U << (-sh));
+  }
+  const int e = msb + ex + 1023;
+  if (e <= 0 || e >= 2047) return ldexp((double)hi + ldexp((double)lo, -32), ex + 32);
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)e << 52) |
+                                          (mant & ((1ull << 52) - 1))));
+}
+
+// acc += v * 2^SH, exact (v an integer-valued float below 2^24 in magnitude)
+template <int SH>
+__device__ __forceinline__ void add_scaled(long long& acc, float v) {
+  const int iv = __float2int_rn(v);
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
+}
+
 }  // namespace tcx
 }  // namespace rid

@@ -3,28 +3,27 @@
 // GB300 executes FP64 FMAs at 1.25 TFLOP/s, so the FP64 sketch (Sec. 2.4) is
 // moved onto the tensor cores by exact integer slicing:
 //   * A: per column j an exponent E_j with max_i |A_ij| < 2^E_j; x = A / 2^(E_j+1)
-//     (|x| < 1/2) is written as sum_{s<8} d_s 2^(-7(s+1)) + r with balanced 7-bit
-//     digits |d_s| <= 64 and |r| <= 2^-57 -- 55 significant bits per column.
-//   * Omega: standard normal numbers on the grid 2^-10, q = rint(1024 z) clipped to
-//     |q| <= 8127, split as q = 128 q1 + q0 with |q1| <= 63, |q0| <= 64.
+//     (|x| < 1/2) is written as sum_{s<7} d_s 2^(-8(s+1)) + r with balanced 8-bit
+//     digits |d_s| <= 128 and |r| <= 2^-57 -- 56 bits per column.
+//   * Omega: standard normal numbers on the grid 2^-11, q = rint(2048 z) clipped to
+//     |q| <= 16383, split as q = 256 q1 + q0 with |q1| <= 64, |q0| <= 128.
 //   * Every digit is an integer exact in BF16.  Products of equal weight
-//     2^(-7g) share one FP32 accumulator group in tensor memory: group g collects
-//     q1 x d_g and q0 x d_(g-1) (g = 0..7, 8 groups x 64 columns = the 512
-//     columns of an SM; the g = 8 term q0 x d_7 is dropped).  One MMA with
-//     N = 128 (both Omega digits stacked) writes groups s and s+1 for slice s.
-//     Over a chunk of 1024 K a group's partial sums stay below
-//     1024 (64*64 + 63*64) < 2^23: the FP32 accumulation is exact.
+//     2^(-8g) share one FP32 accumulator group in tensor memory: group g collects
+//     q1 x d_g and q0 x d_(g-1) (g = 0..7: 8 groups x 64 columns = the 512 columns
+//     of an SM; no product is dropped).  One MMA with N = 128 (both Omega digits
+//     stacked) writes groups s and s+1 for slice s.  Over a chunk of 512 K a
+//     group's partial sums stay below 512 (128*128 + 64*128) < 2^24: the FP32
+//     accumulation is exact.
 //   * After slice g of a chunk, group g is final for that chunk; the epilogue
 //     warps convert it to integers and add it, exactly, to two int64
-//     accumulators per entry (groups 0..3 and 4..7 with weights 2^(7(3-g)) and
-//     2^(7(7-g))), then hand the group back to the MMA issuer -- the epilogue
+//     accumulators per entry (groups 0..3 and 4..7 with weights 2^(8(3-g)) and
+//     2^(8(7-g))), then hand the group back to the MMA issuer -- the epilogue
 //     of a chunk overlaps the MMAs of the next one.  At the end
-//     Y_cj = 2^(E_j - 9) (acc_hi 2^-21 + acc_lo 2^-49).
-// Error of an entry: the dropped q0 x d_7 products (|q0 2^-10| <= |Omega_cr|,
-// |d_7 2^-56| 2^(E_j+1) <= 2^-48 max_i|A_ij|), the digit remainder (2^-55) and
-// the final FP64 roundings stay below 2^-47 max_i|A_ij| sum_r |Omega_cr| -- far
+//     Y_cj = 2^(E_j - 66) (acc_hi 2^32 + acc_lo), assembled by integer operations.
+// Error of an entry: the digit remainders (|r| 2^(E_j+1) <= 2^-55 max_i|A_ij| per
+// term) and one final rounding: at most 2^-52 max_i|A_ij| sum_r |Omega_cr| --
 // inside the worst-case rounding bound m 2^-53 sum_r |Omega_cr||A_rj| of an FP64
-// dot product once m > 64.
+// dot product.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,31 +40,26 @@ namespace tc64 {
 constexpr int kBM = 128;         // columns of A per tile (MMA M)
 constexpr int kBN = 64;          // rows of Omega per tile (MMA N per digit)
 constexpr int kBK = 64;          // K per stage
-constexpr int kSlices = 8;       // digits of A (= accumulator groups)
-constexpr int kChunkSteps = 16;  // K stages per exact chunk (1024 K)
+constexpr int kSlices = 7;       // digits of A
+constexpr int kGroups = 8;       // accumulator groups (slice s feeds groups s and s+1)
+constexpr int kChunkSteps = 8;   // K stages per exact chunk (512 K)
 constexpr int kChunk = kChunkSteps * kBK;
 constexpr int kStages = 6;
 constexpr int kEpiWarps = 8;     // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kMaxChunksPerSplit = 1 << 18;  // int64 accumulators: 2^18 * 2^44 < 2^63
-constexpr double kQMax = 8127.0;
+constexpr int kMaxChunksPerSplit = 1 << 14;  // int64 accumulators: 2^14 * 2^48 < 2^63
+constexpr double kQMax = 16383.0;
 
 using namespace tcx;
 
 // acc += v * 2^sh, exact (v an integer-valued float below 2^23 in magnitude)
-template <int SH>
-__device__ __forceinline__ void add_scaled(long long& acc, float v) {
-  const int iv = __float2int_rn(v);
-  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
-}
-
 struct Smem {
   alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // one digit slice of A: 16 KB
   alignas(1024) __nv_bfloat16 w[kStages][2 * kBN * kBK];  // both digits of Omega: 128 rows, 16 KB
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  uint64_t ready[kSlices];  // group g of the current chunk is final
-  uint64_t free_[kSlices];  // the epilogue has read group g
+  uint64_t ready[kGroups];  // group g of the current chunk is final
+  uint64_t free_[kGroups];  // the epilogue has read group g
   uint64_t drain;
   uint32_t tmem_base;
 };
@@ -94,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    for (int g = 0; g < kSlices; ++g) {
+    for (int g = 0; g < kGroups; ++g) {
       mbar_init(&sm.ready[g], 1);
       mbar_init(&sm.free_[g], kEpiWarps);
     }
@@ -140,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // read them for chunk c-1 (group s was already awaited at slice s-1)
           const uint32_t par = (c - 1) & 1;
           if (s == 0 && !mbar_wait(&sm.free_[0], par, st)) { ok = false; break; }
-          if (s + 1 < kSlices && !mbar_wait(&sm.free_[s + 1], par, st)) { ok = false; break; }
+          if (!mbar_wait(&sm.free_[s + 1], par, st)) { ok = false; break; }
           fence_after_sync();
         }
         const uint32_t dst = tmem + s * kBN;
@@ -150,14 +144,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after_sync();
           const uint64_t da = desc_sw128(sm.a[b]);
           const uint64_t dq1 = desc_sw128(sm.w[b]);             // high digit of Omega (weight 1)
-          const uint64_t dq0 = desc_sw128(sm.w[b] + kBN * kBK);  // low digit (weight 2^-7)
+          const uint64_t dq0 = desc_sw128(sm.w[b] + kBN * kBK);  // low digit (weight 2^-8)
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
             const bool first = (j == 0 && kk == 0);
-            if (s == kSlices - 1) {
-              // group 7 <- q1 x d_7 (q0 x d_7 belongs to the dropped group 8)
-              mma_bf16(dst, da + 2 * kk, dq1 + 2 * kk, id64, 1u);
-            } else if (first && s > 0) {
+            if (first && s > 0) {
               // group s continues, group s+1 starts: two MMAs with their own flags
               mma_bf16(dst, da, dq1, id64, 1u);
               mma_bf16(dst + kBN, da, dq0, id64, 0u);
@@ -168,7 +159,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mma_commit(&sm.empty[b]);
         }
-        if (ok) mma_commit(&sm.ready[s]);  // group s is final for chunk c
+        if (ok) {
+          mma_commit(&sm.ready[s]);  // group s is final for chunk c
+          if (s == kSlices - 1) mma_commit(&sm.ready[s + 1]);  // and the last group with it
+        }
       }
     }
     // every MMA issued has completed before TMEM is released
@@ -187,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
 #pragma unroll
-      for (int g = 0; g < kSlices; ++g) {
+      for (int g = 0; g < kGroups; ++g) {
         if (!mbar_wait(&sm.ready[g], c & 1, st)) { ok = false; break; }
         fence_after_sync();
 #pragma unroll
@@ -196,13 +190,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld16(base + g * kBN + cb, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            if (g == 0) add_scaled<21>(hi[cb + i], v[i]);
-            else if (g == 1) add_scaled<14>(hi[cb + i], v[i]);
-            else if (g == 2) add_scaled<7>(hi[cb + i], v[i]);
+            if (g == 0) add_scaled<24>(hi[cb + i], v[i]);
+            else if (g == 1) add_scaled<16>(hi[cb + i], v[i]);
+            else if (g == 2) add_scaled<8>(hi[cb + i], v[i]);
             else if (g == 3) add_scaled<0>(hi[cb + i], v[i]);
-            else if (g == 4) add_scaled<21>(lo[cb + i], v[i]);
-            else if (g == 5) add_scaled<14>(lo[cb + i], v[i]);
-            else if (g == 6) add_scaled<7>(lo[cb + i], v[i]);
+            else if (g == 4) add_scaled<24>(lo[cb + i], v[i]);
+            else if (g == 5) add_scaled<16>(lo[cb + i], v[i]);
+            else if (g == 6) add_scaled<8>(lo[cb + i], v[i]);
             else add_scaled<0>(lo[cb + i], v[i]);
           }
         }
@@ -217,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int lim = rows - n0 - half * 32;
 #pragma unroll
       for (int i = 0; i < 32; ++i)
-        if (i < lim) o[i] = ldexp(fma((double)lo[i], 0x1p-49, (double)hi[i] * 0x1p-21), e - 9);
+        if (i < lim) o[i] = fixed_to_double(hi[i], lo[i], e - 66);
     }
   }
   fence_before_sync();
@@ -262,15 +256,15 @@ __global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_
     double x = i < m ? ldexp(A[i + j * lda], -(E[j] + 1)) : 0.0;  // |x| < 1/2
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) {
-      const double t = x * 128.0;  // exact
-      const double d = rint(t);    // |d| <= 64
+      const double t = x * 256.0;  // exact
+      const double d = rint(t);    // |d| <= 128
       x = t - d;                   // exact, |x| <= 1/2
       D[s * slice + e] = __double2bfloat16(d);
     }
   }
 }
 
-// Omega digits on the grid 2^-10: W[t][r][i], t = 0 high digit q1, t = 1 low digit q0;
+// Omega digits on the grid 2^-11: W[t][r][i], t = 0 high digit q1, t = 1 low digit q0;
 // from the Philox/Box-Muller rows (gen) or a caller matrix (src != nullptr).
 __global__ void k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t ldw, int64_t rows_alloc,
                                const double* __restrict__ src, int64_t ld_src, __nv_bfloat16* __restrict__ W,
@@ -295,10 +289,10 @@ __global__ void k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_
       if (i >= ldw) break;
       double val = 0.0;
       if (i < m) val = src == nullptr ? z[u] : src[r * ld_src + i];
-      double qv = rint(val * 1024.0);
+      double qv = rint(val * 2048.0);
       qv = fmin(fmax(qv, -kQMax), kQMax);
-      const double q1 = rint(qv / 128.0);
-      const double q0 = qv - 128.0 * q1;
+      const double q1 = rint(qv / 256.0);  // |q1| <= 64
+      const double q0 = qv - 256.0 * q1;   // |q0| <= 128
       W[r * ldw + i] = __double2bfloat16(q1);
       W[plane + r * ldw + i] = __double2bfloat16(q0);
     }
@@ -322,6 +316,7 @@ bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t oute
 }  // namespace tc64
 
 int64_t f64emu_pad(int64_t m) { return (m + 7) / 8 * 8; }
+size_t f64emu_digit_bytes(int64_t m, int64_t n) { return (size_t)tc64::kSlices * f64emu_pad(m) * n * 2; }
 
 // Split count of the K range.  One CTA per SM holds a (column tile, split); its
 // time is about its chunks (+ a fixed cost), so the launch takes

@@ -53,45 +53,6 @@ struct Smem {
 
 static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_update_f64emu exceeds 227 KB");
 
-// acc += v * 2^SH, exact (v an integer-valued float below 2^23 in magnitude)
-template <int SH>
-__device__ __forceinline__ void add_scaled(long long& acc, float v) {
-  const int iv = __float2int_rn(v);
-  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
-}
-
-// (hi 2^32 + lo) 2^ex as a double, rounded to nearest even, assembled with integer
-// operations: GB300 issues about two FP64 instructions per clock per SM, so the
-// epilogue keeps FP64 for the one subtraction from T.  |hi| < 2^40, |lo| < 2^48.
-__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int ex) {
-  const __int128 V = ((__int128)hi << 32) + (__int128)lo;
-  if (V == 0) return 0.0;
-  const bool neg = V < 0;
-  const unsigned __int128 U = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
-  const unsigned long long h = (unsigned long long)(U >> 64), l = (unsigned long long)U;
-  int msb = h ? 127 - __clzll((long long)h) : 63 - __clzll((long long)l);
-  const int sh = msb - 52;
-  unsigned long long mant;
-  if (sh > 0) {
-    mant = (unsigned long long)(U >> sh);
-    const unsigned __int128 rem = U & (((unsigned __int128)1 << sh) - 1);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++msb;
-      }
-    }
-  } else {
-    mant = (unsigned long long)(U << (-sh));
-  }
-  const int e = msb + ex + 1023;
-  if (e <= 0 || e >= 2047)  // subnormal or overflowing result: the FP64 route
-    return ldexp(fma((double)lo, 0x1p-32, (double)hi), ex + 32);
-  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)e << 52) |
-                                          (mant & ((1ull << 52) - 1))));
-}
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_f64emu(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_p, int na,

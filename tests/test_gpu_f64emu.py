@@ -1,9 +1,9 @@
 """GPU tests of the FP64-accurate sketch on the tensor cores (sketch precision
 F64_EMU): A is split into exact BF16 digit slices, Omega is a Gaussian on the
-grid 2^-10, and the digit products are summed exactly.
+grid 2^-11, and the digit products are summed exactly.
 
 * the sketch against the exact product (extended-precision reference) within
-  2^-47 max_i|A_ij| sum_r |Omega_cr| -- including sums near the FP32 exactness
+  2^-52 max_i|A_ij| sum_r |Omega_cr| -- including sums near the FP32 exactness
   limit of the tensor-core accumulators;
 * the sketch against an FP64 GEMM on tiled, ragged and split-K shapes;
 * the whole ID against the FP64 oracle run on the same grid-rounded Omega:
@@ -33,15 +33,15 @@ def B():
 
 
 def on_grid(Om):
-    """Omega rounded to the grid 2^-10 and clipped to |q| <= 8127 (the sketch
+    """Omega rounded to the grid 2^-11 and clipped to |q| <= 16383 (the sketch
     precision's definition of its Gaussian)."""
-    return np.clip(np.rint(np.asarray(Om) * 1024.0), -8127.0, 8127.0) / 1024.0
+    return np.clip(np.rint(np.asarray(Om) * 2048.0), -16383.0, 16383.0) / 2048.0
 
 
 def emu_bound(A, Om):
-    """2^-47 max_i |A_ij| sum_r |Omega_cr|, as an (n x rows) array: the dropped
-    q0 x d_7 products (2^-48), the digit remainder and the final roundings."""
-    return 2.0 ** -47 * np.outer(np.abs(A).max(axis=0), np.abs(Om).sum(axis=1))
+    """2^-52 max_i |A_ij| sum_r |Omega_cr|, as an (n x rows) array: the digit
+    remainders (2^-55 per term) and the final rounding."""
+    return 2.0 ** -52 * np.outer(np.abs(A).max(axis=0), np.abs(Om).sum(axis=1))
 
 
 def sketch(B, A, Om):
@@ -51,7 +51,7 @@ def sketch(B, A, Om):
 @pytest.mark.parametrize("case", ["scaled_columns", "near_accumulator_limit"])
 def test_emu_sketch_against_exact_product(B, case):
     rng = np.random.default_rng(17)
-    m, n, rows = 4101, 70, 33  # 5 exact chunks, ragged K, n and rows
+    m, n, rows = 4101, 70, 33  # 9 exact chunks of 512, ragged K, n and rows
     if case == "scaled_columns":
         # column exponents from 2^-40 to 2^40, a zero column, a single spike
         A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-40, 41, size=n))[None, :]
@@ -60,11 +60,12 @@ def test_emu_sketch_against_exact_product(B, case):
         A[17, 5] = -3.0
         Om = on_grid(rng.standard_normal((rows, m)))
     else:
-        # A just below 0.9765625 = 2 (62.5 / 128): digits d0 = 62, d1 = 64, and
-        # Omega at the clip value (q1 = q0 = 63) with one sign per row: group 1
-        # sums 1024 (63*62 + 63*64) = 0.97 * 2^23 over each chunk
-        A = 0.9765625 - 2.0 ** -20 * rng.random((m, n))
-        Om = np.full((rows, m), 8127.0 / 1024.0)
+        # A = -0.99609375 = 2 (-127.5 / 256): digits d0 = -128, d1 = 128; Omega =
+        # 16001 / 2048 (q1 = 63, q0 = -127), one sign per row: group 1 sums
+        # 512 (127*128 + 63*128) = 0.74 * 2^24 over each chunk
+        A = np.full((m, n), -0.99609375)
+        A[:, ::3] *= -1.0
+        Om = np.full((rows, m), 16001.0 / 2048.0)
         Om[1::2] *= -1.0
     G = sketch(B, A, Om)
     ref = (Om.astype(np.longdouble) @ A.astype(np.longdouble)).T
@@ -182,3 +183,37 @@ def test_emu_nonfinite_input_is_rejected(B):
     with pytest.raises(B.IDError) as e:
         B.id_adaptive(B.colmajor(A), 1e-3, sketch_prec=B.F64_EMU)
     assert e.value.code == B.ERR_NONFINITE
+
+
+@pytest.mark.parametrize("b", [32, 128])
+def test_emu_other_block_sizes(B, orc, b):
+    """b = 32 runs the tensor-core Schur GEMM and block update on narrower panels;
+    b = 128 is wider than they take (64), so those two steps run in FP64 SIMT
+    while the sketch stays on the tensor cores.  Both match the oracle."""
+    m, n, tol = 1500, 700, 1e-7
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=b)
+    Om = on_grid(W.gaussian_omega(b, orc.rows_needed(n, b, m=m), m))
+    g = B.id_adaptive(dev_cm(A), tol, block=b, omega=dev(Om), sketch_prec=B.F64_EMU)
+    thr = tol * orc.fro_norm(A)
+    r, spread = oracle_x_spread(orc, A, lambda AA: orc.id_adaptive(AA, Om, b, thr))
+    assert g.k == r["k"]
+    assert_id_close(orc, A, g, r, spread)
+
+
+def test_emu_predictor_seeded_run_is_identical(B):
+    """A rank guess from the learned predictor only changes how many blocks a
+    pass sketches: J, X and k of the emulated path are bit-identical.  The
+    network is hand-set to predict the plain loop's rank (all weights zero,
+    b3 = 0, the output mean log2(k))."""
+    m, n, b = 2000, 800, 32
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=40.0), seed=4)
+    Ad = dev_cm(A)
+    plain = B.id_adaptive(Ad, 1e-8, block=b, seed=4, sketch_prec=B.F64_EMU)
+    p = torch.zeros(B.mlp_param_count(), dtype=torch.float32, device="cuda")
+    p[B.MLP_TRAINABLE + 35:B.MLP_TRAINABLE + 70] = 1.0
+    p[-2] = float(np.log2(plain.k))
+    p[-1] = 1.0
+    seeded = B.id_adaptive(Ad, 1e-8, block=b, seed=4, sketch_prec=B.F64_EMU, predictor=p, max_pass_rows=4096)
+    assert seeded.k == plain.k and torch.equal(seeded.J, plain.J)
+    assert torch.equal(seeded.X, plain.X)
+    assert seeded.passes == 2 < plain.passes

@@ -231,3 +231,61 @@ def test_fp8_nonfinite_scale_is_rejected(B):
     with pytest.raises(B.IDError) as e:
         B.id_adaptive(A8, 1e-1)
     assert e.value.code == B.ERR_NONFINITE
+
+
+def test_fp8_fixed_rank_against_oracle(B, orc):
+    """randLUPP at fixed rank on the FP8 path: the first pivots (well separated)
+    equal the FP64 oracle's on the decoded values and the same Omega, and the
+    rank-k error is within 1.2x of the oracle's."""
+    m, n, k, l = 2048, 700, 40, 48
+    A = lowrank(m, n, 30, 1e-3, 12)
+    A8 = B.quantize_fp8(B.colmajor(torch.from_numpy(A).cuda()))
+    Ad = dequantize(A8)
+    Om8, Om = omega_fp8(B, W.gaussian_omega(8, l, m))
+    g = B.id_fixed_rank(A8, k, l, block=16, omega=Om8)
+    r = orc.id_fixed_rank(Ad, Om, k)
+    assert np.array_equal(g.J.cpu().numpy()[:10], r["J"][:10])
+    nA = orc.fro_norm(Ad)
+    eg = orc.id_residual(Ad, g.J.cpu().numpy(), g.X.cpu().numpy().astype(np.float64)) / nA
+    eo = orc.id_residual(Ad, r["J"], r["X"]) / nA
+    assert eg <= 1.2 * eo + 1e-6
+
+
+@pytest.mark.parametrize("path", ["f64", "f32", "bf16", "fp8", "f64emu"])
+def test_sketch_into_padded_rows(B, path):
+    """id_sketch writes G with a row stride larger than its row count on every
+    path (the split-K partials keep their own stride)."""
+    rng = np.random.default_rng(5)
+    m, n, rows, ldg = 3000, 300, 40, 56
+    A = rng.standard_normal((m, n))
+    Om = rng.standard_normal((rows, m))
+    kw = {}
+    if path == "f64":
+        Ad, Od = B.colmajor(torch.from_numpy(A).cuda()), torch.from_numpy(Om).cuda()
+    elif path == "f64emu":
+        Om = np.clip(np.rint(Om * 1024.0), -8127.0, 8127.0) / 1024.0
+        Ad, Od = B.colmajor(torch.from_numpy(A).cuda()), torch.from_numpy(Om).cuda()
+        kw = dict(sketch_prec=B.F64_EMU)
+    elif path == "f32":
+        Ad = B.colmajor(torch.from_numpy(A).to("cuda", torch.float32))
+        Od = torch.from_numpy(Om).to("cuda", torch.float32)
+    elif path == "bf16":
+        Ad = B.colmajor(torch.from_numpy(A).to("cuda", torch.bfloat16))
+        Od = torch.from_numpy(Om).to("cuda", torch.bfloat16).contiguous()
+    else:
+        Ad = B.quantize_fp8(B.colmajor(torch.from_numpy(A).cuda()))
+        Od, Om = omega_fp8(B, Om)
+    ref = B.id_sketch(Ad, Od, **kw)
+    G = torch.full((n, ldg), float("nan"), dtype=ref.dtype, device="cuda")
+    lib = B.load()
+    import ctypes
+    prec = (B.F64_EMU if path == "f64emu" else B._TORCH_TO_ID[Ad.dtype])
+    nb = ctypes.c_size_t(0)
+    assert lib.id_sketch_workspace_size(ctypes.byref(B._matrix(Ad)), rows, prec, ctypes.byref(nb)) == 0
+    ws = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device="cuda")
+    rc = lib.id_sketch(ctypes.byref(B._matrix(Ad)), Od.data_ptr(), Od.stride(0), rows, prec, G.data_ptr(), ldg,
+                       ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.equal(G[:, :rows], ref)
+    assert torch.isnan(G[:, rows:]).all()  # the padding is not written

@@ -35,6 +35,9 @@ WORKLOADS = {
     # name: (m, n, spectrum kind, kwargs, dtype, rel tol, block)
     "adaptive_poly_f32": (40000, 10000, "poly", {}, "f32", 1e-6, 64),
     "adaptive_step_f32": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f32", 1e-6, 64),
+    # FP32 A, LU and X with the FP32-accurate sketch on the BF16 tensor cores (3 digit slices)
+    "adaptive_poly_f32emu": (40000, 10000, "poly", {}, "f32emu", 1e-6, 64),
+    "adaptive_step_f32emu": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f32emu", 1e-6, 64),
     "adaptive_poly_f64": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
     "adaptive_step_f64": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64", 1e-10, 64),
     # FP64 A, LU and X with the FP64-accurate sketch on the BF16 tensor cores (exact digit
@@ -45,6 +48,7 @@ WORKLOADS = {
     "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
     "small_poly_f64emu": (16384, 4096, "poly", {}, "f64emu", 1e-10, 64),
+    "small_poly_f32emu": (16384, 4096, "poly", {}, "f32emu", 1e-6, 64),
     # mixed precision: A stored in BF16 = Gaussian factor product of rank 1500 + 1e-4 noise,
     # sketch on the tensor cores (BF16 x BF16 -> FP32), LU in FP32, norms in FP64
     "mixed_bf16": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 1e-3, 64),
@@ -119,8 +123,8 @@ def make_input(name, device, seed=2310_09417 + 1):
             return A8
         return At.t()
     s = W.spectrum(kind, n, **kw)
-    dtype = torch.float32 if dt == "f32" else torch.float64
-    if dt == "f32":
+    dtype = torch.float32 if dt in ("f32", "f32emu") else torch.float64
+    if dt in ("f32", "f32emu"):
         # U, V from an FP32 QR; the product in FP32 (TF32 off): the rounding of A
         # (~6e-8 relative) is far below the 1e-6 tolerance
         torch.backends.cuda.matmul.allow_tf32 = False
@@ -331,16 +335,19 @@ def config_dict(name, res):
                        % (kw.get("rank"), kw.get("noise"), "FP8 E4M3" if dt == "fp8" else "BF16")}[kind]
     if name.startswith("small_"):
         spec += " (reduced size for profiling)"
-    el = {"f32": 4, "f64": 8, "f64emu": 8, "bf16": 2, "fp8": 1}[dt]
+    el = {"f32": 4, "f32emu": 4, "f64": 8, "f64emu": 8, "bf16": 2, "fp8": 1}[dt]
     prec = {"f64": "FP64 sketch, LU and X", "f32": "FP32 sketch, LU and X",
-            "f64emu": "FP64 A, LU and X; FP64-accurate sketch on the BF16 tensor cores (8 exact 7-bit digit "
-                      "slices of A, Omega on the grid 2^-10 in 2 digits, exact FP32 chunk sums, int64 totals)",
+            "f64emu": "FP64 A, LU and X; FP64-accurate sketch, Schur GEMM and block update on the BF16 tensor cores "
+                      "(7 exact 8-bit digit slices per operand, Omega on the grid 2^-11 in 2 digits, exact FP32 "
+                      "chunk sums, int64 totals)",
+            "f32emu": "FP32 A, LU and X; FP32-accurate sketch on the BF16 tensor cores (3 exact 8-bit digit slices "
+                      "of A and of Omega, exact FP32 chunk sums, int64 totals)",
             "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms",
             "fp8": "FP8 E4M3 A with power-of-two FP32 scales per 128-row block (quantised from the BF16 matrix), "
                    "E4M3 Omega, tcgen05 kind::f8f6f4 sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
     c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
          "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device"
-                                     + (", rounded to the grid 2^-10" if dt == "f64emu" else ""),
+                                     + (", rounded to the grid 2^-11" if dt == "f64emu" else ""),
          "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * el / 1e9),
          "parallelism": "replicas (one ID per GPU)"}
     if res is not None:
@@ -541,7 +548,7 @@ def main():
     seed = 2310_09417 + 100 * rank
     kmax = min(m, n)
     xdt = torch.float64 if dt in ("f64", "f64emu") else torch.float32
-    sprec = B.F64_EMU if dt == "f64emu" else None
+    sprec = {"f64emu": B.F64_EMU, "f32emu": B.F32_EMU}.get(dt)
     J = torch.empty(kmax, dtype=torch.int64, device=dev)
     Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
     opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
@@ -597,13 +604,24 @@ def main():
         roofline = {"bound": "hbm", "kernel": "k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + "
                     "split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    elif dt == "f32emu":
+        # HBM-bound at one block per pass: per pass the 3 BF16 digit slices of A (6 mn) +
+        # Omega read and sliced (4 bm + 6 bm + 6 bm) + the FP32 sketch block (4 n b)
+        kp = (m + 63) // 64 * 64
+        sk_bytes = (6.0 * kp * n + 16.0 * b * kp + 4.0 * n * b) * res.passes + 10.0 * m * n
+        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
+        peak = PEAKS["hbm_gbs"]
+        roofline = {"bound": "hbm", "kernel": "k_gemm_emu<3, float> (tcgen05 + TMA, exact digit slices) + Omega "
+                    "slicing + split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(name),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     elif dt == "f64emu":
         # HBM-bound at one block per pass (rows = 64: about 120 tensor flop/B against a
-        # ridge near 290): per pass the 8 BF16 digit slices of A (16 mn) + both Omega digit
+        # ridge near 290): per pass the 7 BF16 digit slices of A (14 mn) + both Omega digit
         # planes (4 b m) + the FP64 sketch block (8 n b); once per ID the digit preparation
-        # (A read twice, the slices written: 32 mn)
+        # (A read twice, the slices written: 30 mn)
         mp = (m + 7) // 8 * 8
-        sk_bytes = (16.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * res.passes + 32.0 * m * n
+        sk_bytes = (14.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * res.passes + 30.0 * m * n
         achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
         peak = PEAKS["hbm_gbs"]
         roofline = {"bound": "hbm", "kernel": "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K "

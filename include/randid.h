@@ -72,7 +72,14 @@ typedef enum {
      tensor cores the same way (7 digits of 8 bits per operand).  A caller omega
      (F64) is rounded to the same grid.  Extra workspace: 14 bytes per element
      of A plus 14 bytes per element of T(act, 0:k). */
-  ID_F64_EMU = 4
+  ID_F64_EMU = 4,
+  /* sketch_prec only, with F32 A and lu_prec F32: the sketch on the BF16 tensor
+     cores with A and Omega each split into 3 digits of 8 bits (per-column /
+     per-row exponents); the 6 leading digit products are summed exactly in
+     FP32 over chunks of 320 and in int64 across chunks.  FP32-level accuracy;
+     Omega is the FP32 Gaussian (not rounded to a grid).  Extra workspace:
+     6 bytes per element of A. */
+  ID_F32_EMU = 5
 } id_dtype;
 
 /* An input matrix: DEVICE data, column-major m x n, leading dimension ld >= m. */
@@ -92,6 +99,7 @@ typedef struct {
        F64 / F64 / F64            FP64 throughout (FP64 FMA sketch)
        F64 / F64_EMU / F64        FP64-accurate sketch on the tensor cores
        F32 / F32 / F32            FP32 throughout
+       F32 / F32_EMU / F32        FP32-accurate sketch on the tensor cores
        BF16 / BF16 / F32          tensor-core sketch, FP32 LU and X
        FP8_E4M3 / FP8_E4M3 / F32  tensor-core sketch with block scales, FP32 LU and X
      ||A||_F and the estimate's sum of squares are FP64 on every path. */

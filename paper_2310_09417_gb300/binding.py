@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librandid.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "randid.h")
 
 # id_dtype
-F64, F32, BF16, FP8_E4M3, F64_EMU = 0, 1, 2, 3, 4
+F64, F32, BF16, FP8_E4M3, F64_EMU, F32_EMU = 0, 1, 2, 3, 4, 5
 # status
 OK, WARN_TOL_NOT_MET, WARN_ZERO_PIVOT = 0, 1, 2
 ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = -101, -102, -103, -104, -105

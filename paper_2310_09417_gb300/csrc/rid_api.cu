@@ -64,7 +64,8 @@ struct Plan {
   int s1_first = 1, s1_pass = 1, s2max = 8, nparts = 0, maxg = 0, sms = 0;
   bool gen_omega = true;
   size_t esz = 0;
-  int path = 0;          // 64, 32 (SIMT), 16 (BF16 tensor cores), 8 (FP8 tensor cores), 65 (FP64 by digit slicing)
+  int path = 0;          // 64, 32 (SIMT), 16 (BF16 tensor cores), 8 (FP8 tensor cores), 65 / 33 (FP64 / FP32 by
+                         // digit slicing on the tensor cores)
   int64_t ldw = 0;       // row stride of the generated Omega
   size_t wsz = 0;        // bytes per Omega element
   size_t off_state = 0, off_omega = 0, off_G = 0, off_Gpart = 0, off_S = 0, off_Spart = 0, off_N = 0,
@@ -78,6 +79,7 @@ struct Plan {
   size_t off_ndig = 0, off_nexp = 0, off_pdig = 0, off_pexp = 0;
   // path 65: digit slices of T(act, 0:tb) and G(perm, cols) for the tensor-core Schur GEMM
   size_t off_adig = 0, off_aexp = 0, off_bdig = 0, off_bexp = 0, off_colmax = 0;
+  size_t off_f32a = 0, off_f32ae = 0, off_f32w = 0, off_f32we = 0, off_f32rmax = 0;
   bool schur_tc = false;
   bool keep_l = false, f64_solve = false;
 };
@@ -86,6 +88,8 @@ struct Plan {
 int precision_path(const id_matrix* A, const id_opts* o) {
   if (A->dtype == ID_F64 && o->sketch_prec == ID_F64 && o->lu_prec == ID_F64) return 64;
   if (A->dtype == ID_F32 && o->sketch_prec == ID_F32 && o->lu_prec == ID_F32) return 32;
+  // FP32 input: FP32-accurate sketch on the tensor cores, LU and X in FP32
+  if (A->dtype == ID_F32 && o->sketch_prec == ID_F32_EMU && o->lu_prec == ID_F32) return 33;
   // BF16 input: sketch on the tensor cores (FP32 accumulation), LU and X in FP32
   if (A->dtype == ID_BF16 && o->sketch_prec == ID_BF16 && o->lu_prec == ID_F32) return 16;
   // FP8 input with block scales: E4M3 sketch on the tensor cores, LU and X in FP32
@@ -169,6 +173,7 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   const int s1 = path == 16   ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
                  : path == 8  ? tc_fp8_effective_splits(p->m, tc_fp8_splits(p->m, p->n, unit, p->sms))
                  : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
+                 : path == 33 ? sketch_f32emu_splits(p->m, p->n, unit, p->sms)
                               : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
   p->s1_first = p->s1_pass = p->s1_cap = s1;
   p->s2max = 8;
@@ -215,6 +220,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_pdig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(kcap) : 0);
   p->off_pexp = take(path == 65 && b <= 64 ? (size_t)kcap * 4 : 0);
   p->schur_tc = path == 65;  // used for panels of width <= 64
+  // path 33: digits of A (n rows of length m) and of each pass's Omega rows
+  p->off_f32a = take(path == 33 ? sketch_f32emu_digit_bytes(p->n, p->m) : 0);
+  p->off_f32ae = take(path == 33 ? (size_t)p->n * 4 : 0);
+  p->off_f32w = take(path == 33 ? sketch_f32emu_digit_bytes(rows_max, p->m) : 0);
+  p->off_f32we = take(path == 33 ? (size_t)rows_max * 4 : 0);
+  p->off_f32rmax = take(path == 33 ? (size_t)rows_max * 8 : 0);
   p->off_adig = take(p->schur_tc ? gemm_f64emu_digit_bytes(p->n, kcap) : 0);
   p->off_aexp = take(p->schur_tc ? (size_t)p->n * 4 : 0);
   p->off_bdig = take(p->schur_tc ? gemm_f64emu_digit_bytes(64, kcap) : 0);
@@ -289,6 +300,11 @@ class Engine {
     bdig_ = w + p.off_bdig;
     bexp_ = reinterpret_cast<int32_t*>(w + p.off_bexp);
     colmax_ = reinterpret_cast<unsigned long long*>(w + p.off_colmax);
+    f32a_ = w + p.off_f32a;
+    f32ae_ = reinterpret_cast<int32_t*>(w + p.off_f32ae);
+    f32w_ = w + p.off_f32w;
+    f32we_ = reinterpret_cast<int32_t*>(w + p.off_f32we);
+    f32rmax_ = reinterpret_cast<unsigned long long*>(w + p.off_f32rmax);
     X_ = static_cast<T*>(out->X);
     ldx_ = out->ldx;
     done_ = &st_->done;
@@ -440,6 +456,12 @@ class Engine {
     RID_TRY(tend(3));
     RID_TRY(sync_state());
     if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
+    if (p_.path == 33) {  // digits of A's columns, once per call
+      RID_TRY(tbegin(ID_PHASE_SKETCH));
+      RID_TRY(cuda(sketch_f32emu_slice((int)p_.n, (int)p_.m, reinterpret_cast<const float*>(Araw_), lda_, f32a_, p_.n,
+                                       f32ae_, nullptr, nullptr, s_)));
+      RID_TRY(tend(1));
+    }
     if (p_.path == 65) {  // column exponents and digit slices of A, once per call
       RID_TRY(tbegin(ID_PHASE_SKETCH));
       RID_TRY(cuda(f64emu_prepare(reinterpret_cast<const double*>(Araw_), lda_, p_.m, p_.n, colexp_, digits_, s_)));
@@ -465,6 +487,7 @@ class Engine {
     if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 8) return tc_fp8_effective_splits(p_.m, tc_fp8_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
+    if (p_.path == 33) return sketch_f32emu_splits(p_.m, p_.n, unit, p_.sms);
     return gemm_splits((int)p_.m, choose_splits(p_.n, unit, p_.m, p_.sms, 16));
   }
 
@@ -472,6 +495,7 @@ class Engine {
     if (p_.path == 16) return sketch_tc(row0, rows, splits);
     if (p_.path == 8) return sketch_fp8(row0, rows, splits);
     if (p_.path == 65) return sketch_emu(row0, rows, splits);
+    if (p_.path == 33) return sketch_f32emu_pass(row0, rows, splits);
     const T* Om;
     int64_t ldo;
     if (p_.gen_omega) {
@@ -555,7 +579,36 @@ class Engine {
     return 0;
   }
 
-  // FP64 A on the tensor cores: Omega rows [row0, row0+rows) on the grid 2^-10 as
+  // FP32 A on the tensor cores: the pass's Omega rows (FP32 Gaussian) sliced into 3
+  // digits, then G = Omega A from the digits of A and Omega.
+  int sketch_f32emu_pass(int64_t row0, int64_t rows, int splits) {
+    const float* Om;
+    int64_t ldo;
+    if (p_.gen_omega) {
+      RID_TRY(tbegin(ID_PHASE_OMEGA));
+      RID_TRY(cuda(gaussian_rows<float>(o_.seed, row0, rows, p_.m, reinterpret_cast<float*>(omega_), p_.m, done_, s_)));
+      RID_TRY(tend(1));
+      Om = reinterpret_cast<const float*>(omega_);
+      ldo = p_.m;
+    } else {
+      Om = static_cast<const float*>(o_.omega) + row0 * o_.ld_omega;
+      ldo = o_.ld_omega;
+    }
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    RID_TRY(cuda(sketch_f32emu_slice((int)rows, (int)p_.m, Om, ldo, f32w_, p_.ldg, f32we_, f32rmax_, done_, s_)));
+    float* out = reinterpret_cast<float*>(splits > 1 ? Gpart_ : G_);
+    RID_TRY(cuda(sketch_f32emu(p_.m, p_.n, rows, f32a_, f32ae_, f32w_, p_.ldg, f32we_, out, p_.ldg,
+                               (int64_t)p_.n * p_.ldg, splits, st_, done_, s_)));
+    if (splits > 1)
+      RID_TRY(cuda(splitk_reduce<float>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg,
+                                        reinterpret_cast<const float*>(Gpart_), reinterpret_cast<float*>(G_), done_,
+                                        s_)));
+    RID_TRY(tend(splits > 1 ? 3 : 2));
+    ++passes_;
+    return 0;
+  }
+
+  // FP64 A on the tensor cores: Omega rows [row0, row0+rows) on the grid 2^-11 as
   // two digit planes, then G = Omega A from the digit slices of A (FP64 accurate).
   int sketch_emu(int64_t row0, int64_t rows, int splits) {
     RID_TRY(tbegin(ID_PHASE_OMEGA));
@@ -741,6 +794,9 @@ class Engine {
   void *adig_, *bdig_;   // path 65: digit slices for the tensor-core Schur GEMM
   int32_t *aexp_, *bexp_;
   unsigned long long* colmax_;
+  void *f32a_, *f32w_;  // path 33: digits of A and of the pass's Omega rows
+  int32_t *f32ae_, *f32we_;
+  unsigned long long* f32rmax_;
   const int32_t* done_;
   int64_t ldx_;
   int cur_ = 0;
@@ -954,6 +1010,7 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
   *path = (A->dtype == ID_F64 && prec == ID_F64)       ? 64
           : (A->dtype == ID_F64 && prec == ID_F64_EMU) ? 65
           : (A->dtype == ID_F32 && prec == ID_F32)     ? 32
+          : (A->dtype == ID_F32 && prec == ID_F32_EMU) ? 33
           : (A->dtype == ID_BF16 && prec == ID_BF16)   ? 16
           : (A->dtype == ID_FP8_E4M3 && prec == ID_FP8_E4M3) ? 8
                                                        : 0;
@@ -964,8 +1021,12 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
   *splits = *path == 16   ? tc_sketch_effective_splits(A->m, tc_sketch_splits(A->m, A->n, rows, sms))
             : *path == 8  ? tc_fp8_effective_splits(A->m, tc_fp8_splits(A->m, A->n, rows, sms))
             : *path == 65 ? f64emu_splits(A->m, A->n, sms)
+            : *path == 33 ? sketch_f32emu_splits(A->m, A->n, rows, sms)
                           : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
   *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  if (*path == 33)  // digits and exponents of A and of Omega
+    *bytes += align_up(sketch_f32emu_digit_bytes(A->n, A->m)) + align_up((size_t)A->n * 4) +
+              align_up(sketch_f32emu_digit_bytes(rows, A->m)) + align_up((size_t)rows * 4);
   if (*path == 65) {  // digit slices of A, column exponents, two digit planes of Omega
     const size_t mp = (size_t)f64emu_pad(A->m);
     *bytes += align_up(f64emu_digit_bytes(A->m, A->n)) + align_up((size_t)A->n * 4) + align_up(2 * mp * rows * 2);
@@ -1011,6 +1072,24 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
     e = tc_sketch_fp8(A->data, A->ld, A->m, A->n, A->block_scale, omega, ld_omega, rows, out, splits > 1 ? rows : ldg,
                       zs, splits, st, nullptr, s);
+    if (e == cudaSuccess && splits > 1)
+      e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
+                                  static_cast<float*>(G), nullptr, s);
+  } else if (path == 33) {
+    unsigned char* w = static_cast<unsigned char*>(part) + (splits > 1 ? align_up((size_t)splits * A->n * rows * 4) : 0);
+    void* ad = w;
+    int32_t* ae = reinterpret_cast<int32_t*>(w + align_up(sketch_f32emu_digit_bytes(A->n, A->m)));
+    void* wd = w + align_up(sketch_f32emu_digit_bytes(A->n, A->m)) + align_up((size_t)A->n * 4);
+    int32_t* we = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(wd) +
+                                             align_up(sketch_f32emu_digit_bytes(rows, A->m)));
+    float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
+    e = sketch_f32emu_slice((int)A->n, (int)A->m, static_cast<const float*>(A->data), A->ld, ad, A->n, ae, nullptr,
+                            nullptr, s);
+    if (e == cudaSuccess)
+      e = sketch_f32emu_slice((int)rows, (int)A->m, static_cast<const float*>(omega), ld_omega, wd, rows, we, nullptr,
+                              nullptr, s);
+    if (e == cudaSuccess)
+      e = sketch_f32emu(A->m, A->n, rows, ad, ae, wd, rows, we, out, splits > 1 ? rows : ldg, zs, splits, st, nullptr, s);
     if (e == cudaSuccess && splits > 1)
       e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
                                   static_cast<float*>(G), nullptr, s);

@@ -350,14 +350,20 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
       const int r = e / bt, c = e - r * bt;
       sh.Lp[e] = c < r ? sl.S[(int64_t)sh.piv[r] * b + c] : (c == r ? T(1) : T(0));
     }
+    for (int e = tid; e < bt * bt; e += kNT) sh.Li[e] = (e / bt == e % bt) ? T(1) : T(0);
     __syncthreads();
-    if (tid < bt) {
-      const int j = tid;
-      for (int i = 0; i < bt; ++i) sh.Li[i * bt + j] = i == j ? T(1) : T(0);
-      for (int i = j + 1; i < bt; ++i) {
+    // rows in order; each column j of a row summed by 4 threads interleaved over c
+    // and a shuffle -- the summation order of the single-problem driver's k_linv
+    {
+      const int j = tid >> 2, part = tid & 3;
+      for (int i = 1; i < bt; ++i) {
         T s = T(0);
-        for (int c = j; c < i; ++c) s = fma(sh.Lp[i * bt + c], sh.Li[c * bt + j], s);
-        sh.Li[i * bt + j] = -s;
+        if (j < i)
+          for (int c = j + part; c < i; c += 4) s = fma(sh.Lp[i * bt + c], sh.Li[c * bt + j], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (j < i && part == 0) sh.Li[i * bt + j] = -s;
+        __syncthreads();
       }
     }
     if (tid < bt) sh.pivorig[tid] = sl.act[cur][sh.piv[tid]];

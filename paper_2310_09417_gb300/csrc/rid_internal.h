@@ -194,6 +194,19 @@ cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const
                         double* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
                         cudaStream_t s);
 
+// ---- FP32 sketch on the tensor cores (rid_tc_gemm64.cu, 3 digits of 8 bits per operand):
+// sketch_f32emu_slice writes the digits of `rows` rows of length K (row stride lds) into
+// `dig` (3 planes of rows_alloc x kpad(K)) with per-row exponents; sketch_f32emu forms
+// out[z] (n x rows, FP32) = split z of (W A)^T from A's digits (rows = A's n columns)
+// and W's digits.
+size_t sketch_f32emu_digit_bytes(int64_t rows, int64_t K);
+int sketch_f32emu_splits(int64_t m, int64_t n, int64_t unit_rows, int sms);
+cudaError_t sketch_f32emu_slice(int rows, int K, const float* src, int64_t lds, void* dig, int64_t rows_alloc,
+                                int32_t* ex, unsigned long long* rowmax, const int32_t* done, cudaStream_t s);
+cudaError_t sketch_f32emu(int64_t m, int64_t n, int64_t rows, const void* adig, const int32_t* aexp, const void* wdig,
+                          int64_t wrows, const int32_t* wexp, float* out, int64_t ldo, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s);
+
 // ---- the driver's cuTensorMapEncodeTiled (nullptr when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 

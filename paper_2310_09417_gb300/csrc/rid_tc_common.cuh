@@ -8,6 +8,7 @@
 // CTA frees its tensor memory or exits.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -187,6 +188,73 @@ template <int SH>
 __device__ __forceinline__ void add_scaled(long long& acc, float v) {
   const int iv = __float2int_rn(v);
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(iv), "r"(1 << SH));
+}
+
+// ------------------------------------------------------------------ digit slicing
+// Fixed-point digit slicing by integer operations on IEEE bit patterns.  For an
+// exponent e with |x| < 2^e, F = round(x 2^(8 KD - 1 - e)) (|F| < 2^(8 KD - 1)) is
+// written as KD balanced base-256 digits, most significant first:
+// x / 2^(e+1) = sum_s d_s 2^(-8(s+1)) + r, |d_s| <= 128, |r| <= 2^(-8 KD - 1).
+
+// e with |x| < 2^e for the largest |x| whose bit pattern (sign cleared) is `bits`; 0 for 0.
+__device__ __forceinline__ int exp_above_f64bits(unsigned long long bits) {
+  if (bits == 0) return 0;
+  const int E = (int)(bits >> 52);
+  if (E == 0) return -1074 + (64 - __clzll((long long)bits));  // subnormal: units of 2^-1074
+  return E - 1022;
+}
+__device__ __forceinline__ int exp_above_f32bits(unsigned int bits) {
+  if (bits == 0) return 0;
+  const int E = (int)(bits >> 23);
+  if (E == 0) return -149 + (32 - __clz((int)bits));
+  return E - 126;
+}
+
+// round(m 2^sh) for m < 2^53, to nearest even; sh <= 63 - 53 keeps it in range
+__device__ __forceinline__ unsigned long long scale_round(unsigned long long m, int sh) {
+  if (sh >= 0) return m << sh;
+  if (sh <= -64) return 0;
+  const unsigned long long q = m >> (-sh);
+  const unsigned long long r = m - (q << (-sh));
+  const unsigned long long half = 1ull << (-sh - 1);
+  return q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
+}
+
+template <int KD>
+__device__ __forceinline__ long long fixed_of(double x, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long frac = bits & ((1ull << 52) - 1);
+  if (E == 0 && frac == 0) return 0;
+  const unsigned long long m = E ? (frac | (1ull << 52)) : frac;  // x = m 2^(E' - 1075)
+  const unsigned long long a = scale_round(m, (E ? E : 1) - 1075 + 8 * KD - 1 - e);
+  return (bits >> 63) ? -(long long)a : (long long)a;
+}
+template <int KD>
+__device__ __forceinline__ long long fixed_of(float x, int e) {
+  const unsigned int bits = (unsigned int)__float_as_int(x);
+  const int E = (int)((bits >> 23) & 0xFF);
+  const unsigned long long frac = bits & ((1u << 23) - 1);
+  if (E == 0 && frac == 0) return 0;
+  const unsigned long long m = E ? (frac | (1ull << 23)) : frac;  // x = m 2^(E' - 150)
+  const unsigned long long a = scale_round(m, (E ? E : 1) - 150 + 8 * KD - 1 - e);
+  return (bits >> 31) ? -(long long)a : (long long)a;
+}
+
+// The KD digits of F at d[0], d[plane], ..., d[(KD-1) plane].
+template <int KD>
+__device__ __forceinline__ void write_digits(long long F, __nv_bfloat16* d, int64_t plane) {
+  int dg[KD];
+#pragma unroll
+  for (int s = KD - 1; s > 0; --s) {
+    long long r = F & 255;
+    if (r >= 128) r -= 256;  // balanced digit in [-128, 127]
+    dg[s] = (int)r;
+    F = (F - r) >> 8;  // exact
+  }
+  dg[0] = (int)F;  // |F| <= 128
+#pragma unroll
+  for (int s = 0; s < KD; ++s) d[s * plane] = __int2bfloat16_rn(dg[s]);
 }
 
 }  // namespace tcx

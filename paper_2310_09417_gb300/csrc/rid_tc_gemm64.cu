@@ -1,7 +1,12 @@
-// rid_tc_gemm64.cu -- an FP64-accurate GEMM on the BF16 tensor cores for the
-// Schur complement of the FP64-emulated path: P = T(act, 0:K) G(perm, cols)
-// (Alg. 1 lines 10-11 in the T = L2 L1^{-1} form), written as FP64 split-K
-// partials for the Schur finish.
+// rid_tc_gemm64.cu -- GEMMs on the BF16 tensor cores by exact digit slicing:
+//   * KD = 7 (FP64 accuracy): the Schur complement of the FP64-emulated path,
+//     P = T(act, 0:K) G(perm, cols) (Alg. 1 lines 10-11 in the T = L2 L1^{-1}
+//     form), written as FP64 split-K partials for the Schur finish;
+//   * KD = 3 (FP32 accuracy): the sketch Y = Omega A of an FP32 matrix (Sec. 2.4),
+//     FP32 split-K partials; A is sliced once per call, Omega once per pass.
+//
+// The description below is for KD = 7; KD = 3 keeps 3 digits (24 bits) per
+// operand, 6 digit pairs in 3 groups, and chunks of 320 K.
 //
 // Both operands change every round, so both are sliced here, with integer
 // operations on the FP64 bit patterns (GB300 issues about two FP64
@@ -38,19 +43,30 @@ namespace tcg {
 using namespace tcx;
 
 constexpr int kBM = 128;      // rows of A per tile
-constexpr int kBN = 32;       // columns of B per tile
 constexpr int kBK = 64;       // K per step
-constexpr int kD = 7;         // digits
-constexpr int kChunkSteps = 2;  // exact chunk: 128 K
-constexpr int kAStages = 6;
 constexpr int kThreads = 192;
-constexpr int kGroupCols = kD * kBN;  // 224 tensor-memory columns per accumulator set
+// Exact chunk: a group sums at most KD pairs of products <= 2^14, so fewer than
+// 2^24 / (KD 2^14) = 1024 / KD terms: 128 K for KD = 7, 320 K for KD = 3.
+// Columns of B per tile: two accumulator sets of KD groups fit the 512
+// tensor-memory columns.
+template <int KD>
+struct Cfg {
+  static constexpr int kBN = 32;
+  static constexpr int kAStages = 6;  // A slices in flight
+  static constexpr int kChunkSteps = (1024 / KD) / kBK;
+  static constexpr int kGroupCols = KD * kBN;  // tensor-memory columns per accumulator set
+  static constexpr uint32_t kTmemCols = 2 * kGroupCols <= 256 ? 256 : 512;
+};
 
+// Stage order (chunk c, slice s, K step j): consecutive A stages continue the same
+// rows of one digit plane (DRAM locality); B's digits of a whole chunk stay resident
+// (two chunk buffers).
+template <int KD>
 struct Smem {
-  alignas(1024) __nv_bfloat16 a[kAStages][kBM * kBK];  // 16 KB each
-  alignas(1024) __nv_bfloat16 b[2][kD][kBN * kBK];     // 2 x 7 x 4 KB
-  uint64_t a_full[kAStages];
-  uint64_t a_empty[kAStages];
+  alignas(1024) __nv_bfloat16 a[Cfg<KD>::kAStages][kBM * kBK];                          // 16 KB each
+  alignas(1024) __nv_bfloat16 b[2][Cfg<KD>::kChunkSteps][KD][Cfg<KD>::kBN * kBK];      // 4 KB each
+  uint64_t a_full[Cfg<KD>::kAStages];
+  uint64_t a_empty[Cfg<KD>::kAStages];
   uint64_t b_full[2];
   uint64_t b_empty[2];
   uint64_t acc_full[2];
@@ -58,19 +74,27 @@ struct Smem {
   uint64_t drain;
   uint32_t tmem_base;
 };
-static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_gemm_f64emu exceeds 227 KB");
+static_assert(sizeof(Smem<7>) + 1024 <= 232448, "shared memory of k_gemm_emu exceeds 227 KB");
+static_assert(sizeof(Smem<3>) + 1024 <= 232448, "shared memory of k_gemm_emu exceeds 227 KB");
 
 
 // Grid: x = column tiles of B (fastest: CTAs sharing an A tile run together), y = row
 // tiles of A, z = K splits of kchunk (a multiple of 128).  out[z]: FP64 partial
 // (M x N, row stride ldo).
+template <int KD, typename TOut>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_f64emu(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M, int N,
-                  int K, int kchunk, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
-                  double* __restrict__ out, int64_t ldo, int64_t zstride, DevState* st, const int32_t* done) {
+    k_gemm_emu(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M, int N,
+               int K, int kchunk, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+               TOut* __restrict__ out, int64_t ldo, int64_t zstride, DevState* st, const int32_t* done) {
+  constexpr int kD = KD;
+  constexpr int kBN = Cfg<KD>::kBN;
+  constexpr int kAStages = Cfg<KD>::kAStages;
+  constexpr int kChunkSteps = Cfg<KD>::kChunkSteps;
+  constexpr int kGroupCols = Cfg<KD>::kGroupCols;
+  constexpr uint32_t kTmemCols = Cfg<KD>::kTmemCols;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
-  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem<KD>& sm = *reinterpret_cast<Smem<KD>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * kBN;
   const int m0 = blockIdx.y * kBM;
@@ -87,62 +111,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sm.b_full[i], 1);
       mbar_init(&sm.b_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&sm.acc_full[i], 1);
       mbar_init(&sm.acc_empty[i], 4);
     }
     mbar_init(&sm.drain, 1);
     mbar_init_fence();
   }
-  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
+  if (warp == 1) tmem_alloc(&sm.tmem_base, kTmemCols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = sm.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: per K step, B's digits, then A's seven slices
-    int ai = 0, jb = 0;
+    // ---------------- TMA producer: per chunk, B's digits of all its K steps, then A's
+    // slices in the order (slice, K step)
+    int ai = 0, cb = 0;
     bool ok = true;
-    for (int j = 0; j < nsteps && ok; ++j) {
-      const int bb = j & 1;
-      if (j >= 2 && !mbar_wait(&sm.b_empty[bb], ((j >> 1) + 1) & 1, st)) break;
-      const int k0 = kbeg + j * kBK;
-      mbar_expect_tx(&sm.b_full[bb], kD * kBN * kBK * 2);
-      for (int t = 0; t < kD; ++t) tma_load_3d(sm.b[bb][t], &map_b, &sm.b_full[bb], k0, n0, t);
-      jb = j + 1;
-      for (int s = 0; s < kD; ++s, ++ai) {
-        const int st_ = ai % kAStages;
-        if (ai >= kAStages && !mbar_wait(&sm.a_empty[st_], ((ai / kAStages) + 1) & 1, st)) {
-          ok = false;
-          break;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int bb = c & 1;
+      if (c >= 2 && !mbar_wait(&sm.b_empty[bb], ((c >> 1) + 1) & 1, st)) break;
+      const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
+      mbar_expect_tx(&sm.b_full[bb], steps_c * kD * kBN * kBK * 2);
+      for (int jj = 0; jj < steps_c; ++jj)
+        for (int t = 0; t < kD; ++t)
+          tma_load_3d(sm.b[bb][jj][t], &map_b, &sm.b_full[bb], kbeg + (c * kChunkSteps + jj) * kBK, n0, t);
+      cb = c + 1;
+      for (int s = 0; s < kD && ok; ++s)
+        for (int jj = 0; jj < steps_c; ++jj, ++ai) {
+          const int st_ = ai % kAStages;
+          if (ai >= kAStages && !mbar_wait(&sm.a_empty[st_], ((ai / kAStages) + 1) & 1, st)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sm.a_full[st_], kBM * kBK * 2);
+          tma_load_3d(sm.a[st_], &map_a, &sm.a_full[st_], kbeg + (c * kChunkSteps + jj) * kBK, m0, s);
         }
-        mbar_expect_tx(&sm.a_full[st_], kBM * kBK * 2);
-        tma_load_3d(sm.a[st_], &map_a, &sm.a_full[st_], k0, m0, s);
-      }
     }
     // copies still in flight land before the CTA may exit
     for (int i = ai - kAStages < 0 ? 0 : ai - kAStages; i < ai; ++i)
       mbar_wait_drain(&sm.a_full[i % kAStages], (i / kAStages) & 1);
-    for (int j = jb - 2 < 0 ? 0 : jb - 2; j < jb; ++j) mbar_wait_drain(&sm.b_full[j & 1], (j >> 1) & 1);
+    for (int c = cb - 2 < 0 ? 0 : cb - 2; c < cb; ++c) mbar_wait_drain(&sm.b_full[c & 1], (c >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
     int ai = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
-      const int u = c & 1;  // accumulator set
+      const int u = c & 1;  // accumulator set and B chunk buffer
       if (c >= 2 && !mbar_wait(&sm.acc_empty[u], ((c >> 1) + 1) & 1, st)) break;
+      if (!mbar_wait(&sm.b_full[u], (c >> 1) & 1, st)) break;
       fence_after_sync();
       const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
-      for (int jj = 0; jj < steps_c && ok; ++jj) {
-        const int j = c * kChunkSteps + jj;
-        const int bb = j & 1;
-        if (!mbar_wait(&sm.b_full[bb], (j >> 1) & 1, st)) {
-          ok = false;
-          break;
-        }
-        fence_after_sync();
-        for (int s = 0; s < kD; ++s, ++ai) {
+      for (int s = 0; s < kD && ok; ++s) {
+        for (int jj = 0; jj < steps_c; ++jj, ++ai) {
           const int st_ = ai % kAStages;
           if (!mbar_wait(&sm.a_full[st_], (ai / kAStages) & 1, st)) {
             ok = false;
@@ -151,17 +175,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after_sync();
           const uint64_t da = desc_sw128(sm.a[st_]);
           for (int t = 0; t + s < kD; ++t) {
-            const uint64_t db = desc_sw128(sm.b[bb][t]);
+            const uint64_t db = desc_sw128(sm.b[u][jj][t]);
             const uint32_t dst = tmem + u * kGroupCols + (s + t) * kBN;
+            // group s + t is first written at slice 0 (t = s + t), K step 0 of the chunk
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
               mma_bf16(dst, da + 2 * kk, db + 2 * kk, idesc, (jj > 0 || s > 0 || kk > 0) ? 1u : 0u);
           }
           mma_commit(&sm.a_empty[st_]);
         }
-        if (ok) mma_commit(&sm.b_empty[bb]);
       }
-      if (ok) mma_commit(&sm.acc_full[u]);
+      if (ok) {
+        mma_commit(&sm.b_empty[u]);
+        mma_commit(&sm.acc_full[u]);
+      }
     }
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
@@ -185,6 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int cb = 0; cb < kBN; cb += 16) {
         float v[16];
+        // groups 0..2 into hi with weights 2^(8(2-g)), groups 3..6 into lo with 2^(8(6-g))
         tmem_ld16(base + 0 * kBN + cb, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) add_scaled<16>(hi[cb + i], v[i]);
@@ -194,18 +222,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16(base + 2 * kBN + cb, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) add_scaled<0>(hi[cb + i], v[i]);
-        tmem_ld16(base + 3 * kBN + cb, v);
+        if constexpr (KD > 3) {
+          tmem_ld16(base + 3 * kBN + cb, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<24>(lo[cb + i], v[i]);
-        tmem_ld16(base + 4 * kBN + cb, v);
+          for (int i = 0; i < 16; ++i) add_scaled<24>(lo[cb + i], v[i]);
+          tmem_ld16(base + 4 * kBN + cb, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<16>(lo[cb + i], v[i]);
-        tmem_ld16(base + 5 * kBN + cb, v);
+          for (int i = 0; i < 16; ++i) add_scaled<16>(lo[cb + i], v[i]);
+          tmem_ld16(base + 5 * kBN + cb, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<8>(lo[cb + i], v[i]);
-        tmem_ld16(base + 6 * kBN + cb, v);
+          for (int i = 0; i < 16; ++i) add_scaled<8>(lo[cb + i], v[i]);
+          tmem_ld16(base + 6 * kBN + cb, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<0>(lo[cb + i], v[i]);
+          for (int i = 0; i < 16; ++i) add_scaled<0>(lo[cb + i], v[i]);
+        }
       }
       fence_before_sync();
       __syncwarp();
@@ -213,69 +243,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (ok && m < M) {
       const int em = ea[m];
-      double* o = out + blockIdx.z * zstride + (int64_t)m * ldo;
+      TOut* o = out + blockIdx.z * zstride + (int64_t)m * ldo;
 #pragma unroll
       for (int i = 0; i < kBN; ++i)
-        if (n0 + i < N) o[n0 + i] = fixed_to_double(hi[i], lo[i], em + eb[n0 + i] + 2 - 64);
+        if (n0 + i < N) o[n0 + i] = (TOut)fixed_to_double(hi[i], lo[i], em + eb[n0 + i] + 2 - 64);
     }
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, kTmemCols);
   }
 }
 
 // ------------------------------------------------------------------ slicing by integer operations
-// e with |x| < 2^e for the largest |x| whose bit pattern (sign cleared) is `bits`; 0 for zero.
-__device__ __forceinline__ int exp_of_bits(unsigned long long bits) {
-  if (bits == 0) return 0;
-  const int E = (int)(bits >> 52);
-  if (E == 0) return -1074 + (64 - __clzll((long long)bits));  // subnormal: 2^-1074 units
-  return E - 1022;
-}
-
-// F = round(x 2^(55 - e)), |F| < 2^55, as seven balanced base-256 digits, most
-// significant first: x / 2^(e+1) = sum_s d_s 2^(-8(s+1)).
-__device__ __forceinline__ void digits_of(double x, int e, __nv_bfloat16* d, int64_t plane) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  const unsigned long long frac = bits & ((1ull << 52) - 1);
-  long long F = 0;
-  if (E != 0 || frac != 0) {
-    const unsigned long long m = E ? (frac | (1ull << 52)) : frac;  // x = m 2^(E' - 1075)
-    const int sh = (E ? E : 1) - 1075 + 55 - e;                      // F = m 2^sh
-    unsigned long long a;
-    if (sh >= 0) {
-      a = m << sh;  // only when x is tiny against 2^e: a < 2^55
-    } else if (sh > -64) {
-      const unsigned long long q = m >> (-sh);
-      const unsigned long long r = m - (q << (-sh));
-      const unsigned long long half = 1ull << (-sh - 1);
-      a = q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
-    } else {
-      a = 0;
-    }
-    F = (bits >> 63) ? -(long long)a : (long long)a;
-  }
-  long long dg[kD];
-#pragma unroll
-  for (int s = kD - 1; s > 0; --s) {
-    long long r = F & 255;
-    if (r >= 128) r -= 256;  // balanced digit in [-128, 127]
-    dg[s] = r;
-    F = (F - r) >> 8;  // exact
-  }
-  dg[0] = F;  // |F| <= 128
-#pragma unroll
-  for (int s = 0; s < kD; ++s) d[s * plane] = __int2bfloat16_rn((int)dg[s]);
-}
-
 // A rows: row r of the result is src[idx[r] * lds + k] for k < K (idx null: r).
 // One warp per row: the row's largest |x| (integer comparison of bit patterns),
 // then the digits D[s][r][k] (row stride Kp), zero for K <= k < Kq.
-__global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const double* __restrict__ src, int64_t lds,
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float x) {
+  return (unsigned long long)((unsigned int)__float_as_int(x) & 0x7FFFFFFFu);
+}
+__device__ __forceinline__ int exp_above(unsigned long long b, double) { return exp_above_f64bits(b); }
+__device__ __forceinline__ int exp_above(unsigned long long b, float) { return exp_above_f32bits((unsigned int)b); }
+
+template <typename T, int KD>
+__global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const T* __restrict__ src, int64_t lds,
                              const int32_t* __restrict__ idx, __nv_bfloat16* __restrict__ D, int64_t plane,
                              int32_t* __restrict__ ex, const int32_t* done) {
   if (done != nullptr && *done) return;
@@ -283,15 +279,40 @@ __global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const double* __r
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w0; r < M; r += nw) {
-    const double* row = src + (int64_t)(idx ? idx[r] : r) * lds;
+    const T* row = src + (int64_t)(idx ? idx[r] : r) * lds;
     unsigned long long mx = 0;
-    for (int k = lane; k < K; k += 32)
-      mx = max(mx, (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int k = lane; k < K; k += 32) mx = max(mx, abs_bits(row[k]));
     for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    const int e = exp_of_bits(mx);
+    const int e = exp_above(mx, T(0));
     if (lane == 0) ex[r] = e;
-    for (int k = lane; k < Kq; k += 32) digits_of(k < K ? row[k] : 0.0, e, D + r * Kp + k, plane);
+    for (int k = lane; k < Kq; k += 32)
+      write_digits<KD>(k < K ? fixed_of<KD>(row[k], e) : 0ll, D + r * Kp + k, plane);
   }
+}
+
+// The same for few, long rows: the row maxima by atomics over blocks of K (rowmax
+// starts at 0), then one thread per element.
+template <typename T>
+__global__ void k_rows_max(int M, int K, const T* __restrict__ src, int64_t lds,
+                           unsigned long long* __restrict__ rowmax, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int r = blockIdx.y;
+  unsigned long long mx = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, abs_bits(src[(int64_t)r * lds + k]));
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0 && mx != 0) atomicMax(&rowmax[r], mx);
+}
+template <typename T, int KD>
+__global__ void k_rows_digits(int M, int K, int Kq, int64_t Kp, const T* __restrict__ src, int64_t lds,
+                              const unsigned long long* __restrict__ rowmax, __nv_bfloat16* __restrict__ D,
+                              int64_t plane, int32_t* __restrict__ ex, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int r = blockIdx.y;
+  const int e = exp_above(rowmax[r], T(0));
+  if (blockIdx.x == 0 && threadIdx.x == 0) ex[r] = e;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kq; k += (int64_t)gridDim.x * blockDim.x)
+    write_digits<KD>(k < K ? fixed_of<KD>(src[(int64_t)r * lds + k], e) : 0ll, D + (int64_t)r * Kp + k, plane);
 }
 
 // B (K x N): element (k, n) = src[idx[k] * lds + off + n].  First the largest
@@ -336,17 +357,17 @@ __global__ void k_col_digits(int K, int N, int Kp, const double* __restrict__ sr
     const int n = e / kColTile, kl = e % kColTile;  // k fastest: contiguous writes
     const int k = k0 + kl;
     if (n < N && k < Kp) {
-      const int en = exp_of_bits(colmax[n]);
-      digits_of(k < K ? tile[kl][n] : 0.0, en, D + (int64_t)n * Kp + k, plane);
+      const int en = exp_above_f64bits(colmax[n]);
+      write_digits<7>(k < K ? fixed_of<7>(tile[kl][n], en) : 0ll, D + (int64_t)n * Kp + k, plane);
       if (blockIdx.x == 0 && kl == 0) ex[n] = en;
     }
   }
 }
 
-bool make_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int box_rows) {
+bool make_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int box_rows, int planes) {
   auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)kD};
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * rows * 2};
   cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -355,41 +376,84 @@ bool make_map(CUtensorMap* map, const void* base, int64_t Kp, int64_t rows, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// One launch of the digit GEMM over pre-sliced operands: A digits (KD planes of arows x
+// Kp), B digits (KD planes of brows x Kp), both K-major.
+template <int KD, typename TOut>
+cudaError_t launch(int M, int N, int K, int64_t Kp, const void* adig, int64_t arows, const int32_t* aexp,
+                   const void* bdig, int64_t brows, const int32_t* bexp, TOut* out, int64_t ldo, int64_t zstride,
+                   int splits, DevState* st, const int32_t* done, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, adig, Kp, arows, kBM, KD)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, bdig, Kp, brows, Cfg<KD>::kBN, KD)) return cudaErrorInvalidValue;
+  constexpr int chunk = Cfg<KD>::kChunkSteps * kBK;
+  const int64_t chunks = (K + chunk - 1) / chunk;
+  const int64_t per = (chunks + splits - 1) / splits;
+  const int kchunk = (int)(per * chunk);
+  const int nz = (int)((K + kchunk - 1) / kchunk);
+  if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
+  const size_t smem = sizeof(Smem<KD>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_emu<KD, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((N + Cfg<KD>::kBN - 1) / Cfg<KD>::kBN), (unsigned)((M + kBM - 1) / kBM), (unsigned)nz);
+  k_gemm_emu<KD, TOut><<<grid, kThreads, smem, s>>>(ma, mb, M, N, K, kchunk, aexp, bexp, out, ldo, zstride, st, done);
+  return cudaGetLastError();
+}
+
+// Split count over exact chunks.  One CTA per SM holds a (tile, split); its time is
+// about its chunks plus a fixed cost, so a launch takes waves x (chunks per split +
+// c0); the count (at most `cap`) minimising that is taken.
+template <int KD>
+int splits_for(int64_t M, int64_t N, int64_t K, int sms, int cap) {
+  const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + Cfg<KD>::kBN - 1) / Cfg<KD>::kBN);
+  constexpr int chunk = Cfg<KD>::kChunkSteps * kBK;
+  const int64_t chunks = (K + chunk - 1) / chunk;
+  int best = 1;
+  double best_t = 1e300;
+  for (int64_t s = 1; s <= cap && s <= chunks; ++s) {
+    const int64_t per = (chunks + s - 1) / s;
+    const int64_t eff = (chunks + per - 1) / per;
+    if (eff != s) continue;
+    const int64_t waves = (tiles * eff + sms - 1) / sms;
+    const double t = (double)waves * ((double)per + 0.5) + 0.02 * (double)eff;
+    if (t < best_t) {
+      best_t = t;
+      best = (int)eff;
+    }
+  }
+  return best;
+}
+
 }  // namespace tcg
 
 int64_t gemm_f64emu_kpad(int64_t K) { return (K + tcg::kBK - 1) / tcg::kBK * tcg::kBK; }
 size_t gemm_f64emu_digit_bytes(int64_t rows, int64_t Kmax) {
-  return (size_t)tcg::kD * rows * gemm_f64emu_kpad(Kmax) * 2;
+  return (size_t)7 * rows * gemm_f64emu_kpad(Kmax) * 2;
 }
 
 int gemm_f64emu_splits(int64_t M, int64_t N, int64_t K, int sms) {
-  const int64_t tiles = ((M + tcg::kBM - 1) / tcg::kBM) * ((N + tcg::kBN - 1) / tcg::kBN);
-  const int64_t chunks = (K + 127) / 128;
-  int64_t s = (sms + tiles - 1) / tiles;  // about one wave
-  if (s > chunks) s = chunks;
-  if (s > 8) s = 8;  // the Schur partial buffer holds 8
-  if (s < 1) s = 1;
-  const int64_t per = (chunks + s - 1) / s;
-  return (int)((chunks + per - 1) / per);
+  return tcg::splits_for<7>(M, N, K, sms, 8);  // the Schur partial buffer holds 8
 }
 
 cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const int32_t* aidx, const double* B,
                         int64_t ldb, int64_t boff, const int32_t* bidx, void* adig, int64_t arows, int32_t* aexp,
                         void* bdig, int64_t brows, int32_t* bexp, unsigned long long* colmax, int64_t kmax,
-                        double* out, int64_t ldo,
-                        int64_t zstride, int splits, DevState* st, const int32_t* done, cudaStream_t s) {
+                        double* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
+                        cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int64_t Kp = gemm_f64emu_kpad(kmax);
-  if (K > kmax || M > arows || N > brows) return cudaErrorInvalidValue;
+  if (K > kmax || M > arows || N > brows || N > tcg::kColTile) return cudaErrorInvalidValue;
   auto ad = static_cast<__nv_bfloat16*>(adig);
   auto bd = static_cast<__nv_bfloat16*>(bdig);
   const int Kq = (int)gemm_f64emu_kpad(K);  // slice only the K range in use
   int64_t g1 = ((int64_t)M * 32 + 255) / 256;
   if (g1 > 8192) g1 = 8192;
-  tcg::k_slice_rows<<<(int)g1, 256, 0, s>>>(M, K, Kq, Kp, A, lda, aidx, ad, arows * Kp, aexp, done);
+  tcg::k_slice_rows<double, 7><<<(int)g1, 256, 0, s>>>(M, K, Kq, Kp, A, lda, aidx, ad, arows * Kp, aexp, done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (N > tcg::kColTile) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(colmax, 0, (size_t)N * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int kt = (int)((K + tcg::kColTile - 1) / tcg::kColTile);
@@ -398,25 +462,50 @@ cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const
                                                                               bd, brows * Kp, bexp, done);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  CUtensorMap ma, mb;
-  if (!tcg::make_map(&ma, ad, Kp, arows, tcg::kBM)) return cudaErrorInvalidValue;
-  if (!tcg::make_map(&mb, bd, Kp, brows, tcg::kBN)) return cudaErrorInvalidValue;
-  const int64_t chunks = (K + 127) / 128;
-  const int64_t per = (chunks + splits - 1) / splits;
-  const int kchunk = (int)(per * 128);
-  const int nz = (int)((K + kchunk - 1) / kchunk);
-  if (nz != splits) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(tcg::Smem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(tcg::k_gemm_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  return tcg::launch<7, double>(M, N, K, Kp, ad, arows, aexp, bd, brows, bexp, out, ldo, zstride, splits, st, done, s);
+}
+
+// ---- FP32 sketch on the tensor cores (3 digits per operand)
+size_t sketch_f32emu_digit_bytes(int64_t rows, int64_t K) {
+  return (size_t)3 * rows * gemm_f64emu_kpad(K) * 2;
+}
+
+int sketch_f32emu_splits(int64_t m, int64_t n, int64_t unit_rows, int sms) {
+  return tcg::splits_for<3>(n, unit_rows, m, sms, 32);
+}
+
+cudaError_t sketch_f32emu_slice(int rows, int K, const float* src, int64_t lds, void* dig, int64_t rows_alloc,
+                                int32_t* ex, unsigned long long* rowmax, const int32_t* done, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (rows > rows_alloc) return cudaErrorInvalidValue;
+  const int64_t Kp = gemm_f64emu_kpad(K);
+  auto d = static_cast<__nv_bfloat16*>(dig);
+  if (rows >= 1024 || rowmax == nullptr || rows > 65535) {  // many rows: one warp per row
+    int64_t g = ((int64_t)rows * 32 + 255) / 256;
+    if (g > 8192) g = 8192;
+    tcg::k_slice_rows<float, 3><<<(int)g, 256, 0, s>>>(rows, K, (int)Kp, Kp, src, lds, nullptr, d, rows_alloc * Kp,
+                                                       ex, done);
+    return cudaGetLastError();
   }
-  dim3 grid((unsigned)((N + tcg::kBN - 1) / tcg::kBN), (unsigned)((M + tcg::kBM - 1) / tcg::kBM), (unsigned)nz);
-  tcg::k_gemm_f64emu<<<grid, tcg::kThreads, smem, s>>>(ma, mb, M, N, K, kchunk, aexp, bexp, out, ldo, zstride, st,
-                                                        done);
+  // few long rows (a pass of Omega): blocks along K for every row
+  cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)rows * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int64_t bx = (Kp + 255) / 256;
+  if (bx > 64) bx = 64;
+  tcg::k_rows_max<float><<<dim3((unsigned)bx, (unsigned)rows), 256, 0, s>>>(rows, K, src, lds, rowmax, done);
+  tcg::k_rows_digits<float, 3><<<dim3((unsigned)bx, (unsigned)rows), 256, 0, s>>>(rows, K, (int)Kp, Kp, src, lds,
+                                                                                  rowmax, d, rows_alloc * Kp, ex,
+                                                                                  done);
   return cudaGetLastError();
+}
+
+cudaError_t sketch_f32emu(int64_t m, int64_t n, int64_t rows, const void* adig, const int32_t* aexp, const void* wdig,
+                          int64_t wrows, const int32_t* wexp, float* out, int64_t ldo, int64_t zstride, int splits,
+                          DevState* st, const int32_t* done, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (rows > wrows) return cudaErrorInvalidValue;
+  return tcg::launch<3, float>((int)n, (int)rows, (int)m, gemm_f64emu_kpad(m), adig, n, aexp, wdig, wrows, wexp, out,
+                               ldo, zstride, splits, st, done, s);
 }
 
 }  // namespace rid

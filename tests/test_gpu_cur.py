@@ -42,8 +42,14 @@ def test_cur_from_id_matches_oracle(B, orc, m, n, tol, dtype):
         # C = W C(I,:) to rounding, like the oracle's
         assert np.linalg.norm(C - Wg @ C[I.cpu().numpy()]) <= 1e-10 * np.linalg.norm(C)
     else:
-        overlap = len(set(I.cpu().numpy()) & set(r["J"])) / k
+        # FP32: the leading (well-separated) row skeletons agree with the FP64 LUPP's;
+        # late pivots sit at the FP32 rounding floor of C and are not compared
+        h = k // 2
+        overlap = len(set(I.cpu().numpy()[:h]) & set(r["J"][:h])) / h
         assert overlap >= 0.9
+        Wg = Wm.double().cpu().numpy()
+        np.testing.assert_array_equal(Wg[I.cpu().numpy()], np.eye(k))
+        assert np.linalg.norm(C - Wg @ C[I.cpu().numpy()]) <= 1e-3 * np.linalg.norm(C)
     # two-sided ID: A ~ W A(I,J) X, as accurate as the column ID (up to a modest factor)
     Ii = I.cpu().numpy()
     X = g.X.double().cpu().numpy()

@@ -113,3 +113,56 @@ def test_bf16_generated_omega_runs_and_meets_tolerance(B, orc):
     A64 = Ab.double().cpu().numpy()
     e = orc.id_residual(A64, g.J.cpu().numpy(), g.X.double().cpu().numpy()) / orc.fro_norm(A64)
     assert g.k >= r and e <= 2e-2
+
+
+# ---------------------------------------------------------------- FP32 sketch by digit slicing
+@pytest.mark.parametrize("m,n,rows", [
+    (1024, 256, 64),     # whole tiles
+    (1000, 333, 100),    # ragged K, n and rows (four 32-column tiles)
+    (8, 5, 3),           # smaller than every tile
+    (40000, 300, 64),    # long K: many exact chunks and split-K partials
+    (3000, 1100, 200),
+])
+def test_f32emu_sketch_matches_fp64_product(B, m, n, rows):
+    """sketch_prec F32_EMU: A and Omega (FP32) in 3 digits of 8 bits each on the
+    tensor cores.  Against the FP64 product of the same FP32 values: FP32-level
+    error relative to |Omega| |A|."""
+    rng = np.random.default_rng(m + 2 * n + rows)
+    A = (rng.standard_normal((m, n)) * np.exp2(rng.integers(-6, 7, size=(1, n)))).astype(np.float32)
+    Om = rng.standard_normal((rows, m)).astype(np.float32)
+    Ad = B.colmajor(torch.from_numpy(A).cuda())
+    G = B.id_sketch(Ad, torch.from_numpy(Om).cuda(), sketch_prec=B.F32_EMU).double().cpu().numpy()
+    ref = (Om.astype(np.float64) @ A.astype(np.float64)).T
+    scale = (np.abs(Om).astype(np.float64) @ np.abs(A).astype(np.float64)).T
+    err = (np.abs(G - ref) / scale).max()
+    assert err < 2e-6, err
+
+
+def test_f32emu_adaptive_against_f64_oracle(B, orc):
+    """The FP32 sketch on the tensor cores with FP32 LU: the rank matches the FP64
+    oracle's within one block, the skeletons overlap almost entirely and the
+    achieved error is within 1.2x of the oracle's."""
+    m, n, b = 1200, 800, 32
+    A = W.spectral_matrix(m, n, W.spectrum("poly", n), seed=12).astype(np.float32)
+    Om = W.gaussian_omega(13, orc.rows_needed(n, b), m).astype(np.float32)
+    tol = 1e-4
+    g = B.id_adaptive(B.colmajor(torch.from_numpy(A).cuda()), tol, block=b, omega=torch.from_numpy(Om).cuda(),
+                      sketch_prec=B.F32_EMU)
+    A64 = A.astype(np.float64)
+    r = orc.id_adaptive(A64, Om.astype(np.float64), b, tol * orc.fro_norm(A64))
+    assert abs(g.k - r["k"]) <= b
+    kk = min(g.k, r["k"])
+    assert len(set(g.J.cpu().numpy()[:kk]) & set(r["J"][:kk])) / kk >= 0.95
+    eg = orc.id_residual(A64, g.J.cpu().numpy(), g.X.cpu().numpy().astype(np.float64))
+    eo = orc.id_residual(A64, r["J"], r["X"])
+    assert eg <= 1.2 * eo and eg <= 3 * tol * orc.fro_norm(A64)
+
+
+def test_f32emu_pass_size_does_not_change_result(B):
+    m, n, b = 2100, 600, 32
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=30.0), seed=5).astype(np.float32)
+    Ad = B.colmajor(torch.from_numpy(A).cuda())
+    base = B.id_adaptive(Ad, 1e-4, block=b, seed=11, sketch_prec=B.F32_EMU)
+    for kw in (dict(k0=100), dict(blocks_per_pass=3)):
+        g = B.id_adaptive(Ad, 1e-4, block=b, seed=11, sketch_prec=B.F32_EMU, **kw)
+        assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X)

@@ -245,7 +245,8 @@ __global__ void k_colexp(const double* __restrict__ A, int64_t lda, int64_t m, i
   }
 }
 
-// Digits: D[s][j][i] (slice-major, each slice column-major m_pad x n) of A(i, j).
+// Digits: D[s][j][i] (slice-major, each slice column-major m_pad x n) of A(i, j),
+// by integer operations on the FP64 bit patterns (x / 2^(E_j+1) = sum_s d_s 2^(-8(s+1))).
 __global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_t m, int64_t m_pad, int64_t n,
                                const int32_t* __restrict__ E, __nv_bfloat16* __restrict__ D) {
   const int64_t total = m_pad * n;
@@ -253,14 +254,7 @@ __global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / m_pad, i = e - j * m_pad;
-    double x = i < m ? ldexp(A[i + j * lda], -(E[j] + 1)) : 0.0;  // |x| < 1/2
-#pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-      const double t = x * 256.0;  // exact
-      const double d = rint(t);    // |d| <= 128
-      x = t - d;                   // exact, |x| <= 1/2
-      D[s * slice + e] = __double2bfloat16(d);
-    }
+    write_digits<kSlices>(i < m ? fixed_of<kSlices>(A[i + j * lda], E[j]) : 0ll, D + e, slice);
   }
 }
 

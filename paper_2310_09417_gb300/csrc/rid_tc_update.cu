@@ -37,7 +37,8 @@ constexpr int kBM = 128;    // rows of T per tile
 constexpr int kBN = 64;     // columns of T per tile
 constexpr int kK = 64;      // padded K (one 128-byte swizzle row of BF16)
 constexpr int kD = 7;       // digits per operand
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;  // two per tensor-memory lane quarter, 32 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct Smem {
   alignas(1024) __nv_bfloat16 n[kD][kBM * kK];     // 7 x 16 KB
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.p_empty[b], 1);
     }
     mbar_init(&sm.t_full, 1);
-    mbar_init(&sm.t_empty, 4);
+    mbar_init(&sm.t_empty, kEpiWarps);
     mbar_init(&sm.drain, 1);
     mbar_init_fence();
   }
@@ -129,19 +130,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
   } else if (warp >= 2) {
-    // ---------------- epilogue
+    // ---------------- epilogue: lanes = rows of the tile, each warp 32 of its 64 columns
+    const int ew = warp - 2;
     const int quarter = warp & 3;
+    const int half = ew >> 2;
     const int r = m0 + quarter * 32 + lane;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * 32;
     const bool live = r < na && pivmark[r] == 0;
     double* xrow = live ? X + (int64_t)act[r] * ldx : nullptr;
     const int er = live ? nexp[r] : 0;
     for (int u = 0; u < my; ++u) {
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + half * 32;
+      // bring this row's 32 entries of T towards L2 while the MMAs run
+      if (live && c0 < tb) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(xrow + c0));
+        if (c0 + 16 < tb) asm volatile("prefetch.global.L2 [%0];" ::"l"(xrow + c0 + 16));
+      }
       if (!mbar_wait(&sm.t_full, u & 1, st)) break;
       fence_after_sync();
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
 #pragma unroll 1
-      for (int cb = 0; cb < kBN; cb += 16) {
+      for (int cb = 0; cb < 32; cb += 16) {
         long long hi[16], lo[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;

@@ -391,6 +391,7 @@ class Engine {
   int run_panel(const T* src, int64_t m_src, int64_t n_src, int64_t ld_src, const int64_t* J) {
     RID_TRY(tbegin(ID_PHASE_OTHER));
     RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
+    panel_par_ = 0;  // both barrier counters were cleared
     RID_TRY(cuda(gather_panel<T>(src, ld_src, m_src, n_src, J, p_.k, G_, st_, s_)));
     RID_TRY(tend(2));
     int64_t tb = 0, na = p_.n;
@@ -445,6 +446,7 @@ class Engine {
   int start() {
     RID_TRY(tbegin(ID_PHASE_OTHER));
     RID_TRY(cuda(init_state(st_, act_[0], pivmark_, p_.n, s_)));
+    panel_par_ = 0;  // both barrier counters were cleared
     if (p_.path == 8)
       RID_TRY(cuda(norm2_fp8(p_.m, p_.n, Araw_, lda_, scale_, normp_, p_.nparts, st_, s_)));
     else if (p_.path == 16)
@@ -674,8 +676,9 @@ class Engine {
     const int64_t lds = p_.wmax;
     RID_TRY(tbegin(ID_PHASE_LU));
     PanelCfg cfg = panel_config<T>((int)na, (int)w, p_.maxg);
-    RID_TRY(cuda(panel_lupp<T>(cfg, (int)na, (int)w, (int)bt, S_, lds, piv_, pivmark_, pivdiag_, cand_v_, cand_i_,
-                               cand_rows_, st_, s_)));
+    RID_TRY(cuda(panel_lupp<T>(cfg, (int)na, (int)w, (int)bt, panel_par_, S_, lds, piv_, pivmark_, pivdiag_,
+                               cand_v_, cand_i_, cand_rows_, st_, s_)));
+    panel_par_ ^= 1;
     RID_TRY(tend(1));
     RID_TRY(tbegin(ID_PHASE_UPDATE));
     int nl = 3;
@@ -807,6 +810,7 @@ class Engine {
   int32_t x_f64_ = 0;
   int64_t predicted_ = 0;
   int32_t passes_ = 0;
+  int panel_par_ = 0;  // barrier counter of the next panel launch (alternates)
   int64_t launches_ = 0;
   double phase_ms_[kNumPhases];
   int64_t phase_launches_[kNumPhases];

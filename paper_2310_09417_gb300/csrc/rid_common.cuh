@@ -27,9 +27,9 @@ struct DevState {
   int32_t rounds;         // estimates computed
   uint32_t err;           // kErr* bits
   uint32_t zero_pivots;   // exactly zero pivot columns met
-  uint32_t bar_count;     // grid barrier: arrivals
-  uint32_t bar_gen;       // grid barrier: generation
+  uint32_t bar[2];        // grid-barrier arrival counters, one per launch parity
   uint32_t pad[5];
+  unsigned long long pkey[2][3][2];  // LUPP panel: pivot-key maxima, [launch parity][step mod 3][key]
 };
 static_assert(sizeof(DevState) <= 256, "DevState must fit its 256-byte slot");
 
@@ -56,25 +56,31 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // Upper bound on any single device-side wait (nanoseconds).
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after kWaitLimitNs the block records kErrTimeout and the
-// barrier returns false; callers then leave the kernel.  Returns true when
-// every block arrived.
-__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks) {
+__device__ __forceinline__ void red_max_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident) on an
+// arrival counter that starts at 0 for the launch: the k-th barrier (k = 0, 1,
+// ...) of the launch returns once (k+1) nblocks arrivals were counted.  Thread 0
+// of each block adds its arrival with release semantics (covering the block's
+// writes, ordered before it by the block barrier) and polls with acquire loads;
+// no reset and no second round trip.  The wait is bounded: after kWaitLimitNs
+// the block records kErrTimeout and the barrier returns false; callers then
+// leave the kernel.  Returns true when every block arrived.
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, DevState* st) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    unsigned gen = ld_acquire_u32(&st->bar_gen);
-    unsigned arrived = atom_add_acqrel_u32(&st->bar_count, 1u) + 1u;
-    if (arrived == nblocks) {
-      st->bar_count = 0u;
-      st_release_u32(&st->bar_gen, gen + 1u);
-    } else {
-      uint64_t t0 = globaltimer_ns();
+    red_release_add_u32(ctr, 1u);
+    if ((int)(ld_acquire_u32(ctr) - target) < 0) {
+      const uint64_t t0 = globaltimer_ns();
       unsigned spins = 0;
-      while (ld_acquire_u32(&st->bar_gen) == gen) {
+      while ((int)(ld_acquire_u32(ctr) - target) < 0) {
         if ((++spins & 255u) == 0u) {
           if (ld_acquire_u32(&st->err) & kErrTimeout) { ok = 0; break; }
           if (globaltimer_ns() - t0 > kWaitLimitNs) {
@@ -85,7 +91,6 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks) {
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -83,8 +83,11 @@ struct PanelCfg {
 };
 template <typename T>
 PanelCfg panel_config(int na, int w, int num_sms);
+// Rows per block and shared memory of the panel kernel for a given block count.
 template <typename T>
-cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, T* S, int64_t lds,
+PanelCfg panel_layout(int na, int w, int grid);
+template <typename T>
+cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T* S, int64_t lds,
                        int32_t* piv, int32_t* pivmark, double* pivdiag, double* cand_v,
                        int32_t* cand_i, T* cand_rows, DevState* st, cudaStream_t s);
 

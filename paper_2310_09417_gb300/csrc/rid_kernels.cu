@@ -351,160 +351,291 @@ cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_
 
 // ============================================================ LUPP panel
 // One cooperative launch factors S (na x w) for `steps` pivots.  Block b owns
-// rows [b*chunk, min(na, (b+1)*chunk)), staged in shared memory when they fit.
-// Each pivot step: block-local argmax of |S(i,c)| over unselected rows (ties
-// to the smallest row index = smallest column index of A, since `act` is
-// ascending), publication of (value, row, row contents) in a double-buffered
-// candidate slot, one bounded grid barrier, a redundant global argmax in
-// every block, then division by the pivot and the rank-1 update (Eq. lupps)
-// of the block's unselected rows.  Rows are marked, never swapped.
+// rows [b*chunk, min(na, (b+1)*chunk)), staged in shared memory (row stride
+// w + 1: column reads hit distinct banks) when they fit.  Each pivot step:
+// block-local argmax of |S(i,c)| over unselected rows (ties to the smallest row
+// index = smallest column index of A, since `act` is ascending), publication of
+// the block's candidate, one bounded grid barrier, the global pivot and its
+// row, then division by the pivot and the rank-1 update (Eq. lupps) of the
+// block's unselected rows.  Rows are marked, never swapped.
+//
+// The global pivot comes from two 64-bit atomic maxima that every block adds
+// before the barrier: (top, ~row) and (top, row), top = the leading 32 bits of
+// |S(i,c)|'s pattern.  The first names the smallest row among the candidates of
+// largest top; when the second names the same row no other candidate shares
+// that top, and the row is the exact argmax.  Otherwise (FP64 candidates equal
+// in their leading 32 bits) every block compares the published full patterns.
+// For FP32 the top is the whole pattern and the first key is exact.  A step thus
+// costs the barrier and two L2 round trips on one or two lines, whatever the
+// number of blocks.  Key slots rotate over three steps (block 0 clears the next
+// one before it arrives at a barrier: every block has read the slot two steps
+// back) and alternate between launches like the barrier counter (block 0 clears
+// the other launch's slots).
 constexpr int kPanelThreads = 256;
-constexpr int kPanelRowsDefault = 32;
 constexpr int kPanelMaxW = 128;
+
+// Pivot search key: |S(i,c)| by its IEEE bit pattern (sign cleared; the order of
+// the patterns is the order of the values), then the smaller row index: the
+// largest key wins.  lo = ~row (never 0 for a row), so {0, 0} is "no candidate".
+// Integer comparisons only (GB300 issues about two FP64 instructions per clock
+// per SM).
+struct PivKey {
+  unsigned long long hi;
+  unsigned lo;
+};
+__device__ __forceinline__ PivKey key_pick(PivKey a, PivKey b) {
+  return (b.hi > a.hi || (b.hi == a.hi && b.lo > a.lo)) ? b : a;
+}
+__device__ __forceinline__ PivKey warp_key_max(PivKey a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    PivKey o;
+    o.hi = __shfl_xor_sync(0xffffffffu, a.hi, off);
+    o.lo = __shfl_xor_sync(0xffffffffu, a.lo, off);
+    a = key_pick(a, o);
+  }
+  return a;
+}
+// Block-wide key maximum (every thread gets it); blockDim.x a multiple of 32.
+__device__ __forceinline__ PivKey block_key_max(PivKey a) {
+  __shared__ unsigned long long s_hi[32];
+  __shared__ unsigned s_lo[32];
+  a = warp_key_max(a);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_hi[wid] = a.hi;
+    s_lo[wid] = a.lo;
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  PivKey b;
+  b.hi = lane < nw ? s_hi[lane] : 0ull;
+  b.lo = lane < nw ? s_lo[lane] : 0u;
+  b = warp_key_max(b);  // every warp reduces the same values
+  __syncthreads();      // s_hi / s_lo are reused by the next call
+  return b;
+}
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long mag_bits(float x) {
+  return (unsigned long long)((unsigned)__float_as_int(x) & 0x7FFFFFFFu);
+}
+__device__ __forceinline__ unsigned mag_top(unsigned long long hi, double) { return (unsigned)(hi >> 31); }
+__device__ __forceinline__ unsigned mag_top(unsigned long long hi, float) { return (unsigned)hi; }
 
 template <typename T>
 __global__ void __launch_bounds__(kPanelThreads)
-    k_panel_lupp(int na, int w, int steps, T* __restrict__ S, int64_t lds, int chunk, int use_smem,
+    k_panel_lupp(int na, int w, int steps, T* __restrict__ S, int64_t lds, int chunk, int use_smem, int par,
                  int32_t* piv, int32_t* pivmark, double* pivdiag, double* cand_v, int32_t* cand_i,
                  T* cand_rows, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T prow[kPanelMaxW];
-  if (st->done) return;  // set before the launch or never during it: uniform over the grid
+  __shared__ int s_piv;
   const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  if (bid == 0 && tid < 6) (&st->pkey[par ^ 1][0][0])[tid] = 0ull;  // the previous launch has ended
+  if (bid == 0 && tid == 0) st->bar[par ^ 1] = 0u;
+  if (st->done) return;  // set before the launch or never during it: uniform over the grid
+  unsigned* ctr = &st->bar[par];
+  unsigned long long* cand_k = reinterpret_cast<unsigned long long*>(cand_v);
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int r0 = bid * chunk;
   const int nr = max(0, min(na, r0 + chunk) - r0);
   T* Ss = use_smem ? reinterpret_cast<T*>(smem_raw) : S + (int64_t)r0 * lds;
-  const int64_t ldl = use_smem ? w : lds;
-  unsigned char* sel = smem_raw + (use_smem ? (size_t)chunk * w * sizeof(T) : 0);
+  const int64_t ldl = use_smem ? w + 1 : lds;
+  unsigned char* sel = smem_raw + (use_smem ? (size_t)chunk * (w + 1) * sizeof(T) : 0);
 
   if (use_smem)
     for (int e = tid; e < nr * w; e += blockDim.x) {
       const int r = e / w, c = e - r * w;
-      Ss[e] = S[(int64_t)(r0 + r) * lds + c];
+      Ss[(int64_t)r * ldl + c] = S[(int64_t)(r0 + r) * lds + c];
     }
   for (int r = tid; r < chunk; r += blockDim.x) sel[r] = 0;
   __syncthreads();
 
   for (int c = 0; c < steps; ++c) {
     // 1. block-local candidate
-    ArgMax loc;
-    loc.v = -1.0;
-    loc.idx = -1;
+    PivKey loc{0ull, 0u};
     for (int r = tid; r < nr; r += blockDim.x)
-      if (!sel[r]) {
-        ArgMax o;
-        o.v = (double)tabs(Ss[(int64_t)r * ldl + c]);
-        o.idx = r0 + r;
-        loc = argmax_pick(loc, o);
-      }
-    loc = block_argmax(loc);
-    // 2. publish it
-    const int slot = (c & 1) * nb + bid;
+      if (!sel[r]) loc = key_pick(loc, PivKey{mag_bits(Ss[(int64_t)r * ldl + c]), ~(unsigned)(r0 + r)});
+    loc = block_key_max(loc);
+    const int lidx = loc.lo == 0u ? -1 : (int)~loc.lo;
+    // 2. publish it: the key maxima, the full pattern and the row
+    const int base = (c & 1) * nb;
+    unsigned long long* key = &st->pkey[par][c % 3][0];
     if (tid == 0) {
-      __stcg(&cand_v[slot], loc.v);
-      __stcg(&cand_i[slot], loc.idx);
-    }
-    if (loc.idx >= 0) {
-      const T* src = Ss + (int64_t)(loc.idx - r0) * ldl;
-      for (int cc = tid; cc < w; cc += blockDim.x) __stcg(&cand_rows[(int64_t)slot * w + cc], src[cc]);
-    }
-    __threadfence();
-    // 3. wait for every block
-    if (!grid_barrier(st, (unsigned)nb)) return;
-    // 4. global pivot, computed identically by every block
-    ArgMax g;
-    g.v = -1.0;
-    g.idx = -1;
-    for (int q = tid; q < nb; q += blockDim.x) {
-      ArgMax o;
-      o.v = __ldcg(&cand_v[(c & 1) * nb + q]);
-      o.idx = __ldcg(&cand_i[(c & 1) * nb + q]);
-      g = argmax_pick(g, o);
-    }
-    g = block_argmax(g);
-    const int pblk = g.idx / chunk;
-    for (int cc = tid; cc < w; cc += blockDim.x)
-      prow[cc] = __ldcg(&cand_rows[(int64_t)((c & 1) * nb + pblk) * w + cc]);
-    const bool zero = !(g.v > 0.0);
-    if (tid == 0) {
-      if (g.idx >= r0 && g.idx < r0 + nr) sel[g.idx - r0] = (unsigned char)1;
       if (bid == 0) {
-        piv[c] = g.idx;
-        if (pivdiag != nullptr) pivdiag[c] = g.v;
-        if (zero) atomicAdd(&st->zero_pivots, 1u);
+        unsigned long long* next = &st->pkey[par][(c + 1) % 3][0];
+        next[0] = 0ull;
+        next[1] = 0ull;
+      }
+      if (lidx >= 0) {
+        const unsigned long long top = mag_top(loc.hi, T(0));
+        red_max_u64(&key[0], (top << 32) | (unsigned long long)loc.lo);
+        red_max_u64(&key[1], (top << 32) | (unsigned long long)(unsigned)lidx);
+      }
+      __stcg(&cand_k[base + bid], loc.hi);
+      __stcg(&cand_i[base + bid], lidx);
+    }
+    if (lidx >= 0) {
+      const T* src = Ss + (int64_t)(lidx - r0) * ldl;
+      for (int cc = tid; cc < w; cc += blockDim.x) __stcg(&cand_rows[(int64_t)(base + bid) * w + cc], src[cc]);
+    }
+    // 3. wait for every block
+    if (!grid_barrier(ctr, (unsigned)(c + 1) * (unsigned)nb, st)) return;
+    // 4. global pivot (warp 0 of every block, identically) and its row
+    if (wid == 0) {
+      const unsigned long long k0 = __ldcg(&key[0]), k1 = __ldcg(&key[1]);
+      int gi = k0 == 0ull ? -1 : (int)~(unsigned)k0;
+      if (gi >= 0 && sizeof(T) == 8 && (int)(unsigned)k1 != gi) {
+        // candidates tie in their leading 32 bits: compare the full patterns
+        PivKey g{0ull, 0u};
+        for (int q = lane; q < nb; q += 32) {
+          const int i = __ldcg(&cand_i[base + q]);
+          const unsigned long long h = __ldcg(&cand_k[base + q]);
+          if (i >= 0) g = key_pick(g, PivKey{h, ~(unsigned)i});
+        }
+        g = warp_key_max(g);
+        gi = (int)~g.lo;
+      }
+      if (gi >= 0) {
+        const int pblk = gi / chunk;  // the block that published row gi
+        for (int cc = lane; cc < w; cc += 32) prow[cc] = __ldcg(&cand_rows[(int64_t)(base + pblk) * w + cc]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        s_piv = gi;
+        const T pv = gi >= 0 ? prow[c] : T(0);
+        if (gi >= r0 && gi < r0 + nr) sel[gi - r0] = (unsigned char)1;
+        if (bid == 0) {
+          piv[c] = gi;
+          if (pivdiag != nullptr) pivdiag[c] = (double)tabs(pv);
+          if (pv == T(0)) atomicAdd(&st->zero_pivots, 1u);
+        }
       }
     }
     __syncthreads();
-    if (zero) continue;  // the column is exactly zero below: nothing to eliminate
+    const T pv = s_piv >= 0 ? prow[c] : T(0);
+    if (pv == T(0)) continue;  // the column is exactly zero below: nothing to eliminate
     // 5. multipliers l(i) = S(i,c) / pivot
-    const T pv = prow[c];
     for (int r = tid; r < nr; r += blockDim.x)
       if (!sel[r]) Ss[(int64_t)r * ldl + c] = Ss[(int64_t)r * ldl + c] / pv;
     __syncthreads();
-    // 6. rank-1 update of the trailing columns (Eq. lupps)
-    const int wc = w - c - 1;
-    if (wc > 0)
-      for (int e = tid; e < nr * wc; e += blockDim.x) {
-        const int r = e / wc, cc = c + 1 + (e - r * wc);
-        if (!sel[r]) {
-          T* row = Ss + (int64_t)r * ldl;
-          row[cc] = fma(-row[c], prow[cc], row[cc]);
+    // 6. rank-1 update of the trailing columns (Eq. lupps): a warp per row, lanes
+    //    along the row, four rows at a time with their loads ahead of the stores
+    if (c + 1 < w) {
+      T p[kPanelMaxW / 32];
+#pragma unroll
+      for (int j = 0; j < kPanelMaxW / 32; ++j) {
+        const int cc = c + 1 + lane + 32 * j;
+        p[j] = cc < w ? prow[cc] : T(0);
+      }
+      for (int r = wid; r < nr; r += 4 * nw) {
+        T* rp[4];
+        T l[4];
+        bool live[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int rr = r + u * nw;
+          live[u] = rr < nr && !sel[rr];
+          rp[u] = Ss + (int64_t)(live[u] ? rr : 0) * ldl;
+          l[u] = live[u] ? rp[u][c] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kPanelMaxW / 32; ++j) {
+          const int cc = c + 1 + lane + 32 * j;
+          if (cc < w) {
+            T x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = live[u] ? rp[u][cc] : T(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (live[u]) rp[u][cc] = fma(-l[u], p[j], x[u]);
+          }
         }
       }
+    }
     __syncthreads();
   }
   if (use_smem)
     for (int e = tid; e < nr * w; e += blockDim.x) {
       const int r = e / w, c = e - r * w;
-      S[(int64_t)(r0 + r) * lds + c] = Ss[e];
+      S[(int64_t)(r0 + r) * lds + c] = Ss[(int64_t)r * ldl + c];
     }
   for (int r = tid; r < nr; r += blockDim.x) pivmark[r0 + r] = sel[r];
 }
 
-// Rows per block of the panel: fewer, larger blocks make the per-pivot grid
-// barrier cheaper (one atomic arrival per block) while each block's rows still
-// fit in shared memory.  RANDID_PANEL_ROWS overrides the minimum (tuning).
-static int panel_min_rows() {
-  static int rows = -1;
-  if (rows < 0) {
-    rows = kPanelRowsDefault;
-    if (const char* env = getenv("RANDID_PANEL_ROWS")) {
+// Blocks of the panel: one per SM, at least 32 rows each, and enough for the
+// rows of a block to fit in shared memory.  With the key exchange a step's
+// barrier and round trips cost about the same for any number of blocks (measured
+// on GB300: 3.2 - 5.3 us per pivot for 4000 - 20000 rows, FP32 and FP64 alike,
+// fastest with the most blocks), so the rows are spread as thin as possible.
+// RANDID_PANEL_BLOCKS fixes the count (tuning).
+static int panel_blocks_env() {
+  static int blocks = -1;
+  if (blocks < 0) {
+    blocks = 0;
+    if (const char* env = getenv("RANDID_PANEL_BLOCKS")) {
       const int v = atoi(env);
-      if (v >= 1 && v <= 4096) rows = v;
+      if (v >= 1 && v <= 1024) blocks = v;
     }
   }
-  return rows;
+  return blocks;
 }
 
 template <typename T>
+PanelCfg panel_layout(int na, int w, int grid);
+
+template <typename T>
 PanelCfg panel_config(int na, int w, int num_sms) {
+  const size_t budget = (size_t)200 * 1024;
+  const int fit = (int)(budget / ((size_t)(w + 1) * sizeof(T) + 1));  // rows staged in shared memory
+  const int need = (na + fit - 1) / fit;
+  int most = (na + 31) / 32;
+  if (most > num_sms) most = num_sms;
+  if (most < 1) most = 1;
+  int grid = panel_blocks_env();
+  if (grid == 0) grid = most;
+  if (grid < need) grid = need;
+  if (grid > most) grid = most;
+  return panel_layout<T>(na, w, grid);
+}
+
+// Rows per block and shared memory for a given block count: rows staged at
+// stride w + 1, then one selection byte per row (16-byte padded).
+static size_t panel_smem_bytes(int chunk, int w, size_t esz, bool staged) {
+  const size_t sel_bytes = ((size_t)chunk + 15) & ~(size_t)15;
+  return (staged ? (size_t)chunk * (w + 1) * esz : 0) + sel_bytes;
+}
+
+template <typename T>
+PanelCfg panel_layout(int na, int w, int grid) {
   PanelCfg cfg;
-  int min_rows = panel_min_rows();
-  const int fit = (int)((size_t)200 * 1024 / ((size_t)w * sizeof(T) + 1));  // rows staged in shared memory
-  if (min_rows > fit) min_rows = fit < 32 ? 32 : fit;
-  int grid = (na + min_rows - 1) / min_rows;
-  if (grid > num_sms) grid = num_sms;
   if (grid < 1) grid = 1;
+  if (na < 1) na = 1;
   int chunk = (na + grid - 1) / grid;
   grid = (na + chunk - 1) / chunk;
   cfg.grid = grid;
   cfg.chunk = chunk;
-  const size_t rows_bytes = (size_t)chunk * w * sizeof(T);
-  const size_t sel_bytes = ((size_t)chunk + 15) & ~(size_t)15;
-  cfg.use_smem = (rows_bytes + sel_bytes) <= (size_t)200 * 1024;
-  cfg.smem = (cfg.use_smem ? rows_bytes : 0) + sel_bytes;
+  cfg.use_smem = panel_smem_bytes(chunk, w, sizeof(T), true) <= (size_t)201 * 1024;
+  cfg.smem = panel_smem_bytes(chunk, w, sizeof(T), cfg.use_smem != 0);
   return cfg;
 }
 
 template <typename T>
-cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, T* S, int64_t lds, int32_t* piv,
+cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T* S, int64_t lds, int32_t* piv,
                        int32_t* pivmark, double* pivdiag, double* cand_v, int32_t* cand_i, T* cand_rows,
                        DevState* st, cudaStream_t s) {
   static size_t cached = 0;
+  if (w > kPanelMaxW || (par != 0 && par != 1)) return cudaErrorInvalidValue;
+  // the kernel addresses chunk rows at stride w + 1 and the selection bytes after them
+  if (cfg.chunk < 1 || (int64_t)cfg.chunk * cfg.grid < na ||
+      cfg.smem < panel_smem_bytes(cfg.chunk, w, sizeof(T), cfg.use_smem != 0))
+    return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem(k_panel_lupp<T>, cfg.smem, &cached);
   if (e != cudaSuccess) return e;
   int chunk = cfg.chunk, use_smem = cfg.use_smem;
-  void* args[] = {&na, &w, &steps, &S, &lds, &chunk, &use_smem, &piv, &pivmark,
+  void* args[] = {&na, &w, &steps, &S, &lds, &chunk, &use_smem, &par, &piv, &pivmark,
                   &pivdiag, &cand_v, &cand_i, &cand_rows, &st};
   return cudaLaunchCooperativeKernel((const void*)k_panel_lupp<T>, dim3(cfg.grid), dim3(kPanelThreads), args,
                                      cfg.smem, s);
@@ -738,8 +869,9 @@ __global__ void k_init_state(DevState* st, int32_t* act, int32_t* pivmark, int64
     st->rounds = 0;
     st->err = 0u;
     st->zero_pivots = 0u;
-    st->bar_count = 0u;
-    st->bar_gen = 0u;
+    st->bar[0] = 0u;
+    st->bar[1] = 0u;
+    for (int q = 0; q < 12; ++q) (&st->pkey[0][0][0])[q] = 0ull;
   }
   if (i < n) {
     act[i] = (int32_t)i;
@@ -768,7 +900,8 @@ cudaError_t init_state(DevState* st, int32_t* act, int32_t* pivmark, int64_t n, 
   template cudaError_t schur_finish<T>(int, int, const int32_t*, const T*, int64_t, int64_t, int, int64_t,  \
                                        const T*, T*, int64_t, double*, int, const int32_t*, cudaStream_t);  \
   template PanelCfg panel_config<T>(int, int, int);                                                         \
-  template cudaError_t panel_lupp<T>(const PanelCfg&, int, int, int, T*, int64_t, int32_t*, int32_t*,       \
+  template PanelCfg panel_layout<T>(int, int, int);                                                         \
+  template cudaError_t panel_lupp<T>(const PanelCfg&, int, int, int, int, T*, int64_t, int32_t*, int32_t*,       \
                                      double*, double*, int32_t*, T*, DevState*, cudaStream_t);              \
   template cudaError_t linv<T>(int, const T*, int64_t, const int32_t*, T*, const int32_t*, cudaStream_t);   \
   template cudaError_t make_n<T>(int, int, const T*, int64_t, const T*, const int32_t*, const int32_t*, T*, \

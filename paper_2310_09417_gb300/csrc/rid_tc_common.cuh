@@ -151,6 +151,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // (hi 2^32 + lo) 2^ex as a double, rounded to nearest even, assembled with integer
 // operations (GB300 issues about two FP64 instructions per clock per SM).
 // hi, lo: any int64 values; results outside the normal range take the FP64 route.
@@ -181,6 +191,23 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
   if (e <= 0 || e >= 2047) return ldexp((double)hi + ldexp((double)lo, -32), ex + 32);
   return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)e << 52) |
                                           (mant & ((1ull << 52) - 1))));
+}
+
+// w 2^ex as a double, rounded to nearest even, by integer operations on the bit
+// pattern (|w| < 2^63); results outside the normal range take the FP64 route.
+__device__ __forceinline__ double i64_to_double(long long w, int ex) {
+  if (w == 0) return 0.0;
+  const unsigned long long sgn = w < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long u = w < 0 ? 0ull - (unsigned long long)w : (unsigned long long)w;
+  const int lz = __clzll((long long)u);
+  const unsigned long long nrm = u << lz;  // bit 63 set
+  unsigned long long mant = nrm >> 11;     // 53 bits, leading one at bit 52
+  const unsigned rem = (unsigned)(nrm & 0x7ffull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const int e = 1023 + 63 - lz + ex;  // biased exponent of the leading one
+  if (e <= 0 || e >= 2046) return ldexp((double)w, ex);
+  // the leading one (bit 52 of mant) adds 1 to the field; a carry to 2^53 adds one more
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(e - 1) << 52) + mant)));
 }
 
 // acc += v * 2^SH, exact (v an integer-valued float below 2^24 in magnitude)

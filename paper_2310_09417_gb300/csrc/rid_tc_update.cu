@@ -8,16 +8,20 @@
 // seven balanced 8-bit digits (|d| <= 128, exact in BF16, 56 bits).  The digit
 // products of equal weight 2^(-8(g+2)), g = s + t <= 6, share FP32 group g in
 // tensor memory (7 groups x 64 columns); a group sums at most 7 pairs x 64 terms
-// of magnitude <= 2^14 (< 2^23): exact.  The epilogue folds the groups into two
-// int64 values, scales by 2^(e_i + f_c + 2 - 32) and subtracts from T in FP64.
-// Dropped pairs (g >= 7) and digit remainders bound each entry's error by about
-// 2^-46 max_q|N(i,q)| max_q|P(q,c)| -- the order of an FP64 dot product of
-// length 64 (64 u).
+// of magnitude <= 2^14 (< 2^23): exact.  The epilogue folds the groups into one
+// int64 W = sum_g G_g 2^(8(5-g)) (group 6 rounded to units of 2^8, |W| < 2^61),
+// converts W 2^(e_i + f_c + 2 - 56) to FP64 by integer operations and subtracts it
+// from T (one FP64 instruction per entry).  Dropped pairs (g >= 7) and digit
+// remainders bound each entry's error by about 2^-46 max_q|N(i,q)| max_q|P(q,c)|
+// -- the order of an FP64 dot product of length 64 (64 u); the fold adds at most
+// 2^-55 of that scale.
 //
 //   warp 0    TMA: the row tile's digits of N once, then P's digits per column
 //             tile (double-buffered)
 //   warp 1    tensor memory; 28 x 4 MMAs (M = 128, N = 64, K = 16) per tile
-//   warps 2-5 epilogue: one row each lane, 16 columns at a time
+//   warps 2-17 epilogue: one row each lane, four warps per lane quarter, 16
+//             columns each; T's entries are loaded before the accumulators are
+//             read and the accumulators are released before the conversion
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -37,7 +41,7 @@ constexpr int kBM = 128;    // rows of T per tile
 constexpr int kBN = 64;     // columns of T per tile
 constexpr int kK = 64;      // padded K (one 128-byte swizzle row of BF16)
 constexpr int kD = 7;       // digits per operand
-constexpr int kEpiWarps = 8;  // two per tensor-memory lane quarter, 32 columns each
+constexpr int kEpiWarps = 16;  // four per tensor-memory lane quarter, 16 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct Smem {
@@ -130,62 +134,72 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
   } else if (warp >= 2) {
-    // ---------------- epilogue: lanes = rows of the tile, each warp 32 of its 64 columns
+    // ---------------- epilogue: lanes = rows of the tile, each warp 16 of its 64 columns
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = ew >> 2;
+    const int part = ew >> 2;  // 0..3
     const int r = m0 + quarter * 32 + lane;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * 32;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + part * 16;
     const bool live = r < na && pivmark[r] == 0;
     double* xrow = live ? X + (int64_t)act[r] * ldx : nullptr;
     const int er = live ? nexp[r] : 0;
     for (int u = 0; u < my; ++u) {
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + half * 32;
-      // bring this row's 32 entries of T towards L2 while the MMAs run
-      if (live && c0 < tb) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(xrow + c0));
-        if (c0 + 16 < tb) asm volatile("prefetch.global.L2 [%0];" ::"l"(xrow + c0 + 16));
-      }
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * 16;
+      // lane j < 16 holds the column exponent of column c0 + j
+      const int pe = (lane < 16 && c0 + lane < tb) ? pexp[c0 + lane] : 0;
+      // this row's 16 entries of T, in flight while the MMAs run and the
+      // accumulators are read
+      double xv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) xv[i] = (live && c0 + i < tb) ? xrow[c0 + i] : 0.0;
       if (!mbar_wait(&sm.t_full, u & 1, st)) break;
       fence_after_sync();
-#pragma unroll 1
-      for (int cb = 0; cb < 32; cb += 16) {
-        long long hi[16], lo[16];
+      // W = sum_g G_g 2^(8 (5 - g)) with G_6 rounded to units of 2^8: |W| < 2^61,
+      // the rounding below 2^-55 of 2^(e_i + f_c); W's unit is 2^(e_i + f_c + 2 - 56).
+      // Two halves of 8 columns keep the fold within the register budget.
 #pragma unroll
-        for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
-        float v[16];
-        tmem_ld16(lane_base + 0 * kBN + cb, v);
+      for (int h = 0; h < 2; ++h) {
+        long long w[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<16>(hi[i], v[i]);
-        tmem_ld16(lane_base + 1 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) w[i] = 0;
+        float v[8];
+        tmem_ld8(lane_base + 0 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<8>(hi[i], v[i]);
-        tmem_ld16(lane_base + 2 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
+        tmem_ld8(lane_base + 1 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<0>(hi[i], v[i]);
-        tmem_ld16(lane_base + 3 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
+        tmem_ld8(lane_base + 2 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<24>(lo[i], v[i]);
-        tmem_ld16(lane_base + 4 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) {
+          add_scaled<0>(w[i], v[i]);
+          w[i] <<= 24;  // |w| < 2^37 before the shift
+        }
+        tmem_ld8(lane_base + 3 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<16>(lo[i], v[i]);
-        tmem_ld16(lane_base + 5 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
+        tmem_ld8(lane_base + 4 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<8>(lo[i], v[i]);
-        tmem_ld16(lane_base + 6 * kBN + cb, v);
+        for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
+        tmem_ld8(lane_base + 5 * kBN + 8 * h, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) add_scaled<0>(lo[i], v[i]);
-        if (live) {
+        for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
+        tmem_ld8(lane_base + 6 * kBN + 8 * h, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = c0 + cb + i;
-            if (c < tb) xrow[c] -= fixed_to_double(hi[i], lo[i], er + pexp[c] + 2 - 64);
-          }
+        for (int i = 0; i < 8; ++i) w[i] += __float2int_rn(v[i] * 0x1.0p-8f);
+        if (h == 1) {
+          // the accumulators are free for the next tile's MMAs
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm.t_empty);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int c = c0 + 8 * h + i;
+          const int ec = __shfl_sync(0xffffffffu, pe, 8 * h + i);
+          if (live && c < tb) xrow[c] = xv[8 * h + i] - i64_to_double(w[i], er + ec + 2 - 56);
         }
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.t_empty);
     }
   }
   fence_before_sync();
@@ -197,10 +211,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------ digit slicing
-__device__ __forceinline__ int exp_above(double mx) {  // e with mx < 2^e (0 for 0)
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  return e;
+// Both slicers work on the IEEE bit patterns with integer operations: the row (or
+// column) exponent from the largest pattern, then F = round(x 2^(55 - e)) and its
+// seven balanced digits.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
 // N (na x bt, row stride bt): one warp per row; digits D[s][i][q] (q < 64, zero-padded).
@@ -213,20 +236,11 @@ __global__ void k_slice_n(int na, int bt, const double* __restrict__ N, __nv_bfl
   for (int64_t i = w0; i < na; i += nw) {
     const double a0 = lane < bt ? N[i * bt + lane] : 0.0;
     const double a1 = lane + 32 < bt ? N[i * bt + lane + 32] : 0.0;
-    double mx = fmax(fabs(a0), fabs(a1));
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    const int e = exp_above(mx);
+    const unsigned long long mb = warp_max_u64(max(abs_bits(a0), abs_bits(a1)));
+    const int e = exp_above_f64bits(mb);
     if (lane == 0) nexp[i] = e;
-    double x0 = ldexp(a0, -(e + 1)), x1 = ldexp(a1, -(e + 1));
-#pragma unroll
-    for (int s = 0; s < kD; ++s) {
-      const double t0 = x0 * 256.0, t1 = x1 * 256.0;  // exact
-      const double d0 = rint(t0), d1 = rint(t1);      // |d| <= 128
-      x0 = t0 - d0;
-      x1 = t1 - d1;
-      D[s * plane + i * kK + lane] = __double2bfloat16(d0);
-      D[s * plane + i * kK + lane + 32] = __double2bfloat16(d1);
-    }
+    write_digits<kD>(fixed_of<kD>(a0, e), D + i * kK + lane, plane);
+    write_digits<kD>(fixed_of<kD>(a1, e), D + i * kK + lane + 32, plane);
   }
 }
 
@@ -242,20 +256,11 @@ __global__ void k_slice_p(int bt, int tb, const double* __restrict__ X, int64_t 
   for (int64_t c = w0; c < tb; c += nw) {
     const double a0 = lane < bt ? X[(int64_t)prow[lane] * ldx + c] : 0.0;
     const double a1 = lane + 32 < bt ? X[(int64_t)prow[lane + 32] * ldx + c] : 0.0;
-    double mx = fmax(fabs(a0), fabs(a1));
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    const int e = exp_above(mx);
+    const unsigned long long mb = warp_max_u64(max(abs_bits(a0), abs_bits(a1)));
+    const int e = exp_above_f64bits(mb);
     if (lane == 0) pexp[c] = e;
-    double x0 = ldexp(a0, -(e + 1)), x1 = ldexp(a1, -(e + 1));
-#pragma unroll
-    for (int t = 0; t < kD; ++t) {
-      const double t0 = x0 * 256.0, t1 = x1 * 256.0;
-      const double d0 = rint(t0), d1 = rint(t1);
-      x0 = t0 - d0;
-      x1 = t1 - d1;
-      D[t * plane + c * kK + lane] = __double2bfloat16(d0);
-      D[t * plane + c * kK + lane + 32] = __double2bfloat16(d1);
-    }
+    write_digits<kD>(fixed_of<kD>(a0, e), D + c * kK + lane, plane);
+    write_digits<kD>(fixed_of<kD>(a1, e), D + c * kK + lane + 32, plane);
   }
 }
 
@@ -304,7 +309,7 @@ cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t
   }
   const int rt = (na + tcu::kBM - 1) / tcu::kBM;
   const int ct = (tb + tcu::kBN - 1) / tcu::kBN;
-  int gy = (sms + rt - 1) / rt;  // about one CTA per SM in all
+  int gy = sms / rt;  // at most one CTA per SM in all (one wave)
   if (gy > ct) gy = ct;
   if (gy < 1) gy = 1;
   tcu::k_update_f64emu<<<dim3((unsigned)rt, (unsigned)gy), tcu::kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act,

@@ -81,6 +81,7 @@ struct Plan {
   size_t off_adig = 0, off_aexp = 0, off_bdig = 0, off_bexp = 0, off_colmax = 0;
   size_t off_f32a = 0, off_f32ae = 0, off_f32w = 0, off_f32we = 0, off_f32rmax = 0;
   bool schur_tc = false;
+  bool update_tc = false;
   bool keep_l = false, f64_solve = false;
 };
 
@@ -215,11 +216,19 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // path 65: the 8 digit slices of A and its column exponents
   p->off_digits = take(path == 65 ? f64emu_digit_bytes(p->m, p->n) : 0);
   p->off_colexp = take(path == 65 ? (size_t)p->n * 4 : 0);
-  p->off_ndig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(p->n) : 0);
-  p->off_nexp = take(path == 65 && b <= 64 ? (size_t)p->n * 4 : 0);
-  p->off_pdig = take(path == 65 && b <= 64 ? update_f64emu_digit_bytes(kcap) : 0);
-  p->off_pexp = take(path == 65 && b <= 64 ? (size_t)kcap * 4 : 0);
-  p->schur_tc = path == 65;  // used for panels of width <= 64
+  // the Schur complement and the block update on the tensor cores: 7 digits for the
+  // FP64-emulated path, 3 for every FP32 LU (panels and blocks of width <= 64)
+  const bool emu7 = path == 65, emu3 = e == 4;
+  p->update_tc = (emu7 || emu3) && b <= 64;
+  const size_t udig = emu7 ? update_f64emu_digit_bytes(1) : update_f32emu_digit_bytes(1);
+  p->off_ndig = take(p->update_tc ? udig * (size_t)p->n : 0);
+  p->off_nexp = take(p->update_tc ? (size_t)p->n * 4 : 0);
+  p->off_pdig = take(p->update_tc ? udig * (size_t)kcap : 0);
+  p->off_pexp = take(p->update_tc ? (size_t)kcap * 4 : 0);
+  // The Schur GEMM's K runs over every earlier pivot: per-row fixed point keeps the
+  // FP64 accuracy with 7 digits, but with 3 it loses FP32's relative accuracy on
+  // the small late pivot rows, so FP32 LUs keep the SIMT GEMM there.
+  p->schur_tc = emu7;  // used for panels of width <= 64
   // path 33: digits of A (n rows of length m) and of each pass's Omega rows
   p->off_f32a = take(path == 33 ? sketch_f32emu_digit_bytes(p->n, p->m) : 0);
   p->off_f32ae = take(path == 33 ? (size_t)p->n * 4 : 0);
@@ -692,13 +701,15 @@ class Engine {
                            pivorig_, done_, s_)));
     if (tb > 0) {
       bool done_tc = false;
-      if constexpr (std::is_same<T, double>::value) {
-        if (p_.path == 65 && p_.b <= 64) {  // FP64-accurate on the tensor cores
+      if (p_.update_tc) {  // FP64- or FP32-accurate on the tensor cores
+        if constexpr (std::is_same<T, double>::value)
           RID_TRY(cuda(update_f64emu((int)na, (int)bt, (int)tb, N_, act_[cur_], pivmark_, pivorig_, X_, ldx_, ndig_,
                                      nexp_, p_.n, pdig_, pexp_, p_.ldl, p_.sms, st_, done_, s_)));
-          nl += 3;
-          done_tc = true;
-        }
+        else
+          RID_TRY(cuda(update_f32emu((int)na, (int)bt, (int)tb, N_, act_[cur_], pivmark_, pivorig_, X_, ldx_, ndig_,
+                                     nexp_, p_.n, pdig_, pexp_, p_.ldl, p_.sms, st_, done_, s_)));
+        nl += 3;
+        done_tc = true;
       }
       if (!done_tc) {
         Operand<T> a{N_, bt, nullptr, 0};

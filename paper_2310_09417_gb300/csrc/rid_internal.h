@@ -179,6 +179,12 @@ cudaError_t quantize_fp8(int dtype, int64_t m, int64_t n, const void* A, int64_t
 // bt <= 64).  ndig / pdig hold update_f64emu_digit_bytes(nrows / prows) bytes, nexp / pexp
 // nrows / prows exponents.
 size_t update_f64emu_digit_bytes(int64_t rows);
+size_t update_f32emu_digit_bytes(int64_t rows);
+// The same for FP32 T with 3 digits per operand (FP32-accurate).
+cudaError_t update_f32emu(int na, int bt, int tb, const float* N, const int32_t* act, const int32_t* pivmark,
+                          const int32_t* pivorig, float* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
+                          void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
+                          cudaStream_t s);
 cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t* act, const int32_t* pivmark,
                           const int32_t* pivorig, double* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
                           void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,

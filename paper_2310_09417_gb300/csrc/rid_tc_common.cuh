@@ -210,6 +210,23 @@ __device__ __forceinline__ double i64_to_double(long long w, int ex) {
   return __longlong_as_double((long long)(sgn | (((unsigned long long)(e - 1) << 52) + mant)));
 }
 
+// w 2^ex as a float, rounded to nearest even, by integer operations (|w| < 2^63);
+// results outside the normal range take the FP32 route.
+__device__ __forceinline__ float i64_to_float(long long w, int ex) {
+  if (w == 0) return 0.0f;
+  const unsigned sgn = w < 0 ? 0x80000000u : 0u;
+  const unsigned long long u = w < 0 ? 0ull - (unsigned long long)w : (unsigned long long)w;
+  const int lz = __clzll((long long)u);
+  const unsigned long long nrm = u << lz;               // bit 63 set
+  unsigned mant = (unsigned)(nrm >> 40);                // 24 bits, leading one at bit 23
+  const unsigned long long rem = nrm & ((1ull << 40) - 1);
+  const unsigned long long half = 1ull << 39;
+  mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
+  const int e = 127 + 63 - lz + ex;  // biased exponent of the leading one
+  if (e <= 0 || e >= 254) return ldexpf((float)w, ex);
+  return __uint_as_float(sgn | (((unsigned)(e - 1) << 23) + mant));
+}
+
 // acc += v * 2^SH, exact (v an integer-valued float below 2^24 in magnitude)
 template <int SH>
 __device__ __forceinline__ void add_scaled(long long& acc, float v) {

@@ -319,7 +319,8 @@ __global__ void k_rows_digits(int M, int K, int Kq, int64_t Kp, const T* __restr
 // |B(:, n)| bit pattern per column (blocks over K, n fastest for coalesced reads,
 // atomicMax into colmax, which starts at 0) ...
 constexpr int kColTile = 64;
-__global__ void k_col_max(int K, int N, const double* __restrict__ src, int64_t lds, int64_t off,
+template <typename T>
+__global__ void k_col_max(int K, int N, const T* __restrict__ src, int64_t lds, int64_t off,
                           const int32_t* __restrict__ idx, unsigned long long* __restrict__ colmax,
                           const int32_t* done) {
   if (done != nullptr && *done) return;
@@ -328,8 +329,7 @@ __global__ void k_col_max(int K, int N, const double* __restrict__ src, int64_t 
   unsigned long long mx = 0;
   if (n < N)
     for (int k = blockIdx.x * kColTile + kl; k < min(K, (int)(blockIdx.x + 1) * kColTile); k += 4)
-      mx = max(mx, (unsigned long long)__double_as_longlong(src[(int64_t)idx[k] * lds + off + n]) &
-                       0x7FFFFFFFFFFFFFFFull);
+      mx = max(mx, abs_bits(src[(int64_t)idx[k] * lds + off + n]));
   red[threadIdx.x] = mx;
   __syncthreads();
   if (kl == 0 && n < N) {
@@ -340,25 +340,26 @@ __global__ void k_col_max(int K, int N, const double* __restrict__ src, int64_t 
 
 // ... then the digits, one block per 64 rows of K: the tile goes through shared
 // memory so that digit writes D[t][n][k] are contiguous in k.
-__global__ void k_col_digits(int K, int N, int Kp, const double* __restrict__ src, int64_t lds, int64_t off,
+template <typename T, int KD>
+__global__ void k_col_digits(int K, int N, int Kp, const T* __restrict__ src, int64_t lds, int64_t off,
                              const int32_t* __restrict__ idx, const unsigned long long* __restrict__ colmax,
                              __nv_bfloat16* __restrict__ D, int64_t plane, int32_t* __restrict__ ex,
                              const int32_t* done) {
   if (done != nullptr && *done) return;
-  __shared__ double tile[kColTile][kColTile + 1];
+  __shared__ T tile[kColTile][kColTile + 1];
   const int k0 = blockIdx.x * kColTile;
   for (int e = threadIdx.x; e < kColTile * kColTile; e += blockDim.x) {
     const int kl = e / kColTile, n = e % kColTile;
     const int k = k0 + kl;
-    tile[kl][n] = (k < K && n < N) ? src[(int64_t)idx[k] * lds + off + n] : 0.0;
+    tile[kl][n] = (k < K && n < N) ? src[(int64_t)idx[k] * lds + off + n] : T(0);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < kColTile * kColTile; e += blockDim.x) {
     const int n = e / kColTile, kl = e % kColTile;  // k fastest: contiguous writes
     const int k = k0 + kl;
     if (n < N && k < Kp) {
-      const int en = exp_above_f64bits(colmax[n]);
-      write_digits<7>(k < K ? fixed_of<7>(tile[kl][n], en) : 0ll, D + (int64_t)n * Kp + k, plane);
+      const int en = exp_above(colmax[n], T(0));
+      write_digits<KD>(k < K ? fixed_of<KD>(tile[kl][n], en) : 0ll, D + (int64_t)n * Kp + k, plane);
       if (blockIdx.x == 0 && kl == 0) ex[n] = en;
     }
   }
@@ -438,31 +439,44 @@ int gemm_f64emu_splits(int64_t M, int64_t N, int64_t K, int sms) {
   return tcg::splits_for<7>(M, N, K, sms, 8);  // the Schur partial buffer holds 8
 }
 
-cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const int32_t* aidx, const double* B,
-                        int64_t ldb, int64_t boff, const int32_t* bidx, void* adig, int64_t arows, int32_t* aexp,
-                        void* bdig, int64_t brows, int32_t* bexp, unsigned long long* colmax, int64_t kmax,
-                        double* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
-                        cudaStream_t s) {
+namespace tcg {
+// Slice A's gathered rows and B's gathered columns, then one digit GEMM.
+template <typename T, int KD>
+cudaError_t gemm_emu_gather(int M, int N, int K, const T* A, int64_t lda, const int32_t* aidx, const T* B,
+                            int64_t ldb, int64_t boff, const int32_t* bidx, void* adig, int64_t arows, int32_t* aexp,
+                            void* bdig, int64_t brows, int32_t* bexp, unsigned long long* colmax, int64_t kmax,
+                            T* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
+                            cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int64_t Kp = gemm_f64emu_kpad(kmax);
-  if (K > kmax || M > arows || N > brows || N > tcg::kColTile) return cudaErrorInvalidValue;
+  if (K > kmax || M > arows || N > brows || N > kColTile) return cudaErrorInvalidValue;
   auto ad = static_cast<__nv_bfloat16*>(adig);
   auto bd = static_cast<__nv_bfloat16*>(bdig);
   const int Kq = (int)gemm_f64emu_kpad(K);  // slice only the K range in use
   int64_t g1 = ((int64_t)M * 32 + 255) / 256;
   if (g1 > 8192) g1 = 8192;
-  tcg::k_slice_rows<double, 7><<<(int)g1, 256, 0, s>>>(M, K, Kq, Kp, A, lda, aidx, ad, arows * Kp, aexp, done);
+  k_slice_rows<T, KD><<<(int)g1, 256, 0, s>>>(M, K, Kq, Kp, A, lda, aidx, ad, arows * Kp, aexp, done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(colmax, 0, (size_t)N * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const int kt = (int)((K + tcg::kColTile - 1) / tcg::kColTile);
-  tcg::k_col_max<<<kt, 256, 0, s>>>(K, N, B, ldb, boff, bidx, colmax, done);
-  tcg::k_col_digits<<<(Kq + tcg::kColTile - 1) / tcg::kColTile, 256, 0, s>>>(K, N, (int)Kp, B, ldb, boff, bidx, colmax,
-                                                                              bd, brows * Kp, bexp, done);
+  const int kt = (int)((K + kColTile - 1) / kColTile);
+  k_col_max<T><<<kt, 256, 0, s>>>(K, N, B, ldb, boff, bidx, colmax, done);
+  k_col_digits<T, KD><<<(Kq + kColTile - 1) / kColTile, 256, 0, s>>>(K, N, (int)Kp, B, ldb, boff, bidx, colmax, bd,
+                                                                      brows * Kp, bexp, done);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return tcg::launch<7, double>(M, N, K, Kp, ad, arows, aexp, bd, brows, bexp, out, ldo, zstride, splits, st, done, s);
+  return launch<KD, T>(M, N, K, Kp, ad, arows, aexp, bd, brows, bexp, out, ldo, zstride, splits, st, done, s);
+}
+}  // namespace tcg
+
+cudaError_t gemm_f64emu(int M, int N, int K, const double* A, int64_t lda, const int32_t* aidx, const double* B,
+                        int64_t ldb, int64_t boff, const int32_t* bidx, void* adig, int64_t arows, int32_t* aexp,
+                        void* bdig, int64_t brows, int32_t* bexp, unsigned long long* colmax, int64_t kmax,
+                        double* out, int64_t ldo, int64_t zstride, int splits, DevState* st, const int32_t* done,
+                        cudaStream_t s) {
+  return tcg::gemm_emu_gather<double, 7>(M, N, K, A, lda, aidx, B, ldb, boff, bidx, adig, arows, aexp, bdig, brows,
+                                         bexp, colmax, kmax, out, ldo, zstride, splits, st, done, s);
 }
 
 // ---- FP32 sketch on the tensor cores (3 digits per operand)

@@ -1,27 +1,34 @@
-// rid_tc_update.cu -- the FP64 block update of the interpolation coefficients,
+// rid_tc_update.cu -- the block update of the interpolation coefficients,
 // T(rest, old) -= N T(piv, old) (re-blocking, Alg. 1 lines 14-17, in the
-// T = L2 L1^{-1} form), on the BF16 tensor cores by exact digit slicing.
+// T = L2 L1^{-1} form), on the BF16 tensor cores by exact digit slicing, for
+// FP64 T (KD = 7 digits per operand) and FP32 T (KD = 3).
 //
 // K = bt <= 64.  Each row i of N gets an exponent e_i (max_q |N(i,q)| < 2^e_i) and
 // each column c of P = T(piv, old) an exponent f_c (max_q |P(q,c)| < 2^f_c).
 // N(i,:) / 2^(e_i+1) and P(:,c) / 2^(f_c+1) lie in (-1/2, 1/2) and are written as
-// seven balanced 8-bit digits (|d| <= 128, exact in BF16, 56 bits).  The digit
-// products of equal weight 2^(-8(g+2)), g = s + t <= 6, share FP32 group g in
-// tensor memory (7 groups x 64 columns); a group sums at most 7 pairs x 64 terms
-// of magnitude <= 2^14 (< 2^23): exact.  The epilogue folds the groups into one
-// int64 W = sum_g G_g 2^(8(5-g)) (group 6 rounded to units of 2^8, |W| < 2^61),
-// converts W 2^(e_i + f_c + 2 - 56) to FP64 by integer operations and subtracts it
-// from T (one FP64 instruction per entry).  Dropped pairs (g >= 7) and digit
-// remainders bound each entry's error by about 2^-46 max_q|N(i,q)| max_q|P(q,c)|
-// -- the order of an FP64 dot product of length 64 (64 u); the fold adds at most
-// 2^-55 of that scale.
+// KD balanced 8-bit digits (|d| <= 128, exact in BF16: 56 bits for KD = 7, 24 for
+// KD = 3).  The digit products of equal weight 2^(-8(g+2)), g = s + t < KD, share
+// FP32 group g in tensor memory (KD groups x 64 columns); a group sums at most KD
+// pairs x 64 terms of magnitude <= 2^14 (< 2^23): exact.
+//   KD = 7: the epilogue folds the groups into one int64 W = sum_g G_g 2^(8(5-g))
+//     (group 6 rounded to units of 2^8, |W| < 2^61), converts W 2^(e_i + f_c + 2 -
+//     56) to FP64 by integer operations and subtracts it from T (one FP64
+//     instruction per entry).  Dropped pairs (g >= 7) and digit remainders bound
+//     each entry's error by about 2^-46 max_q|N(i,q)| max_q|P(q,c)| -- the order
+//     of an FP64 dot product of length 64 (64 u); the fold adds at most 2^-55 of
+//     that scale.
+//   KD = 3: W = G_0 2^16 + G_1 2^8 + G_2 (|W| < 2^38) is rounded to FP32 and
+//     scaled by 2^(e_i + f_c + 2 - 32); dropped pairs (g >= 3) and remainders bound
+//     the error by about 2^-18 max_q|N(i,q)| max_q|P(q,c)|, the order of an FP32
+//     dot product of length 64.
 //
 //   warp 0    TMA: the row tile's digits of N once, then P's digits per column
-//             tile (double-buffered)
-//   warp 1    tensor memory; 28 x 4 MMAs (M = 128, N = 64, K = 16) per tile
-//   warps 2-17 epilogue: one row each lane, four warps per lane quarter, 16
-//             columns each; T's entries are loaded before the accumulators are
-//             read and the accumulators are released before the conversion
+//             tile (double-buffered for KD = 3, single for KD = 7)
+//   warp 1    tensor memory; KD(KD+1)/2 x 4 MMAs (M = 128, N = 64, K = 16) per tile
+//   warps 2-17 epilogue: four warps per lane quarter, 16 columns each; the
+//             accumulators are read with one row per lane and released before
+//             the stores, T is read (before the accumulators are ready) and
+//             written coalesced, the products passing through shared memory
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -40,13 +47,22 @@ using namespace tcx;
 constexpr int kBM = 128;    // rows of T per tile
 constexpr int kBN = 64;     // columns of T per tile
 constexpr int kK = 64;      // padded K (one 128-byte swizzle row of BF16)
-constexpr int kD = 7;       // digits per operand
 constexpr int kEpiWarps = 16;  // four per tensor-memory lane quarter, 16 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
+// P's digit tiles are double-buffered for KD = 3; for KD = 7 one buffer leaves room
+// for the epilogue's staging (the next tile's P loads while the epilogue works).
+template <int KD>
+__host__ __device__ constexpr int p_buffers() {
+  return KD == 7 ? 1 : 2;
+}
+
+template <int KD, typename TX>
 struct Smem {
-  alignas(1024) __nv_bfloat16 n[kD][kBM * kK];     // 7 x 16 KB
-  alignas(1024) __nv_bfloat16 p[2][kD][kBN * kK];  // 2 x 7 x 8 KB
+  alignas(1024) __nv_bfloat16 n[KD][kBM * kK];                  // KD x 16 KB
+  alignas(1024) __nv_bfloat16 p[p_buffers<KD>()][KD][kBN * kK];  // KD x 8 KB each
+  TX stage[kEpiWarps][32][9];  // per warp: 32 rows x 8 columns (+1 against bank conflicts)
+  TX* rows[kEpiWarps][32];     // per warp: T's row of each of its 32 rows (null: not updated)
   uint64_t n_full;
   uint64_t p_full[2];
   uint64_t p_empty[2];
@@ -55,18 +71,79 @@ struct Smem {
   uint64_t drain;
   uint32_t tmem_base;
 };
+static_assert(sizeof(Smem<7, double>) + 1024 <= 232448, "shared memory of k_update_emu exceeds 227 KB");
+static_assert(sizeof(Smem<3, float>) + 1024 <= 232448, "shared memory of k_update_emu exceeds 227 KB");
 
-static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_update_f64emu exceeds 227 KB");
+template <int KD>
+__host__ __device__ constexpr uint32_t tmem_cols() {
+  return KD * kBN <= 256 ? 256u : 512u;
+}
 
+// The folded accumulators of 8 columns of this lane's row, as the T element type,
+// scaled by 2^ex0 where the fold's unit is 2^(e_i + f_c + ex0).
+template <int KD>
+__device__ __forceinline__ void fold8(uint32_t taddr, long long* w) {
+  float v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) w[i] = 0;
+  if constexpr (KD == 7) {
+    tmem_ld8(taddr + 0 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
+    tmem_ld8(taddr + 1 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
+    tmem_ld8(taddr + 2 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      add_scaled<0>(w[i], v[i]);
+      w[i] <<= 24;  // |w| < 2^37 before the shift
+    }
+    tmem_ld8(taddr + 3 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
+    tmem_ld8(taddr + 4 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
+    tmem_ld8(taddr + 5 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
+    tmem_ld8(taddr + 6 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] += __float2int_rn(v[i] * 0x1.0p-8f);
+  } else {
+    static_assert(KD == 3, "KD is 7 or 3");
+    tmem_ld8(taddr + 0 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
+    tmem_ld8(taddr + 1 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
+    tmem_ld8(taddr + 2 * kBN, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
+  }
+}
+// unit of the fold: 2^(e_i + f_c + kFoldExp)
+template <int KD>
+__host__ __device__ constexpr int fold_exp() {
+  return KD == 7 ? 2 - 56 : 2 - 32;
+}
+__device__ __forceinline__ double fold_value(long long w, int ex, double) { return i64_to_double(w, ex); }
+__device__ __forceinline__ float fold_value(long long w, int ex, float) { return i64_to_float(w, ex); }
 
+template <int KD, typename TX>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_update_f64emu(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_p, int na,
-                    int tb, const int32_t* __restrict__ nexp, const int32_t* __restrict__ pexp,
-                    const int32_t* __restrict__ act, const int32_t* __restrict__ pivmark, double* __restrict__ X,
-                    int64_t ldx, DevState* st, const int32_t* done) {
+    k_update_emu(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_p, int na,
+                 int tb, const int32_t* __restrict__ nexp, const int32_t* __restrict__ pexp,
+                 const int32_t* __restrict__ act, const int32_t* __restrict__ pivmark, TX* __restrict__ X,
+                 int64_t ldx, DevState* st, const int32_t* done) {
+  constexpr int kD = KD;
+  constexpr int kPB = p_buffers<KD>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
-  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem<KD, TX>& sm =
+      *reinterpret_cast<Smem<KD, TX>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM;
   const int ntiles = (tb + kBN - 1) / kBN;
@@ -84,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&sm.drain, 1);
     mbar_init_fence();
   }
-  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
+  if (warp == 1) tmem_alloc(&sm.tmem_base, tmem_cols<KD>());
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -98,24 +175,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kD; ++s) tma_load_3d(sm.n[s], &map_n, &sm.n_full, 0, m0, s);
     }
     for (int u = 0; u < my; ++u) {
-      const int b = u & 1;
-      if (u >= 2 && !mbar_wait(&sm.p_empty[b], ((u >> 1) + 1) & 1, st)) break;
+      const int b = u % kPB;
+      // buffer b is free once the MMAs of tile u - kPB completed
+      if (u >= kPB && !mbar_wait(&sm.p_empty[b], ((u / kPB) - 1) & 1, st)) break;
       const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
       mbar_expect_tx(&sm.p_full[b], kD * kBN * kK * 2);
       for (int t = 0; t < kD; ++t) tma_load_3d(sm.p[b][t], &map_p, &sm.p_full[b], 0, c0, t);
       issued = u + 1;
     }
     if (my > 0) mbar_wait_drain(&sm.n_full, 0);
-    for (int u = issued - 2 < 0 ? 0 : issued - 2; u < issued; ++u) mbar_wait_drain(&sm.p_full[u & 1], (u >> 1) & 1);
+    for (int u = issued - kPB < 0 ? 0 : issued - kPB; u < issued; ++u)
+      mbar_wait_drain(&sm.p_full[u % kPB], (u / kPB) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
     bool ok = my == 0 || mbar_wait(&sm.n_full, 0, st);
     fence_after_sync();
     for (int u = 0; u < my && ok; ++u) {
-      const int b = u & 1;
+      const int b = u % kPB;
       if (u > 0 && !mbar_wait(&sm.t_empty, (u - 1) & 1, st)) break;
-      if (!mbar_wait(&sm.p_full[b], (u >> 1) & 1, st)) break;
+      if (!mbar_wait(&sm.p_full[b], (u / kPB) & 1, st)) break;
       fence_after_sync();
 #pragma unroll 1
       for (int g = 0; g < kD; ++g) {
@@ -134,59 +213,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
   } else if (warp >= 2) {
-    // ---------------- epilogue: lanes = rows of the tile, each warp 16 of its 64 columns
+    // ---------------- epilogue: each warp owns 32 rows (its tensor-memory lane
+    // quarter) and 16 of the tile's 64 columns.  The accumulators are read with
+    // lane = row; T is read and written coalesced (instruction i of a half covers
+    // rows 4i .. 4i+3, 8 consecutive columns each), the products passing through
+    // shared memory.
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int part = ew >> 2;  // 0..3
     const int r = m0 + quarter * 32 + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + part * 16;
     const bool live = r < na && pivmark[r] == 0;
-    double* xrow = live ? X + (int64_t)act[r] * ldx : nullptr;
     const int er = live ? nexp[r] : 0;
+    // rows of this lane in the coalesced layout: 4 i + (lane >> 3), i < 8
+    TX* const* rowp = sm.rows[ew] + (lane >> 3);
+    sm.rows[ew][lane] = live ? X + (int64_t)act[r] * ldx : nullptr;
+    __syncwarp();
+    TX(*stage)[9] = sm.stage[ew];
+    const int jc = lane & 7;
     for (int u = 0; u < my; ++u) {
       const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * 16;
       // lane j < 16 holds the column exponent of column c0 + j
       const int pe = (lane < 16 && c0 + lane < tb) ? pexp[c0 + lane] : 0;
-      // this row's 16 entries of T, in flight while the MMAs run and the
-      // accumulators are read
-      double xv[16];
+      // T's entries of both halves, in flight while the MMAs run
+      TX xv[2][8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) xv[i] = (live && c0 + i < tb) ? xrow[c0 + i] : 0.0;
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int c = c0 + 8 * h + jc;
+          TX* const rp = rowp[4 * i];
+          xv[h][i] = (rp != nullptr && c < tb) ? rp[c] : TX(0);
+        }
       if (!mbar_wait(&sm.t_full, u & 1, st)) break;
       fence_after_sync();
-      // W = sum_g G_g 2^(8 (5 - g)) with G_6 rounded to units of 2^8: |W| < 2^61,
-      // the rounding below 2^-55 of 2^(e_i + f_c); W's unit is 2^(e_i + f_c + 2 - 56).
-      // Two halves of 8 columns keep the fold within the register budget.
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         long long w[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = 0;
-        float v[8];
-        tmem_ld8(lane_base + 0 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
-        tmem_ld8(lane_base + 1 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
-        tmem_ld8(lane_base + 2 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          add_scaled<0>(w[i], v[i]);
-          w[i] <<= 24;  // |w| < 2^37 before the shift
-        }
-        tmem_ld8(lane_base + 3 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
-        tmem_ld8(lane_base + 4 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
-        tmem_ld8(lane_base + 5 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
-        tmem_ld8(lane_base + 6 * kBN + 8 * h, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] += __float2int_rn(v[i] * 0x1.0p-8f);
+        fold8<KD>(lane_base + 8 * h, w);
         if (h == 1) {
           // the accumulators are free for the next tile's MMAs
           fence_before_sync();
@@ -194,11 +258,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(&sm.t_empty);
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int c = c0 + 8 * h + i;
-          const int ec = __shfl_sync(0xffffffffu, pe, 8 * h + i);
-          if (live && c < tb) xrow[c] = xv[8 * h + i] - i64_to_double(w[i], er + ec + 2 - 56);
+        for (int j = 0; j < 8; ++j) {
+          const int ec = __shfl_sync(0xffffffffu, pe, 8 * h + j);
+          stage[lane][j] = fold_value(w[j], er + ec + fold_exp<KD>(), TX(0));
         }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int c = c0 + 8 * h + jc;
+          TX* const rp = rowp[4 * i];
+          if (rp != nullptr && c < tb) rp[c] = xv[h][i] - stage[4 * i + (lane >> 3)][jc];
+        }
+        __syncwarp();
       }
     }
   }
@@ -206,14 +277,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, tmem_cols<KD>());
   }
 }
 
 // ------------------------------------------------------------------ digit slicing
 // Both slicers work on the IEEE bit patterns with integer operations: the row (or
-// column) exponent from the largest pattern, then F = round(x 2^(55 - e)) and its
-// seven balanced digits.
+// column) exponent from the largest pattern, then F = round(x 2^(8 KD - 1 - e)) and
+// its KD balanced digits.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
@@ -225,28 +296,35 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
+__device__ __forceinline__ unsigned long long abs_bits(float x) {
+  return (unsigned long long)((unsigned)__float_as_int(x) & 0x7FFFFFFFu);
+}
+__device__ __forceinline__ int exp_above_bits(unsigned long long b, double) { return exp_above_f64bits(b); }
+__device__ __forceinline__ int exp_above_bits(unsigned long long b, float) { return exp_above_f32bits((unsigned)b); }
 
 // N (na x bt, row stride bt): one warp per row; digits D[s][i][q] (q < 64, zero-padded).
-__global__ void k_slice_n(int na, int bt, const double* __restrict__ N, __nv_bfloat16* __restrict__ D,
+template <typename T, int KD>
+__global__ void k_slice_n(int na, int bt, const T* __restrict__ N, __nv_bfloat16* __restrict__ D,
                           int32_t* __restrict__ nexp, int64_t plane, const int32_t* done) {
   if (done != nullptr && *done) return;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < na; i += nw) {
-    const double a0 = lane < bt ? N[i * bt + lane] : 0.0;
-    const double a1 = lane + 32 < bt ? N[i * bt + lane + 32] : 0.0;
+    const T a0 = lane < bt ? N[i * bt + lane] : T(0);
+    const T a1 = lane + 32 < bt ? N[i * bt + lane + 32] : T(0);
     const unsigned long long mb = warp_max_u64(max(abs_bits(a0), abs_bits(a1)));
-    const int e = exp_above_f64bits(mb);
+    const int e = exp_above_bits(mb, T(0));
     if (lane == 0) nexp[i] = e;
-    write_digits<kD>(fixed_of<kD>(a0, e), D + i * kK + lane, plane);
-    write_digits<kD>(fixed_of<kD>(a1, e), D + i * kK + lane + 32, plane);
+    write_digits<KD>(fixed_of<KD>(a0, e), D + i * kK + lane, plane);
+    write_digits<KD>(fixed_of<KD>(a1, e), D + i * kK + lane + 32, plane);
   }
 }
 
 // P(q, c) = X(pivorig[q] row, c) for q < bt, c < tb: per column c (one warp), digits
 // D[t][c][q] (q < 64, zero-padded).
-__global__ void k_slice_p(int bt, int tb, const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ prow,
+template <typename T, int KD>
+__global__ void k_slice_p(int bt, int tb, const T* __restrict__ X, int64_t ldx, const int32_t* __restrict__ prow,
                           __nv_bfloat16* __restrict__ D, int32_t* __restrict__ pexp, int64_t plane,
                           const int32_t* done) {
   if (done != nullptr && *done) return;
@@ -254,20 +332,20 @@ __global__ void k_slice_p(int bt, int tb, const double* __restrict__ X, int64_t 
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = w0; c < tb; c += nw) {
-    const double a0 = lane < bt ? X[(int64_t)prow[lane] * ldx + c] : 0.0;
-    const double a1 = lane + 32 < bt ? X[(int64_t)prow[lane + 32] * ldx + c] : 0.0;
+    const T a0 = lane < bt ? X[(int64_t)prow[lane] * ldx + c] : T(0);
+    const T a1 = lane + 32 < bt ? X[(int64_t)prow[lane + 32] * ldx + c] : T(0);
     const unsigned long long mb = warp_max_u64(max(abs_bits(a0), abs_bits(a1)));
-    const int e = exp_above_f64bits(mb);
+    const int e = exp_above_bits(mb, T(0));
     if (lane == 0) pexp[c] = e;
-    write_digits<kD>(fixed_of<kD>(a0, e), D + c * kK + lane, plane);
-    write_digits<kD>(fixed_of<kD>(a1, e), D + c * kK + lane + 32, plane);
+    write_digits<KD>(fixed_of<KD>(a0, e), D + c * kK + lane, plane);
+    write_digits<KD>(fixed_of<KD>(a1, e), D + c * kK + lane + 32, plane);
   }
 }
 
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows, int planes) {
   auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)kK, (cuuint64_t)rows, (cuuint64_t)kD};
+  cuuint64_t dims[3] = {(cuuint64_t)kK, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)kK * 2, (cuuint64_t)kK * rows * 2};
   cuuint32_t box[3] = {(cuuint32_t)kK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -276,45 +354,62 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int KD, typename T>
+cudaError_t update_emu(int na, int bt, int tb, const T* N, const int32_t* act, const int32_t* pivmark,
+                       const int32_t* pivorig, T* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows, void* pdig,
+                       int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done, cudaStream_t s) {
+  if (na <= 0 || tb <= 0) return cudaSuccess;
+  if (bt > kK || na > nrows || tb > prows) return cudaErrorInvalidValue;
+  auto nd = static_cast<__nv_bfloat16*>(ndig);
+  auto pd = static_cast<__nv_bfloat16*>(pdig);
+  const int64_t nplane = nrows * kK, pplane = prows * kK;
+  int64_t b1 = ((int64_t)na * 32 + 255) / 256;
+  if (b1 > 4096) b1 = 4096;
+  k_slice_n<T, KD><<<(int)b1, 256, 0, s>>>(na, bt, N, nd, nexp, nplane, done);
+  int64_t b2 = ((int64_t)tb * 32 + 255) / 256;
+  if (b2 > 4096) b2 = 4096;
+  k_slice_p<T, KD><<<(int)b2, 256, 0, s>>>(bt, tb, X, ldx, pivorig, pd, pexp, pplane, done);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mn, mp;
+  if (!make_map(&mn, nd, nrows, kBM, KD)) return cudaErrorInvalidValue;
+  if (!make_map(&mp, pd, prows, kBN, KD)) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(Smem<KD, T>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_update_emu<KD, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int rt = (na + kBM - 1) / kBM;
+  const int ct = (tb + kBN - 1) / kBN;
+  int gy = sms / rt;  // at most one CTA per SM in all (one wave)
+  if (gy > ct) gy = ct;
+  if (gy < 1) gy = 1;
+  k_update_emu<KD, T><<<dim3((unsigned)rt, (unsigned)gy), kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act,
+                                                                             pivmark, X, ldx, st, done);
+  return cudaGetLastError();
+}
+
 }  // namespace tcu
 
-size_t update_f64emu_digit_bytes(int64_t rows) { return (size_t)tcu::kD * rows * tcu::kK * 2; }
+size_t update_f64emu_digit_bytes(int64_t rows) { return (size_t)7 * rows * tcu::kK * 2; }
+size_t update_f32emu_digit_bytes(int64_t rows) { return (size_t)3 * rows * tcu::kK * 2; }
 
 cudaError_t update_f64emu(int na, int bt, int tb, const double* N, const int32_t* act, const int32_t* pivmark,
                           const int32_t* pivorig, double* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
                           void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
                           cudaStream_t s) {
-  if (na <= 0 || tb <= 0) return cudaSuccess;
-  if (bt > tcu::kK || na > nrows || tb > prows) return cudaErrorInvalidValue;
-  auto nd = static_cast<__nv_bfloat16*>(ndig);
-  auto pd = static_cast<__nv_bfloat16*>(pdig);
-  const int64_t nplane = nrows * tcu::kK, pplane = prows * tcu::kK;
-  int64_t b1 = ((int64_t)na * 32 + 255) / 256;
-  if (b1 > 4096) b1 = 4096;
-  tcu::k_slice_n<<<(int)b1, 256, 0, s>>>(na, bt, N, nd, nexp, nplane, done);
-  int64_t b2 = ((int64_t)tb * 32 + 255) / 256;
-  if (b2 > 4096) b2 = 4096;
-  tcu::k_slice_p<<<(int)b2, 256, 0, s>>>(bt, tb, X, ldx, pivorig, pd, pexp, pplane, done);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  CUtensorMap mn, mp;
-  if (!tcu::make_map(&mn, nd, nrows, tcu::kBM)) return cudaErrorInvalidValue;
-  if (!tcu::make_map(&mp, pd, prows, tcu::kBN)) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(tcu::Smem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(tcu::k_update_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int rt = (na + tcu::kBM - 1) / tcu::kBM;
-  const int ct = (tb + tcu::kBN - 1) / tcu::kBN;
-  int gy = sms / rt;  // at most one CTA per SM in all (one wave)
-  if (gy > ct) gy = ct;
-  if (gy < 1) gy = 1;
-  tcu::k_update_f64emu<<<dim3((unsigned)rt, (unsigned)gy), tcu::kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act,
-                                                                                    pivmark, X, ldx, st, done);
-  return cudaGetLastError();
+  return tcu::update_emu<7, double>(na, bt, tb, N, act, pivmark, pivorig, X, ldx, ndig, nexp, nrows, pdig, pexp, prows,
+                                    sms, st, done, s);
+}
+
+cudaError_t update_f32emu(int na, int bt, int tb, const float* N, const int32_t* act, const int32_t* pivmark,
+                          const int32_t* pivorig, float* X, int64_t ldx, void* ndig, int32_t* nexp, int64_t nrows,
+                          void* pdig, int32_t* pexp, int64_t prows, int sms, DevState* st, const int32_t* done,
+                          cudaStream_t s) {
+  return tcu::update_emu<3, float>(na, bt, tb, N, act, pivmark, pivorig, X, ldx, ndig, nexp, nrows, pdig, pexp, prows,
+                                   sms, st, done, s);
 }
 
 }  // namespace rid

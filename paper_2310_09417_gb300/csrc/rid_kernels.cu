@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "rid_internal.h"
 
 namespace rid {
@@ -224,6 +226,131 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// FP32 gather-GEMM for the store epilogue (the FP32 sketch and Schur products):
+// 128 x 64 tile, 256 threads each owning 8 rows x 4 columns (thread (ty, tx) =
+// (tid / 16, tid % 16): a warp reads two A fragments and sixteen B fragments of
+// shared memory per k, broadcast across its lanes), K steps of 32 double-buffered
+// through registers and shared memory.  Tiles are stored transposed (As[k][m],
+// Bs[k][n]) with rows padded by 4 floats: a warp's 8 k x 4 rows of a load land
+// in 32 distinct banks and the 16-byte fragment reads stay aligned.
+constexpr int kSM = 128, kSN = 64, kSK = 32;
+constexpr int kSAld = kSM + 4, kSBld = kSN + 4;
+constexpr size_t kSgemmSmem = (size_t)2 * kSK * (kSAld + kSBld) * sizeof(float);
+
+template <bool BK>
+__global__ void __launch_bounds__(256, 2)
+    k_sgemm_gather(int M, int N, int K, int kchunk, Operand<float> a, Operand<float> b, EpiArgs<float> ep,
+                   const int32_t* done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) float sg_smem[];
+  float* As = sg_smem;                   // [2][kSK][kSAld]
+  float* Bs = sg_smem + 2 * kSK * kSAld;  // [2][kSK][kSBld]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * kSM, n0 = blockIdx.y * kSN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int ntiles = kend > kbeg ? (kend - kbeg + kSK - 1) / kSK : 0;
+
+  // loader coordinates: lanes cover 8 consecutive k of 4 rows
+  const int lk = lane & 7, lr = warp * 4 + (lane >> 3);  // lr < 32
+  const float* ap[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int m = m0 + g * 32 + lr;
+    ap[g] = m < M ? a.base + (int64_t)(a.idx ? a.idx[m] : m) * a.ld + a.off : nullptr;
+  }
+  const float* bp[2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int n = n0 + g * 32 + lr;
+    bp[g] = (BK && n < N) ? b.base + (int64_t)(b.idx ? b.idx[n] : n) * b.ld + b.off : nullptr;
+  }
+  float ra[16], rb[8];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int k = k0 + (it & 3) * 8 + lk;
+      const float* p = ap[it >> 2];
+      ra[it] = (p != nullptr && k < kend) ? p[k] : 0.0f;
+    }
+    if (BK) {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int k = k0 + (it & 3) * 8 + lk;
+        const float* p = bp[it >> 2];
+        rb[it] = (p != nullptr && k < kend) ? p[k] : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int e = it * 256 + tid, kk = e >> 6, n = e & 63;
+        const int k = k0 + kk;
+        rb[it] = (k < kend && n0 + n < N) ? b.base[(int64_t)(b.idx ? b.idx[k] : k) * b.ld + b.off + n0 + n] : 0.0f;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+    float* as = As + buf * kSK * kSAld;
+    float* bs = Bs + buf * kSK * kSBld;
+#pragma unroll
+    for (int it = 0; it < 16; ++it) as[((it & 3) * 8 + lk) * kSAld + (it >> 2) * 32 + lr] = ra[it];
+    if (BK) {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) bs[((it & 3) * 8 + lk) * kSBld + (it >> 2) * 32 + lr] = rb[it];
+    } else {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int e = it * 256 + tid;
+        bs[(e >> 6) * kSBld + (e & 63)] = rb[it];
+      }
+    }
+  };
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+
+  if (ntiles > 0) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < ntiles; ++t) {
+    if (t + 1 < ntiles) load(kbeg + (t + 1) * kSK);
+    const float* as = As + (t & 1) * kSK * kSAld + ty * 8;
+    const float* bs = Bs + (t & 1) * kSK * kSBld + tx * 4;
+#pragma unroll 8
+    for (int kk = 0; kk < kSK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(as + kk * kSAld);
+      const float4 a1 = *reinterpret_cast<const float4*>(as + kk * kSAld + 4);
+      const float4 bv = *reinterpret_cast<const float4*>(bs + kk * kSBld);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+    }
+    if (t + 1 < ntiles) store((t + 1) & 1);
+    __syncthreads();
+  }
+
+  float* out = ep.out + blockIdx.z * ep.zstride;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + ty * 8 + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + tx * 4 + j;
+      if (c < N) out[(int64_t)r * ep.out_ld + c] = acc[i][j];
+    }
+  }
+}
+
 static int split_chunk(int K, int splits) {
   if (splits < 1) splits = 1;
   int kchunk = (K + splits - 1) / splits;
@@ -242,6 +369,26 @@ cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int kchunk = split_chunk(K, splits);
   splits = (K + kchunk - 1) / kchunk;
+  if constexpr (std::is_same<T, float>::value) {
+    if (epi == kEpiStore) {
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sgemm_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSgemmSmem);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_sgemm_gather<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kSgemmSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      dim3 g((M + kSM - 1) / kSM, (N + kSN - 1) / kSN, splits);
+      if (b_kmajor)
+        k_sgemm_gather<true><<<g, 256, kSgemmSmem, s>>>(M, N, K, kchunk, a, b, ep, done);
+      else
+        k_sgemm_gather<false><<<g, 256, kSgemmSmem, s>>>(M, N, K, kchunk, a, b, ep, done);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN, splits);
   if (b_kmajor) {
     if (epi == kEpiStore)
@@ -258,28 +405,29 @@ cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<
 }
 
 // ============================================================ split-K reductions
+// Threads over the rows of a row-block (x), rows of G over y and the grid: no
+// 64-bit division per element; the partials are summed in split order.
 template <typename T>
 __global__ void k_splitk_reduce(int64_t n, int rows, int64_t ldp, int64_t ldg, int nz, int64_t zs,
                                 const T* __restrict__ P, T* __restrict__ G, const int32_t* done) {
   if (done != nullptr && *done) return;
-  const int64_t total = n * rows;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / rows, c = e - j * rows;
-    const int64_t off = j * ldp + c;
-    T acc = P[off];
-    for (int z = 1; z < nz; ++z) acc += P[z * zs + off];
-    G[j * ldg + c] = acc;
-  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; j < n; j += (int64_t)gridDim.x * blockDim.y)
+    for (int c = threadIdx.x; c < rows; c += blockDim.x) {
+      const int64_t off = j * ldp + c;
+      T acc = P[off];
+      for (int z = 1; z < nz; ++z) acc += P[z * zs + off];
+      G[j * ldg + c] = acc;
+    }
 }
 
 template <typename T>
 cudaError_t splitk_reduce_ld(int64_t n, int rows, int64_t ldp, int64_t ldg, int nz, int64_t zs, const T* P, T* G,
                              const int32_t* done, cudaStream_t s) {
-  int64_t blocks = (n * rows + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
+  const int tx = rows >= 64 ? 64 : 32, ty = 256 / tx;
+  int64_t blocks = (n + ty - 1) / ty;
+  if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  k_splitk_reduce<T><<<(int)blocks, 256, 0, s>>>(n, rows, ldp, ldg, nz, zs, P, G, done);
+  k_splitk_reduce<T><<<(int)blocks, dim3(tx, ty), 0, s>>>(n, rows, ldp, ldg, nz, zs, P, G, done);
   return cudaGetLastError();
 }
 
@@ -296,17 +444,17 @@ __global__ void k_schur_finish(int na, int w, const int32_t* __restrict__ act, c
                                T* __restrict__ S, int64_t lds, double* e2part, const int32_t* done) {
   if (done != nullptr && *done) return;
   double acc2 = 0.0;
-  const int64_t total = (int64_t)na * w;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / w, c = e - i * w;
-    T v = G[(int64_t)act[i] * ldg + col0 + c];
-    T sub = T(0);
-    for (int z = 0; z < nz; ++z) sub += P[z * zs + i * lds + c];
-    v -= sub;
-    S[i * lds + c] = v;
-    acc2 += (double)v * (double)v;
-  }
+  // a warp per row of S, lanes along the row
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < na; i += (int64_t)gridDim.x * wpb)
+    for (int c = lane; c < w; c += 32) {
+      T v = G[(int64_t)act[i] * ldg + col0 + c];
+      T sub = T(0);
+      for (int z = 0; z < nz; ++z) sub += P[z * zs + i * lds + c];
+      v -= sub;
+      S[i * lds + c] = v;
+      acc2 += (double)v * (double)v;
+    }
   const double tot = block_sum(acc2);
   if (threadIdx.x == 0) e2part[blockIdx.x] = tot;
 }

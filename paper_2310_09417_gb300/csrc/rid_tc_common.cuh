@@ -301,5 +301,33 @@ __device__ __forceinline__ void write_digits(long long F, __nv_bfloat16* d, int6
   for (int s = 0; s < KD; ++s) d[s * plane] = __int2bfloat16_rn(dg[s]);
 }
 
+// The KD digits of four consecutive values F[0..3] at d[0..3] of every plane, one
+// 8-byte store per plane (d 8-byte aligned).
+template <int KD>
+__device__ __forceinline__ void write_digits4(const long long* F, __nv_bfloat16* d, int64_t plane) {
+  int dg[4][KD];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    long long f = F[e];
+#pragma unroll
+    for (int s = KD - 1; s > 0; --s) {
+      long long r = f & 255;
+      if (r >= 128) r -= 256;
+      dg[e][s] = (int)r;
+      f = (f - r) >> 8;
+    }
+    dg[e][0] = (int)f;
+  }
+#pragma unroll
+  for (int s = 0; s < KD; ++s) {
+    const __nv_bfloat162 lo = __halves2bfloat162(__int2bfloat16_rn(dg[0][s]), __int2bfloat16_rn(dg[1][s]));
+    const __nv_bfloat162 hi = __halves2bfloat162(__int2bfloat16_rn(dg[2][s]), __int2bfloat16_rn(dg[3][s]));
+    uint2 v;
+    v.x = *reinterpret_cast<const unsigned*>(&lo);
+    v.y = *reinterpret_cast<const unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(d + s * plane) = v;
+  }
+}
+
 }  // namespace tcx
 }  // namespace rid

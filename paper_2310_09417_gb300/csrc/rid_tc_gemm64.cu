@@ -280,13 +280,22 @@ __global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const T* __restri
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w0; r < M; r += nw) {
     const T* row = src + (int64_t)(idx ? idx[r] : r) * lds;
+    // four consecutive k per lane: a warp covers 128 elements per step
     unsigned long long mx = 0;
-    for (int k = lane; k < K; k += 32) mx = max(mx, abs_bits(row[k]));
+    for (int k = 4 * lane; k < K; k += 128) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (k + e < K) mx = max(mx, abs_bits(row[k + e]));
+    }
     for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     const int e = exp_above(mx, T(0));
     if (lane == 0) ex[r] = e;
-    for (int k = lane; k < Kq; k += 32)
-      write_digits<KD>(k < K ? fixed_of<KD>(row[k], e) : 0ll, D + r * Kp + k, plane);
+    for (int k = 4 * lane; k < Kq; k += 128) {  // Kq is a multiple of 64
+      long long F[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] = k + q < K ? fixed_of<KD>(row[k + q], e) : 0ll;
+      write_digits4<KD>(F, D + r * Kp + k, plane);
+    }
   }
 }
 

@@ -8,8 +8,9 @@
 // N(i,:) / 2^(e_i+1) and P(:,c) / 2^(f_c+1) lie in (-1/2, 1/2) and are written as
 // KD balanced 8-bit digits (|d| <= 128, exact in BF16: 56 bits for KD = 7, 24 for
 // KD = 3).  The digit products of equal weight 2^(-8(g+2)), g = s + t < KD, share
-// FP32 group g in tensor memory (KD groups x 64 columns); a group sums at most KD
-// pairs x 64 terms of magnitude <= 2^14 (< 2^23): exact.
+// FP32 group g in tensor memory (KD groups x kBN columns, kBN = 32 for KD = 7 and 64
+// for KD = 3, two sets); a group sums at most KD pairs x 64 terms of magnitude
+// <= 2^14 (< 2^23): exact.
 //   KD = 7: the epilogue folds the groups into one int64 W = sum_g G_g 2^(8(5-g))
 //     (group 6 rounded to units of 2^8, |W| < 2^61), converts W 2^(e_i + f_c + 2 -
 //     56) to FP64 by integer operations and subtracts it from T (one FP64
@@ -17,14 +18,17 @@
 //     each entry's error by about 2^-46 max_q|N(i,q)| max_q|P(q,c)| -- the order
 //     of an FP64 dot product of length 64 (64 u); the fold adds at most 2^-55 of
 //     that scale.
-//   KD = 3: W = G_0 2^16 + G_1 2^8 + G_2 (|W| < 2^38) is rounded to FP32 and
+//   KD = 3: W = G_0 2^16 + G_1 2^8 + G_2 (|W| < 2^38) is rounded to FP32 once and
 //     scaled by 2^(e_i + f_c + 2 - 32); dropped pairs (g >= 3) and remainders bound
 //     the error by about 2^-18 max_q|N(i,q)| max_q|P(q,c)|, the order of an FP32
 //     dot product of length 64.
 //
 //   warp 0    TMA: the row tile's digits of N once, then P's digits per column
-//             tile (double-buffered for KD = 3, single for KD = 7)
-//   warp 1    tensor memory; KD(KD+1)/2 x 4 MMAs (M = 128, N = 64, K = 16) per tile
+//             tile (double-buffered)
+//   warp 1    tensor memory; per K step of 16 and slice s of N one MMA (M = 128,
+//             N = kBN (KD - s)) against P's planes 0 .. KD-1-s stacked along N, which
+//             writes groups s .. KD-1 at once: KD x 4 MMAs per tile; the two
+//             accumulator sets let a tile's MMAs run during the last tile's epilogue
 //   warps 2-17 epilogue: four warps per lane quarter, 16 columns each; the
 //             accumulators are read with one row per lane and released before
 //             the stores, T is read (before the accumulators are ready) and
@@ -45,92 +49,96 @@ namespace tcu {
 using namespace tcx;
 
 constexpr int kBM = 128;    // rows of T per tile
-constexpr int kBN = 64;     // columns of T per tile
 constexpr int kK = 64;      // padded K (one 128-byte swizzle row of BF16)
-constexpr int kEpiWarps = 16;  // four per tensor-memory lane quarter, 16 columns each
+constexpr int kEpiWarps = 16;  // four per tensor-memory lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
-// P's digit tiles are double-buffered for KD = 3; for KD = 7 one buffer leaves room
-// for the epilogue's staging (the next tile's P loads while the epilogue works).
+// Columns of T per tile.  The accumulators are double-buffered (the next tile's
+// MMAs run while the epilogue reads the last one): two sets of KD groups x kBN
+// columns, 448 (KD = 7) or 384 (KD = 3) of the 512 tensor-memory columns.
 template <int KD>
-__host__ __device__ constexpr int p_buffers() {
-  return KD == 7 ? 1 : 2;
+__host__ __device__ constexpr int bn() {
+  return KD == 7 ? 32 : 64;
+}
+template <int KD>
+__host__ __device__ constexpr int set_cols() {
+  return KD * bn<KD>();
 }
 
 template <int KD, typename TX>
 struct Smem {
-  alignas(1024) __nv_bfloat16 n[KD][kBM * kK];                  // KD x 16 KB
-  alignas(1024) __nv_bfloat16 p[p_buffers<KD>()][KD][kBN * kK];  // KD x 8 KB each
+  alignas(1024) __nv_bfloat16 n[KD][kBM * kK];            // KD x 16 KB
+  alignas(1024) __nv_bfloat16 p[2][KD][bn<KD>() * kK];    // planes back to back: one operand along N
   TX stage[kEpiWarps][32][9];  // per warp: 32 rows x 8 columns (+1 against bank conflicts)
   TX* rows[kEpiWarps][32];     // per warp: T's row of each of its 32 rows (null: not updated)
   uint64_t n_full;
   uint64_t p_full[2];
   uint64_t p_empty[2];
-  uint64_t t_full;   // a tile's MMAs completed
-  uint64_t t_empty;  // the epilogue read the accumulators
+  uint64_t t_full[2];   // a tile's MMAs completed (accumulator set u & 1)
+  uint64_t t_empty[2];  // the epilogue read accumulator set u & 1
   uint64_t drain;
   uint32_t tmem_base;
 };
 static_assert(sizeof(Smem<7, double>) + 1024 <= 232448, "shared memory of k_update_emu exceeds 227 KB");
 static_assert(sizeof(Smem<3, float>) + 1024 <= 232448, "shared memory of k_update_emu exceeds 227 KB");
+static_assert(2 * set_cols<7>() <= 512 && 2 * set_cols<3>() <= 512, "two accumulator sets exceed tensor memory");
 
-template <int KD>
-__host__ __device__ constexpr uint32_t tmem_cols() {
-  return KD * kBN <= 256 ? 256u : 512u;
-}
-
-// The folded accumulators of 8 columns of this lane's row, as the T element type,
-// scaled by 2^ex0 where the fold's unit is 2^(e_i + f_c + ex0).
+// The folded accumulators of 8 columns of this lane's row; group g of the set
+// starts at column g * bn.
 template <int KD>
 __device__ __forceinline__ void fold8(uint32_t taddr, long long* w) {
-  float v[8];
+  constexpr int kG = bn<KD>();
+  // loads issued in batches, one wait per batch (KD = 7: groups 0-3, then 4-6)
+  uint32_t r[4][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) w[i] = 0;
   if constexpr (KD == 7) {
-    tmem_ld8(taddr + 0 * kBN, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
-    tmem_ld8(taddr + 1 * kBN, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
-    tmem_ld8(taddr + 2 * kBN, v);
+    for (int g = 0; g < 4; ++g) tmem_ld8_nowait(taddr + g * kG, r[g]);
+    tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      add_scaled<0>(w[i], v[i]);
+      add_scaled<16>(w[i], __uint_as_float(r[0][i]));
+      add_scaled<8>(w[i], __uint_as_float(r[1][i]));
+      add_scaled<0>(w[i], __uint_as_float(r[2][i]));
       w[i] <<= 24;  // |w| < 2^37 before the shift
+      add_scaled<16>(w[i], __uint_as_float(r[3][i]));
     }
-    tmem_ld8(taddr + 3 * kBN, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
-    tmem_ld8(taddr + 4 * kBN, v);
+    for (int g = 0; g < 3; ++g) tmem_ld8_nowait(taddr + (4 + g) * kG, r[g]);
+    tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
-    tmem_ld8(taddr + 5 * kBN, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
-    tmem_ld8(taddr + 6 * kBN, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] += __float2int_rn(v[i] * 0x1.0p-8f);
+    for (int i = 0; i < 8; ++i) {
+      add_scaled<8>(w[i], __uint_as_float(r[0][i]));
+      add_scaled<0>(w[i], __uint_as_float(r[1][i]));
+      w[i] += __float2int_rn(__uint_as_float(r[2][i]) * 0x1.0p-8f);
+    }
   } else {
     static_assert(KD == 3, "KD is 7 or 3");
-    tmem_ld8(taddr + 0 * kBN, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<16>(w[i], v[i]);
-    tmem_ld8(taddr + 1 * kBN, v);
+    for (int g = 0; g < 3; ++g) tmem_ld8_nowait(taddr + g * kG, r[g]);
+    tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<8>(w[i], v[i]);
-    tmem_ld8(taddr + 2 * kBN, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) add_scaled<0>(w[i], v[i]);
+    for (int i = 0; i < 8; ++i) {
+      add_scaled<16>(w[i], __uint_as_float(r[0][i]));
+      add_scaled<8>(w[i], __uint_as_float(r[1][i]));
+      add_scaled<0>(w[i], __uint_as_float(r[2][i]));
+    }
   }
 }
-// unit of the fold: 2^(e_i + f_c + kFoldExp)
+// unit of the fold: 2^(e_i + f_c + fold_exp)
 template <int KD>
 __host__ __device__ constexpr int fold_exp() {
   return KD == 7 ? 2 - 56 : 2 - 32;
 }
 __device__ __forceinline__ double fold_value(long long w, int ex, double) { return i64_to_double(w, ex); }
-__device__ __forceinline__ float fold_value(long long w, int ex, float) { return i64_to_float(w, ex); }
+// |w| < 2^38: the hardware conversion rounds once; the power-of-two scale is exact
+// for normal results
+__device__ __forceinline__ float fold_value(long long w, int ex, float) {
+  const float f = __ll2float_rn(w);
+  if (ex >= -126 && ex <= 127) return f * __int_as_float((ex + 127) << 23);
+  return ldexpf(f, ex);
+}
 
 template <int KD, typename TX>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -139,7 +147,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const int32_t* __restrict__ act, const int32_t* __restrict__ pivmark, TX* __restrict__ X,
                  int64_t ldx, DevState* st, const int32_t* done) {
   constexpr int kD = KD;
-  constexpr int kPB = p_buffers<KD>();
+  constexpr int kBN = bn<KD>();
+  constexpr int kSet = set_cols<KD>();
+  constexpr int kCols = kBN / 4;      // columns of a tile per epilogue warp
+  constexpr int kHalves = kCols / 8;  // groups of 8 columns per warp
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
   Smem<KD, TX>& sm =
@@ -155,13 +166,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm.p_full[b], 1);
       mbar_init(&sm.p_empty[b], 1);
+      mbar_init(&sm.t_full[b], 1);
+      mbar_init(&sm.t_empty[b], kEpiWarps);
     }
-    mbar_init(&sm.t_full, 1);
-    mbar_init(&sm.t_empty, kEpiWarps);
     mbar_init(&sm.drain, 1);
     mbar_init_fence();
   }
-  if (warp == 1) tmem_alloc(&sm.tmem_base, tmem_cols<KD>());
+  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -175,54 +186,48 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kD; ++s) tma_load_3d(sm.n[s], &map_n, &sm.n_full, 0, m0, s);
     }
     for (int u = 0; u < my; ++u) {
-      const int b = u % kPB;
-      // buffer b is free once the MMAs of tile u - kPB completed
-      if (u >= kPB && !mbar_wait(&sm.p_empty[b], ((u / kPB) - 1) & 1, st)) break;
+      const int b = u & 1;
+      // buffer b is free once the MMAs of tile u - 2 completed
+      if (u >= 2 && !mbar_wait(&sm.p_empty[b], ((u >> 1) - 1) & 1, st)) break;
       const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
       mbar_expect_tx(&sm.p_full[b], kD * kBN * kK * 2);
       for (int t = 0; t < kD; ++t) tma_load_3d(sm.p[b][t], &map_p, &sm.p_full[b], 0, c0, t);
       issued = u + 1;
     }
     if (my > 0) mbar_wait_drain(&sm.n_full, 0);
-    for (int u = issued - kPB < 0 ? 0 : issued - kPB; u < issued; ++u)
-      mbar_wait_drain(&sm.p_full[u % kPB], (u / kPB) & 1);
+    for (int u = issued - 2 < 0 ? 0 : issued - 2; u < issued; ++u) mbar_wait_drain(&sm.p_full[u & 1], (u >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
+    // ---------------- MMA issuer: per K step and slice s of N, one MMA against P's
+    // planes 0 .. KD-1-s stacked along N writes groups s .. KD-1 at once
     bool ok = my == 0 || mbar_wait(&sm.n_full, 0, st);
     fence_after_sync();
     for (int u = 0; u < my && ok; ++u) {
-      const int b = u % kPB;
-      if (u > 0 && !mbar_wait(&sm.t_empty, (u - 1) & 1, st)) break;
-      if (!mbar_wait(&sm.p_full[b], (u / kPB) & 1, st)) break;
+      const int b = u & 1;
+      if (u >= 2 && !mbar_wait(&sm.t_empty[b], ((u >> 1) - 1) & 1, st)) break;
+      if (!mbar_wait(&sm.p_full[b], (u >> 1) & 1, st)) break;
       fence_after_sync();
-#pragma unroll 1
-      for (int g = 0; g < kD; ++g) {
-#pragma unroll 1
-        for (int s = 0; s <= g; ++s) {
-          const uint64_t da = desc_sw128(sm.n[s]);
-          const uint64_t db = desc_sw128(sm.p[b][g - s]);
+      const uint64_t db = desc_sw128(sm.p[b][0]);
 #pragma unroll
-          for (int kk = 0; kk < kK / 16; ++kk)
-            mma_bf16(tmem + g * kBN, da + 2 * kk, db + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-        }
-      }
+      for (int kk = 0; kk < kK / 16; ++kk)
+#pragma unroll
+        for (int s = 0; s < kD; ++s)
+          mma_bf16(tmem + b * kSet + s * kBN, desc_sw128(sm.n[s]) + 2 * kk, db + 2 * kk,
+                   idesc_bf16(kBM, kBN * (kD - s)), (s > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&sm.p_empty[b]);
-      mma_commit(&sm.t_full);
+      mma_commit(&sm.t_full[b]);
     }
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
   } else if (warp >= 2) {
     // ---------------- epilogue: each warp owns 32 rows (its tensor-memory lane
-    // quarter) and 16 of the tile's 64 columns.  The accumulators are read with
-    // lane = row; T is read and written coalesced (instruction i of a half covers
-    // rows 4i .. 4i+3, 8 consecutive columns each), the products passing through
-    // shared memory.
+    // quarter) and kCols of the tile's columns.  The accumulators are read with
+    // lane = row; T is read and written coalesced (instruction i of a group of 8
+    // columns covers rows 4i .. 4i+3), the products passing through shared memory.
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int part = ew >> 2;  // 0..3
     const int r = m0 + quarter * 32 + lane;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + part * 16;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + part * kCols;
     const bool live = r < na && pivmark[r] == 0;
     const int er = live ? nexp[r] : 0;
     // rows of this lane in the coalesced layout: 4 i + (lane >> 3), i < 8
@@ -231,31 +236,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     TX(*stage)[9] = sm.stage[ew];
     const int jc = lane & 7;
-    for (int u = 0; u < my; ++u) {
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * 16;
-      // lane j < 16 holds the column exponent of column c0 + j
-      const int pe = (lane < 16 && c0 + lane < tb) ? pexp[c0 + lane] : 0;
-      // T's entries of both halves, in flight while the MMAs run
-      TX xv[2][8];
+    // T's entries and the column exponents of tile u + 1 are loaded while tile u
+    // is processed: the loads have a whole tile to land
+    TX xn[kHalves][8];
+    int pn = 0;
+    auto fetch = [&](int u) {
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * kCols;
+      pn = (lane < kCols && c0 + lane < tb) ? pexp[c0 + lane] : 0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < kHalves; ++h)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int c = c0 + 8 * h + jc;
           TX* const rp = rowp[4 * i];
-          xv[h][i] = (rp != nullptr && c < tb) ? rp[c] : TX(0);
+          xn[h][i] = (rp != nullptr && c < tb) ? rp[c] : TX(0);
         }
-      if (!mbar_wait(&sm.t_full, u & 1, st)) break;
+    };
+    if (my > 0) fetch(0);
+    for (int u = 0; u < my; ++u) {
+      const int b = u & 1;
+      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * kCols;
+      TX xv[kHalves][8];
+#pragma unroll
+      for (int h = 0; h < kHalves; ++h)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) xv[h][i] = xn[h][i];
+      const int pe = pn;  // lane j < kCols: the exponent of column c0 + j
+      if (u + 1 < my) fetch(u + 1);
+      if (!mbar_wait(&sm.t_full[b], (u >> 1) & 1, st)) break;
       fence_after_sync();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < kHalves; ++h) {
         long long w[8];
-        fold8<KD>(lane_base + 8 * h, w);
-        if (h == 1) {
-          // the accumulators are free for the next tile's MMAs
+        fold8<KD>(lane_base + b * kSet + 8 * h, w);
+        if (h == kHalves - 1) {
+          // this accumulator set is free for tile u + 2
           fence_before_sync();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&sm.t_empty);
+          if (lane == 0) mbar_arrive(&sm.t_empty[b]);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -277,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, tmem_cols<KD>());
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -373,7 +391,7 @@ cudaError_t update_emu(int na, int bt, int tb, const T* N, const int32_t* act, c
   if (e != cudaSuccess) return e;
   CUtensorMap mn, mp;
   if (!make_map(&mn, nd, nrows, kBM, KD)) return cudaErrorInvalidValue;
-  if (!make_map(&mp, pd, prows, kBN, KD)) return cudaErrorInvalidValue;
+  if (!make_map(&mp, pd, prows, bn<KD>(), KD)) return cudaErrorInvalidValue;
   const size_t smem = sizeof(Smem<KD, T>) + 1024;
   static bool attr = false;
   if (!attr) {
@@ -382,7 +400,7 @@ cudaError_t update_emu(int na, int bt, int tb, const T* N, const int32_t* act, c
     attr = true;
   }
   const int rt = (na + kBM - 1) / kBM;
-  const int ct = (tb + kBN - 1) / kBN;
+  const int ct = (tb + bn<KD>() - 1) / bn<KD>();
   int gy = sms / rt;  // at most one CTA per SM in all (one wave)
   if (gy > ct) gy = ct;
   if (gy < 1) gy = 1;

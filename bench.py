@@ -41,7 +41,7 @@ WORKLOADS = {
     "adaptive_poly_f64": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
     "adaptive_step_f64": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64", 1e-10, 64),
     # FP64 A, LU and X with the FP64-accurate sketch on the BF16 tensor cores (exact digit
-    # slices of A, Omega on the grid 2^-10)
+    # slices of A, Omega on the grid 2^-11)
     "adaptive_poly_f64emu": (40000, 10000, "poly", {}, "f64emu", 1e-10, 64),
     "adaptive_step_f64emu": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64emu", 1e-10, 64),
     # reduced sizes of the same families, for profiler captures (inputs still > L2)
@@ -57,9 +57,12 @@ WORKLOADS = {
     "small_mixed_bf16": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "bf16", 1e-3, 64),
     # the same matrix quantised to FP8 E4M3 with power-of-two scales per 128-row block;
     # E4M3 sketch on the tensor cores (kind::f8f6f4), LU in FP32.  The E4M3 rounding
-    # (about 2.6e-2 relative) is part of the stored matrix: tol 5e-2 sits above it
+    # (about 2.6e-2 relative) is part of the stored matrix
     "mixed_fp8": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "fp8", 1e-3, 64),
     "mixed_fp8_tol5e-2": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "fp8", 5e-2, 64),
+    # the ID error of the stored E4M3 matrix is about 8x its rounding (X amplifies it):
+    # 3e-1 stops once the rank-1500 signal is captured
+    "mixed_fp8_tol3e-1": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "fp8", 3e-1, 64),
     "small_mixed_fp8": (32768, 8192, "lowrank", {"rank": 600, "noise": 1e-4}, "fp8", 5e-2, 64),
     # batched: 4096 off-diagonal blocks exp(-|x-y|^2/h^2), h = 0.3, of a k-d tree over 2^20 uniform
     # points in the unit cube (leaves of at most 1024 points, sizes 64..1024), one persistent launch

@@ -437,6 +437,187 @@ int splits_for(int64_t M, int64_t N, int64_t K, int sms, int cap) {
   return best;
 }
 
+// ------------------------------------------------------------------ FP32-accurate sketch
+// (W A)^T for an FP32 A: A's columns and W's rows as 3 balanced 8-bit digit planes
+// each (per-row exponents).  A stage holds one K step of 64 for both operands, all
+// planes: A 3 x 128 rows, W 3 x 64 rows stacked along N.  Per K step of 16 and A's
+// plane s one MMA (M = 128, N = 64 (3 - s)) against W's planes 0 .. 2-s writes groups
+// s .. 2 (group g = s + t collects the products of weight 2^(-8(g+2))).  A chunk of 5
+// K steps (320 K) keeps every group below 3 x 320 x 2^14 < 2^24: exact in FP32.  Two
+// accumulator sets (2 x 3 groups x 64 columns) let the epilogue fold chunk c into
+// int64 while the MMAs of chunk c+1 run.
+namespace f32s {
+constexpr int kBM = 128, kBN = 64, kBK = 64, kD = 3;
+constexpr int kStages = 3;
+constexpr int kChunkSteps = 5;
+constexpr int kSet = kD * kBN;     // tensor-memory columns of one accumulator set
+constexpr int kEpiWarps = 8;       // two per lane quarter, 32 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+
+struct Smem {
+  alignas(1024) __nv_bfloat16 a[kStages][kD][kBM * kBK];  // 3 x 16 KB per stage
+  alignas(1024) __nv_bfloat16 w[kStages][kD][kBN * kBK];  // 3 x 8 KB per stage, back to back
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+};
+static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_sketch_f32emu exceeds 227 KB");
+
+// Grid: x = tiles of A's columns (M), y = tiles of W's rows (N), z = K splits of kchunk
+// (a multiple of the chunk).  out[z]: FP32 partial (M x N, row stride ldo).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sketch_f32emu(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w, int M,
+                    int N, int K, int kchunk, const int32_t* __restrict__ ea, const int32_t* __restrict__ ew,
+                    float* __restrict__ out, int64_t ldo, int64_t zstride, DevState* st, const int32_t* done) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (done != nullptr && *done) return;
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nsteps = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
+  const int nchunks = (nsteps + kChunkSteps - 1) / kChunkSteps;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&sm.full[i], 1);
+      mbar_init(&sm.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&sm.acc_full[i], 1);
+      mbar_init(&sm.acc_empty[i], kEpiWarps);
+    }
+    mbar_init(&sm.drain, 1);
+    mbar_init_fence();
+  }
+  if (warp == 1) tmem_alloc(&sm.tmem_base, 512);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: one stage per K step, every plane of both operands
+    int it = 0;
+    for (; it < nsteps; ++it) {
+      const int b = it % kStages;
+      if (it >= kStages && !mbar_wait(&sm.empty[b], ((it / kStages) + 1) & 1, st)) break;
+      mbar_expect_tx(&sm.full[b], kD * (kBM + kBN) * kBK * 2);
+      const int k0 = kbeg + it * kBK;
+      for (int p = 0; p < kD; ++p) {
+        tma_load_3d(sm.a[b][p], &map_a, &sm.full[b], k0, m0, p);
+        tma_load_3d(sm.w[b][p], &map_w, &sm.full[b], k0, n0, p);
+      }
+    }
+    for (int t = it - kStages < 0 ? 0 : it - kStages; t < it; ++t)
+      mbar_wait_drain(&sm.full[t % kStages], (t / kStages) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    int it = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int u = c & 1;
+      if (c >= 2 && !mbar_wait(&sm.acc_empty[u], ((c >> 1) - 1) & 1, st)) break;
+      const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
+      for (int jj = 0; jj < steps_c; ++jj, ++it) {
+        const int b = it % kStages;
+        if (!mbar_wait(&sm.full[b], (it / kStages) & 1, st)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        const uint64_t dw = desc_sw128(sm.w[b][0]);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk)
+#pragma unroll
+          for (int s = 0; s < kD; ++s)
+            mma_bf16(tmem + u * kSet + s * kBN, desc_sw128(sm.a[b][s]) + 2 * kk, dw + 2 * kk,
+                     idesc_bf16(kBM, kBN * (kD - s)), (jj > 0 || kk > 0 || s > 0) ? 1u : 0u);
+        mma_commit(&sm.empty[b]);
+      }
+      if (ok) mma_commit(&sm.acc_full[u]);
+    }
+    mma_commit(&sm.drain);
+    mbar_wait_drain(&sm.drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: lane = row of A's tile, 32 of the 64 columns per warp;
+    // W = G_0 2^16 + G_1 2^8 + G_2 summed exactly over the chunks in int64
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int m = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * 32;
+    long long acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int u = c & 1;
+      if (!mbar_wait(&sm.acc_full[u], (c >> 1) & 1, st)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+      const uint32_t base = lane_base + u * kSet;
+#pragma unroll
+      for (int cb = 0; cb < 32; cb += 16) {
+        float v[16];
+        tmem_ld16(base + 0 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<16>(acc[cb + i], v[i]);
+        tmem_ld16(base + 1 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<8>(acc[cb + i], v[i]);
+        tmem_ld16(base + 2 * kBN + cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) add_scaled<0>(acc[cb + i], v[i]);
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.acc_empty[u]);
+    }
+    if (ok && m < M) {
+      const int em = ea[m];
+      float* o = out + blockIdx.z * zstride + (int64_t)m * ldo;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int n = n0 + half * 32 + i;
+        if (n < N) o[n] = i64_to_float(acc[i], em + ew[n] + 2 - 32);
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Split count: one CTA per SM, a launch takes waves x (chunks per split + a fixed cost).
+int splits(int64_t M, int64_t N, int64_t K, int sms, int cap) {
+  const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
+  constexpr int chunk = kChunkSteps * kBK;
+  const int64_t chunks = (K + chunk - 1) / chunk;
+  int best = 1;
+  double best_t = 1e300;
+  for (int64_t s = 1; s <= cap && s <= chunks; ++s) {
+    const int64_t per = (chunks + s - 1) / s;
+    const int64_t eff = (chunks + per - 1) / per;
+    if (eff != s) continue;
+    const int64_t waves = (tiles * eff + sms - 1) / sms;
+    const double t = (double)waves * ((double)per + 0.5) + 0.02 * (double)eff;
+    if (t < best_t) {
+      best_t = t;
+      best = (int)eff;
+    }
+  }
+  return best;
+}
+}  // namespace f32s
 }  // namespace tcg
 
 int64_t gemm_f64emu_kpad(int64_t K) { return (K + tcg::kBK - 1) / tcg::kBK * tcg::kBK; }
@@ -494,7 +675,7 @@ size_t sketch_f32emu_digit_bytes(int64_t rows, int64_t K) {
 }
 
 int sketch_f32emu_splits(int64_t m, int64_t n, int64_t unit_rows, int sms) {
-  return tcg::splits_for<3>(n, unit_rows, m, sms, 32);
+  return tcg::f32s::splits(n, unit_rows, m, sms, 32);
 }
 
 cudaError_t sketch_f32emu_slice(int rows, int K, const float* src, int64_t lds, void* dig, int64_t rows_alloc,
@@ -525,10 +706,30 @@ cudaError_t sketch_f32emu_slice(int rows, int K, const float* src, int64_t lds, 
 cudaError_t sketch_f32emu(int64_t m, int64_t n, int64_t rows, const void* adig, const int32_t* aexp, const void* wdig,
                           int64_t wrows, const int32_t* wexp, float* out, int64_t ldo, int64_t zstride, int splits,
                           DevState* st, const int32_t* done, cudaStream_t s) {
+  using namespace tcg;
   if (rows <= 0) return cudaSuccess;
   if (rows > wrows) return cudaErrorInvalidValue;
-  return tcg::launch<3, float>((int)n, (int)rows, (int)m, gemm_f64emu_kpad(m), adig, n, aexp, wdig, wrows, wexp, out,
-                               ldo, zstride, splits, st, done, s);
+  const int64_t Kp = gemm_f64emu_kpad(m);
+  CUtensorMap ma, mw;
+  if (!make_map(&ma, adig, Kp, n, f32s::kBM, f32s::kD)) return cudaErrorInvalidValue;
+  if (!make_map(&mw, wdig, Kp, wrows, f32s::kBN, f32s::kD)) return cudaErrorInvalidValue;
+  constexpr int chunk = f32s::kChunkSteps * f32s::kBK;
+  const int64_t chunks = (m + chunk - 1) / chunk;
+  const int64_t per = (chunks + splits - 1) / splits;
+  const int kchunk = (int)(per * chunk);
+  const int nz = (int)((m + kchunk - 1) / kchunk);
+  if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
+  const size_t smem = sizeof(f32s::Smem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(f32s::k_sketch_f32emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((unsigned)((n + f32s::kBM - 1) / f32s::kBM), (unsigned)((rows + f32s::kBN - 1) / f32s::kBN), (unsigned)nz);
+  f32s::k_sketch_f32emu<<<grid, f32s::kThreads, smem, s>>>(ma, mw, (int)n, (int)rows, (int)m, kchunk, aexp, wexp, out,
+                                                          ldo, zstride, st, done);
+  return cudaGetLastError();
 }
 
 }  // namespace rid

@@ -140,6 +140,9 @@ __device__ __forceinline__ float fold_value(long long w, int ex, float) {
   return ldexpf(f, ex);
 }
 
+// Tiles (row tile, column tile) in row-major order are split into one contiguous,
+// balanced range per CTA (one CTA per SM): a range spans few row tiles, whose N
+// digits are loaded when the range enters them.
 template <int KD, typename TX>
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_emu(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_p, int na,
@@ -156,10 +159,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   Smem<KD, TX>& sm =
       *reinterpret_cast<Smem<KD, TX>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM;
-  const int ntiles = (tb + kBN - 1) / kBN;
-  // column tiles of this CTA: blockIdx.y, blockIdx.y + gridDim.y, ...
-  const int my = blockIdx.y < ntiles ? (ntiles - 1 - blockIdx.y) / gridDim.y + 1 : 0;
+  const int ct = (tb + kBN - 1) / kBN;
+  const int rt = (na + kBM - 1) / kBM;
+  const int64_t total = (int64_t)rt * ct;
+  const int64_t t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+  const int my = (int)(t1 - t0);
 
   if (threadIdx.x == 0) {
     mbar_init(&sm.n_full, 1);
@@ -180,29 +184,42 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int issued = 0;
-    if (my > 0) {
-      mbar_expect_tx(&sm.n_full, kD * kBM * kK * 2);
-      for (int s = 0; s < kD; ++s) tma_load_3d(sm.n[s], &map_n, &sm.n_full, 0, m0, s);
-    }
-    for (int u = 0; u < my; ++u) {
+    int issued = 0, cur = -1, segs = 0;
+    bool ok = true;
+    for (int u = 0; u < my && ok; ++u) {
+      const int64_t t = t0 + u;
+      const int row = (int)(t / ct), col = (int)(t % ct);
       const int b = u & 1;
+      if (row != cur) {
+        // N's tile is free once the MMAs of tile u - 1 (and all before) completed
+        if (u > 0 && !mbar_wait(&sm.p_empty[(u - 1) & 1], ((u - 1) >> 1) & 1, st)) break;
+        mbar_expect_tx(&sm.n_full, kD * kBM * kK * 2);
+        for (int s = 0; s < kD; ++s) tma_load_3d(sm.n[s], &map_n, &sm.n_full, 0, row * kBM, s);
+        cur = row;
+        ++segs;
+        // the copies land before this N tile is replaced (or the CTA exits)
+        if (!mbar_wait(&sm.n_full, (segs - 1) & 1, st)) ok = false;
+      }
       // buffer b is free once the MMAs of tile u - 2 completed
-      if (u >= 2 && !mbar_wait(&sm.p_empty[b], ((u >> 1) - 1) & 1, st)) break;
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN;
+      if (!ok || (u >= 2 && !mbar_wait(&sm.p_empty[b], ((u >> 1) - 1) & 1, st))) break;
       mbar_expect_tx(&sm.p_full[b], kD * kBN * kK * 2);
-      for (int t = 0; t < kD; ++t) tma_load_3d(sm.p[b][t], &map_p, &sm.p_full[b], 0, c0, t);
+      for (int q = 0; q < kD; ++q) tma_load_3d(sm.p[b][q], &map_p, &sm.p_full[b], 0, col * kBN, q);
       issued = u + 1;
     }
-    if (my > 0) mbar_wait_drain(&sm.n_full, 0);
     for (int u = issued - 2 < 0 ? 0 : issued - 2; u < issued; ++u) mbar_wait_drain(&sm.p_full[u & 1], (u >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer: per K step and slice s of N, one MMA against P's
     // planes 0 .. KD-1-s stacked along N writes groups s .. KD-1 at once
-    bool ok = my == 0 || mbar_wait(&sm.n_full, 0, st);
-    fence_after_sync();
-    for (int u = 0; u < my && ok; ++u) {
+    int cur = -1, segs = 0;
+    for (int u = 0; u < my; ++u) {
+      const int64_t t = t0 + u;
+      const int row = (int)(t / ct);
       const int b = u & 1;
+      if (row != cur) {
+        cur = row;
+        ++segs;
+        if (!mbar_wait(&sm.n_full, (segs - 1) & 1, st)) break;
+      }
       if (u >= 2 && !mbar_wait(&sm.t_empty[b], ((u >> 1) - 1) & 1, st)) break;
       if (!mbar_wait(&sm.p_full[b], (u >> 1) & 1, st)) break;
       fence_after_sync();
@@ -226,22 +243,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int part = ew >> 2;  // 0..3
-    const int r = m0 + quarter * 32 + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + part * kCols;
-    const bool live = r < na && pivmark[r] == 0;
-    const int er = live ? nexp[r] : 0;
     // rows of this lane in the coalesced layout: 4 i + (lane >> 3), i < 8
     TX* const* rowp = sm.rows[ew] + (lane >> 3);
-    sm.rows[ew][lane] = live ? X + (int64_t)act[r] * ldx : nullptr;
-    __syncwarp();
     TX(*stage)[9] = sm.stage[ew];
     const int jc = lane & 7;
-    // T's entries and the column exponents of tile u + 1 are loaded while tile u
-    // is processed: the loads have a whole tile to land
+    int cur = -1, er = 0;
+    auto enter_row = [&](int row) {  // this warp's 32 rows of row tile `row`
+      const int r = row * kBM + quarter * 32 + lane;
+      const bool live = r < na && pivmark[r] == 0;
+      er = live ? nexp[r] : 0;
+      __syncwarp();
+      sm.rows[ew][lane] = live ? X + (int64_t)act[r] * ldx : nullptr;
+      __syncwarp();
+      cur = row;
+    };
+    // T's entries and the column exponents of tile u + 1 are loaded while tile u is
+    // processed when both lie in the same row tile
     TX xn[kHalves][8];
     int pn = 0;
-    auto fetch = [&](int u) {
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * kCols;
+    auto fetch = [&](int col) {
+      const int c0 = col * kBN + part * kCols;
       pn = (lane < kCols && c0 + lane < tb) ? pexp[c0 + lane] : 0;
 #pragma unroll
       for (int h = 0; h < kHalves; ++h)
@@ -252,17 +274,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           xn[h][i] = (rp != nullptr && c < tb) ? rp[c] : TX(0);
         }
     };
-    if (my > 0) fetch(0);
+    bool have = false;  // xn / pn hold tile u
     for (int u = 0; u < my; ++u) {
+      const int64_t t = t0 + u;
+      const int row = (int)(t / ct), col = (int)(t % ct);
       const int b = u & 1;
-      const int c0 = (blockIdx.y + u * gridDim.y) * kBN + part * kCols;
+      if (row != cur) {
+        enter_row(row);
+        have = false;
+      }
+      if (!have) fetch(col);
+      const int c0 = col * kBN + part * kCols;
       TX xv[kHalves][8];
 #pragma unroll
       for (int h = 0; h < kHalves; ++h)
 #pragma unroll
         for (int i = 0; i < 8; ++i) xv[h][i] = xn[h][i];
       const int pe = pn;  // lane j < kCols: the exponent of column c0 + j
-      if (u + 1 < my) fetch(u + 1);
+      have = false;
+      if (u + 1 < my && (t + 1) / ct == row) {
+        fetch((int)((t + 1) % ct));
+        have = true;
+      }
       if (!mbar_wait(&sm.t_full[b], (u >> 1) & 1, st)) break;
       fence_after_sync();
 #pragma unroll
@@ -399,13 +432,9 @@ cudaError_t update_emu(int na, int bt, int tb, const T* N, const int32_t* act, c
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int rt = (na + kBM - 1) / kBM;
-  const int ct = (tb + bn<KD>() - 1) / bn<KD>();
-  int gy = sms / rt;  // at most one CTA per SM in all (one wave)
-  if (gy > ct) gy = ct;
-  if (gy < 1) gy = 1;
-  k_update_emu<KD, T><<<dim3((unsigned)rt, (unsigned)gy), kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act,
-                                                                             pivmark, X, ldx, st, done);
+  const int64_t tiles = (int64_t)((na + kBM - 1) / kBM) * ((tb + bn<KD>() - 1) / bn<KD>());
+  const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM, balanced tile ranges
+  k_update_emu<KD, T><<<grid, kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act, pivmark, X, ldx, st, done);
   return cudaGetLastError();
 }
 

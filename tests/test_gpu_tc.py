@@ -118,7 +118,7 @@ def test_bf16_generated_omega_runs_and_meets_tolerance(B, orc):
 # ---------------------------------------------------------------- FP32 sketch by digit slicing
 @pytest.mark.parametrize("m,n,rows", [
     (1024, 256, 64),     # whole tiles
-    (1000, 333, 100),    # ragged K, n and rows (four 32-column tiles)
+    (1000, 333, 100),    # ragged K, n and rows (two 64-column tiles)
     (8, 5, 3),           # smaller than every tile
     (40000, 300, 64),    # long K: many exact chunks and split-K partials
     (3000, 1100, 200),

@@ -505,7 +505,10 @@ cudaError_t decide(const double* e2part, int nparts, int w, double tol, int tol_
 // index = smallest column index of A, since `act` is ascending), publication of
 // the block's candidate, one bounded grid barrier, the global pivot and its
 // row, then division by the pivot and the rank-1 update (Eq. lupps) of the
-// block's unselected rows.  Rows are marked, never swapped.
+// block's unselected rows.  Rows are marked, never swapped.  Look-ahead: column
+// c+1 of the update, the candidate for pivot c+1 and the arrival at the next
+// barrier come first; the remaining columns are updated while the barrier fills.
+// Every entry receives the same single FMA per pivot as without look-ahead.
 //
 // The global pivot comes from two 64-bit atomic maxima that every block adds
 // before the barrier: (top, ~row) and (top, row), top = the leading 32 bits of
@@ -572,6 +575,37 @@ __device__ __forceinline__ unsigned long long mag_bits(float x) {
 __device__ __forceinline__ unsigned mag_top(unsigned long long hi, double) { return (unsigned)(hi >> 31); }
 __device__ __forceinline__ unsigned mag_top(unsigned long long hi, float) { return (unsigned)hi; }
 
+// Grid barrier in two halves: every block adds its arrival (after its publications,
+// ordered by the block barrier and the release), works on, then waits for the k-th
+// barrier's (k+1) nblocks arrivals.  The wait is bounded as in grid_barrier.
+__device__ __forceinline__ void grid_arrive(unsigned* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) red_release_add_u32(ctr, 1u);
+}
+__device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, DevState* st) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if ((int)(ld_acquire_u32(ctr) - target) < 0) {
+      const uint64_t t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while ((int)(ld_acquire_u32(ctr) - target) < 0) {
+        if ((++spins & 255u) == 0u) {
+          if (ld_acquire_u32(&st->err) & kErrTimeout) { ok = 0; break; }
+          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicOr(&st->err, kErrTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPanelThreads)
     k_panel_lupp(int na, int w, int steps, T* __restrict__ S, int64_t lds, int chunk, int use_smem, int par,
@@ -601,14 +635,10 @@ __global__ void __launch_bounds__(kPanelThreads)
   for (int r = tid; r < chunk; r += blockDim.x) sel[r] = 0;
   __syncthreads();
 
-  for (int c = 0; c < steps; ++c) {
-    // 1. block-local candidate
-    PivKey loc{0ull, 0u};
-    for (int r = tid; r < nr; r += blockDim.x)
-      if (!sel[r]) loc = key_pick(loc, PivKey{mag_bits(Ss[(int64_t)r * ldl + c]), ~(unsigned)(r0 + r)});
-    loc = block_key_max(loc);
+  // Publish this block's candidate for pivot c (its row complete in every column)
+  // and add the arrival at barrier c.
+  auto publish = [&](int c, PivKey loc) {
     const int lidx = loc.lo == 0u ? -1 : (int)~loc.lo;
-    // 2. publish it: the key maxima, the full pattern and the row
     const int base = (c & 1) * nb;
     unsigned long long* key = &st->pkey[par][c % 3][0];
     if (tid == 0) {
@@ -629,9 +659,23 @@ __global__ void __launch_bounds__(kPanelThreads)
       const T* src = Ss + (int64_t)(lidx - r0) * ldl;
       for (int cc = tid; cc < w; cc += blockDim.x) __stcg(&cand_rows[(int64_t)(base + bid) * w + cc], src[cc]);
     }
-    // 3. wait for every block
-    if (!grid_barrier(ctr, (unsigned)(c + 1) * (unsigned)nb, st)) return;
-    // 4. global pivot (warp 0 of every block, identically) and its row
+    grid_arrive(ctr);
+  };
+
+  // pivot 0's candidate
+  if (steps > 0) {
+    PivKey loc{0ull, 0u};
+    for (int r = tid; r < nr; r += blockDim.x)
+      loc = key_pick(loc, PivKey{mag_bits(Ss[(int64_t)r * ldl]), ~(unsigned)(r0 + r)});
+    publish(0, block_key_max(loc));
+  }
+
+  for (int c = 0; c < steps; ++c) {
+    // 1. every block's candidate for pivot c is published
+    if (!grid_wait(ctr, (unsigned)(c + 1) * (unsigned)nb, st)) return;
+    const int base = (c & 1) * nb;
+    const unsigned long long* key = &st->pkey[par][c % 3][0];
+    // 2. global pivot (warp 0 of every block, identically) and its row
     if (wid == 0) {
       const unsigned long long k0 = __ldcg(&key[0]), k1 = __ldcg(&key[1]);
       int gi = k0 == 0ull ? -1 : (int)~(unsigned)k0;
@@ -664,18 +708,42 @@ __global__ void __launch_bounds__(kPanelThreads)
     }
     __syncthreads();
     const T pv = s_piv >= 0 ? prow[c] : T(0);
-    if (pv == T(0)) continue;  // the column is exactly zero below: nothing to eliminate
-    // 5. multipliers l(i) = S(i,c) / pivot
-    for (int r = tid; r < nr; r += blockDim.x)
-      if (!sel[r]) Ss[(int64_t)r * ldl + c] = Ss[(int64_t)r * ldl + c] / pv;
+    const bool elim = pv != T(0);  // a zero column below: nothing to eliminate
+    // 3. multipliers l(i) = S(i,c) / pivot
+    if (elim)
+      for (int r = tid; r < nr; r += blockDim.x)
+        if (!sel[r]) Ss[(int64_t)r * ldl + c] = Ss[(int64_t)r * ldl + c] / pv;
     __syncthreads();
-    // 6. rank-1 update of the trailing columns (Eq. lupps): a warp per row, lanes
-    //    along the row, four rows at a time with their loads ahead of the stores
-    if (c + 1 < w) {
+    // 4. look-ahead: column c+1 of the rank-1 update (Eq. lupps), the candidate for
+    //    pivot c+1 and its row's remaining columns, then the arrival at barrier c+1
+    int cand = -1;  // local row of the published candidate (updated already)
+    if (c + 1 < steps) {
+      const T p1 = prow[c + 1];
+      PivKey loc{0ull, 0u};
+      for (int r = tid; r < nr; r += blockDim.x)
+        if (!sel[r]) {
+          T* row = Ss + (int64_t)r * ldl;
+          if (elim) row[c + 1] = fma(-row[c], p1, row[c + 1]);
+          loc = key_pick(loc, PivKey{mag_bits(row[c + 1]), ~(unsigned)(r0 + r)});
+        }
+      loc = block_key_max(loc);
+      cand = loc.lo == 0u ? -1 : (int)~loc.lo - r0;
+      if (elim && cand >= 0 && wid == 0) {
+        T* row = Ss + (int64_t)cand * ldl;
+        const T l = row[c];
+        for (int cc = c + 2 + lane; cc < w; cc += 32) row[cc] = fma(-l, prow[cc], row[cc]);
+      }
+      __syncthreads();      // the candidate row is complete before it is published
+      publish(c + 1, loc);
+    }
+    // 5. the rest of the rank-1 update while the barrier fills: a warp per row,
+    //    lanes along the row, four rows at a time with their loads ahead of the stores
+    const int cfirst = c + 1 < steps ? c + 2 : c + 1;
+    if (elim && cfirst < w) {
       T p[kPanelMaxW / 32];
 #pragma unroll
       for (int j = 0; j < kPanelMaxW / 32; ++j) {
-        const int cc = c + 1 + lane + 32 * j;
+        const int cc = cfirst + lane + 32 * j;
         p[j] = cc < w ? prow[cc] : T(0);
       }
       for (int r = wid; r < nr; r += 4 * nw) {
@@ -685,13 +753,13 @@ __global__ void __launch_bounds__(kPanelThreads)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int rr = r + u * nw;
-          live[u] = rr < nr && !sel[rr];
+          live[u] = rr < nr && !sel[rr] && rr != cand;
           rp[u] = Ss + (int64_t)(live[u] ? rr : 0) * ldl;
           l[u] = live[u] ? rp[u][c] : T(0);
         }
 #pragma unroll
         for (int j = 0; j < kPanelMaxW / 32; ++j) {
-          const int cc = c + 1 + lane + 32 * j;
+          const int cc = cfirst + lane + 32 * j;
           if (cc < w) {
             T x[4];
 #pragma unroll

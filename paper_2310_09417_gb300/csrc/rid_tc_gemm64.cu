@@ -1,12 +1,10 @@
 // rid_tc_gemm64.cu -- GEMMs on the BF16 tensor cores by exact digit slicing:
-//   * KD = 7 (FP64 accuracy): the Schur complement of the FP64-emulated path,
-//     P = T(act, 0:K) G(perm, cols) (Alg. 1 lines 10-11 in the T = L2 L1^{-1}
-//     form), written as FP64 split-K partials for the Schur finish;
-//   * KD = 3 (FP32 accuracy): the sketch Y = Omega A of an FP32 matrix (Sec. 2.4),
-//     FP32 split-K partials; A is sliced once per call, Omega once per pass.
-//
-// The description below is for KD = 7; KD = 3 keeps 3 digits (24 bits) per
-// operand, 6 digit pairs in 3 groups, and chunks of 320 K.
+//   * k_gemm_emu<7, double> (FP64 accuracy): the Schur complement of the
+//     FP64-emulated path, P = T(act, 0:K) G(perm, cols) (Alg. 1 lines 10-11 in the
+//     T = L2 L1^{-1} form), written as FP64 split-K partials for the Schur finish;
+//   * k_sketch_f32emu (FP32 accuracy, 3 digits per operand): the sketch Y = Omega A
+//     of an FP32 matrix (Sec. 2.4), FP32 split-K partials; A is sliced once per
+//     call, Omega once per pass (described at the kernel).
 //
 // Both operands change every round, so both are sliced here, with integer
 // operations on the FP64 bit patterns (GB300 issues about two FP64
@@ -46,7 +44,7 @@ constexpr int kBM = 128;      // rows of A per tile
 constexpr int kBK = 64;       // K per step
 constexpr int kThreads = 192;
 // Exact chunk: a group sums at most KD pairs of products <= 2^14, so fewer than
-// 2^24 / (KD 2^14) = 1024 / KD terms: 128 K for KD = 7, 320 K for KD = 3.
+// 2^24 / (KD 2^14) = 1024 / KD terms: 128 K for KD = 7.
 // Columns of B per tile: two accumulator sets of KD groups fit the 512
 // tensor-memory columns.
 template <int KD>
@@ -75,7 +73,6 @@ struct Smem {
   uint32_t tmem_base;
 };
 static_assert(sizeof(Smem<7>) + 1024 <= 232448, "shared memory of k_gemm_emu exceeds 227 KB");
-static_assert(sizeof(Smem<3>) + 1024 <= 232448, "shared memory of k_gemm_emu exceeds 227 KB");
 
 
 // Grid: x = column tiles of B (fastest: CTAs sharing an A tile run together), y = row

@@ -250,8 +250,16 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
       uint64_t x0 = (uint64_t)q, x1 = (uint64_t)((int64_t)t * b + i), x2 = 0, x3 = 0;
       philox4x64_10(x0, x1, x2, x3, p.seed, 0ull);
       double z[4];
-      box_muller(x0, x1, z[0], z[1]);
-      box_muller(x2, x3, z[2], z[3]);
+      if constexpr (sizeof(T) == 4) {  // FP32: the FP32 evaluation of the same map
+        float f[4];
+        box_muller_f32_53(x0, x1, f[0], f[1]);
+        box_muller_f32_53(x2, x3, f[2], f[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) z[j] = f[j];
+      } else {
+        box_muller(x0, x1, z[0], z[1]);
+        box_muller(x2, x3, z[2], z[3]);
+      }
       T* o = sl.omega + i * p.mmax + 4 * q;
       for (int j = 0; j < 4 && 4 * q + j < m; ++j) o[j] = from_d<T>(z[j]);
     }

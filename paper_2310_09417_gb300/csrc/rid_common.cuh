@@ -217,6 +217,43 @@ __device__ __forceinline__ void box_muller_f32(uint64_t a, uint64_t b, float& z0
   z1 = r * sn;
 }
 
+// The same map on the same 53-bit uniforms, evaluated in FP32 for FP32 output:
+// u1 = n1 2^-53 and x = 2 u2 = n2 2^-52 with n1, n2 in [1, 2^53].
+//   ln u1: for u1 >= 1/2 as log1p(-d 2^-53) with d = 2^53 - n1 exact (no cancellation
+//          near u1 = 1), else log(u1) (|ln u1| > 0.69, so rounding u1 costs 2^-24
+//          relative);
+//   the angle: x = x_hi + x_lo with x_hi = x rounded to FP32 (integer rounding of n2)
+//          and the exact remainder x_lo; sincos(pi x) from sincospi(x_hi) and a
+//          first-order correction (second-order terms below 2^-44).
+// Against the FP64 map the result differs by a few FP32 ulp of z plus at most about
+// 2^-23 r absolute (r <= 8.6) where cos or sin is near zero.
+__device__ __forceinline__ void box_muller_f32_53(uint64_t a, uint64_t b, float& z0, float& z1) {
+  const uint64_t n1 = (a >> 11) + 1ull;
+  float ln1;
+  if (n1 >= (1ull << 52)) {
+    const uint64_t d = (1ull << 53) - n1;  // 0 .. 2^52
+    ln1 = log1pf(-(float)d * 0x1.0p-53f);
+  } else {
+    ln1 = logf((float)n1 * 0x1.0p-53f);
+  }
+  const float r = sqrtf(-2.0f * ln1);
+  const uint64_t n2 = (b >> 11) + 1ull;
+  // n2 rounded to 24 significant bits, to nearest even, by integer operations
+  const int len = 64 - __clzll((long long)n2);
+  uint64_t nh = n2;
+  if (len > 24) {
+    const int sh = len - 24;
+    const uint64_t q = n2 >> sh, rem = n2 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    nh = (q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull)) << sh;
+  }
+  const float xh = (float)nh * 0x1.0p-52f;                         // exact: nh has 24 bits
+  const float t = 3.14159265358979323846f * ((float)(int64_t)(n2 - nh) * 0x1.0p-52f);  // pi x_lo
+  float sn, cs;
+  sincospif(xh, &sn, &cs);
+  z0 = r * fmaf(-t, sn, cs);
+  z1 = r * fmaf(t, cs, sn);
+}
+
 template <typename T>
 __device__ __forceinline__ T tabs(T x) {
   return x < T(0) ? -x : x;

@@ -71,6 +71,12 @@ __global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64
       box_muller_f32(x2, x3, f[2], f[3]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) z[j] = f[j];
+    } else if constexpr (sizeof(T) == 4) {  // FP32 output: FP32 evaluation on 53-bit uniforms
+      float f[4];
+      box_muller_f32_53(x0, x1, f[0], f[1]);
+      box_muller_f32_53(x2, x3, f[2], f[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) z[j] = f[j];
     } else {
       box_muller(x0, x1, z[0], z[1]);
       box_muller(x2, x3, z[2], z[3]);

@@ -87,12 +87,16 @@ def assert_id_close(orc, A, g, r, spread):
 # ---------------------------------------------------------------- Omega
 def test_gaussian_rows_match_oracle(B, orc):
     """Same Philox4x64-10 counters and Box-Muller map on both sides; the only
-    difference is libm vs CUDA log/sincospi in the last bits."""
+    difference is libm vs CUDA log/sincospi in the last bits.  FP32 rows evaluate
+    the same map on the same 53-bit uniforms in FP32: a few FP32 ulp of z plus about
+    2^-23 r absolute (r <= 8.6) where the cosine or sine is near zero."""
     g = B.gaussian_rows(2310_09417, 5, 37, 1001, dtype=torch.float64).cpu().numpy()
     o = orc.gaussian_rows(2310_09417, 5, 37, 1001)
     np.testing.assert_allclose(g, o, rtol=1e-14, atol=1e-14)
-    g32 = B.gaussian_rows(7, 0, 3, 130, dtype=torch.float32).cpu().numpy()
-    np.testing.assert_allclose(g32, orc.gaussian_rows(7, 0, 3, 130).astype(np.float32), rtol=1e-6)
+    g32 = B.gaussian_rows(7, 0, 33, 1300, dtype=torch.float32).cpu().numpy()
+    o32 = orc.gaussian_rows(7, 0, 33, 1300)
+    np.testing.assert_allclose(g32, o32, rtol=1e-6, atol=2e-6)
+    assert np.abs(g32 - o32).max() > 0.0  # the FP32 evaluation, not a rounded FP64 one
 
 
 # ---------------------------------------------------------------- fixed rank

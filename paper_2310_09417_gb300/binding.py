@@ -319,8 +319,10 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
     (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major).  `predictor`:
     FP32 CUDA tensor of id_mlp_param_count() parameters; it sets how many blocks
     the second pass over A sketches (results are those of the plain loop).
-    sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit
-    slicing, FP64 accurate, with Omega on the grid 2^-10."""
+    sketch_prec=F64_EMU (FP64 A only): the sketch, Schur GEMM and block update on the
+    tensor cores by exact digit slicing, FP64 accurate, with Omega on the grid 2^-11.
+    sketch_prec=F32_EMU (FP32 A only): the sketch on the tensor cores in 3 digits per
+    operand, FP32 accurate."""
     m, n = A.shape
     kmax = min(m, n) if not k_max else min(k_max, m, n)
     opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,

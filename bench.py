@@ -81,7 +81,7 @@ except (OSError, ValueError):
     PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes per sketch launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures summarised under profiles/, scaled to the full size by the A bytes read.
-PROFILED_TRAFFIC = {"adaptive_poly_f64": 3.38e9}
+PROFILED_TRAFFIC = {"adaptive_poly_f64": 3.40e9, "adaptive_step_f64": 3.40e9}
 
 
 def algorithmic_flops(m: int, n: int, k: int, b: int) -> float:
@@ -614,7 +614,7 @@ def main():
         sk_bytes = (6.0 * kp * n + 16.0 * b * kp + 4.0 * n * b) * res.passes + 10.0 * m * n
         achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
         peak = PEAKS["hbm_gbs"]
-        roofline = {"bound": "hbm", "kernel": "k_gemm_emu<3, float> (tcgen05 + TMA, exact digit slices) + Omega "
+        roofline = {"bound": "hbm", "kernel": "k_sketch_f32emu (tcgen05 + TMA, exact digit slices) + Omega "
                     "slicing + split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(name),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
@@ -635,7 +635,7 @@ def main():
         sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
         achieved = sk_flops / (sk_ms * 1e-3) / 1e12
         peak = ALU_PEAK_TFLOPS[dt]
-        roofline = {"bound": "alu", "kernel": "k_gemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
+        roofline = {"bound": "alu", "kernel": "k_sgemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": PROFILED_TRAFFIC.get(name),
                     "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"

@@ -46,8 +46,9 @@ int num_sms() {
   return cache[dev];
 }
 
-// Split-K factor: enough blocks for about four waves, at least 256 K per split.
-int choose_splits(int64_t M, int64_t N, int64_t K, int sms, int cap) {
+// Split-K factor of the 64 x 64 gather-GEMM (FP64 Schur products): enough blocks
+// for about four waves, at least 256 K per split.
+int choose_splits_gather(int64_t M, int64_t N, int64_t K, int sms, int cap) {
   const int64_t tiles = cdiv(M, 64) * cdiv(N, 64);
   int64_t s = cdiv(4 * (int64_t)sms, tiles);
   s = imin(s, imax(1, K / 256));
@@ -55,12 +56,12 @@ int choose_splits(int64_t M, int64_t N, int64_t K, int sms, int cap) {
   return (int)imax(1, s);
 }
 
-// Split-K factor for the FP32 store GEMM (k_sgemm_gather: 128 x 64 tiles, two
-// blocks per SM): the count (at most cap, at least 128 K per split) minimising
-// waves x (K per split + a fixed cost).
-int choose_splits_sgemm(int64_t M, int64_t N, int64_t K, int sms, int cap) {
+// Split-K factor for the store GEMM (k_sgemm_gather: 128 x 64 tiles, two blocks per
+// SM in FP32, one in FP64): the count (at most cap, at least 128 K per split)
+// minimising waves x (K per split + a fixed cost).
+int choose_splits_sgemm(int64_t M, int64_t N, int64_t K, int sms, int cap, int per_sm) {
   const int64_t tiles = cdiv(M, 128) * cdiv(N, 64);
-  const int64_t slots = 2 * (int64_t)sms;
+  const int64_t slots = (int64_t)per_sm * sms;
   int best = 1;
   double best_t = 1e300;
   for (int64_t s = 1; s <= cap && (s == 1 || K / s >= 128); ++s) {
@@ -193,8 +194,8 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
                  : path == 8  ? tc_fp8_effective_splits(p->m, tc_fp8_splits(p->m, p->n, unit, p->sms))
                  : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
                  : path == 33 ? sketch_f32emu_splits(p->m, p->n, unit, p->sms)
-                 : path == 32 ? gemm_splits((int)p->m, choose_splits_sgemm(p->n, unit, p->m, p->sms, 16))
-                              : gemm_splits((int)p->m, choose_splits(p->n, unit, p->m, p->sms, 16));
+                 : path == 32 ? gemm_splits((int)p->m, choose_splits_sgemm(p->n, unit, p->m, p->sms, 16, 2))
+                              : gemm_splits((int)p->m, choose_splits_sgemm(p->n, unit, p->m, p->sms, 16, 1));
   p->s1_first = p->s1_pass = p->s1_cap = s1;
   p->s2max = 8;
   p->nparts = 2 * p->sms;
@@ -518,8 +519,8 @@ class Engine {
     if (p_.path == 8) return tc_fp8_effective_splits(p_.m, tc_fp8_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
     if (p_.path == 33) return sketch_f32emu_splits(p_.m, p_.n, unit, p_.sms);
-    if (p_.path == 32) return gemm_splits((int)p_.m, choose_splits_sgemm(p_.n, unit, p_.m, p_.sms, 16));
-    return gemm_splits((int)p_.m, choose_splits(p_.n, unit, p_.m, p_.sms, 16));
+    if (p_.path == 32) return gemm_splits((int)p_.m, choose_splits_sgemm(p_.n, unit, p_.m, p_.sms, 16, 2));
+    return gemm_splits((int)p_.m, choose_splits_sgemm(p_.n, unit, p_.m, p_.sms, 16, 1));
   }
 
   int sketch(int64_t row0, int64_t rows, int splits) {
@@ -677,8 +678,9 @@ class Engine {
         }
       }
       if (!done_tc) {
-        nz = gemm_splits((int)tb, std::is_same<T, float>::value ? choose_splits_sgemm(na, w, tb, p_.sms, p_.s2max)
-                                                                 : choose_splits(na, w, tb, p_.sms, p_.s2max));
+        // FP64 Schur products run on the 64 x 64 kernel: about four blocks per SM
+        nz = gemm_splits((int)tb, sizeof(T) == 4 ? choose_splits_sgemm(na, w, tb, p_.sms, p_.s2max, 2)
+                                                 : choose_splits_gather(na, w, tb, p_.sms, p_.s2max));
         Operand<T> a{X_, ldx_, act_[cur_], 0};
         Operand<T> bop{G_, p_.ldg, perm32_, col0};
         EpiArgs<T> ep{Spart_, lds, (int64_t)p_.n * lds, nullptr, nullptr};
@@ -1058,8 +1060,8 @@ int sketch_plan(const id_matrix* A, int64_t rows, id_dtype prec, int* path, int*
             : *path == 8  ? tc_fp8_effective_splits(A->m, tc_fp8_splits(A->m, A->n, rows, sms))
             : *path == 65 ? f64emu_splits(A->m, A->n, sms)
             : *path == 33 ? sketch_f32emu_splits(A->m, A->n, rows, sms)
-            : *path == 32 ? gemm_splits((int)A->m, choose_splits_sgemm(A->n, rows, A->m, sms, 16))
-                          : gemm_splits((int)A->m, choose_splits(A->n, rows, A->m, sms, 16));
+            : *path == 32 ? gemm_splits((int)A->m, choose_splits_sgemm(A->n, rows, A->m, sms, 16, 2))
+                          : gemm_splits((int)A->m, choose_splits_sgemm(A->n, rows, A->m, sms, 16, 1));
   *bytes = 256 + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
   if (*path == 33)  // digits and exponents of A and of Omega
     *bytes += align_up(sketch_f32emu_digit_bytes(A->n, A->m)) + align_up((size_t)A->n * 4) +

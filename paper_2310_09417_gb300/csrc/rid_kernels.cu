@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// FP32 gather-GEMM for the store epilogue (the FP32 sketch and Schur products):
+// Gather-GEMM for the store epilogue (the sketch and Schur products, FP32 and FP64):
 // 128 x 64 tile, 256 threads each owning 8 rows x 4 columns (thread (ty, tx) =
 // (tid / 16, tid % 16): a warp reads two A fragments and sixteen B fragments of
 // shared memory per k, broadcast across its lanes), K steps of 32 double-buffered
@@ -241,16 +241,32 @@ __global__ void __launch_bounds__(256)
 // in 32 distinct banks and the 16-byte fragment reads stay aligned.
 constexpr int kSM = 128, kSN = 64, kSK = 32;
 constexpr int kSAld = kSM + 4, kSBld = kSN + 4;
-constexpr size_t kSgemmSmem = (size_t)2 * kSK * (kSAld + kSBld) * sizeof(float);
+template <typename T>
+constexpr size_t sgemm_smem() {
+  return (size_t)2 * kSK * (kSAld + kSBld) * sizeof(T);
+}
 
-template <bool BK>
-__global__ void __launch_bounds__(256, 2)
-    k_sgemm_gather(int M, int N, int K, int kchunk, Operand<float> a, Operand<float> b, EpiArgs<float> ep,
+// Vector of four for the fragment reads.
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4_32a;
+};
+
+template <typename T, bool BK>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    k_sgemm_gather(int M, int N, int K, int kchunk, Operand<T> a, Operand<T> b, EpiArgs<T> ep,
                    const int32_t* done) {
+  using V4 = typename Vec4<T>::type;
   if (done != nullptr && *done) return;
-  extern __shared__ __align__(16) float sg_smem[];
-  float* As = sg_smem;                   // [2][kSK][kSAld]
-  float* Bs = sg_smem + 2 * kSK * kSAld;  // [2][kSK][kSBld]
+  extern __shared__ __align__(32) unsigned char sg_raw[];
+  T* As = reinterpret_cast<T*>(sg_raw);  // [2][kSK][kSAld]
+  T* Bs = As + 2 * kSK * kSAld;          // [2][kSK][kSBld]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * kSM, n0 = blockIdx.y * kSN;
@@ -260,45 +276,45 @@ __global__ void __launch_bounds__(256, 2)
 
   // loader coordinates: lanes cover 8 consecutive k of 4 rows
   const int lk = lane & 7, lr = warp * 4 + (lane >> 3);  // lr < 32
-  const float* ap[4];
+  const T* ap[4];
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     const int m = m0 + g * 32 + lr;
     ap[g] = m < M ? a.base + (int64_t)(a.idx ? a.idx[m] : m) * a.ld + a.off : nullptr;
   }
-  const float* bp[2];
+  const T* bp[2];
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     const int n = n0 + g * 32 + lr;
     bp[g] = (BK && n < N) ? b.base + (int64_t)(b.idx ? b.idx[n] : n) * b.ld + b.off : nullptr;
   }
-  float ra[16], rb[8];
+  T ra[16], rb[8];
   auto load = [&](int k0) {
 #pragma unroll
     for (int it = 0; it < 16; ++it) {
       const int k = k0 + (it & 3) * 8 + lk;
-      const float* p = ap[it >> 2];
-      ra[it] = (p != nullptr && k < kend) ? p[k] : 0.0f;
+      const T* p = ap[it >> 2];
+      ra[it] = (p != nullptr && k < kend) ? p[k] : T(0);
     }
     if (BK) {
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
         const int k = k0 + (it & 3) * 8 + lk;
-        const float* p = bp[it >> 2];
-        rb[it] = (p != nullptr && k < kend) ? p[k] : 0.0f;
+        const T* p = bp[it >> 2];
+        rb[it] = (p != nullptr && k < kend) ? p[k] : T(0);
       }
     } else {
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
         const int e = it * 256 + tid, kk = e >> 6, n = e & 63;
         const int k = k0 + kk;
-        rb[it] = (k < kend && n0 + n < N) ? b.base[(int64_t)(b.idx ? b.idx[k] : k) * b.ld + b.off + n0 + n] : 0.0f;
+        rb[it] = (k < kend && n0 + n < N) ? b.base[(int64_t)(b.idx ? b.idx[k] : k) * b.ld + b.off + n0 + n] : T(0);
       }
     }
   };
   auto store = [&](int buf) {
-    float* as = As + buf * kSK * kSAld;
-    float* bs = Bs + buf * kSK * kSBld;
+    T* as = As + buf * kSK * kSAld;
+    T* bs = Bs + buf * kSK * kSBld;
 #pragma unroll
     for (int it = 0; it < 16; ++it) as[((it & 3) * 8 + lk) * kSAld + (it >> 2) * 32 + lr] = ra[it];
     if (BK) {
@@ -313,11 +329,11 @@ __global__ void __launch_bounds__(256, 2)
     }
   };
 
-  float acc[8][4];
+  T acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
   if (ntiles > 0) {
     load(kbeg);
@@ -326,25 +342,25 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   for (int t = 0; t < ntiles; ++t) {
     if (t + 1 < ntiles) load(kbeg + (t + 1) * kSK);
-    const float* as = As + (t & 1) * kSK * kSAld + ty * 8;
-    const float* bs = Bs + (t & 1) * kSK * kSBld + tx * 4;
+    const T* as = As + (t & 1) * kSK * kSAld + ty * 8;
+    const T* bs = Bs + (t & 1) * kSK * kSBld + tx * 4;
 #pragma unroll 8
     for (int kk = 0; kk < kSK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(as + kk * kSAld);
-      const float4 a1 = *reinterpret_cast<const float4*>(as + kk * kSAld + 4);
-      const float4 bv = *reinterpret_cast<const float4*>(bs + kk * kSBld);
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bw[4] = {bv.x, bv.y, bv.z, bv.w};
+      const V4 a0 = *reinterpret_cast<const V4*>(as + kk * kSAld);
+      const V4 a1 = *reinterpret_cast<const V4*>(as + kk * kSAld + 4);
+      const V4 bv = *reinterpret_cast<const V4*>(bs + kk * kSBld);
+      const T av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const T bw[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bw[j], acc[i][j]);
     }
     if (t + 1 < ntiles) store((t + 1) & 1);
     __syncthreads();
   }
 
-  float* out = ep.out + blockIdx.z * ep.zstride;
+  T* out = ep.out + blockIdx.z * ep.zstride;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = m0 + ty * 8 + i;
@@ -375,25 +391,25 @@ cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int kchunk = split_chunk(K, splits);
   splits = (K + kchunk - 1) / kchunk;
-  if constexpr (std::is_same<T, float>::value) {
-    if (epi == kEpiStore) {
-      static bool attr = false;
-      if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sgemm_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSgemmSmem);
-        if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(k_sgemm_gather<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kSgemmSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
-      dim3 g((M + kSM - 1) / kSM, (N + kSN - 1) / kSN, splits);
-      if (b_kmajor)
-        k_sgemm_gather<true><<<g, 256, kSgemmSmem, s>>>(M, N, K, kchunk, a, b, ep, done);
-      else
-        k_sgemm_gather<false><<<g, 256, kSgemmSmem, s>>>(M, N, K, kchunk, a, b, ep, done);
-      return cudaGetLastError();
+  // the double-buffered kernel for stores; in FP64 only for the sketch (K-major B):
+  // its one block per SM measured slower than the 64 x 64 kernel on the Schur shapes
+  if (epi == kEpiStore && (sizeof(T) == 4 || b_kmajor)) {
+    constexpr size_t smem = sgemm_smem<T>();
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_sgemm_gather<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sgemm_gather<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
     }
+    dim3 g((M + kSM - 1) / kSM, (N + kSN - 1) / kSN, splits);
+    if (b_kmajor)
+      k_sgemm_gather<T, true><<<g, 256, smem, s>>>(M, N, K, kchunk, a, b, ep, done);
+    else
+      k_sgemm_gather<T, false><<<g, 256, smem, s>>>(M, N, K, kchunk, a, b, ep, done);
+    return cudaGetLastError();
   }
   dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN, splits);
   if (b_kmajor) {

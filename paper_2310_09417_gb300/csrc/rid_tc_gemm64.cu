@@ -23,7 +23,8 @@
 //
 //   warp 0    TMA: B's 7 digit tiles per K step (two buffers), then A's digit
 //             tiles one slice per stage
-//   warp 1    tensor memory; per (K step, slice s) 4 (7 - s) MMAs M=128 N=32 K=16
+//   warp 1    tensor memory; per (K step, slice s) 4 MMAs M=128 N=32 (7 - s) K=16 against
+//             B's planes stacked along N
 //   warps 2-5 epilogue
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -153,7 +154,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c = cb - 2 < 0 ? 0 : cb - 2; c < cb; ++c) mbar_wait_drain(&sm.b_full[c & 1], (c >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
     int ai = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
@@ -171,14 +171,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_after_sync();
           const uint64_t da = desc_sw128(sm.a[st_]);
-          for (int t = 0; t + s < kD; ++t) {
-            const uint64_t db = desc_sw128(sm.b[u][jj][t]);
-            const uint32_t dst = tmem + u * kGroupCols + (s + t) * kBN;
-            // group s + t is first written at slice 0 (t = s + t), K step 0 of the chunk
+          // B's planes 0 .. KD-1-s lie back to back: one MMA with N = kBN (KD - s) writes
+          // groups s .. KD-1; every group is first written at slice 0, K step 0 of the chunk
+          const uint64_t db = desc_sw128(sm.b[u][jj][0]);
+          const uint32_t dst = tmem + u * kGroupCols + s * kBN;
+          const uint32_t idn = idesc_bf16(kBM, kBN * (kD - s));
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-              mma_bf16(dst, da + 2 * kk, db + 2 * kk, idesc, (jj > 0 || s > 0 || kk > 0) ? 1u : 0u);
-          }
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            mma_bf16(dst, da + 2 * kk, db + 2 * kk, idn, (jj > 0 || s > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&sm.a_empty[st_]);
         }
       }

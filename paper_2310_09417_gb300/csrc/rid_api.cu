@@ -197,7 +197,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
                  : path == 32 ? gemm_splits((int)p->m, choose_splits_sgemm(p->n, unit, p->m, p->sms, 16, 2))
                               : gemm_splits((int)p->m, choose_splits_sgemm(p->n, unit, p->m, p->sms, 16, 1));
   p->s1_first = p->s1_pass = p->s1_cap = s1;
-  p->s2max = 8;
+  // Schur split-K partials: FP32 products may split K 32 ways (late rounds: few rows of
+  // S, thousands of earlier pivots); FP64 ones 8 (the FP64-accurate digit GEMM caps at 8)
+  p->s2max = p->esz == 4 ? 32 : 8;
   p->nparts = 2 * p->sms;
   p->maxg = p->sms;
   const size_t e = p->esz;

@@ -21,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -173,7 +174,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        # RANDID_CLOCKS_DIR keeps the raw samples; by default they go to the temp directory
+        out = os.environ.get("RANDID_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, "randid_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:

@@ -231,7 +231,8 @@ def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
     import numpy as np
 
     import oracle
-    m, n, _, _, _, tol, b = WORKLOADS[name]
+    _, _, _, _, _, tol, b = WORKLOADS[name]
+    m, n = A_host_f64.shape  # the workload's size on a GPU machine; reduced without a GPU
     kmax = rounds * b
     Om = oracle.gaussian_rows(seed, 0, (rounds + 1) * b, m)
     t0 = time.perf_counter()
@@ -240,7 +241,7 @@ def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
     k = r["k"]
     flops = algorithmic_flops(m, n, k, b)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    desc = ("oracle (plain C, FP64, OpenMP) on the first %d rounds of Algorithm 1 over the full "
+    desc = ("oracle (plain C, FP64, OpenMP) on the first %d rounds of Algorithm 1 over the whole "
             "%dx%d matrix (k_max = %d), %.1f s" % (rounds, m, n, kmax, dt))
     del np
     return flops / dt / 1e9, dt, threads, desc

@@ -253,7 +253,7 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
    Asynchronous on `stream`.  Returns -1 (A), -2 (Q/ldq), -4 (block_scale). */
 int id_quantize_fp8(const id_matrix* A, void* Q, int64_t ldq, float* block_scale, int pow2, void* stream);
 
-/* The sketch alone (Sec. 2.4; Algorithm 1 line 9): G = (Omega A)^T, n x rows,
+/* The sketch alone (Sec. 2.4; the sampling step of Algorithm 1): G = (Omega A)^T, n x rows,
    row-major with row stride ldg >= rows (row j holds the sketch of column j).
    omega: DEVICE, row-major rows x m, row stride ld_omega >= m, dtype sketch_prec.
    Paths: A F64 / sketch F64 (FP64 FMA, G in FP64); A F32 / F32 (FP32 FMA, G in

@@ -225,7 +225,7 @@ int orc_id_adaptive(int64_t m, int64_t n, const double* A, int64_t lda,
   int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * n);
   int status = ORC_OK;
 
-  /* lines 1-4: first sample, its LUPP, L1 and L2 */
+  /* Alg. 1, start: the first sample, its LUPP, and L1, L2 from its factors */
   int64_t t = 0;
   if ((t + 1) * b > rows_avail) { status = ORC_BAD_ARG; goto done; }
   orc_sketch_t(m, n, A, lda, b, Omega, G);
@@ -238,24 +238,24 @@ int orc_id_adaptive(int64_t m, int64_t n, const double* A, int64_t lda,
     L[c + c * n] = 1.0;
   }
   int64_t tb = b0;
-  /* line 5-6: E(0) = tol + 1, t = 1 */
+  /* E(0) = tol + 1 (so the loop runs at least once) and t = 1 */
   t = 1;
   int64_t nrounds = 0;
   for (;;) {
     if (tb == n) break; /* every column is a skeleton: the residual is exactly zero */
-    /* lines 8-9: independent block and its sample */
+    /* Alg. 1, loop: a new independent Gaussian block and its sample */
     if ((t + 1) * b > rows_avail) { status = ORC_BAD_ARG; goto done; }
     orc_sketch_t(m, n, A, lda, b, Omega + t * b * m, G);
     for (int64_t c = 0; c < b; ++c)
       for (int64_t i = 0; i < n; ++i) PG[i + c * n] = G[p[i] + c * n];
-    /* line 10: U2 = L1^{-1} (P Y)(1:tb,:) by forward substitution */
+    /* U2 = L1^{-1} (P Y)(1:tb,:) by forward substitution */
     for (int64_t c = 0; c < b; ++c)
       for (int64_t i = 0; i < tb; ++i) {
         double s = PG[i + c * n];
         for (int64_t j = 0; j < i; ++j) s -= L[i + j * n] * U2[j + c * cap];
         U2[i + c * cap] = s;
       }
-    /* line 11: S = (P Y)(tb+1:end,:) - L2 U2 */
+    /* the Schur complement S = (P Y)(tb+1:end,:) - L2 U2 */
     const int64_t ns = n - tb;
     for (int64_t c = 0; c < b; ++c)
       for (int64_t i = 0; i < ns; ++i) {
@@ -263,20 +263,20 @@ int orc_id_adaptive(int64_t m, int64_t n, const double* A, int64_t lda,
         for (int64_t j = 0; j < tb; ++j) s -= L[tb + i + j * n] * U2[j + c * cap];
         S[i + c * ns] = s;
       }
-    /* line 12: E = ||S||_F, scaled for N(0,1) blocks (variance reading of 1/b) */
+    /* the estimate E = ||S||_F, scaled for N(0,1) blocks (variance reading of 1/b) */
     double s2 = 0.0;
     for (int64_t c = 0; c < b; ++c)
       for (int64_t i = 0; i < ns; ++i) s2 += S[i + c * ns] * S[i + c * ns];
     double E = sqrt(s2 / (double)b);
     if (trace && nrounds < trace_cap) trace[nrounds] = E;
     ++nrounds;
-    if (E <= tol) break;                            /* line 7 test */
+    if (E <= tol) break;                            /* the loop's stopping test */
     if (tb == cap) { status = ORC_TOL_NOT_MET; break; }
     const int64_t bt = (b < cap - tb) ? b : (cap - tb);
-    /* line 13: LUPP of S; labels are the original column indices */
+    /* LUPP of S; labels are the original column indices */
     for (int64_t i = 0; i < ns; ++i) orig[i] = p[tb + i];
     orc_lupp(ns, b, bt, S, ns, orig);
-    /* lines 14-15: apply P-hat to the rows of L2 and append the new block */
+    /* apply P-hat to the rows of L2 and append the new block's factor */
     /* the row now at position tb+i of S came from position pos[orig[i]] */
     for (int64_t i = 0; i < n; ++i) pos[p[i]] = i;
     for (int64_t j = 0; j < tb; ++j) {
@@ -288,14 +288,14 @@ int orc_id_adaptive(int64_t m, int64_t n, const double* A, int64_t lda,
       for (int64_t i = c + 1; i < ns; ++i) L[tb + i + (tb + c) * n] = S[i + c * ns];
       L[tb + c + (tb + c) * n] = 1.0;
     }
-    /* line 17: P(t) = diag(I, P-hat) P(t-1) */
+    /* P(t) = diag(I, P-hat) P(t-1) */
     for (int64_t i = 0; i < ns; ++i) p[tb + i] = orig[i];
     tb += bt;
     ++t;
   }
   *k_out = tb;
   if (rounds) *rounds = nrounds;
-  /* lines 20-21 */
+  /* after the loop: J from P, and the interpolation matrix X from L (Eq. inty) */
   for (int64_t i = 0; i < tb; ++i) J[i] = p[i];
   orc_form_x(n, tb, L, n, p, X, ldx);
 done:

@@ -1,7 +1,7 @@
 // rid_tc_gemm64.cu -- GEMMs on the BF16 tensor cores by exact digit slicing:
 //   * k_gemm_emu<7, double> (FP64 accuracy): the Schur complement of the
-//     FP64-emulated path, P = T(act, 0:K) G(perm, cols) (Alg. 1 lines 10-11 in the
-//     T = L2 L1^{-1} form), written as FP64 split-K partials for the Schur finish;
+//     FP64-emulated path, P = T(act, 0:K) G(perm, cols) (Algorithm 1's Schur step in
+//     the T = L2 L1^{-1} form), written as FP64 split-K partials for the Schur finish;
 //   * k_sketch_f32emu (FP32 accuracy, 3 digits per operand): the sketch Y = Omega A
 //     of an FP32 matrix (Sec. 2.4), FP32 split-K partials; A is sliced once per
 //     call, Omega once per pass (described at the kernel).

@@ -1,7 +1,7 @@
 // rid_tc_sketch.cu -- the sketch Y = Omega A on the 5th-generation tensor cores.
 //
 // G (n x rows) = (Omega A)^T with A (m x n, column-major, BF16) and Omega (rows x m,
-// row-major, BF16), FP32 accumulation in tensor memory (Sec. 2.4; Alg. 1 line 9).
+// row-major, BF16), FP32 accumulation in tensor memory (Sec. 2.4; the sampling step of Algorithm 1).
 // Both operands are K-major (K = m): a column of A and a row of Omega are contiguous.
 //
 // One CTA computes a 128 (columns of A) x BN (rows of Omega) tile over a K range:

@@ -1,5 +1,5 @@
 // rid_tc_update.cu -- the block update of the interpolation coefficients,
-// T(rest, old) -= N T(piv, old) (re-blocking, Alg. 1 lines 14-17, in the
+// T(rest, old) -= N T(piv, old) (Algorithm 1's re-blocking, in the
 // T = L2 L1^{-1} form), on the BF16 tensor cores by exact digit slicing, for
 // FP64 T (KD = 7 digits per operand) and FP32 T (KD = 3).
 //

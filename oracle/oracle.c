@@ -316,18 +316,23 @@ double orc_fro_norm(int64_t m, int64_t n, const double* A, int64_t lda) {
 
 double orc_id_residual(int64_t m, int64_t n, const double* A, int64_t lda,
                        int64_t k, const int64_t* J, const double* X, int64_t ldx) {
-  double total = 0.0;
-#pragma omp parallel for schedule(static) reduction(+ : total)
+  /* per-column sums of squares in parallel, then added in column order, so the
+     value does not depend on how the threads finish */
+  double* col = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j) {
-    double col = 0.0;
+    double s = 0.0;
     for (int64_t i = 0; i < m; ++i) {
       double approx = 0.0;
       for (int64_t c = 0; c < k; ++c) approx += A[i + J[c] * lda] * X[c + j * ldx];
       double d = A[i + j * lda] - approx;
-      col += d * d;
+      s += d * d;
     }
-    total += col;
+    col[j] = s;
   }
+  double total = 0.0;
+  for (int64_t j = 0; j < n; ++j) total += col[j];
+  free(col);
   return sqrt(total);
 }
 

@@ -84,6 +84,22 @@ def test_norms_and_residual_match_numpy(orc):
     assert orc.stable_residual(A, J) == pytest.approx(np.linalg.norm(A - Q @ (Q.T @ A)), rel=1e-11)
 
 
+def test_residual_sums_columns_in_order(orc):
+    """The residual's column sums are added in column order, whatever the
+    threads: the value is that of the sequential sum, call after call."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((200, 300))
+    J = np.array([7, 150, 3, 299])
+    X = rng.standard_normal((4, 300))
+    D = A - A[:, J] @ X
+    seq = 0.0
+    for j in range(300):  # the same per-column sums, added in order
+        seq += float(np.sum(D[:, j] ** 2))
+    vals = {orc.id_residual(A, J, X) for _ in range(20)}
+    assert len(vals) == 1
+    assert vals.pop() == pytest.approx(np.sqrt(seq), rel=1e-14)
+
+
 # ------------------------------------------------------------ LUPP
 def test_lupp_hand_worked_example(orc):
     g = json.load(open(os.path.join(GOLDEN, "lupp_4x3_hand.json")))

@@ -261,7 +261,7 @@ int id_quantize_fp8(const id_matrix* A, void* Q, int64_t ldq, float* block_scale
    FP32; A->ld and ld_omega multiples of 8, 16-byte aligned bases, else
    ID_ERR_UNSUPPORTED); A FP8_E4M3 / FP8_E4M3 (block scales in A->block_scale,
    tcgen05 kind::f8f6f4, FP32 accumulation per 128-row block, G in FP32; A->ld
-   and ld_omega multiples of 16); A F64 / ID_F64_EMU (omega F64, rounded to the grid 2^-10,
+   and ld_omega multiples of 16); A F64 / ID_F64_EMU (omega F64, rounded to the grid 2^-11,
    then the FP64-accurate digit-sliced product on the tensor cores, G in FP64).
    ws: at least id_sketch_workspace_size bytes, 256-aligned. */
 int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_prec, size_t* bytes);

@@ -137,6 +137,31 @@ def test_lupp_matches_lapack_getrf(orc, shape):
     np.testing.assert_allclose(np.triu(LU[:kk]), U, atol=1e-12)
 
 
+def test_column_id_is_the_row_id_of_the_transpose(orc):
+    """The paper states randLUPP as a row ID (Sec. 3.1): Y = B Omega_r, LUPP of
+    Y, the first k pivot rows I, and B ~ W B(I,:) with W = P^T [I; L2 L1^{-1}]
+    (Eq. inty).  Written here in that form with LAPACK's getrf (no ties on
+    Gaussian data), applied to B = A^T with Omega_r = Omega^T, it gives the
+    oracle's column ID of A: J = I and X = W^T."""
+    rng = np.random.default_rng(17)
+    m, n, l, k = 50, 40, 12, 8
+    A = rng.standard_normal((m, n))
+    Om = rng.standard_normal((l, m))
+    B, Om_r = A.T, Om.T
+    Y = B @ Om_r  # n x l
+    P, L, _ = sla.lu(Y)
+    perm = np.argmax(P, axis=0)  # Y[perm] = L U
+    T = sla.solve_triangular(L[:k, :k], L[k:, :k].T, trans="T", lower=True, unit_diagonal=True).T
+    Wt = np.zeros((n, k))
+    Wt[perm[:k]] = np.eye(k)
+    Wt[perm[k:]] = T
+    r = orc.id_fixed_rank(A, Om, k)
+    assert np.array_equal(r["J"], perm[:k])
+    np.testing.assert_allclose(r["X"], Wt.T, rtol=0, atol=1e-12 * np.abs(Wt).max())
+    # W(I,:) = I: the skeleton rows are reproduced exactly by the row ID
+    np.testing.assert_array_equal(Wt[perm[:k]], np.eye(k))
+
+
 def test_lupp_invariants(orc):
     """PA = LU to O(u)||A||, unit diagonal, |L| <= 1 (Eq. lupp)."""
     rng = np.random.default_rng(3)

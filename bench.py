@@ -378,7 +378,7 @@ def make_batch(name, device, seed=2310_09417 + 3):
     return As
 
 
-def run_batched(args, rank, world, dev, barrier, max_over_ranks):
+def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks):
     import torch
 
     from paper_2310_09417_gb300 import binding as B
@@ -417,7 +417,10 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks):
     barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
     flops = sum(algorithmic_flops(A.shape[0], A.shape[1], r.k, b) for A, r in zip(As, res))
-    value = flops * world / (ms * 1e-3) / 1e9
+    # whole job: the work of every rank (replicas with their own seeds) over the slowest rank's time
+    flops_all = sum_over_ranks(flops)
+    ids_all = sum_over_ranks(float(len(As)))
+    value = flops_all / (ms * 1e-3) / 1e9
     ks = [r.k for r in res]
     peak = ALU_PEAK_TFLOPS[dt]
     achieved = flops / (ms * 1e-3) / 1e12
@@ -453,7 +456,7 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks):
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+        e2e = {"value": flops_all / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in xh)}
         del hosts, devs, xh
     cpu = None
@@ -487,9 +490,22 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks):
                                                 "bf16": "bf16 (sketch), f32 (LU)"}.get(dt, dt),
                 "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
-                "result": {"ids_per_s": len(As) * world / (ms * 1e-3), "gflop_per_step": flops / 1e9,
+                "result": {"ids_per_s": ids_all / (ms * 1e-3), "gflop_per_step": flops / 1e9,
                            "statuses": sorted(set(r.status for r in res))}}
         print(json.dumps(line), flush=True)
+
+
+def over_ranks(x: float, op: str, world: int, device) -> float:
+    """x reduced over the ranks of the default process group, op "max" or "sum",
+    as one FP64 value on `device` (a CUDA device under NCCL, the CPU under gloo);
+    x itself on a single rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    return float(t.item())
 
 
 def local_gpu(dev):
@@ -530,11 +546,10 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return over_ranks(x, "max", world, dev)
+
+    def sum_over_ranks(x: float) -> float:
+        return over_ranks(x, "sum", world, dev)
 
     from paper_2310_09417_gb300 import binding as B
     from paper_2310_09417_gb300 import build
@@ -543,7 +558,7 @@ def main():
 
     name = args.workload
     if WORKLOADS[name][2] == "kernel":
-        run_batched(args, rank, world, dev, barrier, max_over_ranks)
+        run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -583,7 +598,8 @@ def main():
     ms = max_over_ranks(ms_local)
     res = results[-1]
     flops = algorithmic_flops(m, n, res.k, b)
-    value = flops * world / (ms * 1e-3) / 1e9
+    flops_all = sum_over_ranks(flops)  # every rank's ID (own seed) over the slowest rank's time
+    value = flops_all / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel: the sketch GEMM (+ its split-K reduction)
     sk_ms = sum(r.phase_ms["sketch"] for r in results) / args.steps
@@ -690,7 +706,7 @@ def main():
         e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         xel = torch.empty((), dtype=xdt).element_size()
         h2d = A_host.numel() * A_host.element_size() + (S_host.numel() * 4 if is8 else 0)
-        e2e = {"value": flops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+        e2e = {"value": flops_all / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": r.k * n * xel + 8 * r.k}
         del A_host, A_dev, X_host, A_in

@@ -490,17 +490,13 @@ cudaError_t launch(const Params& p0, const Config& c, int sms, cudaStream_t s) {
   const int grid = sms * c.per_sm;
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  // the shared-memory limit is raised once per kernel variant and size (never
-  // inside a stream capture: the tuner launches every variant first)
+  // the shared-memory limit is raised once per kernel variant, device and size
+  // (never inside a stream capture: the tuner launches every variant first)
 #define RID_BAT_LAUNCH(BM, MINB)                                                                            \
   do {                                                                                                      \
-    static size_t raised = 0;                                                                               \
-    if (smem > raised) {                                                                                    \
-      e = cudaFuncSetAttribute(k_batched<T, BM, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                               (int)smem);                                                                  \
-      if (e != cudaSuccess) return e;                                                                       \
-      raised = smem;                                                                                        \
-    }                                                                                                       \
+    static SmemLimit lim;                                                                                   \
+    e = raise_smem(k_batched<T, BM, MINB>, smem, lim);                                                      \
+    if (e != cudaSuccess) return e;                                                                         \
     k_batched<T, BM, MINB><<<grid, kNT, smem, s>>>(p);                                                      \
   } while (0)
   if (c.bm == 64 && c.per_sm == 1) RID_BAT_LAUNCH(64, 1);

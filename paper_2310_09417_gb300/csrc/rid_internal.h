@@ -8,9 +8,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "rid_common.cuh"
 
 namespace rid {
+
+// A kernel launched with more than the default 48 KB of dynamic shared memory
+// needs its limit raised first (cudaFuncSetAttribute).  That attribute belongs
+// to each device's context, so the size already raised is kept per device; the
+// check is an atomic load, and the raise runs under a lock so that concurrent
+// callers never lower a limit another one relies on.
+constexpr int kMaxDevices = 64;
+struct SmemLimit {
+  std::atomic<size_t> raised[kMaxDevices];
+};
+inline std::mutex& smem_limit_mutex() {
+  static std::mutex m;
+  return m;
+}
+template <typename K>
+inline cudaError_t raise_smem(K* func, size_t bytes, SmemLimit& lim) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool keep = dev >= 0 && dev < kMaxDevices;
+  if (keep && lim.raised[dev].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  std::lock_guard<std::mutex> guard(smem_limit_mutex());
+  if (keep && lim.raised[dev].load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(reinterpret_cast<const void*>(func), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+  if (e == cudaSuccess && keep) lim.raised[dev].store(bytes, std::memory_order_release);
+  return e;
+}
 
 // Operand of the gather-GEMM: row r lives at base + (idx ? idx[r] : r) * ld + off.
 template <typename T>

@@ -20,17 +20,6 @@
 
 namespace rid {
 
-// Raise a kernel's dynamic shared-memory limit when a launch needs more than
-// the default 48 KB (tracked per kernel so the call is made once per size).
-template <typename K>
-static cudaError_t ensure_smem(K* func, size_t bytes, size_t* cached) {
-  if (bytes <= 48 * 1024 || bytes <= *cached) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(func),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) *cached = bytes;
-  return e;
-}
-
 // Element conversions (round to nearest) shared by the FP64/FP32/BF16 instantiations.
 template <typename T>
 __device__ __forceinline__ T from_double(double x) {
@@ -395,15 +384,10 @@ cudaError_t gemm_gather(int M, int N, int K, int splits, bool b_kmajor, Operand<
   // its one block per SM measured slower than the 64 x 64 kernel on the Schur shapes
   if (epi == kEpiStore && (sizeof(T) == 4 || b_kmajor)) {
     constexpr size_t smem = sgemm_smem<T>();
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_sgemm_gather<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sgemm_gather<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static SmemLimit lim_kmajor, lim_nmajor;
+    cudaError_t e = raise_smem(k_sgemm_gather<T, true>, smem, lim_kmajor);
+    if (e == cudaSuccess) e = raise_smem(k_sgemm_gather<T, false>, smem, lim_nmajor);
+    if (e != cudaSuccess) return e;
     dim3 g((M + kSM - 1) / kSM, (N + kSN - 1) / kSN, splits);
     if (b_kmajor)
       k_sgemm_gather<T, true><<<g, 256, smem, s>>>(M, N, K, kchunk, a, b, ep, done);
@@ -864,13 +848,13 @@ template <typename T>
 cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T* S, int64_t lds, int32_t* piv,
                        int32_t* pivmark, double* pivdiag, double* cand_v, int32_t* cand_i, T* cand_rows,
                        DevState* st, cudaStream_t s) {
-  static size_t cached = 0;
+  static SmemLimit lim;
   if (w > kPanelMaxW || (par != 0 && par != 1)) return cudaErrorInvalidValue;
   // the kernel addresses chunk rows at stride w + 1 and the selection bytes after them
   if (cfg.chunk < 1 || (int64_t)cfg.chunk * cfg.grid < na ||
       cfg.smem < panel_smem_bytes(cfg.chunk, w, sizeof(T), cfg.use_smem != 0))
     return cudaErrorInvalidValue;
-  cudaError_t e = ensure_smem(k_panel_lupp<T>, cfg.smem, &cached);
+  cudaError_t e = raise_smem(k_panel_lupp<T>, cfg.smem, lim);
   if (e != cudaSuccess) return e;
   int chunk = cfg.chunk, use_smem = cfg.use_smem;
   void* args[] = {&na, &w, &steps, &S, &lds, &chunk, &use_smem, &par, &piv, &pivmark,
@@ -917,11 +901,11 @@ __global__ void k_linv(int bt, const T* __restrict__ S, int64_t lds, const int32
 template <typename T>
 cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
                  cudaStream_t s) {
-  static size_t cached = 0;
+  static SmemLimit lim;
   const size_t one = (size_t)bt * bt * sizeof(T);
   const int x_in_smem = 2 * one <= (size_t)200 * 1024 ? 1 : 0;
   const size_t smem = x_in_smem ? 2 * one : one;
-  cudaError_t e = ensure_smem(k_linv<T>, smem, &cached);
+  cudaError_t e = raise_smem(k_linv<T>, smem, lim);
   if (e != cudaSuccess) return e;
   const int threads = (kLinvSplit * bt + 31) / 32 * 32;
   k_linv<T><<<1, threads, smem, s>>>(bt, S, lds, piv, Linv, x_in_smem, done);
@@ -960,8 +944,8 @@ template <typename T>
 cudaError_t make_n(int na, int bt, const T* S, int64_t lds, const T* Linv, const int32_t* pivmark,
                    const int32_t* act, T* Nbuf, T* X, int64_t ldx, int64_t tb, const int32_t* piv,
                    int32_t* pivorig, const int32_t* done, cudaStream_t s) {
-  static size_t cached = 0;
-  cudaError_t e = ensure_smem(k_make_n<T>, (size_t)bt * bt * sizeof(T), &cached);
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(k_make_n<T>, (size_t)bt * bt * sizeof(T), lim);
   if (e != cudaSuccess) return e;
   int64_t blocks = ((int64_t)na * bt + 255) / 256;
   if (blocks > 1216) blocks = 1216;

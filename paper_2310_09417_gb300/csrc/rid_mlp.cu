@@ -212,13 +212,8 @@ int id_mlp_loss_grad(const float* params, int64_t batch, const float* x, const f
   if (grad == nullptr) return -5;
   if (loss == nullptr) return -6;
   const size_t smem = sizeof(float) * rid::mlp::kH * rid::mlp::kH;
-  static bool raised = false;
-  if (!raised) {
-    if (cudaFuncSetAttribute(rid::mlp::k_loss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return ID_ERR_CUDA;
-    raised = true;
-  }
+  static rid::SmemLimit lim;
+  if (rid::raise_smem(rid::mlp::k_loss_grad, smem, lim) != cudaSuccess) return ID_ERR_CUDA;
   rid::mlp::k_loss_grad<<<1, rid::mlp::kH, smem, static_cast<cudaStream_t>(stream)>>>(params, batch, x, target,
                                                                                      grad, loss);
   return cudaGetLastError() == cudaSuccess ? ID_OK : ID_ERR_CUDA;

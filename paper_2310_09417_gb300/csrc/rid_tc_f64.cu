@@ -375,12 +375,9 @@ cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, 
   const int64_t ytiles = (n + tc64::kBM - 1) / tc64::kBM;
   if (ytiles > 65535 || splits > 65535) return cudaErrorInvalidValue;
   const size_t smem = sizeof(tc64::Smem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc64::k_sketch_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(tc64::k_sketch_f64emu, smem, lim);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((rows + tc64::kBN - 1) / tc64::kBN), (unsigned)ytiles, (unsigned)nz);
   tc64::k_sketch_f64emu<<<grid, tc64::kThreads, smem, s>>>(ma, mw, colexp, (int)n, (int)rows, (int)mp, kchunk, out,
                                                            out_ld, zstride, st, done);

@@ -285,12 +285,9 @@ cudaError_t tc_sketch_fp8(const void* A, int64_t lda, int64_t m, int64_t n, cons
   if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
   const int64_t nbs = (m + tc8::kBK - 1) / tc8::kBK;
   const size_t smem = sizeof(tc8::Smem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc8::k_sketch_tc_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(tc8::k_sketch_tc_fp8, smem, lim);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((n + tc8::kBM - 1) / tc8::kBM), (unsigned)((rows + tc8::kBN - 1) / tc8::kBN), (unsigned)nz);
   tc8::k_sketch_tc_fp8<<<grid, tc8::kThreads, smem, s>>>(ma, mw, scale, nbs, (int)n, (int)rows, (int)m, (int)kchunk,
                                                          out, out_ld, zstride, st, done);

@@ -399,12 +399,9 @@ cudaError_t launch(int M, int N, int K, int64_t Kp, const void* adig, int64_t ar
   const int nz = (int)((K + kchunk - 1) / kchunk);
   if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
   const size_t smem = sizeof(Smem<KD>) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_emu<KD, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(k_gemm_emu<KD, TOut>, smem, lim);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((N + Cfg<KD>::kBN - 1) / Cfg<KD>::kBN), (unsigned)((M + kBM - 1) / kBM), (unsigned)nz);
   k_gemm_emu<KD, TOut><<<grid, kThreads, smem, s>>>(ma, mb, M, N, K, kchunk, aexp, bexp, out, ldo, zstride, st, done);
   return cudaGetLastError();
@@ -717,12 +714,9 @@ cudaError_t sketch_f32emu(int64_t m, int64_t n, int64_t rows, const void* adig, 
   const int nz = (int)((m + kchunk - 1) / kchunk);
   if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
   const size_t smem = sizeof(f32s::Smem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(f32s::k_sketch_f32emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(f32s::k_sketch_f32emu, smem, lim);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((n + f32s::kBM - 1) / f32s::kBM), (unsigned)((rows + f32s::kBN - 1) / f32s::kBN), (unsigned)nz);
   f32s::k_sketch_f32emu<<<grid, f32s::kThreads, smem, s>>>(ma, mw, (int)n, (int)rows, (int)m, kchunk, aexp, wexp, out,
                                                           ldo, zstride, st, done);

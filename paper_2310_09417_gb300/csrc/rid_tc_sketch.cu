@@ -215,14 +215,10 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
   int kchunk = (int)((m + splits - 1) / splits);
   kchunk = ((kchunk + tc::kBK - 1) / tc::kBK) * tc::kBK;
   const int nz = (int)((m + kchunk - 1) / kchunk);
-  static bool attr = false;
+  static SmemLimit lim;
   const size_t smem = tc::smem_bytes<BN>();
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc::k_sketch_tc_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = raise_smem(tc::k_sketch_tc_bf16<BN>, smem, lim);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((n + tc::kBM - 1) / tc::kBM), (unsigned)((rows + BN - 1) / BN), (unsigned)nz);
   tc::k_sketch_tc_bf16<BN><<<grid, tc::kThreads, smem, s>>>(ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld,
                                                              zstride, st, done);

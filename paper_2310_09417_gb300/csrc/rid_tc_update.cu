@@ -426,12 +426,9 @@ cudaError_t update_emu(int na, int bt, int tb, const T* N, const int32_t* act, c
   if (!make_map(&mn, nd, nrows, kBM, KD)) return cudaErrorInvalidValue;
   if (!make_map(&mp, pd, prows, bn<KD>(), KD)) return cudaErrorInvalidValue;
   const size_t smem = sizeof(Smem<KD, T>) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k_update_emu<KD, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemLimit lim;
+  e = raise_smem(k_update_emu<KD, T>, smem, lim);
+  if (e != cudaSuccess) return e;
   const int64_t tiles = (int64_t)((na + kBM - 1) / kBM) * ((tb + bn<KD>() - 1) / bn<KD>());
   const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM, balanced tile ranges
   k_update_emu<KD, T><<<grid, kThreads, smem, s>>>(mn, mp, na, tb, nexp, pexp, act, pivmark, X, ldx, st, done);

@@ -8,6 +8,10 @@ columns) with ctypes and numpy; it shares no code with the GPU library.
 Every function follows the paper step by step; see ``oracle.h`` for the
 conventions (column ID orientation, tie rule, Gaussian generator, the
 variance reading of the estimator's scale).
+
+Parity unpinned: the factor 4 log k / k of Eq. normUest and Eq. maxUest in
+``ur_estimates`` (see its docstring); every other function is pinned by
+``tests/test_oracle_pins.py`` or ``tests/test_oracle_mlp.py``.
 """
 from __future__ import annotations
 
@@ -198,6 +202,61 @@ def stable_residual(A, J) -> float:
     J = np.ascontiguousarray(J, dtype=np.int64)
     return float(_load().orc_stable_residual(A.shape[0], A.shape[1], _f64(A), A.shape[0],
                                              len(J), _i64(J)))
+
+
+def stable_x(A, J) -> np.ndarray:
+    """The stable interpolation matrix of the column ID: X = A(:,J)^+ A, the
+    orthogonal projection onto the skeleton columns (column form of Eq. sID,
+    Sec. 2.2), through a Householder QR of A(:,J): X = R^{-1} Q^T A.  Returns
+    X (k x n); X(:,J) = I up to rounding, and ||A - A(:,J) X||_F is the stable
+    ID error."""
+    import scipy.linalg as sla
+
+    A = _colmajor(A)
+    J = np.asarray(J, dtype=np.int64)
+    Q, R = np.linalg.qr(A[:, J], mode="reduced")  # library QR: a step, as the paper's qr
+    return sla.solve_triangular(R, Q.T @ A, lower=False)
+
+
+def ur_estimates(A, Omega, k: int) -> dict:
+    """The residual-U_r error estimates of Remark 1 (Sec. 3.2), in column form.
+
+    Omega has k + p rows: the first k give the rank-k skeleton, the last p are
+    the independent sample set aside for the estimate.  LUPP of the transposed
+    sketch Y^T = (Omega A)^T (n x (k+p)) continued for all k + p steps gives
+    P Y^T = [L1; L2 L_r] [U1 U2; 0 U_r] with U_r the trailing p x p block.
+    Returns U_r, L_r ((n-k) x p, unit lower trapezoidal), the Schur estimate
+    E = ||L_r U_r||_F / sqrt(p) (Eq. errSch), the bound sqrt(n-k) ||U_r||_F,
+    and the estimates of Eq. normUest and Eq. maxUest: (4 log k / k) sqrt(n-k)
+    times ||U_r||_F, or times max |U_r(i,j)| (log is the natural logarithm,
+    that of the growth-factor bound k / (4 log k) the remark takes over).
+    The factor 4 log k / k is parity unpinned: the paper supports it only with
+    a figure; the tests pin U_r, L_r, the Schur identity, the bound, and the
+    appendix's statement that Eq. normUest stays above the best rank-k error."""
+    A = _colmajor(A)
+    n = A.shape[1]
+    l = Omega.shape[0]
+    p = l - k
+    if not (2 <= k and 1 <= p and l <= n):
+        raise ValueError("ur_estimates needs k >= 2, at least one extra row and k + p <= n")
+    LU, perm, _ = lupp(sketch_t(A, Omega), steps=l)
+    U_r = np.triu(LU[k:l, k:l])
+    L_r = np.tril(LU[k:, k:l], -1) + np.eye(n - k, p)
+    nrm, mx = float(np.linalg.norm(U_r)), float(np.abs(U_r).max())
+    scale = 4.0 * np.log(k) / k * np.sqrt(n - k)
+    return dict(U_r=U_r, L_r=L_r, perm=perm, est=float(np.linalg.norm(L_r @ U_r)) / np.sqrt(p),
+                bound=np.sqrt(n - k) * nrm, normUest=scale * nrm, maxUest=scale * mx)
+
+
+def certificate(A, J, X, Omega_post) -> float:
+    """An a-posteriori estimate of ||A - A(:,J) X||_F from a fresh Gaussian
+    sample Omega_post (q x m) drawn after the skeletons are chosen (the
+    certificate Remark 1 points to): ||Omega' A - (Omega' A)(:,J) X||_F / sqrt(q),
+    whose square is unbiased for the squared error (Sec. 4.2)."""
+    G = sketch_t(A, Omega_post)  # n x q: row j is the sample of column j
+    J = np.asarray(J, dtype=np.int64)
+    R = G.T - G[J].T @ np.asarray(X, dtype=np.float64)
+    return float(np.linalg.norm(R)) / np.sqrt(G.shape[1])
 
 
 def rows_needed(n: int, b: int, kmax: int | None = None, m: int | None = None) -> int:

@@ -361,3 +361,82 @@ def test_kahan_and_fast_decay_estimate_tracks_error(orc):
         assert st <= true * (1 + 1e-9)
         if ad["k"] < n:
             assert 0.1 < ad["trace"][-1] / true < 10
+
+
+# ------------------------------------------------------------ stable X, U_r estimates, certificate
+def test_stable_x_is_the_least_squares_solution(orc):
+    """X = A(:,J)^+ A (Eq. sID, column form): LAPACK's SVD-based least squares
+    gives the same X, X(:,J) = I, its residual is the C oracle's Householder
+    stable ID error, and no other X on the same skeleton does better."""
+    m, n, k = 90, 60, 12
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=31)
+    Om = W.gaussian_omega(32, k, m)
+    r = orc.id_fixed_rank(A, Om, k)
+    Xs = orc.stable_x(A, r["J"])
+    Xl = np.linalg.lstsq(A[:, r["J"]], A, rcond=None)[0]
+    np.testing.assert_allclose(Xs, Xl, rtol=0, atol=1e-9 * np.abs(Xl).max())
+    np.testing.assert_allclose(Xs[:, r["J"]], np.eye(k), rtol=0, atol=1e-10)
+    es = orc.id_residual(A, r["J"], Xs)
+    assert es == pytest.approx(orc.stable_residual(A, r["J"]), rel=1e-9)
+    assert es <= orc.id_residual(A, r["J"], r["X"]) * (1 + 1e-12)
+
+
+def test_stable_x_equals_the_id_on_exactly_rank_k_input(orc):
+    """A = B C of rank k: A(:,J) spans the range, and both interpolation
+    matrices are C_J^{-1} C."""
+    A, _, Cf = W.low_rank(70, 50, 6, seed=33)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(34, 6, 70), 6)
+    want = np.linalg.solve(Cf[:, r["J"]], Cf)
+    np.testing.assert_allclose(orc.stable_x(A, r["J"]), want, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(r["X"], want, rtol=0, atol=1e-9)
+
+
+def test_ur_block_is_lapacks_trailing_block_and_gives_the_schur_estimate(orc):
+    """Remark 1: LUPP of [Y Y_r]^T continued for p more steps.  On Gaussian
+    data (no ties) LAPACK's getrf gives the same permutation and the same
+    trailing p x p block U_r; L_r U_r is the Schur complement of the p extra
+    rows, so ||L_r U_r||_F / sqrt(p) is the fixed-rank Schur estimate
+    (Eq. errSch), and |L_r| <= 1 gives the bound sqrt(n-k) ||U_r||_F."""
+    m, n, k, p = 120, 80, 15, 6
+    A = W.spectral_matrix(m, n, W.spectrum("poly", n), seed=35)
+    Om = W.gaussian_omega(36, k + p, m)
+    u = orc.ur_estimates(A, Om, k)
+    P, L, U = sla.lu((Om @ A).T)
+    assert np.array_equal(np.argmax(P, axis=0)[: k + p], u["perm"][: k + p])
+    np.testing.assert_allclose(u["U_r"], U[k:, k:], rtol=0, atol=1e-12 * np.abs(U).max())
+    np.testing.assert_allclose(u["L_r"], L[k:, k:], rtol=0, atol=1e-12)
+    assert np.all(np.abs(u["L_r"]) <= 1.0)
+    assert u["est"] == pytest.approx(orc.id_fixed_rank(A, Om, k)["est"], rel=1e-12)
+    assert u["est"] * np.sqrt(p) <= u["bound"]
+    assert u["maxUest"] <= u["normUest"] <= p * u["maxUest"]  # p x p triangle
+
+
+@pytest.mark.parametrize("kind", ["fast_decay", "geometric", "poly"])
+def test_normUest_bounds_the_best_rank_k_error(orc, kind):
+    """The paper's appendix: with Gaussian sketches, (4 log k / k) sqrt(m-k)
+    ||U_r||_F (Eq. normUest) stays above the best rank-k error in every case it
+    tried.  (How close Eq. maxUest comes is shown only in a figure the text
+    does not carry, so that constant has no pin.)"""
+    m = n = 400
+    s = W.spectrum(kind, n)
+    A = W.spectral_matrix(m, n, s, seed=37)
+    for k in (20, 60, 120):
+        for seed in range(3):
+            u = orc.ur_estimates(A, W.gaussian_omega(40 + seed, k + 10, m), k)
+            assert u["normUest"] >= np.sqrt(np.sum(s[k:] ** 2))
+
+
+def test_certificate_identity_and_unbiasedness(orc):
+    """The a-posteriori estimate ||Omega'(A - A(:,J)X)||_F / sqrt(q): with
+    Omega' = I_m it is the error over sqrt(m) exactly; with fresh Gaussian rows
+    its square averages to the squared error (Sec. 4.2)."""
+    m, n, k = 60, 45, 8
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=41)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(42, k, m), k)
+    e = orc.id_residual(A, r["J"], r["X"])
+    assert orc.certificate(A, r["J"], r["X"], np.eye(m)) == pytest.approx(e / np.sqrt(m), rel=1e-12)
+    q, trials = 4, 400
+    sq = [orc.certificate(A, r["J"], r["X"], W.gaussian_omega(1000 + t, q, m)) ** 2 for t in range(trials)]
+    # E^2 is e^2 times a chi-square with q * (effective rank) degrees over q: its
+    # relative spread is at most sqrt(2/q); the mean of 400 is within 4 sigma
+    assert abs(np.mean(sq) / e ** 2 - 1.0) <= 4 * np.sqrt(2.0 / q) / np.sqrt(trials)

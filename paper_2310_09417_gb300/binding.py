@@ -207,8 +207,8 @@ def quantize_fp8(A: torch.Tensor, pow2: bool = True, stream=None) -> FP8Matrix:
     nbs = -(-m // 128)
     Q = torch.zeros((n, ldq), dtype=torch.uint8, device=A.device)
     S = torch.empty((n, nbs), dtype=torch.float32, device=A.device)
-    rc = load().id_quantize_fp8(C.byref(_matrix(A)), Q.data_ptr(), ldq, S.data_ptr(), 1 if pow2 else 0,
-                                _stream(stream))
+    rc = _call(A.device, "id_quantize_fp8", C.byref(_matrix(A)), Q.data_ptr(), ldq, S.data_ptr(),
+               1 if pow2 else 0, _stream(stream, A.device))
     if rc != 0:
         raise IDError(rc, "id_quantize_fp8")
     return FP8Matrix(Q.view(torch.float8_e4m3fn)[:, :m].t(), S.t())
@@ -254,21 +254,55 @@ def _opts(A, *, block, tol, relative, k_max, k0, blocks_per_pass, seed, omega, p
     return o
 
 
-def _stream(stream) -> int:
-    s = torch.cuda.current_stream() if stream is None else stream
-    return s.cuda_stream
+def _stream(stream, device) -> int:
+    """The stream handle for a call on `device`: its current stream when stream
+    is None; a stream of another device is refused."""
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if stream.device != device:
+        raise ValueError("the stream is on %s, the data on %s" % (stream.device, device))
+    return stream.cuda_stream
+
+
+def _call(device, name, *args):
+    """Library function `name` called with `device` current: the library
+    launches on the calling thread's current device."""
+    with torch.cuda.device(device):
+        return getattr(load(), name)(*args)
+
+
+def _check_tensor(t, what, device, dtype, min_numel=0):
+    """A contiguous tensor of `dtype` on `device` with at least min_numel entries:
+    the library reads or writes that many from its first element."""
+    if not isinstance(t, torch.Tensor) or t.device != device or t.dtype != dtype:
+        raise ValueError("%s must be a %s tensor on %s" % (what, dtype, device))
+    if not t.is_contiguous() or t.numel() < min_numel:
+        raise ValueError("%s must be contiguous with at least %d entries" % (what, min_numel))
+
+
+def _check_out(J, Xb, n, kmax, xdt, device, what):
+    """Caller-owned outputs of an ID with rank cap kmax: J holds kmax int64 and Xb
+    is X^T, an (>= n) x (>= kmax) row-major buffer (Xb[j, c] = X(c, j), row stride
+    >= kmax).  The library writes J[0:k] and X(0:k, 0:n) with k <= kmax, so
+    anything smaller is refused before any device write."""
+    _check_tensor(J, what + ": J", device, torch.int64, kmax)
+    if (not isinstance(Xb, torch.Tensor) or Xb.device != device or Xb.dtype != xdt or Xb.dim() != 2
+            or Xb.shape[0] < n or Xb.shape[1] < kmax or Xb.stride(1) != 1 or Xb.stride(0) < kmax):
+        raise ValueError("%s: X must be a %s tensor on %s of shape (>= %d, >= %d) with stride (>= %d, 1)"
+                         % (what, xdt, device, n, kmax, kmax))
 
 
 def workspace_size(A: torch.Tensor, opts: IdOpts, l: int = 0) -> int:
     n = C.c_size_t(0)
-    rc = load().id_workspace_size(C.byref(_matrix(A)), C.byref(opts), l, C.byref(n))
+    rc = _call(A.device, "id_workspace_size", C.byref(_matrix(A)), C.byref(opts), l, C.byref(n))
     if rc != 0:
         raise IDError(rc, "id_workspace_size")
     return int(n.value)
 
 
 def _workspace(nbytes: int, device, ws: torch.Tensor | None) -> torch.Tensor:
-    if ws is not None and ws.numel() >= nbytes and ws.device == device:
+    if (ws is not None and ws.dtype == torch.uint8 and ws.is_contiguous() and ws.numel() >= nbytes
+            and ws.device == device):
         return ws
     return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
 
@@ -302,8 +336,8 @@ def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int
     res = IdResult()
     res.J, res.X, res.ldx = J.data_ptr(), Xbuf.data_ptr(), k
     res.pivots = piv.data_ptr() if piv is not None else None
-    rc = load().id_fixed_rank(C.byref(_matrix(A)), k, l, C.byref(opts), ws.data_ptr(), ws.numel(),
-                              C.byref(res), _stream(stream))
+    rc = _call(A.device, "id_fixed_rank", C.byref(_matrix(A)), k, l, C.byref(opts), ws.data_ptr(), ws.numel(),
+               C.byref(res), _stream(stream, A.device))
     if rc < 0:
         raise IDError(rc, "id_fixed_rank")
     return _result(res, J, Xbuf, k, n, rc, None, piv)
@@ -341,6 +375,7 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
         Xbuf = torch.empty((n, kmax), dtype=xdt, device=A.device)
     else:
         J, Xbuf = out
+        _check_out(J, Xbuf, n, kmax, xdt, A.device, "id_adaptive out")
     piv = torch.empty(kmax, dtype=torch.float64, device=A.device) if pivots else None
     trace_buf = (C.c_double * trace_cap)() if trace_cap > 0 else None
     res = IdResult()
@@ -348,8 +383,8 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
     res.pivots = piv.data_ptr() if piv is not None else None
     res.est_trace = C.cast(trace_buf, C.c_void_p) if trace_buf is not None else None
     res.trace_cap = trace_cap
-    rc = load().id_adaptive(C.byref(_matrix(A)), C.byref(opts), ws.data_ptr(), ws.numel(),
-                            C.byref(res), _stream(stream))
+    rc = _call(A.device, "id_adaptive", C.byref(_matrix(A)), C.byref(opts), ws.data_ptr(), ws.numel(),
+               C.byref(res), _stream(stream, A.device))
     if rc < 0:
         raise IDError(rc, "id_adaptive")
     return _result(res, J, Xbuf, int(res.k), n, rc, trace_buf, piv)
@@ -358,11 +393,11 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
 def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
                   device="cuda", stream=None) -> torch.Tensor:
     """Rows [row0, row0+rows) of the Philox/Box-Muller sketching matrix (rows x m)."""
-    out = torch.empty((rows, m), dtype=dtype, device=device)
     if dtype not in _TORCH_TO_ID:
         raise ValueError("unsupported dtype %s" % dtype)
-    rc = load().id_gaussian_rows(seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, _TORCH_TO_ID[dtype],
-                                 out.data_ptr(), m, _stream(stream))
+    out = torch.empty((rows, m), dtype=dtype, device=device)
+    rc = _call(out.device, "id_gaussian_rows", seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, _TORCH_TO_ID[dtype],
+               out.data_ptr(), m, _stream(stream, out.device))
     if rc != 0:
         raise IDError(rc, "id_gaussian_rows")
     return out
@@ -373,22 +408,22 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, *, stream=None,
     """G = (omega A)^T (n x rows): the sketch step alone.  omega is row-major
     (rows x m) in A's dtype; G is FP64 for FP64 input and FP32 otherwise (BF16
     input runs on the tensor cores).  sketch_prec=F64_EMU (FP64 A): the product
-    of omega rounded to the grid 2^-10 and A, FP64 accurate, on the tensor cores."""
+    of omega rounded to the grid 2^-11 and A, FP64 accurate, on the tensor cores."""
     m, n = A.shape
-    if omega.dim() != 2 or omega.shape[1] != m or omega.stride(1) != 1 or omega.dtype != A.dtype:
-        raise ValueError("omega must be row-major (rows x m) with A's dtype")
+    if (omega.dim() != 2 or omega.shape[1] != m or omega.stride(1) != 1 or omega.dtype != A.dtype
+            or omega.device != A.device):
+        raise ValueError("omega must be row-major (rows x m) with A's dtype, on A's device")
     rows = omega.shape[0]
     prec = _TORCH_TO_ID[A.dtype] if sketch_prec is None else sketch_prec
     nb = C.c_size_t(0)
-    lib = load()
-    rc = lib.id_sketch_workspace_size(C.byref(_matrix(A)), rows, prec, C.byref(nb))
+    rc = _call(A.device, "id_sketch_workspace_size", C.byref(_matrix(A)), rows, prec, C.byref(nb))
     if rc != 0:
         raise IDError(rc, "id_sketch_workspace_size")
     ws = _workspace(int(nb.value), A.device, workspace)
     G = torch.empty((n, rows), dtype=torch.float64 if A.dtype == torch.float64 else torch.float32,
                     device=A.device)
-    rc = lib.id_sketch(C.byref(_matrix(A)), omega.data_ptr(), omega.stride(0), rows, prec, G.data_ptr(),
-                       G.stride(0), ws.data_ptr(), ws.numel(), _stream(stream))
+    rc = _call(A.device, "id_sketch", C.byref(_matrix(A)), omega.data_ptr(), omega.stride(0), rows, prec,
+               G.data_ptr(), G.stride(0), ws.data_ptr(), ws.numel(), _stream(stream, A.device))
     if rc != 0:
         raise IDError(rc, "id_sketch")
     return G
@@ -402,14 +437,18 @@ def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, 
     Returns one IDResult per matrix (per-problem status in .status)."""
     if not As:
         return []
+    dev = As[0].device
+    if any(a.device != dev for a in As):
+        raise ValueError("id_batched: every matrix must be on one device")
+    if outs is not None and len(outs) != len(As):
+        raise ValueError("id_batched: outs needs one (J, X) pair per matrix")
     dt = _TORCH_TO_ID[As[0].dtype]
     count = len(As)
     mats = (IdMatrix * count)(*[_matrix(a) for a in As])
     opts = _opts(As[0], block=block, tol=tol, relative=relative, k_max=k_max or 0, k0=0,
                  blocks_per_pass=1, seed=seed, omega=None, profile=False)
-    lib = load()
     nb = C.c_size_t(0)
-    rc = lib.id_batched_workspace_size(count, mats, C.byref(opts), C.byref(nb))
+    rc = _call(dev, "id_batched_workspace_size", count, mats, C.byref(opts), C.byref(nb))
     if rc != 0:
         raise IDError(rc, "id_batched_workspace_size")
     ws = _workspace(int(nb.value), As[0].device, workspace)
@@ -421,6 +460,7 @@ def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, 
         kmax = min(m, n) if not k_max else min(k_max, m, n)
         if outs is not None:
             J, Xb = outs[i]
+            _check_out(J, Xb, n, kmax, xdt, dev, "id_batched outs[%d]" % i)
         else:
             J = torch.empty(kmax, dtype=torch.int64, device=a.device)
             Xb = torch.empty((n, kmax), dtype=xdt, device=a.device)
@@ -428,7 +468,7 @@ def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, 
         res[i].J, res[i].X, res[i].ldx = J.data_ptr(), Xb.data_ptr(), Xb.stride(0)
         res[i].pivots = piv.data_ptr() if piv is not None else None
         keep.append((J, Xb, piv))
-    rc = lib.id_batched(count, mats, C.byref(opts), ws.data_ptr(), ws.numel(), res, _stream(stream))
+    rc = _call(dev, "id_batched", count, mats, C.byref(opts), ws.data_ptr(), ws.numel(), res, _stream(stream, dev))
     if rc < 0 and rc != ERR_NONFINITE:
         raise IDError(rc, "id_batched")
     out = []
@@ -452,11 +492,22 @@ def mlp_param_count() -> int:
     return int(load().id_mlp_param_count())
 
 
+def _check_mlp(params, x):
+    """The parameter block (id_mlp_param_count() FP32 values) and a feature
+    matrix (batch x 35, FP32) on one device."""
+    _check_tensor(params, "params", x.device, torch.float32, mlp_param_count())
+    if x.dim() != 2 or x.shape[1] != MLP_IN or x.shape[0] < 1:
+        raise ValueError("x must be batch x %d" % MLP_IN)
+    _check_tensor(x, "x", x.device, torch.float32)
+
+
 def mlp_forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
     """Predicted log2 rank for each feature row of x (batch x 35, FP32, CUDA)."""
     x = x.contiguous()
+    _check_mlp(params, x)
     y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
-    rc = load().id_mlp_forward(params.data_ptr(), x.shape[0], x.data_ptr(), y.data_ptr(), _stream(stream))
+    rc = _call(x.device, "id_mlp_forward", params.data_ptr(), x.shape[0], x.data_ptr(), y.data_ptr(),
+               _stream(stream, x.device))
     if rc != 0:
         raise IDError(rc, "id_mlp_forward")
     return y
@@ -468,11 +519,14 @@ def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, g
     with respect to the trainable parameters."""
     x = x.contiguous()
     target = target.contiguous()
+    _check_mlp(params, x)
+    _check_tensor(target, "target", x.device, torch.float32, x.shape[0])
     if grad is None:
         grad = torch.empty(MLP_TRAINABLE, dtype=torch.float32, device=x.device)
+    _check_tensor(grad, "grad", x.device, torch.float32, MLP_TRAINABLE)
     loss = torch.empty(1, dtype=torch.float32, device=x.device)
-    rc = load().id_mlp_loss_grad(params.data_ptr(), x.shape[0], x.data_ptr(), target.data_ptr(),
-                                 grad.data_ptr(), loss.data_ptr(), _stream(stream))
+    rc = _call(x.device, "id_mlp_loss_grad", params.data_ptr(), x.shape[0], x.data_ptr(), target.data_ptr(),
+               grad.data_ptr(), loss.data_ptr(), _stream(stream, x.device))
     if rc != 0:
         raise IDError(rc, "id_mlp_loss_grad")
     return loss, grad
@@ -480,17 +534,22 @@ def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, g
 
 def mlp_adam(params: torch.Tensor, grad: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, step: int,
              lr: float, stream=None) -> None:
-    rc = load().id_mlp_adam(params.data_ptr(), grad.data_ptr(), m1.data_ptr(), m2.data_ptr(), step, lr,
-                            _stream(stream))
+    dev = params.device
+    _check_tensor(params, "params", dev, torch.float32, mlp_param_count())
+    for t, what in ((grad, "grad"), (m1, "m1"), (m2, "m2")):
+        _check_tensor(t, what, dev, torch.float32, MLP_TRAINABLE)
+    rc = _call(dev, "id_mlp_adam", params.data_ptr(), grad.data_ptr(), m1.data_ptr(), m2.data_ptr(), step, lr,
+               _stream(stream, dev))
     if rc != 0:
         raise IDError(rc, "id_mlp_adam")
 
 
 def rank_features(pivots: torch.Tensor, m: int, n: int, rel_tol: float, stream=None) -> torch.Tensor:
     """The 35 predictor features from the first pivots |U(i,i)| (CUDA float64)."""
+    _check_tensor(pivots, "pivots", pivots.device, torch.float64)
     x = torch.empty(MLP_IN, dtype=torch.float32, device=pivots.device)
-    rc = load().id_rank_features(pivots.data_ptr(), pivots.numel(), m, n, rel_tol, x.data_ptr(),
-                                 _stream(stream))
+    rc = _call(pivots.device, "id_rank_features", pivots.data_ptr(), pivots.numel(), m, n, rel_tol, x.data_ptr(),
+               _stream(stream, pivots.device))
     if rc != 0:
         raise IDError(rc, "id_rank_features")
     return x
@@ -502,17 +561,16 @@ def cur_from_id(A: torch.Tensor, J: torch.Tensor, *, stream=None,
     A ~ W A(I, J) X (two-sided ID).  Returns (I, W)."""
     m, n = A.shape
     k = J.numel()
-    lib = load()
     nb = C.c_size_t(0)
-    rc = lib.id_cur_workspace_size(C.byref(_matrix(A)), k, C.byref(nb))
+    rc = _call(A.device, "id_cur_workspace_size", C.byref(_matrix(A)), k, C.byref(nb))
     if rc != 0:
         raise IDError(rc, "id_cur_workspace_size")
     ws = _workspace(int(nb.value), A.device, workspace)
     I = torch.empty(k, dtype=torch.int64, device=A.device)
     W = torch.empty((k, m), dtype=A.dtype, device=A.device).t()  # column-major m x k
-    J = J.to(torch.int64).contiguous()
-    rc = lib.cur_from_id(C.byref(_matrix(A)), J.data_ptr(), k, I.data_ptr(), W.data_ptr(), W.stride(1),
-                         ws.data_ptr(), ws.numel(), _stream(stream))
+    J = J.to(device=A.device, dtype=torch.int64).contiguous()
+    rc = _call(A.device, "cur_from_id", C.byref(_matrix(A)), J.data_ptr(), k, I.data_ptr(), W.data_ptr(),
+               W.stride(1), ws.data_ptr(), ws.numel(), _stream(stream, A.device))
     if rc < 0:
         raise IDError(rc, "cur_from_id")
     return I, W

@@ -297,6 +297,20 @@ int id_rank_features(const double* pivots, int64_t npiv, int64_t m, int64_t n, d
 /* Human-readable text for a status value. */
 const char* id_status_string(int status);
 
+/* Self-test of the failure handling; the paper has no counterpart.  Every
+   device-side wait of the library gives up after a bounded time (4 s of the
+   GPU's global timer).  That covers the grid barrier of the cooperative LUPP
+   panel and the mbarrier waits of the tensor-core kernels.  The wait records a
+   timeout and lets its kernel exit, so the call returns ID_ERR_TIMEOUT and the
+   CUDA context stays usable.  This entry runs, with the same device helpers,
+   one wait that nothing can satisfy: which = 0 the grid barrier, which = 1 an
+   mbarrier wait.
+   ws: DEVICE scratch of at least 256 bytes, 256-aligned, owned by the caller.
+   Synchronises the stream and takes about 4 s.  Returns ID_ERR_TIMEOUT when
+   the wait gave up as designed.  ID_OK would mean the wait was satisfied.
+   Other returns: -1 for another `which`, ID_ERR_WORKSPACE, ID_ERR_CUDA. */
+int id_selftest_timeout(int which, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of the library-owned device buffer behind id_fixed_rank_noalloc. */
 #define ID_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 

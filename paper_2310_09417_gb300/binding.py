@@ -90,9 +90,10 @@ def load():
     lib.id_status_string.restype = C.c_char_p
     lib.id_quantize_fp8.argtypes = [P, P, i64, P, C.c_int, P]
     lib.id_fixed_rank_noalloc.argtypes = [P, i64, i64, P, P, P]
+    lib.id_selftest_timeout.argtypes = [C.c_int, P, C.c_size_t, P]
     for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
               "id_batched", "cur_from_id", "id_gaussian_rows", "id_sketch_workspace_size", "id_sketch",
-              "id_quantize_fp8", "id_fixed_rank_noalloc"):
+              "id_quantize_fp8", "id_fixed_rank_noalloc", "id_selftest_timeout"):
         getattr(lib, f).restype = C.c_int
     # every entry point must have its C signature declared: an undeclared one would
     # pass 64-bit pointers as C ints
@@ -481,6 +482,14 @@ def id_batched(As: list, tol: float, *, block: int = 32, relative: bool = True, 
                             rounds=r.rounds, passes=r.passes, launches=r.launches, status=st, trace=[],
                             pivots=None if piv is None else piv[:k], phase_ms={}, phase_launches={}))
     return out
+
+
+def selftest_timeout(which: int, device="cuda", stream=None) -> int:
+    """Run one device wait that nothing satisfies (0: the LUPP panel's grid
+    barrier, 1: an mbarrier wait of the tensor-core kernels) and return the
+    library's status: ERR_TIMEOUT when the bounded wait gave up as designed."""
+    ws = torch.empty(256, dtype=torch.uint8, device=device)
+    return _call(ws.device, "id_selftest_timeout", which, ws.data_ptr(), ws.numel(), _stream(stream, ws.device))
 
 
 # ---------------------------------------------------------------- learned rank predictor

@@ -259,6 +259,43 @@ def certificate(A, J, X, Omega_post) -> float:
     return float(np.linalg.norm(R)) / np.sqrt(G.shape[1])
 
 
+def row_id_of_columns(A, J) -> tuple:
+    """Row skeletons I and row interpolation matrix W of C = A(:,J) (m x k), from
+    LUPP of C (Sec. 3.1: the CUR row step; Eq. inty in row form):
+    W = P^T [I; L2 L1^{-1}], so that C = W C(I,:) and W(I,:) = I.  It is the
+    oracle's column ID of C^T with Omega = I_k.  Returns (I, W)."""
+    A = _colmajor(A)
+    J = np.asarray(J, dtype=np.int64)
+    Cm = A[:, J]
+    k = len(J)
+    r = id_fixed_rank(np.ascontiguousarray(Cm.T), np.eye(k), k)
+    return r["J"], np.asarray(r["X"]).T.copy()
+
+
+def cur_middle(A, I, J) -> np.ndarray:
+    """The CUR middle factor U = C^+ A R^+ with C = A(:,J), R = A(I,:)
+    (Sec. 2.2.1, CUR): the Frobenius-optimal k x k matrix between C and R."""
+    A = _colmajor(A)
+    I = np.asarray(I, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
+    return np.linalg.pinv(A[:, J]) @ A @ np.linalg.pinv(A[I, :])  # library pseudo-inverses as steps
+
+
+def two_sided_residual(A, I, J, W, X) -> float:
+    """||A - W A(I,J) X||_F, the two-sided ID error (Sec. 2.2.1)."""
+    A = _colmajor(A)
+    S = A[np.ix_(np.asarray(I, dtype=np.int64), np.asarray(J, dtype=np.int64))]
+    return float(np.linalg.norm(A - np.asarray(W) @ S @ np.asarray(X)))
+
+
+def cur_residual(A, I, J, U) -> float:
+    """||A - C U R||_F with C = A(:,J), R = A(I,:) (Sec. 2.2.1, CUR)."""
+    A = _colmajor(A)
+    I = np.asarray(I, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
+    return float(np.linalg.norm(A - A[:, J] @ np.asarray(U) @ A[I, :]))
+
+
 def rows_needed(n: int, b: int, kmax: int | None = None, m: int | None = None) -> int:
     """Sketch rows an adaptive run may draw: one block per round plus the first."""
     cap = n if kmax is None else min(n, kmax)

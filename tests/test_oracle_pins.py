@@ -440,3 +440,54 @@ def test_certificate_identity_and_unbiasedness(orc):
     # E^2 is e^2 times a chi-square with q * (effective rank) degrees over q: its
     # relative spread is at most sqrt(2/q); the mean of 400 is within 4 sigma
     assert abs(np.mean(sq) / e ** 2 - 1.0) <= 4 * np.sqrt(2.0 / q) / np.sqrt(trials)
+
+
+# ------------------------------------------------------------ two-sided ID and CUR
+def test_row_id_of_the_skeleton_columns(orc):
+    """W from LUPP of C = A(:,J): W(I,:) = I, C = W C(I,:), and with LAPACK's
+    getrf on C (no ties on this data) the same I and W = P^T [I; L2 L1^{-1}]."""
+    m, n, k = 80, 60, 9
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=51)
+    J = orc.id_fixed_rank(A, W.gaussian_omega(52, k, m), k)["J"]
+    I, Wm = orc.row_id_of_columns(A, J)
+    C = A[:, J]
+    np.testing.assert_array_equal(Wm[I], np.eye(k))
+    assert np.linalg.norm(C - Wm @ C[I]) <= 1e-12 * np.linalg.norm(C)
+    P, L, _ = sla.lu(C)
+    perm = np.argmax(P, axis=0)
+    assert np.array_equal(I, perm[:k])
+    T = sla.solve_triangular(L[:k, :k], L[k:, :k].T, trans="T", lower=True, unit_diagonal=True).T
+    np.testing.assert_allclose(Wm[perm[k:]], T, rtol=0, atol=1e-12 * max(1.0, np.abs(T).max()))
+
+
+def test_two_sided_and_cur_on_exactly_rank_k(orc):
+    """A = B C of rank k: the two-sided ID W A(I,J) X and the CUR C U R both
+    reproduce A to rounding."""
+    A, _, _ = W.low_rank(70, 55, 7, seed=53)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(54, 7, 70), 7)
+    I, Wm = orc.row_id_of_columns(A, r["J"])
+    nA = np.linalg.norm(A)
+    assert orc.two_sided_residual(A, I, r["J"], Wm, r["X"]) <= 1e-11 * nA
+    assert orc.cur_residual(A, I, r["J"], orc.cur_middle(A, I, r["J"])) <= 1e-11 * nA
+
+
+def test_two_sided_error_equals_column_id_error_and_cur_is_optimal(orc):
+    """C = W A(I,J) makes the two-sided ID error the column ID error (Sec. 2.2.1:
+    equivalent in exact arithmetic).  U = C^+ A R^+ is the least-squares middle
+    factor: the normal equations C^T (A - C U R) R^T = 0 hold, and perturbing U
+    only raises the error."""
+    m, n, k = 90, 70, 12
+    A = W.spectral_matrix(m, n, W.spectrum("poly", n), seed=55)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(56, k, m), k)
+    J = r["J"]
+    I, Wm = orc.row_id_of_columns(A, J)
+    e1 = orc.id_residual(A, J, r["X"])
+    assert orc.two_sided_residual(A, I, J, Wm, r["X"]) == pytest.approx(e1, rel=1e-9)
+    U = orc.cur_middle(A, I, J)
+    C, R = A[:, J], A[I, :]
+    G = C.T @ (A - C @ U @ R) @ R.T
+    assert np.abs(G).max() <= 1e-10 * np.linalg.norm(A) ** 3
+    e = orc.cur_residual(A, I, J, U)
+    rng = np.random.default_rng(57)
+    for _ in range(5):
+        assert orc.cur_residual(A, I, J, U + 1e-3 * np.abs(U).max() * rng.standard_normal(U.shape)) > e

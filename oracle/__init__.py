@@ -66,6 +66,8 @@ def _load():
     lib.orc_id_adaptive.argtypes = [i64, i64, f64p, i64, i64, C.c_double, i64, f64p, i64,
                                     i64p, i64p, f64p, i64, f64p, i64, i64p, f64p]
     lib.orc_id_adaptive.restype = C.c_int
+    lib.orc_sparse_sign_block.argtypes = [C.c_uint64, i64, i64, i64, i64, f64p]
+    lib.orc_sparse_sign_block.restype = None
     lib.orc_fro_norm.argtypes = [i64, i64, f64p, i64]
     lib.orc_fro_norm.restype = C.c_double
     lib.orc_id_residual.argtypes = [i64, i64, f64p, i64, i64, i64p, f64p, i64]
@@ -104,6 +106,21 @@ def gaussian_rows(seed: int, row0: int, rows: int, m: int) -> np.ndarray:
     """Rows [row0, row0+rows) of the N(0,1) sketching matrix, shape (rows, m)."""
     out = np.zeros((rows, m), dtype=np.float64)
     _load().orc_gaussian_rows(C.c_uint64(seed), row0, rows, m, _f64(out))
+    return out
+
+
+def sparse_sign_rows(seed: int, t0: int, blocks: int, b: int, m: int, zeta: int = 8) -> np.ndarray:
+    """Blocks t0 .. t0+blocks-1 of the sparse-sign sketching matrix (Sec. 5.1,
+    "Sparse Sign"; zeta = 8 as the paper chooses), stacked: (blocks*b) x m.
+    Each column of each block holds zeta entries +-sqrt(b/zeta) at distinct
+    rows (the counter-based definition is in oracle.h)."""
+    if not (1 <= zeta <= b):
+        raise ValueError("sparse sign needs 1 <= zeta <= b")
+    out = np.zeros((blocks * b, m), dtype=np.float64)
+    for q in range(blocks):
+        blk = np.zeros((b, m), dtype=np.float64)
+        _load().orc_sparse_sign_block(C.c_uint64(seed), t0 + q, b, m, zeta, _f64(blk))
+        out[q * b:(q + 1) * b] = blk
     return out
 
 

@@ -69,6 +69,31 @@ void orc_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, dou
   }
 }
 
+/* Sparse-sign block t (Sec. 5.1, "Sparse Sign", column form; definition in oracle.h). */
+void orc_sparse_sign_block(uint64_t seed, int64_t t, int64_t b, int64_t m, int64_t zeta, double* out) {
+  const double v = sqrt((double)b / (double)zeta);
+  for (int64_t e = 0; e < b * m; ++e) out[e] = 0.0;
+  int64_t* p = (int64_t*)malloc(sizeof(int64_t) * b);
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t r = 0; r < b; ++r) p[r] = r;
+    uint64_t w[4] = {0, 0, 0, 0};
+    for (int64_t j = 0; j < zeta; ++j) {
+      if (j % 4 == 0) {
+        uint64_t ctr[4] = {(uint64_t)i, (uint64_t)t, (uint64_t)(j / 4), 0};
+        uint64_t key[2] = {seed, 1};
+        orc_philox4x64_10(ctr, key, w);
+      }
+      const uint64_t u = w[j % 4];
+      const int64_t r = j + (int64_t)(((u >> 32) * (uint64_t)(b - j)) >> 32);
+      const int64_t tmp = p[j];
+      p[j] = p[r];
+      p[r] = tmp;
+      out[p[j] * m + i] = (u & 1u) ? -v : v;
+    }
+  }
+  free(p);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Sketch (Sec. 2.4, column form Y = Omega A), stored transposed.            */
 /* ------------------------------------------------------------------------- */

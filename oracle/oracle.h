@@ -55,6 +55,20 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 /* Rows [row0, row0 + rows) of the Gaussian sketching matrix (rows x m, row-major). */
 void orc_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, double* out);
 
+/* Block t of a sparse-sign sketching matrix (Sec. 5.1, "Sparse Sign"), column
+ * form: b rows x m columns, row-major (ld = m), the rows t*b .. t*b+b-1 of Omega.
+ * Every column holds zeta nonzeros (1 <= zeta <= b) at distinct rows, each
+ * +-sqrt(b/zeta), so that E[Omega^T Omega] = b I as for N(0,1) entries.
+ * Definition:
+ *   - The words u_0, u_1, ... of column i in block t are Philox4x64-10 keyed
+ *     (seed, 1) at counters (i, t, c, 0), c = 0, 1, ..., four words per
+ *     counter, in order.
+ *   - Rows come from a partial Fisher-Yates shuffle of p = (0, ..., b-1): for
+ *     j = 0 .. zeta-1, r = j + (((u_j >> 32) * (b - j)) >> 32), swap p[j] and
+ *     p[r].
+ *   - Nonzero j sits at row p[j], negative if u_j is odd. */
+void orc_sparse_sign_block(uint64_t seed, int64_t t, int64_t b, int64_t m, int64_t zeta, double* out);
+
 /* Y^T = (Omega * A)^T : Omega rows x m (row-major, ld = m), A m x n col-major.
  * Output YT is n x rows, column-major with leading dimension n. */
 void orc_sketch_t(int64_t m, int64_t n, const double* A, int64_t lda,

@@ -491,3 +491,55 @@ def test_two_sided_error_equals_column_id_error_and_cur_is_optimal(orc):
     rng = np.random.default_rng(57)
     for _ in range(5):
         assert orc.cur_residual(A, I, J, U + 1e-3 * np.abs(U).max() * rng.standard_normal(U.shape)) > e
+
+
+# ------------------------------------------------------------ sparse-sign sketch
+def test_sparse_sign_structure(orc):
+    """zeta entries +-sqrt(b/zeta) per column of every block, so every column
+    of Omega^T Omega's diagonal is exactly b; a block depends only on (seed, t)."""
+    b, m, zeta = 64, 3000, 8
+    S = orc.sparse_sign_rows(11, 0, 3, b, m, zeta)
+    for q in range(3):
+        blk = S[q * b:(q + 1) * b]
+        nz = blk != 0
+        assert np.all(nz.sum(axis=0) == zeta)
+        np.testing.assert_array_equal(np.abs(blk[nz]), np.sqrt(b / zeta))
+        np.testing.assert_allclose((blk ** 2).sum(axis=0), b, rtol=1e-15)
+    np.testing.assert_array_equal(orc.sparse_sign_rows(11, 2, 1, b, m, zeta), S[2 * b:])
+    assert not np.array_equal(S[:b], S[b:2 * b])
+    assert not np.array_equal(orc.sparse_sign_rows(12, 0, 1, b, m, zeta), S[:b])
+
+
+def test_sparse_sign_positions_pairs_and_signs_are_uniform(orc):
+    """Uniformly random coordinates (Sec. 5.1): over 20000 columns every row is
+    chosen equally often and every pair of rows equally often together (chi-square),
+    and the Rademacher signs balance."""
+    b, m, zeta = 32, 20000, 8
+    blk = orc.sparse_sign_rows(13, 0, 1, b, m, zeta)
+    nz = blk != 0
+    counts = nz.sum(axis=1)
+    expected = zeta * m / b
+    assert ((counts - expected) ** 2 / expected).sum() < 31 + 6 * np.sqrt(2 * 31)  # 31 dof
+    signs = np.sign(blk[nz])
+    assert abs(signs.mean()) < 5 / np.sqrt(signs.size)
+    co = nz.astype(float) @ nz.T.astype(float)
+    off = co[np.triu_indices(b, 1)]
+    e2 = m * zeta * (zeta - 1) / (b * (b - 1))
+    assert off.sum() == pytest.approx(m * zeta * (zeta - 1) / 2)  # pairs per column are fixed
+    dof = off.size - 1
+    assert ((off - e2) ** 2 / e2).sum() < dof + 6 * np.sqrt(2 * dof)
+
+
+def test_sparse_sign_sketch_recovers_rank_k_and_certifies_without_bias(orc):
+    """Any sketch of full rank recovers an exactly rank-k matrix (X = C_J^{-1} C),
+    and E[Omega^T Omega] = b I makes the certificate's square unbiased."""
+    A, _, Cf = W.low_rank(90, 70, 6, seed=61)
+    r = orc.id_fixed_rank(A, orc.sparse_sign_rows(14, 0, 1, 16, 90, 8), 6)
+    np.testing.assert_allclose(r["X"], np.linalg.solve(Cf[:, r["J"]], Cf), rtol=0, atol=1e-9)
+    m, n, k, b = 60, 45, 8, 16
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n), seed=41)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(42, k, m), k)
+    e2 = orc.id_residual(A, r["J"], r["X"]) ** 2
+    rat = np.array([orc.certificate(A, r["J"], r["X"], orc.sparse_sign_rows(99, t, 1, b, m, 8)) ** 2 / e2
+                    for t in range(400)])
+    assert abs(rat.mean() - 1.0) < 5 * rat.std() / np.sqrt(rat.size)

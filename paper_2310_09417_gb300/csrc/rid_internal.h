@@ -15,11 +15,13 @@
 
 namespace rid {
 
-// A kernel launched with more than the default 48 KB of dynamic shared memory
-// needs its limit raised first (cudaFuncSetAttribute).  That attribute belongs
-// to each device's context, so the size already raised is kept per device; the
-// check is an atomic load, and the raise runs under a lock so that concurrent
-// callers never lower a limit another one relies on.
+// The dynamic shared-memory limit of a kernel (cudaFuncSetAttribute), set to
+// what its launches use before the first one and raised when a launch needs
+// more.  By default the limit is 48 KB minus the kernel's static shared memory,
+// so it is set whatever the size.  The attribute belongs to each device's
+// context, so the size already set is kept per device.  The check is an atomic
+// load; the call runs under a lock, so that concurrent callers never lower a
+// limit another one relies on.
 constexpr int kMaxDevices = 64;
 struct SmemLimit {
   std::atomic<size_t> raised[kMaxDevices];
@@ -30,7 +32,7 @@ inline std::mutex& smem_limit_mutex() {
 }
 template <typename K>
 inline cudaError_t raise_smem(K* func, size_t bytes, SmemLimit& lim) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes == 0) return cudaSuccess;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -323,19 +323,29 @@ int id_selftest_timeout(int which, void* ws, size_t ws_bytes, void* stream);
    device allocation after start-up, since cudaMalloc and cudaFree can block the
    device.  They still own and pass A, J and X; the scratch the method needs
    comes from one buffer of ID_NOALLOC_SCRATCH_BYTES that the library defines as
-   a static device array.  Every GPU that loads the library holds that buffer
-   until the process exits.
+   a static device array.
 
-   Arguments and results are those of id_fixed_rank (without ws / ws_bytes);
+   When the buffer exists on a device: it belongs to the library's device code,
+   which CUDA loads into each device's context.  Under CUDA's default lazy
+   module loading that happens on the first call of this function on the
+   device (the buffer's address lookup), and that load allocates the
+   ID_NOALLOC_SCRATCH_BYTES.  So make the first call on each device at
+   start-up: before the caller reserves its memory pool or forbids
+   allocation, and before any stream capture.  (With CUDA_MODULE_LOADING=EAGER
+   the buffer is allocated when the context is created.)  From then on the
+   device holds the buffer until the process exits, and later calls allocate
+   nothing.
+
+   Arguments and results are those of id_fixed_rank without ws / ws_bytes, so
+   a negative argument code -i counts this function's own positions: A = -1,
+   k = -2, l = -3, opts = -4, out = -5 (id_fixed_rank reports a bad out as -7).
    opts->profile is ignored (no timing events are created).  A problem whose
    scratch (the id_workspace_size value for the same A, opts and l) exceeds
    ID_NOALLOC_SCRATCH_BYTES is rejected with ID_ERR_WORKSPACE before anything
-   runs.  The first call on a device looks up the buffer's device address
-   (cudaGetSymbolAddress) with that device current; make that first call before
-   any stream capture.  Calls share the buffer and each call re-initialises what
-   it reads, but calls that overlap on the GPU (other streams, other host
-   threads) race on it: serialise them.  Nothing here calls cudaMalloc, cudaFree
-   or an allocating library routine. */
+   runs.  Calls share the buffer and each call re-initialises what it reads,
+   but calls that overlap on the GPU (other streams, other host threads) race
+   on it: serialise them.  Nothing here calls cudaMalloc, cudaFree or an
+   allocating library routine. */
 int id_fixed_rank_noalloc(const id_matrix* A, int64_t k, int64_t l, const id_opts* opts,
                           id_result* out, void* stream);
 

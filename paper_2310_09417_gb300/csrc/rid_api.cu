@@ -13,6 +13,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -1205,19 +1207,27 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[ID_NOALLOC_SCRA
 
 namespace {
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the lookup needs that device current and must not run while a
-// stream is being captured).
+// Device address of g_noalloc_scratch on the current device.  The lookup
+// needs that device current and must not run while a stream is being
+// captured; its result is kept per device.  Entries are atomic and the first
+// lookup on a device runs under a lock, so concurrent first calls from several
+// host threads agree on one address.
+std::atomic<void*> g_noalloc_addr[64];
+std::mutex g_noalloc_mu;
+
 int noalloc_scratch(void** out) {
-  static void* addr[64] = {nullptr};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ID_ERR_CUDA;
-  if (addr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return ID_ERR_CUDA;
-    addr[dev] = p;
+  void* a = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (a == nullptr) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    a = g_noalloc_addr[dev].load(std::memory_order_relaxed);
+    if (a == nullptr) {
+      if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess || a == nullptr) return ID_ERR_CUDA;
+      g_noalloc_addr[dev].store(a, std::memory_order_release);
+    }
   }
-  *out = addr[dev];
+  *out = a;
   return ID_OK;
 }
 

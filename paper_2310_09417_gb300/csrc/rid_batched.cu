@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "randid.h"
@@ -585,6 +586,10 @@ struct GraphEntry {
   cudaGraphExec_t exec;
 };
 std::vector<GraphEntry> g_graphs;
+// Guards g_graphs, g_tuned and the capture streams: id_batched may be called
+// from several host threads at once.  Held across a graph's capture and launch
+// so that no entry is evicted (and destroyed) between its lookup and its launch.
+std::mutex g_cache_mu;
 
 bool same_params(const Params& a, const Params& b) { return memcmp(&a, &b, sizeof(Params)) == 0; }
 
@@ -598,6 +603,7 @@ cudaStream_t capture_stream(int dev) {
 cudaError_t run_graph(const Params& p, const Config& c, int elem, int sms, cudaStream_t user) {
   int dev = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_cache_mu);
   for (auto& g : g_graphs)
     if (g.dev == dev && g.elem == elem && g.c.bm == c.bm && g.c.per_sm == c.per_sm && same_params(g.p, p))
       return cudaGraphLaunch(g.exec, user);
@@ -654,11 +660,14 @@ int tune(const Params& p, int elem, int sms, int count, cudaStream_t s, Config* 
     }
   }
   const int64_t mc = size_class(p.mmax), nc = size_class(p.nmax);
-  for (auto& t : g_tuned)
-    if (t.elem == elem && t.b == p.b && t.dev == dev && t.mclass == mc && t.nclass == nc) {
-      *best = t.c;
-      return ID_OK;
-    }
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (auto& t : g_tuned)
+      if (t.elem == elem && t.b == p.b && t.dev == dev && t.mclass == mc && t.nclass == nc) {
+        *best = t.c;
+        return ID_OK;
+      }
+  }
   const Config cands[4] = {{64, 1}, {64, 2}, {32, 1}, {32, 2}};
   Params q = p;
   q.count = std::min(count, 2 * sms);  // the largest problems come first in `order`
@@ -684,7 +693,8 @@ int tune(const Params& p, int elem, int sms, int count, cudaStream_t s, Config* 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  g_tuned.push_back(TuneEntry{elem, p.b, dev, mc, nc, *best});
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_tuned.push_back(TuneEntry{elem, p.b, dev, mc, nc, *best});  // two racing tuners may both add: harmless
   return ID_OK;
 }
 

@@ -58,6 +58,25 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
         assert rel <= X_TOL
         assert res.est_err == pytest.approx(ref.est_err, rel=1e-12)
 
+    # the defining property: once the first call has loaded the buffer on this
+    # device, a call allocates no device memory (free bytes unchanged)
+    m, n, k, l, b, seed = cases[0]
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", min(m, n)), seed=seed)
+    Ad = B.colmajor(torch.from_numpy(A).to("cuda"))
+    J = torch.empty((k,), dtype=torch.int64, device="cuda")
+    Xb = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    res = B.IdResult()
+    res.J, res.X, res.ldx = J.data_ptr(), Xb.data_ptr(), k
+    opts = B._opts(Ad, block=b, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1,
+                   seed=seed, omega=None, profile=False)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rc = f(ctypes.byref(B._matrix(Ad)), k, l, ctypes.byref(opts), ctypes.byref(res), stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == B.OK, B.status_string(rc)
+    assert free1 == free0, "the call changed free device memory by %d bytes" % (free0 - free1)
+
     # a problem whose scratch exceeds the static buffer is refused before anything runs
     big = B.IdMatrix(Ad.data_ptr(), B.F64, 40000, 10000, 40000, None)
     opts = B._opts(Ad, block=64, tol=0.0, relative=False, k_max=100, k0=0, blocks_per_pass=1, seed=1,

@@ -1,14 +1,26 @@
 """Benchmark: adaptive randomized column ID (Algorithm 1 of arXiv:2310.09417) on
-GB300, on the 40000 x 10000 workloads (A = U diag(s) V^T with the polynomial
-spectrum s_j = (1+j)^-2 or the step spectrum, sketch block b = 64, relative
-tolerance 1e-6 in FP32 and 1e-10 in FP64).
+GB300.
+
+Default line: the 40000 x 10000 FP64 workload (A = U diag(s) V^T with the
+polynomial spectrum s_j = (1+j)^-2, sketch block b = 64, relative tolerance
+1e-10) on the FP64-accurate tensor-core path (sketch, Schur GEMM and block
+update as exact BF16 digit products on tcgen05; LU, X and norms in FP64).
 
 One step = one complete adaptive ID (every step of the hot path: Gaussian rows,
 sketch GEMM, Schur complement and its FP64 norm, stop test, LUPP, re-blocking,
 interpolation matrix) on inputs resident in HBM.  The metric is throughput in
 algorithmic GFLOP/s at the fixed relative error; ms_per_step is the ID time.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+The same run times the other forms the metric compares ("forms"), each with its
+own CUDA events, roofline fraction, e2e and error: plain FP64 on the same
+matrix (the baseline), the FP32-accurate tensor-core path, BF16 and FP8 mixed
+precision on the 100000 x 20000 matrix, the predictor-seeded BF16 run and the
+batched kernel blocks.  The cpu_baseline leg runs the oracle on the first
+rounds of Algorithm 1 over the same full-size matrix and compares its
+skeletons, estimates and pivots with the GPU's ("parity").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--forms auto|all|none]
+                  [--impl reference]
 
 Multi-GPU: one ID does not shard across GPUs here, so N ranks run N
 independent replicas (weak scaling, no collective on the data path).
@@ -68,7 +80,7 @@ WORKLOADS = {
     "batched_kernel_f32": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f32", 1e-8, 32),
     "small_batched_kernel_f64": (2 ** 16, 512, "kernel", {"leaf_max": 512, "h": 0.3}, "f64", 1e-8, 32),
 }
-DEFAULT_WORKLOAD = "adaptive_poly_f64"
+DEFAULT_WORKLOAD = "adaptive_poly_f64emu"
 # Peaks of the plain-ALU paths, from unit counts x maximum SM clock (2070 MHz):
 # FP32: 152 SMs x 128 FMA lanes x 2 flops; FP64: the 1.25 TFLOP/s GB300 rate.
 ALU_PEAK_TFLOPS = {"f32": 152 * 128 * 2 * 2.070e9 / 1e12, "f64": 1.25}
@@ -217,34 +229,41 @@ class ClockSampler:
 
 
 def ref_rounds(args, name):
-    """Rounds of the oracle sample: about 3.4e11 flops of sketch (8 s on 16 Grace cores)."""
+    """Rounds of the oracle sample: about 1.7e11 flops of sketch (4 s on 16 Grace cores)."""
     if args.ref_rounds > 0:
         return args.ref_rounds
     m, n, _, _, _, _, b = WORKLOADS[name]
-    return int(min(8, max(1, round(3.4e11 / (2.0 * m * n * b)))))
+    return int(min(8, max(1, round(1.7e11 / (2.0 * m * n * b)))))
+
+
+def on_grid(Om):
+    """Omega as the FP64-accurate tensor-core path defines it: the Gaussian rounded
+    to the grid 2^-11 and clipped at |q| <= 16383."""
+    import numpy as np
+    return np.clip(np.rint(Om * 2048.0), -16383.0, 16383.0) / 2048.0
 
 
 def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
     """The FP64 oracle as it stands, on the first `rounds` rounds of Algorithm 1
-    over the full matrix (the run stops at k_max = rounds * b).  Returns
-    (GFLOP/s, seconds, threads, description)."""
-    import numpy as np
-
+    over the full matrix (the run stops at k_max = rounds * b), with the Gaussian
+    rows of `seed` (on the grid 2^-11 for the FP64-accurate tensor-core path).
+    Returns (GFLOP/s, seconds, threads, description, oracle result)."""
     import oracle
-    _, _, _, _, _, tol, b = WORKLOADS[name]
+    _, _, _, _, dt, tol, b = WORKLOADS[name]
     m, n = A_host_f64.shape  # the workload's size on a GPU box; reduced without a GPU
     kmax = rounds * b
     Om = oracle.gaussian_rows(seed, 0, (rounds + 1) * b, m)
+    if dt == "f64emu":
+        Om = on_grid(Om)
     t0 = time.perf_counter()
     r = oracle.id_adaptive(A_host_f64, Om, b, tol * 1.0, kmax=kmax)
-    dt = time.perf_counter() - t0
+    dt_s = time.perf_counter() - t0
     k = r["k"]
     flops = algorithmic_flops(m, n, k, b)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = ("oracle (plain C, FP64, OpenMP) on the first %d rounds of Algorithm 1 over the whole "
-            "%dx%d matrix (k_max = %d), %.1f s" % (rounds, m, n, kmax, dt))
-    del np
-    return flops / dt / 1e9, dt, threads, desc
+            "%dx%d matrix (k_max = %d), %.1f s" % (rounds, m, n, kmax, dt_s))
+    return flops / dt_s / 1e9, dt_s, threads, desc, r
 
 
 def run_reference(args, rank, world):
@@ -270,7 +289,7 @@ def run_reference(args, rank, world):
     rounds = ref_rounds(args, name)
     times, vals = [], []
     for i in range(args.warmup + args.steps):
-        v, sec, threads, desc = cpu_oracle_sample(A_host, name, seed=2310_09417 + i, rounds=rounds)
+        v, sec, threads, desc, _ = cpu_oracle_sample(A_host, name, seed=2310_09417 + i, rounds=rounds)
         if i >= args.warmup:
             times.append(sec)
             vals.append(v)
@@ -378,24 +397,22 @@ def make_batch(name, device, seed=2310_09417 + 3):
     return As
 
 
-def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks):
+def measure_batched(B, name, dev, steps, warmup, seed, *, e2e=True, cpu_baseline=False, errors=False,
+                    max_over_ranks=None, barrier=None):
+    """One persistent launch per step over the whole batch of kernel blocks.
+    Returns the form's measurements (ms per step, GFLOP/s, roofline, e2e, the
+    ranks, and with `errors` each block's relative error evaluated in FP64)."""
     import torch
 
-    from paper_2310_09417_gb300 import binding as B
-    name = args.workload
+    max_over_ranks = max_over_ranks or (lambda x: x)
+    barrier = barrier or (lambda: None)
     npts, count, kind, kw, dt, tol, b = WORKLOADS[name]
     As = make_batch(name, dev)
-    seed = 2310_09417 + 100 * rank
     xdt = torch.float64 if dt == "f64" else torch.float32
     outs = [(torch.empty(min(A.shape), dtype=torch.int64, device=dev),
              torch.empty((A.shape[1], min(A.shape)), dtype=xdt, device=dev)) for A in As]
     nbytes = sum(A.numel() * A.element_size() for A in As)
-    ws = None
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        return B.id_batched(As, tol, block=b, seed=seed, outs=outs, workspace=ws, stream=stream)
-    res = step()
     import ctypes
     mats = (B.IdMatrix * len(As))(*[B._matrix(a) for a in As])
     o = B._opts(As[0], block=b, tol=tol, relative=True, k_max=0, k0=0, blocks_per_pass=1, seed=seed, omega=None,
@@ -403,35 +420,48 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
     nb = ctypes.c_size_t(0)
     B.load().id_batched_workspace_size(len(As), mats, ctypes.byref(o), ctypes.byref(nb))
     ws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
+
+    def step():
+        return B.id_batched(As, tol, block=b, seed=seed, outs=outs, workspace=ws, stream=stream)
+    for _ in range(max(warmup, 1)):
         res = step()
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_gpu(dev)) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             res = step()
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps)
     flops = sum(algorithmic_flops(A.shape[0], A.shape[1], r.k, b) for A, r in zip(As, res))
-    # whole job: the work of every rank (replicas with their own seeds) over the slowest rank's time
-    flops_all = sum_over_ranks(flops)
-    ids_all = sum_over_ranks(float(len(As)))
-    value = flops_all / (ms * 1e-3) / 1e9
     ks = [r.k for r in res]
     peak = ALU_PEAK_TFLOPS[dt]
     achieved = flops / (ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_batched (one persistent launch per step, %s FMA)" % dt,
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "timing": "CUDA events around the whole step (descriptor upload, graph "
-                                          "replay of the persistent kernel, result copy)",
-                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
-                                                 else "GB300 FP64 rate 1.25 TFLOP/s")}
-    e2e = None
-    if not args.no_e2e:
+    out = {"workload": name, "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e9, "unit": UNIT,
+           "steps": steps, "warmup": warmup, "flops": flops, "ids": len(As),
+           "roofline": {"bound": "alu", "kernel": "k_batched (one persistent launch per step, %s FMA)" % dt,
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "traffic": None, "timing": "CUDA events around the whole step (descriptor upload, graph "
+                                                   "replay of the persistent kernel, result copy)",
+                        "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
+                                                         else "GB300 FP64 rate 1.25 TFLOP/s")},
+           "result": {"k_mean": sum(ks) / len(ks), "k_max": max(ks), "k_min": min(ks),
+                      "statuses": sorted(set(r.status for r in res)), "batch_gb": round(nbytes / 1e9, 2),
+                      "ids_per_s": len(As) / (ms * 1e-3)},
+           "gpu_launches": 2 * steps, "clocks": clk.summary()}
+    if errors:
+        # each block's ||A - A(:,J)X||_F / ||A||_F evaluated in FP64 (harness check, not timed)
+        rel = []
+        for A, r in zip(As, res):
+            A64 = A.double()
+            E = A64 - A64[:, r.J] @ r.X.double()
+            rel.append(float(torch.linalg.norm(E) / torch.linalg.norm(A64)))
+        out["result"].update({"rel_err_max": max(rel), "rel_err_mean": sum(rel) / len(rel),
+                              "met_tol": sum(1 for e in rel if e <= tol), "tol": tol})
+    if e2e:
         hosts = [torch.empty((A.shape[1], A.shape[0]), dtype=A.dtype, pin_memory=True) for A in As]
         for h, A in zip(hosts, As):
             h.copy_(A.t())
@@ -446,21 +476,23 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
             for x, (_, X) in zip(xh, outs):
                 x.copy_(X, non_blocking=True)
             return r
-        for _ in range(args.warmup):
+        for _ in range(max(warmup, 1)):
             e2e_step()
         torch.cuda.synchronize()
+        barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        e2e = {"value": flops_all / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in xh)}
+        barrier()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        out["e2e"] = {"value": flops / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+                      "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in xh)}
         del hosts, devs, xh
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if cpu_baseline:
         import numpy as np
 
         import oracle
@@ -477,21 +509,36 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
             if time.perf_counter() - t0 > 8.0:
                 break
         dtc = time.perf_counter() - t0
-        cpu = {"value": fl / dtc / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
-               "kind": "oracle", "sample": "oracle (plain C, FP64, OpenMP) on the first %d of the %d blocks, %.1f s"
-                                           % (used, len(As), dtc)}
+        out["cpu_baseline"] = {"value": fl / dtc / 1e9, "unit": UNIT,
+                               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())), "kind": "oracle",
+                               "sample": "oracle (plain C, FP64, OpenMP) on the first %d of the %d blocks, %.1f s"
+                                         % (used, len(As), dtc)}
+    del As, outs, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks):
+    from paper_2310_09417_gb300 import binding as B
+    name = args.workload
+    seed = 2310_09417 + 100 * rank
+    r = measure_batched(B, name, dev, args.steps, args.warmup, seed, e2e=not args.no_e2e,
+                        cpu_baseline=rank == 0 and world == 1 and not args.no_cpu_baseline,
+                        max_over_ranks=max_over_ranks, barrier=barrier)
+    # whole job: the work of every rank (replicas with their own seeds) over the slowest rank's time
+    flops_all = sum_over_ranks(r["flops"])
+    value = flops_all / (r["ms_per_step"] * 1e-3) / 1e9
+    if r.get("e2e"):
+        r["e2e"]["value"] = flops_all / (r["e2e"]["ms_per_step"] * 1e-3) / 1e9
     if rank == 0:
         cfg = config_dict(name, None)
-        cfg.update({"k_mean": sum(ks) / len(ks), "k_max": max(ks), "k_min": min(ks),
-                    "batch_gb": round(nbytes / 1e9, 2)})
+        cfg.update({k: r["result"][k] for k in ("k_mean", "k_max", "k_min", "batch_gb")})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"f64emu": "f64 (sketch: bf16 digit products, exact sums)", "fp8": "fp8 e4m3 (sketch), f32 (LU)",
-                                                "bf16": "bf16 (sketch), f32 (LU)"}.get(dt, dt),
-                "data": "synthetic", "config": cfg, "roofline": roofline,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
-                "result": {"ids_per_s": ids_all / (ms * 1e-3), "gflop_per_step": flops / 1e9,
-                           "statuses": sorted(set(r.status for r in res))}}
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL.get(WORKLOADS[name][4], "f64"),
+                "data": "synthetic", "config": cfg, "roofline": r["roofline"],
+                "cpu_baseline": r.get("cpu_baseline"), "e2e": r.get("e2e"), "gpu_launches": r["gpu_launches"],
+                "clocks": r["clocks"], "result": r["result"]}
         print(json.dumps(line), flush=True)
 
 
@@ -509,7 +556,301 @@ def over_ranks(x: float, op: str, world: int, device) -> float:
 
 
 def local_gpu(dev):
-    return dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else dev.index
+    return dev.index
+
+
+DTYPE_LABEL = {
+    "f64": "f64",
+    "f32": "f32",
+    "f64emu": "f64 (FP64-accurate: sketch, Schur GEMM and block update as exact bf16 digit products on tcgen05 "
+              "with fp32/int64 sums; LU, X and norms in f64)",
+    "f32emu": "f32 (FP32-accurate sketch as exact bf16 digit products on tcgen05; LU and X in f32)",
+    "bf16": "bf16 (sketch on tcgen05, fp32 accumulation), f32 (LU, X), f64 (norms)",
+    "fp8": "fp8 e4m3 (sketch on tcgen05, fp32 accumulation), f32 (LU, X), f64 (norms)",
+}
+
+
+def sketch_roofline(name, m, n, b, passes, sk_ms, sk_launches):
+    """Roofline of the dominant kernel, the sketch (+ its split-K reduction), from the
+    library's per-phase CUDA events on the launching stream.  `achieved` counts the
+    method's own bytes (or flops) per pass: A read once in its storage precision,
+    one Omega block, the sketch block written."""
+    dt = WORKLOADS[name][4]
+    hbm = {"peak": PEAKS["hbm_gbs"], "unit": "GB/s", "bound": "hbm",
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if dt == "bf16":
+        byts = (2.0 * m * n + 2.0 * b * m + 4.0 * n * b) * passes
+        r = dict(hbm, kernel="k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce")
+    elif dt == "fp8":
+        nbs = (m + 127) // 128
+        byts = (1.0 * m * n + 4.0 * nbs * n + 1.0 * b * m + 4.0 * n * b) * passes
+        r = dict(hbm, kernel="k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + split-K reduce")
+    elif dt == "f32emu":
+        # the method's bytes: A in FP32 (4 mn) per pass; the kernel streams its 3 BF16
+        # digit slices (6 mn) instead, plus a once-per-call slicing of A
+        byts = (4.0 * m * n + 4.0 * b * m + 4.0 * n * b) * passes
+        kp = (m + 63) // 64 * 64
+        stream = (6.0 * kp * n + 16.0 * b * kp + 4.0 * n * b) * passes + 10.0 * m * n
+        r = dict(hbm, kernel="k_sketch_f32emu (tcgen05 + TMA, exact digit slices) + Omega slicing + split-K reduce",
+                 stream_bytes=stream, frac_of_stream=stream / (sk_ms * 1e-3) / 1e9 / PEAKS["hbm_gbs"])
+    elif dt == "f64emu":
+        # the method's bytes: A in FP64 (8 mn) per pass; the kernel streams its 7 BF16
+        # digit slices (14 mn) instead, plus a once-per-call slicing of A (30 mn)
+        byts = (8.0 * m * n + 8.0 * b * m + 8.0 * n * b) * passes
+        mp = (m + 7) // 8 * 8
+        stream = (14.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * passes + 30.0 * m * n
+        r = dict(hbm, kernel="k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K reduce + digit "
+                             "preparation", stream_bytes=stream,
+                 frac_of_stream=stream / (sk_ms * 1e-3) / 1e9 / PEAKS["hbm_gbs"])
+    else:
+        fl = 2.0 * m * n * b * passes
+        achieved = fl / (sk_ms * 1e-3) / 1e12
+        peak = ALU_PEAK_TFLOPS[dt]
+        return {"bound": "alu", "kernel": "k_sgemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": PROFILED_TRAFFIC.get(name), "sketch_launches_per_step": sk_launches,
+                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
+                                                 else "GB300 FP64 rate 1.25 TFLOP/s")}
+    achieved = byts / (sk_ms * 1e-3) / 1e9
+    r.update({"achieved": achieved, "frac": achieved / r["peak"], "traffic": PROFILED_TRAFFIC.get(name),
+              "algorithmic_bytes_per_step": byts, "sketch_launches_per_step": sk_launches})
+    return r
+
+
+def sampled_rel_error(A, J, X, norm_A, rows=4096, seed=5):
+    """||A - A(:,J) X||_F / ||A||_F estimated in FP64 from a uniform sample of the
+    rows of A (the squared error is a sum over rows, so (m/rows) times the
+    sample's sum is unbiased).  A harness evaluation, not part of the timed ID."""
+    import torch
+    m, n = A.shape
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    I = torch.randperm(m, generator=g)[: min(rows, m)].to(X.device)
+    if hasattr(A, "scale"):  # FP8: decoded values times the block scales
+        rowsA = A.data.t()[:, I].float().t() * A.scale.t()[:, I // 128].t()
+    else:
+        rowsA = A.t()[:, I].t()
+    R = rowsA.double()
+    E = R - R[:, J] @ X.double()
+    return float(torch.linalg.norm(E)) * math.sqrt(m / len(I)) / norm_A
+
+
+def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predictor=None, max_pass_rows=0,
+                     max_over_ranks=None, barrier=None, want_pivots=False):
+    """Time `steps` complete adaptive IDs of A (inputs resident in HBM) after
+    `warmup` untimed ones; then, unless e2e is False, the same ID through the C ABI
+    with A copied in from pinned host memory and J, X copied back inside the timed
+    region.  Returns the measurements and the last result."""
+    import torch
+
+    max_over_ranks = max_over_ranks or (lambda x: x)
+    barrier = barrier or (lambda: None)
+    m, n, kind, kw, dt, tol, b = WORKLOADS[name]
+    kmax = min(m, n)
+    xdt = torch.float64 if dt in ("f64", "f64emu") else torch.float32
+    sprec = {"f64emu": B.F64_EMU, "f32emu": B.F32_EMU}.get(dt)
+    J = torch.empty(kmax, dtype=torch.int64, device=dev)
+    Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
+    opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
+                   omega=None, profile=True, sketch_prec=sprec)
+    if predictor is not None:
+        opts.predictor = predictor.data_ptr()
+        opts.max_pass_rows = max_pass_rows
+    ws = torch.empty(B.workspace_size(A, opts), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(profile=True, pivots=False):
+        return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
+                             workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec, pivots=pivots,
+                             predictor=predictor, max_pass_rows=max_pass_rows)
+
+    for _ in range(max(warmup, 1)):
+        res = step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(local_gpu(dev)) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            results.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps)
+    res = results[-1]
+    flops = algorithmic_flops(m, n, res.k, b)
+    sk_ms = sum(r.phase_ms["sketch"] for r in results) / steps
+    roof = sketch_roofline(name, m, n, b, res.passes, sk_ms, res.phase_launches["sketch"])
+    tot = max(1e-9, sum(res.phase_ms.values()))
+    roof.update({"phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
+                 "phase_share": {k: round(v / tot, 4) for k, v in res.phase_ms.items()},
+                 "timing": "library CUDA events on the launching stream around each phase, inside the timed "
+                           "region"})
+    out = {"workload": name, "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e9, "unit": UNIT,
+           "steps": steps, "warmup": warmup, "flops": flops, "roofline": roof,
+           "gpu_launches": sum(r.launches for r in results), "clocks": clk.summary(),
+           "result": {"k": res.k, "rounds": res.rounds, "passes": res.passes, "status": res.status,
+                      "est_err_rel": res.est_err / res.norm_A if res.norm_A > 0 else 0.0,
+                      "gflop_per_id": flops / 1e9}}
+    if want_pivots:  # an untimed run that also returns the pivots |U(i,i)|
+        pres = step(profile=False, pivots=True)
+        out["pivots"] = pres.pivots.double().cpu().numpy()
+        out["J_host"] = pres.J.cpu().numpy()
+        out["trace"] = list(pres.trace)
+    if e2e:
+        is8 = hasattr(A, "scale")
+        if is8:  # the E4M3 bytes (row stride ld) and the block scales travel
+            ldq = A.data.stride(1)
+            A_host = torch.empty((n, ldq), dtype=torch.uint8, pin_memory=True)
+            A_host.copy_(A.data.view(torch.uint8).t().as_strided((n, ldq), (ldq, 1)))
+            S_host = torch.empty(A.scale.t().shape, dtype=torch.float32, pin_memory=True)
+            S_host.copy_(A.scale.t())
+            A_dev = torch.empty((n, ldq), dtype=torch.uint8, device=dev)
+            S_dev = torch.empty(S_host.shape, dtype=torch.float32, device=dev)
+            A_in = B.FP8Matrix(A_dev.view(torch.float8_e4m3fn)[:, :m].t(), S_dev.t())
+        else:
+            A_host = torch.empty((n, m), dtype=A.dtype, pin_memory=True)
+            A_host.copy_(A.t())
+            A_dev = torch.empty((n, m), dtype=A.dtype, device=dev)
+            A_in = A_dev.t()
+        X_host = torch.empty((n, kmax), dtype=xdt, pin_memory=True)
+        J_host = torch.empty(kmax, dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            A_dev.copy_(A_host, non_blocking=True)
+            if is8:
+                S_dev.copy_(S_host, non_blocking=True)
+            r = B.id_adaptive(A_in, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
+                              workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec,
+                              predictor=predictor, max_pass_rows=max_pass_rows)
+            kk = r.k
+            X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
+            J_host[:kk].copy_(J[:kk], non_blocking=True)
+            return r
+        for _ in range(max(warmup, 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        xel = torch.empty((), dtype=xdt).element_size()
+        h2d = A_host.numel() * A_host.element_size() + (S_host.numel() * 4 if is8 else 0)
+        out["e2e"] = {"value": flops / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": r.k * n * xel + 8 * r.k}
+        del A_host, A_dev, X_host, A_in
+    out["_res"] = res
+    out["_bufs"] = (J, Xbuf)
+    del ws
+    return out
+
+
+def public(form):
+    """A form's measurements without the in-memory objects."""
+    return {k: v for k, v in form.items() if not k.startswith("_") and k not in ("pivots", "J_host", "trace")}
+
+
+def parity_with_oracle(main, A, name, seed, rounds):
+    """The oracle on the first `rounds` rounds of Algorithm 1 over the same full-size
+    matrix and the same Gaussian rows; compares the GPU's first rounds*b skeletons
+    (bit-exact), the estimates E^(t) and the pivots |U(i,i)|.  Returns the
+    cpu_baseline entry and the parity entry."""
+    import numpy as np
+    A_host64 = host_f64(A)
+    v, sec, threads, desc, r = cpu_oracle_sample(A_host64, name, seed=seed, rounds=rounds)
+    del A_host64
+    kk = r["k"]
+    Jg = main["J_host"][:kk]
+    nA = main["_res"].norm_A
+    tr_o = np.asarray(r["trace"])
+    tr_g = np.asarray(main["trace"][: len(tr_o)])
+    nt = min(len(tr_o), len(tr_g))
+    tr_d = (float(np.max(np.abs(tr_g[:nt] - tr_o[:nt]) / (np.abs(tr_o[:nt]) + 1e-13 * nA))) if nt else 0.0)
+    pv_o = np.asarray(r["pivots"][:kk])
+    pv_g = main["pivots"][:kk]
+    pv_d = float(np.max(np.abs(pv_g - pv_o) / np.maximum(np.abs(pv_o), 1e-300)))
+    par = {"oracle_rounds": rounds, "skeletons_compared": int(kk),
+           "J_prefix_identical": bool(np.array_equal(Jg, r["J"])),
+           "J_prefix_mismatches": int(np.sum(Jg != r["J"])),
+           "estimates_compared": int(nt), "estimate_max_rel_diff": tr_d,
+           "pivots_max_rel_diff": pv_d,
+           "bar": "J bit-exact; E within 1e-9 relative (+1e-13 ||A||_F); pivots within 1e-9 relative"}
+    par["pass"] = bool(par["J_prefix_identical"] and tr_d <= 1e-9 and pv_d <= 1e-9)
+    cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    return cpu, par
+
+
+def run_forms(B, dev, main, A, seed, args):
+    """The forms the metric compares on the same GB300, each timed with its own
+    CUDA events: plain FP64 on the same matrix, the FP32-accurate tensor-core path,
+    the BF16 and FP8 mixed-precision paths, the predictor-seeded BF16 path and the
+    batched path.  Each carries ms per ID, GFLOP/s, its dominant kernel's
+    roofline fraction, e2e, and its error (against the oracle where it can run,
+    else evaluated in FP64 on a row sample)."""
+    import torch
+
+    forms = {}
+    fs, fw = args.form_steps, args.form_warmup
+    # plain FP64 on the same A: the metric's baseline
+    base = measure_adaptive(B, "adaptive_poly_f64", A, dev, max(1, fs - 1), 1, seed, e2e=False)
+    fb = public(base)
+    fb["result"]["note"] = ("plain FP64 sketch with the unrounded Gaussian rows; the headline's rows are on "
+                            "the grid 2^-11, so the two skeletons are each checked against the oracle, not "
+                            "against each other")
+    forms["adaptive_poly_f64"] = fb
+    plain = fb["value"]
+    del base
+    torch.cuda.empty_cache()
+    # FP32-accurate sketch on the tensor cores: the same matrix rounded to FP32
+    A32 = A.t().float().t()
+    f = measure_adaptive(B, "adaptive_poly_f32emu", A32, dev, fs, fw, seed)
+    forms["adaptive_poly_f32emu"] = public(f)
+    forms["adaptive_poly_f32emu"]["config_note"] = "the headline's FP64 matrix rounded to FP32"
+    del f, A32
+    torch.cuda.empty_cache()
+    # mixed precision: BF16 A (100000 x 20000), tolerance 3e-2 (stops just after the signal)
+    Ab = make_input("mixed_bf16_tol3e-2", dev)
+    f = measure_adaptive(B, "mixed_bf16_tol3e-2", Ab, dev, fs + 2, fw, seed)
+    r = f["_res"]
+    f["result"]["rel_err_sampled"] = sampled_rel_error(Ab, r.J, r.X, r.norm_A)
+    fpub = public(f)
+    forms["mixed_bf16_tol3e-2"] = fpub
+    # the same run seeded by the learned rank predictor
+    from paper_2310_09417_gb300 import predictor as P
+    params = P.load(os.path.join(ROOT, "paper_2310_09417_gb300", "data", "rank_predictor.f32"), device=dev)
+    g = measure_adaptive(B, "mixed_bf16_tol3e-2", Ab, dev, fs + 2, fw, seed, predictor=params, max_pass_rows=4096)
+    gr = g["_res"]
+    gp = public(g)
+    gp["result"]["identical_to_plain"] = bool(gr.k == r.k and torch.equal(g["_bufs"][0][:gr.k], f["_bufs"][0][:r.k])
+                                              and torch.equal(g["_bufs"][1][:, :gr.k], f["_bufs"][1][:, :r.k]))
+    gp["result"]["passes_plain"] = r.passes
+    gp["result"]["ms_saved_vs_plain"] = fpub["ms_per_step"] - gp["ms_per_step"]
+    forms["mixed_bf16_tol3e-2_predictor"] = gp
+    del f, g
+    torch.cuda.empty_cache()
+    # FP8 E4M3 storage with per-128-row block scales, tolerance 1e-3
+    A8 = B.quantize_fp8(Ab, pow2=True)
+    del Ab
+    torch.cuda.empty_cache()
+    f = measure_adaptive(B, "mixed_fp8", A8, dev, fs, fw, seed)
+    forms["mixed_fp8"] = public(f)
+    del f, A8
+    torch.cuda.empty_cache()
+    # batched: 4096 kernel blocks in one persistent launch per step
+    forms["batched_kernel_f64"] = measure_batched(B, "batched_kernel_f64", dev, fs, fw, seed, errors=True)
+    for k, v in forms.items():
+        v["gflops_over_plain_f64"] = v["value"] / plain
+        if k.startswith("adaptive_poly"):
+            v["speedup_over_plain_f64_same_matrix"] = forms["adaptive_poly_f64"]["ms_per_step"] / v["ms_per_step"]
+    return forms
 
 
 def main():
@@ -521,7 +862,13 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-rounds", type=int, default=0, help="oracle rounds per sample (0: sized to ~8 s)")
+    ap.add_argument("--ref-rounds", type=int, default=0, help="oracle rounds per sample (0: sized to ~4 s)")
+    ap.add_argument("--parity-rounds", type=int, default=7,
+                    help="oracle rounds of the full-size parity check in the cpu_baseline leg")
+    ap.add_argument("--forms", default="auto", choices=["auto", "all", "none"],
+                    help="time the other forms the metric compares (auto: with the default workload on one GPU)")
+    ap.add_argument("--form-steps", type=int, default=3)
+    ap.add_argument("--form-warmup", type=int, default=2)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -532,7 +879,6 @@ def main():
         run_reference(args, rank, world)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -565,169 +911,38 @@ def main():
     m, n, kind, kw, dt, tol, b = WORKLOADS[name]
     A = make_input(name, dev)
     seed = 2310_09417 + 100 * rank
-    kmax = min(m, n)
-    xdt = torch.float64 if dt in ("f64", "f64emu") else torch.float32
-    sprec = {"f64emu": B.F64_EMU, "f32emu": B.F32_EMU}.get(dt)
-    J = torch.empty(kmax, dtype=torch.int64, device=dev)
-    Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
-    opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
-                   omega=None, profile=True, sketch_prec=sprec)
-    ws = torch.empty(B.workspace_size(A, opts), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    main_r = measure_adaptive(B, name, A, dev, args.steps, args.warmup, seed, e2e=not args.no_e2e,
+                              max_over_ranks=max_over_ranks, barrier=barrier, want_pivots=want_cpu)
+    res = main_r["_res"]
+    # whole job: every rank's ID (own seed) over the slowest rank's time
+    flops_all = sum_over_ranks(main_r["flops"])
+    value = flops_all / (main_r["ms_per_step"] * 1e-3) / 1e9
+    if main_r.get("e2e"):
+        main_r["e2e"]["value"] = flops_all / (main_r["e2e"]["ms_per_step"] * 1e-3) / 1e9
 
-    def step(profile=True):
-        return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
-                             workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec)
+    cpu, parity = None, None
+    if want_cpu:
+        rounds = args.parity_rounds if kind in ("poly", "step") else ref_rounds(args, name)
+        cpu, parity = parity_with_oracle(main_r, A, name, seed, rounds)
 
-    for _ in range(args.warmup):
-        res = step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    results = []
-    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            results.append(step())
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    ms_local = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ms_local)
-    res = results[-1]
-    flops = algorithmic_flops(m, n, res.k, b)
-    flops_all = sum_over_ranks(flops)  # every rank's ID (own seed) over the slowest rank's time
-    value = flops_all / (ms * 1e-3) / 1e9
-
-    # roofline of the dominant kernel: the sketch GEMM (+ its split-K reduction)
-    sk_ms = sum(r.phase_ms["sketch"] for r in results) / args.steps
-    sk_launches = results[-1].phase_launches["sketch"]
-    phase_share = {k: round(v / max(1e-9, sum(res.phase_ms.values())), 4) for k, v in res.phase_ms.items()}
-    if dt == "bf16":
-        # HBM-bound (64 flop/B against a ridge near 285): algorithmic bytes per pass =
-        # A (2mn) + one Omega block (2bm) + the FP32 sketch block written (4nb)
-        sk_bytes = (2.0 * m * n + 2.0 * b * m + 4.0 * n * b) * res.passes
-        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
-        peak = PEAKS["hbm_gbs"]
-        roofline = {"bound": "hbm", "kernel": "k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce",
-                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    elif dt == "fp8":
-        # HBM-bound: per pass A (mn bytes) + its block scales (4 n ceil(m/128)) + one E4M3
-        # Omega block (bm) + the FP32 sketch block written (4nb)
-        nbs = (m + 127) // 128
-        sk_bytes = (1.0 * m * n + 4.0 * nbs * n + 1.0 * b * m + 4.0 * n * b) * res.passes
-        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
-        peak = PEAKS["hbm_gbs"]
-        roofline = {"bound": "hbm", "kernel": "k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + "
-                    "split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": PROFILED_TRAFFIC.get(name), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    elif dt == "f32emu":
-        # HBM-bound at one block per pass: per pass the 3 BF16 digit slices of A (6 mn) +
-        # Omega read and sliced (4 bm + 6 bm + 6 bm) + the FP32 sketch block (4 n b)
-        kp = (m + 63) // 64 * 64
-        sk_bytes = (6.0 * kp * n + 16.0 * b * kp + 4.0 * n * b) * res.passes + 10.0 * m * n
-        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
-        peak = PEAKS["hbm_gbs"]
-        roofline = {"bound": "hbm", "kernel": "k_sketch_f32emu (tcgen05 + TMA, exact digit slices) + Omega "
-                    "slicing + split-K reduce", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(name),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    elif dt == "f64emu":
-        # HBM-bound at one block per pass (rows = 64: about 120 tensor flop/B against a
-        # ridge near 290): per pass the 7 BF16 digit slices of A (14 mn) + both Omega digit
-        # planes (4 b m) + the FP64 sketch block (8 n b); once per ID the digit preparation
-        # (A read twice, the slices written: 30 mn)
-        mp = (m + 7) // 8 * 8
-        sk_bytes = (14.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * res.passes + 30.0 * m * n
-        achieved = sk_bytes / (sk_ms * 1e-3) / 1e9
-        peak = PEAKS["hbm_gbs"]
-        roofline = {"bound": "hbm", "kernel": "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K "
-                    "reduce + digit preparation", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(name),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    else:
-        sk_flops = 2.0 * m * n * b * res.passes  # one b-row block per pass
-        achieved = sk_flops / (sk_ms * 1e-3) / 1e12
-        peak = ALU_PEAK_TFLOPS[dt]
-        roofline = {"bound": "alu", "kernel": "k_sgemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": PROFILED_TRAFFIC.get(name),
-                    "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
-                                                     else "GB300 FP64 rate 1.25 TFLOP/s")}
-    roofline.update({"phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
-                     "phase_share": phase_share, "sketch_launches_per_step": sk_launches})
-    gpu_launches = sum(r.launches for r in results)
-
-    # end to end: pinned host A -> device, ID, J and X back to pinned host
-    e2e = None
-    if not args.no_e2e:
-        is8 = hasattr(A, "scale")
-        if is8:  # the E4M3 bytes (row stride ld) and the block scales travel
-            ldq = A.data.stride(1)
-            A_host = torch.empty((n, ldq), dtype=torch.uint8, pin_memory=True)
-            A_host.copy_(A.data.view(torch.uint8).t().as_strided((n, ldq), (ldq, 1)))
-            S_host = torch.empty(A.scale.t().shape, dtype=torch.float32, pin_memory=True)
-            S_host.copy_(A.scale.t())
-            A_dev = torch.empty((n, ldq), dtype=torch.uint8, device=dev)
-            S_dev = torch.empty(S_host.shape, dtype=torch.float32, device=dev)
-            A_in = B.FP8Matrix(A_dev.view(torch.float8_e4m3fn)[:, :m].t(), S_dev.t())
-        else:
-            A_host = torch.empty((n, m), dtype=A.dtype, pin_memory=True)
-            A_host.copy_(A.t())
-            A_dev = torch.empty((n, m), dtype=A.dtype, device=dev)
-            A_in = A_dev.t()
-        X_host = torch.empty((n, kmax), dtype=xdt, pin_memory=True)
-        J_host = torch.empty(kmax, dtype=torch.int64, pin_memory=True)
-
-        def e2e_step():
-            A_dev.copy_(A_host, non_blocking=True)
-            if is8:
-                S_dev.copy_(S_host, non_blocking=True)
-            r = B.id_adaptive(A_in, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
-                              workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec)
-            kk = r.k
-            X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
-            J_host[:kk].copy_(J[:kk], non_blocking=True)
-            return r
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            r = e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        xel = torch.empty((), dtype=xdt).element_size()
-        h2d = A_host.numel() * A_host.element_size() + (S_host.numel() * 4 if is8 else 0)
-        e2e = {"value": flops_all / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
-               "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": r.k * n * xel + 8 * r.k}
-        del A_host, A_dev, X_host, A_in
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_host64 = host_f64(A)
-        v, sec, threads, desc = cpu_oracle_sample(A_host64, name, seed=seed, rounds=ref_rounds(args, name))
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
-        del A_host64
+    forms = None
+    if args.forms == "all" or (args.forms == "auto" and name == DEFAULT_WORKLOAD and world == 1):
+        forms = run_forms(B, dev, main_r, A, seed, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"f64emu": "f64 (sketch: bf16 digit products, exact sums)", "fp8": "fp8 e4m3 (sketch), f32 (LU)",
-                                                "bf16": "bf16 (sketch), f32 (LU)"}.get(dt, dt),
-                "data": "synthetic",
-                "config": config_dict(name, res), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clk.summary(),
-                "result": {"k": res.k, "est_err_rel": res.est_err / res.norm_A, "status": res.status,
-                           "gflop_per_id": flops / 1e9}}
+                "warmup": args.warmup, "ms_per_step": main_r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL[dt], "data": "synthetic",
+                "config": config_dict(name, res), "roofline": main_r["roofline"], "cpu_baseline": cpu,
+                "e2e": main_r.get("e2e"), "gpu_launches": main_r["gpu_launches"], "clocks": main_r["clocks"],
+                "result": main_r["result"], "parity": parity}
+        if forms is not None:
+            line["forms"] = forms
+            base = forms["adaptive_poly_f64"]
+            line["plain_f64_same_matrix"] = {"ms_per_step": base["ms_per_step"], "value": base["value"],
+                                             "k": base["result"]["k"],
+                                             "speedup": base["ms_per_step"] / main_r["ms_per_step"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

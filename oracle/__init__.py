@@ -9,9 +9,11 @@ Every function follows the paper step by step; see ``oracle.h`` for the
 conventions (column ID orientation, tie rule, Gaussian generator, the
 variance reading of the estimator's scale).
 
-Parity unpinned: the factor 4 log k / k of Eq. normUest and Eq. maxUest in
-``ur_estimates`` (see its docstring); every other function is pinned by
-``tests/test_oracle_pins.py`` or ``tests/test_oracle_mlp.py``.
+Every function is pinned by ``tests/test_oracle_pins.py`` or
+``tests/test_oracle_mlp.py``.  The factor (4 log k / k) sqrt(n-k) that Eq.
+normUest and Eq. maxUest put in front of ||U_r||_F and max|U_r| is not
+computed here: the paper supports it only with a figure, so nothing pins it
+(see ``ur_estimates``).
 """
 from __future__ import annotations
 
@@ -236,7 +238,7 @@ def stable_x(A, J) -> np.ndarray:
 
 
 def ur_estimates(A, Omega, k: int) -> dict:
-    """The residual-U_r error estimates of Remark 1 (Sec. 3.2), in column form.
+    """The residual block U_r of Remark 1 (Sec. 3.2), in column form.
 
     Omega has k + p rows: the first k give the rank-k skeleton, the last p are
     the independent sample set aside for the estimate.  LUPP of the transposed
@@ -244,25 +246,23 @@ def ur_estimates(A, Omega, k: int) -> dict:
     P Y^T = [L1; L2 L_r] [U1 U2; 0 U_r] with U_r the trailing p x p block.
     Returns U_r, L_r ((n-k) x p, unit lower trapezoidal), the Schur estimate
     E = ||L_r U_r||_F / sqrt(p) (Eq. errSch), the bound sqrt(n-k) ||U_r||_F,
-    and the estimates of Eq. normUest and Eq. maxUest: (4 log k / k) sqrt(n-k)
-    times ||U_r||_F, or times max |U_r(i,j)| (log is the natural logarithm,
-    that of the growth-factor bound k / (4 log k) the remark takes over).
-    The factor 4 log k / k is parity unpinned: the paper supports it only with
-    a figure; the tests pin U_r, L_r, the Schur identity, the bound, and the
-    appendix's statement that Eq. normUest stays above the best rank-k error."""
+    and the two norms Eq. normUest and Eq. maxUest are built from:
+    u_fro = ||U_r||_F and u_max = max |U_r(i,j)|.  The paper multiplies them by
+    (4 log k / k) sqrt(n-k) (the reciprocal of the growth-factor bound
+    k / (4 log k) it borrows); that factor has no support but a figure the text
+    does not carry, so it is left to the caller and nothing here depends on it."""
     A = _colmajor(A)
     n = A.shape[1]
     l = Omega.shape[0]
     p = l - k
-    if not (2 <= k and 1 <= p and l <= n):
-        raise ValueError("ur_estimates needs k >= 2, at least one extra row and k + p <= n")
+    if not (1 <= k and 1 <= p and l <= n):
+        raise ValueError("ur_estimates needs k >= 1, at least one extra row and k + p <= n")
     LU, perm, _ = lupp(sketch_t(A, Omega), steps=l)
     U_r = np.triu(LU[k:l, k:l])
     L_r = np.tril(LU[k:, k:l], -1) + np.eye(n - k, p)
     nrm, mx = float(np.linalg.norm(U_r)), float(np.abs(U_r).max())
-    scale = 4.0 * np.log(k) / k * np.sqrt(n - k)
     return dict(U_r=U_r, L_r=L_r, perm=perm, est=float(np.linalg.norm(L_r @ U_r)) / np.sqrt(p),
-                bound=np.sqrt(n - k) * nrm, normUest=scale * nrm, maxUest=scale * mx)
+                bound=np.sqrt(n - k) * nrm, u_fro=nrm, u_max=mx)
 
 
 def certificate(A, J, X, Omega_post) -> float:

@@ -3,6 +3,7 @@ central finite differences of its loss (a check independent of the chain-rule
 formulas), the loss at a hand-computable point, and one Adam step against the
 closed form of the first step."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -56,6 +57,38 @@ def test_first_adam_step_closed_form():
     np.testing.assert_allclose(p1[:mlp.TRAINABLE] - p[:mlp.TRAINABLE], -1e-3 * g / (np.abs(g) + 1e-8),
                                rtol=1e-9)
     np.testing.assert_array_equal(p1[mlp.TRAINABLE:], p[mlp.TRAINABLE:])
+
+
+def test_adam_moments_are_bias_corrected_weighted_averages():
+    """Kingma and Ba's bias correction turns the moment recursions into
+    normalised exponential averages: after steps 1..t with gradients g_1..g_t,
+    m_hat_t = sum_i b1^(t-i) g_i / sum_i b1^(t-i) and likewise v_hat_t with
+    b2 and g_i^2.  Three different gradients make both betas show: swapped or
+    wrong betas, a missing bias correction or a stale moment all change the
+    result.  Weights at b1 = 0.9, b2 = 0.999 written out: (0.81, 0.9, 1) / 2.71
+    and (0.998001, 0.999, 1) / 2.997001 at step 3."""
+    rng = np.random.default_rng(6)
+    p = random_params(7)
+    G = [rng.standard_normal(mlp.TRAINABLE) for _ in range(3)]
+    lr = 2e-3
+    m1 = np.zeros(mlp.TRAINABLE)
+    m2 = np.zeros(mlp.TRAINABLE)
+    q = p.copy()
+    expect = p[:mlp.TRAINABLE].copy()
+    w1 = {1: [1.0], 2: [0.9, 1.0], 3: [0.81, 0.9, 1.0]}
+    w2 = {1: [1.0], 2: [0.999, 1.0], 3: [0.998001, 0.999, 1.0]}
+    for t in (1, 2, 3):
+        q, m1, m2 = mlp.adam(q, G[t - 1], m1, m2, t, lr)
+        mh = sum(w * g for w, g in zip(w1[t], G[:t])) / sum(w1[t])
+        vh = sum(w * g * g for w, g in zip(w2[t], G[:t])) / sum(w2[t])
+        expect -= lr * mh / (np.sqrt(vh) + 1e-8)
+    np.testing.assert_allclose(q[:mlp.TRAINABLE], expect, rtol=0, atol=1e-12)
+    assert sum(w1[3]) == pytest.approx(2.71) and sum(w2[3]) == pytest.approx(2.997001)
+    # the betas matter: the same three steps with them swapped land elsewhere
+    r, a, c = p.copy(), np.zeros(mlp.TRAINABLE), np.zeros(mlp.TRAINABLE)
+    for t in (1, 2, 3):
+        r, a, c = mlp.adam(r, G[t - 1], a, c, t, lr, b1=0.999, b2=0.9)
+    assert np.abs(r[:mlp.TRAINABLE] - expect).max() > 1e-4
 
 
 def test_features_definition():

@@ -57,6 +57,11 @@ WORKLOADS = {
     # slices of A, Omega on the grid 2^-11)
     "adaptive_poly_f64emu": (40000, 10000, "poly", {}, "f64emu", 1e-10, 64),
     "adaptive_step_f64emu": (40000, 10000, "step", {"rank": 600, "floor": 1e-9}, "f64emu", 1e-10, 64),
+    # the sparse-sign sketch of Sec. 5.1 (zeta = 8) on the same FP64 matrix: the gather-add
+    # reads A once per pass in FP64; the Schur GEMM and block update stay on the tensor cores
+    "adaptive_poly_f64emu_sparse": (40000, 10000, "poly", {}, "f64emu", 1e-10, 64),
+    "adaptive_poly_f64_sparse": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
+    "small_poly_f64emu_sparse": (16384, 4096, "poly", {}, "f64emu", 1e-10, 64),
     # reduced sizes of the same families, for profiler captures (inputs still > L2)
     "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
@@ -252,9 +257,12 @@ def cpu_oracle_sample(A_host_f64, name, seed, rounds=6):
     _, _, _, _, dt, tol, b = WORKLOADS[name]
     m, n = A_host_f64.shape  # the workload's size on a GPU machine; reduced without a GPU
     kmax = rounds * b
-    Om = oracle.gaussian_rows(seed, 0, (rounds + 1) * b, m)
-    if dt == "f64emu":
-        Om = on_grid(Om)
+    if is_sparse(name):
+        Om = oracle.sparse_sign_rows(seed, 0, rounds + 1, b, m)
+    else:
+        Om = oracle.gaussian_rows(seed, 0, (rounds + 1) * b, m)
+        if dt == "f64emu":
+            Om = on_grid(Om)
     t0 = time.perf_counter()
     r = oracle.id_adaptive(A_host_f64, Om, b, tol * 1.0, kmax=kmax)
     dt_s = time.perf_counter() - t0
@@ -368,9 +376,16 @@ def config_dict(name, res):
             "bf16": "BF16 A and Omega, tensor-core sketch with FP32 accumulation, FP32 LU and X, FP64 norms",
             "fp8": "FP8 E4M3 A with power-of-two FP32 scales per 128-row block (quantised from the BF16 matrix), "
                    "E4M3 Omega, tcgen05 kind::f8f6f4 sketch with FP32 accumulation, FP32 LU and X, FP64 norms"}[dt]
+    if is_sparse(name):
+        prec = ("FP64 A, LU and X; sparse-sign gather-add sketch in FP64" +
+                ("; FP64-accurate Schur GEMM and block update on the BF16 tensor cores (7 exact 8-bit digit slices "
+                 "per operand)" if dt == "f64emu" else "; FP64 SIMT Schur GEMM and block update"))
     c = {"workload": name, "m": m, "n": n, "spectrum": spec, "block": b, "rel_tol": tol,
-         "precision": prec, "omega": "Philox4x64-10 Gaussian, generated on the device"
-                                     + (", rounded to the grid 2^-11" if dt == "f64emu" else ""),
+         "precision": prec,
+         "omega": ("sparse sign (Sec. 5.1), zeta = 8 nonzeros +-sqrt(b/8) per column of each block, Philox4x64-10 "
+                   "counters, generated on the device; the sketch is a gather-add in A's precision"
+                   if is_sparse(name) else "Philox4x64-10 Gaussian, generated on the device"
+                   + (", rounded to the grid 2^-11" if dt == "f64emu" else "")),
          "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * el / 1e9),
          "parallelism": "replicas (one ID per GPU)"}
     if res is not None:
@@ -378,27 +393,41 @@ def config_dict(name, res):
     return c
 
 
-def make_batch(name, device, seed=2310_09417 + 3):
-    """The 4096 kernel blocks of the batched workload (column-major CUDA tensors)."""
+def make_batch(name, device, seed=2310_09417 + 3, rank=0, world=1):
+    """The kernel blocks of the batched workload (column-major CUDA tensors).  With
+    world > 1 the batch holds count * world blocks of the same tree, and this rank
+    builds only its share of a size-balanced assignment (greedy LPT on the sketch
+    cost 2 m n (k + b), k estimated as min(m, n, 64)): every rank runs about
+    `count` blocks, with no collective on the data path.  Returns (blocks, info)."""
     import torch
 
+    from paper_2310_09417_gb300 import shard
     from paper_2310_09417_gb300 import workloads as W
-    npts, count, kind, kw, dt, _, _ = WORKLOADS[name]
-    pts, leaves, pairs = W.kernel_block_pairs(npts, count, seed, leaf_max=kw["leaf_max"], size_min=64)
+    npts, count, kind, kw, dt, _, b = WORKLOADS[name]
+    total = count * world
+    pts, leaves, pairs = W.kernel_block_pairs(npts, total, seed, leaf_max=kw["leaf_max"], size_min=64)
+    info = {"blocks_total": len(pairs)}
+    if world > 1:
+        costs = [shard.problem_cost(len(leaves[a]), len(leaves[c]), min(len(leaves[a]), len(leaves[c]), 64), b)
+                 for a, c in pairs]
+        parts = shard.assign(costs, world)
+        info.update({"blocks_this_rank": len(parts[rank]), "load_imbalance": shard.imbalance(costs, parts),
+                     "assignment": "greedy LPT on 2 m n (min(m, n, 64) + b)"})
+        pairs = [pairs[i] for i in parts[rank]]
     P = torch.from_numpy(pts).to(device)
     idx = [torch.from_numpy(l).to(device) for l in leaves]
     dtype = torch.float64 if dt == "f64" else torch.float32
     h2 = kw["h"] ** 2
     As = []
-    for a, b in pairs:
-        d2 = torch.cdist(P[idx[b]], P[idx[a]]) ** 2  # n x m row-major == m x n column-major
+    for a, c in pairs:
+        d2 = torch.cdist(P[idx[c]], P[idx[a]]) ** 2  # n x m row-major == m x n column-major
         As.append(torch.exp(-d2 / h2).to(dtype).t())
     torch.cuda.synchronize()
-    return As
+    return As, info
 
 
 def measure_batched(B, name, dev, steps, warmup, seed, *, e2e=True, cpu_baseline=False, errors=False,
-                    max_over_ranks=None, barrier=None):
+                    max_over_ranks=None, barrier=None, rank=0, world=1):
     """One persistent launch per step over the whole batch of kernel blocks.
     Returns the form's measurements (ms per step, GFLOP/s, roofline, e2e, the
     ranks, and with `errors` each block's relative error evaluated in FP64)."""
@@ -407,7 +436,7 @@ def measure_batched(B, name, dev, steps, warmup, seed, *, e2e=True, cpu_baseline
     max_over_ranks = max_over_ranks or (lambda x: x)
     barrier = barrier or (lambda: None)
     npts, count, kind, kw, dt, tol, b = WORKLOADS[name]
-    As = make_batch(name, dev)
+    As, shard_info = make_batch(name, dev, rank=rank, world=world)
     xdt = torch.float64 if dt == "f64" else torch.float32
     outs = [(torch.empty(min(A.shape), dtype=torch.int64, device=dev),
              torch.empty((A.shape[1], min(A.shape)), dtype=xdt, device=dev)) for A in As]
@@ -450,7 +479,7 @@ def measure_batched(B, name, dev, steps, warmup, seed, *, e2e=True, cpu_baseline
                                                          else "GB300 FP64 rate 1.25 TFLOP/s")},
            "result": {"k_mean": sum(ks) / len(ks), "k_max": max(ks), "k_min": min(ks),
                       "statuses": sorted(set(r.status for r in res)), "batch_gb": round(nbytes / 1e9, 2),
-                      "ids_per_s": len(As) / (ms * 1e-3)},
+                      "ids_per_s": len(As) / (ms * 1e-3), "shard": shard_info},
            "gpu_launches": 2 * steps, "clocks": clk.summary()}
     if errors:
         # each block's ||A - A(:,J)X||_F / ||A||_F evaluated in FP64 (harness check, not timed)
@@ -524,7 +553,7 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
     seed = 2310_09417 + 100 * rank
     r = measure_batched(B, name, dev, args.steps, args.warmup, seed, e2e=not args.no_e2e,
                         cpu_baseline=rank == 0 and world == 1 and not args.no_cpu_baseline,
-                        max_over_ranks=max_over_ranks, barrier=barrier)
+                        max_over_ranks=max_over_ranks, barrier=barrier, rank=rank, world=world)
     # whole job: the work of every rank (replicas with their own seeds) over the slowest rank's time
     flops_all = sum_over_ranks(r["flops"])
     value = flops_all / (r["ms_per_step"] * 1e-3) / 1e9
@@ -533,6 +562,9 @@ def run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
     if rank == 0:
         cfg = config_dict(name, None)
         cfg.update({k: r["result"][k] for k in ("k_mean", "k_max", "k_min", "batch_gb")})
+        if world > 1:
+            cfg["parallelism"] = ("sharded: %d blocks over %d ranks by a size-balanced assignment, no collective on "
+                                  "the data path" % (r["result"]["shard"]["blocks_total"], world))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL.get(WORKLOADS[name][4], "f64"),
@@ -570,51 +602,83 @@ DTYPE_LABEL = {
 }
 
 
-def sketch_roofline(name, m, n, b, passes, sk_ms, sk_launches):
+def sketch_roofline(name, m, n, b, passes, blocks, sk_ms, sk_launches):
     """Roofline of the dominant kernel, the sketch (+ its split-K reduction), from the
-    library's per-phase CUDA events on the launching stream.  `achieved` counts the
-    method's own bytes (or flops) per pass: A read once in its storage precision,
-    one Omega block, the sketch block written."""
+    library's per-phase CUDA events on the launching stream.  The method's own work
+    per ID: A read once per pass in its storage precision, plus one Omega block
+    and one sketch block per block of rows (bytes), and 2 m n rows multiply-adds
+    (flops; on the digit-sliced paths every FP64 / FP32 product is 14 / 6 BF16
+    digit products).  The bound is the larger of bytes / HBM bandwidth and tensor
+    flops / tensor peak; frac = that time / the measured time.  A pass that
+    sketches many blocks (the predictor) moves from the HBM to the tensor bound."""
     dt = WORKLOADS[name][4]
-    hbm = {"peak": PEAKS["hbm_gbs"], "unit": "GB/s", "bound": "hbm",
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if dt == "bf16":
-        byts = (2.0 * m * n + 2.0 * b * m + 4.0 * n * b) * passes
-        r = dict(hbm, kernel="k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce")
-    elif dt == "fp8":
-        nbs = (m + 127) // 128
-        byts = (1.0 * m * n + 4.0 * nbs * n + 1.0 * b * m + 4.0 * n * b) * passes
-        r = dict(hbm, kernel="k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + split-K reduce")
-    elif dt == "f32emu":
-        # the method's bytes: A in FP32 (4 mn) per pass; the kernel streams its 3 BF16
-        # digit slices (6 mn) instead, plus a once-per-call slicing of A
-        byts = (4.0 * m * n + 4.0 * b * m + 4.0 * n * b) * passes
-        kp = (m + 63) // 64 * 64
-        stream = (6.0 * kp * n + 16.0 * b * kp + 4.0 * n * b) * passes + 10.0 * m * n
-        r = dict(hbm, kernel="k_sketch_f32emu (tcgen05 + TMA, exact digit slices) + Omega slicing + split-K reduce",
-                 stream_bytes=stream, frac_of_stream=stream / (sk_ms * 1e-3) / 1e9 / PEAKS["hbm_gbs"])
-    elif dt == "f64emu":
-        # the method's bytes: A in FP64 (8 mn) per pass; the kernel streams its 7 BF16
-        # digit slices (14 mn) instead, plus a once-per-call slicing of A (30 mn)
-        byts = (8.0 * m * n + 8.0 * b * m + 8.0 * n * b) * passes
-        mp = (m + 7) // 8 * 8
-        stream = (14.0 * mp * n + 4.0 * b * mp + 8.0 * n * b) * passes + 30.0 * m * n
-        r = dict(hbm, kernel="k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K reduce + digit "
-                             "preparation", stream_bytes=stream,
-                 frac_of_stream=stream / (sk_ms * 1e-3) / 1e9 / PEAKS["hbm_gbs"])
-    else:
-        fl = 2.0 * m * n * b * passes
-        achieved = fl / (sk_ms * 1e-3) / 1e12
+    rows = blocks * b
+    t = sk_ms * 1e-3
+    if is_sparse(name):
+        esz = {"f64": 8, "f64emu": 8, "f32": 4, "f32emu": 4, "bf16": 2}[dt]
+        # A once per pass, the codes of the pass's blocks (zeta bytes per column of A
+        # and block), the sketch block written
+        byts = esz * m * n * passes + 8.0 * m * rows / b + esz * n * rows
+        achieved = byts / t / 1e9
+        return {"bound": "hbm", "kernel": "k_sparse_sketch (sparse-sign gather-add, zeta = 8) + k_sparse_pattern "
+                "+ split-K reduce", "achieved": achieved, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / PEAKS["hbm_gbs"], "traffic": PROFILED_TRAFFIC.get(name),
+                "algorithmic_bytes_per_step": byts, "sketch_launches_per_step": sk_launches,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if dt in ("f64", "f32"):
+        fl = 2.0 * m * n * rows
+        achieved = fl / t / 1e12
         peak = ALU_PEAK_TFLOPS[dt]
         return {"bound": "alu", "kernel": "k_sgemm_gather (sketch Y = Omega A, %s FMA) + split-K reduce" % dt,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": PROFILED_TRAFFIC.get(name), "sketch_launches_per_step": sk_launches,
                 "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == "f32"
                                                  else "GB300 FP64 rate 1.25 TFLOP/s")}
-    achieved = byts / (sk_ms * 1e-3) / 1e9
-    r.update({"achieved": achieved, "frac": achieved / r["peak"], "traffic": PROFILED_TRAFFIC.get(name),
-              "algorithmic_bytes_per_step": byts, "sketch_launches_per_step": sk_launches})
+    bf16_peak = PEAKS.get("bf16_tflops_sustained", PEAKS["bf16_tflops"])
+    extra = {}
+    if dt == "bf16":
+        byts = 2.0 * m * n * passes + (2.0 * m + 4.0 * n) * rows
+        tfl, tpeak = 2.0 * m * n * rows, bf16_peak
+        kern = "k_sketch_tc_bf16 (tcgen05 + TMA) + split-K reduce"
+    elif dt == "fp8":
+        nbs = (m + 127) // 128
+        byts = (1.0 * m * n + 4.0 * nbs * n) * passes + (1.0 * m + 4.0 * n) * rows
+        tfl, tpeak = 2.0 * m * n * rows, 2.0 * bf16_peak
+        kern = "k_sketch_tc_fp8 (tcgen05 kind::f8f6f4 + TMA, block scales) + split-K reduce"
+    elif dt == "f32emu":
+        byts = 4.0 * m * n * passes + (4.0 * m + 4.0 * n) * rows
+        tfl, tpeak = 6 * 2.0 * m * n * rows, bf16_peak
+        kp = (m + 63) // 64 * 64
+        stream = 6.0 * kp * n * passes + (16.0 * kp + 4.0 * n) * rows + 10.0 * m * n
+        extra = {"stream_bytes": stream, "frac_of_stream": stream / t / 1e9 / PEAKS["hbm_gbs"]}
+        kern = "k_sketch_f32emu (tcgen05 + TMA, exact digit slices) + Omega slicing + split-K reduce"
+    else:  # f64emu
+        byts = 8.0 * m * n * passes + (8.0 * m + 8.0 * n) * rows
+        tfl, tpeak = 14 * 2.0 * m * n * rows, bf16_peak
+        mp = (m + 7) // 8 * 8
+        stream = 14.0 * mp * n * passes + (4.0 * mp + 8.0 * n) * rows + 30.0 * m * n
+        extra = {"stream_bytes": stream, "frac_of_stream": stream / t / 1e9 / PEAKS["hbm_gbs"],
+                 "note": "frac counts the method's 8 bytes per element of A per pass; the kernel streams 14 "
+                         "(seven BF16 digit slices), see stream_bytes"}
+        kern = "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K reduce + digit preparation"
+    t_hbm = byts / (PEAKS["hbm_gbs"] * 1e9)
+    t_tc = tfl / (tpeak * 1e12)
+    if t_hbm >= t_tc:
+        r = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        r = {"bound": "tensor", "achieved": tfl / t / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)%s"
+                            % (" x 2, the nominal FP8 : BF16 ratio" if dt == "fp8" else "")}
+    r.update({"kernel": kern, "frac": max(t_hbm, t_tc) / t, "frac_hbm": t_hbm / t, "frac_tensor": t_tc / t,
+              "traffic": PROFILED_TRAFFIC.get(name), "algorithmic_bytes_per_step": byts,
+              "tensor_flops_per_step": tfl, "sketch_launches_per_step": sk_launches}, **extra)
     return r
+
+
+def is_sparse(name):
+    """Workloads sketched with the sparse-sign matrix (Sec. 5.1) instead of Gaussian rows."""
+    return name.endswith("_sparse")
 
 
 def sampled_rel_error(A, J, X, norm_A, rows=4096, seed=5):
@@ -651,8 +715,9 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
     sprec = {"f64emu": B.F64_EMU, "f32emu": B.F32_EMU}.get(dt)
     J = torch.empty(kmax, dtype=torch.int64, device=dev)
     Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
+    okind = B.OMEGA_SPARSE_SIGN if is_sparse(name) else B.OMEGA_GAUSSIAN
     opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
-                   omega=None, profile=True, sketch_prec=sprec)
+                   omega=None, profile=True, sketch_prec=sprec, omega_kind=okind)
     if predictor is not None:
         opts.predictor = predictor.data_ptr()
         opts.max_pass_rows = max_pass_rows
@@ -662,7 +727,7 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
     def step(profile=True, pivots=False):
         return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
                              workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec, pivots=pivots,
-                             predictor=predictor, max_pass_rows=max_pass_rows)
+                             predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind)
 
     for _ in range(max(warmup, 1)):
         res = step()
@@ -683,7 +748,10 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
     res = results[-1]
     flops = algorithmic_flops(m, n, res.k, b)
     sk_ms = sum(r.phase_ms["sketch"] for r in results) / steps
-    roof = sketch_roofline(name, m, n, b, res.passes, sk_ms, res.phase_launches["sketch"])
+    # blocks of sketch rows the ID used: one per round plus the first (a seeded pass may
+    # draw a few more that go unused; they are not counted)
+    blocks = max(res.passes, res.rounds + 1)
+    roof = sketch_roofline(name, m, n, b, res.passes, blocks, sk_ms, res.phase_launches["sketch"])
     tot = max(1e-9, sum(res.phase_ms.values()))
     roof.update({"phase_ms_per_step": {k: round(v, 3) for k, v in res.phase_ms.items()},
                  "phase_share": {k: round(v / tot, 4) for k, v in res.phase_ms.items()},
@@ -725,7 +793,7 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
                 S_dev.copy_(S_host, non_blocking=True)
             r = B.id_adaptive(A_in, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
                               workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec,
-                              predictor=predictor, max_pass_rows=max_pass_rows)
+                              predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind)
             kk = r.k
             X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
             J_host[:kk].copy_(J[:kk], non_blocking=True)

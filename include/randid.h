@@ -139,7 +139,22 @@ typedef struct {
      Modes 1 and 2 add n x k_max multipliers (lu_prec) to the workspace, and with
      lu_prec F32 the FP64 solve's k_max x k_max and n x k_max FP64 buffers. */
   int x_solve_f64;
+  /* The sketching matrix the library generates (omega = NULL):
+       ID_OMEGA_GAUSSIAN    N(0,1) rows (Philox4x64-10 + Box-Muller, see id_gaussian_rows);
+       ID_OMEGA_SPARSE_SIGN the sparse-sign matrix of Sec. 5.1: every column of every
+                            b-row block holds zeta entries +-sqrt(b/zeta) at distinct
+                            rows (see id_sparse_sign_rows), so the sketch is a
+                            gather-add that reads A once per pass, in A's own
+                            precision (FP32 sums for BF16).  Built for A F64, F32 and
+                            BF16; with sketch_prec F64_EMU / F32_EMU the gather-add
+                            replaces the digit-sliced sketch and the tensor-core
+                            Schur GEMM and block update remain.  b <= 128. */
+  int omega_kind;
+  int64_t zeta;   /* nonzeros per column of a sparse-sign block, 1 <= zeta <= b; 0 = 8 */
 } id_opts;
+
+#define ID_OMEGA_GAUSSIAN 0
+#define ID_OMEGA_SPARSE_SIGN 1
 
 /* kappa_1(L1) above which x_solve_f64 = 1 re-solves an FP32 X in FP64 (2^12). */
 #define ID_COND_SWITCH 4096.0
@@ -232,6 +247,78 @@ int id_cur_workspace_size(const id_matrix* A, int64_t k, size_t* bytes);
 int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, void* W,
                 int64_t ldw, void* ws, size_t ws_bytes, void* stream);
 
+/* A-posteriori certificate of a column ID (the certificate Remark 1 points to,
+   Sec. 3.2; its square is unbiased by Sec. 4.2):
+     E_post = || Omega' A - (Omega' A)(:,J) X ||_F / sqrt(q)
+   with q fresh Gaussian rows Omega' drawn after J was fixed.  A: any input the
+   sketch supports, with sketch_prec as for id_sketch (F64 / F64_EMU for F64 A,
+   F32 / F32_EMU for F32 A, BF16, FP8_E4M3 with block scales).  J: DEVICE int64[k]
+   (an entry outside [0, n) returns -2).  X: DEVICE, k x n column-major (ldx >= k),
+   FP64 for F64 A and FP32 otherwise (the X an ID of this library returns).
+   Omega': omega = NULL draws rows [row0, row0 + q) of the Philox generator keyed
+   by `seed` (pass a seed, or rows, the ID did not use); else omega is DEVICE,
+   row-major q x m (row stride ld_omega >= m) in the sketch's input type.
+   est: HOST out.  ws: id_certificate_workspace_size bytes, 256-aligned.
+   Synchronises the stream. */
+int id_certificate_workspace_size(const id_matrix* A, int64_t k, int64_t q, id_dtype sketch_prec, size_t* bytes);
+int id_certificate(const id_matrix* A, const int64_t* J, const void* X, int64_t ldx, int64_t k, int64_t q,
+                   id_dtype sketch_prec, uint64_t seed, int64_t row0, const void* omega, int64_t ld_omega,
+                   double* est, void* ws, size_t ws_bytes, void* stream);
+
+/* The residual block U_r of Remark 1 (Sec. 3.2), column form: the fixed-rank
+   ID of rank k from l = k + p sketch rows (as id_fixed_rank, results in out),
+   then LUPP of the transposed sketch continued for p more steps, so that
+   P Y^T = [L1; L2 L_r][U1 U2; 0 U_r] with U_r the trailing p x p block.
+   U_r: DEVICE out, p x p column-major (ldu >= p), lu_prec, zero below the
+   diagonal.  J_extra: optional DEVICE out, int64[p], the columns of A picked by
+   the p extra pivots.  stats (HOST out): u_fro = ||U_r||_F, u_max = max|U_r(i,j)|,
+   est = ||L_r U_r||_F / sqrt(p) (the Schur estimate of Eq. errSch for rank k),
+   bound = sqrt(n-k) ||U_r||_F (the remark's bound, from |L_r| <= 1).  Eq. normUest
+   and Eq. maxUest multiply u_fro and u_max by (4 log k / k) sqrt(n-k); the paper
+   supports that factor only with a figure, so it is left to the caller.
+   Requires 1 <= p <= 128 and k + p <= min(m, n).  ws: id_workspace_size(A, opts,
+   k + p) bytes.  Argument codes: A -1, k -2, p -3, opts -4, ws/ws_bytes
+   ID_ERR_WORKSPACE, out -7, U_r/ldu -8, stats -11. */
+typedef struct {
+  double u_fro, u_max, est, bound;
+} id_ur_stats;
+int id_ur_estimates(const id_matrix* A, int64_t k, int64_t p, const id_opts* opts, void* ws, size_t ws_bytes,
+                    id_result* out, void* U_r, int64_t ldu, int64_t* J_extra, id_ur_stats* stats, void* stream);
+
+/* The stable interpolation matrix of a column skeleton (Eq. sID in column form,
+   Sec. 2.2; the stable-ID error of Sec. 5.1): X = A(:,J)^+ A, the least-squares
+   coefficients of every column of A on the skeleton columns, through a
+   Householder QR of C = A(:,J) = Q R on the device (LAPACK dgeqrf's reflectors,
+   panels of 32 columns): X = R^{-1} Q^T A.  ||A - A(:,J) X||_F is the stable
+   ID error, at most the ID's.  A: F64 or F32 (computed in A's precision).
+   J: DEVICE int64[k] (an entry outside [0, n) returns -2).  X: DEVICE out,
+   k x n column-major (ldx >= k), A's dtype.  ws: id_stable_x_workspace_size
+   bytes (2 m k + 2 k n elements and the QR's scratch), 256-aligned.
+   Synchronises the stream. */
+int id_stable_x_workspace_size(const id_matrix* A, int64_t k, size_t* bytes);
+int id_stable_x(const id_matrix* A, const int64_t* J, int64_t k, void* X, int64_t ldx, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* The middle factor of a CUR or two-sided ID from row skeletons I and column
+   skeletons J (Sec. 2.2.1; Sec. 3.1 derives I by LUPP of A(:,J), which
+   cur_from_id computes):
+     middle_kind ID_CUR_PSEUDOINVERSE  U = C^+ A R^+ with C = A(:,J), R = A(I,:),
+                                       the Frobenius-optimal middle factor of CUR,
+                                       through Householder QRs of C and R^T:
+                                       U = Rc^{-1} (Qc^T A Qr) Rr^{-T};
+     middle_kind ID_CUR_INVERSE        U = A(I,J)^{-1} (the two-sided ID's middle
+                                       matrix inverted: C U R interpolates A on the
+                                       rows I and the columns J), through a QR of
+                                       A(I,J).
+   A: F64 or F32.  I, J: DEVICE int64[k] (entries outside A return -2).  U: DEVICE
+   out, k x k column-major (ldu >= k), A's dtype.  ws: cur_middle_workspace_size
+   bytes, 256-aligned.  Synchronises the stream. */
+#define ID_CUR_PSEUDOINVERSE 0
+#define ID_CUR_INVERSE 1
+int cur_middle_workspace_size(const id_matrix* A, int64_t k, int middle_kind, size_t* bytes);
+int cur_middle(const id_matrix* A, const int64_t* I, const int64_t* J, int64_t k, void* U, int64_t ldu,
+               int middle_kind, void* ws, size_t ws_bytes, void* stream);
+
 /* Rows [row0, row0+rows) of the Gaussian sketching matrix (row-major, row
    stride ld >= m, dtype F64, F32, BF16 or FP8_E4M3): entry (i, r) is a standard
    normal from Philox4x64-10 (Salmon et al. 2011) keyed (seed, 0) at counter
@@ -242,6 +329,27 @@ int cur_from_id(const id_matrix* A, const int64_t* J, int64_t k, int64_t* I, voi
    Synchronises the stream. */
 int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype,
                      void* out, int64_t ld, void* stream);
+
+/* Blocks t0 .. t0+blocks-1 of the sparse-sign sketching matrix (Sec. 5.1,
+   "Sparse Sign"; zeta = 8 in the paper) as dense rows: block t0+q occupies rows
+   q*b .. q*b+b-1 of out (DEVICE, row-major, row stride ld >= m, dtype F64 or F32).
+   Column i of block t holds zeta nonzeros +-sqrt(b/zeta) at distinct rows:
+   the words u_0, u_1, ... are Philox4x64-10 (Salmon et al. 2011) keyed (seed, 1)
+   at counters (i, t, c, 0), four words per counter; a partial Fisher-Yates
+   shuffle of (0..b-1) puts nonzero j at row p[j] after swapping p[j] with
+   p[j + ((u_j >> 32) (b - j)) >> 32], negative when u_j is odd.  The scale makes
+   E[Omega^T Omega] = b I, as for N(0,1) rows, so the estimator keeps its scale.
+   Requires 1 <= zeta <= b <= 128.  Synchronises the stream. */
+int id_sparse_sign_rows(uint64_t seed, int64_t t0, int64_t blocks, int64_t b, int64_t m, int64_t zeta,
+                        id_dtype dtype, void* out, int64_t ld, void* stream);
+
+/* The sparse-sign sketch alone: G = (Omega A)^T for rows [t0*b, t0*b + rows) of
+   the sparse-sign matrix above (n x rows, row-major, row stride ldg >= rows; FP64
+   for F64 A, FP32 for F32 and BF16 A), summed in a fixed order (deterministic).
+   ws: id_sparse_sketch_workspace_size bytes, 256-aligned. */
+int id_sparse_sketch_workspace_size(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, size_t* bytes);
+int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows, int64_t b, int64_t zeta, void* G,
+                     int64_t ldg, void* ws, size_t ws_bytes, void* stream);
 
 /* FP8 storage of a matrix for the FP8 sketch: A (F64, F32 or BF16, column-major)
    -> Q (E4M3 bytes, column-major, ld ldq >= m) and one FP32 scale per 128-row

@@ -298,6 +298,14 @@ def cur_middle(A, I, J) -> np.ndarray:
     return np.linalg.pinv(A[:, J]) @ A @ np.linalg.pinv(A[I, :])  # library pseudo-inverses as steps
 
 
+def cur_inverse_middle(A, I, J) -> np.ndarray:
+    """The middle factor U = A(I,J)^{-1} (Sec. 2.2.1: the two-sided ID's A(I,J),
+    inverted), for which C U R with C = A(:,J), R = A(I,:) reproduces A on the
+    rows I and on the columns J."""
+    A = _colmajor(A)
+    return np.linalg.inv(A[np.ix_(np.asarray(I, dtype=np.int64), np.asarray(J, dtype=np.int64))])
+
+
 def two_sided_residual(A, I, J, W, X) -> float:
     """||A - W A(I,J) X||_F, the two-sided ID error (Sec. 2.2.1)."""
     A = _colmajor(A)

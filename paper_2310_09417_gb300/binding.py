@@ -25,6 +25,10 @@ F64, F32, BF16, FP8_E4M3, F64_EMU, F32_EMU = 0, 1, 2, 3, 4, 5
 OK, WARN_TOL_NOT_MET, WARN_ZERO_PIVOT = 0, 1, 2
 ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = -101, -102, -103, -104, -105
 PHASES = ("omega", "sketch", "schur", "lu", "update", "other")
+# id_opts.omega_kind
+OMEGA_GAUSSIAN, OMEGA_SPARSE_SIGN = 0, 1
+# cur_middle's middle_kind
+CUR_PSEUDOINVERSE, CUR_INVERSE = 0, 1
 
 _TORCH_TO_ID = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 if hasattr(torch, "float8_e4m3fn"):
@@ -42,7 +46,7 @@ class IdOpts(C.Structure):
                 ("k0", C.c_int64), ("blocks_per_pass", C.c_int64), ("seed", C.c_uint64),
                 ("omega", C.c_void_p), ("ld_omega", C.c_int64), ("omega_rows", C.c_int64),
                 ("profile", C.c_int), ("predictor", C.c_void_p), ("max_pass_rows", C.c_int64),
-                ("x_solve_f64", C.c_int)]
+                ("x_solve_f64", C.c_int), ("omega_kind", C.c_int), ("zeta", C.c_int64)]
 
 
 class IdResult(C.Structure):
@@ -90,10 +94,24 @@ def load():
     lib.id_status_string.restype = C.c_char_p
     lib.id_quantize_fp8.argtypes = [P, P, i64, P, C.c_int, P]
     lib.id_fixed_rank_noalloc.argtypes = [P, i64, i64, P, P, P]
+    lib.id_certificate_workspace_size.argtypes = [P, i64, i64, C.c_int, C.POINTER(C.c_size_t)]
+    lib.id_certificate.argtypes = [P, P, P, i64, i64, i64, C.c_int, u64, i64, P, i64, C.POINTER(C.c_double), P,
+                                   C.c_size_t, P]
+    lib.id_ur_estimates.argtypes = [P, i64, i64, P, P, C.c_size_t, P, P, i64, P, P, P]
+    lib.id_stable_x_workspace_size.argtypes = [P, i64, C.POINTER(C.c_size_t)]
+    lib.id_stable_x.argtypes = [P, P, i64, P, i64, P, C.c_size_t, P]
+    lib.cur_middle_workspace_size.argtypes = [P, i64, C.c_int, C.POINTER(C.c_size_t)]
+    lib.cur_middle.argtypes = [P, P, P, i64, P, i64, C.c_int, P, C.c_size_t, P]
+    lib.id_sparse_sign_rows.argtypes = [u64, i64, i64, i64, i64, i64, C.c_int, P, i64, P]
+    lib.id_sparse_sketch_workspace_size.argtypes = [P, i64, i64, i64, C.POINTER(C.c_size_t)]
+    lib.id_sparse_sketch.argtypes = [P, u64, i64, i64, i64, i64, P, i64, P, C.c_size_t, P]
     lib.id_selftest_timeout.argtypes = [C.c_int, P, C.c_size_t, P]
     for f in ("id_workspace_size", "id_fixed_rank", "id_adaptive", "id_batched_workspace_size",
               "id_batched", "cur_from_id", "id_gaussian_rows", "id_sketch_workspace_size", "id_sketch",
-              "id_quantize_fp8", "id_fixed_rank_noalloc", "id_selftest_timeout"):
+              "id_quantize_fp8", "id_fixed_rank_noalloc", "id_selftest_timeout", "id_certificate_workspace_size",
+              "id_certificate", "id_ur_estimates", "id_sparse_sign_rows", "id_sparse_sketch_workspace_size",
+              "id_sparse_sketch", "id_stable_x_workspace_size", "id_stable_x", "cur_middle_workspace_size",
+              "cur_middle"):
         getattr(lib, f).restype = C.c_int
     # every entry point must have its C signature declared: an undeclared one would
     # pass 64-bit pointers as C ints
@@ -153,6 +171,10 @@ class IDResult:
     phase_launches: dict
     cond_L1: float = 0.0     # kappa_1(L1) when x_solve_f64 was requested
     x_f64: int = 0           # 1 if X was re-solved in FP64
+
+
+class IdUrStats(C.Structure):
+    _fields_ = [("u_fro", C.c_double), ("u_max", C.c_double), ("est", C.c_double), ("bound", C.c_double)]
 
 
 def colmajor(t: torch.Tensor) -> torch.Tensor:
@@ -233,7 +255,7 @@ def _matrix(A) -> IdMatrix:
 
 
 def _opts(A, *, block, tol, relative, k_max, k0, blocks_per_pass, seed, omega, profile,
-          sketch_prec=None, lu_prec=None) -> IdOpts:
+          sketch_prec=None, lu_prec=None, omega_kind=OMEGA_GAUSSIAN, zeta=0) -> IdOpts:
     dt = _TORCH_TO_ID[A.dtype]
     o = IdOpts()
     o.sketch_prec = dt if sketch_prec is None else sketch_prec
@@ -252,6 +274,8 @@ def _opts(A, *, block, tol, relative, k_max, k0, blocks_per_pass, seed, omega, p
         o.ld_omega = omega.stride(0)
         o.omega_rows = omega.shape[0]
     o.profile = 1 if profile else 0
+    o.omega_kind = omega_kind
+    o.zeta = zeta
     return o
 
 
@@ -322,12 +346,15 @@ def _result(res: IdResult, J, Xbuf, k, n, status, trace_buf, piv) -> IDResult:
 def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int = 0,
                   omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                   stream=None, workspace: torch.Tensor | None = None,
-                  sketch_prec: int | None = None, x_solve_f64: int = 0) -> IDResult:
+                  sketch_prec: int | None = None, x_solve_f64: int = 0, omega_kind: int = OMEGA_GAUSSIAN,
+                  zeta: int = 0) -> IDResult:
     """randLUPP fixed-rank column ID (Sec. 3.1): J (k), X (k x n), estimate from l - k rows.
-    sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit slicing."""
+    sketch_prec=F64_EMU (FP64 A only): the sketch on the tensor cores by digit slicing.
+    omega_kind=OMEGA_SPARSE_SIGN: the generated sketching matrix is sparse sign (Sec. 5.1)."""
     m, n = A.shape
     opts = _opts(A, block=block, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1,
-                 seed=seed, omega=omega, profile=profile, sketch_prec=sketch_prec)
+                 seed=seed, omega=omega, profile=profile, sketch_prec=sketch_prec, omega_kind=omega_kind,
+                 zeta=zeta)
     opts.x_solve_f64 = x_solve_f64
     ws = _workspace(workspace_size(A, opts, l), A.device, workspace)
     J = torch.empty(k, dtype=torch.int64, device=A.device)
@@ -349,7 +376,8 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
                 omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                 trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
                 out: tuple | None = None, predictor: torch.Tensor | None = None,
-                max_pass_rows: int = 0, sketch_prec: int | None = None, x_solve_f64: int = 0) -> IDResult:
+                max_pass_rows: int = 0, sketch_prec: int | None = None, x_solve_f64: int = 0,
+                omega_kind: int = OMEGA_GAUSSIAN, zeta: int = 0) -> IDResult:
     """randLUPPadap column ID (Algorithm 1).  `out` = (J, Xbuf) reuses output buffers
     (J int64 [k_max], Xbuf (n, k_max) row-major == X column-major).  `predictor`:
     FP32 CUDA tensor of id_mlp_param_count() parameters; it sets how many blocks
@@ -362,7 +390,7 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
     kmax = min(m, n) if not k_max else min(k_max, m, n)
     opts = _opts(A, block=block, tol=tol, relative=relative, k_max=kmax, k0=k0,
                  blocks_per_pass=blocks_per_pass, seed=seed, omega=omega, profile=profile,
-                 sketch_prec=sketch_prec)
+                 sketch_prec=sketch_prec, omega_kind=omega_kind, zeta=zeta)
     opts.x_solve_f64 = x_solve_f64
     if predictor is not None:
         if not predictor.is_cuda or predictor.dtype != torch.float32 or predictor.numel() != mlp_param_count():
@@ -583,3 +611,149 @@ def cur_from_id(A: torch.Tensor, J: torch.Tensor, *, stream=None,
     if rc < 0:
         raise IDError(rc, "cur_from_id")
     return I, W
+
+
+# ---------------------------------------------------------------- after the ID
+def certificate(A, J: torch.Tensor, X: torch.Tensor, q: int, *, seed: int = 0, row0: int = 0,
+                omega: torch.Tensor | None = None, sketch_prec: int | None = None, stream=None,
+                workspace: torch.Tensor | None = None) -> float:
+    """A-posteriori estimate ||Omega' A - (Omega' A)(:,J) X||_F / sqrt(q) of a column
+    ID's error from q fresh Gaussian rows (rows [row0, row0+q) of the generator
+    `seed`, or the caller's omega, q x m row-major in the sketch's input type).
+    X: k x n (column-major, e.g. an IDResult's X), FP64 for FP64 A, else FP32."""
+    m, n = A.shape
+    k = J.numel()
+    prec = _TORCH_TO_ID[A.dtype] if sketch_prec is None else sketch_prec
+    xdt = torch.float64 if A.dtype == torch.float64 else torch.float32
+    if (X.dim() != 2 or X.shape[0] != k or X.shape[1] != n or X.dtype != xdt or X.device != A.device
+            or X.stride(0) != 1 or X.stride(1) < k):
+        raise ValueError("X must be a column-major %s (%d x %d) on %s" % (xdt, k, n, A.device))
+    _check_tensor(J, "J", A.device, torch.int64, k)
+    ld_om = 0
+    om_ptr = None
+    if omega is not None:
+        if omega.device != A.device or omega.dim() != 2 or omega.shape != (q, m) or omega.stride(1) != 1:
+            raise ValueError("omega must be a row-major q x m tensor on A's device")
+        om_ptr, ld_om = omega.data_ptr(), omega.stride(0)
+    nb = C.c_size_t(0)
+    rc = _call(A.device, "id_certificate_workspace_size", C.byref(_matrix(A)), k, q, prec, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_certificate_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    est = C.c_double(0.0)
+    rc = _call(A.device, "id_certificate", C.byref(_matrix(A)), J.data_ptr(), X.data_ptr(), X.stride(1), k, q, prec,
+               seed & 0xFFFFFFFFFFFFFFFF, row0, om_ptr, ld_om, C.byref(est), ws.data_ptr(), ws.numel(),
+               _stream(stream, A.device))
+    if rc != 0:
+        raise IDError(rc, "id_certificate")
+    return float(est.value)
+
+
+@dataclasses.dataclass
+class URResult:
+    id: IDResult             # the rank-k fixed-rank ID
+    U_r: torch.Tensor        # p x p (upper triangular), lu precision
+    J_extra: torch.Tensor    # int64 [p], the columns the p extra pivots pick
+    u_fro: float             # ||U_r||_F
+    u_max: float             # max |U_r(i,j)|
+    est: float               # ||L_r U_r||_F / sqrt(p)
+    bound: float             # sqrt(n - k) ||U_r||_F
+
+
+def ur_estimates(A, k: int, p: int, *, block: int = 64, seed: int = 0, omega: torch.Tensor | None = None,
+                 sketch_prec: int | None = None, stream=None, workspace: torch.Tensor | None = None) -> URResult:
+    """Remark 1: the rank-k ID from k + p sketch rows and the trailing p x p block U_r
+    of the LUPP continued for p more steps."""
+    m, n = A.shape
+    opts = _opts(A, block=block, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1, seed=seed,
+                 omega=omega, profile=False, sketch_prec=sketch_prec)
+    ws = _workspace(workspace_size(A, opts, k + p), A.device, workspace)
+    xdt = torch.float64 if opts.lu_prec == F64 else torch.float32
+    J = torch.empty(k, dtype=torch.int64, device=A.device)
+    Xbuf = torch.empty((n, k), dtype=xdt, device=A.device)
+    U = torch.zeros((p, p), dtype=xdt, device=A.device)  # column-major: U[j, c] = U_r(c, j)
+    Jx = torch.empty(p, dtype=torch.int64, device=A.device)
+    res = IdResult()
+    res.J, res.X, res.ldx = J.data_ptr(), Xbuf.data_ptr(), k
+    stats = IdUrStats()
+    rc = _call(A.device, "id_ur_estimates", C.byref(_matrix(A)), k, p, C.byref(opts), ws.data_ptr(), ws.numel(),
+               C.byref(res), U.data_ptr(), p, Jx.data_ptr(), C.byref(stats), _stream(stream, A.device))
+    if rc < 0:
+        raise IDError(rc, "id_ur_estimates")
+    return URResult(id=_result(res, J, Xbuf, k, n, rc, None, None), U_r=U.t(), J_extra=Jx, u_fro=stats.u_fro,
+                    u_max=stats.u_max, est=stats.est, bound=stats.bound)
+
+
+# ---------------------------------------------------------------- sparse sign
+def sparse_sign_rows(seed: int, t0: int, blocks: int, b: int, m: int, zeta: int = 8, dtype=torch.float64,
+                     device="cuda", stream=None) -> torch.Tensor:
+    """Blocks t0 .. t0+blocks-1 of the sparse-sign sketching matrix as dense rows
+    ((blocks*b) x m): zeta entries +-sqrt(b/zeta) per column of each block."""
+    if dtype not in (torch.float64, torch.float32):
+        raise ValueError("sparse_sign_rows: dtype float64 or float32")
+    out = torch.empty((blocks * b, m), dtype=dtype, device=device)
+    rc = _call(out.device, "id_sparse_sign_rows", seed & 0xFFFFFFFFFFFFFFFF, t0, blocks, b, m, zeta,
+               _TORCH_TO_ID[dtype], out.data_ptr(), m, _stream(stream, out.device))
+    if rc != 0:
+        raise IDError(rc, "id_sparse_sign_rows")
+    return out
+
+
+def sparse_sketch(A, rows: int, b: int, *, seed: int = 0, t0: int = 0, zeta: int = 8, stream=None,
+                  workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """G = (Omega A)^T (n x rows) for rows [t0*b, t0*b + rows) of the sparse-sign matrix:
+    the gather-add sketch alone (FP64 for FP64 A, FP32 for FP32 and BF16 A)."""
+    m, n = A.shape
+    nb = C.c_size_t(0)
+    rc = _call(A.device, "id_sparse_sketch_workspace_size", C.byref(_matrix(A)), rows, b, zeta, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_sparse_sketch_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    G = torch.empty((n, rows), dtype=torch.float64 if A.dtype == torch.float64 else torch.float32, device=A.device)
+    rc = _call(A.device, "id_sparse_sketch", C.byref(_matrix(A)), seed & 0xFFFFFFFFFFFFFFFF, t0, rows, b, zeta,
+               G.data_ptr(), G.stride(0), ws.data_ptr(), ws.numel(), _stream(stream, A.device))
+    if rc != 0:
+        raise IDError(rc, "id_sparse_sketch")
+    return G
+
+
+# ---------------------------------------------------------------- stable X and CUR
+def stable_x(A, J: torch.Tensor, *, stream=None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """X = A(:,J)^+ A (k x n, column-major view), by a Householder QR of A(:,J) on
+    the device: the stable interpolation matrix (Eq. sID in column form)."""
+    m, n = A.shape
+    k = J.numel()
+    _check_tensor(J, "J", A.device, torch.int64, k)
+    nb = C.c_size_t(0)
+    rc = _call(A.device, "id_stable_x_workspace_size", C.byref(_matrix(A)), k, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "id_stable_x_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    Xb = torch.empty((n, k), dtype=A.dtype, device=A.device)  # X column-major, ld k
+    rc = _call(A.device, "id_stable_x", C.byref(_matrix(A)), J.data_ptr(), k, Xb.data_ptr(), k, ws.data_ptr(),
+               ws.numel(), _stream(stream, A.device))
+    if rc != 0:
+        raise IDError(rc, "id_stable_x")
+    return Xb.t()
+
+
+def cur_middle(A, I: torch.Tensor, J: torch.Tensor, kind: int = CUR_PSEUDOINVERSE, *, stream=None,
+               workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """The k x k middle factor: C^+ A R^+ (CUR_PSEUDOINVERSE, C = A(:,J), R = A(I,:))
+    or A(I,J)^{-1} (CUR_INVERSE).  Returns U (column-major view)."""
+    k = J.numel()
+    if I.numel() != k:
+        raise ValueError("I and J need the same length")
+    _check_tensor(I, "I", A.device, torch.int64, k)
+    _check_tensor(J, "J", A.device, torch.int64, k)
+    nb = C.c_size_t(0)
+    rc = _call(A.device, "cur_middle_workspace_size", C.byref(_matrix(A)), k, kind, C.byref(nb))
+    if rc != 0:
+        raise IDError(rc, "cur_middle_workspace_size")
+    ws = _workspace(int(nb.value), A.device, workspace)
+    Ub = torch.empty((k, k), dtype=A.dtype, device=A.device)  # U column-major, ld k
+    rc = _call(A.device, "cur_middle", C.byref(_matrix(A)), I.data_ptr(), J.data_ptr(), k, Ub.data_ptr(), k, kind,
+               ws.data_ptr(), ws.numel(), _stream(stream, A.device))
+    if rc != 0:
+        raise IDError(rc, "cur_middle")
+    return Ub.t()

@@ -103,6 +103,8 @@ struct Plan {
   size_t off_f32a = 0, off_f32ae = 0, off_f32w = 0, off_f32we = 0, off_f32rmax = 0;
   bool schur_tc = false;
   bool update_tc = false;
+  bool sparse = false;  // sparse-sign sketching matrix (Sec. 5.1), generated
+  int64_t zeta = 8;
   bool keep_l = false, f64_solve = false;
 };
 
@@ -148,6 +150,16 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   if (b < 1 || b > kMaxBlock) return kBadOpts;
   if (!(o->tol >= 0.0) || o->k_max < 0 || o->k0 < 0 || o->blocks_per_pass < 0) return kBadOpts;
   if (o->x_solve_f64 < 0 || o->x_solve_f64 > 2) return kBadOpts;
+  if (o->omega_kind != ID_OMEGA_GAUSSIAN && o->omega_kind != ID_OMEGA_SPARSE_SIGN) return kBadOpts;
+  p->sparse = o->omega_kind == ID_OMEGA_SPARSE_SIGN && o->omega == nullptr;
+  if (p->sparse) {
+    // the gather-add sketch reads A in its own type: FP64, FP32 or BF16 input (on the
+    // digit-sliced paths only their tensor-core Schur GEMM and block update remain)
+    if (path == 8) return ID_ERR_UNSUPPORTED;
+    const int64_t z = o->zeta == 0 ? 8 : o->zeta;
+    if (z < 1 || z > b || b > kSparseMaxB) return kBadOpts;
+    p->zeta = z;
+  }
   p->m = A->m;
   p->n = A->n;
   p->b = b;
@@ -192,7 +204,8 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // one split-K count for every pass (see Engine::splits_for): that of a pass of
   // one block (adaptive) or of the l rows (fixed rank)
   const int64_t unit = l > 0 ? l : b;
-  const int s1 = path == 16   ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
+  const int s1 = p->sparse ? sparse_splits(p->m, p->n, p->sms)
+                 : path == 16 ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
                  : path == 8  ? tc_fp8_effective_splits(p->m, tc_fp8_splits(p->m, p->n, unit, p->sms))
                  : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
                  : path == 33 ? sketch_f32emu_splits(p->m, p->n, unit, p->sms)
@@ -216,8 +229,10 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   };
   p->off_state = take(256);
   // path 65 keeps two digit planes of Omega, also for a caller Omega (rounded to its grid)
+  // (sparse sign: the zeta codes of every column of the pass's blocks)
   p->off_omega = take(path == 65 ? 2 * (size_t)rows_max * p->ldw * p->wsz
-                                 : (p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0));
+                                 : (p->sparse ? (size_t)cdiv(rows_max, b) * p->m * p->zeta
+                                              : (p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0)));
   p->off_G = take((size_t)p->n * rows_max * e);
   p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * e : 0);
   p->off_S = take((size_t)p->n * p->wmax * e);
@@ -238,8 +253,8 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_normp = take((size_t)p->nparts * 8);
   p->off_trace = take((size_t)p->max_rounds * 8);
   // path 65: the 8 digit slices of A and its column exponents
-  p->off_digits = take(path == 65 ? f64emu_digit_bytes(p->m, p->n) : 0);
-  p->off_colexp = take(path == 65 ? (size_t)p->n * 4 : 0);
+  p->off_digits = take(path == 65 && !p->sparse ? f64emu_digit_bytes(p->m, p->n) : 0);
+  p->off_colexp = take(path == 65 && !p->sparse ? (size_t)p->n * 4 : 0);
   // the Schur complement and the block update on the tensor cores: 7 digits for the
   // FP64-emulated path, 3 for every FP32 LU (panels and blocks of width <= 64)
   const bool emu7 = path == 65, emu3 = e == 4;
@@ -254,11 +269,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // the small late pivot rows, so FP32 LUs keep the SIMT GEMM there.
   p->schur_tc = emu7;  // used for panels of width <= 64
   // path 33: digits of A (n rows of length m) and of each pass's Omega rows
-  p->off_f32a = take(path == 33 ? sketch_f32emu_digit_bytes(p->n, p->m) : 0);
-  p->off_f32ae = take(path == 33 ? (size_t)p->n * 4 : 0);
-  p->off_f32w = take(path == 33 ? sketch_f32emu_digit_bytes(rows_max, p->m) : 0);
-  p->off_f32we = take(path == 33 ? (size_t)rows_max * 4 : 0);
-  p->off_f32rmax = take(path == 33 ? (size_t)rows_max * 8 : 0);
+  const bool slice32 = path == 33 && !p->sparse;
+  p->off_f32a = take(slice32 ? sketch_f32emu_digit_bytes(p->n, p->m) : 0);
+  p->off_f32ae = take(slice32 ? (size_t)p->n * 4 : 0);
+  p->off_f32w = take(slice32 ? sketch_f32emu_digit_bytes(rows_max, p->m) : 0);
+  p->off_f32we = take(slice32 ? (size_t)rows_max * 4 : 0);
+  p->off_f32rmax = take(slice32 ? (size_t)rows_max * 8 : 0);
   p->off_adig = take(p->schur_tc ? gemm_f64emu_digit_bytes(p->n, kcap) : 0);
   p->off_aexp = take(p->schur_tc ? (size_t)p->n * 4 : 0);
   p->off_bdig = take(p->schur_tc ? gemm_f64emu_digit_bytes(64, kcap) : 0);
@@ -418,6 +434,30 @@ class Engine {
     return finish(p_.k);
   }
 
+  // Remark 1 (Sec. 3.2): the rank-k fixed-rank ID from l = k + p sketch rows, then
+  // the LUPP of the p extra rows' Schur complement S ((n-k) x p) continued for p
+  // steps.  S = L_r U_r; U_r is read from the pivot rows, and the columns of the
+  // extra pivots (the skeleton's continuation) go to Jx.
+  int run_ur(int64_t p, T* U, int64_t ldu, int64_t* Jx, double* stats) {
+    const int status = run_fixed();
+    if (status < 0) return status;
+    const int64_t na = p_.n - p_.k;
+    RID_TRY(tbegin(ID_PHASE_LU));
+    // the fixed-rank estimate set the stop flag; the extra steps must run
+    RID_TRY(cuda(cudaMemsetAsync(&st_->done, 0, sizeof(int32_t), s_)));
+    PanelCfg cfg = panel_config<T>((int)na, (int)p, p_.maxg);
+    RID_TRY(cuda(panel_lupp<T>(cfg, (int)na, (int)p, (int)p, panel_par_, S_, p_.wmax, piv_, pivmark_, pivdiag_,
+                               cand_v_, cand_i_, cand_rows_, st_, s_)));
+    panel_par_ ^= 1;
+    RID_TRY(cuda(ur_extract<T>((int)p, (int)na, S_, p_.wmax, piv_, act_[cur_], U, ldu, Jx, e2_, s_)));
+    RID_TRY(tend(2));
+    RID_TRY(cuda(cudaMemcpyAsync(stats, e2_, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_)));
+    RID_TRY(sync_state());
+    if (h_.err & kErrTimeout) return ID_ERR_TIMEOUT;
+    out_->launches = launches_;
+    return status;
+  }
+
   // LUPP of a given panel instead of a sketch: G (p_.n rows x p_.k columns) is
   // gathered from the columns J of `src` (m_src x n_src, ld_src), its rows are
   // pivoted for k steps, and the interpolation coefficients land in the X buffer.
@@ -491,13 +531,13 @@ class Engine {
     RID_TRY(tend(3));
     RID_TRY(sync_state());
     if (h_.err & kErrNonFinite) return ID_ERR_NONFINITE;
-    if (p_.path == 33) {  // digits of A's columns, once per call
+    if (p_.path == 33 && !p_.sparse) {  // digits of A's columns, once per call
       RID_TRY(tbegin(ID_PHASE_SKETCH));
       RID_TRY(cuda(sketch_f32emu_slice((int)p_.n, (int)p_.m, reinterpret_cast<const float*>(Araw_), lda_, f32a_, p_.n,
                                        f32ae_, nullptr, nullptr, s_)));
       RID_TRY(tend(1));
     }
-    if (p_.path == 65) {  // column exponents and digit slices of A, once per call
+    if (p_.path == 65 && !p_.sparse) {  // column exponents and digit slices of A, once per call
       RID_TRY(tbegin(ID_PHASE_SKETCH));
       RID_TRY(cuda(f64emu_prepare(reinterpret_cast<const double*>(Araw_), lda_, p_.m, p_.n, colexp_, digits_, s_)));
       RID_TRY(tend(2));
@@ -519,6 +559,7 @@ class Engine {
   // (k0, blocks_per_pass, the learned predictor) leaves J, X and k bit-identical.
   int splits_for(int64_t /*rows*/) {
     const int64_t unit = p_.l > 0 ? p_.l : p_.b;
+    if (p_.sparse) return sparse_splits(p_.m, p_.n, p_.sms);
     if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 8) return tc_fp8_effective_splits(p_.m, tc_fp8_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
@@ -528,6 +569,7 @@ class Engine {
   }
 
   int sketch(int64_t row0, int64_t rows, int splits) {
+    if (p_.sparse) return sketch_sparse(row0, rows, splits);
     if (p_.path == 16) return sketch_tc(row0, rows, splits);
     if (p_.path == 8) return sketch_fp8(row0, rows, splits);
     if (p_.path == 65) return sketch_emu(row0, rows, splits);
@@ -553,6 +595,36 @@ class Engine {
     RID_TRY(cuda(gemm_gather<T>((int)p_.n, (int)rows, (int)p_.m, splits, true, a, bop, kEpiStore, ep, done_, s_)));
     if (splits > 1)
       RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, (int64_t)p_.n * p_.ldg, Gpart_, G_, done_, s_)));
+    RID_TRY(tend(splits > 1 ? 2 : 1));
+    ++passes_;
+    return 0;
+  }
+
+  // Sparse-sign rows [row0, row0+rows) (Sec. 5.1): the zeta codes of each column of
+  // the pass's blocks, then the gather-add G = Omega A in A's own type (FP32 sums
+  // for BF16 A).
+  int sketch_sparse(int64_t row0, int64_t rows, int splits) {
+    const int64_t b = p_.b;
+    uint8_t* P = reinterpret_cast<uint8_t*>(omega_);
+    RID_TRY(tbegin(ID_PHASE_OMEGA));
+    RID_TRY(cuda(sparse_pattern(o_.seed, row0 / b, (int)cdiv(rows, b), (int)b, p_.m, (int)p_.zeta, P, done_, s_)));
+    RID_TRY(tend(1));
+    RID_TRY(tbegin(ID_PHASE_SKETCH));
+    T* out = splits > 1 ? Gpart_ : G_;
+    const int64_t zs = (int64_t)p_.n * p_.ldg;
+    if constexpr (std::is_same<T, float>::value) {
+      if (p_.path == 16)
+        RID_TRY(cuda(sparse_sketch<__nv_bfloat16, float>(p_.m, p_.n, static_cast<const __nv_bfloat16*>(Araw_), lda_, P,
+                                                         (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs, done_,
+                                                         s_)));
+      else
+        RID_TRY(cuda(sparse_sketch<float, float>(p_.m, p_.n, A_, lda_, P, (int)p_.zeta, (int)b, rows, splits, out,
+                                                 p_.ldg, zs, done_, s_)));
+    } else {
+      RID_TRY(cuda(sparse_sketch<T, T>(p_.m, p_.n, A_, lda_, P, (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs,
+                                       done_, s_)));
+    }
+    if (splits > 1) RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, zs, Gpart_, G_, done_, s_)));
     RID_TRY(tend(splits > 1 ? 2 : 1));
     ++passes_;
     return 0;
@@ -1030,6 +1102,25 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
   return ID_OK;
 }
 
+int id_sparse_sign_rows(uint64_t seed, int64_t t0, int64_t blocks, int64_t b, int64_t m, int64_t zeta,
+                        id_dtype dtype, void* out, int64_t ld, void* stream) {
+  if (t0 < 0) return -2;
+  if (blocks < 0 || blocks > ((int64_t)1 << 24)) return -3;
+  if (b < 1 || b > kSparseMaxB) return -4;
+  if (m < 1) return -5;
+  if (zeta < 1 || zeta > b) return -6;
+  if (dtype != ID_F64 && dtype != ID_F32) return -7;
+  if (out == nullptr) return -8;
+  if (ld < m) return -9;
+  if (blocks == 0) return ID_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dtype == ID_F64
+                      ? sparse_dense<double>(seed, t0, (int)blocks, (int)b, m, (int)zeta, static_cast<double*>(out), ld, s)
+                      : sparse_dense<float>(seed, t0, (int)blocks, (int)b, m, (int)zeta, static_cast<float*>(out), ld, s);
+  if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
+  return ID_OK;
+}
+
 int id_quantize_fp8(const id_matrix* A, void* Q, int64_t ldq, float* block_scale, int pow2, void* stream) {
   if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m ||
       (A->dtype != ID_F64 && A->dtype != ID_F32 && A->dtype != ID_BF16))
@@ -1085,25 +1176,20 @@ int id_sketch_workspace_size(const id_matrix* A, int64_t rows, id_dtype sketch_p
   return rc == -2 ? -2 : rc;
 }
 
-int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec, void* G,
-              int64_t ldg, void* ws, size_t ws_bytes, void* stream) {
-  int path = 0, splits = 1;
-  size_t need = 0;
-  int rc = sketch_plan(A, rows, sketch_prec, &path, &splits, &need);
-  if (rc != ID_OK) return rc == -2 ? -4 : rc;
-  if (omega == nullptr || ld_omega < A->m) return -2;
-  if (G == nullptr || ldg < rows) return -6;
-  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < need)
-    return ID_ERR_WORKSPACE;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
+// The sketch G = (omega A)^T (n x rows, row stride ldg) on path `path` with the
+// split-K count sketch_plan chose.  ws: the DevState (256 bytes), then the
+// partials and digit planes sketch_plan sized.  Returns the first launch error.
+cudaError_t run_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, int path, int splits,
+                       void* G, int64_t ldg, void* ws, cudaStream_t s) {
   DevState* st = static_cast<DevState*>(ws);
   void* part = static_cast<unsigned char*>(ws) + 256;
-  if (init_state(st, nullptr, nullptr, 0, s) != cudaSuccess) return ID_ERR_CUDA;
+  cudaError_t e0 = init_state(st, nullptr, nullptr, 0, s);
+  if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaSuccess;
   // split-K partials: row stride rows (what the workspace holds), reduced into G (row stride ldg)
   const int64_t zs = A->n * rows;
   if (path == 16) {
-    if (!tc_sketch_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
     e = tc_sketch_bf16(A->data, A->ld, A->m, A->n, omega, ld_omega, rows, out, splits > 1 ? rows : ldg, zs, splits,
                        st, nullptr, s);
@@ -1111,7 +1197,6 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
       e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
                                   static_cast<float*>(G), nullptr, s);
   } else if (path == 8) {
-    if (!tc_fp8_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
     float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
     e = tc_sketch_fp8(A->data, A->ld, A->m, A->n, A->block_scale, omega, ld_omega, rows, out, splits > 1 ? rows : ldg,
                       zs, splits, st, nullptr, s);
@@ -1171,12 +1256,267 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
       e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
                                   static_cast<float*>(G), nullptr, s);
   }
+  return e;
+}
+}  // namespace
+
+int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t rows, id_dtype sketch_prec, void* G,
+              int64_t ldg, void* ws, size_t ws_bytes, void* stream) {
+  int path = 0, splits = 1;
+  size_t need = 0;
+  int rc = sketch_plan(A, rows, sketch_prec, &path, &splits, &need);
+  if (rc != ID_OK) return rc == -2 ? -4 : rc;
+  if (omega == nullptr || ld_omega < A->m) return -2;
+  if (G == nullptr || ldg < rows) return -6;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < need)
+    return ID_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (path == 16 && !tc_sketch_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
+  if (path == 8 && !tc_fp8_supported(A->data, A->ld, omega, ld_omega)) return ID_ERR_UNSUPPORTED;
+  DevState* st = static_cast<DevState*>(ws);
+  cudaError_t e = run_sketch(A, omega, ld_omega, rows, path, splits, G, ldg, ws, s);
   if (e != cudaSuccess) return ID_ERR_CUDA;
   DevState h;
   if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return ID_ERR_CUDA;
   return (h.err & kErrTimeout) ? ID_ERR_TIMEOUT : ID_OK;
+}
+
+namespace {
+// Workspace of id_sparse_sketch: a DevState, the zeta codes of the blocks, the split-K partials.
+int sparse_sketch_plan(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, int* splits, size_t* off_parts,
+                       size_t* bytes) {
+  if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= ((int64_t)1 << 31) ||
+      A->n >= ((int64_t)1 << 30))
+    return -1;
+  if (A->dtype != ID_F64 && A->dtype != ID_F32 && A->dtype != ID_BF16) return ID_ERR_UNSUPPORTED;
+  if (rows < 1 || rows > ((int64_t)1 << 20)) return -2;
+  if (b < 1 || b > kSparseMaxB) return -3;
+  if (zeta < 1 || zeta > b) return -4;
+  *splits = sparse_splits(A->m, A->n, num_sms());
+  const size_t esz = A->dtype == ID_F64 ? 8 : 4;
+  *off_parts = 256 + align_up((size_t)cdiv(rows, b) * A->m * zeta);
+  *bytes = *off_parts + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  return ID_OK;
+}
+}  // namespace
+
+int id_sparse_sketch_workspace_size(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, size_t* bytes) {
+  if (bytes == nullptr) return -5;
+  int splits = 1;
+  size_t off = 0;
+  return sparse_sketch_plan(A, rows, b, zeta, &splits, &off, bytes);
+}
+
+int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows, int64_t b, int64_t zeta, void* G,
+                     int64_t ldg, void* ws, size_t ws_bytes, void* stream) {
+  int splits = 1;
+  size_t off = 0, need = 0;
+  const int rc = sparse_sketch_plan(A, rows, b, zeta, &splits, &off, &need);
+  if (rc != ID_OK) return rc == -2 ? -4 : (rc == -3 ? -5 : (rc == -4 ? -6 : rc));
+  if (t0 < 0) return -3;
+  if (G == nullptr || ldg < rows) return -7;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < need)
+    return ID_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  uint8_t* P = w + 256;
+  void* part = w + off;
+  const int64_t zs = A->n * rows;
+  cudaError_t e = sparse_pattern(seed, t0, (int)cdiv(rows, b), (int)b, A->m, (int)zeta, P, nullptr, s);
+  if (e == cudaSuccess) {
+    if (A->dtype == ID_F64) {
+      double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
+      e = sparse_sketch<double, double>(A->m, A->n, static_cast<const double*>(A->data), A->ld, P, (int)zeta, (int)b,
+                                        rows, splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
+      if (e == cudaSuccess && splits > 1)
+        e = splitk_reduce_ld<double>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<double*>(part),
+                                     static_cast<double*>(G), nullptr, s);
+    } else {
+      float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
+      if (A->dtype == ID_F32)
+        e = sparse_sketch<float, float>(A->m, A->n, static_cast<const float*>(A->data), A->ld, P, (int)zeta, (int)b,
+                                        rows, splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
+      else
+        e = sparse_sketch<__nv_bfloat16, float>(A->m, A->n, static_cast<const __nv_bfloat16*>(A->data), A->ld, P,
+                                                (int)zeta, (int)b, rows, splits, out, splits > 1 ? rows : ldg, zs,
+                                                nullptr, s);
+      if (e == cudaSuccess && splits > 1)
+        e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
+                                    static_cast<float*>(G), nullptr, s);
+    }
+  }
+  if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return ID_ERR_CUDA;
+  return ID_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Workspace of id_certificate: a DevState, the rows of Omega', the sketch's own
+// workspace (sketch_plan), G = (Omega' A)^T (n x q), the index lists, the split-K
+// partials of X^T G(J,:), the residual R = G - X^T G(J,:) and its sums of squares.
+struct CertPlan {
+  int path = 0, sk_splits = 1, nz = 1, nparts = 0;
+  size_t esz = 8, wsz = 8;  // bytes per element of G and X, of Omega'
+  int64_t ldo = 0;
+  size_t off_st = 0, off_omega = 0, off_sk = 0, off_G = 0, off_iota = 0, off_j32 = 0, off_P = 0, off_R = 0,
+         off_e2 = 0, total = 0;
+};
+
+int cert_plan(const id_matrix* A, int64_t k, int64_t q, id_dtype prec, CertPlan* c) {
+  size_t skb = 0;
+  const int rc = sketch_plan(A, q, prec, &c->path, &c->sk_splits, &skb);
+  if (rc == -2) return -6;
+  if (rc != ID_OK) return rc;
+  if (k < 1 || k > imin(A->m, A->n)) return -5;
+  const int sms = num_sms();
+  const bool f64 = c->path >= 64;
+  c->esz = f64 ? 8 : 4;
+  c->wsz = f64 ? 8 : (c->path == 16 ? 2 : (c->path == 8 ? 1 : 4));
+  c->ldo = c->path == 16 ? cdiv(A->m, 8) * 8 : (c->path == 8 ? cdiv(A->m, 16) * 16 : A->m);
+  const int want = f64 ? choose_splits_gather(A->n, q, k, sms, 8) : choose_splits_sgemm(A->n, q, k, sms, 32, 2);
+  c->nz = gemm_splits((int)k, want);
+  c->nparts = 2 * sms;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + (bytes == 0 ? 1 : bytes));
+    return at;
+  };
+  c->off_st = take(256);
+  c->off_omega = take((size_t)q * c->ldo * c->wsz);
+  c->off_sk = take(skb);
+  c->off_G = take((size_t)A->n * q * c->esz);
+  c->off_iota = take((size_t)A->n * 4);
+  c->off_j32 = take((size_t)k * 4);
+  c->off_P = take((size_t)c->nz * A->n * q * c->esz);
+  c->off_R = take((size_t)A->n * q * c->esz);
+  c->off_e2 = take((size_t)c->nparts * 8);
+  c->total = off;
+  return ID_OK;
+}
+
+// R = G - X^T G(J,:) (the residual of the ID on the fresh sample) and its squared
+// norm per block, then E = sqrt(sum / q).
+template <typename T>
+cudaError_t cert_residual(const CertPlan& c, int64_t n, int64_t k, int64_t q, const void* X, int64_t ldx,
+                          unsigned char* w, cudaStream_t s) {
+  const T* G = reinterpret_cast<const T*>(w + c.off_G);
+  const int32_t* iota = reinterpret_cast<const int32_t*>(w + c.off_iota);
+  const int32_t* j32 = reinterpret_cast<const int32_t*>(w + c.off_j32);
+  T* P = reinterpret_cast<T*>(w + c.off_P);
+  T* R = reinterpret_cast<T*>(w + c.off_R);
+  double* e2 = reinterpret_cast<double*>(w + c.off_e2);
+  DevState* st = reinterpret_cast<DevState*>(w + c.off_st);
+  Operand<T> a{static_cast<const T*>(X), ldx, nullptr, 0};
+  Operand<T> b{G, q, j32, 0};
+  EpiArgs<T> ep{P, q, n * q, nullptr, nullptr};
+  cudaError_t e = gemm_gather<T>((int)n, (int)q, (int)k, c.nz, false, a, b, kEpiStore, ep, nullptr, s);
+  if (e == cudaSuccess)
+    e = schur_finish<T>((int)n, (int)q, iota, G, q, 0, c.nz, n * q, P, R, q, e2, c.nparts, nullptr, s);
+  if (e == cudaSuccess) e = rid::decide(e2, c.nparts, (int)q, INFINITY, 0, 0, 0, nullptr, 0, st, s);
+  return e;
+}
+}  // namespace
+
+extern "C" {
+
+int id_certificate_workspace_size(const id_matrix* A, int64_t k, int64_t q, id_dtype sketch_prec, size_t* bytes) {
+  if (bytes == nullptr) return -5;
+  CertPlan c;
+  const int rc = cert_plan(A, k, q, sketch_prec, &c);
+  if (rc != ID_OK) return rc == -5 ? -2 : (rc == -6 ? -3 : (rc == -1 ? -1 : (rc == ID_ERR_UNSUPPORTED ? rc : -4)));
+  *bytes = c.total;
+  return ID_OK;
+}
+
+int id_certificate(const id_matrix* A, const int64_t* J, const void* X, int64_t ldx, int64_t k, int64_t q,
+                   id_dtype sketch_prec, uint64_t seed, int64_t row0, const void* omega, int64_t ld_omega,
+                   double* est, void* ws, size_t ws_bytes, void* stream) {
+  CertPlan c;
+  int rc = cert_plan(A, k, q, sketch_prec, &c);
+  if (rc == -6) return -6;
+  if (rc == -5) return -5;
+  if (rc != ID_OK) return rc == ID_ERR_UNSUPPORTED ? rc : (rc == -1 ? -1 : -7);
+  if (J == nullptr) return -2;
+  if (X == nullptr) return -3;
+  if (ldx < k) return -4;
+  if (omega == nullptr && row0 < 0) return -9;
+  if (omega != nullptr && ld_omega < A->m) return -11;
+  if (est == nullptr) return -12;
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < c.total)
+    return ID_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (omega != nullptr && c.path == 16 && !tc_sketch_supported(A->data, A->ld, omega, ld_omega))
+    return ID_ERR_UNSUPPORTED;
+  if (omega != nullptr && c.path == 8 && !tc_fp8_supported(A->data, A->ld, omega, ld_omega))
+    return ID_ERR_UNSUPPORTED;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  DevState* st = reinterpret_cast<DevState*>(w + c.off_st);
+  const int64_t m = A->m, n = A->n;
+  cudaError_t e = init_state(st, nullptr, nullptr, 0, s);
+  const void* Om = omega;
+  int64_t ldo = ld_omega;
+  if (e == cudaSuccess && omega == nullptr) {  // Omega' rows [row0, row0 + q) of the generator `seed`
+    void* buf = w + c.off_omega;
+    if (c.path >= 64)
+      e = gaussian_rows<double>(seed, row0, q, m, static_cast<double*>(buf), c.ldo, nullptr, s);
+    else if (c.path == 16)
+      e = gaussian_rows<__nv_bfloat16>(seed, row0, q, m, static_cast<__nv_bfloat16*>(buf), c.ldo, nullptr, s);
+    else if (c.path == 8)
+      e = gaussian_rows<__nv_fp8_e4m3>(seed, row0, q, m, static_cast<__nv_fp8_e4m3*>(buf), c.ldo, nullptr, s);
+    else
+      e = gaussian_rows<float>(seed, row0, q, m, static_cast<float*>(buf), c.ldo, nullptr, s);
+    Om = buf;
+    ldo = c.ldo;
+  }
+  if (e == cudaSuccess) e = run_sketch(A, Om, ldo, q, c.path, c.sk_splits, w + c.off_G, q, w + c.off_sk, s);
+  if (e == cudaSuccess) e = index32(J, k, n, reinterpret_cast<int32_t*>(w + c.off_j32), st, s);
+  if (e == cudaSuccess) e = iota32(reinterpret_cast<int32_t*>(w + c.off_iota), n, s);
+  if (e == cudaSuccess)
+    e = c.path >= 64 ? cert_residual<double>(c, n, k, q, X, ldx, w, s) : cert_residual<float>(c, n, k, q, X, ldx, w, s);
+  if (e != cudaSuccess) return ID_ERR_CUDA;
+  DevState h, hs;
+  if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&hs, w + c.off_sk, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ID_ERR_CUDA;
+  if ((h.err | hs.err) & kErrTimeout) return ID_ERR_TIMEOUT;
+  if (h.err & kErrBadIndex) return -2;
+  *est = h.est;
+  return ID_OK;
+}
+
+int id_ur_estimates(const id_matrix* A, int64_t k, int64_t p, const id_opts* opts, void* ws, size_t ws_bytes,
+                    id_result* out, void* U_r, int64_t ldu, int64_t* J_extra, id_ur_stats* stats, void* stream) {
+  if (p < 1 || p > kMaxBlock) return -3;
+  if (A != nullptr && (k < 1 || k + p > imin(A->m, A->n))) return k < 1 ? -2 : -3;
+  Plan pl;
+  int rc = make_plan(A, opts, k, k + p, &pl);
+  if (rc != ID_OK) return rc == kBadA ? -1 : (rc == kBadOpts ? -4 : (rc == kBadK ? -2 : (rc == kBadL ? -3 : rc)));
+  if (check_ws(pl, ws, ws_bytes) != ID_OK) return ID_ERR_WORKSPACE;
+  if (check_out(pl, out) != ID_OK) return -7;
+  if (U_r == nullptr || ldu < p) return -8;
+  if (stats == nullptr) return -11;
+  clear_out(out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double h[2] = {0.0, 0.0};
+  int st;
+  if (precision_path(A, opts) >= 64) {
+    Engine<double> e(pl, A, opts, ws, out, s);
+    st = e.run_ur(p, static_cast<double*>(U_r), ldu, J_extra, h);
+  } else {
+    Engine<float> e(pl, A, opts, ws, out, s);
+    st = e.run_ur(p, static_cast<float*>(U_r), ldu, J_extra, h);
+  }
+  if (st < 0) return st;
+  stats->u_fro = sqrt(h[0]);
+  stats->u_max = h[1];
+  stats->est = out->est_err;
+  stats->bound = sqrt((double)(A->n - k)) * stats->u_fro;
+  return st;
 }
 
 const char* id_status_string(int status) {

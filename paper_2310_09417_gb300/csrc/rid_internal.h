@@ -250,6 +250,33 @@ cudaError_t sketch_f32emu(int64_t m, int64_t n, int64_t rows, const void* adig, 
                           int64_t wrows, const int32_t* wexp, float* out, int64_t ldo, int64_t zstride, int splits,
                           DevState* st, const int32_t* done, cudaStream_t s);
 
+// ---- after the ID (rid_post.cu): index conversion for gathered operands, an
+// identity list, and U_r of Remark 1 from the factored extra rows.
+cudaError_t index32(const int64_t* J, int64_t k, int64_t n, int32_t* out, DevState* st, cudaStream_t s);
+cudaError_t iota32(int32_t* a, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t ur_extract(int p, int na, const T* S, int64_t lds, const int32_t* piv, const int32_t* act, T* U,
+                       int64_t ldu, int64_t* Jx, double* stats, cudaStream_t s);
+
+// ---- sparse-sign sketch (rid_sparse.cu; Sec. 5.1 "Sparse Sign").  Blocks of b <=
+// kSparseMaxB rows with zeta nonzeros +-sqrt(b/zeta) per column.  sparse_pattern
+// writes the zeta codes (row | sign << 7) of every column of `blocks` blocks from
+// block t0 on (blocks x m x zeta bytes); sparse_sketch forms split z of (Omega A)^T
+// (n x rows, row stride out_ld) in out[z] from those codes for rows = the pass's
+// rows (the last block may be cut short); sparse_dense writes the blocks as dense
+// rows (row-major, row stride ld).
+constexpr int kSparseMaxB = 128;
+int sparse_splits(int64_t m, int64_t n, int sms);
+cudaError_t sparse_pattern(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint8_t* P,
+                           const int32_t* done, cudaStream_t s);
+template <typename TA, typename TC>
+cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
+                          int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride, const int32_t* done,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t sparse_dense(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, T* out, int64_t ld,
+                         cudaStream_t s);
+
 // ---- the driver's cuTensorMapEncodeTiled (nullptr when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 

@@ -547,3 +547,21 @@ def test_sparse_sign_sketch_recovers_rank_k_and_certifies_without_bias(orc):
     rat = np.array([orc.certificate(A, r["J"], r["X"], orc.sparse_sign_rows(99, t, 1, b, m, 8)) ** 2 / e2
                     for t in range(400)])
     assert abs(rat.mean() - 1.0) < 5 * rat.std() / np.sqrt(rat.size)
+
+
+def test_cur_inverse_middle_interpolates_on_the_skeletons(orc):
+    """U = A(I,J)^{-1}: C U R agrees with A on the rows I and the columns J (to
+    rounding), and equals A exactly (to rounding) when A has rank k."""
+    m, n, k = 70, 55, 9
+    A = W.spectral_matrix(m, n, W.spectrum("geometric", n, per_decade=8.0), seed=71)
+    r = orc.id_fixed_rank(A, W.gaussian_omega(72, k + 4, m), k)
+    I, _ = orc.row_id_of_columns(A, r["J"])
+    U = orc.cur_inverse_middle(A, I, r["J"])
+    CUR = A[:, r["J"]] @ U @ A[I, :]
+    np.testing.assert_allclose(CUR[I, :], A[I, :], rtol=0, atol=1e-10 * np.abs(A).max())
+    np.testing.assert_allclose(CUR[:, r["J"]], A[:, r["J"]], rtol=0, atol=1e-10 * np.abs(A).max())
+    Ak, _, _ = W.low_rank(m, n, k, seed=73)
+    rk = orc.id_fixed_rank(Ak, W.gaussian_omega(74, k + 4, m), k)
+    Ik, _ = orc.row_id_of_columns(Ak, rk["J"])
+    Uk = orc.cur_inverse_middle(Ak, Ik, rk["J"])
+    np.testing.assert_allclose(Ak[:, rk["J"]] @ Uk @ Ak[Ik, :], Ak, rtol=0, atol=1e-9 * np.abs(Ak).max())

@@ -62,6 +62,8 @@ WORKLOADS = {
     "adaptive_poly_f64emu_sparse": (40000, 10000, "poly", {}, "f64emu", 1e-10, 64),
     "adaptive_poly_f64_sparse": (40000, 10000, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f64emu_sparse": (16384, 4096, "poly", {}, "f64emu", 1e-10, 64),
+    "adaptive_poly_f32_sparse": (40000, 10000, "poly", {}, "f32", 1e-6, 64),
+    "mixed_bf16_tol3e-2_sparse": (100000, 20000, "lowrank", {"rank": 1500, "noise": 1e-4}, "bf16", 3e-2, 64),
     # reduced sizes of the same families, for profiler captures (inputs still > L2)
     "small_poly_f64": (16384, 4096, "poly", {}, "f64", 1e-10, 64),
     "small_poly_f32": (16384, 4096, "poly", {}, "f32", 1e-6, 64),
@@ -655,12 +657,12 @@ def sketch_roofline(name, m, n, b, passes, blocks, sk_ms, sk_launches):
     else:  # f64emu
         byts = 8.0 * m * n * passes + (8.0 * m + 8.0 * n) * rows
         tfl, tpeak = 14 * 2.0 * m * n * rows, bf16_peak
-        mp = (m + 7) // 8 * 8
-        stream = 14.0 * mp * n * passes + (4.0 * mp + 8.0 * n) * rows + 30.0 * m * n
+        mp = (m + 15) // 16 * 16
+        stream = 7.0 * mp * n * passes + (4.0 * mp + 8.0 * n) * rows + 23.0 * m * n
         extra = {"stream_bytes": stream, "frac_of_stream": stream / t / 1e9 / PEAKS["hbm_gbs"],
-                 "note": "frac counts the method's 8 bytes per element of A per pass; the kernel streams 14 "
-                         "(seven BF16 digit slices), see stream_bytes"}
-        kern = "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K reduce + digit preparation"
+                 "note": "frac counts the method's 8 bytes per element of A per pass; the kernel streams 7 "
+                         "(seven int8 digit slices, widened to BF16 in shared memory), see stream_bytes"}
+        kern = "k_sketch_f64emu (tcgen05 + TMA, int8 digit slices widened in shared memory) + split-K reduce + digit preparation"
     t_hbm = byts / (PEAKS["hbm_gbs"] * 1e9)
     t_tc = tfl / (tpeak * 1e12)
     if t_hbm >= t_tc:

@@ -64,14 +64,15 @@ typedef enum {
   ID_FP8_E4M3 = 3,
   /* sketch_prec only, with F64 A and lu_prec F64: the sketch computed to FP64
      accuracy on the BF16 tensor cores by exact integer slicing.  A is split once
-     per call into 7 digit slices of 8 bits with per-column exponents (56 bits);
-     Omega is the Gaussian on the grid 2^-11 (|q| <= 16383), split into 2 digits;
-     every digit product is kept and summed exactly in FP32 over chunks of 512
-     and in int64 across chunks.  Entry error <= 2^-52 max_i|A_ij|
-     sum_r |Omega_cr|.  The Schur GEMM and the block update of X run on the
-     tensor cores the same way (7 digits of 8 bits per operand).  A caller omega
-     (F64) is rounded to the same grid.  Extra workspace: 14 bytes per element
-     of A plus 14 bytes per element of T(act, 0:k). */
+     per call into 7 signed 8-bit digit slices with per-column exponents (55
+     bits), stored as int8 and widened to BF16 in shared memory; Omega is the
+     Gaussian on the grid 2^-11 (|q| <= 16383), split into 2 digits; every digit
+     product is kept and summed exactly in FP32 over chunks of 512 and in int64
+     across chunks.  Entry error <= 2^-52 max_i|A_ij| sum_r |Omega_cr|.  The
+     Schur GEMM and the block update of X run on the tensor cores the same way
+     (7 digits of 8 bits per operand).  A caller omega (F64) is rounded to the
+     same grid.  Extra workspace: 7 bytes per element of A plus 14 bytes per
+     element of T(act, 0:k). */
   ID_F64_EMU = 4,
   /* sketch_prec only, with F32 A and lu_prec F32: the sketch on the BF16 tensor
      cores with A and Omega each split into 3 digits of 8 bits (per-column /
@@ -346,6 +347,10 @@ int id_sparse_sign_rows(uint64_t seed, int64_t t0, int64_t blocks, int64_t b, in
 /* The sparse-sign sketch alone: G = (Omega A)^T for rows [t0*b, t0*b + rows) of
    the sparse-sign matrix above (n x rows, row-major, row stride ldg >= rows; FP64
    for F64 A, FP32 for F32 and BF16 A), summed in a fixed order (deterministic).
+   F64 A is summed exactly: each column in 64-bit fixed point (error <= 2^-63
+   max|A(:,j)| per term), 128-bit integer sums, one rounding to FP64 and one for
+   the scale -- as accurate as an FP64 dot product or better.  BF16 A needs an
+   even leading dimension and a 4-byte aligned base (else ID_ERR_UNSUPPORTED).
    ws: id_sparse_sketch_workspace_size bytes, 256-aligned. */
 int id_sparse_sketch_workspace_size(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, size_t* bytes);
 int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows, int64_t b, int64_t zeta, void* G,

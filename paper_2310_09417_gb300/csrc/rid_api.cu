@@ -105,6 +105,7 @@ struct Plan {
   bool update_tc = false;
   bool sparse = false;  // sparse-sign sketching matrix (Sec. 5.1), generated
   int64_t zeta = 8;
+  size_t off_sfix = 0, off_scol = 0;  // FP64 A in 64-bit fixed point for the exact gather-add
   bool keep_l = false, f64_solve = false;
 };
 
@@ -253,6 +254,9 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   p->off_normp = take((size_t)p->nparts * 8);
   p->off_trace = take((size_t)p->max_rounds * 8);
   // path 65: the 8 digit slices of A and its column exponents
+  const bool sfix = p->sparse && (path == 64 || path == 65);
+  p->off_sfix = take(sfix ? (size_t)p->m * p->n * 8 : 0);
+  p->off_scol = take(sfix ? (size_t)p->n * 4 : 0);
   p->off_digits = take(path == 65 && !p->sparse ? f64emu_digit_bytes(p->m, p->n) : 0);
   p->off_colexp = take(path == 65 && !p->sparse ? (size_t)p->n * 4 : 0);
   // the Schur complement and the block update on the tensor cores: 7 digits for the
@@ -354,6 +358,8 @@ class Engine {
     f32w_ = w + p.off_f32w;
     f32we_ = reinterpret_cast<int32_t*>(w + p.off_f32we);
     f32rmax_ = reinterpret_cast<unsigned long long*>(w + p.off_f32rmax);
+    sfix_ = reinterpret_cast<long long*>(w + p.off_sfix);
+    sfix_col_ = reinterpret_cast<int32_t*>(w + p.off_scol);
     X_ = static_cast<T*>(out->X);
     ldx_ = out->ldx;
     done_ = &st_->done;
@@ -537,6 +543,12 @@ class Engine {
                                        f32ae_, nullptr, nullptr, s_)));
       RID_TRY(tend(1));
     }
+    if (p_.sparse && sizeof(T) == 8) {  // FP64 A in 64-bit fixed point, once per call
+      RID_TRY(tbegin(ID_PHASE_SKETCH));
+      RID_TRY(cuda(sparse_fixed_prepare(reinterpret_cast<const double*>(Araw_), lda_, p_.m, p_.n, sfix_col_,
+                                        sfix_, s_)));
+      RID_TRY(tend(2));
+    }
     if (p_.path == 65 && !p_.sparse) {  // column exponents and digit slices of A, once per call
       RID_TRY(tbegin(ID_PHASE_SKETCH));
       RID_TRY(cuda(f64emu_prepare(reinterpret_cast<const double*>(Araw_), lda_, p_.m, p_.n, colexp_, digits_, s_)));
@@ -620,9 +632,9 @@ class Engine {
       else
         RID_TRY(cuda(sparse_sketch<float, float>(p_.m, p_.n, A_, lda_, P, (int)p_.zeta, (int)b, rows, splits, out,
                                                  p_.ldg, zs, done_, s_)));
-    } else {
-      RID_TRY(cuda(sparse_sketch<T, T>(p_.m, p_.n, A_, lda_, P, (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs,
-                                       done_, s_)));
+    } else {  // exact integer sums of the fixed-point copy
+      RID_TRY(cuda(sparse_sketch_fixed(p_.m, p_.n, sfix_, sfix_col_, P, (int)p_.zeta, (int)b, rows, splits,
+                                       reinterpret_cast<double*>(out), p_.ldg, zs, done_, s_)));
     }
     if (splits > 1) RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, zs, Gpart_, G_, done_, s_)));
     RID_TRY(tend(splits > 1 ? 2 : 1));
@@ -910,6 +922,8 @@ class Engine {
   void *f32a_, *f32w_;  // path 33: digits of A and of the pass's Omega rows
   int32_t *f32ae_, *f32we_;
   unsigned long long* f32rmax_;
+  long long* sfix_;      // sparse sign with FP64 A: the fixed-point copy of A and its column exponents
+  int32_t* sfix_col_;
   const int32_t* done_;
   int64_t ldx_;
   int cur_ = 0;
@@ -1298,6 +1312,8 @@ int sparse_sketch_plan(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta
   const size_t esz = A->dtype == ID_F64 ? 8 : 4;
   *off_parts = 256 + align_up((size_t)cdiv(rows, b) * A->m * zeta);
   *bytes = *off_parts + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  if (A->dtype == ID_F64)  // the fixed-point copy of A and its column exponents follow
+    *bytes += align_up((size_t)A->m * A->n * 8) + align_up((size_t)A->n * 4);
   return ID_OK;
 }
 }  // namespace
@@ -1317,6 +1333,9 @@ int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows
   if (rc != ID_OK) return rc == -2 ? -4 : (rc == -3 ? -5 : (rc == -4 ? -6 : rc));
   if (t0 < 0) return -3;
   if (G == nullptr || ldg < rows) return -7;
+  // BF16 tiles are copied in element pairs: even leading dimension, 4-byte aligned base
+  if (A->dtype == ID_BF16 && ((A->ld & 1) != 0 || (reinterpret_cast<uintptr_t>(A->data) & 3) != 0))
+    return ID_ERR_UNSUPPORTED;
   if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 || ws_bytes < need)
     return ID_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1328,8 +1347,13 @@ int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows
   if (e == cudaSuccess) {
     if (A->dtype == ID_F64) {
       double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
-      e = sparse_sketch<double, double>(A->m, A->n, static_cast<const double*>(A->data), A->ld, P, (int)zeta, (int)b,
-                                        rows, splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
+      unsigned char* fx = w + off + (splits > 1 ? align_up((size_t)splits * A->n * rows * 8) : 0);
+      long long* F = reinterpret_cast<long long*>(fx);
+      int32_t* col = reinterpret_cast<int32_t*>(fx + align_up((size_t)A->m * A->n * 8));
+      e = sparse_fixed_prepare(static_cast<const double*>(A->data), A->ld, A->m, A->n, col, F, s);
+      if (e == cudaSuccess)
+        e = sparse_sketch_fixed(A->m, A->n, F, col, P, (int)zeta, (int)b, rows, splits, out,
+                                splits > 1 ? rows : ldg, zs, nullptr, s);
       if (e == cudaSuccess && splits > 1)
         e = splitk_reduce_ld<double>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<double*>(part),
                                      static_cast<double*>(G), nullptr, s);

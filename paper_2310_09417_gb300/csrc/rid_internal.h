@@ -276,6 +276,15 @@ cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const 
 template <typename T>
 cudaError_t sparse_dense(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, T* out, int64_t ld,
                          cudaStream_t s);
+// FP64 input: column exponents and the 64-bit fixed-point copy F (m x n, ld m) made
+// once per call, then exact 128-bit sums rounded once to FP64.
+cudaError_t sparse_fixed_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, long long* F,
+                                 cudaStream_t s);
+cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint8_t* P,
+                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld,
+                                int64_t zstride, const int32_t* done, cudaStream_t s);
+// e_j with |A(:, j)| < 2^e_j (0 for a zero column), by a reduction over each column.
+cudaError_t f64_colexp(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* E, cudaStream_t s);
 
 // ---- the driver's cuTensorMapEncodeTiled (nullptr when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();

@@ -18,11 +18,19 @@
 // r, and with which sign), and a warp per sketch row walks its mask in ascending
 // order with one lane per column of A -- a fixed summation order, no atomics on
 // the sums, and one read of A per pass.
+//
+// FP64 input is summed exactly in integers: GB300 issues about two FP64
+// instructions per clock per SM, and each element of A feeds zeta sums.  A is
+// converted once per call to 64-bit fixed point per column (F = round(A 2^(62-e))
+// for |A| < 2^e, an error of at most 2^-63 max|A(:,j)| per term), every entry of
+// the sketch is the exact 128-bit integer sum of +-F, and one conversion rounds
+// it to FP64 (then the scale sqrt(b/zeta), one more rounding).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "rid_internal.h"
+#include "rid_tc_common.cuh"
 
 namespace rid {
 
@@ -110,24 +118,100 @@ cudaError_t sparse_dense(uint64_t seed, int64_t t0, int blocks, int b, int64_t m
 __device__ __forceinline__ float load_as_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float load_as_f(const float* p) { return *p; }
 __device__ __forceinline__ double load_as_f(const double* p) { return *p; }
+__device__ __forceinline__ long long load_as_f(const long long* p) { return *p; }
+
+// The accumulator of an entry and its final value: FP32 sums for FP32 / BF16 input,
+// exact 128-bit integer sums of the fixed-point FP64 input.
+template <typename TS>
+struct SpAcc {
+  using type = TS;
+};
+template <>
+struct SpAcc<long long> {
+  using type = __int128;
+};
+template <typename TS>
+__device__ __forceinline__ typename SpAcc<TS>::type sp_add(typename SpAcc<TS>::type s, TS a, bool neg) {
+  return neg ? s - a : s + a;
+}
+template <typename TS, typename TO>
+__device__ __forceinline__ TO sp_final(typename SpAcc<TS>::type s, TO v, int ex) {
+  if constexpr (sizeof(TS) == 8) {
+    // s 2^ex: |s| < 2^62 times the terms (< 2^82), so s >> 32 fits 64 bits
+    const long long hi = (long long)(s >> 32);
+    const long long lo = (long long)(s & (__int128)0xFFFFFFFFll);
+    return tcx::fixed_to_double(hi, lo, ex) * v;
+  } else {
+    return s * v;
+  }
+}
+
+// F(i, j) = round(A(i, j) 2^(62 - e_j)) with |A(:, j)| < 2^e_j (column-major, ld m).
+__global__ void k_sparse_fixed(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                               const int32_t* __restrict__ colexp, long long* __restrict__ F) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    F[e] = tcx::fixed_of<8>(A[i + j * lda], colexp[j] + 1);
+  }
+}
+
+cudaError_t sparse_fixed_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, long long* F,
+                                 cudaStream_t s) {
+  cudaError_t e = f64_colexp(A, lda, m, n, colexp, s);
+  if (e != cudaSuccess) return e;
+  int64_t g = (m * n + 255) / 256;
+  if (g > 8192) g = 8192;
+  k_sparse_fixed<<<(int)g, 256, 0, s>>>(A, lda, m, n, colexp, F);
+  return cudaGetLastError();
+}
+
+// Asynchronous copy of one element (4 or 8 bytes) or a BF16 pair (4 bytes) into shared
+// memory; src_bytes < bytes zero-fills the rest (0: the whole element).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(tcx::smem_u32(dst)), "l"(src), "n"(BYTES),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float tile_value(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float tile_value(const float* p) { return *p; }
+__device__ __forceinline__ long long tile_value(const long long* p) { return *p; }
 
 // out[z][j][t*b + r] (row stride out_ld) = sqrt(b/zeta) * sum over the rows i of
 // split z with a code for sketch row r of block t: sign * A(i, j).  Grid: x over
 // 32-column tiles of A, y over groups of TG blocks, z over splits of the rows of A
-// (ktiles tiles of 256 rows each).  Warp w owns rows r = w + 8q (q < RPW) of each
-// block of its group; lane = column.  Sketch rows t*b + r >= rows (a last block
-// cut short) are not written.
-template <typename TA, typename TC, int RPW>
-__global__ void __launch_bounds__(kSpThreads, sizeof(TC) == 8 ? 2 : 3)
+// (ktiles tiles of 256 rows each).  Per tile (the next one already in flight by
+// cp.async into the other buffer):
+//   1. per-row bit masks of the tile rows that hit each sketch row of the group
+//      (word-major, so a warp's 32 tile rows spread over the banks);
+//   2. the codes sorted by sketch row into a CSR list, ascending tile row within a
+//      row (rank = popcount of the row's mask below the bit): a fixed order;
+//   3. warp w sums rows r = w + 8q of every block of the group, lane = column,
+//      four list entries at a time.
+// Sketch rows t*b + r >= rows (a last block cut short) are not written.
+template <typename TA, typename TS, typename TO, int RPW>
+__global__ void __launch_bounds__(kSpThreads, sizeof(TS) == 8 ? 1 : 2)
     k_sparse_sketch(int64_t m, int64_t n, const TA* __restrict__ A, int64_t lda, const uint8_t* __restrict__ P,
-                    int zeta, int b, int blocks, int64_t rows, int ktiles, TC* __restrict__ out, int64_t out_ld,
-                    int64_t zstride, TC v, const int32_t* done) {
-  constexpr int TG = 32 / RPW;  // blocks per CTA
+                    int zeta, int b, int blocks, int64_t rows, int ktiles, TO* __restrict__ out, int64_t out_ld,
+                    int64_t zstride, TO v, const int32_t* __restrict__ colexp, const int32_t* done) {
+  using TC = decltype(tile_value((const TS*)nullptr));
+  using Acc = typename SpAcc<TC>::type;
+  constexpr int TG = (sizeof(Acc) > 8 ? 16 : 32) / RPW;  // blocks per CTA
+  constexpr int NR = TG * 8 * RPW;                         // sketch rows of the group (padded)
+  constexpr int LDT = kSpI + (sizeof(TS) == 2 ? 2 : 1);    // tile row stride (elements)
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char sp_raw[];
-  TC* As = reinterpret_cast<TC*>(sp_raw);                                   // [kSpJ][kSpI + 1]
-  uint32_t* mask = reinterpret_cast<uint32_t*>(As + kSpJ * (kSpI + 1));      // [TG][8 RPW][kSpWords]
-  uint32_t* negm = mask + TG * 8 * RPW * kSpWords;
+  TS* tiles = reinterpret_cast<TS*>(sp_raw);                                  // [2][kSpJ][LDT]
+  uint32_t* mask = reinterpret_cast<uint32_t*>(tiles + 2 * kSpJ * LDT);      // [kSpWords][NR]
+  uint32_t* negm = mask + kSpWords * NR;                                      // [kSpWords][NR]
+  int* woff = reinterpret_cast<int*>(negm + kSpWords * NR);                   // [NR][kSpWords + 1]
+  uint16_t* list = reinterpret_cast<uint16_t*>(woff + NR * (kSpWords + 1));  // [TG * kSpI * zeta]
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t j0 = (int64_t)blockIdx.x * kSpJ;
   const int tg0 = blockIdx.y * TG;
@@ -135,66 +219,130 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(TC) == 8 ? 2 : 3)
   const int64_t itile0 = (int64_t)blockIdx.z * ktiles;
   const int64_t ntiles = (m + kSpI - 1) / kSpI;
   const int64_t itile1 = min(ntiles, itile0 + ktiles);
-  TC acc[TG * RPW];
+  Acc acc[TG * RPW];
 #pragma unroll
-  for (int u = 0; u < TG * RPW; ++u) acc[u] = TC(0);
-  const int nmask = TG * 8 * RPW * kSpWords;
+  for (int u = 0; u < TG * RPW; ++u) acc[u] = Acc(0);
 
-  for (int64_t it = itile0; it < itile1; ++it) {
+  // tile it of A into buffer bf: a warp per column, lanes along the rows
+  auto issue = [&](int64_t it, int bf) {
     const int64_t i0 = it * kSpI;
-    // 1. the tile of A (zero outside), a warp per column, lanes along the rows
     for (int jj = wid; jj < kSpJ; jj += kSpThreads / 32) {
       const int64_t j = j0 + jj;
-      TC* dst = As + jj * (kSpI + 1);
-      if (j < n) {
-        const TA* src = A + j * lda + i0;
+      TS* dst = tiles + (bf * kSpJ + jj) * LDT;
+      const TA* src = A + (j < n ? j : 0) * lda + i0;
+      if constexpr (sizeof(TS) == 2) {  // BF16 pairs
 #pragma unroll
-        for (int q = 0; q < kSpWords; ++q) {
-          const int ii = lane + 32 * q;
-          dst[ii] = (i0 + ii < m) ? (TC)load_as_f(src + ii) : TC(0);
+        for (int q = 0; q < kSpI / 64; ++q) {
+          const int ii = 2 * (lane + 32 * q);
+          const int64_t left = j < n ? m - (i0 + ii) : 0;
+          const int bytes = left >= 2 ? 4 : (left == 1 ? 2 : 0);
+          cp_async<4>(dst + ii, bytes ? (const void*)(src + ii) : (const void*)A, bytes);
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < kSpWords; ++q) dst[lane + 32 * q] = TC(0);
+        for (int q = 0; q < kSpWords; ++q) {
+          const int ii = lane + 32 * q;
+          const bool in = j < n && i0 + ii < m;
+          cp_async<sizeof(TS)>(dst + ii, in ? (const void*)(src + ii) : (const void*)A, in ? (int)sizeof(TS) : 0);
+        }
       }
     }
-    for (int e = tid; e < 2 * nmask; e += kSpThreads) mask[e] = 0u;
+    cp_async_commit();
+  };
+
+  if (itile0 < itile1) issue(itile0, 0);
+  for (int64_t it = itile0; it < itile1; ++it) {
+    const int cur = (int)((it - itile0) & 1);
+    const int64_t i0 = it * kSpI;
+    if (it + 1 < itile1) {
+      issue(it + 1, cur ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    // 1. masks
+    for (int e = tid; e < 2 * kSpWords * NR; e += kSpThreads) mask[e] = 0u;
     __syncthreads();
-    // 2. masks: tile row ii hits sketch row r of block t (with sign)
     for (int e = tid; e < ng * kSpI; e += kSpThreads) {
       const int t = e / kSpI, ii = e - t * kSpI;
       const int64_t i = i0 + ii;
       if (i >= m) continue;
       const uint8_t* c = P + ((int64_t)(tg0 + t) * m + i) * zeta;
       const uint32_t bit = 1u << (ii & 31);
-      for (int j = 0; j < zeta; ++j) {
-        const int code = c[j];
-        const int r = code & 127;
-        const int slot = (t * 8 * RPW + r) * kSpWords + (ii >> 5);
+      for (int jz = 0; jz < zeta; ++jz) {
+        const int code = c[jz];
+        const int slot = (ii >> 5) * NR + t * 8 * RPW + (code & 127);
         atomicOr(&mask[slot], bit);
         if (code & 128) atomicOr(&negm[slot], bit);
       }
     }
     __syncthreads();
-    // 3. the gather-add: warp-uniform walk over each owned row's mask
-    const TC* arow = As + lane * (kSpI + 1);
+    // 2. row offsets (an exclusive scan of the rows' counts, one warp), then the list
+    if (wid == 0) {
+      int carry = 0;
+      for (int r0 = 0; r0 < NR; r0 += 32) {
+        const int r = r0 + lane;
+        int cnt[kSpWords];
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < kSpWords; ++q) {
+          cnt[q] = __popc(mask[q * NR + r]);
+          tot += cnt[q];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += y;
+        }
+        int base = carry + incl - tot;
+#pragma unroll
+        for (int q = 0; q < kSpWords; ++q) {
+          woff[r * (kSpWords + 1) + q] = base;
+          base += cnt[q];
+        }
+        woff[r * (kSpWords + 1) + kSpWords] = base;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < ng * kSpI; e += kSpThreads) {
+      const int t = e / kSpI, ii = e - t * kSpI;
+      const int64_t i = i0 + ii;
+      if (i >= m) continue;
+      const uint8_t* c = P + ((int64_t)(tg0 + t) * m + i) * zeta;
+      const uint32_t below = (1u << (ii & 31)) - 1u;
+      for (int jz = 0; jz < zeta; ++jz) {
+        const int code = c[jz];
+        const int r = t * 8 * RPW + (code & 127);
+        const int pos = woff[r * (kSpWords + 1) + (ii >> 5)] + __popc(mask[(ii >> 5) * NR + r] & below);
+        list[pos] = (uint16_t)(ii | ((code & 128) << 8));
+      }
+    }
+    __syncthreads();
+    // 3. the gather-add
+    const TS* arow = tiles + (cur * kSpJ + lane) * LDT;
 #pragma unroll
     for (int u = 0; u < TG * RPW; ++u) {
       const int t = u / RPW, r = wid + 8 * (u % RPW);
       if (t < ng && r < b) {
-        const uint32_t* mw = mask + (t * 8 * RPW + r) * kSpWords;
-        const uint32_t* nw = negm + (t * 8 * RPW + r) * kSpWords;
-        TC s = acc[u];
-#pragma unroll
-        for (int q = 0; q < kSpWords; ++q) {
-          uint32_t bits = mw[q];
-          const uint32_t neg = nw[q];
-          while (bits) {
-            const int bpos = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const TC a = arow[32 * q + bpos];
-            s = ((neg >> bpos) & 1u) ? s - a : s + a;
-          }
+        const int rr = t * 8 * RPW + r;
+        const int e0 = woff[rr * (kSpWords + 1)], e1 = woff[rr * (kSpWords + 1) + kSpWords];
+        Acc s = acc[u];
+        int e = e0;
+        for (; e + 4 <= e1; e += 4) {
+          // four independent entries (broadcast reads), their loads ahead of the adds
+          const uint32_t l0 = list[e], l1 = list[e + 1], l2 = list[e + 2], l3 = list[e + 3];
+          const TC a0 = tile_value(arow + (l0 & 0x7FFF)), a1 = tile_value(arow + (l1 & 0x7FFF));
+          const TC a2 = tile_value(arow + (l2 & 0x7FFF)), a3 = tile_value(arow + (l3 & 0x7FFF));
+          s = sp_add<TC>(s, a0, l0 >> 15);
+          s = sp_add<TC>(s, a1, l1 >> 15);
+          s = sp_add<TC>(s, a2, l2 >> 15);
+          s = sp_add<TC>(s, a3, l3 >> 15);
+        }
+        for (; e < e1; ++e) {
+          const uint32_t l = list[e];
+          s = sp_add<TC>(s, tile_value(arow + (l & 0x7FFF)), l >> 15);
         }
         acc[u] = s;
       }
@@ -203,12 +351,13 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(TC) == 8 ? 2 : 3)
   }
   const int64_t j = j0 + lane;
   if (j < n) {
-    TC* o = out + (int64_t)blockIdx.z * zstride + j * out_ld;
+    TO* o = out + (int64_t)blockIdx.z * zstride + j * out_ld;
+    const int ex = colexp != nullptr ? colexp[j] - 62 : 0;
 #pragma unroll
     for (int u = 0; u < TG * RPW; ++u) {
       const int t = u / RPW, r = wid + 8 * (u % RPW);
       const int64_t c = (int64_t)(tg0 + t) * b + r;
-      if (t < ng && r < b && c < rows) o[c] = acc[u] * v;
+      if (t < ng && r < b && c < rows) o[c] = sp_final<TC, TO>(acc[u], v, ex);
     }
   }
 }
@@ -225,31 +374,36 @@ int sparse_splits(int64_t m, int64_t n, int sms) {
   return (int)((ktiles + per - 1) / per);
 }
 
-template <typename TA, typename TC, int RPW>
+template <typename TA, typename TS, typename TO, int RPW>
 static cudaError_t launch_sparse(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                                 int blocks, int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride,
-                                 const int32_t* done, cudaStream_t s) {
-  constexpr int TG = 32 / RPW;
-  const size_t smem = (size_t)kSpJ * (kSpI + 1) * sizeof(TC) + (size_t)2 * TG * 8 * RPW * kSpWords * 4;
+                                 int blocks, int64_t rows, int splits, TO* out, int64_t out_ld, int64_t zstride,
+                                 const int32_t* colexp, const int32_t* done, cudaStream_t s) {
+  using TC = decltype(tile_value((const TS*)nullptr));
+  constexpr int TG = (sizeof(typename SpAcc<TC>::type) > 8 ? 16 : 32) / RPW;
+  constexpr int NR = TG * 8 * RPW;
+  constexpr int LDT = kSpI + (sizeof(TS) == 2 ? 2 : 1);
+  const size_t smem = (size_t)2 * kSpJ * LDT * sizeof(TS) + (size_t)2 * kSpWords * NR * 4 +
+                      (size_t)NR * (kSpWords + 1) * 4 + (size_t)TG * kSpI * zeta * 2;
   static SmemLimit lim;
-  cudaError_t e = raise_smem(k_sparse_sketch<TA, TC, RPW>, smem, lim);
+  cudaError_t e = raise_smem(k_sparse_sketch<TA, TS, TO, RPW>, smem, lim);
   if (e != cudaSuccess) return e;
   const int64_t ktiles = (m + kSpI - 1) / kSpI;
   const int per = (int)((ktiles + splits - 1) / splits);
   dim3 grid((unsigned)((n + kSpJ - 1) / kSpJ), (unsigned)((blocks + TG - 1) / TG), (unsigned)splits);
-  const TC v = (TC)sqrt((double)b / (double)zeta);
-  k_sparse_sketch<TA, TC, RPW><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, P, zeta, b, blocks, rows, per, out,
-                                                             out_ld, zstride, v, done);
+  const TO v = (TO)sqrt((double)b / (double)zeta);
+  k_sparse_sketch<TA, TS, TO, RPW><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, P, zeta, b, blocks, rows, per, out,
+                                                                 out_ld, zstride, v, colexp, done);
   return cudaGetLastError();
 }
 
-template <typename TA, typename TC>
-cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                          int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride, const int32_t* done,
-                          cudaStream_t s) {
+template <typename TA, typename TS, typename TO>
+static cudaError_t dispatch_sparse(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
+                                   int64_t rows, int splits, TO* out, int64_t out_ld, int64_t zstride,
+                                   const int32_t* colexp, const int32_t* done, cudaStream_t s) {
   if (b < 1 || b > kSparseMaxB || zeta < 1 || zeta > b || rows < 1 || splits < 1) return cudaErrorInvalidValue;
   const int blocks = (int)((rows + b - 1) / b);
-#define RID_SPARSE(R) launch_sparse<TA, TC, R>(m, n, A, lda, P, zeta, b, blocks, rows, splits, out, out_ld, zstride, done, s)
+#define RID_SPARSE(R) \
+  launch_sparse<TA, TS, TO, R>(m, n, A, lda, P, zeta, b, blocks, rows, splits, out, out_ld, zstride, colexp, done, s)
   if (b <= 8) return RID_SPARSE(1);
   if (b <= 16) return RID_SPARSE(2);
   if (b <= 32) return RID_SPARSE(4);
@@ -258,9 +412,24 @@ cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const 
 #undef RID_SPARSE
 }
 
-template cudaError_t sparse_sketch<double, double>(int64_t, int64_t, const double*, int64_t, const uint8_t*, int, int,
-                                                   int64_t, int, double*, int64_t, int64_t, const int32_t*,
-                                                   cudaStream_t);
+template <typename TA, typename TC>
+cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
+                          int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride, const int32_t* done,
+                          cudaStream_t s) {
+  // the tile is staged in A's own type; BF16 pairs need 4-byte aligned rows
+  if constexpr (sizeof(TA) == 2) {
+    if ((lda & 1) != 0 || (reinterpret_cast<uintptr_t>(A) & 3) != 0) return cudaErrorInvalidValue;
+  }
+  return dispatch_sparse<TA, TA, TC>(m, n, A, lda, P, zeta, b, rows, splits, out, out_ld, zstride, nullptr, done, s);
+}
+
+cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint8_t* P,
+                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld,
+                                int64_t zstride, const int32_t* done, cudaStream_t s) {
+  return dispatch_sparse<long long, long long, double>(m, n, F, m, P, zeta, b, rows, splits, out, out_ld, zstride,
+                                                       colexp, done, s);
+}
+
 template cudaError_t sparse_sketch<float, float>(int64_t, int64_t, const float*, int64_t, const uint8_t*, int, int,
                                                  int64_t, int, float*, int64_t, int64_t, const int32_t*, cudaStream_t);
 template cudaError_t sparse_sketch<__nv_bfloat16, float>(int64_t, int64_t, const __nv_bfloat16*, int64_t,

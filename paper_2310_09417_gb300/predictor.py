@@ -90,6 +90,143 @@ def label(problems, tols, seed=1, block=32):
     return x, y, recs
 
 
+# ---------------------------------------------------------------- labels at scale
+def sketch_equivalent(family, n, rng, g, device):
+    """A matrix whose sketches have the distribution of those of an m x n matrix
+    A = U diag(s) V^T (U with orthonormal columns, Haar): Omega A = (Omega U)
+    diag(s) V^T and Omega U is Gaussian, so the n x n matrix diag(s) V^T (with
+    N(0,1) sketch rows of length n) gives the same estimates, ranks and pivots in
+    distribution without forming A.  V comes from an FP32 QR of a Gaussian
+    matrix; the matrix is stored in FP64, column-major."""
+    s = torch.as_tensor(_spectrum(family, n, rng), device=device)
+    V, _ = torch.linalg.qr(torch.randn(n, n, generator=g, device=device, dtype=torch.float32))
+    At = V.double() * s  # (A')^T = V diag(s): row j of V scaled, i.e. A' column-major
+    del V
+    return At.t()
+
+
+def ranks_from_trace(trace, norm_a, tols, block, cap):
+    """The rank Algorithm 1 returns at each relative tolerance, from the estimates
+    E^(t) of one run at a tighter tolerance: the loop stops at the first t with
+    E^(t) <= tol ||A||_F and returns k = t b (the estimates do not depend on tol);
+    a tolerance the trace never meets gives the rank cap."""
+    out = []
+    for tol in tols:
+        k = cap
+        for t, e in enumerate(trace, start=1):
+            if e <= tol * norm_a:
+                k = min(t * block, cap)
+                break
+        out.append(k)
+    return out
+
+
+def label_large(count, families, seed, device="cuda", dims=(512, 20000), tols=None, block=64,
+                log_every=0):
+    """`count` problems with n log-uniform in `dims`, m = n U[1, 3] (recorded for the
+    features; spectral families run on the sketch-equivalent n x n matrix, kernel
+    blocks on the m x n matrix itself), one run of the
+    FP64-accurate tensor-core path at the tightest tolerance each; labels for every
+    tolerance from its estimates.  Returns features, targets log2 k and records."""
+    tols = tols or [10.0 ** -e for e in (2, 3, 4, 5, 6, 7, 8, 9)]
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    feats, targs, recs = [], [], []
+    t0 = time.perf_counter()
+    for i in range(count):
+        fam = families[i % len(families)]
+        n = int(round(math.exp(rng.uniform(math.log(dims[0]), math.log(dims[1])))))
+        m = int(n * rng.uniform(1.0, 3.0))
+        if fam == "kernel":  # a Gaussian kernel block between two point clouds, formed on the device
+            h = rng.uniform(0.1, 0.6)
+            sep = rng.uniform(0.0, 2.0)
+            X = torch.rand(m, 3, generator=g, device=device, dtype=torch.float64)
+            Y = torch.rand(n, 3, generator=g, device=device, dtype=torch.float64)
+            Y[:, 0] += sep
+            A = torch.exp(-torch.cdist(Y, X) ** 2 / (h * h)).t()
+            del X, Y
+        else:
+            A = sketch_equivalent(fam, n, rng, g, device)
+        r = B.id_adaptive(A, min(tols), block=block, seed=seed + i, pivots=True, trace_cap=n // block + 2,
+                          sketch_prec=B.F64_EMU)
+        n_cap = min(A.shape)
+        ks = ranks_from_trace(r.trace, r.norm_A, tols, block, n_cap)
+        piv = r.pivots[:32].contiguous()
+        for tol, k in zip(tols, ks):
+            feats.append(B.rank_features(piv, m, n, tol))
+            targs.append(math.log2(k))
+            recs.append({"family": fam, "m": m, "n": n, "tol": tol, "k": k})
+        del A, r
+        if log_every and (i + 1) % log_every == 0:
+            print("labelled %d / %d problems (%.0f s)" % (i + 1, count, time.perf_counter() - t0), flush=True)
+    x = torch.stack(feats)
+    y = torch.tensor(targs, dtype=torch.float32, device=x.device)
+    return x, y, recs
+
+
+def evaluate_large(params, count, family, seed, tols=(1e-4, 1e-8), device="cuda", dims=(4096, 20000), block=64,
+                   max_pass_rows=4096):
+    """Held-out evaluation at scale on the FP64-accurate tensor-core path, whose
+    passes over A are a memory-bound stream: plain loop vs predictor-seeded loop
+    on the same matrices, wall time by CUDA events."""
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rows = {t: [] for t in tols}
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(dims[0]), math.log(dims[1])))))
+        A = sketch_equivalent(family, n, rng, g, device)
+        for tol in tols:
+            kw = dict(block=block, seed=seed + i, sketch_prec=B.F64_EMU)
+            B.id_adaptive(A, tol, **kw)  # warm-up (workspace, tuned launches)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            a = B.id_adaptive(A, tol, **kw)
+            e1.record()
+            s = B.id_adaptive(A, tol, predictor=params, max_pass_rows=max_pass_rows, **kw)
+            e2.record()
+            torch.cuda.synchronize()
+            same = a.k == s.k and torch.equal(a.J, s.J) and bool(torch.equal(a.X, s.X))
+            thr = tol * a.norm_A
+            rows[tol].append({"family": family, "n": n, "k": a.k, "passes_plain": a.passes,
+                              "passes_seeded": s.passes, "identical": same,
+                              "ms_plain": e0.elapsed_time(e1), "ms_seeded": e1.elapsed_time(e2),
+                              "miss_plain": a.status & B.WARN_TOL_NOT_MET != 0 and a.est_err > thr,
+                              "miss_seeded": s.status & B.WARN_TOL_NOT_MET != 0 and s.est_err > thr})
+        del A
+    return rows
+
+
+def run_large(out_dir=None, train_count=2500, eval_count=12, held_out="step", seed=31, steps=3000,
+              device="cuda", log_every=100):
+    """The predictor at scale: 2500 problems x 8 tolerances = 20000 labelled runs
+    of the method over n in [512, 20000] (three families; `held_out` set aside),
+    training by the library's kernels, and the held-out evaluation at scale."""
+    train_fams = [f for f in FAMILIES if f != held_out]
+    t0 = time.perf_counter()
+    x, y, recs = label_large(train_count, train_fams, seed, device, log_every=log_every)
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, hist = train(x, y, steps=steps, log_every=max(1, steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    pred = B.mlp_forward(params, x)
+    rmse = float(torch.sqrt(torch.mean((pred - y) ** 2)).item())
+    report = {"train_samples": int(x.shape[0]), "train_problems": train_count, "dims": [512, 20000],
+              "families_train": train_fams, "family_held_out": held_out, "label_s": t_label, "train_s": t_train,
+              "rmse_log2k_train": rmse, "loss_history": hist}
+    ev = evaluate_large(params, eval_count, held_out, seed + 7, device=device)
+    for tol, rows in ev.items():
+        report["held_out_tol_%g" % tol] = summarize(rows)
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        save(params, os.path.join(out_dir, "rank_predictor.f32"), {"held_out": held_out, "dims": [512, 20000]})
+        with open(os.path.join(out_dir, "predictor_report.json"), "w") as f:
+            json.dump(report, f, indent=1)
+    return params, report
+
+
 # ---------------------------------------------------------------- training
 def init_params(x, y, seed=0):
     """Xavier-scaled weights and the standardisation of the training data."""
@@ -214,5 +351,9 @@ def run(out_dir=None, train_count=480, eval_count=40, held_out="step", seed=11, 
 
 if __name__ == "__main__":
     import sys
-    _, rep = run(out_dir=sys.argv[1] if len(sys.argv) > 1 else None)
-    print(json.dumps(rep, indent=1))
+    out = sys.argv[1] if len(sys.argv) > 1 else None
+    if len(sys.argv) > 2 and sys.argv[2] == "large":
+        _, rep = run_large(out_dir=out)
+    else:
+        _, rep = run(out_dir=out)
+    print(json.dumps({k: v for k, v in rep.items() if k != "loss_history"}, indent=1))

@@ -68,15 +68,57 @@ def test_batched_against_oracle(B, orc):
 
 
 def test_batched_fp32(B, orc):
+    """FP32 problems against the FP64 oracle run on the FP32-rounded blocks with the
+    same counter-based Gaussian rows: the rank within one block of the oracle's,
+    the leading skeletons identical, and the achieved error within 1.2 x the
+    oracle's at the smaller of the two ranks (as the single-problem FP32 tests)."""
+    from idcheck import oracle_error_at_rank
     blocks = kernel_blocks(24, seed=3)
     As = [to_dev(A, torch.float32) for A in blocks]
-    res = B.id_batched(As, 1e-4, block=32, seed=9)
+    b, tol, seed = 32, 1e-4, 9
+    res = B.id_batched(As, tol, block=b, seed=seed)
     for A, r in zip(blocks, res):
         A32 = A.astype(np.float32).astype(np.float64)
-        e = orc.id_residual(A32, r.J.cpu().numpy(), r.X.double().cpu().numpy()) / orc.fro_norm(A32)
+        m, n = A32.shape
+        Om = orc.gaussian_rows(seed, 0, orc.rows_needed(n, b, m=m), m)
+        o = orc.id_adaptive(A32, Om, b, tol * orc.fro_norm(A32))
         assert r.status in (0, B.WARN_TOL_NOT_MET)
-        if r.status == 0:
-            assert e <= 3e-4
+        assert abs(r.k - o["k"]) <= b
+        kk = min(r.k, o["k"])
+        J = r.J.cpu().numpy()
+        # the leading pivots are far apart (kernel blocks decay fast); later ones near
+        # the FP32 rounding level may legitimately differ, which the error check covers
+        assert np.array_equal(J[:8], o["J"][:8])
+        e = orc.id_residual(A32, J, r.X.double().cpu().numpy())
+        eo = oracle_error_at_rank(orc, A32, Om, o, kk, b)
+        assert e <= 1.2 * eo + 1e-6 * orc.fro_norm(A32), (e, eo)
+
+
+def test_batched_concurrent_host_threads(B):
+    """Two host threads calling id_batched at once (own streams and workspaces)
+    share the graph and autotuner caches: the results equal the sequential ones."""
+    import threading
+    sets = [[to_dev(A) for A in kernel_blocks(12, seed=s)] for s in (11, 12)]
+    ref = [B.id_batched(As, 1e-8, block=16, seed=4) for As in sets]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out = [None, None]
+    err = []
+
+    def run(i):
+        try:
+            for _ in range(5):
+                out[i] = B.id_batched(sets[i], 1e-8, block=16, seed=4, stream=streams[i])
+        except Exception as e:  # reported in the main thread
+            err.append(e)
+    th = [threading.Thread(target=run, args=(i,)) for i in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not err, err
+    for i in (0, 1):
+        for a, c in zip(ref[i], out[i]):
+            assert a.k == c.k and torch.equal(a.J, c.J) and torch.equal(a.X, c.X)
 
 
 @pytest.mark.parametrize("cfg", ["32x1", "32x2", "64x1", "64x2"])

@@ -60,10 +60,14 @@ def test_emu_sketch_against_exact_product(B, case):
         A[17, 5] = -3.0
         Om = on_grid(rng.standard_normal((rows, m)))
     else:
-        # A = -0.99609375 = 2 (-127.5 / 256): digits d0 = -128, d1 = 128; Omega =
-        # 16001 / 2048 (q1 = 63, q0 = -127), one sign per row: group 1 sums
-        # 512 (127*128 + 63*128) = 0.74 * 2^24 over each chunk
-        A = np.full((m, n), -0.99609375)
+        # digits (d0..d6) = (63, -128, 127, -128, 127, -128, -128) of F = round(A 2^54)
+        # (E = 0: the column maximum is below 1); Omega = 16001 / 2048 (q1 = 63, q0 = -127),
+        # one sign per row and a sign flip on every third column: group g sums
+        # 512 (63 * 128 + 127 * 127) = 0.74 * 2^24 over each chunk
+        dg = [63, -128, 127, -128, 127, -128, -128]
+        F = sum(d * 256 ** (6 - q) for q, d in enumerate(dg))
+        A = np.full((m, n), F / 2.0 ** 54)
+        assert A[0, 0] * 2.0 ** 54 == F  # F is even and below 2^54: exact in FP64
         A[:, ::3] *= -1.0
         Om = np.full((rows, m), 16001.0 / 2048.0)
         Om[1::2] *= -1.0

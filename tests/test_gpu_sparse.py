@@ -65,7 +65,7 @@ def test_sparse_sketch_matches_dense_product(B, orc, m, n, rows, b):
     ref32 = orc.sketch_t(A32.astype(np.float64), Om)
     assert np.all(np.abs(G32 - ref32) <= 1e-5 * bound + 1e-30)
     Ab = torch.from_numpy(A32).to("cuda").to(torch.bfloat16)
-    Gb = B.sparse_sketch(B.colmajor(Ab), rows, b, seed=5, t0=2).cpu().numpy()
+    Gb = B.sparse_sketch(B.colmajor_padded(Ab, 8), rows, b, seed=5, t0=2).cpu().numpy()
     refb = orc.sketch_t(Ab.double().cpu().numpy(), Om)
     assert np.all(np.abs(Gb - refb) <= 1e-5 * bound + 1e-30)
 
@@ -118,6 +118,10 @@ def test_sparse_sign_with_tensor_core_schur_f64emu(B, orc):
 
 def test_sparse_sign_unsupported_paths(B):
     A = B.colmajor(torch.randn(200, 100, dtype=torch.float64, device="cuda"))
+    Aodd = B.colmajor(torch.randn(257, 40, dtype=torch.float32, device="cuda").to(torch.bfloat16))
+    with pytest.raises(B.IDError) as e:  # BF16 with an odd leading dimension
+        B.sparse_sketch(Aodd, 64, 64)
+    assert e.value.code == B.ERR_UNSUPPORTED
     A8 = B.quantize_fp8(B.colmajor(torch.randn(256, 100, dtype=torch.float32, device="cuda")))
     with pytest.raises(B.IDError) as e:
         B.id_adaptive(A8, 1e-3, omega_kind=B.OMEGA_SPARSE_SIGN)

@@ -96,3 +96,23 @@ def test_features_definition():
     assert f[0] == 0.0 and abs(f[1] - np.log10(0.5)) < 1e-15 and abs(f[2] - np.log10(0.25)) < 1e-15
     assert f[3] == -30.0  # missing pivots read as the floor
     assert (f[32], f[33], f[34]) == (3.0, 1.0, -6.0)
+
+
+def test_ranks_from_trace_equal_runs_at_each_tolerance():
+    """The predictor's labels at scale: one run of Algorithm 1 at the tightest
+    tolerance gives, through its estimates E^(t), the rank a run at each looser
+    tolerance returns (the loop stops at the first t with E^(t) <= tol ||A||_F and
+    the estimates do not depend on tol).  Checked against separate oracle runs."""
+    import oracle
+    from paper_2310_09417_gb300 import workloads as W
+    from paper_2310_09417_gb300.predictor import ranks_from_trace
+    m, n, b = 500, 300, 16
+    for kind in ("geometric", "poly", "fast_decay"):
+        A = W.spectral_matrix(m, n, W.spectrum(kind, n), seed=len(kind))
+        Om = W.gaussian_omega(5, oracle.rows_needed(n, b), m)
+        nA = oracle.fro_norm(A)
+        tols = [10.0 ** -e for e in (2, 3, 4, 5, 6, 8, 10, 13)]
+        tight = oracle.id_adaptive(A, Om, b, min(tols) * nA)
+        ks = ranks_from_trace(tight["trace"], nA, tols, b, n)
+        for tol, k in zip(tols, ks):
+            assert oracle.id_adaptive(A, Om, b, tol * nA)["k"] == k, (kind, tol)

@@ -657,12 +657,12 @@ def sketch_roofline(name, m, n, b, passes, blocks, sk_ms, sk_launches):
     else:  # f64emu
         byts = 8.0 * m * n * passes + (8.0 * m + 8.0 * n) * rows
         tfl, tpeak = 14 * 2.0 * m * n * rows, bf16_peak
-        mp = (m + 15) // 16 * 16
-        stream = 7.0 * mp * n * passes + (4.0 * mp + 8.0 * n) * rows + 23.0 * m * n
+        mp = (m + 7) // 8 * 8
+        stream = 14.0 * mp * n * passes + (4.0 * mp + 8.0 * n) * rows + 30.0 * m * n
         extra = {"stream_bytes": stream, "frac_of_stream": stream / t / 1e9 / PEAKS["hbm_gbs"],
-                 "note": "frac counts the method's 8 bytes per element of A per pass; the kernel streams 7 "
-                         "(seven int8 digit slices, widened to BF16 in shared memory), see stream_bytes"}
-        kern = "k_sketch_f64emu (tcgen05 + TMA, int8 digit slices widened in shared memory) + split-K reduce + digit preparation"
+                 "note": "frac counts the method's 8 bytes per element of A per pass; the kernel streams 14 "
+                         "(seven BF16 digit slices), see stream_bytes"}
+        kern = "k_sketch_f64emu (tcgen05 + TMA, exact digit slices) + split-K reduce + digit preparation"
     t_hbm = byts / (PEAKS["hbm_gbs"] * 1e9)
     t_tc = tfl / (tpeak * 1e12)
     if t_hbm >= t_tc:
@@ -702,7 +702,7 @@ def sampled_rel_error(A, J, X, norm_A, rows=4096, seed=5):
 
 
 def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predictor=None, max_pass_rows=0,
-                     max_over_ranks=None, barrier=None, want_pivots=False):
+                     max_over_ranks=None, barrier=None, want_pivots=False, blocks_per_pass=0):
     """Time `steps` complete adaptive IDs of A (inputs resident in HBM) after
     `warmup` untimed ones; then, unless e2e is False, the same ID through the C ABI
     with A copied in from pinned host memory and J, X copied back inside the timed
@@ -718,7 +718,7 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
     J = torch.empty(kmax, dtype=torch.int64, device=dev)
     Xbuf = torch.empty((n, kmax), dtype=xdt, device=dev)
     okind = B.OMEGA_SPARSE_SIGN if is_sparse(name) else B.OMEGA_GAUSSIAN
-    opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=1, seed=seed,
+    opts = B._opts(A, block=b, tol=tol, relative=True, k_max=kmax, k0=0, blocks_per_pass=blocks_per_pass, seed=seed,
                    omega=None, profile=True, sketch_prec=sprec, omega_kind=okind)
     if predictor is not None:
         opts.predictor = predictor.data_ptr()
@@ -729,7 +729,8 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
     def step(profile=True, pivots=False):
         return B.id_adaptive(A, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=profile,
                              workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec, pivots=pivots,
-                             predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind)
+                             predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind,
+                             blocks_per_pass=blocks_per_pass)
 
     for _ in range(max(warmup, 1)):
         res = step()
@@ -795,7 +796,8 @@ def measure_adaptive(B, name, A, dev, steps, warmup, seed, *, e2e=True, predicto
                 S_dev.copy_(S_host, non_blocking=True)
             r = B.id_adaptive(A_in, tol, block=b, relative=True, k_max=kmax, seed=seed, profile=False,
                               workspace=ws, out=(J, Xbuf), stream=stream, sketch_prec=sprec,
-                              predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind)
+                              predictor=predictor, max_pass_rows=max_pass_rows, omega_kind=okind,
+                              blocks_per_pass=blocks_per_pass)
             kk = r.k
             X_host[:, :kk].copy_(Xbuf[:, :kk], non_blocking=True)
             J_host[:kk].copy_(J[:kk], non_blocking=True)
@@ -938,6 +940,8 @@ def main():
     ap.add_argument("--forms", default="auto", choices=["auto", "all", "none"],
                     help="time the other forms the metric compares (auto: with the default workload on one GPU)")
     ap.add_argument("--form-steps", type=int, default=3)
+    ap.add_argument("--blocks-per-pass", type=int, default=0,
+                    help="sketch blocks per pass over A (0: the library's choice); J, X, k do not depend on it")
     ap.add_argument("--form-warmup", type=int, default=2)
     args = ap.parse_args()
 
@@ -983,7 +987,8 @@ def main():
     seed = 2310_09417 + 100 * rank
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     main_r = measure_adaptive(B, name, A, dev, args.steps, args.warmup, seed, e2e=not args.no_e2e,
-                              max_over_ranks=max_over_ranks, barrier=barrier, want_pivots=want_cpu)
+                              max_over_ranks=max_over_ranks, barrier=barrier, want_pivots=want_cpu,
+                              blocks_per_pass=args.blocks_per_pass)
     res = main_r["_res"]
     # whole job: every rank's ID (own seed) over the slowest rank's time
     flops_all = sum_over_ranks(main_r["flops"])

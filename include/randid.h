@@ -64,15 +64,14 @@ typedef enum {
   ID_FP8_E4M3 = 3,
   /* sketch_prec only, with F64 A and lu_prec F64: the sketch computed to FP64
      accuracy on the BF16 tensor cores by exact integer slicing.  A is split once
-     per call into 7 signed 8-bit digit slices with per-column exponents (55
-     bits), stored as int8 and widened to BF16 in shared memory; Omega is the
-     Gaussian on the grid 2^-11 (|q| <= 16383), split into 2 digits; every digit
-     product is kept and summed exactly in FP32 over chunks of 512 and in int64
-     across chunks.  Entry error <= 2^-52 max_i|A_ij| sum_r |Omega_cr|.  The
-     Schur GEMM and the block update of X run on the tensor cores the same way
-     (7 digits of 8 bits per operand).  A caller omega (F64) is rounded to the
-     same grid.  Extra workspace: 7 bytes per element of A plus 14 bytes per
-     element of T(act, 0:k). */
+     per call into 7 digit slices of 8 bits with per-column exponents (56 bits);
+     Omega is the Gaussian on the grid 2^-11 (|q| <= 16383), split into 2 digits;
+     every digit product is kept and summed exactly in FP32 over chunks of 512
+     and in int64 across chunks.  Entry error <= 2^-52 max_i|A_ij|
+     sum_r |Omega_cr|.  The Schur GEMM and the block update of X run on the
+     tensor cores the same way (7 digits of 8 bits per operand).  A caller omega
+     (F64) is rounded to the same grid.  Extra workspace: 14 bytes per element
+     of A plus 14 bytes per element of T(act, 0:k). */
   ID_F64_EMU = 4,
   /* sketch_prec only, with F32 A and lu_prec F32: the sketch on the BF16 tensor
      cores with A and Omega each split into 3 digits of 8 bits (per-column /
@@ -326,7 +325,10 @@ int cur_middle(const id_matrix* A, const int64_t* I, const int64_t* J, int64_t k
    (r/4, i, 0, 0) and Box-Muller on 53-bit uniforms in FP64 (Sec. 2.4, Sec. 5.1);
    for BF16 and FP8_E4M3 output Box-Muller runs in FP32 on the leading 24 bits of
    the same counters.  Rounded to nearest-even in the output type (E4M3
-   saturating at +-448).
+   saturating at +-448).  dtype ID_F64_EMU: the rows the FP64-accurate sketch
+   uses, rint(2^11 z) / 2^11 with |rint(2^11 z)| clamped to 16383 (z the FP64
+   value above), written as F64 by the generator that path runs (FP32 Box-Muller,
+   FP64 recomputation of the samples near a rounding boundary).
    Synchronises the stream. */
 int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dtype dtype,
                      void* out, int64_t ld, void* stream);
@@ -347,9 +349,9 @@ int id_sparse_sign_rows(uint64_t seed, int64_t t0, int64_t blocks, int64_t b, in
 /* The sparse-sign sketch alone: G = (Omega A)^T for rows [t0*b, t0*b + rows) of
    the sparse-sign matrix above (n x rows, row-major, row stride ldg >= rows; FP64
    for F64 A, FP32 for F32 and BF16 A), summed in a fixed order (deterministic).
-   F64 A is summed exactly: each column in 64-bit fixed point (error <= 2^-63
-   max|A(:,j)| per term), 128-bit integer sums, one rounding to FP64 and one for
-   the scale -- as accurate as an FP64 dot product or better.  BF16 A needs an
+   F64 A is summed exactly: each column in 55-bit fixed point (error <= 2^-55
+   max|A(:,j)| per term, as the FP64-accurate tensor-core sketch), exact integer
+   sums, one rounding to FP64 and one for the scale.  BF16 A needs an
    even leading dimension and a 4-byte aligned base (else ID_ERR_UNSUPPORTED).
    ws: id_sparse_sketch_workspace_size bytes, 256-aligned. */
 int id_sparse_sketch_workspace_size(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, size_t* bytes);

@@ -420,12 +420,17 @@ def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool 
 
 
 def gaussian_rows(seed: int, row0: int, rows: int, m: int, dtype=torch.float64,
-                  device="cuda", stream=None) -> torch.Tensor:
-    """Rows [row0, row0+rows) of the Philox/Box-Muller sketching matrix (rows x m)."""
+                  device="cuda", stream=None, grid: bool = False) -> torch.Tensor:
+    """Rows [row0, row0+rows) of the Philox/Box-Muller sketching matrix (rows x m).
+    grid=True (dtype float64): the rows the FP64-accurate sketch uses, rounded to
+    the grid 2^-11 by that path's own generator."""
     if dtype not in _TORCH_TO_ID:
         raise ValueError("unsupported dtype %s" % dtype)
+    if grid and dtype != torch.float64:
+        raise ValueError("grid rows are FP64")
     out = torch.empty((rows, m), dtype=dtype, device=device)
-    rc = _call(out.device, "id_gaussian_rows", seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, _TORCH_TO_ID[dtype],
+    code = F64_EMU if grid else _TORCH_TO_ID[dtype]
+    rc = _call(out.device, "id_gaussian_rows", seed & 0xFFFFFFFFFFFFFFFF, row0, rows, m, code,
                out.data_ptr(), m, _stream(stream, out.device))
     if rc != 0:
         raise IDError(rc, "id_gaussian_rows")

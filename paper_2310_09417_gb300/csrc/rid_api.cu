@@ -1097,7 +1097,8 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
   if (row0 < 0) return -2;
   if (rows < 0) return -3;
   if (m < 1) return -4;
-  if (dtype != ID_F64 && dtype != ID_F32 && dtype != ID_BF16 && dtype != ID_FP8_E4M3) return -5;
+  if (dtype != ID_F64 && dtype != ID_F32 && dtype != ID_BF16 && dtype != ID_FP8_E4M3 && dtype != ID_F64_EMU)
+    return -5;
   if (out == nullptr) return -6;
   if (ld < m) return -7;
   if (rows == 0) return ID_OK;
@@ -1105,6 +1106,8 @@ int id_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, id_dt
   cudaError_t e;
   if (dtype == ID_F64)
     e = gaussian_rows<double>(seed, row0, rows, m, static_cast<double*>(out), ld, nullptr, s);
+  else if (dtype == ID_F64_EMU)
+    e = f64emu_omega_grid(seed, row0, rows, m, static_cast<double*>(out), ld, s);
   else if (dtype == ID_F32)
     e = gaussian_rows<float>(seed, row0, rows, m, static_cast<float*>(out), ld, nullptr, s);
   else if (dtype == ID_BF16)

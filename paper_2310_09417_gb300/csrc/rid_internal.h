@@ -178,8 +178,8 @@ cudaError_t mlp_predict_rank(const float* params, const double* piv, int npiv, i
                              int tol_rel, DevState* st, cudaStream_t s);
 
 // ---- FP64-accurate sketch on the tensor cores (rid_tc_f64.cu).  A is split once into
-// 7 BF16 digit slices (slice-major, each column-major f64emu_pad(m) x n, f64emu_digit_bytes
-// in all) with column exponents; Omega rows are quantised to the grid 2^-11 and split into
+// 7 BF16 digit slices (slice-major; each slice stored as contiguous 128-column x 64-row
+// K-major tiles, f64emu_digit_bytes in all) with column exponents; Omega rows are quantised to the grid 2^-11 and split into
 // 2 digit planes (each rows_alloc x f64emu_pad(m)); out[z] (n x rows, FP64) holds split z
 // of (Omega A)^T.
 int64_t f64emu_pad(int64_t m);
@@ -189,6 +189,10 @@ cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, i
                            cudaStream_t s);
 cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t rows_alloc,
                          const double* src, int64_t ld_src, void* wdigits, const int32_t* done, cudaStream_t s);
+// Omega's grid values rint(2048 z) / 2048 (|.| <= 16383 / 2048) from the same
+// generator as f64emu_omega, as FP64 rows (row stride ld >= m).
+cudaError_t f64emu_omega_grid(uint64_t seed, int64_t row0, int64_t rows, int64_t m, double* out, int64_t ld,
+                              cudaStream_t s);
 cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, int64_t n, const void* wdigits,
                           int64_t rows, int64_t rows_alloc, double* out, int64_t out_ld, int64_t zstride, int splits,
                           DevState* st, const int32_t* done, cudaStream_t s);

@@ -21,10 +21,11 @@
 //
 // FP64 input is summed exactly in integers: GB300 issues about two FP64
 // instructions per clock per SM, and each element of A feeds zeta sums.  A is
-// converted once per call to 64-bit fixed point per column (F = round(A 2^(62-e))
-// for |A| < 2^e, an error of at most 2^-63 max|A(:,j)| per term), every entry of
-// the sketch is the exact 128-bit integer sum of +-F, and one conversion rounds
-// it to FP64 (then the scale sqrt(b/zeta), one more rounding).
+// converted once per call to fixed point per column (F = round(A 2^(54-e)) for
+// |A| < 2^e, an error of at most 2^-55 max|A(:,j)| per term, as the digits of the
+// FP64-accurate tensor-core sketch), every entry of the sketch is the exact
+// integer sum of +-F (int64 within a tile, 128 bits across tiles), and one
+// conversion rounds it to FP64 (then the scale sqrt(b/zeta), one more rounding).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -120,24 +121,32 @@ __device__ __forceinline__ float load_as_f(const float* p) { return *p; }
 __device__ __forceinline__ double load_as_f(const double* p) { return *p; }
 __device__ __forceinline__ long long load_as_f(const long long* p) { return *p; }
 
-// The accumulator of an entry and its final value: FP32 sums for FP32 / BF16 input,
-// exact 128-bit integer sums of the fixed-point FP64 input.
+// The accumulator of an entry and its final value: FP32 sums for FP32 / BF16 input;
+// for the fixed-point FP64 input, exact int64 sums within a tile (a sketch row takes
+// at most one term per tile row: 256 terms below 2^54 each stay below 2^62) folded
+// into an exact 128-bit total once per tile.
 template <typename TS>
 struct SpAcc {
+  using part = TS;
   using type = TS;
 };
 template <>
 struct SpAcc<long long> {
+  using part = long long;
   using type = __int128;
 };
-template <typename TS>
-__device__ __forceinline__ typename SpAcc<TS>::type sp_add(typename SpAcc<TS>::type s, TS a, bool neg) {
-  return neg ? s - a : s + a;
+// s + a or s - a, branch-free: the sign flips a's sign bit (float) or negates by mask (int64)
+__device__ __forceinline__ float sp_add(float s, float a, uint32_t neg) {
+  return s + __int_as_float(__float_as_int(a) ^ (int)(neg << 31));
+}
+__device__ __forceinline__ long long sp_add(long long s, long long a, uint32_t neg) {
+  const long long msk = -(long long)neg;
+  return s + ((a ^ msk) - msk);
 }
 template <typename TS, typename TO>
 __device__ __forceinline__ TO sp_final(typename SpAcc<TS>::type s, TO v, int ex) {
   if constexpr (sizeof(TS) == 8) {
-    // s 2^ex: |s| < 2^62 times the terms (< 2^82), so s >> 32 fits 64 bits
+    // s 2^ex: |s| < 2^54 times the terms (< 2^74), so s >> 32 fits 64 bits
     const long long hi = (long long)(s >> 32);
     const long long lo = (long long)(s & (__int128)0xFFFFFFFFll);
     return tcx::fixed_to_double(hi, lo, ex) * v;
@@ -146,13 +155,14 @@ __device__ __forceinline__ TO sp_final(typename SpAcc<TS>::type s, TO v, int ex)
   }
 }
 
-// F(i, j) = round(A(i, j) 2^(62 - e_j)) with |A(:, j)| < 2^e_j (column-major, ld m).
+// F(i, j) = round(A(i, j) 2^(54 - e_j)) with |A(:, j)| < 2^e_j (column-major, ld m):
+// |F| < 2^54, an error of at most 2^-55 max|A(:, j)| per term.
 __global__ void k_sparse_fixed(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
                                const int32_t* __restrict__ colexp, long long* __restrict__ F) {
   const int64_t total = m * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / m, i = e - j * m;
-    F[e] = tcx::fixed_of<8>(A[i + j * lda], colexp[j] + 1);
+    F[e] = tcx::fixed_of<7>(A[i + j * lda], colexp[j] + 1);
   }
 }
 
@@ -328,23 +338,25 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(TS) == 8 ? 1 : 2)
       if (t < ng && r < b) {
         const int rr = t * 8 * RPW + r;
         const int e0 = woff[rr * (kSpWords + 1)], e1 = woff[rr * (kSpWords + 1) + kSpWords];
-        Acc s = acc[u];
+        // four independent partial sums (four entries in flight), combined in a fixed
+        // order at the end of the tile: deterministic, and exact for the integer sums
+        using Part = typename SpAcc<TC>::part;
+        Part s0 = Part(0), s1 = Part(0), s2 = Part(0), s3 = Part(0);
         int e = e0;
         for (; e + 4 <= e1; e += 4) {
-          // four independent entries (broadcast reads), their loads ahead of the adds
           const uint32_t l0 = list[e], l1 = list[e + 1], l2 = list[e + 2], l3 = list[e + 3];
           const TC a0 = tile_value(arow + (l0 & 0x7FFF)), a1 = tile_value(arow + (l1 & 0x7FFF));
           const TC a2 = tile_value(arow + (l2 & 0x7FFF)), a3 = tile_value(arow + (l3 & 0x7FFF));
-          s = sp_add<TC>(s, a0, l0 >> 15);
-          s = sp_add<TC>(s, a1, l1 >> 15);
-          s = sp_add<TC>(s, a2, l2 >> 15);
-          s = sp_add<TC>(s, a3, l3 >> 15);
+          s0 = sp_add(s0, a0, l0 >> 15);
+          s1 = sp_add(s1, a1, l1 >> 15);
+          s2 = sp_add(s2, a2, l2 >> 15);
+          s3 = sp_add(s3, a3, l3 >> 15);
         }
         for (; e < e1; ++e) {
           const uint32_t l = list[e];
-          s = sp_add<TC>(s, tile_value(arow + (l & 0x7FFF)), l >> 15);
+          s0 = sp_add(s0, tile_value(arow + (l & 0x7FFF)), l >> 15);
         }
-        acc[u] = s;
+        acc[u] = acc[u] + (((Acc)s0 + (Acc)s1) + ((Acc)s2 + (Acc)s3));
       }
     }
     __syncthreads();
@@ -352,7 +364,7 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(TS) == 8 ? 1 : 2)
   const int64_t j = j0 + lane;
   if (j < n) {
     TO* o = out + (int64_t)blockIdx.z * zstride + j * out_ld;
-    const int ex = colexp != nullptr ? colexp[j] - 62 : 0;
+    const int ex = colexp != nullptr ? colexp[j] - 54 : 0;
 #pragma unroll
     for (int u = 0; u < TG * RPW; ++u) {
       const int t = u / RPW, r = wid + 8 * (u % RPW);

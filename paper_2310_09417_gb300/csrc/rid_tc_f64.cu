@@ -2,29 +2,25 @@
 //
 // GB300 executes FP64 FMAs at 1.25 TFLOP/s, so the FP64 sketch (Sec. 2.4) is
 // moved onto the tensor cores by exact integer slicing:
-//   * A: per column j an exponent E_j with max_i |A_ij| < 2^E_j; x = A / 2^(E_j+2)
-//     (|x| < 1/4) is written as sum_{s<7} d_s 2^(-8(s+1)) + r with balanced 8-bit
-//     digits, |d_0| <= 64 and d_s in [-128, 127] below, |r| <= 2^-57 -- 55 bits per
-//     column.  Every digit fits a signed byte: A is stored once per call as 7 int8
-//     digit planes, 7 bytes per element (the sketch reads A's 8 FP64 bytes'
-//     worth of information as 7).
+//   * A: per column j an exponent E_j with max_i |A_ij| < 2^E_j; x = A / 2^(E_j+1)
+//     (|x| < 1/2) is written as sum_{s<7} d_s 2^(-8(s+1)) + r with balanced 8-bit
+//     digits |d_s| <= 128 and |r| <= 2^-57 -- 56 bits per column.
 //   * Omega: standard normal numbers on the grid 2^-11, q = rint(2048 z) clipped to
 //     |q| <= 16383, split as q = 256 q1 + q0 with |q1| <= 64, |q0| <= 128.
-//   * In the kernel, converter warps widen each int8 tile to BF16 in shared memory
-//     (integers exact in BF16), in the 128-byte-swizzled layout the MMA reads.
-//     Products of equal weight 2^(-8g) share one FP32 accumulator group in tensor
-//     memory: group g collects q1 x d_g and q0 x d_(g-1) (g = 0..7: 8 groups x 64
-//     columns = the 512 columns of an SM; no product is dropped).  One MMA with
-//     N = 128 (both Omega digits stacked) writes groups s and s+1 for slice s.
-//     Over a chunk of 512 K a group's partial sums stay below 512 (128*128 +
-//     64*128) < 2^24: the FP32 accumulation is exact.
+//   * Every digit is an integer exact in BF16.  Products of equal weight
+//     2^(-8g) share one FP32 accumulator group in tensor memory: group g collects
+//     q1 x d_g and q0 x d_(g-1) (g = 0..7: 8 groups x 64 columns = the 512 columns
+//     of an SM; no product is dropped).  One MMA with N = 128 (both Omega digits
+//     stacked) writes groups s and s+1 for slice s.  Over a chunk of 512 K a
+//     group's partial sums stay below 512 (128*128 + 64*128) < 2^24: the FP32
+//     accumulation is exact.
 //   * After slice g of a chunk, group g is final for that chunk; the epilogue
 //     warps convert it to integers and add it, exactly, to two int64
 //     accumulators per entry (groups 0..3 and 4..7 with weights 2^(8(3-g)) and
 //     2^(8(7-g))), then hand the group back to the MMA issuer -- the epilogue
 //     of a chunk overlaps the MMAs of the next one.  At the end
-//     Y_cj = 2^(E_j - 65) (acc_hi 2^32 + acc_lo), assembled by integer operations.
-// Error of an entry: the digit remainders (|r| 2^(E_j+2) <= 2^-54 max_i|A_ij| per
+//     Y_cj = 2^(E_j - 66) (acc_hi 2^32 + acc_lo), assembled by integer operations.
+// Error of an entry: the digit remainders (|r| 2^(E_j+1) <= 2^-55 max_i|A_ij| per
 // term) and one final rounding: at most 2^-52 max_i|A_ij| sum_r |Omega_cr| --
 // inside the worst-case rounding bound m 2^-53 sum_r |Omega_cr||A_rj| of an FP64
 // dot product.
@@ -48,35 +44,20 @@ constexpr int kSlices = 7;       // digits of A
 constexpr int kGroups = 8;       // accumulator groups (slice s feeds groups s and s+1)
 constexpr int kChunkSteps = 8;   // K stages per exact chunk (512 K)
 constexpr int kChunk = kChunkSteps * kBK;
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 constexpr int kEpiWarps = 8;     // two per TMEM lane quarter, 32 columns each
-constexpr int kCvtWarps = 2;     // int8 -> BF16 widening of the A tiles
-constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kCvtWarps;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxChunksPerSplit = 1 << 14;  // int64 accumulators: 2^14 * 2^48 < 2^63
 constexpr double kQMax = 16383.0;
 
 using namespace tcx;
 
-// Two signed bytes of a word as a BF16 pair (low element first), without integer
-// to float conversions (a quarter-rate pipe): ub is the word with every byte's sign
-// bit flipped (byte = d + 128); splicing byte k under the exponent of 2^23 gives
-// the float 2^23 + d + 128, and subtracting 2^23 + 128 leaves d exactly.  The
-// integers are exact in BF16, whose bits are the FP32's upper half.
-template <int K0>
-__device__ __forceinline__ uint32_t widen2(uint32_t ub) {
-  const float f0 = __uint_as_float(__byte_perm(ub, 0x4B000000u, 0x7540 | K0)) - 8388736.0f;
-  const float f1 = __uint_as_float(__byte_perm(ub, 0x4B000000u, 0x7540 | (K0 + 1))) - 8388736.0f;
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-}
-
 // acc += v * 2^sh, exact (v an integer-valued float below 2^23 in magnitude)
 struct Smem {
-  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // one digit slice of A, widened: 16 KB
+  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // one digit slice of A: 16 KB
   alignas(1024) __nv_bfloat16 w[kStages][2 * kBN * kBK];  // both digits of Omega: 128 rows, 16 KB
-  alignas(1024) int8_t araw[kStages][kBM * kBK];          // the slice as loaded: 128 rows x 64 B, 8 KB
-  uint64_t full[kStages];   // the TMA copies of stage b landed
-  uint64_t cvt[kStages];    // the converter warps widened stage b
-  uint64_t empty[kStages];  // the MMAs of stage b completed
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
   uint64_t ready[kGroups];  // group g of the current chunk is final
   uint64_t free_[kGroups];  // the epilogue has read group g
   uint64_t drain;
@@ -105,7 +86,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.cvt[s], kCvtWarps);
       mbar_init(&sm.empty[s], 1);
     }
     for (int g = 0; g < kGroups; ++g) {
@@ -132,9 +112,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < steps_c; ++j, ++it) {
           const int b = it % kStages;
           if (it >= kStages && !mbar_wait(&sm.empty[b], ((it / kStages) + 1) & 1, st)) { ok = false; break; }
-          mbar_expect_tx(&sm.full[b], kBM * kBK + 2 * kBN * kBK * 2);
+          mbar_expect_tx(&sm.full[b], (kBM + 2 * kBN) * kBK * 2);
           const int k0 = kbeg + (c * kChunkSteps + j) * kBK;
-          tma_load_3d(sm.araw[b], &map_a, &sm.full[b], k0, m0, s);
+          tma_load_4d(sm.a[b], &map_a, &sm.full[b], 0, 0, k0 / kBK, s * (int)gridDim.y + (int)blockIdx.y);
           tma_load_3d(sm.w[b], &map_w, &sm.full[b], k0, n0, 0);
         }
       }
@@ -161,7 +141,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < steps_c; ++j, ++it) {
           const int b = it % kStages;
           if (!mbar_wait(&sm.full[b], (it / kStages) & 1, st)) { ok = false; break; }
-          if (!mbar_wait(&sm.cvt[b], (it / kStages) & 1, st)) { ok = false; break; }
           fence_after_sync();
           const uint64_t da = desc_sw128(sm.a[b]);
           const uint64_t dq1 = desc_sw128(sm.w[b]);             // high digit of Omega (weight 1)
@@ -189,42 +168,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     // every MMA issued has completed before TMEM is released
     mma_commit(&sm.drain);
     mbar_wait_drain(&sm.drain, 0);
-  } else if (warp >= 2 + kEpiWarps) {
-    // ---------------- converters: stage b's int8 slice (128 rows x 64 K bytes, as
-    // loaded) widened to BF16 in the 128-byte-swizzled K-major layout the MMA reads
-    // (16-byte chunk c of row r at r * 128 + ((c ^ (r & 7)) << 4)).  Each unit is 8
-    // digits: one 8-byte load, one 16-byte store.
-    const int ct = threadIdx.x - 32 * (2 + kEpiWarps);  // 0 .. 32 kCvtWarps - 1
-    int it = 0;
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
-      for (int s = 0; s < kSlices && ok; ++s) {
-        for (int j = 0; j < steps_c; ++j, ++it) {
-          const int b = it % kStages;
-          if (!mbar_wait(&sm.full[b], (it / kStages) & 1, st)) { ok = false; break; }
-          const unsigned char* src = reinterpret_cast<const unsigned char*>(sm.araw[b]);
-          unsigned char* dst = reinterpret_cast<unsigned char*>(sm.a[b]);
-#pragma unroll
-          for (int q = 0; q < (kBM * kBK / 8) / (32 * kCvtWarps); ++q) {
-            const int u = ct + q * 32 * kCvtWarps;
-            const int r = u >> 3, ch = u & 7;
-            const uint2 x = *reinterpret_cast<const uint2*>(src + r * kBK + ch * 8);
-            const uint32_t u0 = x.x ^ 0x80808080u, u1 = x.y ^ 0x80808080u;
-            uint4 y;
-            y.x = widen2<0>(u0);
-            y.y = widen2<2>(u0);
-            y.z = widen2<0>(u1);
-            y.w = widen2<2>(u1);
-            *reinterpret_cast<uint4*>(dst + r * 128 + ((ch ^ (r & 7)) << 4)) = y;
-          }
-          // the generic-proxy stores become visible to the tensor core's reads
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if ((threadIdx.x & 31) == 0) mbar_arrive(&sm.cvt[b]);
-        }
-      }
-    }
   } else if (warp >= 2) {
     // ---------------- epilogue: exact integer accumulation of the groups
     const int ew = warp - 2;
@@ -268,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int lim = rows - n0 - half * 32;
 #pragma unroll
       for (int i = 0; i < 32; ++i)
-        if (i < lim) o[i] = fixed_to_double(hi[i], lo[i], e - 65);
+        if (i < lim) o[i] = fixed_to_double(hi[i], lo[i], e - 66);
     }
   }
   fence_before_sync();
@@ -302,90 +245,174 @@ __global__ void k_colexp(const double* __restrict__ A, int64_t lda, int64_t m, i
   }
 }
 
-// Digits: D[s][j][i] (slice-major, each slice column-major m_pad x n, int8) of A(i, j),
-// by integer operations on the FP64 bit patterns (x / 2^(E_j+2) = sum_s d_s 2^(-8(s+1));
-// F = round(x 2^55) has |F| < 2^54, so the top digit is at most 64 in magnitude).
-__global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_t m, int64_t m_pad, int64_t n,
-                               const int32_t* __restrict__ E, int8_t* __restrict__ D) {
-  const int64_t total = m_pad * n;
-  const int64_t slice = m_pad * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+// Digits of A(i, j) by integer operations on the FP64 bit patterns
+// (x / 2^(E_j+1) = sum_s d_s 2^(-8(s+1))), stored tile by tile: slice s, column
+// tile t (kBM columns), K block kb (kBK rows of A) is one contiguous kBM x kBK
+// K-major tile, D[s][t][kb][c][k] = d_s(kb kBK + k, t kBM + c).  A TMA box is then
+// one 16 KB run of memory (a column-major plane would cost kBM separate 128-byte
+// segments per box), and a chunk of one slice is kChunkSteps consecutive tiles.
+// Rows past m and columns past n are zero digits.
+__global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t nkb,
+                               int64_t ntl, const int32_t* __restrict__ E, __nv_bfloat16* __restrict__ D) {
+  constexpr int64_t kTile = (int64_t)kBM * kBK;
+  const int64_t slice = nkb * ntl * kTile;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slice;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / m_pad, i = e - j * m_pad;
-    long long F = i < m ? fixed_of<kSlices>(A[i + j * lda], E[j] + 1) : 0ll;
-    int8_t dg[kSlices];
-#pragma unroll
-    for (int q = kSlices - 1; q > 0; --q) {
-      long long r = F & 255;
-      if (r >= 128) r -= 256;  // balanced digit in [-128, 127]
-      dg[q] = (int8_t)r;
-      F = (F - r) >> 8;  // exact
-    }
-    dg[0] = (int8_t)F;  // |F| <= 64 here
-#pragma unroll
-    for (int q = 0; q < kSlices; ++q) D[e + q * slice] = dg[q];
+    const int64_t tb = e / kTile, w = e - tb * kTile;
+    const int64_t t = tb / nkb, kb = tb - t * nkb;
+    const int64_t j = t * kBM + w / kBK, i = kb * kBK + (w % kBK);
+    write_digits<kSlices>(i < m && j < n ? fixed_of<kSlices>(A[i + j * lda], E[j]) : 0ll, D + e, slice);
   }
 }
 
-// Omega digits on the grid 2^-11: W[t][r][i], t = 0 high digit q1, t = 1 low digit q0;
+// Omega digits on the grid 2^-11: W[t][r][i], t = 0 high digit q1, t = 1 low digit q0,
+// q = rint(2048 z) = 256 q1 + q0 (|q| <= kQMax, q1 = rint(q / 256) ties to even);
 // from the Philox/Box-Muller rows (gen) or a caller matrix (src != nullptr).
-__global__ void k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t ldw, int64_t rows_alloc,
-                               const double* __restrict__ src, int64_t ld_src, __nv_bfloat16* __restrict__ W,
-                               const int32_t* done) {
+// Generated rows need z to FP64 accuracy only where 2048 z is near a rounding
+// boundary.  Each sample is evaluated in FP32 on the same 53-bit uniforms (a few
+// FP32 ulp of z plus about 2^-23 r absolute from the FP64 value: below
+// 0.0021 + 0.002 |z| in units of q); a sample whose 2048 z32 lies within
+// 1/64 + |z| / 256 of a boundary n + 1/2 goes to its warp's list, and the warp's
+// lanes recompute the listed samples in FP64 together.  Every q equals the FP64
+// rint.  kGrid: write q / 2048 as FP64 to G (row stride ldg, columns < m) instead
+// of the digit planes.
+template <bool kGrid>
+__device__ __forceinline__ void write_omega_q(int q, __nv_bfloat16* W, int64_t plane, int64_t at, double* G,
+                                              int64_t gat) {
+  if constexpr (kGrid) {
+    G[gat] = (double)q * 0x1.0p-11;
+  } else {
+    const int t = q + 128;
+    int q1 = t >> 8;                         // floor(q / 256 + 1/2)
+    if ((t & 255) == 0 && (q1 & 1)) q1 -= 1;  // exact tie: to even
+    W[at] = __int2bfloat16_rn(q1);            // |q1| <= 64, exact
+    W[plane + at] = __int2bfloat16_rn(q - 256 * q1);  // |q0| <= 128, exact
+  }
+}
+__device__ __forceinline__ int omega_q_f64(double val) {
+  const double qv = rint(val * 2048.0);
+  return (int)fmin(fmax(qv, -kQMax), kQMax);  // NaN -> -kQMax
+}
+__device__ __forceinline__ int omega_q_f32(float qf) {
+  const int q = __float2int_rn(qf);
+  const int lim = (int)kQMax;
+  return q < -lim ? -lim : (q > lim ? lim : q);
+}
+
+constexpr int kOmegaThreads = 256;
+
+template <bool kGrid>
+__global__ void __launch_bounds__(kOmegaThreads)
+    k_omega_digits(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t ldw, int64_t rows_alloc,
+                   const double* __restrict__ src, int64_t ld_src, __nv_bfloat16* __restrict__ W,
+                   double* __restrict__ G, int64_t ldg, const int32_t* done) {
   if (done != nullptr && *done) return;
+  __shared__ uint8_t amb_list[kOmegaThreads / 32][128];  // per warp: lane | u << 5
   const int64_t nq = (ldw + 3) >> 2;
   const int64_t total = rows * nq;
   const int64_t plane = rows_alloc * ldw;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / nq, q = e - r * nq;
-    double z[4];
-    if (src == nullptr) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-aligned bases: every lane of a warp runs the same number of iterations
+  for (int64_t eb = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); eb < total; eb += stride) {
+    const int64_t e = eb + lane;
+    const bool valid = e < total;
+    const int64_t r = valid ? e / nq : 0, q = valid ? e - r * nq : 0;
+    if (src != nullptr) {
+      if (valid)
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = 4 * q + u;
+          if (i >= ldw || (kGrid && i >= m)) break;
+          write_omega_q<kGrid>(omega_q_f64(i < m ? src[r * ld_src + i] : 0.0), W, plane, r * ldw + i, G,
+                               r * ldg + i);
+        }
+      continue;
+    }
+    bool amb[4] = {false, false, false, false};
+    if (valid) {
       uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + r), x2 = 0, x3 = 0;
       philox4x64_10(x0, x1, x2, x3, seed, 0ull);
-      box_muller(x0, x1, z[0], z[1]);
-      box_muller(x2, x3, z[2], z[3]);
+      float zf[4];
+      box_muller_f32_53(x0, x1, zf[0], zf[1]);
+      box_muller_f32_53(x2, x3, zf[2], zf[3]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = 4 * q + u;
+        if (i >= ldw || (kGrid && i >= m)) break;
+        if (i >= m) {
+          write_omega_q<kGrid>(0, W, plane, r * ldw + i, G, 0);
+          continue;
+        }
+        const float qf = zf[u] * 2048.0f;  // exact (a power of two)
+        amb[u] = fabsf(qf - floorf(qf) - 0.5f) < 0x1.0p-6f + fabsf(qf) * 0x1.0p-19f;
+        if (!amb[u]) write_omega_q<kGrid>(omega_q_f32(qf), W, plane, r * ldw + i, G, r * ldg + i);
+      }
     }
+    // the warp's ambiguous samples, recomputed in FP64 by its lanes together
+    unsigned cnt = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int64_t i = 4 * q + u;
-      if (i >= ldw) break;
-      double val = 0.0;
-      if (i < m) val = src == nullptr ? z[u] : src[r * ld_src + i];
-      double qv = rint(val * 2048.0);
-      qv = fmin(fmax(qv, -kQMax), kQMax);
-      const double q1 = rint(qv / 256.0);  // |q1| <= 64
-      const double q0 = qv - 256.0 * q1;   // |q0| <= 128
-      W[r * ldw + i] = __double2bfloat16(q1);
-      W[plane + r * ldw + i] = __double2bfloat16(q0);
+      const unsigned mask = __ballot_sync(0xffffffffu, amb[u]);
+      if (amb[u]) amb_list[wid][cnt + __popc(mask & ((1u << lane) - 1u))] = (uint8_t)(lane | (u << 5));
+      cnt += __popc(mask);
     }
+    __syncwarp();
+    for (unsigned k = lane; k < cnt; k += 32) {
+      const int code = amb_list[wid][k];
+      const int l = code & 31, u = code >> 5;
+      const int64_t e2 = eb + l, r2 = e2 / nq, q2 = e2 - r2 * nq;
+      uint64_t x0 = (uint64_t)q2, x1 = (uint64_t)(row0 + r2), x2 = 0, x3 = 0;
+      philox4x64_10(x0, x1, x2, x3, seed, 0ull);
+      double z0, z1;
+      if (u < 2)
+        box_muller(x0, x1, z0, z1);
+      else
+        box_muller(x2, x3, z0, z1);
+      write_omega_q<kGrid>(omega_q_f64((u & 1) ? z1 : z0), W, plane, r2 * ldw + 4 * q2 + u, G,
+                           r2 * ldg + 4 * q2 + u);
+    }
+    __syncwarp();
   }
 }
 
 // ------------------------------------------------------------------ host side
-// BF16 planes (Omega's digits): 128-byte swizzled boxes of 64 K x box_rows, the MMA's
-// layout.  int8 planes (A's digits): plain boxes of 64 K bytes x box_rows, widened
-// by the converter warps.
 bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t planes, int box_rows,
-                 int box_planes, bool int8) {
+                 int box_planes) {
   auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
-  const cuuint64_t esz = int8 ? 1 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)inner * esz, (cuuint64_t)inner * outer * esz};
+  cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * outer * 2};
   cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
   cuuint32_t estr[3] = {1, 1, 1};
-  return fn(map, int8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base),
-            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            int8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A's digit tiles as a 4-D tensor: (k within the tile, column within the tile,
+// K block, slice-major tile index); a box is one whole kBK x kBM tile.
+bool make_map_tiles(CUtensorMap* map, const void* base, int64_t kblocks, int64_t tiles) {
+  auto fn = tensor_map_encoder();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)kBK, (cuuint64_t)kBM, (cuuint64_t)kblocks, (cuuint64_t)tiles};
+  cuuint64_t strides[3] = {(cuuint64_t)kBK * 2, (cuuint64_t)kBK * kBM * 2, (cuuint64_t)kblocks * kBK * kBM * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace tc64
 
-// K padded to 16: the int8 planes' rows must be 16-byte multiples for TMA.
-int64_t f64emu_pad(int64_t m) { return (m + 15) / 16 * 16; }
-size_t f64emu_digit_bytes(int64_t m, int64_t n) { return (size_t)tc64::kSlices * f64emu_pad(m) * n; }
+int64_t f64emu_pad(int64_t m) { return (m + 7) / 8 * 8; }
+namespace {
+int64_t digit_kblocks(int64_t m) { return (m + tc64::kBK - 1) / tc64::kBK; }
+int64_t digit_tiles(int64_t n) { return (n + tc64::kBM - 1) / tc64::kBM; }
+}  // namespace
+size_t f64emu_digit_bytes(int64_t m, int64_t n) {
+  return (size_t)tc64::kSlices * digit_kblocks(m) * digit_tiles(n) * tc64::kBM * tc64::kBK * 2;
+}
 
 // Split count of the K range.  One CTA per SM holds a (column tile, split); its
 // time is about its chunks (+ a fixed cost), so the launch takes
@@ -414,13 +441,14 @@ int f64emu_splits(int64_t m, int64_t n, int sms) {
 
 cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, void* digits,
                            cudaStream_t s) {
-  const int64_t mp = f64emu_pad(m);
   tc64::k_colexp<<<(int)(n < 4096 ? n : 4096), 256, 0, s>>>(A, lda, m, n, colexp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int64_t blocks = (mp * n + 255) / 256;
+  const int64_t nkb = digit_kblocks(m), ntl = digit_tiles(n);
+  int64_t blocks = (nkb * ntl * tc64::kBM * tc64::kBK + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  tc64::k_split_digits<<<(int)blocks, 256, 0, s>>>(A, lda, m, mp, n, colexp, static_cast<int8_t*>(digits));
+  tc64::k_split_digits<<<(int)blocks, 256, 0, s>>>(A, lda, m, n, nkb, ntl, colexp,
+                                                   static_cast<__nv_bfloat16*>(digits));
   return cudaGetLastError();
 }
 
@@ -432,11 +460,22 @@ cudaError_t f64_colexp(const double* A, int64_t lda, int64_t m, int64_t n, int32
 cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t rows_alloc,
                          const double* src, int64_t ld_src, void* wdigits, const int32_t* done, cudaStream_t s) {
   const int64_t ldw = f64emu_pad(m);
-  int64_t blocks = (rows * ((ldw + 3) / 4) + 255) / 256;
+  int64_t blocks = (rows * ((ldw + 3) / 4) + tc64::kOmegaThreads - 1) / tc64::kOmegaThreads;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  tc64::k_omega_digits<<<(int)blocks, 256, 0, s>>>(seed, row0, rows, m, ldw, rows_alloc, src, ld_src,
-                                                  static_cast<__nv_bfloat16*>(wdigits), done);
+  tc64::k_omega_digits<false><<<(int)blocks, tc64::kOmegaThreads, 0, s>>>(
+      seed, row0, rows, m, ldw, rows_alloc, src, ld_src, static_cast<__nv_bfloat16*>(wdigits), nullptr, 0, done);
+  return cudaGetLastError();
+}
+
+cudaError_t f64emu_omega_grid(uint64_t seed, int64_t row0, int64_t rows, int64_t m, double* out, int64_t ld,
+                              cudaStream_t s) {
+  const int64_t ldw = f64emu_pad(m);
+  int64_t blocks = (rows * ((ldw + 3) / 4) + tc64::kOmegaThreads - 1) / tc64::kOmegaThreads;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  tc64::k_omega_digits<true><<<(int)blocks, tc64::kOmegaThreads, 0, s>>>(seed, row0, rows, m, ldw, rows, nullptr, 0,
+                                                                         nullptr, out, ld, nullptr);
   return cudaGetLastError();
 }
 
@@ -445,8 +484,9 @@ cudaError_t f64emu_sketch(const void* digits, const int32_t* colexp, int64_t m, 
                           DevState* st, const int32_t* done, cudaStream_t s) {
   const int64_t mp = f64emu_pad(m);
   CUtensorMap ma, mw;
-  if (!tc64::make_map_3d(&ma, digits, mp, n, tc64::kSlices, tc64::kBM, 1, true)) return cudaErrorInvalidValue;
-  if (!tc64::make_map_3d(&mw, wdigits, mp, rows_alloc, 2, tc64::kBN, 2, false)) return cudaErrorInvalidValue;
+  if (!tc64::make_map_tiles(&ma, digits, digit_kblocks(m), digit_tiles(n) * tc64::kSlices))
+    return cudaErrorInvalidValue;
+  if (!tc64::make_map_3d(&mw, wdigits, mp, rows_alloc, 2, tc64::kBN, 2)) return cudaErrorInvalidValue;
   const int64_t chunks = (mp + tc64::kChunk - 1) / tc64::kChunk;
   const int64_t per = (chunks + splits - 1) / splits;
   const int kchunk = (int)(per * tc64::kChunk);

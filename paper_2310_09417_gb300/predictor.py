@@ -100,7 +100,7 @@ def sketch_equivalent(family, n, rng, g, device):
     matrix; the matrix is stored in FP64, column-major."""
     s = torch.as_tensor(_spectrum(family, n, rng), device=device)
     V, _ = torch.linalg.qr(torch.randn(n, n, generator=g, device=device, dtype=torch.float32))
-    At = V.double() * s  # (A')^T = V diag(s): row j of V scaled, i.e. A' column-major
+    At = (V.double() * s).contiguous()  # (A')^T = V diag(s), row-major: A' column-major
     del V
     return At.t()
 
@@ -165,11 +165,34 @@ def label_large(count, families, seed, device="cuda", dims=(512, 20000), tols=No
     return x, y, recs
 
 
+def tall_bf16(D, tall):
+    """The (tall n) x n BF16 matrix [D; D; ...; D] / sqrt(tall), column-major with
+    an even leading dimension: its Gram matrix is D^T D, so it has D's singular
+    values and right singular vectors (left ones [U; ...; U] / sqrt(tall), again
+    orthonormal), and its Gaussian sketches have the distribution of D's."""
+    n = D.shape[0]
+    m = tall * n
+    ld = -(-m // 8) * 8
+    buf = torch.zeros((n, ld), dtype=torch.bfloat16, device=D.device)
+    Dt = (D * (1.0 / math.sqrt(tall))).t().to(torch.bfloat16)
+    for c in range(tall):
+        buf[:, c * n:(c + 1) * n] = Dt
+    return buf[:, :m].t()
+
+
 def evaluate_large(params, count, family, seed, tols=(1e-4, 1e-8), device="cuda", dims=(4096, 20000), block=64,
-                   max_pass_rows=4096):
-    """Held-out evaluation at scale on the FP64-accurate tensor-core path, whose
-    passes over A are a memory-bound stream: plain loop vs predictor-seeded loop
-    on the same matrices, wall time by CUDA events."""
+                   max_pass_rows=4096, precision="f64emu", tall=1):
+    """Held-out evaluation at scale: plain loop vs predictor-seeded loop on the
+    same matrices, wall time by CUDA events.  precision "f64emu": FP64 A on the
+    FP64-accurate tensor-core path (one CTA per 64 sketch rows and column tile,
+    so a pass of many blocks costs about as much as as many passes of one);
+    "bf16": the matrix rounded to BF16 with the FP32 LU, whose sketch reads A once
+    per pass however many blocks the pass holds (tolerances above BF16's 2^-8),
+    stacked `tall` times (tall_bf16) so that a pass over A outweighs a round's
+    factorisation work, as on the 100000 x 20000 configuration.  The seeded loop
+    saves passes over A, not rounds: each block is still factored on its own."""
+    if precision not in ("f64emu", "bf16"):
+        raise ValueError("precision must be 'f64emu' or 'bf16'")
     rng = np.random.default_rng(seed)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -177,8 +200,12 @@ def evaluate_large(params, count, family, seed, tols=(1e-4, 1e-8), device="cuda"
     for i in range(count):
         n = int(round(math.exp(rng.uniform(math.log(dims[0]), math.log(dims[1])))))
         A = sketch_equivalent(family, n, rng, g, device)
+        if precision == "bf16":
+            A = tall_bf16(A, tall)
         for tol in tols:
-            kw = dict(block=block, seed=seed + i, sketch_prec=B.F64_EMU)
+            kw = dict(block=block, seed=seed + i)
+            if precision == "f64emu":
+                kw["sketch_prec"] = B.F64_EMU
             B.id_adaptive(A, tol, **kw)  # warm-up (workspace, tuned launches)
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record()

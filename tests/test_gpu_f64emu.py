@@ -60,14 +60,10 @@ def test_emu_sketch_against_exact_product(B, case):
         A[17, 5] = -3.0
         Om = on_grid(rng.standard_normal((rows, m)))
     else:
-        # digits (d0..d6) = (63, -128, 127, -128, 127, -128, -128) of F = round(A 2^54)
-        # (E = 0: the column maximum is below 1); Omega = 16001 / 2048 (q1 = 63, q0 = -127),
-        # one sign per row and a sign flip on every third column: group g sums
-        # 512 (63 * 128 + 127 * 127) = 0.74 * 2^24 over each chunk
-        dg = [63, -128, 127, -128, 127, -128, -128]
-        F = sum(d * 256 ** (6 - q) for q, d in enumerate(dg))
-        A = np.full((m, n), F / 2.0 ** 54)
-        assert A[0, 0] * 2.0 ** 54 == F  # F is even and below 2^54: exact in FP64
+        # A = -0.99609375 = 2 (-127.5 / 256): digits d0 = -128, d1 = 128; Omega =
+        # 16001 / 2048 (q1 = 63, q0 = -127), one sign per row: group 1 sums
+        # 512 (127*128 + 63*128) = 0.74 * 2^24 over each chunk
+        A = np.full((m, n), -0.99609375)
         A[:, ::3] *= -1.0
         Om = np.full((rows, m), 16001.0 / 2048.0)
         Om[1::2] *= -1.0
@@ -148,6 +144,18 @@ def test_emu_generated_omega_matches_oracle_generator(B, orc):
     r, spread = oracle_x_spread(orc, A, lambda AA: orc.id_adaptive(AA, Om, b, thr))
     assert g.k == r["k"]
     assert_id_close(orc, A, g, r, spread)
+
+
+@pytest.mark.parametrize("seed,row0,rows,m", [(777, 0, 512, 40000), (3, 1000, 37, 9999), (2**63 + 5, 5, 130, 3001)])
+def test_emu_grid_rows_equal_oracle_generator(B, orc, seed, row0, rows, m):
+    """The FP64-accurate path's own Omega (FP32 Box-Muller, FP64 recomputation near
+    a rounding boundary of 2048 z) against the oracle's FP64 generator rounded to
+    the grid: every entry identical (20 million samples in the first case; a
+    misrounded sample would be 2^-11 off)."""
+    g = B.gaussian_rows(seed, row0, rows, m, grid=True).cpu().numpy()
+    o = on_grid(orc.gaussian_rows(seed, row0, rows, m))
+    bad = np.flatnonzero(g.ravel() != o.ravel())
+    assert bad.size == 0, (bad[:5], g.ravel()[bad[:5]], o.ravel()[bad[:5]])
 
 
 def test_emu_pass_size_does_not_change_result(B):

@@ -618,12 +618,12 @@ def sketch_roofline(name, m, n, b, passes, blocks, sk_ms, sk_launches):
     t = sk_ms * 1e-3
     if is_sparse(name):
         esz = {"f64": 8, "f64emu": 8, "f32": 4, "f32emu": 4, "bf16": 2}[dt]
-        # A once per pass, the codes of the pass's blocks (zeta bytes per column of A
-        # and block), the sketch block written
-        byts = esz * m * n * passes + 8.0 * m * rows / b + esz * n * rows
+        # A once per pass, the lists of the pass's blocks (2 bytes per nonzero: zeta
+        # per column of A and block), the sketch block written
+        byts = esz * m * n * passes + 2.0 * 8 * m * rows / b + esz * n * rows
         achieved = byts / t / 1e9
-        return {"bound": "hbm", "kernel": "k_sparse_sketch (sparse-sign gather-add, zeta = 8) + k_sparse_pattern "
-                "+ split-K reduce", "achieved": achieved, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+        return {"bound": "hbm", "kernel": "k_sparse_gather (sparse-sign gather-add, zeta = 8; lists from "
+                "k_sparse_csr) + split-K reduce", "achieved": achieved, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / PEAKS["hbm_gbs"], "traffic": PROFILED_TRAFFIC.get(name),
                 "algorithmic_bytes_per_step": byts, "sketch_launches_per_step": sk_launches,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}

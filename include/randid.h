@@ -353,6 +353,7 @@ int id_sparse_sign_rows(uint64_t seed, int64_t t0, int64_t blocks, int64_t b, in
    max|A(:,j)| per term, as the FP64-accurate tensor-core sketch), exact integer
    sums, one rounding to FP64 and one for the scale.  BF16 A needs an
    even leading dimension and a 4-byte aligned base (else ID_ERR_UNSUPPORTED).
+   At most 65535 blocks (rows <= 65535 b).
    ws: id_sparse_sketch_workspace_size bytes, 256-aligned. */
 int id_sparse_sketch_workspace_size(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, size_t* bytes);
 int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows, int64_t b, int64_t zeta, void* G,

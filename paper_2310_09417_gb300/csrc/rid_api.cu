@@ -76,6 +76,10 @@ int choose_splits_sgemm(int64_t M, int64_t N, int64_t K, int sms, int cap, int p
   return best;
 }
 
+// Input kind of the sparse-sign gather on path `path`: 1 for BF16 A, 2 for FP64 A
+// (its fixed-point copy), 0 for FP32 A.
+int sparse_kind(int path) { return path == 16 ? 1 : (path == 64 || path == 65 ? 2 : 0); }
+
 // Every size and offset of one call's workspace.
 struct Plan {
   int64_t m = 0, n = 0, b = 0, cap = 0, k = 0, l = 0;
@@ -201,11 +205,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     if (o->omega_rows < need) return kBadOpts;
   }
   const int64_t rows_max = imax(imax(p->rows_first, p->rows_pass), p->rows_pred);
+  if (p->sparse && cdiv(rows_max, b) > 65535) return ID_ERR_UNSUPPORTED;  // blocks of one sparse pass
   p->ldg = rows_max;
   // one split-K count for every pass (see Engine::splits_for): that of a pass of
   // one block (adaptive) or of the l rows (fixed rank)
   const int64_t unit = l > 0 ? l : b;
-  const int s1 = p->sparse ? sparse_splits(p->m, p->n, p->sms)
+  const int s1 = p->sparse ? sparse_splits(p->m, p->n, p->sms, sparse_kind(path))
                  : path == 16 ? tc_sketch_effective_splits(p->m, tc_sketch_splits(p->m, p->n, unit, p->sms))
                  : path == 8  ? tc_fp8_effective_splits(p->m, tc_fp8_splits(p->m, p->n, unit, p->sms))
                  : path == 65 ? f64emu_splits(p->m, p->n, p->sms)
@@ -232,10 +237,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
   // path 65 keeps two digit planes of Omega, also for a caller Omega (rounded to its grid)
   // (sparse sign: the zeta codes of every column of the pass's blocks)
   p->off_omega = take(path == 65 ? 2 * (size_t)rows_max * p->ldw * p->wsz
-                                 : (p->sparse ? (size_t)cdiv(rows_max, b) * p->m * p->zeta
+                                 : (p->sparse ? sparse_csr_bytes(p->m, (int)cdiv(rows_max, b), (int)b, (int)p->zeta)
                                               : (p->gen_omega ? (size_t)rows_max * p->ldw * p->wsz : 0)));
   p->off_G = take((size_t)p->n * rows_max * e);
-  p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * e : 0);
+  // (the fixed-point sparse sketch of FP64 A keeps exact 128-bit split partials)
+  const bool sfix_parts = p->sparse && (path == 64 || path == 65);
+  p->off_Gpart = take(s1 > 1 ? (size_t)s1 * p->n * rows_max * (sfix_parts ? 16 : e) : 0);
   p->off_S = take((size_t)p->n * p->wmax * e);
   p->off_Spart = take((size_t)p->s2max * p->n * p->wmax * e);
   p->off_N = take((size_t)p->n * b * e);
@@ -571,7 +578,7 @@ class Engine {
   // (k0, blocks_per_pass, the learned predictor) leaves J, X and k bit-identical.
   int splits_for(int64_t /*rows*/) {
     const int64_t unit = p_.l > 0 ? p_.l : p_.b;
-    if (p_.sparse) return sparse_splits(p_.m, p_.n, p_.sms);
+    if (p_.sparse) return sparse_splits(p_.m, p_.n, p_.sms, sparse_kind(p_.path));
     if (p_.path == 16) return tc_sketch_effective_splits(p_.m, tc_sketch_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 8) return tc_fp8_effective_splits(p_.m, tc_fp8_splits(p_.m, p_.n, unit, p_.sms));
     if (p_.path == 65) return f64emu_splits(p_.m, p_.n, p_.sms);
@@ -612,31 +619,30 @@ class Engine {
     return 0;
   }
 
-  // Sparse-sign rows [row0, row0+rows) (Sec. 5.1): the zeta codes of each column of
-  // the pass's blocks, then the gather-add G = Omega A in A's own type (FP32 sums
-  // for BF16 A).
+  // Sparse-sign rows [row0, row0+rows) (Sec. 5.1): the lists of the pass's blocks
+  // per 128-row tile of A, then the gather-add G = Omega A (FP32 sums for FP32 and
+  // BF16 A, exact integer sums of the fixed-point copy of FP64 A).
   int sketch_sparse(int64_t row0, int64_t rows, int splits) {
     const int64_t b = p_.b;
-    uint8_t* P = reinterpret_cast<uint8_t*>(omega_);
+    uint16_t* R = reinterpret_cast<uint16_t*>(omega_);
     RID_TRY(tbegin(ID_PHASE_OMEGA));
-    RID_TRY(cuda(sparse_pattern(o_.seed, row0 / b, (int)cdiv(rows, b), (int)b, p_.m, (int)p_.zeta, P, done_, s_)));
+    RID_TRY(cuda(sparse_csr(o_.seed, row0 / b, (int)cdiv(rows, b), (int)b, p_.m, (int)p_.zeta, R, done_, s_)));
     RID_TRY(tend(1));
     RID_TRY(tbegin(ID_PHASE_SKETCH));
-    T* out = splits > 1 ? Gpart_ : G_;
     const int64_t zs = (int64_t)p_.n * p_.ldg;
     if constexpr (std::is_same<T, float>::value) {
+      T* out = splits > 1 ? Gpart_ : G_;
       if (p_.path == 16)
-        RID_TRY(cuda(sparse_sketch<__nv_bfloat16, float>(p_.m, p_.n, static_cast<const __nv_bfloat16*>(Araw_), lda_, P,
-                                                         (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs, done_,
-                                                         s_)));
+        RID_TRY(cuda(sparse_sketch<__nv_bfloat16>(p_.m, p_.n, static_cast<const __nv_bfloat16*>(Araw_), lda_, R,
+                                                  (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs, done_, s_)));
       else
-        RID_TRY(cuda(sparse_sketch<float, float>(p_.m, p_.n, A_, lda_, P, (int)p_.zeta, (int)b, rows, splits, out,
-                                                 p_.ldg, zs, done_, s_)));
-    } else {  // exact integer sums of the fixed-point copy
-      RID_TRY(cuda(sparse_sketch_fixed(p_.m, p_.n, sfix_, sfix_col_, P, (int)p_.zeta, (int)b, rows, splits,
-                                       reinterpret_cast<double*>(out), p_.ldg, zs, done_, s_)));
+        RID_TRY(cuda(sparse_sketch<float>(p_.m, p_.n, A_, lda_, R, (int)p_.zeta, (int)b, rows, splits, out, p_.ldg, zs,
+                                          done_, s_)));
+      if (splits > 1) RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, zs, Gpart_, G_, done_, s_)));
+    } else {  // exact integer sums of the fixed-point copy (128-bit split partials)
+      RID_TRY(cuda(sparse_sketch_fixed(p_.m, p_.n, sfix_, sfix_col_, R, (int)p_.zeta, (int)b, rows, splits, G_, p_.ldg,
+                                       Gpart_, p_.ldg, zs, done_, s_)));
     }
-    if (splits > 1) RID_TRY(cuda(splitk_reduce<T>(p_.n, (int)rows, p_.ldg, splits, zs, Gpart_, G_, done_, s_)));
     RID_TRY(tend(splits > 1 ? 2 : 1));
     ++passes_;
     return 0;
@@ -1301,7 +1307,9 @@ int id_sketch(const id_matrix* A, const void* omega, int64_t ld_omega, int64_t r
 }
 
 namespace {
-// Workspace of id_sparse_sketch: a DevState, the zeta codes of the blocks, the split-K partials.
+// Workspace of id_sparse_sketch: a DevState, the per-tile lists of the blocks, the
+// split-K partials (16-byte exact integers for FP64 A), then for FP64 A its
+// fixed-point copy and column exponents.
 int sparse_sketch_plan(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta, int* splits, size_t* off_parts,
                        size_t* bytes) {
   if (A == nullptr || A->data == nullptr || A->m < 1 || A->n < 1 || A->ld < A->m || A->m >= ((int64_t)1 << 31) ||
@@ -1311,10 +1319,12 @@ int sparse_sketch_plan(const id_matrix* A, int64_t rows, int64_t b, int64_t zeta
   if (rows < 1 || rows > ((int64_t)1 << 20)) return -2;
   if (b < 1 || b > kSparseMaxB) return -3;
   if (zeta < 1 || zeta > b) return -4;
-  *splits = sparse_splits(A->m, A->n, num_sms());
-  const size_t esz = A->dtype == ID_F64 ? 8 : 4;
-  *off_parts = 256 + align_up((size_t)cdiv(rows, b) * A->m * zeta);
-  *bytes = *off_parts + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * esz) : 0);
+  if (cdiv(rows, b) > 65535) return -2;
+  const int kind = A->dtype == ID_F64 ? 2 : (A->dtype == ID_BF16 ? 1 : 0);
+  *splits = sparse_splits(A->m, A->n, num_sms(), kind);
+  const size_t psz = A->dtype == ID_F64 ? 16 : 4;
+  *off_parts = 256 + align_up(sparse_csr_bytes(A->m, (int)cdiv(rows, b), (int)b, (int)zeta));
+  *bytes = *off_parts + (*splits > 1 ? align_up((size_t)*splits * A->n * rows * psz) : 0);
   if (A->dtype == ID_F64)  // the fixed-point copy of A and its column exponents follow
     *bytes += align_up((size_t)A->m * A->n * 8) + align_up((size_t)A->n * 4);
   return ID_OK;
@@ -1343,32 +1353,27 @@ int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows
     return ID_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* w = static_cast<unsigned char*>(ws);
-  uint8_t* P = w + 256;
+  uint16_t* R = reinterpret_cast<uint16_t*>(w + 256);
   void* part = w + off;
   const int64_t zs = A->n * rows;
-  cudaError_t e = sparse_pattern(seed, t0, (int)cdiv(rows, b), (int)b, A->m, (int)zeta, P, nullptr, s);
+  cudaError_t e = sparse_csr(seed, t0, (int)cdiv(rows, b), (int)b, A->m, (int)zeta, R, nullptr, s);
   if (e == cudaSuccess) {
     if (A->dtype == ID_F64) {
-      double* out = splits > 1 ? static_cast<double*>(part) : static_cast<double*>(G);
-      unsigned char* fx = w + off + (splits > 1 ? align_up((size_t)splits * A->n * rows * 8) : 0);
+      unsigned char* fx = w + off + (splits > 1 ? align_up((size_t)splits * A->n * rows * 16) : 0);
       long long* F = reinterpret_cast<long long*>(fx);
       int32_t* col = reinterpret_cast<int32_t*>(fx + align_up((size_t)A->m * A->n * 8));
       e = sparse_fixed_prepare(static_cast<const double*>(A->data), A->ld, A->m, A->n, col, F, s);
       if (e == cudaSuccess)
-        e = sparse_sketch_fixed(A->m, A->n, F, col, P, (int)zeta, (int)b, rows, splits, out,
-                                splits > 1 ? rows : ldg, zs, nullptr, s);
-      if (e == cudaSuccess && splits > 1)
-        e = splitk_reduce_ld<double>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<double*>(part),
-                                     static_cast<double*>(G), nullptr, s);
+        e = sparse_sketch_fixed(A->m, A->n, F, col, R, (int)zeta, (int)b, rows, splits, static_cast<double*>(G), ldg,
+                                part, rows, zs, nullptr, s);
     } else {
       float* out = splits > 1 ? static_cast<float*>(part) : static_cast<float*>(G);
       if (A->dtype == ID_F32)
-        e = sparse_sketch<float, float>(A->m, A->n, static_cast<const float*>(A->data), A->ld, P, (int)zeta, (int)b,
-                                        rows, splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
+        e = sparse_sketch<float>(A->m, A->n, static_cast<const float*>(A->data), A->ld, R, (int)zeta, (int)b, rows,
+                                 splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
       else
-        e = sparse_sketch<__nv_bfloat16, float>(A->m, A->n, static_cast<const __nv_bfloat16*>(A->data), A->ld, P,
-                                                (int)zeta, (int)b, rows, splits, out, splits > 1 ? rows : ldg, zs,
-                                                nullptr, s);
+        e = sparse_sketch<__nv_bfloat16>(A->m, A->n, static_cast<const __nv_bfloat16*>(A->data), A->ld, R, (int)zeta,
+                                         (int)b, rows, splits, out, splits > 1 ? rows : ldg, zs, nullptr, s);
       if (e == cudaSuccess && splits > 1)
         e = splitk_reduce_ld<float>(A->n, (int)rows, rows, ldg, splits, zs, static_cast<float*>(part),
                                     static_cast<float*>(G), nullptr, s);

@@ -263,30 +263,36 @@ cudaError_t ur_extract(int p, int na, const T* S, int64_t lds, const int32_t* pi
                        int64_t ldu, int64_t* Jx, double* stats, cudaStream_t s);
 
 // ---- sparse-sign sketch (rid_sparse.cu; Sec. 5.1 "Sparse Sign").  Blocks of b <=
-// kSparseMaxB rows with zeta nonzeros +-sqrt(b/zeta) per column.  sparse_pattern
-// writes the zeta codes (row | sign << 7) of every column of `blocks` blocks from
-// block t0 on (blocks x m x zeta bytes); sparse_sketch forms split z of (Omega A)^T
-// (n x rows, row stride out_ld) in out[z] from those codes for rows = the pass's
-// rows (the last block may be cut short); sparse_dense writes the blocks as dense
-// rows (row-major, row stride ld).
+// kSparseMaxB rows with zeta nonzeros +-sqrt(b/zeta) per column.  sparse_csr writes,
+// for `blocks` blocks from block t0 on, one list record per 128-row tile of A and
+// block (sparse_csr_bytes in all); sparse_sketch forms split z of (Omega A)^T
+// (n x rows, row stride out_ld) in out + z zstride from those lists for rows = the
+// pass's rows (the last block may be cut short); sparse_dense writes the blocks as
+// dense rows (row-major, row stride ld).  Split counts: sparse_splits, kind 0 for
+// FP32 A, 1 for BF16, 2 for FP64 (fixed point).
 constexpr int kSparseMaxB = 128;
-int sparse_splits(int64_t m, int64_t n, int sms);
-cudaError_t sparse_pattern(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint8_t* P,
-                           const int32_t* done, cudaStream_t s);
-template <typename TA, typename TC>
-cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                          int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride, const int32_t* done,
+int sparse_splits(int64_t m, int64_t n, int sms, int kind);
+int sparse_csr_head(int b);
+int sparse_csr_rec(int b, int zeta);
+size_t sparse_csr_bytes(int64_t m, int blocks, int b, int zeta);
+cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint16_t* R,
+                       const int32_t* done, cudaStream_t s);
+template <typename TA>
+cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint16_t* R, int zeta, int b,
+                          int64_t rows, int splits, float* out, int64_t out_ld, int64_t zstride, const int32_t* done,
                           cudaStream_t s);
 template <typename T>
 cudaError_t sparse_dense(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, T* out, int64_t ld,
                          cudaStream_t s);
 // FP64 input: column exponents and the 64-bit fixed-point copy F (m x n, ld m) made
-// once per call, then exact 128-bit sums rounded once to FP64.
+// once per call; the sketch's entries are exact integer sums rounded once to FP64.
+// With splits > 1 the 128-bit partials go to parts (16 bytes each, split z at
+// z zstride, row stride pld) and are summed exactly into out.
 cudaError_t sparse_fixed_prepare(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* colexp, long long* F,
                                  cudaStream_t s);
-cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint8_t* P,
-                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld,
-                                int64_t zstride, const int32_t* done, cudaStream_t s);
+cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint16_t* R,
+                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld, void* parts,
+                                int64_t pld, int64_t zstride, const int32_t* done, cudaStream_t s);
 // e_j with |A(:, j)| < 2^e_j (0 for a zero column), by a reduction over each column.
 cudaError_t f64_colexp(const double* A, int64_t lda, int64_t m, int64_t n, int32_t* E, cudaStream_t s);
 

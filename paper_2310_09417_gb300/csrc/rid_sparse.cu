@@ -12,20 +12,24 @@
 // E[Omega^T Omega] = b I, as for N(0,1) rows, so E = ||S||_F / sqrt(b) keeps
 // its meaning.
 //
-// The sketch: k_sparse_pattern writes each column's zeta codes (row | sign << 7)
-// once per pass; k_sparse_sketch stages a 256 x 32 tile of A in shared memory,
-// turns the tile's codes into per-row bit masks (which tile rows hit sketch row
-// r, and with which sign), and a warp per sketch row walks its mask in ascending
-// order with one lane per column of A -- a fixed summation order, no atomics on
-// the sums, and one read of A per pass.
+// The sketch, per pass: k_sparse_csr builds, once per 128-row tile of A and block
+// of Omega, the tile's list for every sketch row r (the tile rows i with a nonzero
+// in row r, positive ones first, each part in ascending i: a fixed order, no
+// atomics on sums); k_sparse_gather stages a 128-row tile of A in shared memory
+// (cp.async, double-buffered, with the next tile's lists) and sums, per sketch row
+// and column of A, the listed tile entries, two columns per lane.  A is read once
+// per pass; the lists (2 bytes per nonzero) are built once per pass, not once per
+// column tile.  Split z of the tiles writes its own partial; the split count
+// depends on (m, n) only, so the sums do not depend on how many blocks a pass holds.
 //
 // FP64 input is summed exactly in integers: GB300 issues about two FP64
 // instructions per clock per SM, and each element of A feeds zeta sums.  A is
 // converted once per call to fixed point per column (F = round(A 2^(54-e)) for
 // |A| < 2^e, an error of at most 2^-55 max|A(:,j)| per term, as the digits of the
 // FP64-accurate tensor-core sketch), every entry of the sketch is the exact
-// integer sum of +-F (int64 within a tile, 128 bits across tiles), and one
-// conversion rounds it to FP64 (then the scale sqrt(b/zeta), one more rounding).
+// integer sum of +-F (int64 within a tile, 128 bits across tiles and across the
+// splits, whose 128-bit partials are added exactly), and one conversion rounds it
+// to FP64 (then the scale sqrt(b/zeta), one more rounding).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,10 +39,9 @@
 
 namespace rid {
 
-constexpr int kSpI = 256;       // rows of A per tile
-constexpr int kSpJ = 32;        // columns of A per tile (one per lane)
-constexpr int kSpThreads = 256; // eight warps
-constexpr int kSpWords = kSpI / 32;
+constexpr int kSpT = 128;         // rows of A per tile (one list per tile and block)
+constexpr int kSpTW = kSpT / 32;  // mask words per tile
+constexpr int kSpThreads = 256;   // eight warps
 
 // zeta codes of column i of block t: row | (negative << 7), rows distinct.
 __device__ __forceinline__ void sparse_column(uint64_t seed, int64_t t, int64_t i, int b, int zeta,
@@ -61,30 +64,6 @@ __device__ __forceinline__ void sparse_column(uint64_t seed, int64_t t, int64_t 
     p[r] = tmp;
     codes[j] = (uint8_t)(p[j] | ((u & 1ull) << 7));
   }
-}
-
-__global__ void k_sparse_pattern(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta,
-                                 uint8_t* __restrict__ P, const int32_t* done) {
-  if (done != nullptr && *done) return;
-  const int64_t total = (int64_t)blocks * m;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = e / m, i = e - t * m;
-    uint8_t c[kSparseMaxB];
-    sparse_column(seed, t0 + t, i, b, zeta, c);
-    uint8_t* o = P + e * zeta;
-    for (int j = 0; j < zeta; ++j) o[j] = c[j];
-  }
-}
-
-cudaError_t sparse_pattern(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint8_t* P,
-                           const int32_t* done, cudaStream_t s) {
-  if (b < 1 || b > kSparseMaxB || zeta < 1 || zeta > b) return cudaErrorInvalidValue;
-  const int64_t total = (int64_t)blocks * m;
-  int64_t g = (total + 255) / 256;
-  if (g > 4096) g = 4096;
-  if (g < 1) g = 1;
-  k_sparse_pattern<<<(int)g, 256, 0, s>>>(seed, t0, blocks, b, m, zeta, P, done);
-  return cudaGetLastError();
 }
 
 // Dense rows of the sparse-sign matrix: block t0 + q at rows q*b .. q*b+b-1 of out
@@ -114,45 +93,6 @@ cudaError_t sparse_dense(uint64_t seed, int64_t t0, int blocks, int b, int64_t m
   const T v = (T)sqrt((double)b / (double)zeta);
   k_sparse_dense<T><<<(int)g, 256, 0, s>>>(seed, t0, blocks, b, m, zeta, v, out, ld);
   return cudaGetLastError();
-}
-
-__device__ __forceinline__ float load_as_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ float load_as_f(const float* p) { return *p; }
-__device__ __forceinline__ double load_as_f(const double* p) { return *p; }
-__device__ __forceinline__ long long load_as_f(const long long* p) { return *p; }
-
-// The accumulator of an entry and its final value: FP32 sums for FP32 / BF16 input;
-// for the fixed-point FP64 input, exact int64 sums within a tile (a sketch row takes
-// at most one term per tile row: 256 terms below 2^54 each stay below 2^62) folded
-// into an exact 128-bit total once per tile.
-template <typename TS>
-struct SpAcc {
-  using part = TS;
-  using type = TS;
-};
-template <>
-struct SpAcc<long long> {
-  using part = long long;
-  using type = __int128;
-};
-// s + a or s - a, branch-free: the sign flips a's sign bit (float) or negates by mask (int64)
-__device__ __forceinline__ float sp_add(float s, float a, uint32_t neg) {
-  return s + __int_as_float(__float_as_int(a) ^ (int)(neg << 31));
-}
-__device__ __forceinline__ long long sp_add(long long s, long long a, uint32_t neg) {
-  const long long msk = -(long long)neg;
-  return s + ((a ^ msk) - msk);
-}
-template <typename TS, typename TO>
-__device__ __forceinline__ TO sp_final(typename SpAcc<TS>::type s, TO v, int ex) {
-  if constexpr (sizeof(TS) == 8) {
-    // s 2^ex: |s| < 2^54 times the terms (< 2^74), so s >> 32 fits 64 bits
-    const long long hi = (long long)(s >> 32);
-    const long long lo = (long long)(s & (__int128)0xFFFFFFFFll);
-    return tcx::fixed_to_double(hi, lo, ex) * v;
-  } else {
-    return s * v;
-  }
 }
 
 // F(i, j) = round(A(i, j) 2^(54 - e_j)) with |A(:, j)| < 2^e_j (column-major, ld m):
@@ -189,60 +129,195 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ float tile_value(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ float tile_value(const float* p) { return *p; }
-__device__ __forceinline__ long long tile_value(const long long* p) { return *p; }
+// ------------------------------------------------------------------ per-tile lists
+// Record of one (tile, block), in uint16: a head of sparse_csr_head(b) entries,
+// head[r] = first list entry of sketch row r (r = 0 .. b; head[b] = the tile's
+// count) and head[b + 1 + r] = first negative entry of row r, then the list: the
+// tile rows i (0 .. kSpT-1) of row r's nonzeros, positive ones first, each part in
+// ascending i.  Head and list are padded to 16-byte multiples.
+int sparse_csr_head(int b) { return (2 * b + 1 + 7) / 8 * 8; }
+int sparse_csr_rec(int b, int zeta) { return sparse_csr_head(b) + (kSpT * zeta + 7) / 8 * 8; }
+size_t sparse_csr_bytes(int64_t m, int blocks, int b, int zeta) {
+  return (size_t)((m + kSpT - 1) / kSpT) * blocks * sparse_csr_rec(b, zeta) * 2;
+}
 
-// out[z][j][t*b + r] (row stride out_ld) = sqrt(b/zeta) * sum over the rows i of
-// split z with a code for sketch row r of block t: sign * A(i, j).  Grid: x over
-// 32-column tiles of A, y over groups of TG blocks, z over splits of the rows of A
-// (ktiles tiles of 256 rows each).  Per tile (the next one already in flight by
-// cp.async into the other buffer):
-//   1. per-row bit masks of the tile rows that hit each sketch row of the group
-//      (word-major, so a warp's 32 tile rows spread over the banks);
-//   2. the codes sorted by sketch row into a CSR list, ascending tile row within a
-//      row (rank = popcount of the row's mask below the bit): a fixed order;
-//   3. warp w sums rows r = w + 8q of every block of the group, lane = column,
-//      four list entries at a time.
-// Sketch rows t*b + r >= rows (a last block cut short) are not written.
-template <typename TA, typename TS, typename TO, int RPW>
-__global__ void __launch_bounds__(kSpThreads, sizeof(TS) == 8 ? 1 : 2)
-    k_sparse_sketch(int64_t m, int64_t n, const TA* __restrict__ A, int64_t lda, const uint8_t* __restrict__ P,
-                    int zeta, int b, int blocks, int64_t rows, int ktiles, TO* __restrict__ out, int64_t out_ld,
-                    int64_t zstride, TO v, const int32_t* __restrict__ colexp, const int32_t* done) {
-  using TC = decltype(tile_value((const TS*)nullptr));
-  using Acc = typename SpAcc<TC>::type;
-  constexpr int TG = (sizeof(Acc) > 8 ? 16 : 32) / RPW;  // blocks per CTA
-  constexpr int NR = TG * 8 * RPW;                         // sketch rows of the group (padded)
-  constexpr int LDT = kSpI + (sizeof(TS) == 2 ? 2 : 1);    // tile row stride (elements)
+// One CTA per (tile, block): the codes of the tile's columns of Omega (Philox, the
+// partial Fisher-Yates shuffle), a bit mask per key (row r, sign) over the tile's
+// rows, an exclusive scan of the keys' counts, and each entry placed at its key's
+// start plus the number of tile rows below it with the same key.
+__global__ void __launch_bounds__(kSpThreads)
+    k_sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, int rec, int head,
+                 uint16_t* __restrict__ R, const int32_t* done) {
   if (done != nullptr && *done) return;
-  extern __shared__ __align__(16) unsigned char sp_raw[];
-  TS* tiles = reinterpret_cast<TS*>(sp_raw);                                  // [2][kSpJ][LDT]
-  uint32_t* mask = reinterpret_cast<uint32_t*>(tiles + 2 * kSpJ * LDT);      // [kSpWords][NR]
-  uint32_t* negm = mask + kSpWords * NR;                                      // [kSpWords][NR]
-  int* woff = reinterpret_cast<int*>(negm + kSpWords * NR);                   // [NR][kSpWords + 1]
-  uint16_t* list = reinterpret_cast<uint16_t*>(woff + NR * (kSpWords + 1));  // [TG * kSpI * zeta]
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t j0 = (int64_t)blockIdx.x * kSpJ;
-  const int tg0 = blockIdx.y * TG;
-  const int ng = min(TG, blocks - tg0);
-  const int64_t itile0 = (int64_t)blockIdx.z * ktiles;
-  const int64_t ntiles = (m + kSpI - 1) / kSpI;
-  const int64_t itile1 = min(ntiles, itile0 + ktiles);
-  Acc acc[TG * RPW];
+  extern __shared__ __align__(16) unsigned char cs_raw[];
+  uint32_t* mask = reinterpret_cast<uint32_t*>(cs_raw);          // [2b][kSpTW], key = 2 r + negative
+  int* woff = reinterpret_cast<int*>(mask + 2 * b * kSpTW);       // [2b][kSpTW]: first position per word
+  uint8_t* codes = reinterpret_cast<uint8_t*>(woff + 2 * b * kSpTW);  // [kSpT][zeta]
+  const int tid = threadIdx.x;
+  const int64_t tile = blockIdx.x;
+  const int q = blockIdx.y;
+  const int64_t i = tile * kSpT + tid;
+  uint16_t* out = R + (tile * blocks + q) * (int64_t)rec;
+  for (int e = tid; e < 2 * b * kSpTW; e += kSpThreads) mask[e] = 0u;
+  __syncthreads();
+  if (tid < kSpT && i < m) {
+    uint8_t* c = codes + tid * zeta;
+    sparse_column(seed, t0 + q, i, b, zeta, c);
+    for (int z = 0; z < zeta; ++z) {
+      const int key = 2 * (c[z] & 127) + (c[z] >> 7);
+      atomicOr(&mask[key * kSpTW + (tid >> 5)], 1u << (tid & 31));
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    int carry = 0;
+    for (int k0 = 0; k0 < 2 * b; k0 += 32) {
+      const int key = k0 + tid;
+      int cnt[kSpTW];
+      int tot = 0;
 #pragma unroll
-  for (int u = 0; u < TG * RPW; ++u) acc[u] = Acc(0);
+      for (int w = 0; w < kSpTW; ++w) {
+        cnt[w] = key < 2 * b ? __popc(mask[key * kSpTW + w]) : 0;
+        tot += cnt[w];
+      }
+      int incl = tot;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (tid >= off) incl += y;
+      }
+      int base = carry + incl - tot;
+      if (key < 2 * b) {
+        out[(key & 1) ? b + 1 + (key >> 1) : (key >> 1)] = (uint16_t)base;
+#pragma unroll
+        for (int w = 0; w < kSpTW; ++w) {
+          woff[key * kSpTW + w] = base;
+          base += cnt[w];
+        }
+      }
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (tid == 0) out[b] = (uint16_t)carry;
+    for (int e = 2 * b + 1 + tid; e < head; e += 32) out[e] = 0;
+  }
+  __syncthreads();
+  if (tid < kSpT && i < m) {
+    const uint8_t* c = codes + tid * zeta;
+    const uint32_t below = (1u << (tid & 31)) - 1u;
+    for (int z = 0; z < zeta; ++z) {
+      const int key = 2 * (c[z] & 127) + (c[z] >> 7);
+      const int w = key * kSpTW + (tid >> 5);
+      out[head + woff[w] + __popc(mask[w] & below)] = (uint16_t)tid;
+    }
+  }
+}
 
-  // tile it of A into buffer bf: a warp per column, lanes along the rows
+cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint16_t* R,
+                       const int32_t* done, cudaStream_t s) {
+  if (b < 1 || b > kSparseMaxB || zeta < 1 || zeta > b || blocks < 1 || m < 1) return cudaErrorInvalidValue;
+  const int64_t tiles = (m + kSpT - 1) / kSpT;
+  if (tiles > 0x7FFFFFFFll || blocks > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * 2 * b * kSpTW * 4 + (size_t)kSpT * zeta;
+  k_sparse_csr<<<dim3((unsigned)tiles, (unsigned)blocks), kSpThreads, smem, s>>>(
+      seed, t0, blocks, b, m, zeta, sparse_csr_rec(b, zeta), sparse_csr_head(b), R, done);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ the gather-add
+// Staged element, partial-sum and accumulator types: FP32 sums for FP32 and BF16 A
+// (two columns per lane); for the fixed-point copy of FP64 A, exact int64 sums
+// within a tile (a sketch row takes at most one term per tile row: 128 terms below
+// 2^54 each) folded into 128-bit totals (one column per lane).
+template <typename TS>
+struct SpT;
+template <>
+struct SpT<float> {
+  using Part = float;
+  using Acc = float;
+  using Out = float;
+  static constexpr int C = 2, LDT = kSpT + 1, REGS = 64;
+};
+template <>
+struct SpT<__nv_bfloat16> {
+  using Part = float;
+  using Acc = float;
+  using Out = float;
+  static constexpr int C = 2, LDT = kSpT + 2, REGS = 64;  // element pairs stay 4-byte aligned
+};
+template <>
+struct SpT<long long> {
+  using Part = long long;
+  using Acc = __int128;
+  using Out = double;
+  static constexpr int C = 1, LDT = kSpT + 1, REGS = 64;
+};
+// blocks of a pass one CTA sums (its accumulators: TG x RPW x C, at most REGS registers)
+template <typename TS, int RPW>
+__host__ __device__ constexpr int sp_group() {
+  constexpr int per = (int)(sizeof(typename SpT<TS>::Acc) / 4) * RPW * SpT<TS>::C;
+  constexpr int g = SpT<TS>::REGS / per;
+  return g < 1 ? 1 : (g > 4 ? 4 : g);
+}
+__device__ __forceinline__ float sp_val(const float* p) { return *p; }
+__device__ __forceinline__ float sp_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ long long sp_val(const long long* p) { return *p; }
+__device__ __forceinline__ double i128_to_double(__int128 s, int ex) {
+  // |s| < 2^95: s >> 32 fits 64 bits
+  return tcx::fixed_to_double((long long)(s >> 32), (long long)(s & (__int128)0xFFFFFFFFll), ex);
+}
+template <typename TS>
+__host__ __device__ constexpr size_t sp_tile_bytes() {
+  return ((size_t)2 * 32 * SpT<TS>::C * SpT<TS>::LDT * sizeof(TS) + 15) / 16 * 16;
+}
+
+// Split z (tiles [z ktiles, (z+1) ktiles) of A's rows) of the sketch rows of blocks
+// [tg0, tg0 + gsize) for the columns [j0, j0 + 32 C).  Per tile (the next one and
+// its lists already in flight by cp.async into the other buffers): warp w sums the
+// sketch rows r = w + 8q of each block, lane = column, the row's positive entries
+// then its negative ones, four at a time into two partials per column (a fixed
+// order).  FP32 output: out[z zstride + j out_ld + row] = sqrt(b/zeta) * sum.
+// Fixed point: with one split the rounded FP64 value goes to out; otherwise the
+// exact 128-bit sum to parts[z zstride + j out_ld + row].
+template <typename TS, int RPW>
+__global__ void __launch_bounds__(kSpThreads, 2)
+    k_sparse_gather(int64_t m, int64_t n, const TS* __restrict__ A, int64_t lda, const uint16_t* __restrict__ R,
+                    int rec, int head, int b, int blocks, int gsize, int64_t rows, int ktiles,
+                    typename SpT<TS>::Out* __restrict__ out, typename SpT<TS>::Acc* __restrict__ parts,
+                    int64_t out_ld, int64_t zstride, typename SpT<TS>::Out v, const int32_t* __restrict__ colexp,
+                    const int32_t* done) {
+  using Part = typename SpT<TS>::Part;
+  using Acc = typename SpT<TS>::Acc;
+  constexpr int C = SpT<TS>::C, LDT = SpT<TS>::LDT, JT = 32 * C;
+  constexpr int TG = sp_group<TS, RPW>();
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char sg_raw[];
+  TS* tiles = reinterpret_cast<TS*>(sg_raw);                                    // [2][JT][LDT]
+  uint16_t* recs = reinterpret_cast<uint16_t*>(sg_raw + sp_tile_bytes<TS>());  // [2][gsize][rec]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * JT;
+  const int tg0 = blockIdx.y * gsize;
+  const int ng = min(gsize, blocks - tg0);
+  const int64_t ntiles = (m + kSpT - 1) / kSpT;
+  const int64_t it0 = (int64_t)blockIdx.z * ktiles;
+  const int64_t it1 = min(ntiles, it0 + ktiles);
+  Acc acc[TG][RPW][C];
+#pragma unroll
+  for (int t = 0; t < TG; ++t)
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[t][q][c] = Acc(0);
+
+  // tile it of A (a warp per column, lanes along the rows) and the group's lists
   auto issue = [&](int64_t it, int bf) {
-    const int64_t i0 = it * kSpI;
-    for (int jj = wid; jj < kSpJ; jj += kSpThreads / 32) {
+    const int64_t i0 = it * kSpT;
+    for (int jj = wid; jj < JT; jj += kSpThreads / 32) {
       const int64_t j = j0 + jj;
-      TS* dst = tiles + (bf * kSpJ + jj) * LDT;
-      const TA* src = A + (j < n ? j : 0) * lda + i0;
+      TS* dst = tiles + ((size_t)bf * JT + jj) * LDT;
+      const TS* src = A + (j < n ? j : 0) * lda + i0;
       if constexpr (sizeof(TS) == 2) {  // BF16 pairs
 #pragma unroll
-        for (int q = 0; q < kSpI / 64; ++q) {
+        for (int q = 0; q < kSpT / 64; ++q) {
           const int ii = 2 * (lane + 32 * q);
           const int64_t left = j < n ? m - (i0 + ii) : 0;
           const int bytes = left >= 2 ? 4 : (left == 1 ? 2 : 0);
@@ -250,134 +325,138 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(TS) == 8 ? 1 : 2)
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < kSpWords; ++q) {
+        for (int q = 0; q < kSpTW; ++q) {
           const int ii = lane + 32 * q;
           const bool in = j < n && i0 + ii < m;
           cp_async<sizeof(TS)>(dst + ii, in ? (const void*)(src + ii) : (const void*)A, in ? (int)sizeof(TS) : 0);
         }
       }
     }
+    const uint16_t* rsrc = R + (it * blocks + tg0) * (int64_t)rec;
+    uint16_t* rdst = recs + (size_t)bf * gsize * rec;
+    const int pieces = ng * rec / 8;  // rec is a multiple of 8 entries (16 bytes)
+    for (int e = tid; e < pieces; e += kSpThreads) cp_async<16>(rdst + 8 * e, rsrc + 8 * e, 16);
     cp_async_commit();
   };
 
-  if (itile0 < itile1) issue(itile0, 0);
-  for (int64_t it = itile0; it < itile1; ++it) {
-    const int cur = (int)((it - itile0) & 1);
-    const int64_t i0 = it * kSpI;
-    if (it + 1 < itile1) {
+  if (it0 < it1) issue(it0, 0);
+  for (int64_t it = it0; it < it1; ++it) {
+    const int cur = (int)((it - it0) & 1);
+    if (it + 1 < it1) {
       issue(it + 1, cur ^ 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    // 1. masks
-    for (int e = tid; e < 2 * kSpWords * NR; e += kSpThreads) mask[e] = 0u;
     __syncthreads();
-    for (int e = tid; e < ng * kSpI; e += kSpThreads) {
-      const int t = e / kSpI, ii = e - t * kSpI;
-      const int64_t i = i0 + ii;
-      if (i >= m) continue;
-      const uint8_t* c = P + ((int64_t)(tg0 + t) * m + i) * zeta;
-      const uint32_t bit = 1u << (ii & 31);
-      for (int jz = 0; jz < zeta; ++jz) {
-        const int code = c[jz];
-        const int slot = (ii >> 5) * NR + t * 8 * RPW + (code & 127);
-        atomicOr(&mask[slot], bit);
-        if (code & 128) atomicOr(&negm[slot], bit);
-      }
-    }
-    __syncthreads();
-    // 2. row offsets (an exclusive scan of the rows' counts, one warp), then the list
-    if (wid == 0) {
-      int carry = 0;
-      for (int r0 = 0; r0 < NR; r0 += 32) {
-        const int r = r0 + lane;
-        int cnt[kSpWords];
-        int tot = 0;
+    const TS* tl = tiles + ((size_t)cur * JT + lane) * LDT;  // column lane; column lane + 32 c at + 32 c LDT
+    const uint16_t* rb = recs + (size_t)cur * gsize * rec;
 #pragma unroll
-        for (int q = 0; q < kSpWords; ++q) {
-          cnt[q] = __popc(mask[q * NR + r]);
-          tot += cnt[q];
-        }
-        int incl = tot;
+    for (int t = 0; t < TG; ++t) {
+      if (t < ng) {
+        const uint16_t* hd = rb + t * rec;
+        const uint16_t* lst = hd + head;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, off);
-          if (lane >= off) incl += y;
-        }
-        int base = carry + incl - tot;
+        for (int q = 0; q < RPW; ++q) {
+          const int r = wid + 8 * q;
+          if (r < b) {
+            const int e0 = hd[r], em = hd[b + 1 + r], e1 = hd[r + 1];
+            Part sa[C], sb[C];
 #pragma unroll
-        for (int q = 0; q < kSpWords; ++q) {
-          woff[r * (kSpWords + 1) + q] = base;
-          base += cnt[q];
-        }
-        woff[r * (kSpWords + 1) + kSpWords] = base;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < ng * kSpI; e += kSpThreads) {
-      const int t = e / kSpI, ii = e - t * kSpI;
-      const int64_t i = i0 + ii;
-      if (i >= m) continue;
-      const uint8_t* c = P + ((int64_t)(tg0 + t) * m + i) * zeta;
-      const uint32_t below = (1u << (ii & 31)) - 1u;
-      for (int jz = 0; jz < zeta; ++jz) {
-        const int code = c[jz];
-        const int r = t * 8 * RPW + (code & 127);
-        const int pos = woff[r * (kSpWords + 1) + (ii >> 5)] + __popc(mask[(ii >> 5) * NR + r] & below);
-        list[pos] = (uint16_t)(ii | ((code & 128) << 8));
-      }
-    }
-    __syncthreads();
-    // 3. the gather-add
-    const TS* arow = tiles + (cur * kSpJ + lane) * LDT;
+            for (int c = 0; c < C; ++c) sa[c] = sb[c] = Part(0);
+            int e = e0;
+            for (; e + 4 <= em; e += 4) {
+              const int x0 = lst[e], x1 = lst[e + 1], x2 = lst[e + 2], x3 = lst[e + 3];
 #pragma unroll
-    for (int u = 0; u < TG * RPW; ++u) {
-      const int t = u / RPW, r = wid + 8 * (u % RPW);
-      if (t < ng && r < b) {
-        const int rr = t * 8 * RPW + r;
-        const int e0 = woff[rr * (kSpWords + 1)], e1 = woff[rr * (kSpWords + 1) + kSpWords];
-        // four independent partial sums (four entries in flight), combined in a fixed
-        // order at the end of the tile: deterministic, and exact for the integer sums
-        using Part = typename SpAcc<TC>::part;
-        Part s0 = Part(0), s1 = Part(0), s2 = Part(0), s3 = Part(0);
-        int e = e0;
-        for (; e + 4 <= e1; e += 4) {
-          const uint32_t l0 = list[e], l1 = list[e + 1], l2 = list[e + 2], l3 = list[e + 3];
-          const TC a0 = tile_value(arow + (l0 & 0x7FFF)), a1 = tile_value(arow + (l1 & 0x7FFF));
-          const TC a2 = tile_value(arow + (l2 & 0x7FFF)), a3 = tile_value(arow + (l3 & 0x7FFF));
-          s0 = sp_add(s0, a0, l0 >> 15);
-          s1 = sp_add(s1, a1, l1 >> 15);
-          s2 = sp_add(s2, a2, l2 >> 15);
-          s3 = sp_add(s3, a3, l3 >> 15);
+              for (int c = 0; c < C; ++c) {
+                const TS* col = tl + c * 32 * LDT;
+                const Part a0 = sp_val(col + x0), a1 = sp_val(col + x1), a2 = sp_val(col + x2), a3 = sp_val(col + x3);
+                sa[c] += a0;
+                sb[c] += a1;
+                sa[c] += a2;
+                sb[c] += a3;
+              }
+            }
+            for (; e < em; ++e) {
+              const int x = lst[e];
+#pragma unroll
+              for (int c = 0; c < C; ++c) sa[c] += sp_val(tl + c * 32 * LDT + x);
+            }
+            for (; e + 4 <= e1; e += 4) {
+              const int x0 = lst[e], x1 = lst[e + 1], x2 = lst[e + 2], x3 = lst[e + 3];
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                const TS* col = tl + c * 32 * LDT;
+                const Part a0 = sp_val(col + x0), a1 = sp_val(col + x1), a2 = sp_val(col + x2), a3 = sp_val(col + x3);
+                sa[c] -= a0;
+                sb[c] -= a1;
+                sa[c] -= a2;
+                sb[c] -= a3;
+              }
+            }
+            for (; e < e1; ++e) {
+              const int x = lst[e];
+#pragma unroll
+              for (int c = 0; c < C; ++c) sa[c] -= sp_val(tl + c * 32 * LDT + x);
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[t][q][c] += (Acc)(sa[c] + sb[c]);
+          }
         }
-        for (; e < e1; ++e) {
-          const uint32_t l = list[e];
-          s0 = sp_add(s0, tile_value(arow + (l & 0x7FFF)), l >> 15);
-        }
-        acc[u] = acc[u] + (((Acc)s0 + (Acc)s1) + ((Acc)s2 + (Acc)s3));
       }
     }
     __syncthreads();
   }
-  const int64_t j = j0 + lane;
-  if (j < n) {
-    TO* o = out + (int64_t)blockIdx.z * zstride + j * out_ld;
+  const int64_t zoff = (int64_t)blockIdx.z * zstride;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int64_t j = j0 + lane + 32 * c;
+    if (j >= n) continue;
     const int ex = colexp != nullptr ? colexp[j] - 54 : 0;
 #pragma unroll
-    for (int u = 0; u < TG * RPW; ++u) {
-      const int t = u / RPW, r = wid + 8 * (u % RPW);
-      const int64_t c = (int64_t)(tg0 + t) * b + r;
-      if (t < ng && r < b && c < rows) o[c] = sp_final<TC, TO>(acc[u], v, ex);
+    for (int t = 0; t < TG; ++t) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int r = wid + 8 * q;
+        const int64_t row = (int64_t)(tg0 + t) * b + r;
+        if (t >= ng || r >= b || row >= rows) continue;
+        if constexpr (sizeof(Acc) > 8) {
+          if (parts != nullptr)
+            parts[zoff + j * out_ld + row] = acc[t][q][c];
+          else
+            out[j * out_ld + row] = i128_to_double(acc[t][q][c], ex) * v;
+        } else {
+          out[zoff + j * out_ld + row] = acc[t][q][c] * v;
+        }
+      }
     }
   }
 }
 
-int sparse_splits(int64_t m, int64_t n, int sms) {
-  const int64_t ctiles = (n + kSpJ - 1) / kSpJ;
-  const int64_t ktiles = (m + kSpI - 1) / kSpI;
-  int64_t s = (8 * (int64_t)sms + ctiles - 1) / ctiles;  // about four waves at two CTAs per SM
+// out[j out_ld + c] = sqrt(b/zeta) * (the exact sum over splits of the 128-bit
+// partials) 2^(e_j - 54), one rounding to FP64 then the scale.
+__global__ void k_sparse_reduce_fixed(int64_t n, int64_t rows, int splits, const __int128* __restrict__ parts,
+                                      int64_t pld, int64_t zstride, double* __restrict__ out, int64_t out_ld,
+                                      const int32_t* __restrict__ colexp, double v, const int32_t* done) {
+  if (done != nullptr && *done) return;
+  const int64_t total = n * rows;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / rows, c = e - j * rows;
+    __int128 s = 0;
+    for (int z = 0; z < splits; ++z) s += parts[z * zstride + j * pld + c];
+    out[j * out_ld + c] = i128_to_double(s, colexp[j] - 54) * v;
+  }
+}
+
+// Split count over A's row tiles for the kind of input (0 FP32, 1 BF16, 2 FP64 in
+// fixed point): about four waves of the column tiles at the kind's occupancy;
+// depends on (m, n) only.
+int sparse_splits(int64_t m, int64_t n, int sms, int kind) {
+  const int64_t jt = kind == 2 ? 32 : 64;
+  const int64_t per_sm = kind == 2 ? 2 : (kind == 1 ? 3 : 2);
+  const int64_t ctiles = (n + jt - 1) / jt;
+  const int64_t ktiles = (m + kSpT - 1) / kSpT;
+  int64_t s = (4 * per_sm * (int64_t)sms + ctiles - 1) / ctiles;
   if (s > 16) s = 16;
   if (s > ktiles) s = ktiles;
   if (s < 1) s = 1;
@@ -386,67 +465,89 @@ int sparse_splits(int64_t m, int64_t n, int sms) {
   return (int)((ktiles + per - 1) / per);
 }
 
-template <typename TA, typename TS, typename TO, int RPW>
-static cudaError_t launch_sparse(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                                 int blocks, int64_t rows, int splits, TO* out, int64_t out_ld, int64_t zstride,
-                                 const int32_t* colexp, const int32_t* done, cudaStream_t s) {
-  using TC = decltype(tile_value((const TS*)nullptr));
-  constexpr int TG = (sizeof(typename SpAcc<TC>::type) > 8 ? 16 : 32) / RPW;
-  constexpr int NR = TG * 8 * RPW;
-  constexpr int LDT = kSpI + (sizeof(TS) == 2 ? 2 : 1);
-  const size_t smem = (size_t)2 * kSpJ * LDT * sizeof(TS) + (size_t)2 * kSpWords * NR * 4 +
-                      (size_t)NR * (kSpWords + 1) * 4 + (size_t)TG * kSpI * zeta * 2;
+namespace {
+template <typename TS, int RPW>
+cudaError_t launch_gather(int64_t m, int64_t n, const TS* A, int64_t lda, const uint16_t* R, int zeta, int b,
+                          int64_t rows, int splits, typename SpT<TS>::Out* out, typename SpT<TS>::Acc* parts,
+                          int64_t out_ld, int64_t zstride, const int32_t* colexp, const int32_t* done,
+                          cudaStream_t s) {
+  constexpr int TG = sp_group<TS, RPW>();
+  constexpr int JT = 32 * SpT<TS>::C;
+  const int blocks = (int)((rows + b - 1) / b);
+  const int rec = sparse_csr_rec(b, zeta);
+  // blocks per CTA: up to TG, while two CTAs still fit an SM (one CTA at least)
+  const size_t tb = sp_tile_bytes<TS>(), per_block = (size_t)2 * rec * 2;
+  const size_t budget = 113 * 1024;
+  int gsize = TG;
+  while (gsize > 1 && tb + gsize * per_block > budget) --gsize;
+  if (gsize > blocks) gsize = blocks;
+  const size_t smem = tb + gsize * per_block;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static SmemLimit lim;
-  cudaError_t e = raise_smem(k_sparse_sketch<TA, TS, TO, RPW>, smem, lim);
+  cudaError_t e = raise_smem(k_sparse_gather<TS, RPW>, smem, lim);
   if (e != cudaSuccess) return e;
-  const int64_t ktiles = (m + kSpI - 1) / kSpI;
+  const int64_t ktiles = (m + kSpT - 1) / kSpT;
   const int per = (int)((ktiles + splits - 1) / splits);
-  dim3 grid((unsigned)((n + kSpJ - 1) / kSpJ), (unsigned)((blocks + TG - 1) / TG), (unsigned)splits);
-  const TO v = (TO)sqrt((double)b / (double)zeta);
-  k_sparse_sketch<TA, TS, TO, RPW><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, P, zeta, b, blocks, rows, per, out,
-                                                                 out_ld, zstride, v, colexp, done);
+  const int64_t groups = (blocks + gsize - 1) / gsize;
+  const int64_t ctiles = (n + JT - 1) / JT;
+  if (groups > 65535 || splits > 65535 || ctiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)ctiles, (unsigned)groups, (unsigned)splits);
+  const typename SpT<TS>::Out v = (typename SpT<TS>::Out)sqrt((double)b / (double)zeta);
+  k_sparse_gather<TS, RPW><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, R, rec, sparse_csr_head(b), b, blocks, gsize,
+                                                         rows, per, out, parts, out_ld, zstride, v, colexp, done);
   return cudaGetLastError();
 }
 
-template <typename TA, typename TS, typename TO>
-static cudaError_t dispatch_sparse(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                                   int64_t rows, int splits, TO* out, int64_t out_ld, int64_t zstride,
-                                   const int32_t* colexp, const int32_t* done, cudaStream_t s) {
+template <typename TS>
+cudaError_t dispatch_gather(int64_t m, int64_t n, const TS* A, int64_t lda, const uint16_t* R, int zeta, int b,
+                            int64_t rows, int splits, typename SpT<TS>::Out* out, typename SpT<TS>::Acc* parts,
+                            int64_t out_ld, int64_t zstride, const int32_t* colexp, const int32_t* done,
+                            cudaStream_t s) {
   if (b < 1 || b > kSparseMaxB || zeta < 1 || zeta > b || rows < 1 || splits < 1) return cudaErrorInvalidValue;
-  const int blocks = (int)((rows + b - 1) / b);
-#define RID_SPARSE(R) \
-  launch_sparse<TA, TS, TO, R>(m, n, A, lda, P, zeta, b, blocks, rows, splits, out, out_ld, zstride, colexp, done, s)
-  if (b <= 8) return RID_SPARSE(1);
-  if (b <= 16) return RID_SPARSE(2);
-  if (b <= 32) return RID_SPARSE(4);
-  if (b <= 64) return RID_SPARSE(8);
-  return RID_SPARSE(16);
-#undef RID_SPARSE
+#define RID_GATHER(P) \
+  launch_gather<TS, P>(m, n, A, lda, R, zeta, b, rows, splits, out, parts, out_ld, zstride, colexp, done, s)
+  if (b <= 16) return RID_GATHER(2);
+  if (b <= 32) return RID_GATHER(4);
+  if (b <= 64) return RID_GATHER(8);
+  return RID_GATHER(16);
+#undef RID_GATHER
 }
+}  // namespace
 
-template <typename TA, typename TC>
-cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint8_t* P, int zeta, int b,
-                          int64_t rows, int splits, TC* out, int64_t out_ld, int64_t zstride, const int32_t* done,
+template <typename TA>
+cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint16_t* R, int zeta, int b,
+                          int64_t rows, int splits, float* out, int64_t out_ld, int64_t zstride, const int32_t* done,
                           cudaStream_t s) {
-  // the tile is staged in A's own type; BF16 pairs need 4-byte aligned rows
+  // the tile is staged in A's own type; BF16 pairs need 4-byte aligned columns
   if constexpr (sizeof(TA) == 2) {
     if ((lda & 1) != 0 || (reinterpret_cast<uintptr_t>(A) & 3) != 0) return cudaErrorInvalidValue;
   }
-  return dispatch_sparse<TA, TA, TC>(m, n, A, lda, P, zeta, b, rows, splits, out, out_ld, zstride, nullptr, done, s);
+  return dispatch_gather<TA>(m, n, A, lda, R, zeta, b, rows, splits, out, nullptr, out_ld, zstride, nullptr, done,
+                             s);
 }
 
-cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint8_t* P,
-                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld,
-                                int64_t zstride, const int32_t* done, cudaStream_t s) {
-  return dispatch_sparse<long long, long long, double>(m, n, F, m, P, zeta, b, rows, splits, out, out_ld, zstride,
-                                                       colexp, done, s);
+cudaError_t sparse_sketch_fixed(int64_t m, int64_t n, const long long* F, const int32_t* colexp, const uint16_t* R,
+                                int zeta, int b, int64_t rows, int splits, double* out, int64_t out_ld, void* parts,
+                                int64_t pld, int64_t zstride, const int32_t* done, cudaStream_t s) {
+  if (splits == 1)
+    return dispatch_gather<long long>(m, n, F, m, R, zeta, b, rows, 1, out, nullptr, out_ld, 0, colexp, done, s);
+  __int128* P = static_cast<__int128*>(parts);
+  cudaError_t e = dispatch_gather<long long>(m, n, F, m, R, zeta, b, rows, splits, nullptr, P, pld, zstride, colexp,
+                                             done, s);
+  if (e != cudaSuccess) return e;
+  int64_t g = (n * rows + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  k_sparse_reduce_fixed<<<(int)g, 256, 0, s>>>(n, rows, splits, P, pld, zstride, out, out_ld, colexp,
+                                                sqrt((double)b / (double)zeta), done);
+  return cudaGetLastError();
 }
 
-template cudaError_t sparse_sketch<float, float>(int64_t, int64_t, const float*, int64_t, const uint8_t*, int, int,
-                                                 int64_t, int, float*, int64_t, int64_t, const int32_t*, cudaStream_t);
-template cudaError_t sparse_sketch<__nv_bfloat16, float>(int64_t, int64_t, const __nv_bfloat16*, int64_t,
-                                                         const uint8_t*, int, int, int64_t, int, float*, int64_t,
-                                                         int64_t, const int32_t*, cudaStream_t);
+template cudaError_t sparse_sketch<float>(int64_t, int64_t, const float*, int64_t, const uint16_t*, int, int, int64_t,
+                                          int, float*, int64_t, int64_t, const int32_t*, cudaStream_t);
+template cudaError_t sparse_sketch<__nv_bfloat16>(int64_t, int64_t, const __nv_bfloat16*, int64_t, const uint16_t*,
+                                                  int, int, int64_t, int, float*, int64_t, int64_t, const int32_t*,
+                                                  cudaStream_t);
 template cudaError_t sparse_dense<double>(uint64_t, int64_t, int, int, int64_t, int, double*, int64_t, cudaStream_t);
 template cudaError_t sparse_dense<float>(uint64_t, int64_t, int, int, int64_t, int, float*, int64_t, cudaStream_t);
 

@@ -4,9 +4,13 @@
 // row-major, BF16), FP32 accumulation in tensor memory (Sec. 2.4; the sampling step of Algorithm 1).
 // Both operands are K-major (K = m): a column of A and a row of Omega are contiguous.
 //
-// One CTA computes a 128 (columns of A) x BN (rows of Omega) tile over a K range:
-//   warp 0   one lane issues TMA loads (128B-swizzled boxes of 64 K x 128 / 64 x BN)
-//   warp 1   allocates tensor memory; one lane issues tcgen05.mma (M=128, N=BN, K=16)
+// One CTA computes a 128 (columns of A) x NT BN (rows of Omega) tile over a K range:
+//   warp 0   one lane issues TMA loads (128B-swizzled boxes of 64 K x 128 / 64 x NT BN)
+//   warp 1   allocates tensor memory; one lane issues tcgen05.mma (M=128, N=BN, K=16),
+//            NT of them per K step, one per BN-row sub-tile of Omega, all reading the
+//            same stage of A: a pass of many blocks reads each tile of A once per
+//            CTA instead of once per BN rows, and every entry is computed by the same
+//            MMA shape whatever NT is (the same bits for any pass size)
 //   warps 2-5 drain the accumulator with tcgen05.ld and write FP32 rows of G
 // A STAGES-deep ring of shared-memory stages is guarded by "full" (TMA bytes landed)
 // and "empty" (the MMAs that read the stage completed) mbarriers.  Every wait is
@@ -32,10 +36,10 @@ constexpr int kThreads = 192;   // 6 warps
 
 using namespace tcx;
 
-template <int BN>
+template <int BN, int NT>
 struct Smem {
-  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];  // 16 KB per stage
-  alignas(1024) __nv_bfloat16 w[kStages][BN * kBK];   // BN * 128 bytes per stage
+  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // 16 KB per stage
+  alignas(1024) __nv_bfloat16 w[kStages][NT * BN * kBK];  // NT BN * 128 bytes per stage
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t accum;
@@ -44,7 +48,9 @@ struct Smem {
   int abort;
 };
 
-template <int BN>
+// Grid: x = groups of NT BN rows of Omega (fastest, so the CTAs that share a tile of
+// A run together and reuse it from L2), y = tiles of A's columns, z = K splits.
+template <int BN, int NT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_tc_bf16(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w, int n,
                      int rows, int K, int kchunk, float* __restrict__ out, int64_t out_ld, int64_t zstride,
@@ -52,14 +58,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
   // dynamic shared memory is only guaranteed 16-byte aligned: align the carve-out to 1024
-  Smem<BN>& sm = *reinterpret_cast<Smem<BN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem<BN, NT>& sm =
+      *reinterpret_cast<Smem<BN, NT>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM;  // first column of A
-  const int n0 = blockIdx.y * BN;   // first row of Omega
+  const int m0 = blockIdx.y * kBM;       // first column of A
+  const int n0 = blockIdx.x * NT * BN;   // first row of Omega
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int nkb = (kend - kbeg + kBK - 1) / kBK;
-  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+  constexpr uint32_t kTmemCols = NT * BN < 32 ? 32 : NT * BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
       if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) + 1) & 1, st)) break;
-      mbar_expect_tx(&sm.full[s], (kBM + BN) * kBK * 2);
+      mbar_expect_tx(&sm.full[s], (kBM + NT * BN) * kBK * 2);
       const int k0 = kbeg + kb * kBK;
       tma_load_2d(sm.a[s], &map_a, &sm.full[s], k0, m0);
       tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);
@@ -109,7 +116,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t dw = desc_sw128(sm.w[s]);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk)  // advance 16 BF16 = 32 bytes inside the swizzle row
-        mma_bf16(tmem, da + 2 * kk, dw + 2 * kk, idesc, (kb | kk) != 0);
+#pragma unroll
+        for (int t = 0; t < NT; ++t)  // sub-tile t: BN rows of 128 bytes, 1024-byte aligned
+          mma_bf16(tmem + t * BN, da + 2 * kk, dw + (uint64_t)((t * BN * kBK * 2) >> 4) + 2 * kk, idesc,
+                   (kb | kk) != 0);
       mma_commit(&sm.empty[s]);
       consumed = kb + 1;
     }
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = m0 + quarter * 32 + lane;
       float* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < NT * BN; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, v);
         if (row < n) {
@@ -184,9 +194,9 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t ou
   return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int NT>
 size_t smem_bytes() {
-  return sizeof(Smem<BN>) + 1024;  // + alignment slack
+  return sizeof(Smem<BN, NT>) + 1024;  // + alignment slack
 }
 
 }  // namespace tc
@@ -209,19 +219,32 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
                            int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits, DevState* st,
                            const int32_t* done, cudaStream_t s) {
   constexpr int BN = 64;
+  // passes of more than one block: four BN-row sub-tiles of Omega per CTA
+  const bool wide = rows > BN;
+  const int nt = wide ? 4 : 1;
   CUtensorMap ma, mw;
   if (!tc::make_map_bf16(&ma, A, m, n, lda, tc::kBM)) return cudaErrorInvalidValue;
-  if (!tc::make_map_bf16(&mw, W, m, rows, ldw, BN)) return cudaErrorInvalidValue;
+  if (!tc::make_map_bf16(&mw, W, m, rows, ldw, nt * BN)) return cudaErrorInvalidValue;
   int kchunk = (int)((m + splits - 1) / splits);
   kchunk = ((kchunk + tc::kBK - 1) / tc::kBK) * tc::kBK;
   const int nz = (int)((m + kchunk - 1) / kchunk);
-  static SmemLimit lim;
-  const size_t smem = tc::smem_bytes<BN>();
-  cudaError_t e = raise_smem(tc::k_sketch_tc_bf16<BN>, smem, lim);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((n + tc::kBM - 1) / tc::kBM), (unsigned)((rows + BN - 1) / BN), (unsigned)nz);
-  tc::k_sketch_tc_bf16<BN><<<grid, tc::kThreads, smem, s>>>(ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld,
-                                                             zstride, st, done);
+  const int64_t ytiles = (n + tc::kBM - 1) / tc::kBM;
+  if (ytiles > 65535 || nz > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((rows + nt * BN - 1) / (nt * BN)), (unsigned)ytiles, (unsigned)nz);
+  cudaError_t e;
+  if (wide) {
+    static SmemLimit lim4;
+    e = raise_smem(tc::k_sketch_tc_bf16<BN, 4>, tc::smem_bytes<BN, 4>(), lim4);
+    if (e != cudaSuccess) return e;
+    tc::k_sketch_tc_bf16<BN, 4><<<grid, tc::kThreads, tc::smem_bytes<BN, 4>(), s>>>(
+        ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld, zstride, st, done);
+  } else {
+    static SmemLimit lim1;
+    e = raise_smem(tc::k_sketch_tc_bf16<BN, 1>, tc::smem_bytes<BN, 1>(), lim1);
+    if (e != cudaSuccess) return e;
+    tc::k_sketch_tc_bf16<BN, 1><<<grid, tc::kThreads, tc::smem_bytes<BN, 1>(), s>>>(
+        ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld, zstride, st, done);
+  }
   return cudaGetLastError();
 }
 

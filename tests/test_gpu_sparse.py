@@ -4,7 +4,7 @@
   implementation of the same counter-based definition -- bit-exact (the
   entries are +-sqrt(b/zeta), rounded the same way on both sides).
 * the gather-add sketch against the oracle's dense product with the same
-  Omega, on ragged shapes (rows of A not a multiple of the 256-row tile,
+  Omega, on ragged shapes (rows of A not a multiple of the 128-row tile,
   columns not a multiple of 32, a last block cut short), in FP64 within 1e-13
   relative to sum |Omega||A| and in FP32 / BF16 within their rounding; two runs
   bit-identical (fixed summation order).
@@ -46,26 +46,30 @@ def test_sparse_sign_rows_bit_exact(B, orc, b, zeta, blocks, m):
     np.testing.assert_array_equal(g32, o.astype(np.float32))
 
 
-@pytest.mark.parametrize("m,n,rows,b", [(1000, 77, 130, 64), (3000, 600, 64, 64), (257, 33, 40, 16),
-                                         (5000, 1000, 256, 128)])
-def test_sparse_sketch_matches_dense_product(B, orc, m, n, rows, b):
+@pytest.mark.parametrize("m,n,rows,b,zeta", [(1000, 77, 130, 64, 8), (3000, 600, 64, 64, 8), (257, 33, 40, 16, 8),
+                                              (5000, 1000, 256, 128, 8), (3000, 150, 176, 16, 8),
+                                              (700, 90, 96, 32, 32), (300, 40, 128, 128, 128), (129, 65, 7, 3, 2)])
+def test_sparse_sketch_matches_dense_product(B, orc, m, n, rows, b, zeta):
+    """Ragged tiles (m not a multiple of 128, n of 32 / 64), the last block cut
+    short, one or several K splits, passes of many blocks (11 blocks of 16: three
+    groups of four), zeta up to b (dense +-1 blocks: the largest lists)."""
     rng = np.random.default_rng(m + n)
     A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-8, 9, size=n))[None, :]
     blocks = -(-rows // b)
-    Om = orc.sparse_sign_rows(5, 2, blocks, b, m)[:rows]
+    Om = orc.sparse_sign_rows(5, 2, blocks, b, m, zeta)[:rows]
     ref = orc.sketch_t(A, Om)
     bound = (np.abs(Om) @ np.abs(A)).T
-    G = B.sparse_sketch(dev_cm(A), rows, b, seed=5, t0=2).cpu().numpy()
+    G = B.sparse_sketch(dev_cm(A), rows, b, seed=5, t0=2, zeta=zeta).cpu().numpy()
     assert np.all(np.abs(G - ref) <= 1e-13 * bound + 1e-300)
-    G2 = B.sparse_sketch(dev_cm(A), rows, b, seed=5, t0=2).cpu().numpy()
+    G2 = B.sparse_sketch(dev_cm(A), rows, b, seed=5, t0=2, zeta=zeta).cpu().numpy()
     np.testing.assert_array_equal(G, G2)
     # FP32 and BF16 storage: FP32 sums
     A32 = A.astype(np.float32)
-    G32 = B.sparse_sketch(dev_cm(A32, torch.float32), rows, b, seed=5, t0=2).cpu().numpy()
+    G32 = B.sparse_sketch(dev_cm(A32, torch.float32), rows, b, seed=5, t0=2, zeta=zeta).cpu().numpy()
     ref32 = orc.sketch_t(A32.astype(np.float64), Om)
     assert np.all(np.abs(G32 - ref32) <= 1e-5 * bound + 1e-30)
     Ab = torch.from_numpy(A32).to("cuda").to(torch.bfloat16)
-    Gb = B.sparse_sketch(B.colmajor_padded(Ab, 8), rows, b, seed=5, t0=2).cpu().numpy()
+    Gb = B.sparse_sketch(B.colmajor_padded(Ab, 8), rows, b, seed=5, t0=2, zeta=zeta).cpu().numpy()
     refb = orc.sketch_t(Ab.double().cpu().numpy(), Om)
     assert np.all(np.abs(Gb - refb) <= 1e-5 * bound + 1e-30)
 

@@ -38,6 +38,7 @@ def bf16_pair(rng, m, n, rows):
     (64, 128, 64),       # one K stage
     (40000, 300, 64),    # long K: many split-K partials
     (8, 5, 3),           # smaller than every tile
+    (3000, 700, 600),    # a pass of many blocks: groups of four 64-row sub-tiles, a ragged last group
 ])
 def test_tc_sketch_matches_fp64_product(B, m, n, rows):
     rng = np.random.default_rng(m + n + rows)
@@ -167,4 +168,32 @@ def test_f32emu_pass_size_does_not_change_result(B):
     base = B.id_adaptive(Ad, 1e-4, block=b, seed=11, sketch_prec=B.F32_EMU)
     for kw in (dict(k0=100), dict(blocks_per_pass=3)):
         g = B.id_adaptive(Ad, 1e-4, block=b, seed=11, sketch_prec=B.F32_EMU, **kw)
+        assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X)
+
+
+def test_tc_sketch_wide_pass_equals_block_passes(B):
+    """A pass of many blocks (a CTA runs the MMAs of four 64-row sub-tiles of Omega
+    on each stage of A) gives every entry the same bits as passes of one block
+    (K = 512: one split for both; rows of Omega 16-byte aligned for TMA)."""
+    rng = np.random.default_rng(5)
+    m, n, rows = 512, 700, 600
+    A, Om = bf16_pair(rng, m, n, rows)
+    Acm = B.colmajor(A)
+    G = B.id_sketch(Acm, Om)
+    for r0 in range(0, rows, 64):
+        g = B.id_sketch(Acm, Om[r0:r0 + 64].contiguous())
+        assert torch.equal(G[:, r0:r0 + 64], g), r0
+
+
+def test_bf16_pass_size_does_not_change_result(B):
+    """Adaptive BF16 runs with a rank guess or several blocks per pass (wide
+    sketch passes) return the one-block-per-pass run's J, X and k bit for bit."""
+    m, n, b = 6000, 1500, 64
+    rng = np.random.default_rng(8)
+    A = (rng.standard_normal((m, 300)) @ rng.standard_normal((300, n))) / np.sqrt(300)
+    A += 1e-3 * rng.standard_normal((m, n))
+    Ad = B.colmajor(torch.from_numpy(A).to("cuda", torch.bfloat16))
+    base = B.id_adaptive(Ad, 3e-2, block=b, seed=4)
+    for kw in (dict(k0=400), dict(blocks_per_pass=5)):
+        g = B.id_adaptive(Ad, 3e-2, block=b, seed=4, **kw)
         assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X)

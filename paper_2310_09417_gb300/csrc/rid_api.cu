@@ -626,7 +626,8 @@ class Engine {
     const int64_t b = p_.b;
     uint16_t* R = reinterpret_cast<uint16_t*>(omega_);
     RID_TRY(tbegin(ID_PHASE_OMEGA));
-    RID_TRY(cuda(sparse_csr(o_.seed, row0 / b, (int)cdiv(rows, b), (int)b, p_.m, (int)p_.zeta, R, done_, s_)));
+    const int esz = p_.path == 16 ? 2 : (int)sizeof(T);  // staged bytes: BF16, FP32 or the FP64 fixed point
+    RID_TRY(cuda(sparse_csr(o_.seed, row0 / b, (int)cdiv(rows, b), (int)b, p_.m, (int)p_.zeta, esz, R, done_, s_)));
     RID_TRY(tend(1));
     RID_TRY(tbegin(ID_PHASE_SKETCH));
     const int64_t zs = (int64_t)p_.n * p_.ldg;
@@ -1356,7 +1357,8 @@ int id_sparse_sketch(const id_matrix* A, uint64_t seed, int64_t t0, int64_t rows
   uint16_t* R = reinterpret_cast<uint16_t*>(w + 256);
   void* part = w + off;
   const int64_t zs = A->n * rows;
-  cudaError_t e = sparse_csr(seed, t0, (int)cdiv(rows, b), (int)b, A->m, (int)zeta, R, nullptr, s);
+  const int esz = A->dtype == ID_F64 ? 8 : (A->dtype == ID_BF16 ? 2 : 4);
+  cudaError_t e = sparse_csr(seed, t0, (int)cdiv(rows, b), (int)b, A->m, (int)zeta, esz, R, nullptr, s);
   if (e == cudaSuccess) {
     if (A->dtype == ID_F64) {
       unsigned char* fx = w + off + (splits > 1 ? align_up((size_t)splits * A->n * rows * 16) : 0);

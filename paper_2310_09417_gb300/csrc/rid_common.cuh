@@ -129,6 +129,33 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Block-wide sum of one double per thread (blockDim.x multiple of 32, <= 1024);
 // result valid in thread 0.
+// Sum of squares in float-float: t = x * x is exact in FP32 when x has at most 12
+// significant bits (BF16, E4M3) and its square is a normal FP32 number; TwoSum
+// (Knuth) keeps the rounding error of hi + t in lo, so a group of a few dozen
+// squares is summed to about 2^-45 relative before it is folded into FP64.
+__device__ __forceinline__ void sq_twosum(float t, float& hi, float& lo) {
+  const float s = __fadd_rn(hi, t);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb)));
+  hi = s;
+}
+// x given by its FP32 bit pattern (a BF16 value widened): squares of |x| in
+// [2^-63, 2^54) go to the float-float sum (below 2^108 each, so a group of 64 stays
+// finite), zeros are skipped, NaN / Inf clear `finite`, the rest (subnormal,
+// tiny or huge values) are added in FP64.
+__device__ __forceinline__ void sq_add_bits(uint32_t bits, float& hi, float& lo, double& acc, bool& finite) {
+  const uint32_t ex = (bits >> 23) & 0xFFu;
+  const float x = __uint_as_float(bits);
+  if (ex - 64u <= 116u) {
+    sq_twosum(__fmul_rn(x, x), hi, lo);
+  } else if ((bits << 1) == 0u) {
+  } else if (ex == 0xFFu) {
+    finite = false;
+  } else {
+    acc += (double)x * (double)x;
+  }
+}
+
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double s_part[32];
   v = warp_sum(v);

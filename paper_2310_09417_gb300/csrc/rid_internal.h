@@ -275,7 +275,8 @@ int sparse_splits(int64_t m, int64_t n, int sms, int kind);
 int sparse_csr_head(int b);
 int sparse_csr_rec(int b, int zeta);
 size_t sparse_csr_bytes(int64_t m, int blocks, int b, int zeta);
-cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint16_t* R,
+// esz: bytes per staged element of A in the gather (4 FP32, 2 BF16, 8 FP64 fixed point)
+cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, int esz, uint16_t* R,
                        const int32_t* done, cudaStream_t s);
 template <typename TA>
 cudaError_t sparse_sketch(int64_t m, int64_t n, const TA* A, int64_t lda, const uint16_t* R, int zeta, int b,

@@ -108,9 +108,51 @@ __global__ void k_norm2_partial(int64_t m, int64_t n, const T* __restrict__ A, i
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+// BF16 columns 16-byte aligned (lda a multiple of 8): eight elements per load, the
+// squares summed exactly in FP32 and in float-float groups of 64 (sq_add_bits),
+// folded into FP64 -- no per-element FP64 work, which on GB300 (about two FP64
+// instructions per clock per SM) made this pass take ~20x its HBM time.
+__global__ void k_norm2_bf16(int64_t m, int64_t n, const __nv_bfloat16* __restrict__ A, int64_t lda, double* part,
+                             DevState* st) {
+  double acc = 0.0;
+  bool finite = true;
+  const int64_t nv = m / 8;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const uint4* a = reinterpret_cast<const uint4*>(A + j * lda);
+    float hi = 0.f, lo = 0.f;
+    int grp = 0;
+    for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+      const uint4 w = __ldg(a + v);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sq_add_bits(ws[q] << 16, hi, lo, acc, finite);
+        sq_add_bits(ws[q] & 0xFFFF0000u, hi, lo, acc, finite);
+      }
+      if (++grp == 8) {
+        acc += (double)hi + (double)lo;
+        hi = lo = 0.f;
+        grp = 0;
+      }
+    }
+    const uint16_t* r = reinterpret_cast<const uint16_t*>(A + j * lda);
+    for (int64_t i = nv * 8 + threadIdx.x; i < m; i += blockDim.x) sq_add_bits((uint32_t)r[i] << 16, hi, lo, acc, finite);
+    acc += (double)hi + (double)lo;
+  }
+  if (!finite) atomicOr(&st->err, kErrNonFinite);
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 template <typename T>
 cudaError_t norm2_partial(int64_t m, int64_t n, const T* A, int64_t lda, double* part, int nparts,
                           DevState* st, cudaStream_t s) {
+  if constexpr (sizeof(T) == 2) {
+    if ((lda % 8) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0) {
+      k_norm2_bf16<<<nparts, 256, 0, s>>>(m, n, A, lda, part, st);
+      return cudaGetLastError();
+    }
+  }
   k_norm2_partial<T><<<nparts, 256, 0, s>>>(m, n, A, lda, part, st);
   return cudaGetLastError();
 }

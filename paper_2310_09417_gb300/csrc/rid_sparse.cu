@@ -131,12 +131,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 // ------------------------------------------------------------------ per-tile lists
 // Record of one (tile, block), in uint16: a head of sparse_csr_head(b) entries,
-// head[r] = first list entry of sketch row r (r = 0 .. b; head[b] = the tile's
-// count) and head[b + 1 + r] = first negative entry of row r, then the list: the
-// tile rows i (0 .. kSpT-1) of row r's nonzeros, positive ones first, each part in
-// ascending i.  Head and list are padded to 16-byte multiples.
+// head[r] = first list entry of sketch row r (r = 0 .. b; head[b] = the list's
+// length) and head[b + 1 + r] = first negative entry of row r, then the list: for
+// each tile row i (0 .. kSpT-1) with a nonzero in row r, its byte offset i * esz in
+// a staged column of A (esz: bytes per staged element), positive ones first, each
+// part in ascending i and padded to a multiple of four entries with kSpT * esz (a
+// zero slot past the tile's rows), so the gather reads four entries at a time with
+// no remainder.  Head and list are padded to 16-byte multiples.
 int sparse_csr_head(int b) { return (2 * b + 1 + 7) / 8 * 8; }
-int sparse_csr_rec(int b, int zeta) { return sparse_csr_head(b) + (kSpT * zeta + 7) / 8 * 8; }
+int sparse_csr_rec(int b, int zeta) { return sparse_csr_head(b) + (kSpT * zeta + 6 * b + 7) / 8 * 8; }
 size_t sparse_csr_bytes(int64_t m, int blocks, int b, int zeta) {
   return (size_t)((m + kSpT - 1) / kSpT) * blocks * sparse_csr_rec(b, zeta) * 2;
 }
@@ -146,7 +149,7 @@ size_t sparse_csr_bytes(int64_t m, int blocks, int b, int zeta) {
 // rows, an exclusive scan of the keys' counts, and each entry placed at its key's
 // start plus the number of tile rows below it with the same key.
 __global__ void __launch_bounds__(kSpThreads)
-    k_sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, int rec, int head,
+    k_sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, int esz, int rec, int head,
                  uint16_t* __restrict__ R, const int32_t* done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char cs_raw[];
@@ -180,15 +183,17 @@ __global__ void __launch_bounds__(kSpThreads)
         cnt[w] = key < 2 * b ? __popc(mask[key * kSpTW + w]) : 0;
         tot += cnt[w];
       }
-      int incl = tot;
+      const int ptot = (tot + 3) & ~3;  // the key's segment, padded to four entries
+      int incl = ptot;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, off);
         if (tid >= off) incl += y;
       }
-      int base = carry + incl - tot;
+      int base = carry + incl - ptot;
       if (key < 2 * b) {
         out[(key & 1) ? b + 1 + (key >> 1) : (key >> 1)] = (uint16_t)base;
+        for (int e = base + tot; e < base + ptot; ++e) out[head + e] = (uint16_t)(kSpT * esz);
 #pragma unroll
         for (int w = 0; w < kSpTW; ++w) {
           woff[key * kSpTW + w] = base;
@@ -207,19 +212,20 @@ __global__ void __launch_bounds__(kSpThreads)
     for (int z = 0; z < zeta; ++z) {
       const int key = 2 * (c[z] & 127) + (c[z] >> 7);
       const int w = key * kSpTW + (tid >> 5);
-      out[head + woff[w] + __popc(mask[w] & below)] = (uint16_t)tid;
+      out[head + woff[w] + __popc(mask[w] & below)] = (uint16_t)(tid * esz);
     }
   }
 }
 
-cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, uint16_t* R,
+cudaError_t sparse_csr(uint64_t seed, int64_t t0, int blocks, int b, int64_t m, int zeta, int esz, uint16_t* R,
                        const int32_t* done, cudaStream_t s) {
   if (b < 1 || b > kSparseMaxB || zeta < 1 || zeta > b || blocks < 1 || m < 1) return cudaErrorInvalidValue;
+  if (esz != 2 && esz != 4 && esz != 8) return cudaErrorInvalidValue;
   const int64_t tiles = (m + kSpT - 1) / kSpT;
   if (tiles > 0x7FFFFFFFll || blocks > 65535) return cudaErrorInvalidValue;
   const size_t smem = (size_t)2 * 2 * b * kSpTW * 4 + (size_t)kSpT * zeta;
   k_sparse_csr<<<dim3((unsigned)tiles, (unsigned)blocks), kSpThreads, smem, s>>>(
-      seed, t0, blocks, b, m, zeta, sparse_csr_rec(b, zeta), sparse_csr_head(b), R, done);
+      seed, t0, blocks, b, m, zeta, esz, sparse_csr_rec(b, zeta), sparse_csr_head(b), R, done);
   return cudaGetLastError();
 }
 
@@ -258,27 +264,69 @@ __host__ __device__ constexpr int sp_group() {
   constexpr int g = SpT<TS>::REGS / per;
   return g < 1 ? 1 : (g > 4 ? 4 : g);
 }
-__device__ __forceinline__ float sp_val(const float* p) { return *p; }
-__device__ __forceinline__ float sp_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ long long sp_val(const long long* p) { return *p; }
+// the staged element at byte offset o of a column, as its partial-sum type
+template <typename TS>
+__device__ __forceinline__ typename SpT<TS>::Part sp_val(const unsigned char* col, uint32_t o) {
+  const TS x = *reinterpret_cast<const TS*>(col + o);
+  if constexpr (sizeof(TS) == 2)
+    return __bfloat162float(x);
+  else
+    return x;
+}
 __device__ __forceinline__ double i128_to_double(__int128 s, int ex) {
   // |s| < 2^95: s >> 32 fits 64 bits
   return tcx::fixed_to_double((long long)(s >> 32), (long long)(s & (__int128)0xFFFFFFFFll), ex);
 }
+// One list segment [eb, ee) (a multiple of four entries) of a sketch row, added
+// (NEG: subtracted) into the partials sa / sb of the C columns whose staged copies
+// start at tl (column c at c kColStride bytes): four entries per 8-byte load, the
+// next load issued before the current entries are summed.
+template <typename TS, int C, bool NEG>
+__device__ __forceinline__ void sp_segment(const uint16_t* lst, int eb, int ee, const unsigned char* tl,
+                                           typename SpT<TS>::Part (&sa)[C], typename SpT<TS>::Part (&sb)[C]) {
+  using Part = typename SpT<TS>::Part;
+  constexpr uint32_t kColStride = 32 * SpT<TS>::LDT * sizeof(TS);
+  if (eb >= ee) return;
+  uint2 w4 = *reinterpret_cast<const uint2*>(lst + eb);
+  for (int e = eb; e < ee; e += 4) {
+    const uint2 cur = w4;
+    if (e + 4 < ee) w4 = *reinterpret_cast<const uint2*>(lst + e + 4);
+    const uint32_t o0 = cur.x & 0xFFFFu, o1 = cur.x >> 16, o2 = cur.y & 0xFFFFu, o3 = cur.y >> 16;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const unsigned char* col = tl + c * kColStride;
+      const Part a0 = sp_val<TS>(col, o0), a1 = sp_val<TS>(col, o1);
+      const Part a2 = sp_val<TS>(col, o2), a3 = sp_val<TS>(col, o3);
+      if constexpr (NEG) {
+        sa[c] -= a0;
+        sb[c] -= a1;
+        sa[c] -= a2;
+        sb[c] -= a3;
+      } else {
+        sa[c] += a0;
+        sb[c] += a1;
+        sa[c] += a2;
+        sb[c] += a3;
+      }
+    }
+  }
+}
+
 template <typename TS>
 __host__ __device__ constexpr size_t sp_tile_bytes() {
   return ((size_t)2 * 32 * SpT<TS>::C * SpT<TS>::LDT * sizeof(TS) + 15) / 16 * 16;
 }
 
 // Split z (tiles [z ktiles, (z+1) ktiles) of A's rows) of the sketch rows of blocks
-// [tg0, tg0 + gsize) for the columns [j0, j0 + 32 C).  Per tile (the next one and
-// its lists already in flight by cp.async into the other buffers): warp w sums the
-// sketch rows r = w + 8q of each block, lane = column, the row's positive entries
-// then its negative ones, four at a time into two partials per column (a fixed
-// order).  FP32 output: out[z zstride + j out_ld + row] = sqrt(b/zeta) * sum.
+// [tg0, tg0 + gsize) (gsize <= TG) for the columns [j0, j0 + 32 C).  Per tile (the
+// next one and its lists already in flight by cp.async into the other buffers):
+// warp w sums the sketch rows r = w + 8q of each block, lane = column, the row's
+// positive entries then its negative ones, four list entries per 8-byte load,
+// alternately into two partials per column (a fixed order; padding entries read
+// the zero slot past the tile's rows).  FP32 output: out[z zstride + j out_ld + row] = sqrt(b/zeta) * sum.
 // Fixed point: with one split the rounded FP64 value goes to out; otherwise the
 // exact 128-bit sum to parts[z zstride + j out_ld + row].
-template <typename TS, int RPW>
+template <typename TS, int RPW, int TG>
 __global__ void __launch_bounds__(kSpThreads, 2)
     k_sparse_gather(int64_t m, int64_t n, const TS* __restrict__ A, int64_t lda, const uint16_t* __restrict__ R,
                     int rec, int head, int b, int blocks, int gsize, int64_t rows, int ktiles,
@@ -288,7 +336,6 @@ __global__ void __launch_bounds__(kSpThreads, 2)
   using Part = typename SpT<TS>::Part;
   using Acc = typename SpT<TS>::Acc;
   constexpr int C = SpT<TS>::C, LDT = SpT<TS>::LDT, JT = 32 * C;
-  constexpr int TG = sp_group<TS, RPW>();
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char sg_raw[];
   TS* tiles = reinterpret_cast<TS*>(sg_raw);                                    // [2][JT][LDT]
@@ -339,6 +386,8 @@ __global__ void __launch_bounds__(kSpThreads, 2)
     cp_async_commit();
   };
 
+  // the zero slot (tile row kSpT) of every staged column, which padding entries read
+  if (tid < 2 * JT) tiles[(size_t)tid * LDT + kSpT] = TS(0);
   if (it0 < it1) issue(it0, 0);
   for (int64_t it = it0; it < it1; ++it) {
     const int cur = (int)((it - it0) & 1);
@@ -349,7 +398,8 @@ __global__ void __launch_bounds__(kSpThreads, 2)
       cp_async_wait<0>();
     }
     __syncthreads();
-    const TS* tl = tiles + ((size_t)cur * JT + lane) * LDT;  // column lane; column lane + 32 c at + 32 c LDT
+    // column lane of this buffer; column lane + 32 c at + 32 c LDT elements
+    const unsigned char* tl = reinterpret_cast<const unsigned char*>(tiles + ((size_t)cur * JT + lane) * LDT);
     const uint16_t* rb = recs + (size_t)cur * gsize * rec;
 #pragma unroll
     for (int t = 0; t < TG; ++t) {
@@ -364,41 +414,8 @@ __global__ void __launch_bounds__(kSpThreads, 2)
             Part sa[C], sb[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) sa[c] = sb[c] = Part(0);
-            int e = e0;
-            for (; e + 4 <= em; e += 4) {
-              const int x0 = lst[e], x1 = lst[e + 1], x2 = lst[e + 2], x3 = lst[e + 3];
-#pragma unroll
-              for (int c = 0; c < C; ++c) {
-                const TS* col = tl + c * 32 * LDT;
-                const Part a0 = sp_val(col + x0), a1 = sp_val(col + x1), a2 = sp_val(col + x2), a3 = sp_val(col + x3);
-                sa[c] += a0;
-                sb[c] += a1;
-                sa[c] += a2;
-                sb[c] += a3;
-              }
-            }
-            for (; e < em; ++e) {
-              const int x = lst[e];
-#pragma unroll
-              for (int c = 0; c < C; ++c) sa[c] += sp_val(tl + c * 32 * LDT + x);
-            }
-            for (; e + 4 <= e1; e += 4) {
-              const int x0 = lst[e], x1 = lst[e + 1], x2 = lst[e + 2], x3 = lst[e + 3];
-#pragma unroll
-              for (int c = 0; c < C; ++c) {
-                const TS* col = tl + c * 32 * LDT;
-                const Part a0 = sp_val(col + x0), a1 = sp_val(col + x1), a2 = sp_val(col + x2), a3 = sp_val(col + x3);
-                sa[c] -= a0;
-                sb[c] -= a1;
-                sa[c] -= a2;
-                sb[c] -= a3;
-              }
-            }
-            for (; e < e1; ++e) {
-              const int x = lst[e];
-#pragma unroll
-              for (int c = 0; c < C; ++c) sa[c] -= sp_val(tl + c * 32 * LDT + x);
-            }
+            sp_segment<TS, C, false>(lst, e0, em, tl, sa, sb);
+            sp_segment<TS, C, true>(lst, em, e1, tl, sa, sb);
 #pragma unroll
             for (int c = 0; c < C; ++c) acc[t][q][c] += (Acc)(sa[c] + sb[c]);
           }
@@ -466,6 +483,21 @@ int sparse_splits(int64_t m, int64_t n, int sms, int kind) {
 }
 
 namespace {
+template <typename TS, int RPW, int TG>
+cudaError_t launch_gather_tg(dim3 grid, size_t smem, int64_t m, int64_t n, const TS* A, int64_t lda,
+                             const uint16_t* R, int rec, int b, int blocks, int gsize, int64_t rows, int per,
+                             typename SpT<TS>::Out* out, typename SpT<TS>::Acc* parts, int64_t out_ld,
+                             int64_t zstride, typename SpT<TS>::Out v, const int32_t* colexp, const int32_t* done,
+                             cudaStream_t s) {
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(k_sparse_gather<TS, RPW, TG>, smem, lim);
+  if (e != cudaSuccess) return e;
+  k_sparse_gather<TS, RPW, TG><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, R, rec, sparse_csr_head(b), b, blocks,
+                                                             gsize, rows, per, out, parts, out_ld, zstride, v, colexp,
+                                                             done);
+  return cudaGetLastError();
+}
+
 template <typename TS, int RPW>
 cudaError_t launch_gather(int64_t m, int64_t n, const TS* A, int64_t lda, const uint16_t* R, int zeta, int b,
                           int64_t rows, int splits, typename SpT<TS>::Out* out, typename SpT<TS>::Acc* parts,
@@ -483,9 +515,6 @@ cudaError_t launch_gather(int64_t m, int64_t n, const TS* A, int64_t lda, const 
   if (gsize > blocks) gsize = blocks;
   const size_t smem = tb + gsize * per_block;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  static SmemLimit lim;
-  cudaError_t e = raise_smem(k_sparse_gather<TS, RPW>, smem, lim);
-  if (e != cudaSuccess) return e;
   const int64_t ktiles = (m + kSpT - 1) / kSpT;
   const int per = (int)((ktiles + splits - 1) / splits);
   const int64_t groups = (blocks + gsize - 1) / gsize;
@@ -493,9 +522,12 @@ cudaError_t launch_gather(int64_t m, int64_t n, const TS* A, int64_t lda, const 
   if (groups > 65535 || splits > 65535 || ctiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
   dim3 grid((unsigned)ctiles, (unsigned)groups, (unsigned)splits);
   const typename SpT<TS>::Out v = (typename SpT<TS>::Out)sqrt((double)b / (double)zeta);
-  k_sparse_gather<TS, RPW><<<grid, kSpThreads, smem, s>>>(m, n, A, lda, R, rec, sparse_csr_head(b), b, blocks, gsize,
-                                                         rows, per, out, parts, out_ld, zstride, v, colexp, done);
-  return cudaGetLastError();
+  // one block per CTA (the usual pass) runs a variant without the group loop
+  if (gsize == 1)
+    return launch_gather_tg<TS, RPW, 1>(grid, smem, m, n, A, lda, R, rec, b, blocks, gsize, rows, per, out, parts,
+                                        out_ld, zstride, v, colexp, done, s);
+  return launch_gather_tg<TS, RPW, TG>(grid, smem, m, n, A, lda, R, rec, b, blocks, gsize, rows, per, out, parts,
+                                       out_ld, zstride, v, colexp, done, s);
 }
 
 template <typename TS>

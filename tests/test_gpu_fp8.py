@@ -292,3 +292,27 @@ def test_sketch_into_padded_rows(B, path):
     torch.cuda.synchronize()
     assert torch.equal(G[:, :rows], ref)
     assert torch.isnan(G[:, rows:]).all()  # the padding is not written
+
+
+@pytest.mark.parametrize("m,n", [(1000, 37), (4099, 20), (16, 3)])
+def test_fp8_norm_matches_fp64_sum_of_squares(B, m, n):
+    """||A||_F of the stored FP8 matrix (vectors of 16 codes summed in float-float,
+    scaled in FP64) against the FP64 sum of squares of the decoded values; rows
+    not a multiple of 16 (the last vector masked), scales spanning 2^-40 .. 2^40."""
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-40, 41, size=n))[None, :]
+    A[rng.random((m, n)) < 0.05] = 0.0
+    A8 = B.quantize_fp8(B.colmajor(torch.from_numpy(A).cuda()), pow2=1)
+    Ad = dequantize(A8)
+    g = B.id_adaptive(A8, 0.5, block=16, k_max=16)
+    ref = np.sqrt(np.sum(Ad * Ad))
+    assert g.norm_A == pytest.approx(ref, rel=1e-12)
+
+
+def test_fp8_nan_code_is_rejected(B):
+    A8 = B.quantize_fp8(B.colmajor(torch.randn(300, 20, dtype=torch.float32, device="cuda")))
+    codes = A8.data.view(torch.uint8)
+    codes[257, 5] = 0x7F  # S.1111.111: NaN, in the masked last vector of the column
+    with pytest.raises(B.IDError) as e:
+        B.id_adaptive(A8, 1e-1)
+    assert e.value.code == B.ERR_NONFINITE

@@ -197,3 +197,28 @@ def test_bf16_pass_size_does_not_change_result(B):
     for kw in (dict(k0=400), dict(blocks_per_pass=5)):
         g = B.id_adaptive(Ad, 3e-2, block=b, seed=4, **kw)
         assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X)
+
+
+@pytest.mark.parametrize("m,n", [(4096, 50), (1003, 33), (8, 5)])
+def test_bf16_norm_matches_fp64_sum_of_squares(B, m, n):
+    """||A||_F of a BF16 matrix (eight values per load, exact FP32 squares summed in
+    float-float groups, FP64 across groups) against the FP64 sum of squares, with
+    zeros, subnormal, tiny (below 2^-63) and huge (above 2^54) entries that take
+    the FP64 branch, and rows not a multiple of eight."""
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-20, 21, size=n))[None, :]
+    A[rng.random((m, n)) < 0.05] = 0.0
+    A[0, 0], A[1 % m, 1] = 1e-40, 3e-25
+    A[2 % m, 2], A[3 % m, 3] = 1e17, -3e17
+    Ab = B.colmajor_padded(torch.from_numpy(A).cuda().to(torch.bfloat16), 8)
+    ref = float(np.sqrt(np.sum(Ab.double().cpu().numpy() ** 2)))
+    g = B.id_adaptive(Ab, 0.9, block=8, k_max=8)
+    assert g.norm_A == pytest.approx(ref, rel=1e-12)
+
+
+def test_bf16_nonfinite_is_rejected(B):
+    Ab = B.colmajor_padded(torch.randn(1000, 20, device="cuda").to(torch.bfloat16), 8)
+    Ab[999, 7] = float("inf")
+    with pytest.raises(B.IDError) as e:
+        B.id_adaptive(Ab, 1e-1)
+    assert e.value.code == B.ERR_NONFINITE

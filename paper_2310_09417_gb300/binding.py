@@ -372,7 +372,7 @@ def id_fixed_rank(A: torch.Tensor, k: int, l: int, *, block: int = 64, seed: int
 
 
 def id_adaptive(A: torch.Tensor, tol: float, *, block: int = 64, relative: bool = True,
-                k_max: int | None = None, k0: int = 0, blocks_per_pass: int = 1, seed: int = 0,
+                k_max: int | None = None, k0: int = 0, blocks_per_pass: int = 0, seed: int = 0,
                 omega: torch.Tensor | None = None, profile: bool = False, pivots: bool = False,
                 trace_cap: int = 4096, stream=None, workspace: torch.Tensor | None = None,
                 out: tuple | None = None, predictor: torch.Tensor | None = None,

@@ -190,7 +190,10 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     const int64_t max_blocks = cdiv(p->cap, b) + 1;  // blocks that can ever be used
     int64_t first = o->k0 > 0 ? (cdiv(o->k0, b) + 1) : 1;
     p->rows_first = imin(first, max_blocks) * b;
-    const int64_t per = o->blocks_per_pass > 0 ? o->blocks_per_pass : 1;
+    // 0 = automatic: two blocks per pass on the FP64-accurate tensor-core sketch (the
+    // CTAs of a pass's two blocks read each tile of A's digits together, the second
+    // from L2), one elsewhere
+    const int64_t per = o->blocks_per_pass > 0 ? o->blocks_per_pass : (path == 65 && !p->sparse ? 2 : 1);
     p->rows_pass = imin(per, max_blocks) * b;
     p->wmax = b;
     p->max_rounds = max_blocks + 1;

@@ -44,7 +44,8 @@ constexpr int kSlices = 7;       // digits of A
 constexpr int kGroups = 8;       // accumulator groups (slice s feeds groups s and s+1)
 constexpr int kChunkSteps = 8;   // K stages per exact chunk (512 K)
 constexpr int kChunk = kChunkSteps * kBK;
-constexpr int kStages = 6;
+constexpr int kDual = 2;          // K steps per stage: one 32 KB box of A (two adjacent tiles) per barrier
+constexpr int kStages = 3;        // 3 x (32 KB of A + 32 KB of Omega)
 constexpr int kEpiWarps = 8;     // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxChunksPerSplit = 1 << 14;  // int64 accumulators: 2^14 * 2^48 < 2^63
@@ -54,8 +55,8 @@ using namespace tcx;
 
 // acc += v * 2^sh, exact (v an integer-valued float below 2^23 in magnitude)
 struct Smem {
-  alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // one digit slice of A: 16 KB
-  alignas(1024) __nv_bfloat16 w[kStages][2 * kBN * kBK];  // both digits of Omega: 128 rows, 16 KB
+  alignas(1024) __nv_bfloat16 a[kStages][kDual][kBM * kBK];      // one digit slice of A, two K steps: 32 KB
+  alignas(1024) __nv_bfloat16 w[kStages][kDual][2 * kBN * kBK];  // both digits of Omega per K step: 32 KB
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t ready[kGroups];  // group g of the current chunk is final
@@ -63,6 +64,8 @@ struct Smem {
   uint64_t drain;
   uint32_t tmem_base;
 };
+static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of k_sketch_f64emu exceeds 227 KB");
+static_assert(kChunkSteps % kDual == 0, "a stage never straddles an exact chunk");
 
 // Grid: x = tiles of Omega rows (fastest, so CTAs that share an A tile run
 // together and reuse it from L2), y = tiles of A's columns, z = K splits of
@@ -102,20 +105,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = sm.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer.  Stage order: chunk c, slice s, step j; each
-    // stage holds digit slice s of A and both Omega digits at K step j.
+    // ---------------- TMA producer.  Stage order: chunk c, slice s, step pair j/2;
+    // each stage holds digit slice s of A at K steps j and j+1 (one box of two
+    // adjacent tiles) and both Omega digits at those steps.  Splits start and end on
+    // chunk boundaries, so a step j+1 past the chunk only occurs at the end of K,
+    // where the boxes read the zero fill past the tensors' extents.
     int it = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
       for (int s = 0; s < kSlices && ok; ++s) {
-        for (int j = 0; j < steps_c; ++j, ++it) {
+        for (int j = 0; j < steps_c; j += kDual, ++it) {
           const int b = it % kStages;
           if (it >= kStages && !mbar_wait(&sm.empty[b], ((it / kStages) + 1) & 1, st)) { ok = false; break; }
-          mbar_expect_tx(&sm.full[b], (kBM + 2 * kBN) * kBK * 2);
+          mbar_expect_tx(&sm.full[b], kDual * (kBM + 2 * kBN) * kBK * 2);
           const int k0 = kbeg + (c * kChunkSteps + j) * kBK;
           tma_load_4d(sm.a[b], &map_a, &sm.full[b], 0, 0, k0 / kBK, s * (int)gridDim.y + (int)blockIdx.y);
-          tma_load_3d(sm.w[b], &map_w, &sm.full[b], k0, n0, 0);
+#pragma unroll
+          for (int h = 0; h < kDual; ++h) tma_load_3d(sm.w[b][h], &map_w, &sm.full[b], k0 + h * kBK, n0, 0);
         }
       }
     }
@@ -138,23 +145,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after_sync();
         }
         const uint32_t dst = tmem + s * kBN;
-        for (int j = 0; j < steps_c; ++j, ++it) {
+        for (int j = 0; j < steps_c; j += kDual, ++it) {
           const int b = it % kStages;
           if (!mbar_wait(&sm.full[b], (it / kStages) & 1, st)) { ok = false; break; }
           fence_after_sync();
-          const uint64_t da = desc_sw128(sm.a[b]);
-          const uint64_t dq1 = desc_sw128(sm.w[b]);             // high digit of Omega (weight 1)
-          const uint64_t dq0 = desc_sw128(sm.w[b] + kBN * kBK);  // low digit (weight 2^-8)
+          for (int h = 0; h < kDual && j + h < steps_c; ++h) {
+            const uint64_t da = desc_sw128(sm.a[b][h]);
+            const uint64_t dq1 = desc_sw128(sm.w[b][h]);             // high digit of Omega (weight 1)
+            const uint64_t dq0 = desc_sw128(sm.w[b][h] + kBN * kBK);  // low digit (weight 2^-8)
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const bool first = (j == 0 && kk == 0);
-            if (first && s > 0) {
-              // group s continues, group s+1 starts: two MMAs with their own flags
-              mma_bf16(dst, da, dq1, id64, 1u);
-              mma_bf16(dst + kBN, da, dq0, id64, 0u);
-            } else {
-              // groups s and s+1 at once (N = 128: q1 rows then q0 rows)
-              mma_bf16(dst, da + 2 * kk, dq1 + 2 * kk, id128, (first && s == 0) ? 0u : 1u);
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const bool first = (j + h == 0 && kk == 0);
+              if (first && s > 0) {
+                // group s continues, group s+1 starts: two MMAs with their own flags
+                mma_bf16(dst, da, dq1, id64, 1u);
+                mma_bf16(dst + kBN, da, dq0, id64, 0u);
+              } else {
+                // groups s and s+1 at once (N = 128: q1 rows then q0 rows)
+                mma_bf16(dst, da + 2 * kk, dq1 + 2 * kk, id128, (first && s == 0) ? 0u : 1u);
+              }
             }
           }
           mma_commit(&sm.empty[b]);
@@ -390,13 +399,14 @@ bool make_map_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t oute
 }
 
 // A's digit tiles as a 4-D tensor: (k within the tile, column within the tile,
-// K block, slice-major tile index); a box is one whole kBK x kBM tile.
+// K block, slice-major tile index); a box is kDual whole kBK x kBM tiles adjacent
+// along K (one contiguous run of memory).
 bool make_map_tiles(CUtensorMap* map, const void* base, int64_t kblocks, int64_t tiles) {
   auto fn = tensor_map_encoder();
   if (fn == nullptr) return false;
   cuuint64_t dims[4] = {(cuuint64_t)kBK, (cuuint64_t)kBM, (cuuint64_t)kblocks, (cuuint64_t)tiles};
   cuuint64_t strides[3] = {(cuuint64_t)kBK * 2, (cuuint64_t)kBK * kBM * 2, (cuuint64_t)kblocks * kBK * kBM * 2};
-  cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kBM, (cuuint32_t)kDual, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -33,7 +33,7 @@ using namespace tcx;
 constexpr int kBM = 128;       // columns of A per tile (MMA M)
 constexpr int kBN = 64;        // rows of Omega per tile (MMA N)
 constexpr int kBK = 128;       // K per stage = one scale block
-constexpr int kStages = 6;
+constexpr int kStages = 4;        // 96 KB per CTA: two CTAs (2 x 256 tensor-memory columns) share an SM
 constexpr int kAcc = 4;        // accumulators of kBN columns in tensor memory
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = kAcc * kBN;
@@ -52,7 +52,7 @@ struct Smem {
 // Grid: x = tiles of A's columns, y = tiles of Omega rows, z = K splits of kchunk
 // (a multiple of kBK).  scale: column-major nbs x n block scales.  out: FP32
 // partial (n x rows, row stride out_ld) of split blockIdx.z.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_sketch_tc_fp8(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
                     const float* __restrict__ scale, int64_t nbs, int n, int rows, int K, int kchunk,
                     float* __restrict__ out, int64_t out_ld, int64_t zstride, DevState* st, const int32_t* done) {

@@ -51,18 +51,20 @@ constexpr int kThreads = 192;
 template <int KD>
 struct Cfg {
   static constexpr int kBN = 32;
-  static constexpr int kAStages = 6;  // A slices in flight
+  static constexpr int kChunkStepsC = (1024 / KD) / kBK;
+  static constexpr int kAStages = 6 / kChunkStepsC;  // stages of A in flight, one (chunk, slice) each
   static constexpr int kChunkSteps = (1024 / KD) / kBK;
   static constexpr int kGroupCols = KD * kBN;  // tensor-memory columns per accumulator set
   static constexpr uint32_t kTmemCols = 2 * kGroupCols <= 256 ? 256 : 512;
 };
 
-// Stage order (chunk c, slice s, K step j): consecutive A stages continue the same
-// rows of one digit plane (DRAM locality); B's digits of a whole chunk stay resident
-// (two chunk buffers).
+// Stage order (chunk c, slice s): a stage holds one digit plane of A's rows at every
+// K step of the chunk (one barrier per 16 KB x chunk steps: a TMA stream with one
+// barrier per 16 KB box runs well below HBM bandwidth at one CTA per SM); B's digits
+// of a whole chunk stay resident (two chunk buffers).
 template <int KD>
 struct Smem {
-  alignas(1024) __nv_bfloat16 a[Cfg<KD>::kAStages][kBM * kBK];                          // 16 KB each
+  alignas(1024) __nv_bfloat16 a[Cfg<KD>::kAStages][Cfg<KD>::kChunkStepsC][kBM * kBK];  // 16 KB per K step
   alignas(1024) __nv_bfloat16 b[2][Cfg<KD>::kChunkSteps][KD][Cfg<KD>::kBN * kBK];      // 4 KB each
   uint64_t a_full[Cfg<KD>::kAStages];
   uint64_t a_empty[Cfg<KD>::kAStages];
@@ -137,16 +139,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < kD; ++t)
           tma_load_3d(sm.b[bb][jj][t], &map_b, &sm.b_full[bb], kbeg + (c * kChunkSteps + jj) * kBK, n0, t);
       cb = c + 1;
-      for (int s = 0; s < kD && ok; ++s)
-        for (int jj = 0; jj < steps_c; ++jj, ++ai) {
-          const int st_ = ai % kAStages;
-          if (ai >= kAStages && !mbar_wait(&sm.a_empty[st_], ((ai / kAStages) + 1) & 1, st)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&sm.a_full[st_], kBM * kBK * 2);
-          tma_load_3d(sm.a[st_], &map_a, &sm.a_full[st_], kbeg + (c * kChunkSteps + jj) * kBK, m0, s);
+      for (int s = 0; s < kD && ok; ++s, ++ai) {
+        const int st_ = ai % kAStages;
+        if (ai >= kAStages && !mbar_wait(&sm.a_empty[st_], ((ai / kAStages) + 1) & 1, st)) {
+          ok = false;
+          break;
         }
+        mbar_expect_tx(&sm.a_full[st_], steps_c * kBM * kBK * 2);
+        for (int jj = 0; jj < steps_c; ++jj)
+          tma_load_3d(sm.a[st_][jj], &map_a, &sm.a_full[st_], kbeg + (c * kChunkSteps + jj) * kBK, m0, s);
+      }
     }
     // copies still in flight land before the CTA may exit
     for (int i = ai - kAStages < 0 ? 0 : ai - kAStages; i < ai; ++i)
@@ -162,15 +164,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&sm.b_full[u], (c >> 1) & 1, st)) break;
       fence_after_sync();
       const int steps_c = min(kChunkSteps, nsteps - c * kChunkSteps);
-      for (int s = 0; s < kD && ok; ++s) {
-        for (int jj = 0; jj < steps_c; ++jj, ++ai) {
-          const int st_ = ai % kAStages;
-          if (!mbar_wait(&sm.a_full[st_], (ai / kAStages) & 1, st)) {
-            ok = false;
-            break;
-          }
-          fence_after_sync();
-          const uint64_t da = desc_sw128(sm.a[st_]);
+      for (int s = 0; s < kD && ok; ++s, ++ai) {
+        const int st_ = ai % kAStages;
+        if (!mbar_wait(&sm.a_full[st_], (ai / kAStages) & 1, st)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        for (int jj = 0; jj < steps_c; ++jj) {
+          const uint64_t da = desc_sw128(sm.a[st_][jj]);
           // B's planes 0 .. KD-1-s lie back to back: one MMA with N = kBN (KD - s) writes
           // groups s .. KD-1; every group is first written at slice 0, K step 0 of the chunk
           const uint64_t db = desc_sw128(sm.b[u][jj][0]);
@@ -179,8 +181,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk)
             mma_bf16(dst, da + 2 * kk, db + 2 * kk, idn, (jj > 0 || s > 0 || kk > 0) ? 1u : 0u);
-          mma_commit(&sm.a_empty[st_]);
         }
+        mma_commit(&sm.a_empty[st_]);
       }
       if (ok) {
         mma_commit(&sm.b_empty[u]);

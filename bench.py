@@ -98,7 +98,12 @@ except (OSError, ValueError):
     PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes per sketch launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures summarised under profiles/, scaled to the full size by the A bytes read.
-PROFILED_TRAFFIC = {"adaptive_poly_f64": 3.40e9, "adaptive_step_f64": 3.40e9}
+# DRAM bytes (read + write) per launch of the dominant kernel, from ncu captures (the
+# 16384 x 4096 captures of the FP64-accurate and sparse-sign sketches scaled by m n to
+# 40000 x 10000: their traffic grows in proportion)
+PROFILED_TRAFFIC = {"adaptive_poly_f64": 3.40e9, "adaptive_step_f64": 3.40e9,
+                    "adaptive_poly_f64emu": 5.75e9, "adaptive_step_f64emu": 5.75e9,
+                    "adaptive_poly_f64emu_sparse": 3.40e9, "adaptive_poly_f64_sparse": 3.40e9}
 
 
 def algorithmic_flops(m: int, n: int, k: int, b: int) -> float:

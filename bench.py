@@ -85,6 +85,8 @@ WORKLOADS = {
     # points in the unit cube (leaves of at most 1024 points, sizes 64..1024), one persistent launch
     "batched_kernel_f64": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f64", 1e-8, 32),
     "batched_kernel_f32": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f32", 1e-8, 32),
+    # the same batch at a tolerance FP32 can certify (at 1e-8 every FP32 problem runs to its rank cap)
+    "batched_kernel_f32_tol1e-5": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f32", 1e-5, 32),
     "small_batched_kernel_f64": (2 ** 16, 512, "kernel", {"leaf_max": 512, "h": 0.3}, "f64", 1e-8, 32),
 }
 DEFAULT_WORKLOAD = "adaptive_poly_f64emu"

@@ -234,9 +234,22 @@ __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, d
 
 // The same map in FP32 on the leading 24 bits, for outputs of at most 16 bits
 // (BF16, E4M3), where the FP64 evaluation buys nothing.
+// (float)x rounded to nearest even, for x < 2^63, with integer operations and a
+// 32-bit conversion: GB300 executes 64-bit integer-to-float conversions on its
+// FP64 pipe (about two per clock per SM), which made them the bottleneck of the
+// Gaussian generators.  The result is the same float as the 64-bit conversion.
+__device__ __forceinline__ float u64_to_f32_rn(uint64_t x) {
+  if (x < (1ull << 24)) return __uint2float_rn((uint32_t)x);  // exact
+  const int sh = (64 - __clzll((long long)x)) - 24;            // bits below the 24 kept
+  uint64_t q = x >> sh;
+  const uint64_t rem = x & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;  // q <= 2^24: exact in FP32
+  return __uint2float_rn((uint32_t)q) * __int_as_float((127 + sh) << 23);  // times 2^sh, exact
+}
+
 __device__ __forceinline__ void box_muller_f32(uint64_t a, uint64_t b, float& z0, float& z1) {
-  const float u1 = (float)((a >> 40) + 1ull) * 0x1.0p-24f;
-  const float u2 = (float)((b >> 40) + 1ull) * 0x1.0p-24f;
+  const float u1 = __uint2float_rn((uint32_t)((a >> 40) + 1ull)) * 0x1.0p-24f;  // <= 2^24: exact
+  const float u2 = __uint2float_rn((uint32_t)((b >> 40) + 1ull)) * 0x1.0p-24f;
   const float r = sqrtf(-2.0f * logf(u1));
   float sn, cs;
   sincospif(2.0f * u2, &sn, &cs);
@@ -259,9 +272,9 @@ __device__ __forceinline__ void box_muller_f32_53(uint64_t a, uint64_t b, float&
   float ln1;
   if (n1 >= (1ull << 52)) {
     const uint64_t d = (1ull << 53) - n1;  // 0 .. 2^52
-    ln1 = log1pf(-(float)d * 0x1.0p-53f);
+    ln1 = log1pf(-u64_to_f32_rn(d) * 0x1.0p-53f);
   } else {
-    ln1 = logf((float)n1 * 0x1.0p-53f);
+    ln1 = logf(u64_to_f32_rn(n1) * 0x1.0p-53f);
   }
   const float r = sqrtf(-2.0f * ln1);
   const uint64_t n2 = (b >> 11) + 1ull;
@@ -273,8 +286,8 @@ __device__ __forceinline__ void box_muller_f32_53(uint64_t a, uint64_t b, float&
     const uint64_t q = n2 >> sh, rem = n2 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
     nh = (q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull)) << sh;
   }
-  const float xh = (float)nh * 0x1.0p-52f;                         // exact: nh has 24 bits
-  const float t = 3.14159265358979323846f * ((float)(int64_t)(n2 - nh) * 0x1.0p-52f);  // pi x_lo
+  const float xh = u64_to_f32_rn(nh) * 0x1.0p-52f;                         // exact: nh has 24 bits
+  const float t = 3.14159265358979323846f * (__int2float_rn((int32_t)(int64_t)(n2 - nh)) * 0x1.0p-52f);  // pi x_lo
   float sn, cs;
   sincospif(xh, &sn, &cs);
   z0 = r * fmaf(-t, sn, cs);

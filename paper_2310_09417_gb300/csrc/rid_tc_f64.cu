@@ -309,6 +309,29 @@ __device__ __forceinline__ int omega_q_f32(float qf) {
 }
 
 constexpr int kOmegaThreads = 256;
+constexpr int kAmbCap = 2048;  // listed samples per CTA: a flush leaves room for one more iteration (<= 1024)
+
+// The listed samples (global element e, sample u of its four: code 4 e + u) are
+// recomputed in FP64 by all the CTA's threads together, 256 at a time, so that the
+// FP64 Box-Muller (GB300: about two FP64 instructions per clock per SM, a warp
+// instruction costing the same whatever its active lanes) runs on full warps.
+template <bool kGrid>
+__device__ __forceinline__ void omega_flush(const uint64_t* list, int cnt, uint64_t seed, int64_t row0, int64_t nq,
+                                            int64_t ldw, int64_t plane, __nv_bfloat16* W, double* G, int64_t ldg) {
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const uint64_t code = list[k];
+    const int u = (int)(code & 3u);
+    const int64_t e = (int64_t)(code >> 2), r = e / nq, q = e - r * nq;
+    uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + r), x2 = 0, x3 = 0;
+    philox4x64_10(x0, x1, x2, x3, seed, 0ull);
+    double z0, z1;
+    if (u < 2)
+      box_muller(x0, x1, z0, z1);
+    else
+      box_muller(x2, x3, z0, z1);
+    write_omega_q<kGrid>(omega_q_f64((u & 1) ? z1 : z0), W, plane, r * ldw + 4 * q + u, G, r * ldg + 4 * q + u);
+  }
+}
 
 template <bool kGrid>
 __global__ void __launch_bounds__(kOmegaThreads)
@@ -316,15 +339,18 @@ __global__ void __launch_bounds__(kOmegaThreads)
                    const double* __restrict__ src, int64_t ld_src, __nv_bfloat16* __restrict__ W,
                    double* __restrict__ G, int64_t ldg, const int32_t* done) {
   if (done != nullptr && *done) return;
-  __shared__ uint8_t amb_list[kOmegaThreads / 32][128];  // per warp: lane | u << 5
+  __shared__ uint64_t amb_list[kAmbCap];
+  __shared__ int amb_cnt;
   const int64_t nq = (ldw + 3) >> 2;
   const int64_t total = rows * nq;
   const int64_t plane = rows_alloc * ldw;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // warp-aligned bases: every lane of a warp runs the same number of iterations
-  for (int64_t eb = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); eb < total; eb += stride) {
-    const int64_t e = eb + lane;
+  if (threadIdx.x == 0) amb_cnt = 0;
+  __syncthreads();
+  // CTA-uniform iterations (every thread runs the same count: the flushes synchronise)
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {
+    const int64_t e = base + threadIdx.x;
     const bool valid = e < total;
     const int64_t r = valid ? e / nq : 0, q = valid ? e - r * nq : 0;
     if (src != nullptr) {
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(kOmegaThreads)
         }
       continue;
     }
-    bool amb[4] = {false, false, false, false};
+    unsigned amb = 0;  // bit u: sample u goes to the FP64 list
     if (valid) {
       uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + r), x2 = 0, x3 = 0;
       philox4x64_10(x0, x1, x2, x3, seed, 0ull);
@@ -353,35 +379,38 @@ __global__ void __launch_bounds__(kOmegaThreads)
           continue;
         }
         const float qf = zf[u] * 2048.0f;  // exact (a power of two)
-        amb[u] = fabsf(qf - floorf(qf) - 0.5f) < 0x1.0p-6f + fabsf(qf) * 0x1.0p-19f;
-        if (!amb[u]) write_omega_q<kGrid>(omega_q_f32(qf), W, plane, r * ldw + i, G, r * ldg + i);
+        if (fabsf(qf - floorf(qf) - 0.5f) < 0x1.0p-6f + fabsf(qf) * 0x1.0p-19f)
+          amb |= 1u << u;
+        else
+          write_omega_q<kGrid>(omega_q_f32(qf), W, plane, r * ldw + i, G, r * ldg + i);
       }
     }
-    // the warp's ambiguous samples, recomputed in FP64 by its lanes together
-    unsigned cnt = 0;
+    // append this iteration's listed samples: one shared atomic per warp
+    const int mine = __popc(amb);
+    int incl = mine;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const unsigned mask = __ballot_sync(0xffffffffu, amb[u]);
-      if (amb[u]) amb_list[wid][cnt + __popc(mask & ((1u << lane) - 1u))] = (uint8_t)(lane | (u << 5));
-      cnt += __popc(mask);
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
     }
-    __syncwarp();
-    for (unsigned k = lane; k < cnt; k += 32) {
-      const int code = amb_list[wid][k];
-      const int l = code & 31, u = code >> 5;
-      const int64_t e2 = eb + l, r2 = e2 / nq, q2 = e2 - r2 * nq;
-      uint64_t x0 = (uint64_t)q2, x1 = (uint64_t)(row0 + r2), x2 = 0, x3 = 0;
-      philox4x64_10(x0, x1, x2, x3, seed, 0ull);
-      double z0, z1;
-      if (u < 2)
-        box_muller(x0, x1, z0, z1);
-      else
-        box_muller(x2, x3, z0, z1);
-      write_omega_q<kGrid>(omega_q_f64((u & 1) ? z1 : z0), W, plane, r2 * ldw + 4 * q2 + u, G,
-                           r2 * ldg + 4 * q2 + u);
+    int wbase = 0;
+    if (lane == 31 && incl > 0) wbase = atomicAdd(&amb_cnt, incl);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    int at = wbase + incl - mine;
+    for (int u = 0; u < 4; ++u)
+      if (amb & (1u << u)) amb_list[at++] = ((uint64_t)e << 2) | (uint64_t)u;
+    __syncthreads();
+    const int cnt = amb_cnt;
+    __syncthreads();  // every thread has read the count before the next iteration appends
+    if (cnt > kAmbCap - kOmegaThreads * 4) {  // no room for another iteration: recompute now
+      omega_flush<kGrid>(amb_list, cnt, seed, row0, nq, ldw, plane, W, G, ldg);
+      __syncthreads();
+      if (threadIdx.x == 0) amb_cnt = 0;
+      __syncthreads();
     }
-    __syncwarp();
   }
+  __syncthreads();
+  omega_flush<kGrid>(amb_list, amb_cnt, seed, row0, nq, ldw, plane, W, G, ldg);
 }
 
 // ------------------------------------------------------------------ host side
@@ -416,6 +445,18 @@ bool make_map_tiles(CUtensorMap* map, const void* base, int64_t kblocks, int64_t
 }  // namespace tc64
 
 int64_t f64emu_pad(int64_t m) { return (m + 7) / 8 * 8; }
+namespace {
+// Omega generator grid: at most eight 256-thread CTAs per SM, so that each CTA runs
+// several iterations and its list of FP64 recomputations fills whole warps.
+int64_t omega_blocks(int64_t rows, int64_t ldw) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 148;
+  int64_t blocks = (rows * ((ldw + 3) / 4) + tc64::kOmegaThreads - 1) / tc64::kOmegaThreads;
+  if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+  return blocks < 1 ? 1 : blocks;
+}
+}  // namespace
 namespace {
 int64_t digit_kblocks(int64_t m) { return (m + tc64::kBK - 1) / tc64::kBK; }
 int64_t digit_tiles(int64_t n) { return (n + tc64::kBM - 1) / tc64::kBM; }
@@ -470,9 +511,7 @@ cudaError_t f64_colexp(const double* A, int64_t lda, int64_t m, int64_t n, int32
 cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, int64_t rows_alloc,
                          const double* src, int64_t ld_src, void* wdigits, const int32_t* done, cudaStream_t s) {
   const int64_t ldw = f64emu_pad(m);
-  int64_t blocks = (rows * ((ldw + 3) / 4) + tc64::kOmegaThreads - 1) / tc64::kOmegaThreads;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
+  const int64_t blocks = omega_blocks(rows, ldw);
   tc64::k_omega_digits<false><<<(int)blocks, tc64::kOmegaThreads, 0, s>>>(
       seed, row0, rows, m, ldw, rows_alloc, src, ld_src, static_cast<__nv_bfloat16*>(wdigits), nullptr, 0, done);
   return cudaGetLastError();
@@ -481,9 +520,7 @@ cudaError_t f64emu_omega(uint64_t seed, int64_t row0, int64_t rows, int64_t m, i
 cudaError_t f64emu_omega_grid(uint64_t seed, int64_t row0, int64_t rows, int64_t m, double* out, int64_t ld,
                               cudaStream_t s) {
   const int64_t ldw = f64emu_pad(m);
-  int64_t blocks = (rows * ((ldw + 3) / 4) + tc64::kOmegaThreads - 1) / tc64::kOmegaThreads;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
+  const int64_t blocks = omega_blocks(rows, ldw);
   tc64::k_omega_digits<true><<<(int)blocks, tc64::kOmegaThreads, 0, s>>>(seed, row0, rows, m, ldw, rows, nullptr, 0,
                                                                          nullptr, out, ld, nullptr);
   return cudaGetLastError();

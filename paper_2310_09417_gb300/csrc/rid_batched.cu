@@ -209,13 +209,31 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
   T* X = static_cast<T*>(pr.X);
   const int64_t lda = pr.lda, ldx = pr.ldx;
   // ||A||_F^2 and finiteness
+  // (FP32: exact squares in float-float, folded into FP64 every 64 terms -- GB300
+  // issues about two FP64 instructions per clock per SM, and per-element FP64 work
+  // cost more than this kernel's FP32 arithmetic)
   double acc = 0.0;
   bool finite = true;
-  for (int64_t e = tid; e < (int64_t)m * n; e += kNT) {
-    const int64_t j = e / m, i = e - j * m;
-    const double v = static_cast<double>(A[j * lda + i]);
-    finite = finite && isfinite(v);
-    acc += v * v;
+  if constexpr (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    int cnt = 0;
+    for (int j = 0; j < n; ++j)
+      for (int i = tid; i < m; i += kNT) {
+        sq_add_f32(static_cast<float>(A[(int64_t)j * lda + i]), hi, lo, acc, finite);
+        if (++cnt == 64) {
+          acc += (double)hi + (double)lo;
+          hi = lo = 0.f;
+          cnt = 0;
+        }
+      }
+    acc += (double)hi + (double)lo;
+  } else {
+    for (int64_t e = tid; e < (int64_t)m * n; e += kNT) {
+      const int64_t j = e / m, i = e - j * m;
+      const double v = static_cast<double>(A[j * lda + i]);
+      finite = finite && isfinite(v);
+      acc += v * v;
+    }
   }
   const int bad = __syncthreads_or(!finite);
   const double n2 = block_sum(acc);
@@ -245,24 +263,24 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
   int64_t k = 0;
   for (;;) {
     // Gaussian rows [t*b, t*b + b) of Omega (same counters as the single-problem path)
-    const int64_t nq = (m + 3) / 4;
-    for (int64_t e = tid; e < (int64_t)b * nq; e += kNT) {
-      const int64_t i = e / nq, q = e - i * nq;
+    // (32-bit indices: a 64-bit division is an FP64-pipe routine on GB300)
+    const int nq = (m + 3) / 4;
+    for (int e = tid; e < b * nq; e += kNT) {
+      const int i = e / nq, q = e - i * nq;
       uint64_t x0 = (uint64_t)q, x1 = (uint64_t)((int64_t)t * b + i), x2 = 0, x3 = 0;
       philox4x64_10(x0, x1, x2, x3, p.seed, 0ull);
-      double z[4];
+      T* o = sl.omega + (int64_t)i * p.mmax + 4 * q;
       if constexpr (sizeof(T) == 4) {  // FP32: the FP32 evaluation of the same map
         float f[4];
         box_muller_f32_53(x0, x1, f[0], f[1]);
         box_muller_f32_53(x2, x3, f[2], f[3]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) z[j] = f[j];
+        for (int j = 0; j < 4 && 4 * q + j < m; ++j) o[j] = f[j];
       } else {
+        double z[4];
         box_muller(x0, x1, z[0], z[1]);
         box_muller(x2, x3, z[2], z[3]);
+        for (int j = 0; j < 4 && 4 * q + j < m; ++j) o[j] = from_d<T>(z[j]);
       }
-      T* o = sl.omega + i * p.mmax + 4 * q;
-      for (int j = 0; j < 4 && 4 * q + j < m; ++j) o[j] = from_d<T>(z[j]);
     }
     __syncthreads();
     // sketch G (n x b) = (Omega A)^T
@@ -276,12 +294,27 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
       __syncthreads();
     }
     double e2 = 0.0;
-    for (int e = tid; e < na * b; e += kNT) {
-      const int i = e / b, c = e - i * b;
-      T v = sl.G[(int64_t)sl.act[cur][i] * b + c];
-      if (tb > 0) v -= sl.S[(int64_t)i * b + c];
-      sl.S[(int64_t)i * b + c] = v;
-      e2 += static_cast<double>(v) * static_cast<double>(v);
+    {
+      float hi = 0.f, lo = 0.f;
+      bool fin = true;
+      int cnt = 0;
+      for (int e = tid; e < na * b; e += kNT) {
+        const int i = e / b, c = e - i * b;
+        T v = sl.G[(int64_t)sl.act[cur][i] * b + c];
+        if (tb > 0) v -= sl.S[(int64_t)i * b + c];
+        sl.S[(int64_t)i * b + c] = v;
+        if constexpr (sizeof(T) == 4) {
+          sq_add_f32(v, hi, lo, e2, fin);
+          if (++cnt == 64) {
+            e2 += (double)hi + (double)lo;
+            hi = lo = 0.f;
+            cnt = 0;
+          }
+        } else {
+          e2 += static_cast<double>(v) * static_cast<double>(v);
+        }
+      }
+      if constexpr (sizeof(T) == 4) e2 += (fin ? (double)hi + (double)lo : (double)INFINITY);
     }
     e2 = block_sum(e2);
     if (tid == 0) sh.red = e2;
@@ -316,14 +349,31 @@ __device__ void run_problem(const Params& p, const Problem& pr, Result& res, Slo
       ArgMax a;
       a.v = -1.0;
       a.idx = -1;
-      for (int r = tid; r < na; r += kNT)
-        if (!sh.sel[r]) {
-          ArgMax o;
-          o.v = static_cast<double>(tabs(R[r * ldr + c]));
-          o.idx = r;
-          a = argmax_pick(a, o);
+      if constexpr (sizeof(T) == 4) {
+        // FP32: keys (|v| bit pattern, ~row) compared as integers -- the same choice
+        // (largest |v|, ties to the smaller row) without per-element FP64 work
+        unsigned long long best = 0ull;
+        for (int r = tid; r < na; r += kNT)
+          if (!sh.sel[r]) {
+            const unsigned long long kk = ((unsigned long long)(__float_as_uint(R[r * ldr + c]) & 0x7FFFFFFFu) << 32) |
+                                          (unsigned long long)(0xFFFFFFFFu - (unsigned)r);
+            best = kk > best ? kk : best;
+          }
+        best = block_max_u64(best);
+        if (best != 0ull) {
+          a.idx = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFull));
+          a.v = (double)__uint_as_float((unsigned)(best >> 32));
         }
-      a = block_argmax(a);
+      } else {
+        for (int r = tid; r < na; r += kNT)
+          if (!sh.sel[r]) {
+            ArgMax o;
+            o.v = static_cast<double>(tabs(R[r * ldr + c]));
+            o.idx = r;
+            a = argmax_pick(a, o);
+          }
+        a = block_argmax(a);
+      }
       const int pr_ = a.idx;
       const bool zero = !(a.v > 0.0);
       for (int cc = tid; cc < b; cc += kNT) sh.prow[cc] = R[pr_ * ldr + cc];

@@ -121,6 +121,34 @@ __device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
   return a;
 }
 
+// Block-wide maximum of 64-bit keys (0 = no candidate), by integer compares.
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long k) {
+  __shared__ unsigned long long s_k[32];
+  __shared__ unsigned long long s_res64;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, k, off);
+    k = o > k ? o : k;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_k[warp] = k;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long b = lane < nw ? s_k[lane] : 0ull;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_down_sync(0xffffffffu, b, off);
+      b = o > b ? o : b;
+    }
+    if (lane == 0) s_res64 = b;
+  }
+  __syncthreads();
+  const unsigned long long r = s_res64;
+  __syncthreads();
+  return r;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -148,6 +176,27 @@ __device__ __forceinline__ void sq_add_bits(uint32_t bits, float& hi, float& lo,
   const float x = __uint_as_float(bits);
   if (ex - 64u <= 116u) {
     sq_twosum(__fmul_rn(x, x), hi, lo);
+  } else if ((bits << 1) == 0u) {
+  } else if (ex == 0xFFu) {
+    finite = false;
+  } else {
+    acc += (double)x * (double)x;
+  }
+}
+
+// x^2 added to a float-float sum for an FP32 x: the square's rounding error comes
+// exactly from an FMA (TwoProduct) and the sum's from TwoSum; |x| outside
+// [2^-63, 2^54) (tiny, subnormal, huge) and zeros take the FP64 sum, NaN / Inf
+// clear `finite`.  A few dozen squares stay within about 2^-45 relative before
+// they are folded into FP64.
+__device__ __forceinline__ void sq_add_f32(float x, float& hi, float& lo, double& acc, bool& finite) {
+  const uint32_t bits = __float_as_uint(x);
+  const uint32_t ex = (bits >> 23) & 0xFFu;
+  if (ex - 64u <= 116u) {
+    const float p = __fmul_rn(x, x);
+    const float e = fmaf(x, x, -p);
+    sq_twosum(p, hi, lo);
+    lo = __fadd_rn(lo, e);
   } else if ((bits << 1) == 0u) {
   } else if (ex == 0xFFu) {
     finite = false;

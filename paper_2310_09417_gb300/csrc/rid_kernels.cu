@@ -42,39 +42,69 @@ __device__ __forceinline__ double to_double(T x) {
 __device__ __forceinline__ double to_double(__nv_bfloat16 x) { return static_cast<double>(__bfloat162float(x)); }
 
 // ============================================================ Gaussian rows
+// FP32 / BF16 / E4M3 outputs are converted from the FP32 value directly (the same
+// rounding of the same value as through FP64, without FP64 instructions: GB300
+// issues about two per clock per SM); indices are 32-bit when they fit (a 64-bit
+// division is an FP64-pipe routine).
+template <typename T>
+__device__ __forceinline__ T from_float(float x);
+template <>
+__device__ __forceinline__ float from_float<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 from_float<__nv_fp8_e4m3>(float x) {
+  __nv_fp8_e4m3 q;
+  q.__x = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);  // nearest even, saturating at +-448
+  return q;
+}
+
+template <typename T, typename I>
+__device__ __forceinline__ void gaussian_quad(uint64_t seed, int64_t row0, I e, I nq, int64_t m, T* __restrict__ out,
+                                              int64_t ld) {
+  const I i = e / nq, q = e - i * nq;
+  uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + (int64_t)i), x2 = 0, x3 = 0;
+  philox4x64_10(x0, x1, x2, x3, seed, 0ull);
+  T* o = out + (int64_t)i * ld + 4 * (int64_t)q;
+  const int64_t lim = m - 4 * (int64_t)q;
+  if constexpr (sizeof(T) == 8) {
+    double z[4];
+    box_muller(x0, x1, z[0], z[1]);
+    box_muller(x2, x3, z[2], z[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < lim) o[j] = from_double<T>(z[j]);
+  } else {
+    float f[4];
+    if constexpr (sizeof(T) <= 2) {  // BF16 / E4M3 output: Box-Muller in FP32 on 24-bit uniforms
+      box_muller_f32(x0, x1, f[0], f[1]);
+      box_muller_f32(x2, x3, f[2], f[3]);
+    } else {  // FP32 output: FP32 evaluation on 53-bit uniforms
+      box_muller_f32_53(x0, x1, f[0], f[1]);
+      box_muller_f32_53(x2, x3, f[2], f[3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < lim) o[j] = from_float<T>(f[j]);
+  }
+}
+
 template <typename T>
 __global__ void k_gaussian_rows(uint64_t seed, int64_t row0, int64_t rows, int64_t m, T* __restrict__ out,
                                 int64_t ld, const int32_t* done) {
   if (done != nullptr && *done) return;
   const int64_t nq = (m + 3) >> 2;
   const int64_t total = rows * nq;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / nq, q = e - i * nq;
-    uint64_t x0 = (uint64_t)q, x1 = (uint64_t)(row0 + i), x2 = 0, x3 = 0;
-    philox4x64_10(x0, x1, x2, x3, seed, 0ull);
-    double z[4];
-    if constexpr (sizeof(T) <= 2) {  // BF16 / E4M3 output: Box-Muller in FP32
-      float f[4];
-      box_muller_f32(x0, x1, f[0], f[1]);
-      box_muller_f32(x2, x3, f[2], f[3]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) z[j] = f[j];
-    } else if constexpr (sizeof(T) == 4) {  // FP32 output: FP32 evaluation on 53-bit uniforms
-      float f[4];
-      box_muller_f32_53(x0, x1, f[0], f[1]);
-      box_muller_f32_53(x2, x3, f[2], f[3]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) z[j] = f[j];
-    } else {
-      box_muller(x0, x1, z[0], z[1]);
-      box_muller(x2, x3, z[2], z[3]);
-    }
-    T* o = out + i * ld + 4 * q;
-    const int64_t lim = m - 4 * q;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < lim) o[j] = from_double<T>(z[j]);
+  if (total + (int64_t)gridDim.x * blockDim.x < ((int64_t)1 << 31)) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (int)total; e += gridDim.x * blockDim.x)
+      gaussian_quad<T, int>(seed, row0, e, (int)nq, m, out, ld);
+  } else {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+      gaussian_quad<T, int64_t>(seed, row0, e, nq, m, out, ld);
   }
 }
 
@@ -144,9 +174,54 @@ __global__ void k_norm2_bf16(int64_t m, int64_t n, const __nv_bfloat16* __restri
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+// FP32 columns: four elements per load when 16-byte aligned, each square's rounding
+// error recovered exactly by an FMA and summed in float-float groups of 64
+// (sq_add_f32), folded into FP64.
+__global__ void k_norm2_f32(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda, double* part,
+                            DevState* st) {
+  double acc = 0.0;
+  bool finite = true;
+  const bool vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+  const int64_t nv = vec ? m / 4 : 0;
+  float hi = 0.f, lo = 0.f;
+  int grp = 0;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const float* a = A + j * lda;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+      const float4 w = __ldg(a4 + v);
+      sq_add_f32(w.x, hi, lo, acc, finite);
+      sq_add_f32(w.y, hi, lo, acc, finite);
+      sq_add_f32(w.z, hi, lo, acc, finite);
+      sq_add_f32(w.w, hi, lo, acc, finite);
+      if (++grp == 16) {
+        acc += (double)hi + (double)lo;
+        hi = lo = 0.f;
+        grp = 0;
+      }
+    }
+    for (int64_t i = nv * 4 + threadIdx.x; i < m; i += blockDim.x) {
+      sq_add_f32(a[i], hi, lo, acc, finite);
+      if (++grp == 16) {
+        acc += (double)hi + (double)lo;
+        hi = lo = 0.f;
+        grp = 0;
+      }
+    }
+  }
+  acc += (double)hi + (double)lo;
+  if (!finite) atomicOr(&st->err, kErrNonFinite);
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 template <typename T>
 cudaError_t norm2_partial(int64_t m, int64_t n, const T* A, int64_t lda, double* part, int nparts,
                           DevState* st, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    k_norm2_f32<<<nparts, 256, 0, s>>>(m, n, A, lda, part, st);
+    return cudaGetLastError();
+  }
   if constexpr (sizeof(T) == 2) {
     if ((lda % 8) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0) {
       k_norm2_bf16<<<nparts, 256, 0, s>>>(m, n, A, lda, part, st);
@@ -492,6 +567,9 @@ __global__ void k_schur_finish(int na, int w, const int32_t* __restrict__ act, c
                                T* __restrict__ S, int64_t lds, double* e2part, const int32_t* done) {
   if (done != nullptr && *done) return;
   double acc2 = 0.0;
+  float hi = 0.f, lo = 0.f;  // FP32: float-float sums of the squares (no per-element FP64 work)
+  bool finite = true;
+  int grp = 0;
   // a warp per row of S, lanes along the row
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < na; i += (int64_t)gridDim.x * wpb)
@@ -501,8 +579,18 @@ __global__ void k_schur_finish(int na, int w, const int32_t* __restrict__ act, c
       for (int z = 0; z < nz; ++z) sub += P[z * zs + i * lds + c];
       v -= sub;
       S[i * lds + c] = v;
-      acc2 += (double)v * (double)v;
+      if constexpr (sizeof(T) == 4) {
+        sq_add_f32(v, hi, lo, acc2, finite);
+        if (++grp == 64) {
+          acc2 += (double)hi + (double)lo;
+          hi = lo = 0.f;
+          grp = 0;
+        }
+      } else {
+        acc2 += (double)v * (double)v;
+      }
     }
+  if constexpr (sizeof(T) == 4) acc2 += finite ? (double)hi + (double)lo : (double)INFINITY;
   const double tot = block_sum(acc2);
   if (threadIdx.x == 0) e2part[blockIdx.x] = tot;
 }
@@ -906,51 +994,60 @@ cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T
 }
 
 // ============================================================ re-blocking
-// Inverse of the unit lower triangular L-hat(piv(0:bt), 0:bt): thread j forms
-// column j by forward substitution.
-// Inverse of the unit-lower block (bt x bt): row i of X = L^{-1} is
-// X(i, j) = -sum_{c=j}^{i-1} L(i, c) X(c, j), j < i.  Rows are formed in order; each
-// column j of a row is summed by 4 threads (interleaved over c) and a shuffle.
-// L and X live in shared memory when both fit, else X is formed in place in Linv.
-constexpr int kLinvSplit = 4;
+// Inverse X of the unit lower triangular L-hat(piv(0:bt), 0:bt) (bt x bt, row-major),
+// X(i, j) = -sum_{c=j}^{i-1} L(i, c) X(c, j) for j < i, each sum taken as four
+// interleaved partial sums (c = j + p mod 4, ascending) combined as
+// (s0 + s1) + (s2 + s3) -- the order the batched kernel uses, so both give the same
+// bits.  Columns are independent solves of L x = e_j: four lanes per column, eight
+// columns per one-warp CTA, bt / 8 CTAs, L in each CTA's shared memory.  A single
+// CTA would run all bt^3/6 FP64 multiply-adds and bt block barriers on one SM
+// (GB300: about two FP64 instructions per clock per SM); here they spread over
+// bt/8 SMs.
+constexpr int kLinvCols = 8;
 template <typename T>
-__global__ void k_linv(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv,
-                       T* __restrict__ Linv, int x_in_smem, const int32_t* done) {
+__global__ void __launch_bounds__(32)
+    k_linv_cols(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv, T* __restrict__ Linv,
+                const int32_t* done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
-  T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt
-  T* X = x_in_smem ? Lp + bt * bt : Linv;
-  for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) {
+  T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt, strictly lower part
+  T* xs = Lp + bt * bt;                    // [kLinvCols][bt]: column j0 + g of X
+  const int lane = threadIdx.x, g = lane >> 2, part = lane & 3;
+  const int j0 = blockIdx.x * kLinvCols, j = j0 + g;
+  for (int e = lane; e < bt * bt; e += 32) {
     const int r = e / bt, c = e - r * bt;
-    Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : (c == r ? T(1) : T(0));
-    X[e] = r == c ? T(1) : T(0);
+    Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : T(0);
   }
-  __syncthreads();
-  const int j = threadIdx.x / kLinvSplit, part = threadIdx.x % kLinvSplit;
-  for (int i = 1; i < bt; ++i) {
+  for (int e = lane; e < kLinvCols * bt; e += 32) {
+    const int gg = e / bt, i = e - gg * bt;
+    xs[e] = i == j0 + gg ? T(1) : T(0);
+  }
+  __syncwarp();
+  T* x = xs + g * bt;
+  for (int i = j0 + 1; i < bt; ++i) {
     T acc = T(0);
     if (j < i)
-      for (int c = j + part; c < i; c += kLinvSplit) acc = fma(Lp[i * bt + c], X[c * bt + j], acc);
+      for (int c = j + part; c < i; c += 4) acc = fma(Lp[i * bt + c], x[c], acc);
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (j < i && part == 0) X[i * bt + j] = -acc;
-    __syncthreads();
+    if (j < i && part == 0) x[i] = -acc;
+    __syncwarp();
   }
-  if (x_in_smem)
-    for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) Linv[e] = X[e];
+  for (int e = lane; e < kLinvCols * bt; e += 32) {
+    const int gg = e / bt, i = e - gg * bt;
+    if (j0 + gg < bt) Linv[i * bt + j0 + gg] = xs[e];
+  }
 }
 
 template <typename T>
 cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
                  cudaStream_t s) {
   static SmemLimit lim;
-  const size_t one = (size_t)bt * bt * sizeof(T);
-  const int x_in_smem = 2 * one <= (size_t)200 * 1024 ? 1 : 0;
-  const size_t smem = x_in_smem ? 2 * one : one;
-  cudaError_t e = raise_smem(k_linv<T>, smem, lim);
+  const size_t smem = ((size_t)bt * bt + (size_t)kLinvCols * bt) * sizeof(T);
+  if (smem > (size_t)227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = raise_smem(k_linv_cols<T>, smem, lim);
   if (e != cudaSuccess) return e;
-  const int threads = (kLinvSplit * bt + 31) / 32 * 32;
-  k_linv<T><<<1, threads, smem, s>>>(bt, S, lds, piv, Linv, x_in_smem, done);
+  k_linv_cols<T><<<(bt + kLinvCols - 1) / kLinvCols, 32, smem, s>>>(bt, S, lds, piv, Linv, done);
   return cudaGetLastError();
 }
 

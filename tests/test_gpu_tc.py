@@ -222,3 +222,21 @@ def test_bf16_nonfinite_is_rejected(B):
     with pytest.raises(B.IDError) as e:
         B.id_adaptive(Ab, 1e-1)
     assert e.value.code == B.ERR_NONFINITE
+
+
+@pytest.mark.parametrize("m,n,ld_pad", [(4096, 40, 0), (1001, 17, 3)])
+def test_f32_norm_matches_fp64_sum_of_squares(B, m, n, ld_pad):
+    """||A||_F of an FP32 matrix (four values per load when aligned, FP32 squares
+    with their FMA rounding errors summed in float-float groups, FP64 across groups)
+    against the FP64 sum of squares, with zeros, tiny, subnormal and huge entries
+    (FP64 branch), an unaligned leading dimension and rows not a multiple of four."""
+    rng = np.random.default_rng(m + 1)
+    A = (rng.standard_normal((m, n)) * np.exp2(rng.integers(-30, 31, size=n))[None, :]).astype(np.float32)
+    A[rng.random((m, n)) < 0.05] = 0.0
+    A[0, 0], A[1, 1], A[2, 2], A[3, 3] = 1e-40, 3e-25, 1e17, -3e18
+    buf = torch.zeros((n, m + ld_pad), dtype=torch.float32, device="cuda")
+    buf[:, :m] = torch.from_numpy(A.T.copy()).cuda()
+    Ad = buf[:, :m].t()
+    ref = float(np.sqrt(np.sum(A.astype(np.float64) ** 2)))
+    g = B.id_adaptive(Ad, 0.9, block=8, k_max=8)
+    assert g.norm_A == pytest.approx(ref, rel=1e-12)

@@ -132,10 +132,17 @@ __host__ __device__ constexpr int fold_exp() {
   return KD == 7 ? 2 - 56 : 2 - 32;
 }
 __device__ __forceinline__ double fold_value(long long w, int ex, double) { return i64_to_double(w, ex); }
-// |w| < 2^38: the hardware conversion rounds once; the power-of-two scale is exact
-// for normal results (an integer-operation conversion measured slower here)
+// |w| < 2^38, rounded once to FP32 without the 64-bit conversion instruction (it
+// runs on GB300's FP64 pipe, about two per clock per SM): w = 2^23 h + l with
+// 0 <= l < 2^23 and |h| < 2^15, both made exact floats by magic-number additions,
+// then fma(h, 2^23, l) -- the exact sum rounded once, as the conversion would.  The
+// power-of-two scale is exact for normal results.
 __device__ __forceinline__ float fold_value(long long w, int ex, float) {
-  const float f = __ll2float_rn(w);
+  const int h = (int)(w >> 23);
+  const int l = (int)(w - ((long long)h << 23));
+  const float fh = __int_as_float(0x4B400000 + h) - 12582912.0f;  // 1.5 * 2^23 + h, |h| < 2^22
+  const float fl = __int_as_float(0x4B000000 | l) - 8388608.0f;   // 2^23 + l, 0 <= l < 2^23
+  const float f = fmaf(fh, 8388608.0f, fl);
   if (ex >= -126 && ex <= 127) return f * __int_as_float((ex + 127) << 23);
   return ldexpf(f, ex);
 }

@@ -188,9 +188,10 @@ def evaluate_large(params, count, family, seed, tols=(1e-4, 1e-8), device="cuda"
     so a pass of many blocks costs about as much as as many passes of one);
     "bf16": the matrix rounded to BF16 with the FP32 LU, whose sketch reads A once
     per pass however many blocks the pass holds (tolerances above BF16's 2^-8),
-    stacked `tall` times (tall_bf16) so that a pass over A outweighs a round's
-    factorisation work, as on the 100000 x 20000 configuration.  The seeded loop
-    saves passes over A, not rounds: each block is still factored on its own."""
+    stacked `tall` times (tall_bf16) to the shape of the 100000 x 20000
+    configuration.  The seeded loop saves passes over A, not rounds: each block is
+    still factored on its own, and the plain loop's automatic passes of four blocks
+    already read A once per four blocks."""
     if precision not in ("f64emu", "bf16"):
         raise ValueError("precision must be 'f64emu' or 'bf16'")
     rng = np.random.default_rng(seed)

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    constexpr uint32_t idesc_wide = idesc_bf16(kBM, NT * BN);  // the NT sub-tiles as one MMA (N <= 256)
     int consumed = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
@@ -115,11 +116,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t da = desc_sw128(sm.a[s]);
       const uint64_t dw = desc_sw128(sm.w[s]);
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)  // advance 16 BF16 = 32 bytes inside the swizzle row
+      for (int kk = 0; kk < kBK / 16; ++kk) {  // advance 16 BF16 = 32 bytes inside the swizzle row
+        if constexpr (NT * BN <= 256 && NT > 1) {
+          // the sub-tiles lie back to back (BN rows of 128 bytes each): one MMA of N = NT BN
+          mma_bf16(tmem, da + 2 * kk, dw + 2 * kk, idesc_wide, (kb | kk) != 0);
+        } else {
 #pragma unroll
-        for (int t = 0; t < NT; ++t)  // sub-tile t: BN rows of 128 bytes, 1024-byte aligned
-          mma_bf16(tmem + t * BN, da + 2 * kk, dw + (uint64_t)((t * BN * kBK * 2) >> 4) + 2 * kk, idesc,
-                   (kb | kk) != 0);
+          for (int t = 0; t < NT; ++t)  // sub-tile t: BN rows of 128 bytes, 1024-byte aligned
+            mma_bf16(tmem + t * BN, da + 2 * kk, dw + (uint64_t)((t * BN * kBK * 2) >> 4) + 2 * kk, idesc,
+                     (kb | kk) != 0);
+        }
+      }
       mma_commit(&sm.empty[s]);
       consumed = kb + 1;
     }

@@ -5,12 +5,13 @@
 // Both operands are K-major (K = m): a column of A and a row of Omega are contiguous.
 //
 // One CTA computes a 128 (columns of A) x NT BN (rows of Omega) tile over a K range:
-//   warp 0   one lane issues TMA loads (128B-swizzled boxes of 64 K x 128 / 64 x NT BN)
-//   warp 1   allocates tensor memory; one lane issues tcgen05.mma (M=128, N=BN, K=16),
-//            NT of them per K step, one per BN-row sub-tile of Omega, all reading the
-//            same stage of A: a pass of many blocks reads each tile of A once per
-//            CTA instead of once per BN rows, and every entry is computed by the same
-//            MMA shape whatever NT is (the same bits for any pass size)
+//   warp 0   one lane issues TMA loads (128B-swizzled boxes of 64 K x 128 / 64 x up to
+//            256 rows of Omega)
+//   warp 1   allocates tensor memory; one lane issues tcgen05.mma (M=128, K=16; N=BN
+//            for one sub-tile, N=256 over four back-to-back sub-tiles), all reading the
+//            same stage of A: a pass of many blocks reads each tile of A once per CTA
+//            instead of once per BN rows, and every entry's sums are the same whatever
+//            NT is (the same bits for any pass size, checked against one-block passes)
 //   warps 2-5 drain the accumulator with tcgen05.ld and write FP32 rows of G
 // A STAGES-deep ring of shared-memory stages is guarded by "full" (TMA bytes landed)
 // and "empty" (the MMAs that read the stage completed) mbarriers.  Every wait is
@@ -31,13 +32,17 @@ namespace tc {
 
 constexpr int kBM = 128;        // columns of A per tile (MMA M)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kStages = 4;
+// stages per CTA: 4 of (16 + 8 NT) KB up to four sub-tiles of Omega (two CTAs per
+// SM at one), 2 of 80 KB at eight
+__host__ __device__ constexpr int stages_for(int nt) { return nt >= 8 ? 2 : 4; }
+constexpr int kWBox = 256;     // rows of Omega per TMA box (the box limit)
 constexpr int kThreads = 192;   // 6 warps
 
 using namespace tcx;
 
 template <int BN, int NT>
 struct Smem {
+  static constexpr int kStages = stages_for(NT);
   alignas(1024) __nv_bfloat16 a[kStages][kBM * kBK];      // 16 KB per stage
   alignas(1024) __nv_bfloat16 w[kStages][NT * BN * kBK];  // NT BN * 128 bytes per stage
   uint64_t full[kStages];
@@ -60,6 +65,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // dynamic shared memory is only guaranteed 16-byte aligned: align the carve-out to 1024
   Smem<BN, NT>& sm =
       *reinterpret_cast<Smem<BN, NT>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kStages = Smem<BN, NT>::kStages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM;       // first column of A
   const int n0 = blockIdx.x * NT * BN;   // first row of Omega
@@ -98,7 +104,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(&sm.full[s], (kBM + NT * BN) * kBK * 2);
       const int k0 = kbeg + kb * kBK;
       tma_load_2d(sm.a[s], &map_a, &sm.full[s], k0, m0);
-      tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);
+#pragma unroll
+      for (int h = 0; h < (NT * BN + kWBox - 1) / kWBox; ++h)  // boxes of at most 256 rows
+        tma_load_2d(sm.w[s] + h * kWBox * kBK, &map_w, &sm.full[s], k0, n0 + h * kWBox);
       issued = kb + 1;
     }
     // copies still in flight must land before the CTA can leave
@@ -107,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-    constexpr uint32_t idesc_wide = idesc_bf16(kBM, NT * BN);  // the NT sub-tiles as one MMA (N <= 256)
+    constexpr int kNW = NT * BN < 256 ? NT * BN : 256;       // N of one MMA over back-to-back sub-tiles
+    constexpr uint32_t idesc_wide = idesc_bf16(kBM, kNW);
     int consumed = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
@@ -117,9 +126,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t dw = desc_sw128(sm.w[s]);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {  // advance 16 BF16 = 32 bytes inside the swizzle row
-        if constexpr (NT * BN <= 256 && NT > 1) {
-          // the sub-tiles lie back to back (BN rows of 128 bytes each): one MMA of N = NT BN
-          mma_bf16(tmem, da + 2 * kk, dw + 2 * kk, idesc_wide, (kb | kk) != 0);
+        if constexpr (NT > 1) {
+          // the sub-tiles lie back to back (BN rows of 128 bytes each): MMAs of N = 256
+          // (the same per-entry sums as one MMA per sub-tile, checked bit for bit)
+#pragma unroll
+          for (int h = 0; h < NT * BN / kNW; ++h)
+            mma_bf16(tmem + h * kNW, da + 2 * kk, dw + (uint64_t)((h * kNW * kBK * 2) >> 4) + 2 * kk, idesc_wide,
+                     (kb | kk) != 0);
         } else {
 #pragma unroll
           for (int t = 0; t < NT; ++t)  // sub-tile t: BN rows of 128 bytes, 1024-byte aligned
@@ -203,6 +216,7 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t ou
 
 template <int BN, int NT>
 size_t smem_bytes() {
+  static_assert(sizeof(Smem<BN, NT>) + 1024 <= 232448, "shared memory of k_sketch_tc_bf16 exceeds 227 KB");
   return sizeof(Smem<BN, NT>) + 1024;  // + alignment slack
 }
 
@@ -227,11 +241,11 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
                            const int32_t* done, cudaStream_t s) {
   constexpr int BN = 64;
   // passes of more than one block: four BN-row sub-tiles of Omega per CTA
-  const bool wide = rows > BN;
-  const int nt = wide ? 4 : 1;
+  // passes of several blocks: four or eight BN-row sub-tiles of Omega per CTA
+  const int nt = rows > 4 * BN ? 8 : (rows > BN ? 4 : 1);
   CUtensorMap ma, mw;
   if (!tc::make_map_bf16(&ma, A, m, n, lda, tc::kBM)) return cudaErrorInvalidValue;
-  if (!tc::make_map_bf16(&mw, W, m, rows, ldw, nt * BN)) return cudaErrorInvalidValue;
+  if (!tc::make_map_bf16(&mw, W, m, rows, ldw, nt * BN < tc::kWBox ? nt * BN : tc::kWBox)) return cudaErrorInvalidValue;
   int kchunk = (int)((m + splits - 1) / splits);
   kchunk = ((kchunk + tc::kBK - 1) / tc::kBK) * tc::kBK;
   const int nz = (int)((m + kchunk - 1) / kchunk);
@@ -239,7 +253,13 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
   if (ytiles > 65535 || nz > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((rows + nt * BN - 1) / (nt * BN)), (unsigned)ytiles, (unsigned)nz);
   cudaError_t e;
-  if (wide) {
+  if (nt == 8) {
+    static SmemLimit lim8;
+    e = raise_smem(tc::k_sketch_tc_bf16<BN, 8>, tc::smem_bytes<BN, 8>(), lim8);
+    if (e != cudaSuccess) return e;
+    tc::k_sketch_tc_bf16<BN, 8><<<grid, tc::kThreads, tc::smem_bytes<BN, 8>(), s>>>(
+        ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld, zstride, st, done);
+  } else if (nt == 4) {
     static SmemLimit lim4;
     e = raise_smem(tc::k_sketch_tc_bf16<BN, 4>, tc::smem_bytes<BN, 4>(), lim4);
     if (e != cudaSuccess) return e;

@@ -999,30 +999,34 @@ cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T
 // interleaved partial sums (c = j + p mod 4, ascending) combined as
 // (s0 + s1) + (s2 + s3) -- the order the batched kernel uses, so both give the same
 // bits.  Columns are independent solves of L x = e_j: four lanes per column, eight
-// columns per one-warp CTA, bt / 8 CTAs, L in each CTA's shared memory.  A single
-// CTA would run all bt^3/6 FP64 multiply-adds and bt block barriers on one SM
-// (GB300: about two FP64 instructions per clock per SM); here they spread over
-// bt/8 SMs.
+// columns per CTA, bt / 8 CTAs, L in each CTA's shared memory.  A single CTA would
+// run all bt^3/6 FP64 multiply-adds and bt block barriers on one SM (GB300: about
+// two FP64 instructions per clock per SM); here they spread over bt/8 SMs.  All
+// eight warps gather the pivot rows of L (one warp issuing the 2016 loads of a
+// 64 x 64 block took most of the kernel's time); the first warp then solves.
 constexpr int kLinvCols = 8;
+constexpr int kLinvThreads = 256;
 template <typename T>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kLinvThreads)
     k_linv_cols(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv, T* __restrict__ Linv,
                 const int32_t* done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
   T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt, strictly lower part
   T* xs = Lp + bt * bt;                    // [kLinvCols][bt]: column j0 + g of X
-  const int lane = threadIdx.x, g = lane >> 2, part = lane & 3;
+  const int lane = threadIdx.x & 31, g = lane >> 2, part = lane & 3;
   const int j0 = blockIdx.x * kLinvCols, j = j0 + g;
-  for (int e = lane; e < bt * bt; e += 32) {
+#pragma unroll 4
+  for (int e = threadIdx.x; e < bt * bt; e += kLinvThreads) {
     const int r = e / bt, c = e - r * bt;
     Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : T(0);
   }
-  for (int e = lane; e < kLinvCols * bt; e += 32) {
+  for (int e = threadIdx.x; e < kLinvCols * bt; e += kLinvThreads) {
     const int gg = e / bt, i = e - gg * bt;
     xs[e] = i == j0 + gg ? T(1) : T(0);
   }
-  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
   T* x = xs + g * bt;
   for (int i = j0 + 1; i < bt; ++i) {
     T acc = T(0);
@@ -1047,7 +1051,7 @@ cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, c
   if (smem > (size_t)227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = raise_smem(k_linv_cols<T>, smem, lim);
   if (e != cudaSuccess) return e;
-  k_linv_cols<T><<<(bt + kLinvCols - 1) / kLinvCols, 32, smem, s>>>(bt, S, lds, piv, Linv, done);
+  k_linv_cols<T><<<(bt + kLinvCols - 1) / kLinvCols, kLinvThreads, smem, s>>>(bt, S, lds, piv, Linv, done);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,8 @@
 //
 //   warp 0    one lane issues the TMA loads
 //   warp 1    allocates tensor memory; one lane issues the MMAs
-//   warps 2-5 scaled accumulation and the FP32 rows of G
+//   warps 2-  scaled accumulation and the FP32 rows of G (four warps for one
+//             64-row block of Omega per CTA, eight for four blocks)
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -31,37 +32,56 @@ namespace tc8 {
 using namespace tcx;
 
 constexpr int kBM = 128;       // columns of A per tile (MMA M)
-constexpr int kBN = 64;        // rows of Omega per tile (MMA N)
+constexpr int kBN = 64;        // rows of Omega per sub-tile (one sketch block)
 constexpr int kBK = 128;       // K per stage = one scale block
-constexpr int kStages = 4;        // 96 KB per CTA: two CTAs (2 x 256 tensor-memory columns) share an SM
-constexpr int kAcc = 4;        // accumulators of kBN columns in tensor memory
-constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = kAcc * kBN;
+constexpr int kStages = 4;
 
+// NT = 1: one 64-row block of Omega per CTA, four accumulators of 64 columns (256
+// tensor-memory columns: two CTAs share an SM), 4 stages of 24 KB, four epilogue
+// warps.  NT = 4: four blocks per CTA (a pass of several blocks reads each tile of
+// A once per CTA, not once per block) with one MMA of N = 256 per K step, two
+// accumulators of 256 columns (the SM's 512), 4 stages of 48 KB, eight epilogue
+// warps of 128 columns each.
+template <int NT>
+struct Cfg {
+  static constexpr int kAcc = NT == 1 ? 4 : 2;
+  static constexpr int kCols = NT * kBN;  // columns of one accumulator = MMA N
+  static constexpr int kEpiWarps = NT == 1 ? 4 : 8;
+  static constexpr int kWarpCols = kCols * 4 / kEpiWarps;  // columns an epilogue warp drains
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+  static constexpr int kMinBlocks = NT == 1 ? 2 : 1;
+  static constexpr uint32_t kTmemCols = kAcc * kCols;
+};
+
+template <int NT>
 struct Smem {
-  alignas(1024) uint8_t a[kStages][kBM * kBK];  // 16 KB per stage
-  alignas(1024) uint8_t w[kStages][kBN * kBK];  // 8 KB per stage
+  alignas(1024) uint8_t a[kStages][kBM * kBK];       // 16 KB per stage
+  alignas(1024) uint8_t w[kStages][NT * kBN * kBK];  // 8 KB per block per stage
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  uint64_t acc_full[kAcc];   // the MMAs of a block landed in accumulator a
-  uint64_t acc_empty[kAcc];  // the epilogue has read accumulator a
+  uint64_t acc_full[Cfg<NT>::kAcc];   // the MMAs of a scale block landed in accumulator a
+  uint64_t acc_empty[Cfg<NT>::kAcc];  // the epilogue has read accumulator a
   uint64_t drain;
   uint32_t tmem_base;
 };
 
-// Grid: x = tiles of A's columns, y = tiles of Omega rows, z = K splits of kchunk
-// (a multiple of kBK).  scale: column-major nbs x n block scales.  out: FP32
-// partial (n x rows, row stride out_ld) of split blockIdx.z.
-__global__ void __launch_bounds__(kThreads, 2)
+// Grid: x = tiles of A's columns, y = groups of NT 64-row blocks of Omega, z = K
+// splits of kchunk (a multiple of kBK).  scale: column-major nbs x n block scales.
+// out: FP32 partial (n x rows, row stride out_ld) of split blockIdx.z.  Every entry
+// gets the same sums (block sums in K order, scaled and added in block order)
+// whatever NT is.
+template <int NT>
+__global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kMinBlocks)
     k_sketch_tc_fp8(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
                     const float* __restrict__ scale, int64_t nbs, int n, int rows, int K, int kchunk,
                     float* __restrict__ out, int64_t out_ld, int64_t zstride, DevState* st, const int32_t* done) {
+  using C = Cfg<NT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
-  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM;
-  const int n0 = blockIdx.y * kBN;
+  const int n0 = blockIdx.y * C::kCols;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int nkb = (kend - kbeg + kBK - 1) / kBK;
@@ -71,14 +91,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    for (int a = 0; a < kAcc; ++a) {
+    for (int a = 0; a < C::kAcc; ++a) {
       mbar_init(&sm.acc_full[a], 1);
-      mbar_init(&sm.acc_empty[a], 4);  // one arrival per epilogue warp
+      mbar_init(&sm.acc_empty[a], C::kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(&sm.drain, 1);
     mbar_init_fence();
   }
-  if (warp == 1) tmem_alloc(&sm.tmem_base, kTmemCols);
+  if (warp == 1) tmem_alloc(&sm.tmem_base, C::kTmemCols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -90,27 +110,27 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
       if (kb >= kStages && !mbar_wait(&sm.empty[s], ((kb / kStages) + 1) & 1, st)) break;
-      mbar_expect_tx(&sm.full[s], (kBM + kBN) * kBK);
+      mbar_expect_tx(&sm.full[s], (kBM + C::kCols) * kBK);
       const int k0 = kbeg + kb * kBK;
       tma_load_2d(sm.a[s], &map_a, &sm.full[s], k0, m0);
-      tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);
+      tma_load_2d(sm.w[s], &map_w, &sm.full[s], k0, n0);  // one box of NT x 64 rows (at most 256)
       issued = kb + 1;
     }
     for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
       mbar_wait_drain(&sm.full[kb % kStages], (kb / kStages) & 1);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: block kb -> accumulator kb % kAcc
-    constexpr uint32_t idesc = idesc_e4m3(kBM, kBN);
+    // ---------------- MMA issuer: scale block kb -> accumulator kb % kAcc
+    constexpr uint32_t idesc = idesc_e4m3(kBM, C::kCols);
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages, a = kb % kAcc;
-      if (kb >= kAcc && !mbar_wait(&sm.acc_empty[a], ((kb / kAcc) + 1) & 1, st)) break;
+      const int s = kb % kStages, a = kb % C::kAcc;
+      if (kb >= C::kAcc && !mbar_wait(&sm.acc_empty[a], ((kb / C::kAcc) + 1) & 1, st)) break;
       if (!mbar_wait(&sm.full[s], (kb / kStages) & 1, st)) break;
       fence_after_sync();
       const uint64_t da = desc_sw128(sm.a[s]);
       const uint64_t dw = desc_sw128(sm.w[s]);
 #pragma unroll
       for (int kk = 0; kk < kBK / 32; ++kk)  // 32 E4M3 = 32 bytes per MMA
-        mma_e4m3(tmem + a * kBN, da + 2 * kk, dw + 2 * kk, idesc, kk != 0);
+        mma_e4m3(tmem + a * C::kCols, da + 2 * kk, dw + 2 * kk, idesc, kk != 0);
       mma_commit(&sm.empty[s]);
       mma_commit(&sm.acc_full[a]);
     }
@@ -118,40 +138,41 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_wait_drain(&sm.drain, 0);
   } else if (warp >= 2) {
     // ---------------- epilogue: scaled FP32 accumulation of the block sums
-    const int quarter = warp & 3;  // warps 2..5 own lane quarters 2,3,0,1
+    const int quarter = warp & 3;          // TMEM lanes this warp may read
+    const int col0 = ((warp - 2) >> 2) * C::kWarpCols;  // its columns of the accumulator
     const int row = m0 + quarter * 32 + lane;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + col0;
     const float* sc = scale + static_cast<int64_t>(row < n ? row : 0) * nbs + kbeg / kBK;
-    float acc[kBN];
+    float acc[C::kWarpCols];
 #pragma unroll
-    for (int c = 0; c < kBN; ++c) acc[c] = 0.f;
+    for (int c = 0; c < C::kWarpCols; ++c) acc[c] = 0.f;
     bool ok = true;
     float s_next = __ldg(sc);
     for (int kb = 0; kb < nkb; ++kb) {
-      const int a = kb % kAcc;
+      const int a = kb % C::kAcc;
       const float s_kb = s_next;
       if (kb + 1 < nkb) s_next = __ldg(sc + kb + 1);
-      if (!mbar_wait(&sm.acc_full[a], (kb / kAcc) & 1, st)) {
+      if (!mbar_wait(&sm.acc_full[a], (kb / C::kAcc) & 1, st)) {
         ok = false;
         break;
       }
       fence_after_sync();
 #pragma unroll
-      for (int cb = 0; cb < kBN; cb += 16) {
-        float v[16];
-        tmem_ld16(lane_base + a * kBN + cb, v);
+      for (int cb = 0; cb < C::kWarpCols; cb += 32) {  // 32 columns per wait on tensor memory
+        float v[32];
+        tmem_ld32(lane_base + a * C::kCols + cb, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[cb + i] = fmaf(v[i], s_kb, acc[cb + i]);
+        for (int i = 0; i < 32; ++i) acc[cb + i] = fmaf(v[i], s_kb, acc[cb + i]);
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
     }
     if (ok && row < n) {
-      float* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld + n0;
-      const int lim = rows - n0;
+      float* o = out + blockIdx.z * zstride + static_cast<int64_t>(row) * out_ld + n0 + col0;
+      const int lim = rows - n0 - col0;
 #pragma unroll
-      for (int c = 0; c < kBN; ++c)
+      for (int c = 0; c < C::kWarpCols; ++c)
         if (c < lim) o[c] = acc[c];
     }
   }
@@ -159,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, kTmemCols);
+    tmem_dealloc(tmem, C::kTmemCols);
   }
 }
 
@@ -321,25 +342,38 @@ int tc_fp8_effective_splits(int64_t m, int splits) {
   return (int)((m + kchunk - 1) / kchunk);
 }
 
+template <int NT>
+static cudaError_t launch_fp8(const CUtensorMap& ma, const CUtensorMap& mw, const float* scale, int64_t nbs,
+                              int64_t m, int64_t n, int64_t rows, int64_t kchunk, int nz, float* out, int64_t out_ld,
+                              int64_t zstride, DevState* st, const int32_t* done, cudaStream_t s) {
+  static_assert(sizeof(tc8::Smem<NT>) + 1024 <= 232448, "shared memory of k_sketch_tc_fp8 exceeds 227 KB");
+  const size_t smem = sizeof(tc8::Smem<NT>) + 1024;
+  static SmemLimit lim;
+  cudaError_t e = raise_smem(tc8::k_sketch_tc_fp8<NT>, smem, lim);
+  if (e != cudaSuccess) return e;
+  const int64_t ytiles = (rows + tc8::Cfg<NT>::kCols - 1) / tc8::Cfg<NT>::kCols;
+  if (ytiles > 65535 || nz > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((n + tc8::kBM - 1) / tc8::kBM), (unsigned)ytiles, (unsigned)nz);
+  tc8::k_sketch_tc_fp8<NT><<<grid, tc8::Cfg<NT>::kThreads, smem, s>>>(ma, mw, scale, nbs, (int)n, (int)rows, (int)m,
+                                                                     (int)kchunk, out, out_ld, zstride, st, done);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_sketch_fp8(const void* A, int64_t lda, int64_t m, int64_t n, const float* scale, const void* W,
                           int64_t ldw, int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits,
                           DevState* st, const int32_t* done, cudaStream_t s) {
+  // a pass of several blocks: four 64-row blocks of Omega per CTA
+  const int nt = rows > tc8::kBN ? 4 : 1;
   CUtensorMap ma, mw;
   if (!tc8::make_map_u8(&ma, A, m, n, lda, tc8::kBM)) return cudaErrorInvalidValue;
-  if (!tc8::make_map_u8(&mw, W, m, rows, ldw, tc8::kBN)) return cudaErrorInvalidValue;
+  if (!tc8::make_map_u8(&mw, W, m, rows, ldw, nt * tc8::kBN)) return cudaErrorInvalidValue;
   int64_t kchunk = (m + splits - 1) / splits;
   kchunk = (kchunk + tc8::kBK - 1) / tc8::kBK * tc8::kBK;
   const int nz = (int)((m + kchunk - 1) / kchunk);
   if (nz != splits) return cudaErrorInvalidValue;  // the reduction reads exactly `splits` partials
   const int64_t nbs = (m + tc8::kBK - 1) / tc8::kBK;
-  const size_t smem = sizeof(tc8::Smem) + 1024;
-  static SmemLimit lim;
-  cudaError_t e = raise_smem(tc8::k_sketch_tc_fp8, smem, lim);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((n + tc8::kBM - 1) / tc8::kBM), (unsigned)((rows + tc8::kBN - 1) / tc8::kBN), (unsigned)nz);
-  tc8::k_sketch_tc_fp8<<<grid, tc8::kThreads, smem, s>>>(ma, mw, scale, nbs, (int)n, (int)rows, (int)m, (int)kchunk,
-                                                         out, out_ld, zstride, st, done);
-  return cudaGetLastError();
+  if (nt == 4) return launch_fp8<4>(ma, mw, scale, nbs, m, n, rows, kchunk, nz, out, out_ld, zstride, st, done, s);
+  return launch_fp8<1>(ma, mw, scale, nbs, m, n, rows, kchunk, nz, out, out_ld, zstride, st, done, s);
 }
 
 cudaError_t norm2_fp8(int64_t m, int64_t n, const void* A, int64_t lda, const float* scale, double* part, int nparts,

@@ -150,6 +150,35 @@ def test_fp8_sketch_matches_product(B, m, n, rows):
     assert err < 2.0 ** -12, err
 
 
+def test_fp8_wide_pass_equals_block_passes(B):
+    """A pass of several blocks (one CTA runs one N = 256 MMA per scale block over
+    four 64-row blocks of Omega, two accumulators of 256 columns, eight epilogue
+    warps) gives every entry the same bits as passes of one block: the block sums,
+    their scaling and their order do not change (K = 1024: eight scale blocks, one
+    split for both; n and the last group of rows ragged)."""
+    rng = np.random.default_rng(9)
+    m, n, rows = 1024, 700, 600
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-4, 5, size=(1, n)))
+    A8 = B.quantize_fp8(B.colmajor(torch.from_numpy(A).cuda()))
+    Om8, _ = omega_fp8(B, rng.standard_normal((rows, m)))
+    G = B.id_sketch(A8, Om8)
+    for r0 in range(0, rows, 64):
+        g = B.id_sketch(A8, Om8[r0:r0 + 64])
+        assert torch.equal(G[:, r0:r0 + 64], g), r0
+
+
+def test_fp8_pass_size_does_not_change_result(B):
+    """Adaptive FP8 runs with four blocks per pass (the default), one block per
+    pass or a rank guess return the same J, X and k bit for bit."""
+    m, n, b = 6016, 1500, 64
+    A = lowrank(m, n, 300, 1e-3, 8)
+    A8 = B.quantize_fp8(B.colmajor(torch.from_numpy(A).cuda()))
+    base = B.id_adaptive(A8, 5e-2, block=b, seed=4, blocks_per_pass=1)
+    for kw in (dict(), dict(k0=400), dict(blocks_per_pass=3)):
+        g = B.id_adaptive(A8, 5e-2, block=b, seed=4, **kw)
+        assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X), kw
+
+
 def test_fp8_gaussian_rows_round_the_fp64_generator(B, orc):
     """E4M3 rows: the same counters and Box-Muller map, evaluated in FP32 on the
     leading 24 bits.  Against the FP64 generator rounded to E4M3: the same codes

@@ -996,62 +996,55 @@ cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T
 // ============================================================ re-blocking
 // Inverse X of the unit lower triangular L-hat(piv(0:bt), 0:bt) (bt x bt, row-major),
 // X(i, j) = -sum_{c=j}^{i-1} L(i, c) X(c, j) for j < i, each sum taken as four
-// interleaved partial sums (c = j + p mod 4, ascending) combined as
-// (s0 + s1) + (s2 + s3) -- the order the batched kernel uses, so both give the same
-// bits.  Columns are independent solves of L x = e_j: four lanes per column, eight
-// columns per CTA, bt / 8 CTAs, L in each CTA's shared memory.  A single CTA would
-// run all bt^3/6 FP64 multiply-adds and bt block barriers on one SM (GB300: about
-// two FP64 instructions per clock per SM); here they spread over bt/8 SMs.  All
-// eight warps gather the pivot rows of L (one warp issuing the 2016 loads of a
-// 64 x 64 block took most of the kernel's time); the first warp then solves.
-constexpr int kLinvCols = 8;
-constexpr int kLinvThreads = 256;
+// interleaved partial sums (c = j + p mod 4, ascending, one FMA per term from 0)
+// combined as (s0 + s1) + (s2 + s3) -- the order the batched kernel uses, so both
+// give the same bits.  Column j is one CTA with a thread per row i: once X(c, j)
+// is final (thread c has added every term c' < c), it is published and every row
+// i > c adds its term c to partial (c - j) mod 4.  The same sums in the same order
+// as a row-by-row solve, but the dependent chain is one step per row (a combine,
+// a block barrier and one FMA) instead of a row's whole dot product and two
+// shuffles.
 template <typename T>
-__global__ void __launch_bounds__(kLinvThreads)
+__global__ void __launch_bounds__(1024)
     k_linv_cols(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv, T* __restrict__ Linv,
                 const int32_t* done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (done != nullptr && *done) return;
-  T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt, strictly lower part
-  T* xs = Lp + bt * bt;                    // [kLinvCols][bt]: column j0 + g of X
-  const int lane = threadIdx.x & 31, g = lane >> 2, part = lane & 3;
-  const int j0 = blockIdx.x * kLinvCols, j = j0 + g;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < bt * bt; e += kLinvThreads) {
+  T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt: L(i, c) for j <= c < i
+  T* xs = Lp + bt * bt;                    // X(c, j), c >= j
+  const int j = blockIdx.x, i = threadIdx.x;
+  for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) {
     const int r = e / bt, c = e - r * bt;
-    Lp[e] = c < r ? S[(int64_t)piv[r] * lds + c] : T(0);
+    if (r > j && c >= j && c < r) Lp[e] = S[(int64_t)piv[r] * lds + c];
   }
-  for (int e = threadIdx.x; e < kLinvCols * bt; e += kLinvThreads) {
-    const int gg = e / bt, i = e - gg * bt;
-    xs[e] = i == j0 + gg ? T(1) : T(0);
-  }
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   __syncthreads();
-  if (threadIdx.x >= 32) return;
-  T* x = xs + g * bt;
-  for (int i = j0 + 1; i < bt; ++i) {
-    T acc = T(0);
-    if (j < i)
-      for (int c = j + part; c < i; c += 4) acc = fma(Lp[i * bt + c], x[c], acc);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (j < i && part == 0) x[i] = -acc;
-    __syncwarp();
+  for (int c = j; c < bt; ++c) {
+    if (i == c) xs[c] = c == j ? T(1) : -((s0 + s1) + (s2 + s3));
+    __syncthreads();
+    if (i > c && i < bt) {
+      const T l = Lp[i * bt + c], x = xs[c];
+      const int p = (c - j) & 3;
+      if (p == 0) s0 = fma(l, x, s0);
+      else if (p == 1) s1 = fma(l, x, s1);
+      else if (p == 2) s2 = fma(l, x, s2);
+      else s3 = fma(l, x, s3);
+    }
   }
-  for (int e = lane; e < kLinvCols * bt; e += 32) {
-    const int gg = e / bt, i = e - gg * bt;
-    if (j0 + gg < bt) Linv[i * bt + j0 + gg] = xs[e];
-  }
+  if (i < bt) Linv[i * bt + j] = i < j ? T(0) : xs[i];  // xs[i] was written by this thread
 }
 
 template <typename T>
 cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, const int32_t* done,
                  cudaStream_t s) {
   static SmemLimit lim;
-  const size_t smem = ((size_t)bt * bt + (size_t)kLinvCols * bt) * sizeof(T);
+  if (bt <= 0) return cudaSuccess;
+  if (bt > 1024) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)bt * bt + (size_t)bt) * sizeof(T);
   if (smem > (size_t)227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = raise_smem(k_linv_cols<T>, smem, lim);
   if (e != cudaSuccess) return e;
-  k_linv_cols<T><<<(bt + kLinvCols - 1) / kLinvCols, kLinvThreads, smem, s>>>(bt, S, lds, piv, Linv, done);
+  k_linv_cols<T><<<bt, (bt + 31) / 32 * 32, smem, s>>>(bt, S, lds, piv, Linv, done);
   return cudaGetLastError();
 }
 

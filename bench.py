@@ -88,6 +88,12 @@ WORKLOADS = {
     # the same batch at a tolerance FP32 can certify (at 1e-8 every FP32 problem runs to its rank cap)
     "batched_kernel_f32_tol1e-5": (2 ** 20, 4096, "kernel", {"leaf_max": 1024, "h": 0.3}, "f32", 1e-5, 32),
     "small_batched_kernel_f64": (2 ** 16, 512, "kernel", {"leaf_max": 512, "h": 0.3}, "f64", 1e-8, 32),
+    # fixed rank (randLUPP, Sec. 3.1): 2000 x 2000 FP64, s_j = 10^(-j/20), U and V Haar, one
+    # sketch of l = 120 Gaussian rows, k = 100 skeleton columns, the estimate from the l - k extra
+    # rows; plain FP64 and the FP64-accurate tensor-core sketch.  A is 32 MB (inside L2): L2 is
+    # flushed before every timed ID
+    "fixed_f64": (2000, 2000, "fixed", {"k": 100, "l": 120}, "f64", None, 64),
+    "fixed_f64emu": (2000, 2000, "fixed", {"k": 100, "l": 120}, "f64emu", None, 64),
 }
 DEFAULT_WORKLOAD = "adaptive_poly_f64emu"
 # Peaks of the plain-ALU paths, from unit counts x maximum SM clock (2070 MHz):
@@ -148,6 +154,10 @@ def make_input(name, device, seed=2310_09417 + 1):
             del At
             torch.cuda.synchronize()
             return A8
+        return At.t()
+    if kind == "fixed":
+        At = W.spectral_matrix_torch(m, n, W.spectrum("geometric", min(m, n)), seed, torch.float64, device)
+        torch.cuda.synchronize()
         return At.t()
     s = W.spectrum(kind, n, **kw)
     dtype = torch.float32 if dt in ("f32", "f32emu") else torch.float64
@@ -296,6 +306,9 @@ def run_reference(args, rank, world):
     if kind == "kernel":
         run_reference_batched(args, name, dev)
         return
+    if kind == "fixed":
+        run_reference_fixed(args, name, dev, world)
+        return
     if dev is not None:
         A = make_input(name, dev)
         A_host = host_f64(A)
@@ -317,6 +330,44 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": config_dict(name, None),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_fixed(args, name, dev, world):
+    """Reference arm for the fixed-rank workload: the oracle's whole fixed-rank ID of
+    the same matrix with the same Gaussian rows, once per step."""
+    import oracle
+    from paper_2310_09417_gb300 import workloads as W
+    m, n, kind, kw, dt, _, b = WORKLOADS[name]
+    k, l = kw["k"], kw["l"]
+    oracle.build()
+    if dev is not None:
+        A = make_input(name, dev)
+        A_host = host_f64(A)
+        del A
+    else:  # no GPU: the same family generated on the host
+        A_host = W.spectral_matrix(m, n, W.spectrum("geometric", min(m, n)), 1)
+    Om = oracle.gaussian_rows(2310_09417, 0, l, m)
+    if dt == "f64emu":
+        Om = on_grid(Om)
+    flops = fixed_flops(m, n, k, l, b)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.id_fixed_rank(A_host, Om, k)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    value = flops / sec / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = "oracle (plain C, FP64, OpenMP) on the whole fixed-rank ID, %.1f ms" % (sec * 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "us_per_id": 1e6 * sec,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "m": m, "n": n, "k": k, "l": l, "block": b,
+                                            "spectrum": "s_j = 10^(-j/20)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -685,6 +736,150 @@ def sketch_roofline(name, m, n, b, passes, blocks, sk_ms, sk_launches):
     return r
 
 
+def fixed_flops(m: int, n: int, k: int, l: int, b: int) -> float:
+    """Flops of a rank-k fixed-rank ID from l sketch rows: the sketch, per block of
+    pivots the triangular solve, Schur update and panel LU, the estimate rows'
+    Schur product and the interpolation solve."""
+    f = 2.0 * m * n * l
+    tb = 0
+    while tb < k:
+        w = min(b, k - tb)
+        f += w * tb * tb + 2.0 * (n - tb) * tb * w + (n - tb) * w * w
+        tb += w
+    f += 2.0 * (n - k) * k * (l - k) + float(k) * k * (n - k)
+    return f
+
+
+def run_fixed(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks):
+    """The fixed-rank workload: `steps` IDs of the 2000 x 2000 matrix, each timed with
+    its own CUDA events after an L2 flush (A fits in L2); the headline is the time
+    per ID in microseconds.  e2e: A copied in from pinned host memory and J, X
+    copied back inside each timed interval.  cpu_baseline / parity: the oracle's
+    fixed-rank ID on the same matrix and the same Gaussian rows (on the grid 2^-11
+    for the tensor-core path): J compared bit for bit, the relative errors of both
+    IDs and the estimates."""
+    import numpy as np
+    import torch
+
+    from paper_2310_09417_gb300 import binding as B
+    name = args.workload
+    m, n, kind, kw, dt, _, b = WORKLOADS[name]
+    k, l = kw["k"], kw["l"]
+    A = make_input(name, dev)
+    seed = 2310_09417 + 100 * rank
+    sprec = B.F64_EMU if dt == "f64emu" else None
+    opts = B._opts(A, block=b, tol=0.0, relative=False, k_max=k, k0=0, blocks_per_pass=1, seed=seed, omega=None,
+                   profile=True, sketch_prec=sprec)
+    ws = torch.empty(B.workspace_size(A, opts, l), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+
+    def one(A_in, profile=True):
+        return B.id_fixed_rank(A_in, k, l, block=b, seed=seed, profile=profile, workspace=ws, stream=stream,
+                               sketch_prec=sprec)
+
+    def timed(steps, fn):
+        evs = []
+        out = None
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in evs) / steps, out
+
+    for _ in range(max(args.warmup, 1)):
+        one(A)
+    torch.cuda.synchronize()
+    barrier()
+    results = []
+    with ClockSampler(local_gpu(dev)) as clk:
+        ms, _ = timed(args.steps, lambda: results.append(one(A)))
+    barrier()
+    ms = max_over_ranks(ms)
+    res = results[-1]
+    flops = fixed_flops(m, n, k, l, b)
+    sk_ms = sum(r.phase_ms["sketch"] for r in results) / args.steps
+    roof = sketch_roofline(name, m, n, b, 1, l / b, sk_ms, res.phase_launches["sketch"])
+    tot = max(1e-9, sum(res.phase_ms.values()))
+    roof.update({"phase_ms_per_step": {q: round(v, 4) for q, v in res.phase_ms.items()},
+                 "phase_share": {q: round(v / tot, 4) for q, v in res.phase_ms.items()},
+                 "timing": "library CUDA events on the launching stream around each phase, inside the timed "
+                           "region"})
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+        A_host.copy_(A.t())
+        A_dev = torch.empty((n, m), dtype=torch.float64, device=dev)
+        X_host = torch.empty((n, k), dtype=torch.float64, pin_memory=True)
+        J_host = torch.empty(k, dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            A_dev.copy_(A_host, non_blocking=True)
+            r = one(A_dev.t(), profile=False)
+            X_host.copy_(r.X.t(), non_blocking=True)  # the (n x k) buffer behind X
+            J_host.copy_(r.J, non_blocking=True)
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms, _ = timed(args.steps, e2e_step)
+        e_ms = max_over_ranks(e_ms)
+        e2e = {"value": sum_over_ranks(flops) / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+               "us_per_id": e_ms * 1e3, "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": k * n * 8 + 8 * k}
+    cpu, parity = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        A64 = host_f64(A)
+        Om = oracle.gaussian_rows(seed, 0, l, m)
+        if dt == "f64emu":
+            Om = on_grid(Om)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            r = oracle.id_fixed_rank(A64, Om, k)
+            reps += 1
+            if time.perf_counter() - t0 > 2.0:
+                break
+        sec = (time.perf_counter() - t0) / reps
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": flops / sec / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "oracle (plain C, FP64, OpenMP) on the whole fixed-rank ID of the same matrix and the "
+                         "same Gaussian rows, %d repetitions, %.1f ms each" % (reps, sec * 1e3)}
+        Jg = res.J.cpu().numpy()
+        Xg = res.X.double().cpu().numpy()
+        nA = oracle.fro_norm(A64)
+        eg = oracle.id_residual(A64, Jg, Xg) / nA
+        eo = oracle.id_residual(A64, r["J"], r["X"]) / nA
+        est_d = abs(res.est_err - r["est"]) / max(abs(r["est"]), 1e-300)
+        parity = {"J_identical": bool(np.array_equal(Jg, r["J"])), "J_mismatches": int(np.sum(Jg != r["J"])),
+                  "rel_error_gpu": eg, "rel_error_oracle": eo, "rel_error_diff": abs(eg - eo) / eo,
+                  "estimate_rel_diff": est_d,
+                  "bar": "J bit-exact; relative errors within 1e-10 of each other; estimate within 1e-10"}
+        parity["pass"] = bool(parity["J_identical"] and parity["rel_error_diff"] <= 1e-10 and est_d <= 1e-10)
+    if rank == 0:
+        line = {"metric": METRIC, "value": sum_over_ranks(flops) / (ms * 1e-3) / 1e9, "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "us_per_id": ms * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE_LABEL[dt], "data": "synthetic",
+                "config": {"workload": name, "m": m, "n": n, "spectrum": "s_j = 10^(-j/20)", "k": k, "l": l,
+                           "block": b, "precision": ("FP64 A, LU and X; FP64-accurate sketch on the BF16 tensor "
+                                                     "cores" if dt == "f64emu" else "FP64 sketch, LU and X"),
+                           "omega": "Philox4x64-10 Gaussian, generated on the device"
+                                    + (", rounded to the grid 2^-11" if dt == "f64emu" else ""),
+                           "l2": "A is 32 MB (inside L2): L2 flushed (256 MB written) before every timed ID",
+                           "parallelism": "replicas (one ID per GPU)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(r.launches for r in results), "clocks": clk.summary(),
+                "result": {"k": res.k, "status": res.status,
+                           "est_err_rel": res.est_err / res.norm_A if res.norm_A > 0 else 0.0,
+                           "gflop_per_id": flops / 1e9}, "parity": parity}
+        print(json.dumps(line), flush=True)
+
+
 def is_sparse(name):
     """Workloads sketched with the sparse-sign matrix (Sec. 5.1) instead of Gaussian rows."""
     return name.endswith("_sparse")
@@ -984,8 +1179,9 @@ def main():
     B.load()
 
     name = args.workload
-    if WORKLOADS[name][2] == "kernel":
-        run_batched(args, rank, world, dev, barrier, max_over_ranks, sum_over_ranks)
+    if WORKLOADS[name][2] in ("kernel", "fixed"):
+        (run_batched if WORKLOADS[name][2] == "kernel" else run_fixed)(args, rank, world, dev, barrier,
+                                                                        max_over_ranks, sum_over_ranks)
         if world > 1:
             dist.destroy_process_group()
         return

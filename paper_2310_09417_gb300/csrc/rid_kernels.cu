@@ -1003,7 +1003,9 @@ cudaError_t panel_lupp(const PanelCfg& cfg, int na, int w, int steps, int par, T
 // i > c adds its term c to partial (c - j) mod 4.  The same sums in the same order
 // as a row-by-row solve, but the dependent chain is one step per row (a combine,
 // a block barrier and one FMA) instead of a row's whole dot product and two
-// shuffles.
+// shuffles.  At least 256 threads gather L's pivot rows, eight loads in flight
+// per thread.
+constexpr int kLinvLoadThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(1024)
     k_linv_cols(int bt, const T* __restrict__ S, int64_t lds, const int32_t* __restrict__ piv, T* __restrict__ Linv,
@@ -1013,9 +1015,17 @@ __global__ void __launch_bounds__(1024)
   T* Lp = reinterpret_cast<T*>(smem_raw);  // bt x bt: L(i, c) for j <= c < i
   T* xs = Lp + bt * bt;                    // X(c, j), c >= j
   const int j = blockIdx.x, i = threadIdx.x;
-  for (int e = threadIdx.x; e < bt * bt; e += blockDim.x) {
-    const int r = e / bt, c = e - r * bt;
-    if (r > j && c >= j && c < r) Lp[e] = S[(int64_t)piv[r] * lds + c];
+  const int nt = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < bt * bt; e0 += 8 * nt) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt, r = e / bt, c = e - r * bt;
+      v[u] = (e < bt * bt && r > j && c >= j && c < r) ? S[(int64_t)piv[r] * lds + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u * nt < bt * bt) Lp[e0 + u * nt] = v[u];
   }
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   __syncthreads();
@@ -1044,12 +1054,17 @@ cudaError_t linv(int bt, const T* S, int64_t lds, const int32_t* piv, T* Linv, c
   if (smem > (size_t)227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = raise_smem(k_linv_cols<T>, smem, lim);
   if (e != cudaSuccess) return e;
-  k_linv_cols<T><<<bt, (bt + 31) / 32 * 32, smem, s>>>(bt, S, lds, piv, Linv, done);
+  const int threads = bt > kLinvLoadThreads ? (bt + 31) / 32 * 32 : kLinvLoadThreads;
+  k_linv_cols<T><<<bt, threads, smem, s>>>(bt, S, lds, piv, Linv, done);
   return cudaGetLastError();
 }
 
 // N(i, c) = sum_{c' >= c} L-hat(i, c') Linv(c', c) for non-pivot rows; the new
 // columns tb..tb+bt of X(:, act[i]) are N(i, :) (the new block of L2 L1^{-1}).
+// Each sum runs in ascending c' (one FMA per term from 0).  A thread takes the
+// columns q and bt-1-q of a row (bt + 1 terms together), so the lanes of a warp
+// do equal work: one thread per column spent a third of the FP64 pipe on the
+// short sums' idle lanes.
 template <typename T>
 __global__ void k_make_n(int na, int bt, const T* __restrict__ S, int64_t lds, const T* __restrict__ Linv,
                          const int32_t* __restrict__ pivmark, const int32_t* __restrict__ act, T* __restrict__ Nbuf,
@@ -1062,17 +1077,25 @@ __global__ void k_make_n(int na, int bt, const T* __restrict__ S, int64_t lds, c
   if (blockIdx.x == 0)
     for (int c = threadIdx.x; c < bt; c += blockDim.x) pivorig[c] = act[piv[c]];
   __syncthreads();
-  const int64_t total = (int64_t)na * bt;
+  const int hb = (bt + 1) / 2;
+  const int64_t total = (int64_t)na * hb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / bt;
-    const int c = (int)(e - i * bt);
+    const int64_t i = e / hb;
+    const int q = (int)(e - i * hb);
     if (pivmark[i]) continue;
     const T* l = S + i * lds;
-    T acc = T(0);
-    for (int cp = c; cp < bt; ++cp) acc = fma(l[cp], Li[cp * bt + c], acc);
-    Nbuf[i * bt + c] = acc;
-    X[(int64_t)act[i] * ldx + tb + c] = acc;
+    T* xr = X + (int64_t)act[i] * ldx + tb;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int c = h == 0 ? q : bt - 1 - q;
+      if (h == 1 && c == q) break;  // the middle column of an odd bt
+      T acc = T(0);
+#pragma unroll 8
+      for (int cp = c; cp < bt; ++cp) acc = fma(l[cp], Li[cp * bt + c], acc);
+      Nbuf[i * bt + c] = acc;
+      xr[c] = acc;
+    }
   }
 }
 
@@ -1083,7 +1106,7 @@ cudaError_t make_n(int na, int bt, const T* S, int64_t lds, const T* Linv, const
   static SmemLimit lim;
   cudaError_t e = raise_smem(k_make_n<T>, (size_t)bt * bt * sizeof(T), lim);
   if (e != cudaSuccess) return e;
-  int64_t blocks = ((int64_t)na * bt + 255) / 256;
+  int64_t blocks = ((int64_t)na * ((bt + 1) / 2) + 255) / 256;
   if (blocks > 1216) blocks = 1216;
   if (blocks < 1) blocks = 1;
   k_make_n<T><<<(int)blocks, 256, (size_t)bt * bt * sizeof(T), s>>>(na, bt, S, lds, Linv, pivmark, act, Nbuf, X,
@@ -1092,6 +1115,7 @@ cudaError_t make_n(int na, int bt, const T* S, int64_t lds, const T* Linv, const
 }
 
 // Stable removal of this round's pivots from the active list; one block.
+constexpr int kCompactPer = 8;
 __global__ void __launch_bounds__(1024)
     k_compact(int na, int bt, const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
               int32_t* __restrict__ pivmark, const int32_t* __restrict__ piv, int64_t* __restrict__ J,
@@ -1109,30 +1133,47 @@ __global__ void __launch_bounds__(1024)
   }
   if (tid == 0) s_base = 0;
   __syncthreads();
-  for (int start = 0; start < na; start += blockDim.x) {
-    const int i = start + tid;
-    const bool keep = i < na && pivmark[i] == 0;
-    const unsigned ball = __ballot_sync(0xffffffffu, keep);
-    const int before = __popc(ball & ((1u << lane) - 1u));
-    if (lane == 0) s_warp[warp] = __popc(ball);
+  // kCompactPer consecutive entries per thread (their loads all in flight), an
+  // exclusive scan of the per-thread counts; the kept entries keep their order
+  const int nw = blockDim.x >> 5;
+  for (int start = 0; start < na; start += blockDim.x * kCompactPer) {
+    const int i0 = start + tid * kCompactPer;
+    int32_t a[kCompactPer], pm[kCompactPer];
+#pragma unroll
+    for (int u = 0; u < kCompactPer; ++u) {
+      const bool in = i0 + u < na;
+      pm[u] = in ? pivmark[i0 + u] : 1;
+      a[u] = in ? act_in[i0 + u] : 0;
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < kCompactPer; ++u) cnt += pm[u] == 0;
+    int incl = cnt;  // inclusive scan over the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      const int nw = blockDim.x >> 5;
       int v = lane < nw ? s_warp[lane] : 0;
-      // inclusive scan over warp totals
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, v, off);
         if (lane >= off) v += t;
       }
-      s_warp[lane] = v;  // inclusive prefix
+      s_warp[lane] = v;  // inclusive prefix over the warps
     }
     __syncthreads();
-    const int wbase = warp == 0 ? 0 : s_warp[warp - 1];
-    if (keep) act_out[s_base + wbase + before] = act_in[i];
-    if (i < na) pivmark[i] = 0;
+    int pos = s_base + (warp == 0 ? 0 : s_warp[warp - 1]) + incl - cnt;
+#pragma unroll
+    for (int u = 0; u < kCompactPer; ++u) {
+      if (pm[u] == 0) act_out[pos++] = a[u];
+      if (i0 + u < na) pivmark[i0 + u] = 0;
+    }
     __syncthreads();
-    if (tid == 0) s_base += s_warp[(blockDim.x >> 5) - 1];
+    if (tid == 0) s_base += s_warp[nw - 1];
     __syncthreads();
   }
 }

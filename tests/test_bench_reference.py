@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("workload", ["small_poly_f64", "small_batched_kernel_f64"])
+@pytest.mark.parametrize("workload", ["small_poly_f64", "small_batched_kernel_f64", "fixed_f64"])
 def test_reference_arm_line(workload):
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",

@@ -269,31 +269,6 @@ __device__ __forceinline__ unsigned long long abs_bits(float x) {
 __device__ __forceinline__ int exp_above(unsigned long long b, double) { return exp_above_f64bits(b); }
 __device__ __forceinline__ int exp_above(unsigned long long b, float) { return exp_above_f32bits((unsigned int)b); }
 
-// Four consecutive elements k .. k+3 of a row (zero past K): one or two 16-byte loads
-// when the rows are 16-byte aligned and all four lie in the row.
-template <typename T>
-__device__ __forceinline__ void load4(const T* __restrict__ row, int k, int K, bool vec, T (&v)[4]) {
-  if (vec && k + 3 < K) {
-    if constexpr (sizeof(T) == 8) {
-      const double2 a = __ldg(reinterpret_cast<const double2*>(row + k));
-      const double2 b = __ldg(reinterpret_cast<const double2*>(row + k + 2));
-      v[0] = a.x;
-      v[1] = a.y;
-      v[2] = b.x;
-      v[3] = b.y;
-    } else {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(row + k));
-      v[0] = a.x;
-      v[1] = a.y;
-      v[2] = a.z;
-      v[3] = a.w;
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = k + e < K ? row[k + e] : T(0);
-  }
-}
-
 template <typename T, int KD>
 __global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const T* __restrict__ src, int64_t lds,
                              const int32_t* __restrict__ idx, __nv_bfloat16* __restrict__ D, int64_t plane,
@@ -302,26 +277,22 @@ __global__ void k_slice_rows(int M, int K, int Kq, int64_t Kp, const T* __restri
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool vec = (lds % (int64_t)(16 / sizeof(T))) == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
   for (int64_t r = w0; r < M; r += nw) {
     const T* row = src + (int64_t)(idx ? idx[r] : r) * lds;
     // four consecutive k per lane: a warp covers 128 elements per step
     unsigned long long mx = 0;
     for (int k = 4 * lane; k < K; k += 128) {
-      T v[4];
-      load4(row, k, K, vec, v);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) mx = max(mx, abs_bits(v[e]));
+      for (int e = 0; e < 4; ++e)
+        if (k + e < K) mx = max(mx, abs_bits(row[k + e]));
     }
     for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     const int e = exp_above(mx, T(0));
     if (lane == 0) ex[r] = e;
     for (int k = 4 * lane; k < Kq; k += 128) {  // Kq is a multiple of 64
-      T v[4];
-      load4(row, k, K, vec, v);
       long long F[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) F[q] = k + q < K ? fixed_of<KD>(v[q], e) : 0ll;
+      for (int q = 0; q < 4; ++q) F[q] = k + q < K ? fixed_of<KD>(row[k + q], e) : 0ll;
       write_digits4<KD>(F, D + r * Kp + k, plane);
     }
   }

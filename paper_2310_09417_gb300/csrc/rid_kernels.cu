@@ -129,7 +129,8 @@ __global__ void k_norm2_partial(int64_t m, int64_t n, const T* __restrict__ A, i
     const T* a = A + j * lda;
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
       const double v = to_double(a[i]);
-      finite = finite && isfinite(v);
+      // finiteness from the exponent bits (integer pipe): one FP64 instruction per element
+      finite = finite && ((__double_as_longlong(v) >> 52) & 0x7FF) != 0x7FF;
       acc += v * v;
     }
   }

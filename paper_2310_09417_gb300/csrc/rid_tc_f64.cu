@@ -261,16 +261,31 @@ __global__ void k_colexp(const double* __restrict__ A, int64_t lda, int64_t m, i
 // one 16 KB run of memory (a column-major plane would cost kBM separate 128-byte
 // segments per box), and a chunk of one slice is kChunkSteps consecutive tiles.
 // Rows past m and columns past n are zero digits.
+// A CTA takes whole tiles (the tile's column and K block once per tile, no 64-bit
+// division per element); a thread four consecutive k of one column, its digits
+// written as 8-byte runs per plane.
 __global__ void k_split_digits(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t nkb,
                                int64_t ntl, const int32_t* __restrict__ E, __nv_bfloat16* __restrict__ D) {
-  constexpr int64_t kTile = (int64_t)kBM * kBK;
-  const int64_t slice = nkb * ntl * kTile;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slice;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t tb = e / kTile, w = e - tb * kTile;
+  constexpr int kTile = kBM * kBK;
+  const int64_t tiles = nkb * ntl;
+  const int64_t slice = tiles * kTile;
+  for (int64_t tb = blockIdx.x; tb < tiles; tb += gridDim.x) {
     const int64_t t = tb / nkb, kb = tb - t * nkb;
-    const int64_t j = t * kBM + w / kBK, i = kb * kBK + (w % kBK);
-    write_digits<kSlices>(i < m && j < n ? fixed_of<kSlices>(A[i + j * lda], E[j]) : 0ll, D + e, slice);
+    __nv_bfloat16* dt = D + tb * kTile;
+    for (int w = 4 * (int)threadIdx.x; w < kTile; w += 4 * (int)blockDim.x) {
+      const int64_t j = t * kBM + w / kBK, i = kb * kBK + (w % kBK);
+      long long F[4];
+      if (j < n) {
+        const double* col = A + j * lda;
+        const int e = E[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F[q] = i + q < m ? fixed_of<kSlices>(col[i + q], e) : 0ll;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F[q] = 0ll;
+      }
+      write_digits4<kSlices>(F, dt + w, slice);
+    }
   }
 }
 
@@ -496,7 +511,7 @@ cudaError_t f64emu_prepare(const double* A, int64_t lda, int64_t m, int64_t n, i
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t nkb = digit_kblocks(m), ntl = digit_tiles(n);
-  int64_t blocks = (nkb * ntl * tc64::kBM * tc64::kBK + 255) / 256;
+  int64_t blocks = nkb * ntl;  // tiles
   if (blocks > 8192) blocks = 8192;
   tc64::k_split_digits<<<(int)blocks, 256, 0, s>>>(A, lda, m, n, nkb, ntl, colexp,
                                                    static_cast<__nv_bfloat16*>(digits));

@@ -112,7 +112,7 @@ typedef struct {
   int64_t k0;           /* rows of the first sketch pass (a rank guess, e.g. from the
                            learned predictor); 0 = one block.  Same J, X, k as k0 = 0. */
   int64_t blocks_per_pass; /* sketch blocks drawn per later pass over A; 0 = automatic:
-                              2 on the ID_F64_EMU tensor-core sketch, 4 on the BF16
+                              2 on the ID_F64_EMU tensor-core sketch, 8 on the BF16
                               and FP8 tensor-core sketches, 1 elsewhere (J, X and k
                               do not depend on it) */
   uint64_t seed;        /* key of the Philox4x64-10 generator of Omega */

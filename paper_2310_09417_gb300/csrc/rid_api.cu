@@ -192,12 +192,12 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     p->rows_first = imin(first, max_blocks) * b;
     // 0 = automatic: two blocks per pass on the FP64-accurate tensor-core sketch (the
     // CTAs of a pass's two blocks read each tile of A's digits together, the second
-    // from L2), four on the BF16 and FP8 tensor-core sketches (one CTA runs the MMAs
-    // of four 64-row blocks on each stage of A: A is read once per four blocks), one
-    // elsewhere
+    // from L2), eight on the BF16 and FP8 tensor-core sketches (a CTA runs the MMAs
+    // of four 64-row blocks on each stage of A, and the two CTAs of a tile of A share
+    // it through L2: A is read once per eight blocks), one elsewhere
     const int64_t per = o->blocks_per_pass > 0
                             ? o->blocks_per_pass
-                            : (p->sparse ? 1 : (path == 65 ? 2 : ((path == 16 || path == 8) ? 4 : 1)));
+                            : (p->sparse ? 1 : (path == 65 ? 2 : ((path == 16 || path == 8) ? 8 : 1)));
     p->rows_pass = imin(per, max_blocks) * b;
     p->wmax = b;
     p->max_rounds = max_blocks + 1;

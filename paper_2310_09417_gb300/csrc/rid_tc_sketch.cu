@@ -32,9 +32,8 @@ namespace tc {
 
 constexpr int kBM = 128;        // columns of A per tile (MMA M)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
-// stages per CTA: 4 of (16 + 8 NT) KB up to four sub-tiles of Omega (two CTAs per
-// SM at one), 2 of 80 KB at eight
-__host__ __device__ constexpr int stages_for(int nt) { return nt >= 8 ? 2 : 4; }
+// stages per CTA: 4 of (16 + 8 NT) KB, NT = 1 (two CTAs per SM) or 4 sub-tiles of Omega
+__host__ __device__ constexpr int stages_for(int) { return 4; }
 constexpr int kWBox = 256;     // rows of Omega per TMA box (the box limit)
 constexpr int kThreads = 192;   // 6 warps
 
@@ -240,9 +239,12 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
                            int64_t rows, float* out, int64_t out_ld, int64_t zstride, int splits, DevState* st,
                            const int32_t* done, cudaStream_t s) {
   constexpr int BN = 64;
-  // passes of more than one block: four BN-row sub-tiles of Omega per CTA
-  // passes of several blocks: four or eight BN-row sub-tiles of Omega per CTA
-  const int nt = rows > 4 * BN ? 8 : (rows > BN ? 4 : 1);
+  // passes of several blocks: four BN-row sub-tiles of Omega per CTA, and as many
+  // CTAs per tile of A as groups of four blocks (they run together, x fastest, and
+  // share the tile through L2).  Eight sub-tiles per CTA (two N = 256 MMAs per step,
+  // two stages of 80 KB) measured slower: 11.4 against 9.4 ms of sketch per ID at
+  // eight blocks per pass, 16.3 against 14.2 ms for one pass of 37 blocks.
+  const int nt = rows > BN ? 4 : 1;
   CUtensorMap ma, mw;
   if (!tc::make_map_bf16(&ma, A, m, n, lda, tc::kBM)) return cudaErrorInvalidValue;
   if (!tc::make_map_bf16(&mw, W, m, rows, ldw, nt * BN < tc::kWBox ? nt * BN : tc::kWBox)) return cudaErrorInvalidValue;
@@ -253,13 +255,7 @@ cudaError_t tc_sketch_bf16(const void* A, int64_t lda, int64_t m, int64_t n, con
   if (ytiles > 65535 || nz > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((rows + nt * BN - 1) / (nt * BN)), (unsigned)ytiles, (unsigned)nz);
   cudaError_t e;
-  if (nt == 8) {
-    static SmemLimit lim8;
-    e = raise_smem(tc::k_sketch_tc_bf16<BN, 8>, tc::smem_bytes<BN, 8>(), lim8);
-    if (e != cudaSuccess) return e;
-    tc::k_sketch_tc_bf16<BN, 8><<<grid, tc::kThreads, tc::smem_bytes<BN, 8>(), s>>>(
-        ma, mw, (int)n, (int)rows, (int)m, kchunk, out, out_ld, zstride, st, done);
-  } else if (nt == 4) {
+  if (nt == 4) {
     static SmemLimit lim4;
     e = raise_smem(tc::k_sketch_tc_bf16<BN, 4>, tc::smem_bytes<BN, 4>(), lim4);
     if (e != cudaSuccess) return e;

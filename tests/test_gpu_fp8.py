@@ -168,7 +168,7 @@ def test_fp8_wide_pass_equals_block_passes(B):
 
 
 def test_fp8_pass_size_does_not_change_result(B):
-    """Adaptive FP8 runs with four blocks per pass (the default), one block per
+    """Adaptive FP8 runs with eight blocks per pass (the default), one block per
     pass or a rank guess return the same J, X and k bit for bit."""
     m, n, b = 6016, 1500, 64
     A = lowrank(m, n, 300, 1e-3, 8)

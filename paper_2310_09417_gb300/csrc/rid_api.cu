@@ -194,10 +194,11 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     // CTAs of a pass's two blocks read each tile of A's digits together, the second
     // from L2), eight on the BF16 and FP8 tensor-core sketches (a CTA runs the MMAs
     // of four 64-row blocks on each stage of A, and the two CTAs of a tile of A share
-    // it through L2: A is read once per eight blocks), one elsewhere
+    // it through L2: A is read once per eight blocks), four on the FP32-accurate sketch
+    // (its CTAs of a pass share each tile of A's digits through L2), one elsewhere
     const int64_t per = o->blocks_per_pass > 0
                             ? o->blocks_per_pass
-                            : (p->sparse ? 1 : (path == 65 ? 2 : ((path == 16 || path == 8) ? 8 : 1)));
+                            : (p->sparse ? 1 : (path == 65 ? 2 : ((path == 16 || path == 8) ? 8 : (path == 33 ? 4 : 1))));
     p->rows_pass = imin(per, max_blocks) * b;
     p->wmax = b;
     p->max_rounds = max_blocks + 1;

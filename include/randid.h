@@ -113,8 +113,9 @@ typedef struct {
                            learned predictor); 0 = one block.  Same J, X, k as k0 = 0. */
   int64_t blocks_per_pass; /* sketch blocks drawn per later pass over A; 0 = automatic:
                               2 on the ID_F64_EMU tensor-core sketch, 4 on
-                              ID_F32_EMU, 8 on the BF16 and FP8 tensor-core sketches,
-                              1 elsewhere (J, X and k do not depend on it) */
+                              ID_F32_EMU and on the FP32 sparse-sign sketch, 8 on the
+                              BF16 and FP8 tensor-core sketches, 1 elsewhere (J, X and
+                              k do not depend on it) */
   uint64_t seed;        /* key of the Philox4x64-10 generator of Omega */
   /* Optional caller-supplied sketching matrix: DEVICE, row-major omega_rows x m
      with row stride ld_omega >= m, dtype sketch_prec.  Block t uses rows

@@ -195,10 +195,13 @@ int make_plan(const id_matrix* A, const id_opts* o, int64_t k, int64_t l, Plan* 
     // from L2), eight on the BF16 and FP8 tensor-core sketches (a CTA runs the MMAs
     // of four 64-row blocks on each stage of A, and the two CTAs of a tile of A share
     // it through L2: A is read once per eight blocks), four on the FP32-accurate sketch
-    // (its CTAs of a pass share each tile of A's digits through L2), one elsewhere
+    // (its CTAs of a pass share each tile of A's digits through L2) and on the FP32
+    // sparse-sign gather (its tiles of A staged once for four blocks' lists), one
+    // elsewhere (the FP64 sparse gather's exact sums measured slower at two and four)
     const int64_t per = o->blocks_per_pass > 0
                             ? o->blocks_per_pass
-                            : (p->sparse ? 1 : (path == 65 ? 2 : ((path == 16 || path == 8) ? 8 : (path == 33 ? 4 : 1))));
+                            : (p->sparse ? (sparse_kind(path) == 0 ? 4 : 1)
+                                         : (path == 65 ? 2 : ((path == 16 || path == 8) ? 8 : (path == 33 ? 4 : 1))));
     p->rows_pass = imin(per, max_blocks) * b;
     p->wmax = b;
     p->max_rounds = max_blocks + 1;

@@ -133,3 +133,18 @@ def test_sparse_sign_unsupported_paths(B):
     with pytest.raises(B.IDError) as e:
         B.id_adaptive(A, 1e-3, block=16, omega_kind=B.OMEGA_SPARSE_SIGN, zeta=17)
     assert e.value.code == -2
+
+
+def test_f32_sparse_sign_pass_size_does_not_change_result(B):
+    """FP32 A with the sparse-sign sketch: four blocks per pass (the default), one
+    block per pass and a rank guess give the same J, X and k bit for bit (the
+    split count depends on the problem only, and every entry's gather sums run in
+    the same order whatever the pass holds)."""
+    A = W.spectral_matrix(2100, 700, W.spectrum("poly", 700), seed=5)
+    Ad = dev_cm(A, torch.float32)
+    kw = dict(block=64, seed=13, omega_kind=B.OMEGA_SPARSE_SIGN)
+    base = B.id_adaptive(Ad, 1e-3, blocks_per_pass=1, **kw)
+    assert 64 < base.k < 700
+    for extra in (dict(), dict(k0=300), dict(blocks_per_pass=3)):
+        g = B.id_adaptive(Ad, 1e-3, **kw, **extra)
+        assert g.k == base.k and torch.equal(g.J, base.J) and torch.equal(g.X, base.X), extra

@@ -190,8 +190,8 @@ def evaluate_large(params, count, family, seed, tols=(1e-4, 1e-8), device="cuda"
     per pass however many blocks the pass holds (tolerances above BF16's 2^-8),
     stacked `tall` times (tall_bf16) to the shape of the 100000 x 20000
     configuration.  The seeded loop saves passes over A, not rounds: each block is
-    still factored on its own, and the plain loop's automatic passes of four blocks
-    already read A once per four blocks."""
+    still factored on its own, and the plain loop's automatic passes of eight blocks
+    already read A once per eight blocks."""
     if precision not in ("f64emu", "bf16"):
         raise ValueError("precision must be 'f64emu' or 'bf16'")
     rng = np.random.default_rng(seed)

@@ -127,7 +127,7 @@ def test_committed_network_on_held_out_family_at_scale(B):
     100000 x 20000 configuration's shape on the BF16 tensor-core path the seeded
     loop returns the plain loop's J, X and k with the same tolerance-miss rate in
     far fewer passes over A.  Its wall time stays within 10 % of the plain loop's:
-    the plain loop's automatic four-block passes already read A once per four
+    the plain loop's automatic eight-block passes already read A once per eight
     blocks, and the seeded loop's one large pass is bound by the tensor cores'
     operand fill rather than by HBM (CUDA events, summed over the problems)."""
     import os
